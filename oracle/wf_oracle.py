@@ -1,0 +1,444 @@
+"""FP64 CPU oracle for the Wiener-filter MAP objective, its solution and the
+simulation-based band powers of Horowitz, Seljak & Aslanyan (arXiv:1810.00503).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import or run this module.  The GPU library
+never calls it and shares no code with it: this file uses full-plane complex
+numpy FFTs, a pixel-basis real state vector and dense linear algebra, written
+to be read against the paper, not to be fast.
+
+Variables
+---------
+The paper minimises chi^2(s) = s^T S^-1 s + (d - R s)^T N^-1 (d - R s) (Sec. 2.2,
+eq. eq_chi).  Here S is diagonal in Fourier space with per-mode variance P_m and
+R = M (mask).  We use the whitened real pixel field z, s = A z with
+A = U^-1 diag(sqrt P) U (U the unitary 2-D DFT), which turns the prior into
+z^T z.  With W = M N^-1 (diagonal, zero on masked pixels):
+
+    chi^2(z) = z^T z + (d - A z)^T W (d - A z)
+    grad     = 2 (z - A^T W (d - A z))       (twice eq. eq_cost)
+
+For the joint E/B shear case (App. C) the operator is two-channel:
+A = U^-1 R(k) diag(sqrt P_E, sqrt P_B) U with the per-mode Kaiser-Squires
+rotation R(k) = [[c, -s], [s, c]], c = (kx^2 - ky^2)/k^2, s = 2 kx ky / k^2.
+The paper's derivative operator equals this up to -k^2, absorbed into P.  The
+odd term s is set to 0 on the Nyquist row and column (where k and -k alias),
+the usual convention for odd spectral derivatives; R = I at k = 0.
+
+Pins (what fixes this file independently of itself) live in
+tests/test_oracle_pins.py: naive O(n^4) DFT, Parseval, unmasked closed form
+S/(S+N), Woodbury agreement of the two dense Wiener-filter forms, exact central
+differences of a quadratic, the lambda_min >= 1 certificate, analytic band
+terms without a mask, and the Fisher identity Cov(E) = F.
+Parity unpinned: iteration counts and chi^2-versus-iteration curves, because the
+paper gives them only as figures.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Fourier machinery (full plane, unitary)
+# ---------------------------------------------------------------------------
+
+
+def dft2_naive(x: np.ndarray) -> np.ndarray:
+    """Unitary 2-D DFT by the definition, O(n^4): X[ky,kx] = (1/n) sum
+    x[y,x] exp(-2 pi i (ky y + kx x)/n).  For pinning the FFT-based code."""
+    n = x.shape[-1]
+    out = np.zeros(x.shape, dtype=np.complex128)
+    idx = np.arange(n)
+    for ky in range(n):
+        ey = np.exp(-2j * np.pi * ky * idx / n)
+        for kx in range(n):
+            ex = np.exp(-2j * np.pi * kx * idx / n)
+            out[..., ky, kx] = np.einsum("...yx,y,x->...", x, ey, ex) / n
+    return out
+
+
+def fft2u(x):
+    return np.fft.fft2(x, norm="ortho")
+
+
+def ifft2u(X):
+    return np.fft.ifft2(X, norm="ortho")
+
+
+def signed_modes(n: int):
+    f = np.fft.fftfreq(n, d=1.0 / n)
+    my, mx = np.meshgrid(f, f, indexing="ij")
+    return my, mx
+
+
+def ks_rotation(n: int):
+    """Per-mode Kaiser-Squires cosine and sine (App. C, E/B operator), full plane."""
+    my, mx = signed_modes(n)
+    k2 = mx * mx + my * my
+    c = np.ones((n, n))
+    s = np.zeros((n, n))
+    nz = k2 > 0
+    c[nz] = (mx[nz] ** 2 - my[nz] ** 2) / k2[nz]
+    s[nz] = 2.0 * mx[nz] * my[nz] / k2[nz]
+    nyq = (np.abs(mx) == n // 2) | (np.abs(my) == n // 2)
+    s[nyq] = 0.0
+    return c, s
+
+
+def apply_A(z: np.ndarray, P: np.ndarray) -> np.ndarray:
+    """Signal map s = A z for a whitened real field z (C, n, n); P (C, n, n)."""
+    C, n = z.shape[0], z.shape[-1]
+    Z = fft2u(z) * np.sqrt(P)
+    if C == 2:
+        c, s = ks_rotation(n)
+        Z = np.stack([c * Z[0] - s * Z[1], s * Z[0] + c * Z[1]])
+    x = ifft2u(Z)
+    return x.real
+
+
+def apply_At(x: np.ndarray, P: np.ndarray) -> np.ndarray:
+    """Transpose of apply_A: A^T = U^-1 diag(sqrt P) R(k)^T U."""
+    C, n = x.shape[0], x.shape[-1]
+    X = fft2u(x)
+    if C == 2:
+        c, s = ks_rotation(n)
+        X = np.stack([c * X[0] + s * X[1], -s * X[0] + c * X[1]])
+    return ifft2u(X * np.sqrt(P)).real
+
+
+def synthesize_data(z, noise, mask, P):
+    """Step 2 of the paper's procedure (Sec. 2.5): d = M (A z + n)."""
+    return (apply_A(z, P) + noise) * mask[None]
+
+
+# ---------------------------------------------------------------------------
+# Objective and gradient (Sec. 2.2, eq_chi and eq_cost)
+# ---------------------------------------------------------------------------
+
+
+def chi2(z, d, W, P) -> float:
+    r = d - apply_A(z, P)
+    return float(np.sum(z * z) + np.sum(r * W * r))
+
+
+def chi2_parts(z, d, W, P):
+    """(prior z^T z, data (d - Az)^T W (d - Az))."""
+    r = d - apply_A(z, P)
+    return float(np.sum(z * z)), float(np.sum(r * W * r))
+
+
+def grad(z, d, W, P) -> np.ndarray:
+    r = d - apply_A(z, P)
+    return 2.0 * (z - apply_At(W * r, P))
+
+
+def hess_vec(v, W, P) -> np.ndarray:
+    """Full Hessian of chi^2 times v: 2 (I + A^T W A) v (twice eq_curv)."""
+    return 2.0 * (v + apply_At(W * apply_A(v, P), P))
+
+
+# ---------------------------------------------------------------------------
+# Dense Wiener filter (App. A, eq. eq:wiener), small maps only
+# ---------------------------------------------------------------------------
+
+
+def dense_operator(P: np.ndarray) -> np.ndarray:
+    """A as a dense (C n^2) x (C n^2) matrix, column j = A e_j."""
+    C, n = P.shape[0], P.shape[-1]
+    N = C * n * n
+    A = np.empty((N, N))
+    e = np.zeros(N)
+    for j in range(N):
+        e[j] = 1.0
+        A[:, j] = apply_A(e.reshape(C, n, n), P).ravel()
+        e[j] = 0.0
+    return A
+
+
+def dense_wf_whitened(d, W, P, A=None):
+    """Minimiser of chi^2 from the normal equations (I + A^T W A) z = A^T W d,
+    solved by Cholesky.  Returns z* (C, n, n)."""
+    A = dense_operator(P) if A is None else A
+    w = W.ravel()
+    H = np.eye(A.shape[0]) + A.T @ (w[:, None] * A)
+    b = A.T @ (w * d.ravel())
+    L = np.linalg.cholesky(H)
+    z = np.linalg.solve(L.T, np.linalg.solve(L, b))
+    return z.reshape(d.shape)
+
+
+def dense_wf_covariance(d, mask, Ninv, P, A=None):
+    """Paper's form s_hat = S R^dagger C^-1 d (App. A, eq:wiener) over the
+    observed pixels only: S = A A^T (pixel signal covariance), R = mask
+    selection, C = R S R^T + N.  Returns (x*, z*) with x* the Wiener-filtered
+    signal map and z* = A^T R^T C^-1 d the same solution in whitened variables."""
+    A = dense_operator(P) if A is None else A
+    obs = np.broadcast_to(mask[None] == 1, d.shape).ravel()
+    Ao = A[obs]
+    Cmat = Ao @ Ao.T + np.diag(1.0 / Ninv.ravel()[obs])
+    L = np.linalg.cholesky(Cmat)
+    y = np.linalg.solve(L.T, np.linalg.solve(L, d.ravel()[obs]))
+    S_cols = A @ Ao.T                      # S R^T = A A^T restricted to observed columns
+    x = (S_cols @ y).reshape(d.shape)
+    z = (Ao.T @ y).reshape(d.shape)
+    return x, z
+
+
+def chi2_min_dense(d, mask, Ninv, P, A=None) -> float:
+    """Minimum of chi^2 = d_o^T C^-1 d_o (Woodbury on the normal equations)."""
+    A = dense_operator(P) if A is None else A
+    obs = np.broadcast_to(mask[None] == 1, d.shape).ravel()
+    Ao = A[obs]
+    Cmat = Ao @ Ao.T + np.diag(1.0 / Ninv.ravel()[obs])
+    do = d.ravel()[obs]
+    return float(do @ np.linalg.solve(Cmat, do))
+
+
+# ---------------------------------------------------------------------------
+# Textbook L-BFGS (Sec. 2.2: low-rank quasi-Newton; Nocedal & Wright,
+# Numerical Optimization 2nd ed., Alg. 7.4 two-loop, Alg. 7.5 driver,
+# Alg. 3.5 / 3.6 strong-Wolfe line search with zoom)
+# ---------------------------------------------------------------------------
+
+
+def _two_loop(g, S, Y):
+    q = g.copy()
+    alphas = []
+    for s, y in zip(reversed(S), reversed(Y)):
+        rho = 1.0 / np.dot(y, s)
+        a = rho * np.dot(s, q)
+        q -= a * y
+        alphas.append((a, rho))
+    if S:
+        gamma = np.dot(S[-1], Y[-1]) / np.dot(Y[-1], Y[-1])
+    else:
+        gamma = 1.0
+    r = gamma * q
+    for (s, y), (a, rho) in zip(zip(S, Y), reversed(alphas)):
+        b = rho * np.dot(y, r)
+        r += s * (a - b)
+    return -r
+
+
+def _sufficient(f, f0, a, d0, c1, eps_f):
+    """Armijo condition, relaxed by eps_f |f0| so that a step is not rejected
+    when f changes by less than its own rounding error near the minimum (the
+    approximate-Wolfe relaxation of Hager & Zhang, SIAM J. Optim. 16 (2005))."""
+    return f <= f0 + c1 * a * d0 + eps_f * abs(f0)
+
+
+def _zoom(phi, lo, hi, f0, d0, c1, c2, max_iter=60, eps_f=1e-14):
+    a_lo, f_lo, d_lo = lo
+    a_hi, f_hi, d_hi = hi
+    for _ in range(max_iter):
+        # cubic-free safeguarded quadratic interpolation from (a_lo, f_lo, d_lo) and f_hi
+        da = a_hi - a_lo
+        denom = 2.0 * (f_hi - f_lo - d_lo * da)
+        a = a_lo - d_lo * da * da / denom if denom > 0 else 0.5 * (a_lo + a_hi)
+        lo_b, hi_b = sorted((a_lo, a_hi))
+        if not (lo_b + 0.1 * (hi_b - lo_b) <= a <= hi_b - 0.1 * (hi_b - lo_b)):
+            a = 0.5 * (a_lo + a_hi)
+        f, d, gvec = phi(a)
+        if not _sufficient(f, f0, a, d0, c1, eps_f) or f > f_lo + eps_f * abs(f0):
+            a_hi, f_hi, d_hi = a, f, d
+        else:
+            if abs(d) <= -c2 * d0:
+                return a, f, gvec
+            if d * (a_hi - a_lo) >= 0:
+                a_hi, f_hi, d_hi = a_lo, f_lo, d_lo
+            a_lo, f_lo, d_lo = a, f, d
+    return a_lo, f_lo, None
+
+
+def _line_search(fg, x, f0, g0, p, c1, c2, a_max=1e6, max_iter=40, eps_f=1e-14):
+    d0 = float(np.dot(g0, p))
+    cache = {}
+
+    def phi(a):
+        if a not in cache:
+            f, g = fg(x + a * p)
+            cache[a] = (f, float(np.dot(g, p)), g)
+        return cache[a]
+
+    a_prev, f_prev, d_prev = 0.0, f0, d0
+    a = 1.0
+    for i in range(max_iter):
+        f, d, g = phi(a)
+        if not _sufficient(f, f0, a, d0, c1, eps_f) or (i > 0 and f > f_prev + eps_f * abs(f0)):
+            return _zoom(phi, (a_prev, f_prev, d_prev), (a, f, d), f0, d0, c1, c2)
+        if abs(d) <= -c2 * d0:
+            return a, f, g
+        if d >= 0:
+            return _zoom(phi, (a, f, d), (a_prev, f_prev, d_prev), f0, d0, c1, c2)
+        a_prev, f_prev, d_prev = a, f, d
+        a = min(2.0 * a, a_max)
+    return a, f, g
+
+
+def lbfgs(fg, x0, m=10, gtol_rel=1e-10, dchi2_abs=0.0, max_iter=10000,
+          c1=1e-4, c2=0.9, callback=None):
+    """Minimise f with L-BFGS.  fg(x) -> (f, grad).  Stops when
+    ||g|| <= gtol_rel ||g0||, or |f_k - f_{k-1}| < dchi2_abs (the paper's
+    Delta chi^2 rule, Sec. 3), or after max_iter iterations.
+    Returns (x, info) with info = dict(iters, evals, f, gnorm_rel, history)."""
+    x = np.array(x0, dtype=np.float64, copy=True).ravel()
+    shape = np.shape(x0)
+    evals = [0]
+
+    def fgv(v):
+        evals[0] += 1
+        f, g = fg(v.reshape(shape))
+        return f, np.asarray(g, dtype=np.float64).ravel()
+
+    f, g = fgv(x)
+    g0n = float(np.linalg.norm(g))
+    S, Y = [], []
+    hist = [f]
+    it = 0
+    status = "maxiter"
+    if g0n == 0.0:
+        status = "converged"
+    while it < max_iter and status != "converged":
+        p = _two_loop(g, S, Y)
+        a, f_new, g_new = _line_search(fgv, x, f, g, p, c1, c2)
+        if g_new is None:
+            f_new, g_new = fgv(x + a * p)
+        s = a * p
+        y = g_new - g
+        x = x + s
+        sy = float(np.dot(s, y))
+        if sy > 1e-12 * np.linalg.norm(s) * np.linalg.norm(y):
+            S.append(s)
+            Y.append(y)
+            if len(S) > m:
+                S.pop(0)
+                Y.pop(0)
+        df = abs(f_new - f)
+        f, g = f_new, g_new
+        it += 1
+        hist.append(f)
+        if callback is not None:
+            callback(it, x, f, g)
+        if np.linalg.norm(g) <= gtol_rel * g0n:
+            status = "converged"
+        elif dchi2_abs > 0 and df < dchi2_abs:
+            status = "converged"
+    info = dict(iters=it, evals=evals[0], f=f,
+                gnorm_rel=float(np.linalg.norm(g)) / g0n if g0n else 0.0,
+                status=status, history=np.array(hist))
+    return x.reshape(shape), info
+
+
+def map_solve(d, W, P, m=10, gtol_rel=1e-10, dchi2_abs=0.0, max_iter=10000, z0=None):
+    """MAP field (Sec. 2.2) in whitened variables by textbook L-BFGS from z0 = 0
+    (the start does not matter: the objective is strictly convex)."""
+    z0 = np.zeros_like(d) if z0 is None else z0
+
+    def fg(z):
+        r = d - apply_A(z, P)
+        return float(np.sum(z * z) + np.sum(r * W * r)), 2.0 * (z - apply_At(W * r, P))
+
+    return lbfgs(fg, z0, m=m, gtol_rel=gtol_rel, dchi2_abs=dchi2_abs, max_iter=max_iter)
+
+
+def exact_step(g, p, W, P):
+    """Exact minimiser along p of the quadratic chi^2: -g.p / p.H p."""
+    return -float(np.sum(g * p)) / float(np.sum(p * hess_vec(p, W, P)))
+
+
+# ---------------------------------------------------------------------------
+# Band powers (Sec. 2.3-2.5)
+# ---------------------------------------------------------------------------
+
+
+def theta_fid(P, bands, n_bands):
+    """Theta_fid,l: mean of the fiducial P over the band's modes (Sec. 2.3,
+    eq. pilin; the paper leaves the per-band normalisation open)."""
+    out = np.zeros(n_bands)
+    for l in range(n_bands):
+        sel = bands == l
+        out[l] = P[sel].mean()
+    return out
+
+
+def band_E(z, bands, theta, n_bands):
+    """E_l = 1/2 sum_{k in l} s_k^2 / (Theta_fid,l S_fid,k) (Sec. 2.4, eq. el).
+    In whitened variables s_k^2 / S_fid,k = |z_k|^2, summed over the full plane."""
+    Z = fft2u(z)
+    a2 = np.abs(Z) ** 2
+    E = np.zeros(n_bands)
+    for l in range(n_bands):
+        E[l] = 0.5 * a2[bands == l].sum() / theta[l]
+    return E
+
+
+def band_signal(u, P, bands, band):
+    """Field with the fiducial spectrum restricted to one band, from white noise u:
+    U^-1 sqrt(P 1_band) U u (the extra signal Delta Theta_l' Pi_l' of eq. fisher
+    with Delta Theta = Theta_fid)."""
+    Pl = np.where(bands == band, P, 0.0)
+    return apply_A(u, Pl)
+
+
+def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
+                   m=10, gtol_rel=1e-10, max_iter=20000):
+    """Simulation estimates of Sec. 2.5 on one data map (C = 1).
+
+    * E(d): eq. el on the MAP of the data.
+    * b_l = mean_j E_l(MAP(d_j)), d_j = M (A z_j + n_j)        (eq. blmv)
+    * F_ll' Delta Theta_l' = mean_j [E_l(MAP(d_j + delta_l'j)) - E_l(MAP(d_j))],
+      delta_l'j = M A_l' u_l'j, Delta Theta_l' = Theta_fid,l'   (eq. fisher)
+      with common random numbers: the j-th finite-difference map reuses d_j.
+    * Theta_hat = Theta_fid + F^-1 (E - b)                      (eq. eq:wfmv)
+    * cov = F^-1 (eq. eq:var), and the sample covariance of E over the sims.
+    z_sims, n_sims: (J, C, n, n) white signal fields and noise realisations.
+    u_fd: (n_bands, J_fd, C, n, n) white fields for the Fisher perturbations;
+    J_fd <= J, and the j-th perturbation is added to sim j.
+    """
+    W = mask[None] * Ninv
+    theta = theta_fid(P, bands, n_bands)
+
+    def E_of(data):
+        z, _ = map_solve(data, W, P, m=m, gtol_rel=gtol_rel, max_iter=max_iter)
+        return band_E(z, bands, theta, n_bands)
+
+    E_d = E_of(d)
+    J = z_sims.shape[0]
+    sims = [synthesize_data(z_sims[j], n_sims[j], mask, P) for j in range(J)]
+    E_s = np.array([E_of(sd) for sd in sims])
+    b = E_s.mean(axis=0)
+    J_fd = u_fd.shape[1]
+    F = np.zeros((n_bands, n_bands))
+    for lp in range(n_bands):
+        acc = np.zeros(n_bands)
+        for j in range(J_fd):
+            delta = band_signal(u_fd[lp, j], P, bands, lp) * mask[None]
+            acc += E_of(sims[j] + delta) - E_s[j]
+        F[:, lp] = acc / J_fd / theta[lp]
+    Finv = np.linalg.inv(F)
+    theta_hat = theta + Finv @ (E_d - b)
+    covE = np.cov(E_s.T, ddof=1) if J > 1 else np.zeros((n_bands, n_bands))
+    return dict(E=E_d, b=b, F=F, cov=Finv, theta_hat=theta_hat, theta_fid=theta,
+                E_sims=E_s, cov_E=covE)
+
+
+def exact_band_terms(mask, Ninv, P, bands, n_bands, A=None):
+    """Exact noise bias and Fisher matrix by dense traces (App. A, eq.
+    eq:wf_exact_f, first equality; Sec. 2.1 Q_l = dC/dTheta_l):
+    C = M A A^T M^T + N,  Q_l = M A Pi_l A^T M^T / Theta_fid,l,
+    b_l = 1/2 tr(C^-1 Q_l),  F_ll' = 1/2 tr(C^-1 Q_l C^-1 Q_l')."""
+    C_, n = P.shape[0], P.shape[-1]
+    A = dense_operator(P) if A is None else A
+    obs = np.broadcast_to(mask[None] == 1, P.shape).ravel()
+    Ao = A[obs]
+    Cmat = Ao @ Ao.T + np.diag(1.0 / Ninv.ravel()[obs])
+    Cinv = np.linalg.inv(Cmat)
+    theta = theta_fid(P, bands, n_bands)
+    Ms = []
+    for l in range(n_bands):
+        Al = dense_operator(np.where(bands == l, P, 0.0))[obs]
+        Ql = (Al @ Al.T) / theta[l]
+        Ms.append(Cinv @ Ql)
+    b = np.array([0.5 * np.trace(M) for M in Ms])
+    F = np.array([[0.5 * np.sum(Ms[i] * Ms[j].T) for j in range(n_bands)]
+                  for i in range(n_bands)])
+    return b, F, theta

@@ -1,0 +1,218 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+textbook DFT definitions and closed forms, exact identities of a quadratic,
+Woodbury agreement of two independent dense Wiener-filter forms, and analytic
+band terms for an unmasked map with homogeneous noise."""
+import numpy as np
+import pytest
+
+from oracle import wf_oracle as O
+from paper_1810_00503_gb300 import synth
+
+
+def test_naive_dft_plane_wave_and_delta():
+    # Unitary DFT of a delta is 1/n everywhere; of exp(+2 pi i (a y + b x)/n) it is n at (a, b).
+    n = 8
+    x = np.zeros((n, n)); x[0, 0] = 1.0
+    assert np.allclose(O.dft2_naive(x), 1.0 / n, atol=1e-15)
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    a, b = 3, 5
+    w = np.exp(2j * np.pi * (a * yy + b * xx) / n)
+    X = O.dft2_naive(w)
+    ref = np.zeros((n, n), complex); ref[a, b] = n
+    assert np.allclose(X, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 4, 8])
+def test_fft_matches_naive_dft(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((2, n, n)) + 1j * rng.standard_normal((2, n, n))
+    assert np.allclose(O.fft2u(x), O.dft2_naive(x), atol=1e-13, rtol=0)
+
+
+def test_parseval_and_roundtrip():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 32, 32))
+    X = O.fft2u(x)
+    assert np.isclose(np.sum(np.abs(X) ** 2), np.sum(x * x), rtol=1e-14)
+    assert np.allclose(O.ifft2u(X).real, x, atol=1e-14)
+
+
+def test_operator_identity_and_adjoint():
+    n = 16
+    rng = np.random.default_rng(2)
+    z = rng.standard_normal((1, n, n))
+    assert np.allclose(O.apply_A(z, np.ones((1, n, n))), z, atol=1e-14)
+    for C in (1, 2):
+        P = rng.uniform(0.1, 2.0, size=(C, n, n))
+        P = 0.5 * (P + P[:, (-np.arange(n)) % n][:, :, (-np.arange(n)) % n])  # even in k
+        a = rng.standard_normal((C, n, n)); b = rng.standard_normal((C, n, n))
+        lhs = np.sum(O.apply_A(a, P) * b)
+        rhs = np.sum(a * O.apply_At(b, P))
+        assert np.isclose(lhs, rhs, rtol=1e-12)
+        # a real field stays real: the imaginary part before .real is round-off only
+        Z = O.fft2u(a) * np.sqrt(P)
+        assert np.abs(O.ifft2u(Z).imag).max() < 1e-12
+
+
+def test_ks_rotation_plane_wave_closed_form():
+    # Pure E-mode cosine wave with unit power on one mode pair: gamma1 = c phi,
+    # gamma2 = s phi with c = (kx^2-ky^2)/k^2, s = 2 kx ky / k^2 (App. C operator
+    # divided by -k^2).  Pins orientation (x = last axis) and sign.
+    n = 16
+    ky, kx = 2, 3
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    phi = np.cos(2 * np.pi * (ky * yy + kx * xx) / n)
+    z = np.stack([phi, np.zeros_like(phi)])
+    g = O.apply_A(z, np.ones((2, n, n)))
+    k2 = kx * kx + ky * ky
+    assert np.allclose(g[0], (kx * kx - ky * ky) / k2 * phi, atol=1e-13)
+    assert np.allclose(g[1], 2 * kx * ky / k2 * phi, atol=1e-13)
+    # and a pure B mode rotates the other way
+    zb = np.stack([np.zeros_like(phi), phi])
+    gb = O.apply_A(zb, np.ones((2, n, n)))
+    assert np.allclose(gb[0], -2 * kx * ky / k2 * phi, atol=1e-13)
+    assert np.allclose(gb[1], (kx * kx - ky * ky) / k2 * phi, atol=1e-13)
+
+
+def test_ks_rotation_orthogonal_off_nyquist():
+    n = 16
+    c, s = O.ks_rotation(n)
+    my, mx = O.signed_modes(n)
+    off = (np.abs(mx) != n // 2) & (np.abs(my) != n // 2)
+    assert np.allclose((c * c + s * s)[off], 1.0, atol=1e-15)
+    assert np.all(s[~off] == 0)
+
+
+@pytest.mark.parametrize("C", [1, 2])
+def test_gradient_is_exact_central_difference(C):
+    # chi^2 is quadratic, so (f(z+hv) - f(z-hv)) / 2h equals g.v up to round-off.
+    n = 16
+    inp = synth.density_small(n, seed=5) if C == 1 else synth.shear_eb(n, seed=5)
+    W = inp.mask[None] * inp.Ninv
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    rng = np.random.default_rng(7)
+    z = rng.standard_normal(d.shape)
+    g = O.grad(z, d, W, inp.P)
+    f0 = O.chi2(z, d, W, inp.P)
+    h = 1e-3
+    for _ in range(20):
+        v = rng.standard_normal(d.shape)
+        fd = (O.chi2(z + h * v, d, W, inp.P) - O.chi2(z - h * v, d, W, inp.P)) / (2 * h)
+        assert abs(fd - np.sum(g * v)) <= 1e-13 * abs(f0) / h + 1e-9 * abs(fd)
+
+
+def test_hessian_vector_is_gradient_difference():
+    n = 16
+    inp = synth.density_small(n, seed=3)
+    W = inp.mask[None] * inp.Ninv
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal(d.shape); v = rng.standard_normal(d.shape)
+    lhs = O.grad(z + v, d, W, inp.P) - O.grad(z, d, W, inp.P)
+    assert np.allclose(lhs, O.hess_vec(v, W, inp.P), rtol=1e-11, atol=1e-9)
+
+
+def test_unmasked_homogeneous_closed_form():
+    # No mask, constant noise sigma^2: z*_m = sqrt(P_m) d_m / (P_m + sigma^2) per mode
+    # (the S / (S + N) filter of App. A in whitened variables).
+    n, sig2 = 32, 0.3
+    inp = synth.density_small(n, seed=11)
+    mask = np.ones((n, n), np.uint8)
+    W = np.full((1, n, n), 1.0 / sig2)
+    d = O.synthesize_data(inp.z, np.sqrt(sig2) * inp.z[::-1], mask, inp.P)
+    D = O.fft2u(d)
+    zstar = O.ifft2u(np.sqrt(inp.P) * D / (inp.P + sig2)).real
+    z_dense = O.dense_wf_whitened(d, W, inp.P)
+    assert np.linalg.norm(z_dense - zstar) <= 1e-12 * np.linalg.norm(zstar)
+    z_lb, info = O.map_solve(d, W, inp.P, gtol_rel=1e-12)
+    assert info["status"] == "converged"
+    assert np.linalg.norm(z_lb - zstar) <= 1e-10 * np.linalg.norm(zstar)
+
+
+def test_dense_forms_agree_woodbury_and_lbfgs():
+    inp = synth.density_small(32, seed=0)
+    W = inp.mask[None] * inp.Ninv
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    A = O.dense_operator(inp.P)
+    z1 = O.dense_wf_whitened(d, W, inp.P, A=A)
+    x2, z2 = O.dense_wf_covariance(d, inp.mask, inp.Ninv, inp.P, A=A)
+    assert np.linalg.norm(z1 - z2) <= 1e-11 * np.linalg.norm(z1)
+    assert np.allclose(O.apply_A(z1, inp.P), x2, rtol=0, atol=1e-10 * np.abs(x2).max())
+    # chi^2 at the minimiser equals d_o^T C^-1 d_o
+    assert np.isclose(O.chi2(z1, d, W, inp.P), O.chi2_min_dense(d, inp.mask, inp.Ninv, inp.P, A=A),
+                      rtol=1e-11)
+    # textbook L-BFGS reaches the same point; certificate ||z - z*|| <= ||grad|| / 2
+    zl, info = O.map_solve(d, W, inp.P, m=10, gtol_rel=1e-12, max_iter=5000)
+    gl = O.grad(zl, d, W, inp.P)
+    err = np.linalg.norm(zl - z1)
+    assert err <= 0.5 * np.linalg.norm(gl) * (1 + 1e-6) + 1e-13 * np.linalg.norm(z1)
+    assert err <= 1e-10 * np.linalg.norm(z1)
+
+
+def test_certificate_bound_is_tight_enough_and_valid():
+    # lambda_min of the half-Hessian I + A^T W A is >= 1, so ||z - z*|| <= ||g|| / 2
+    inp = synth.density_small(16, seed=4)
+    W = inp.mask[None] * inp.Ninv
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    zs = O.dense_wf_whitened(d, W, inp.P)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        z = zs + 1e-3 * rng.standard_normal(zs.shape)
+        g = O.grad(z, d, W, inp.P)
+        assert np.linalg.norm(z - zs) <= 0.5 * np.linalg.norm(g) * (1 + 1e-12)
+
+
+def test_exact_step_minimises_along_line():
+    inp = synth.density_small(16, seed=6)
+    W = inp.mask[None] * inp.Ninv
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    rng = np.random.default_rng(1)
+    z = rng.standard_normal(d.shape); p = rng.standard_normal(d.shape)
+    g = O.grad(z, d, W, inp.P)
+    a = O.exact_step(g, p, W, inp.P)
+    g_new = O.grad(z + a * p, d, W, inp.P)
+    assert abs(np.sum(g_new * p)) <= 1e-10 * np.linalg.norm(g) * np.linalg.norm(p)
+
+
+def test_exact_band_terms_unmasked_closed_form():
+    # No mask, homogeneous noise: C is diagonal in Fourier with P_m + sigma^2, so
+    # b_l = (1/2 Theta_l) sum_{m in l} P_m / (P_m + s2),
+    # F_ll' = delta_ll' (1/2 Theta_l^2) sum_{m in l} P_m^2 / (P_m + s2)^2.
+    n, s2, nb = 8, 0.5, 3
+    inp = synth.density_small(n, seed=2)
+    mask = np.ones((n, n), np.uint8)
+    Ninv = np.full((1, n, n), 1.0 / s2)
+    bands = synth.log_bands(n, nb)
+    b, F, th = O.exact_band_terms(mask, Ninv, inp.P, bands, nb)
+    P = inp.P
+    for l in range(nb):
+        sel = bands == l
+        assert np.isclose(b[l], 0.5 / th[l] * np.sum(P[sel] / (P[sel] + s2)), rtol=1e-11)
+        assert np.isclose(F[l, l], 0.5 / th[l] ** 2 * np.sum(P[sel] ** 2 / (P[sel] + s2) ** 2),
+                          rtol=1e-11)
+    off = F - np.diag(np.diag(F))
+    assert np.abs(off).max() <= 1e-12 * np.abs(F).max()
+
+
+@pytest.mark.slow
+def test_simulated_band_terms_match_exact_traces():
+    # b from simulations (eq. blmv) and F by finite differences (eq. fisher) agree with
+    # the exact traces of eq:wf_exact_f within Monte-Carlo error; the sample covariance
+    # of E over the simulations agrees with F (Fisher identity).
+    n, nb, J = 8, 3, 400
+    inp = synth.density_small(n, seed=9, masked_frac=0.25)
+    bands = synth.log_bands(n, nb)
+    rng = np.random.default_rng(21)
+    z_s = rng.standard_normal((J, 1, n, n))
+    n_s = rng.standard_normal((J, 1, n, n)) / np.sqrt(np.where(inp.Ninv > 0, inp.Ninv, 1.0))
+    u_fd = rng.standard_normal((nb, J, 1, n, n))
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    res = O.bandpower_sims(d, inp.mask, inp.Ninv, inp.P, bands, nb, z_s, n_s, u_fd,
+                           gtol_rel=1e-9)
+    b_ex, F_ex, th = O.exact_band_terms(inp.mask, inp.Ninv, inp.P, bands, nb)
+    # MC standard error of b_l is sqrt(F_ll / J) (Var E_l = F_ll at the fiducial)
+    se_b = np.sqrt(np.diag(F_ex) / J)
+    assert np.all(np.abs(res["b"] - b_ex) <= 5 * se_b)
+    # finite-difference F: each entry is a mean of J cross terms; loose 5-sigma-ish bound
+    assert np.allclose(res["F"], F_ex, rtol=0.25, atol=0.1 * np.abs(F_ex).max())
+    assert np.allclose(res["cov_E"], F_ex, rtol=0.3, atol=0.1 * np.abs(F_ex).max())
