@@ -1,0 +1,182 @@
+/*
+ * wf.h - C ABI of the GB300 Wiener-filter MAP library.
+ *
+ * The method (Horowitz, Seljak & Aslanyan, arXiv:1810.00503):
+ *   data model d = R s + n, S diagonal in Fourier space, N diagonal in pixels
+ *   (Sec. 2, eq. ddecomp); MAP field by minimising
+ *   chi^2(s) = s^T S^-1 s + (d - R s)^T N^-1 (d - R s)      (Sec. 2.2, eq_chi)
+ *   with its analytic gradient (eq_cost) and an L-BFGS quasi-Newton driver
+ *   (Sec. 2.2); band powers from simulations (Sec. 2.4-2.5: eq. el, blmv,
+ *   fisher, eq:wfmv).
+ *
+ * Variables.  The library works in whitened Fourier modes: the state is
+ *   s_hat = U s_w, the unitary 2-D DFT of a real white field s_w, and the
+ *   signal map is x = A s_w with A = U^-1 R(k) diag(sqrt P) U.  In these
+ *   variables chi^2 = |s_hat|^2 + (d - x)^T W (d - x), W = mask * Ninv.
+ *   The gradient returned is the full d chi^2 / d s_hat (twice the paper's g).
+ *   For two channels (joint E/B shear, App. C) R(k) is the per-mode
+ *   Kaiser-Squires rotation [[c, -s], [s, c]], c = (kx^2 - ky^2)/k^2,
+ *   s = 2 kx ky / k^2, with s = 0 on the Nyquist row and column; one channel
+ *   has R = 1.
+ *
+ * Layouts (row-major, C-contiguous):
+ *   pixel maps   [count][C][n][n]            y (row) then x (column)
+ *   spectra      [count][C][n][n/2+1]        complex (re, im) pairs, numpy
+ *                                            rfft2 layout, unitary scaling
+ *   mask         [n][n] uint8, 1 = observed, shared by the channels
+ *   P            [C][n][n/2+1] real: variance of each unitary Fourier mode of
+ *                the signal, >= 0; the kx = 0 and kx = n/2 columns must be
+ *                symmetric under ky -> n - ky.
+ * n is a power of two in [8, 1024]; C is 1 or 2.
+ *
+ * Pointers.  Every array pointer is a DEVICE pointer owned by the caller,
+ * unless stated otherwise; the library never frees a caller pointer nor keeps
+ * it after the call returns (wf_problem_create copies what it needs).  Calls
+ * are ordered on the CUDA stream passed in (NULL = legacy default stream).
+ *
+ * Errors.  Every call returns a wf_status; WF_OK is 0.  On failure
+ * wf_last_error() returns a message for the calling thread.  Calls that launch
+ * work return after enqueueing it unless documented to synchronise.
+ */
+#ifndef WF_H_
+#define WF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WF_OK = 0,
+  WF_EINVAL = 1,         /* bad argument: size, channel count, null pointer, negative Ninv or P */
+  WF_ENONFINITE = 2,     /* a NaN or Inf in the inputs or met during a solve */
+  WF_ENOMEM = 3,         /* device allocation failed */
+  WF_ECUDA = 4,          /* a CUDA runtime call failed */
+  WF_ENOTCONVERGED = 5,  /* iteration limit reached; outputs are still written */
+  WF_ELINESEARCH = 6,    /* no decrease along the search direction */
+  WF_ETIMEOUT = 7        /* a bounded device wait gave up */
+} wf_status;
+
+typedef enum { WF_FP64 = 0, WF_MIXED = 1 } wf_precision;  /* MIXED: FP32 fields, FP64 sums */
+typedef enum { WF_F32 = 0, WF_F64 = 1 } wf_dtype;
+
+typedef struct wf_handle wf_handle;
+typedef struct wf_problem wf_problem;
+
+/* One input map.  All pointers are device pointers, read once by
+ * wf_problem_create (or wf_problem_set_data for d).  Values have the dtype
+ * given to wf_problem_create. */
+typedef struct {
+  const void* d;               /* [C][n][n] data (0 is fine on masked pixels) */
+  const unsigned char* mask;   /* [n][n] 1 = observed, 0 = masked */
+  const void* Ninv;            /* [C][n][n] inverse noise variance, >= 0, finite */
+  const void* P;               /* [C][n][n/2+1] signal power per mode, >= 0 */
+} wf_map;
+
+typedef struct {
+  int lbfgs_m;        /* L-BFGS memory (pairs kept), 1..32; default 10 */
+  int max_iter;       /* iteration limit; default 10000 */
+  double gtol_rel;    /* stop when |g| <= gtol_rel |g0|; default 1e-6; 0 = off */
+  double dchi2_abs;   /* stop when |chi2_k - chi2_{k-1}| < dchi2_abs (the paper's
+                         Delta chi^2 rule, Sec. 3); default 0 = off */
+  int refresh_every;  /* recompute the true gradient from the data every this many
+                         iterations (0 = only at the start and the end); default 0 */
+  int check_every;    /* iterations between host polls of the convergence flags
+                         (one synchronisation each); default 16 */
+  int use_graphs;     /* capture check_every iterations in one CUDA graph; default 1 */
+  void* stream;       /* cudaStream_t for all work of the call; NULL = default stream */
+} wf_opts;
+
+typedef struct {
+  int iters;          /* L-BFGS iterations taken */
+  int evals;          /* operator applications (Hessian-vector and gradient passes) */
+  int status;         /* wf_status of this map */
+  int pad_;
+  double chi2;        /* final chi^2 (true value from the data at the returned state) */
+  double gnorm_rel;   /* final |g| / |g0| (true gradient) */
+} wf_solve_stats;
+
+/* Library handle: owns the twiddle tables for the current device.  Create one
+ * per device and thread of use.  Returns WF_ECUDA if no device is usable. */
+wf_status wf_create(wf_handle** out);
+wf_status wf_destroy(wf_handle* h);
+
+/* Message for the last failing call on this thread ("" if none).  The pointer
+ * stays valid until the next call from the same thread. */
+const char* wf_last_error(void);
+
+/* Fill *o with the defaults listed in wf_opts. */
+void wf_opts_default(wf_opts* o);
+
+/* Prepare a batch of `count` maps of one shape (n, C) for repeated use:
+ * converts the inputs to the working precision, forms W = mask * Ninv and
+ * sqrt(P), checks them (negative or non-finite values -> WF_EINVAL /
+ * WF_ENONFINITE) and allocates the device workspace: about
+ * (4 + 2 m) C n^2 values of the working type per map plus scratch.
+ * maps: HOST array of `count` descriptors holding device pointers.
+ * dtype: WF_F32 or WF_F64 for every floating array of the maps and of later
+ * calls on this problem (s, grad, s_out, x_out, z, noise).
+ * precision: WF_FP64 computes everything in FP64; WF_MIXED keeps fields and
+ * FFTs in FP32 and all reductions and L-BFGS scalars in FP64.
+ * Synchronises the stream once (to read the input check).  Paper: Sec. 2
+ * (data model) and Sec. 2.2 (eq_chi: the inputs of the objective). */
+wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, int C,
+                            int dtype, int precision, int lbfgs_m, void* stream,
+                            wf_problem** out);
+wf_status wf_problem_destroy(wf_problem* p);
+
+/* Replace the data maps d of every map (device [count][C][n][n], problem
+ * dtype); masked pixels are ignored.  Stream ordered, no synchronisation. */
+wf_status wf_problem_set_data(wf_problem* p, const void* d, void* stream);
+
+/* One objective + gradient pass per map (Sec. 2.2, eq_chi and eq_cost):
+ *   chi2[b] = |s_hat_b|^2 + (d_b - x_b)^T W_b (d_b - x_b)
+ *   grad[b] = d chi2 / d s_hat = 2 (s_hat - sqrt P R^T U W (d - x))
+ * s: device [count][C][n][n/2+1] complex of the problem dtype (whitened modes,
+ * Hermitian-consistent in the kx = 0 and kx = n/2 columns); grad: same shape,
+ * written; chi2: device double [count], written; any may alias nothing else.
+ * Stream ordered, no synchronisation. */
+wf_status wf_eval(wf_problem* p, const void* s, void* grad, double* chi2, void* stream);
+
+/* Hessian-vector product of chi^2 (twice eq_curv): hv = 2 (v + A^T W A v),
+ * same layouts as wf_eval.  Stream ordered. */
+wf_status wf_hess_vec(wf_problem* p, const void* v, void* hv, void* stream);
+
+/* Signal map x = A s_w for a whitened state (the Wiener-filtered map when s is
+ * the MAP): s [count][C][n][n/2+1], x [count][C][n][n].  Stream ordered. */
+wf_status wf_signal_map(wf_problem* p, const void* s, void* x, void* stream);
+
+/* MAP solve of every map by L-BFGS with an exact line search (Sec. 2.2; the
+ * objective is quadratic, so the step along p is -g.p / p.Hp, the point where a
+ * strong-Wolfe search would stop).  Starts from s0 (device, spectrum layout) or
+ * from 0 when s0 is NULL.  Writes s_out (device, spectrum layout) and, if
+ * x_out is not NULL, the signal map A s_out (device, pixel layout).
+ * stats: HOST array of `count` entries, written.  Returns the worst per-map
+ * status (WF_ENOTCONVERGED if any map hit max_iter; outputs still written).
+ * Synchronises the stream every opts->check_every iterations. */
+wf_status wf_map_solve(wf_problem* p, const wf_opts* opts, const void* s0, void* s_out,
+                       void* x_out, wf_solve_stats* stats);
+
+/* Data synthesis for simulations (Sec. 2.5, steps 1-2; eq. blmv):
+ * d_b = mask * (A z_b + noise_b), z and noise device [count][C][n][n] of the
+ * problem dtype (z white N(0,1), noise with variance 1/Ninv), d_out the same
+ * shape.  Uses each map's mask and P.  Stream ordered. */
+wf_status wf_simulate_data(wf_problem* p, const void* z, const void* noise, void* d_out,
+                           void* stream);
+
+/* Band powers of the MAP fields (Sec. 2.4, eq. el):
+ *   E[b][l] = 1/(2 Theta_l) sum over full-plane modes k in band l of |s_hat_k|^2
+ * s: device spectra [count][C][n][n/2+1] (problem dtype); band: device int16
+ * [C][n][n/2+1] band id per half-plane mode (-1 = none), ids < n_bands;
+ * theta: device double [n_bands]; E: device double [count][n_bands], written.
+ * Stream ordered. */
+wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
+                         const double* theta, int n_bands, double* E, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WF_H_ */

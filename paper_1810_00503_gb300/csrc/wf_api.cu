@@ -1,0 +1,290 @@
+// C ABI of the Wiener-filter library: handle, prepared problems and the
+// single-pass operator calls.  The L-BFGS driver lives in wf_solve.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "wf_api_internal.h"
+
+static thread_local char g_errbuf[1024];
+
+wf_status wf_fail(wf_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_errbuf, sizeof g_errbuf, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+wf_status wf_cuda_fail(cudaError_t e, const char* what) {
+  return wf_fail(e == cudaErrorMemoryAllocation ? WF_ENOMEM : WF_ECUDA, "%s: %s (%s)", what,
+                 cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+extern "C" const char* wf_last_error(void) { return g_errbuf; }
+
+extern "C" void wf_opts_default(wf_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->lbfgs_m = 10;
+  o->max_iter = 10000;
+  o->gtol_rel = 1e-6;
+  o->dchi2_abs = 0.0;
+  o->refresh_every = 0;
+  o->check_every = 16;
+  o->use_graphs = 1;
+  o->stream = nullptr;
+}
+
+WfGeo wf_make_geo(int n, int C) {
+  WfGeo g;
+  g.n = n;
+  g.h = n / 2;
+  g.C = C;
+  g.lgn = 0;
+  while ((1 << g.lgn) < n) ++g.lgn;
+  g.lgh = g.lgn - 1;
+  int tc = WF_TILE / (C * n);
+  if (tc > g.h) tc = g.h;
+  if (tc < 1) tc = 1;
+  g.TC = tc;
+  g.ntile = g.h / tc;
+  int rb = WF_TILE / g.h;
+  if (rb > C * n) rb = C * n;
+  g.RB = rb;
+  g.nrb = C * n / rb;
+  g.maxblk = g.ntile > g.nrb ? g.ntile : g.nrb;
+  return g;
+}
+
+// Roots of unity exp(-2 pi i k / WF_NT), computed in long double; the values
+// at multiples of pi/2 are set exactly.
+static void make_twiddles(double2* out) {
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int k = 0; k < WF_NT; ++k) {
+    long double a = -two_pi * (long double)k / (long double)WF_NT;
+    double c = (double)cosl(a), s = (double)sinl(a);
+    if (k % (WF_NT / 4) == 0) {
+      const int q = k / (WF_NT / 4);
+      c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+      s = (q == 1) ? -1.0 : (q == 3 ? 1.0 : 0.0);
+    }
+    out[k].x = c;
+    out[k].y = s;
+  }
+}
+
+extern "C" wf_status wf_create(wf_handle** out) {
+  if (!out) return wf_fail(WF_EINVAL, "wf_create: null output pointer");
+  *out = nullptr;
+  wf_handle* h = (wf_handle*)calloc(1, sizeof(wf_handle));
+  if (!h) return wf_fail(WF_ENOMEM, "wf_create: host allocation failed");
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { free(h); return wf_cuda_fail(e, "wf_create: cudaGetDevice"); }
+  double2 tw64[WF_NT];
+  float2 tw32[WF_NT];
+  make_twiddles(tw64);
+  for (int k = 0; k < WF_NT; ++k) { tw32[k].x = (float)tw64[k].x; tw32[k].y = (float)tw64[k].y; }
+  e = cudaMalloc(&h->tw64, sizeof tw64);
+  if (e == cudaSuccess) e = cudaMalloc(&h->tw32, sizeof tw32);
+  if (e == cudaSuccess) e = cudaMemcpy(h->tw64, tw64, sizeof tw64, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->tw32, tw32, sizeof tw32, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (h->tw64) cudaFree(h->tw64);
+    if (h->tw32) cudaFree(h->tw32);
+    free(h);
+    return wf_cuda_fail(e, "wf_create: twiddle tables");
+  }
+  *out = h;
+  return WF_OK;
+}
+
+extern "C" wf_status wf_destroy(wf_handle* h) {
+  if (!h) return WF_OK;
+  cudaFree(h->tw64);
+  cudaFree(h->tw32);
+  free(h);
+  return WF_OK;
+}
+
+static void free_problem(wf_problem* p) {
+  if (!p) return;
+  void* ptrs[] = {p->d, p->w, p->sp, p->scratch, p->part, p->flags};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  wf_solver_free(p);
+  free(p);
+}
+
+wf_status wf_alloc(void** ptr, size_t bytes, const char* what) {
+  *ptr = nullptr;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return wf_fail(e == cudaErrorMemoryAllocation ? WF_ENOMEM : WF_ECUDA,
+                   "device allocation of %zu bytes for %s failed: %s", bytes, what,
+                   cudaGetErrorString(e));
+  }
+  return WF_OK;
+}
+
+extern "C" wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, int C,
+                                       int dtype, int precision, int lbfgs_m, void* stream,
+                                       wf_problem** out) {
+  if (!out) return wf_fail(WF_EINVAL, "wf_problem_create: null output pointer");
+  *out = nullptr;
+  if (!h) return wf_fail(WF_EINVAL, "wf_problem_create: null handle");
+  if (!maps || count < 1) return wf_fail(WF_EINVAL, "wf_problem_create: need count >= 1 maps");
+  if (n < 8 || n > WF_NT || (n & (n - 1)))
+    return wf_fail(WF_EINVAL, "wf_problem_create: n = %d is not a power of two in [8, %d]", n, WF_NT);
+  if (C != 1 && C != 2) return wf_fail(WF_EINVAL, "wf_problem_create: C = %d (must be 1 or 2)", C);
+  if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "wf_problem_create: bad dtype %d", dtype);
+  if (precision != WF_FP64 && precision != WF_MIXED)
+    return wf_fail(WF_EINVAL, "wf_problem_create: bad precision %d", precision);
+  if (lbfgs_m < 1 || lbfgs_m > WF_MAXM)
+    return wf_fail(WF_EINVAL, "wf_problem_create: lbfgs_m = %d outside [1, %d]", lbfgs_m, WF_MAXM);
+  for (int i = 0; i < count; ++i)
+    if (!maps[i].mask || !maps[i].Ninv || !maps[i].P)
+      return wf_fail(WF_EINVAL, "wf_problem_create: map %d has a null mask, Ninv or P pointer", i);
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device)
+    return wf_fail(WF_EINVAL, "wf_problem_create: current device %d differs from the handle's %d", dev,
+                   h->device);
+
+  wf_problem* p = (wf_problem*)calloc(1, sizeof(wf_problem));
+  if (!p) return wf_fail(WF_ENOMEM, "wf_problem_create: host allocation failed");
+  p->h = h;
+  p->count = count;
+  p->n = n;
+  p->C = C;
+  p->dtype = dtype;
+  p->precision = precision;
+  p->m = lbfgs_m;
+  p->g = wf_make_geo(n, C);
+  p->elt = precision == WF_FP64 ? sizeof(double) : sizeof(float);
+  int shared = 1;
+  for (int i = 1; i < count; ++i) shared &= maps[i].P == maps[0].P;
+  p->sp_shared = shared;
+  const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
+  p->sp_stride = shared ? 0 : (long long)nsp;
+  wf_status s = WF_OK;
+  if (s == WF_OK) s = wf_alloc(&p->d, npix * count * p->elt, "data maps");
+  if (s == WF_OK) s = wf_alloc(&p->w, npix * count * p->elt, "weights");
+  if (s == WF_OK) s = wf_alloc(&p->sp, nsp * (shared ? 1 : count) * p->elt, "sqrt(P) tables");
+  if (s == WF_OK) s = wf_alloc(&p->scratch, npix * count * p->elt, "scratch");
+  if (s == WF_OK) s = wf_alloc((void**)&p->part, sizeof(double) * WF_NSLOT * p->g.maxblk * count, "partial sums");
+  if (s == WF_OK) s = wf_alloc((void**)&p->flags, sizeof(int) * 4, "flags");
+  if (s != WF_OK) { free_problem(p); return s; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(p->flags, 0, sizeof(int) * 4, st);
+  const void** dp = (const void**)malloc(sizeof(void*) * 4 * (size_t)count);
+  if (!dp) { free_problem(p); return wf_fail(WF_ENOMEM, "wf_problem_create: host allocation failed"); }
+  const unsigned char** mp = (const unsigned char**)(dp + count);
+  const void** np = dp + 2 * count;
+  const void** pp = dp + 3 * count;
+  for (int i = 0; i < count; ++i) {
+    dp[i] = maps[i].d;
+    mp[i] = maps[i].mask;
+    np[i] = maps[i].Ninv;
+    pp[i] = maps[i].P;
+  }
+  if (e == cudaSuccess) {
+    if (precision == WF_FP64)
+      e = wf_launch_prep<double>(p->g, dp, mp, np, pp, dtype == WF_F64, count, p->d, p->w, p->sp,
+                                 shared, p->flags, st);
+    else
+      e = wf_launch_prep<float>(p->g, dp, mp, np, pp, dtype == WF_F64, count, p->d, p->w, p->sp,
+                                shared, p->flags, st);
+  }
+  free(dp);
+  if (e != cudaSuccess) { free_problem(p); return wf_cuda_fail(e, "wf_problem_create: input preparation"); }
+  int flags = 0;
+  e = cudaMemcpy(&flags, p->flags, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { free_problem(p); return wf_cuda_fail(e, "wf_problem_create: reading checks"); }
+  if (flags & (1 << WF_ENONFINITE)) {
+    free_problem(p);
+    return wf_fail(WF_ENONFINITE, "wf_problem_create: non-finite value in d, Ninv or P");
+  }
+  if (flags & (1 << WF_EINVAL)) {
+    free_problem(p);
+    return wf_fail(WF_EINVAL, "wf_problem_create: negative value in Ninv or P");
+  }
+  *out = p;
+  return WF_OK;
+}
+
+extern "C" wf_status wf_problem_destroy(wf_problem* p) {
+  if (p) {
+    cudaDeviceSynchronize();
+    free_problem(p);
+  }
+  return WF_OK;
+}
+
+WfBufs wf_bufs(const wf_problem* p) {
+  WfBufs b;
+  b.d = p->d;
+  b.w = p->w;
+  b.sp = p->sp;
+  b.sp_stride = p->sp_stride;
+  b.scratch = p->scratch;
+  b.part = p->part;
+  b.tw = p->precision == WF_FP64 ? p->h->tw64 : p->h->tw32;
+  b.B = p->count;
+  return b;
+}
+
+#define WF_DISPATCH(p, call)                                                    \
+  ((p)->precision == WF_FP64 ? call<double> : call<float>)
+
+extern "C" wf_status wf_problem_set_data(wf_problem* p, const void* d, void* stream) {
+  if (!p || !d) return wf_fail(WF_EINVAL, "wf_problem_set_data: null argument");
+  cudaError_t e = WF_DISPATCH(p, wf_launch_set_data)(p->g, d, p->count, p->d, (cudaStream_t)stream);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_problem_set_data");
+}
+
+extern "C" wf_status wf_eval(wf_problem* p, const void* s, void* grad, double* chi2, void* stream) {
+  if (!p || !s || !grad) return wf_fail(WF_EINVAL, "wf_eval: null argument");
+  if (s == grad) return wf_fail(WF_EINVAL, "wf_eval: s and grad must not alias");
+  WfBufs b = wf_bufs(p);
+  cudaError_t e = WF_DISPATCH(p, wf_launch_eval)(p->g, b, WF_ROW_DATA, WF_IN_STD, s, grad, chi2,
+                                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_eval");
+}
+
+extern "C" wf_status wf_hess_vec(wf_problem* p, const void* v, void* hv, void* stream) {
+  if (!p || !v || !hv) return wf_fail(WF_EINVAL, "wf_hess_vec: null argument");
+  if (v == hv) return wf_fail(WF_EINVAL, "wf_hess_vec: v and hv must not alias");
+  WfBufs b = wf_bufs(p);
+  cudaError_t e = WF_DISPATCH(p, wf_launch_eval)(p->g, b, WF_ROW_NODATA, WF_IN_STD, v, hv, nullptr,
+                                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_hess_vec");
+}
+
+extern "C" wf_status wf_signal_map(wf_problem* p, const void* s, void* x, void* stream) {
+  if (!p || !s || !x) return wf_fail(WF_EINVAL, "wf_signal_map: null argument");
+  WfBufs b = wf_bufs(p);
+  cudaError_t e = WF_DISPATCH(p, wf_launch_signal)(p->g, b, WF_IN_STD, s, x, (cudaStream_t)stream);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_signal_map");
+}
+
+extern "C" wf_status wf_simulate_data(wf_problem* p, const void* z, const void* noise, void* d_out,
+                                      void* stream) {
+  if (!p || !z || !noise || !d_out) return wf_fail(WF_EINVAL, "wf_simulate_data: null argument");
+  WfBufs b = wf_bufs(p);
+  cudaError_t e = WF_DISPATCH(p, wf_launch_simulate)(p->g, b, z, noise, d_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_simulate_data");
+}
+
+extern "C" wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
+                                    const double* theta, int n_bands, double* E, void* stream) {
+  if (!p || !s || !band || !theta || !E) return wf_fail(WF_EINVAL, "wf_band_energy: null argument");
+  if (n_bands < 1 || n_bands > 4096) return wf_fail(WF_EINVAL, "wf_band_energy: n_bands = %d", n_bands);
+  cudaError_t e = WF_DISPATCH(p, wf_launch_band_energy)(p->g, p->count, s, band, theta, n_bands, E,
+                                                        (cudaStream_t)stream);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_band_energy");
+}

@@ -1,0 +1,33 @@
+// Host-side structures of the C ABI (handle, prepared problem, solver state).
+#pragma once
+#include "wf_internal.h"
+
+struct wf_handle {
+  int device;
+  void* tw64;   // WF_NT double2 roots of unity
+  void* tw32;   // WF_NT float2 roots of unity
+};
+
+struct WfSolver;  // L-BFGS state, allocated on the first solve (wf_solve.cu)
+
+struct wf_problem {
+  wf_handle* h;
+  int count, n, C, dtype, precision, m;
+  WfGeo g;
+  size_t elt;            // bytes of the working type
+  int sp_shared;         // one sqrt(P) table serves every map
+  long long sp_stride;   // elements between maps' sqrt(P) tables
+  void* d;               // [count][C][n][n] working type
+  void* w;               // [count][C][n][n] mask * Ninv
+  void* sp;              // [1 or count][C][n][n/2+1] sqrt(P)/n
+  void* scratch;         // [count][C][n][n/2] complex
+  double* part;          // [count][WF_NSLOT][maxblk]
+  int* flags;            // device status words
+  WfSolver* solver;
+};
+
+wf_status wf_fail(wf_status s, const char* fmt, ...);
+wf_status wf_cuda_fail(cudaError_t e, const char* what);
+wf_status wf_alloc(void** ptr, size_t bytes, const char* what);
+WfBufs wf_bufs(const wf_problem* p);
+void wf_solver_free(wf_problem* p);

@@ -1,0 +1,183 @@
+// Shared-memory FFT building blocks for the Wiener-filter operator kernels.
+//
+// Transforms are power-of-two lengths L <= WF_NT held in shared memory as a
+// set of `cnt` independent sequences: sample j of sequence t sits at
+// buf[t * ts + j * js].  Each transform is a Stockham autosort FFT: a chain of
+// radix-R passes (R in {2, 4, 8, 16}), each pass reading R samples strided by
+// L/R, applying twiddles, doing a length-R DFT in registers and writing the R
+// results strided by the running span Ns.  Every thread stages all of its
+// butterflies in registers between two barriers, so a pass is in place.
+//
+// Sign convention: DIR = -1 is the forward transform sum_j x_j e^{-2 pi i jk/L},
+// DIR = +1 the unnormalised inverse.  Twiddles come from a table of the WF_NT-th
+// roots of unity, tw[k] = exp(-2 pi i k / WF_NT), computed on the host in long
+// double and staged in shared memory by the caller.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wf_internal.h"
+
+
+template <typename T> struct V2t;
+template <> struct V2t<float>  { typedef float2  type; };
+template <> struct V2t<double> { typedef double2 type; };
+
+template <typename T> using V2 = typename V2t<T>::type;
+
+template <typename T> __device__ __forceinline__ V2<T> mk(T x, T y) { V2<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ V2<T> cadd(V2<T> a, V2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ V2<T> csub(V2<T> a, V2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ V2<T> cmul(V2<T> a, V2<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ V2<T> conj_(V2<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ V2<T> cscale(V2<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// multiply by i
+template <typename T> __device__ __forceinline__ V2<T> mul_i(V2<T> a) { return mk<T>(-a.y, a.x); }
+
+// Sixteenth roots of unity, cos and sin of 2 pi k / 16 for k = 0..7, to the
+// precision of the mathematics (values of cos(pi/8), sqrt(2)/2, sin(pi/8)).
+#define WF_C1 0.9238795325112867561281832
+#define WF_S1 0.3826834323650897717284600
+#define WF_R2 0.7071067811865475244008444
+
+// Multiply v by exp(DIR * 2 pi i q / 16) with q known at compile time.
+template <typename T, int DIR, int Q>
+__device__ __forceinline__ V2<T> rot16(V2<T> v) {
+  static_assert(Q >= 0 && Q < 8, "root index");
+  constexpr T s = (T)DIR;  // sign of the angle
+  if constexpr (Q == 0) {
+    return v;
+  } else if constexpr (Q == 4) {  // exp(DIR i pi/2) = DIR * i
+    return (DIR > 0) ? mul_i<T>(v) : mk<T>(v.y, -v.x);
+  } else {
+    constexpr double cs[8] = {1.0, WF_C1, WF_R2, WF_S1, 0.0, -WF_S1, -WF_R2, -WF_C1};
+    constexpr double sn[8] = {0.0, WF_S1, WF_R2, WF_C1, 1.0, WF_C1, WF_R2, WF_S1};
+    const T c = (T)cs[Q], sv = s * (T)sn[Q];
+    return mk<T>(v.x * c - v.y * sv, v.x * sv + v.y * c);
+  }
+}
+
+template <int R> struct Log2R;
+template <> struct Log2R<1> { static constexpr int v = 0; };
+template <> struct Log2R<2> { static constexpr int v = 1; };
+template <> struct Log2R<4> { static constexpr int v = 2; };
+template <> struct Log2R<8> { static constexpr int v = 3; };
+template <> struct Log2R<16> { static constexpr int v = 4; };
+
+__host__ __device__ constexpr int bitrev_c(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+// Butterfly stage of an in-register radix-2 DIT network: span LEN, applied to
+// every group of LEN consecutive (bit-reversed) registers.
+template <typename T, int R, int DIR, int LEN, int Q>
+__device__ __forceinline__ void dit_q(V2<T>* v) {
+  if constexpr (Q < LEN / 2) {
+#pragma unroll
+    for (int s = 0; s < R; s += LEN) {
+      V2<T> a = v[s + Q];
+      V2<T> b = rot16<T, DIR, Q * (16 / LEN)>(v[s + Q + LEN / 2]);
+      v[s + Q] = cadd<T>(a, b);
+      v[s + Q + LEN / 2] = csub<T>(a, b);
+    }
+    dit_q<T, R, DIR, LEN, Q + 1>(v);
+  }
+}
+
+template <typename T, int R, int DIR, int LEN>
+__device__ __forceinline__ void dit_stages(V2<T>* v) {
+  if constexpr (LEN <= R) {
+    dit_q<T, R, DIR, LEN, 0>(v);
+    dit_stages<T, R, DIR, LEN * 2>(v);
+  }
+}
+
+// Length-R DFT in registers, natural order in and out: v_q <- sum_r v_r w^{DIR r q}.
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft_reg(V2<T>* v) {
+  constexpr int B = Log2R<R>::v;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int j = bitrev_c(i, B);
+    if (i < j) { V2<T> t = v[i]; v[i] = v[j]; v[j] = t; }
+  }
+  dit_stages<T, R, DIR, 2>(v);
+}
+
+// Twiddle exp(DIR * 2 pi i * k / WF_NT) from the shared table (k < WF_NT).
+template <typename T, int DIR>
+__device__ __forceinline__ V2<T> twid(const V2<T>* tw, int k) {
+  V2<T> w = tw[k];
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+// One Stockham pass.  EMAX = most samples a thread holds (compile time).
+template <typename T, int R, int DIR, int EMAX>
+__device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, int ts, int js,
+                                         int Ns, int lgNs, const V2<T>* tw) {
+  constexpr int NB = (EMAX / R) > 0 ? (EMAX / R) : 1;
+  constexpr int lgR = Log2R<R>::v;
+  const int lgLR = lgL - lgR;
+  const int LR = 1 << lgLR;
+  const int nbf = cnt << lgLR;
+  V2<T> v[NB][R];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = threadIdx.x + i * blockDim.x;
+    if (b < nbf) {
+      const int t = b >> lgLR, j = b & (LR - 1);
+      const V2<T>* base = buf + t * ts;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = base[(j + r * LR) * js];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = threadIdx.x + i * blockDim.x;
+    if (b < nbf) {
+      const int t = b >> lgLR, j = b & (LR - 1);
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+        // w_{Ns R}^{k r} = table[k r WF_NT / (Ns R)]
+        const int sh = WF_LOG2_NT - lgNs - lgR;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[i][r] = cmul<T>(v[i][r], twid<T, DIR>(tw, (k * r) << sh));
+      }
+      dft_reg<T, R, DIR>(v[i]);
+      const int o = ((j - k) << lgR) + k;
+      V2<T>* base = buf + t * ts;
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[(o + r * Ns) * js] = v[i][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full transform of `cnt` sequences of length L = 2^lgL (1 <= lgL <= 10).
+// Radix plan: ceil(lgL / 4) passes with the bits spread as evenly as possible,
+// larger radices first.  Requires cnt * L <= EMAX * blockDim.x.
+template <typename T, int DIR, int EMAX>
+__device__ __forceinline__ void fft_smem(V2<T>* buf, int lgL, int cnt, int ts, int js, const V2<T>* tw) {
+  const int L = 1 << lgL;
+  const int np = (lgL + 3) >> 2;
+  int rem = lgL, lgNs = 0;
+  for (int p = 0; p < np; ++p) {
+    const int left = np - p;
+    const int bits = (rem + left - 1) / left;  // ceil(rem / left)
+    const int Ns = 1 << lgNs;
+    switch (bits) {
+      case 4: fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
+      case 3: fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
+      case 2: fft_pass<T, 4, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
+      default: fft_pass<T, 2, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
+    }
+    rem -= bits;
+    lgNs += bits;
+  }
+}

@@ -1,0 +1,512 @@
+// Operator kernels of the Wiener-filter objective (Sec. 2.2, eq_chi / eq_cost).
+//
+// One objective+gradient pass over a batch of n x n maps is three kernels:
+//   k_col_inv  column stage of the inverse transform: load a tile of packed
+//              spectrum columns, multiply by R(k) sqrt(P)/n (step A1), inverse
+//              FFT along y (first half of A2), store the tile to scratch;
+//   k_row      row stage: c2r along x (rest of A2), pixel residual
+//              r = d - x, wr = w r and the data term sum r w r (A3), r2c of wr
+//              along x (first half of A4), store back to scratch;
+//   k_col_fwd  forward FFT along y (rest of A4), sqrt(P) R(k)^T / n (adjoint,
+//              A5), g = 2 (s - .), prior term sum |s|^2, store g.
+// Spectra are held in a packed half-plane layout [n][n/2] in which column 0
+// carries the two self-conjugate columns kx = 0 and kx = n/2 as X0 + i Xh;
+// the column FFT of that packed column is then an ordinary complex FFT whose
+// real and imaginary parts are the two real row-DC / row-Nyquist signals.
+// Only per-mode operations unpack it, pairing ky with n - ky.
+#pragma once
+#include "wf_fft.cuh"
+#include "wf_internal.h"
+
+template <typename T> __device__ __forceinline__ bool wf_isfinite(T x) { return isfinite(x); }
+
+// Sum over the block of one double per thread; valid in thread 0.
+__device__ __forceinline__ double wf_block_sum(double v) {
+  __shared__ double red[WF_THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < WF_THREADS / 32; ++i) r += red[i];
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void wf_stage_tw(V2<T>* s_tw, const V2<T>* g_tw) {
+  for (int i = threadIdx.x; i < WF_NT; i += blockDim.x) s_tw[i] = g_tw[i];
+}
+
+// Kaiser-Squires cosine / sine of half-plane mode (row j, column kx), kx in
+// [0, n/2]: c = (kx^2 - ky^2)/k^2, s = 2 kx ky / k^2 with ky the signed row
+// frequency (row n/2 taken as -n/2); s = 0 on the Nyquist row and column, and
+// R = identity at k = 0 (App. C operator divided by -k^2).
+template <typename T>
+__device__ __forceinline__ void wf_ks(int kx, int j, int n, T& c, T& s) {
+  const int h = n >> 1;
+  const int ky = j < h ? j : j - n;
+  const int k2 = kx * kx + ky * ky;
+  if (k2 == 0) { c = (T)1; s = (T)0; return; }
+  const T inv = (T)1 / (T)k2;
+  c = (T)(kx * kx - ky * ky) * inv;
+  s = (kx == h || ky == -h) ? (T)0 : (T)(2 * kx * ky) * inv;
+}
+
+// Per-mode operator on the C channel values of one mode.
+//   forward (ADJ = false): v <- R(k) diag(sp) v * extra        (step A1)
+//   adjoint (ADJ = true):  v <- diag(sp) R(k)^T v * extra      (step A5)
+// sp points at this map's [C][n][n/2+1] table of sqrt(P)/n.
+template <typename T, int C, bool ADJ>
+__device__ __forceinline__ void wf_mode_op(V2<T>* v, int j, int kx, int n, const T* sp, T extra) {
+  const int pitch = (n >> 1) + 1;
+  const T a0 = sp[j * pitch + kx] * extra;
+  if constexpr (C == 1) {
+    v[0] = cscale<T>(v[0], a0);
+  } else {
+    const T a1 = sp[(size_t)n * pitch + j * pitch + kx] * extra;
+    T c, s;
+    wf_ks<T>(kx, j, n, c, s);
+    if constexpr (!ADJ) {
+      const V2<T> e = cscale<T>(v[0], a0), b = cscale<T>(v[1], a1);
+      v[0] = mk<T>(c * e.x - s * b.x, c * e.y - s * b.y);
+      v[1] = mk<T>(s * e.x + c * b.x, s * e.y + c * b.y);
+    } else {
+      const V2<T> e = v[0], b = v[1];
+      v[0] = cscale<T>(mk<T>(c * e.x + s * b.x, c * e.y + s * b.y), a0);
+      v[1] = cscale<T>(mk<T>(-s * e.x + c * b.x, -s * e.y + c * b.y), a1);
+    }
+  }
+}
+
+// Unpack the packed column value pair (Y[j], Y[n-j]) into the kx = 0 and
+// kx = n/2 values at row j: X0 = (Y + conj Ym)/2, Xh = -i (Y - conj Ym)/2.
+template <typename T>
+__device__ __forceinline__ void wf_unpack0(V2<T> Y, V2<T> Ym, V2<T>& X0, V2<T>& Xh) {
+  X0 = mk<T>((T)0.5 * (Y.x + Ym.x), (T)0.5 * (Y.y - Ym.y));
+  const V2<T> dlt = mk<T>(Y.x - Ym.x, Y.y + Ym.y);  // Y - conj(Ym)
+  Xh = mk<T>((T)0.5 * dlt.y, (T)-0.5 * dlt.x);
+}
+// Y = X0 + i Xh
+template <typename T>
+__device__ __forceinline__ V2<T> wf_pack0(V2<T> X0, V2<T> Xh) { return mk<T>(X0.x - Xh.y, X0.y + Xh.x); }
+
+// Apply the per-mode operator to a column tile held as [n][C*TC] in shared
+// memory (element (row j, channel c, column t) at j*C*TC + c*TC + t), tile
+// starting at packed column kx0.  The packed column 0 is unpacked in pairs.
+template <typename T, int C, bool ADJ>
+__device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx0, const T* sp, T extra) {
+  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1;
+  for (int e = threadIdx.x; e < n * TC; e += blockDim.x) {
+    const int t = e & (TC - 1), j = e >> lgTC, kx = kx0 + t;
+    if (kx == 0) continue;
+    V2<T> v[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) v[c] = buf[j * CT + c * TC + t];
+    wf_mode_op<T, C, ADJ>(v, j, kx, n, sp, extra);
+#pragma unroll
+    for (int c = 0; c < C; ++c) buf[j * CT + c * TC + t] = v[c];
+  }
+  if (kx0 == 0) {
+    for (int j = threadIdx.x; j <= h; j += blockDim.x) {
+      const int jm = (n - j) & (n - 1);
+      V2<T> X0[C], Xh[C], X0m[C], Xhm[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const V2<T> Y = buf[j * CT + c * TC], Ym = buf[jm * CT + c * TC];
+        wf_unpack0<T>(Y, Ym, X0[c], Xh[c]);
+        wf_unpack0<T>(Ym, Y, X0m[c], Xhm[c]);
+      }
+      wf_mode_op<T, C, ADJ>(X0, j, 0, n, sp, extra);
+      wf_mode_op<T, C, ADJ>(Xh, j, h, n, sp, extra);
+      wf_mode_op<T, C, ADJ>(X0m, jm, 0, n, sp, extra);
+      wf_mode_op<T, C, ADJ>(Xhm, jm, h, n, sp, extra);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        buf[j * CT + c * TC] = wf_pack0<T>(X0[c], Xh[c]);
+        buf[jm * CT + c * TC] = wf_pack0<T>(X0m[c], Xhm[c]);
+      }
+    }
+  }
+}
+
+// Load a column tile of a spectrum given either packed ([C][n][h]) or in the
+// standard rfft2 layout ([C][n][h+1]); the tile is stored packed.
+template <typename T, int C, int IN>
+__device__ __forceinline__ V2<T> wf_load_spec(const V2<T>* src, int c, int j, int kx, int n) {
+  const int h = n >> 1;
+  if constexpr (IN == WF_IN_PK) {
+    return src[((size_t)c * n + j) * h + kx];
+  } else {
+    const V2<T>* row = src + ((size_t)c * n + j) * (h + 1);
+    if (kx == 0) return wf_pack0<T>(row[0], row[h]);
+    return row[kx];
+  }
+}
+
+template <typename T, int C, int IN>
+__device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n, int lgTC, int kx0) {
+  const int TC = 1 << lgTC, CT = C * TC, lgn = __ffs(n) - 1;
+  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
+    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+    buf[j * CT + c * TC + t] = wf_load_spec<T, C, IN>(src, c, j, kx0 + t, n);
+  }
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, int n, int lgTC, int kx0) {
+  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, lgn = __ffs(n) - 1;
+  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
+    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+    dst[((size_t)c * n + j) * h + kx0 + t] = buf[j * CT + c * TC + t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_col_inv: spectrum tile -> R sqrt(P)/n -> inverse FFT along y -> scratch
+// ---------------------------------------------------------------------------
+template <typename T, int C, int IN>
+__global__ void __launch_bounds__(WF_THREADS)
+k_col_inv(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_tw = (V2<T>*)wf_smem;
+  V2<T>* buf = s_tw + WF_NT;
+  const int b = blockIdx.y, n = g.n, h = g.h;
+  const int lgTC = __ffs(g.TC) - 1, kx0 = blockIdx.x * g.TC;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
+  wf_tile_load<T, C, IN>(buf, (const V2<T>*)src_ + (size_t)b * sstride, n, lgTC, kx0);
+  __syncthreads();
+  wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
+  __syncthreads();
+  fft_smem<T, +1, WF_EMAX>(buf, g.lgn, C * g.TC, 1, C * g.TC, s_tw);
+  wf_tile_store_pk<T, C>((V2<T>*)scratch_ + (size_t)b * C * n * h, buf, n, lgTC, kx0);
+}
+
+// ---------------------------------------------------------------------------
+// k_col_fwd: scratch tile -> forward FFT along y -> sqrt(P) R^T / n = a ->
+// out = 2 (src - a) (the gradient, or the Hessian-vector product when the row
+// stage ran without data); prior partial sum |src|^2 with half-plane weights.
+// ---------------------------------------------------------------------------
+template <typename T, int C, int IN>
+__global__ void __launch_bounds__(WF_THREADS)
+k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const void* scratch_,
+          void* dst_, double* part, const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_tw = (V2<T>*)wf_smem;
+  V2<T>* buf = s_tw + WF_NT;
+  const int b = blockIdx.y, n = g.n, h = g.h, lgn = g.lgn;
+  const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  {
+    const V2<T>* sc = (const V2<T>*)scratch_ + (size_t)b * C * n * h;
+    for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
+      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+      buf[j * CT + c * TC + t] = sc[((size_t)c * n + j) * h + kx0 + t];
+    }
+  }
+  __syncthreads();
+  fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
+  wf_col_scale<T, C, true>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
+  __syncthreads();
+  const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
+  const V2<T>* src = (const V2<T>*)src_ + (size_t)b * sstride;
+  V2<T>* dst = (V2<T>*)dst_ + (size_t)b * sstride;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
+    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+    const int kx = kx0 + t;
+    const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n);
+    const V2<T> a = buf[j * CT + c * TC + t];
+    const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
+    const T m2 = sv.x * sv.x + sv.y * sv.y;
+    acc += (kx == 0) ? (double)m2 : 2.0 * (double)m2;
+    if constexpr (IN == WF_IN_PK) {
+      dst[((size_t)c * n + j) * h + kx] = o;
+    } else {
+      if (kx == 0) buf[j * CT + c * TC + t] = o;
+      else dst[((size_t)c * n + j) * (h + 1) + kx] = o;
+    }
+  }
+  if constexpr (IN == WF_IN_STD) {
+    if (kx0 == 0) {
+      __syncthreads();
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int jm = (n - j) & (n - 1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          V2<T> X0, Xh;
+          wf_unpack0<T>(buf[j * CT + c * TC], buf[jm * CT + c * TC], X0, Xh);
+          V2<T>* row = dst + ((size_t)c * n + j) * (h + 1);
+          row[0] = X0;
+          row[h] = Xh;
+        }
+      }
+    }
+  }
+  const double tot = wf_block_sum(acc);
+  if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_PRIOR) * g.maxblk + blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// k_col_sim: scratch tile holding the row r2c of a white field z -> forward
+// FFT along y -> scale by 1/n (unitary U z) -> R sqrt(P)/n -> inverse FFT
+// along y -> scratch.  Used to synthesise A z for simulations.
+// ---------------------------------------------------------------------------
+template <typename T, int C>
+__global__ void __launch_bounds__(WF_THREADS)
+k_col_sim(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_tw = (V2<T>*)wf_smem;
+  V2<T>* buf = s_tw + WF_NT;
+  const int b = blockIdx.y, n = g.n, h = g.h, lgn = g.lgn;
+  const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  V2<T>* sc = (V2<T>*)scratch_ + (size_t)b * C * n * h;
+  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
+    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+    buf[j * CT + c * TC + t] = sc[((size_t)c * n + j) * h + kx0 + t];
+  }
+  __syncthreads();
+  fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
+  wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1 / (T)n);
+  __syncthreads();
+  fft_smem<T, +1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
+  wf_tile_store_pk<T, C>(sc, buf, n, lgTC, kx0);
+}
+
+// ---------------------------------------------------------------------------
+// k_row: row stage over RB of the C*n rows of each map.
+//   MODE DATA / NODATA: c2r, r = d - x (or -x), wr = w r, data partial sum
+//     r.wr, r2c of wr, store packed rows back to scratch.
+//   MODE SIGNAL: c2r, write x to out (pixel layout).
+//   MODE SIM: c2r, out = (w > 0) ? x + aux : 0 (aux = noise).
+//   MODE RFFT: r2c of the pixel rows of aux (a white field), store to scratch.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(WF_THREADS)
+k_row(WfGeo g, void* scratch_, const void* d_, const void* w_, const void* aux_, void* out_,
+      double* part, const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_tw = (V2<T>*)wf_smem;
+  V2<T>* buf = s_tw + WF_NT;
+  const int b = blockIdx.y, n = g.n, h = g.h, lgh = g.lgh, RB = g.RB;
+  const int row0 = blockIdx.x * RB;
+  const size_t npix = (size_t)g.C * n * n;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  V2<T>* sc = (V2<T>*)scratch_ + (size_t)b * g.C * n * h + (size_t)row0 * h;
+  const int tot = RB * h;
+  const int lgNTn = WF_LOG2_NT - g.lgn;  // table stride of the n-th roots
+  double acc = 0.0;
+
+  if constexpr (MODE == WF_ROW_RFFT) {
+    const V2<T>* z = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * n);
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) buf[e] = z[e];
+    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) buf[e] = sc[e];
+    __syncthreads();
+    // c2r pre-processing: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]),
+    // w = exp(+2 pi i / n), X[0], X[h] the real parts packed in Y[0].
+    for (int e = threadIdx.x; e < RB * (h / 2 + 1); e += blockDim.x) {
+      const int t = e / (h / 2 + 1), k = e - t * (h / 2 + 1);
+      V2<T>* row = buf + t * h;
+      if (k == 0) {
+        const V2<T> Y = row[0];
+        row[0] = mk<T>(Y.x + Y.y, Y.x - Y.y);
+      } else {
+        const int km = h - k;
+        const V2<T> Xk = row[k], Xm = row[km];
+        const V2<T> w1 = twid<T, +1>(s_tw, k << lgNTn), w2 = twid<T, +1>(s_tw, km << lgNTn);
+        const V2<T> s1 = mk<T>(Xk.x + Xm.x, Xk.y - Xm.y), d1 = mk<T>(Xk.x - Xm.x, Xk.y + Xm.y);
+        const V2<T> s2 = mk<T>(Xm.x + Xk.x, Xm.y - Xk.y), d2 = mk<T>(Xm.x - Xk.x, Xm.y + Xk.y);
+        row[k] = cadd<T>(s1, mul_i<T>(cmul<T>(w1, d1)));
+        row[km] = cadd<T>(s2, mul_i<T>(cmul<T>(w2, d2)));
+      }
+    }
+    __syncthreads();
+    fft_smem<T, +1, WF_EMAX>(buf, lgh, RB, h, 1, s_tw);
+    // pixel stage: buf[t][m] holds pixels (2m, 2m+1) of row row0 + t
+    const V2<T>* dv = (const V2<T>*)((const T*)d_ + (size_t)b * npix + (size_t)row0 * n);
+    const V2<T>* wv = (const V2<T>*)((const T*)w_ + (size_t)b * npix + (size_t)row0 * n);
+    if constexpr (MODE == WF_ROW_SIGNAL) {
+      V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * n);
+      for (int e = threadIdx.x; e < tot; e += blockDim.x) ov[e] = buf[e];
+      return;
+    } else if constexpr (MODE == WF_ROW_SIM) {
+      V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * n);
+      const V2<T>* nz = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * n);
+      for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const V2<T> x = buf[e], w = wv[e], q = nz[e];
+        ov[e] = mk<T>(w.x > (T)0 ? x.x + q.x : (T)0, w.y > (T)0 ? x.y + q.y : (T)0);
+      }
+      return;
+    } else {
+      float accf = 0.f;
+      for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const V2<T> x = buf[e], w = wv[e];
+        V2<T> r;
+        if constexpr (MODE == WF_ROW_DATA) {
+          const V2<T> dd = dv[e];
+          r = mk<T>(dd.x - x.x, dd.y - x.y);
+        } else {
+          r = mk<T>(-x.x, -x.y);
+        }
+        const V2<T> wr = mk<T>(w.x * r.x, w.y * r.y);
+        if constexpr (sizeof(T) == 4) accf += r.x * wr.x + r.y * wr.y;
+        else acc += (double)(r.x * wr.x) + (double)(r.y * wr.y);
+        buf[e] = wr;
+      }
+      acc += (double)accf;
+      __syncthreads();
+    }
+  }
+  // r2c: forward FFT of the packed pairs, then
+  // X[k] = (Z[k] + conj Z[h-k])/2 - i w^-k (Z[k] - conj Z[h-k])/2, X[0], X[h] packed.
+  fft_smem<T, -1, WF_EMAX>(buf, lgh, RB, h, 1, s_tw);
+  for (int e = threadIdx.x; e < RB * (h / 2 + 1); e += blockDim.x) {
+    const int t = e / (h / 2 + 1), k = e - t * (h / 2 + 1);
+    V2<T>* row = buf + t * h;
+    if (k == 0) {
+      const V2<T> Z = row[0];
+      row[0] = mk<T>(Z.x + Z.y, Z.x - Z.y);
+    } else {
+      const int km = h - k;
+      const V2<T> Zk = row[k], Zm = row[km];
+      const V2<T> w1 = twid<T, -1>(s_tw, k << lgNTn), w2 = twid<T, -1>(s_tw, km << lgNTn);
+      const V2<T> s1 = mk<T>(Zk.x + Zm.x, Zk.y - Zm.y), d1 = mk<T>(Zk.x - Zm.x, Zk.y + Zm.y);
+      const V2<T> s2 = mk<T>(Zm.x + Zk.x, Zm.y - Zk.y), d2 = mk<T>(Zm.x - Zk.x, Zm.y + Zk.y);
+      const V2<T> i1 = mul_i<T>(cmul<T>(w1, d1)), i2 = mul_i<T>(cmul<T>(w2, d2));
+      row[k] = mk<T>((T)0.5 * (s1.x - i1.x), (T)0.5 * (s1.y - i1.y));
+      row[km] = mk<T>((T)0.5 * (s2.x - i2.x), (T)0.5 * (s2.y - i2.y));
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) sc[e] = buf[e];
+  if constexpr (MODE == WF_ROW_DATA || MODE == WF_ROW_NODATA) {
+    const double s = wf_block_sum(acc);
+    if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;
+  }
+}
+
+// chi2[b] = sum of the prior and data partial sums, in a fixed order.
+static __global__ void __launch_bounds__(WF_THREADS)
+k_finalize_chi2(const double* part, int maxblk, int nprior, int ndata, double* chi2) {
+  const int b = blockIdx.x;
+  double acc = 0.0;
+  const double* pp = part + (size_t)b * WF_NSLOT * maxblk;
+  for (int i = threadIdx.x; i < nprior; i += blockDim.x) acc += pp[WF_SLOT_PRIOR * maxblk + i];
+  for (int i = threadIdx.x; i < ndata; i += blockDim.x) acc += pp[WF_SLOT_DATA * maxblk + i];
+  const double s = wf_block_sum(acc);
+  if (threadIdx.x == 0) chi2[b] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Input preparation: working-type copies of d, W = mask * Ninv, sqrt(P)/n,
+// with checks recorded in flags[0] as a wf_status bit set (1 << status).
+// ---------------------------------------------------------------------------
+struct WfMapPtrs { const void* d; const unsigned char* mask; const void* Ninv; const void* P; };
+
+template <typename S>
+__device__ __forceinline__ double wf_rd(const void* p, size_t i) { return (double)((const S*)p)[i]; }
+
+template <typename T>
+__global__ void k_prep(WfGeo g, const WfMapPtrs* maps, int in_f64, T* d, T* w, T* sp, int sp_shared,
+                       int* flags) {
+  const int b = blockIdx.y, n = g.n, C = g.C;
+  const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (g.h + 1);
+  const WfMapPtrs m = maps[b];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride) {
+    const size_t pix = i % ((size_t)n * n);
+    const double ni = in_f64 ? wf_rd<double>(m.Ninv, i) : wf_rd<float>(m.Ninv, i);
+    const double dv = m.d ? (in_f64 ? wf_rd<double>(m.d, i) : wf_rd<float>(m.d, i)) : 0.0;
+    const bool obs = m.mask[pix] != 0;
+    if (!isfinite(ni)) atomicOr(flags, 1 << WF_ENONFINITE);
+    else if (ni < 0.0) atomicOr(flags, 1 << WF_EINVAL);
+    if (obs && !isfinite(dv)) atomicOr(flags, 1 << WF_ENONFINITE);
+    const double wv = obs && isfinite(ni) && ni > 0.0 ? ni : 0.0;
+    w[(size_t)b * npix + i] = (T)wv;
+    d[(size_t)b * npix + i] = (T)(obs && isfinite(dv) ? dv : 0.0);
+  }
+  if (sp_shared && b > 0) return;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsp; i += stride) {
+    const double pv = in_f64 ? wf_rd<double>(m.P, i) : wf_rd<float>(m.P, i);
+    if (!isfinite(pv)) atomicOr(flags, 1 << WF_ENONFINITE);
+    else if (pv < 0.0) atomicOr(flags, 1 << WF_EINVAL);
+    const double s = (isfinite(pv) && pv > 0.0) ? sqrt(pv) / (double)n : 0.0;
+    sp[(size_t)b * nsp + i] = (T)s;
+  }
+}
+
+template <typename T>
+__global__ void k_set_data(size_t total, const T* src, T* d) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) d[i] = src[i];
+}
+
+// Standard [C][n][h+1] <-> packed [C][n][h] spectra.
+template <typename T>
+__global__ void k_pack(WfGeo g, int B, const V2<T>* in, V2<T>* out) {
+  const int n = g.n, h = g.h;
+  const size_t rows = (size_t)B * g.C * n;
+  const size_t total = rows * h, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const size_t r = i / h;
+    const int kx = (int)(i - r * h);
+    const V2<T>* row = in + r * (h + 1);
+    out[i] = kx == 0 ? wf_pack0<T>(row[0], row[h]) : row[kx];
+  }
+}
+
+template <typename T>
+__global__ void k_unpack(WfGeo g, int B, const V2<T>* in, V2<T>* out) {
+  const int n = g.n, h = g.h;
+  const size_t rows = (size_t)B * g.C * n;
+  const size_t total = rows * h, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const size_t r = i / h;
+    const int kx = (int)(i - r * h);
+    V2<T>* orow = out + r * (h + 1);
+    if (kx == 0) {
+      const int j = (int)(r % n);
+      const size_t r0 = r - j, rm = r0 + ((n - j) & (n - 1));
+      V2<T> X0, Xh;
+      wf_unpack0<T>(in[r * h], in[rm * h], X0, Xh);
+      orow[0] = X0;
+      orow[h] = Xh;
+    } else {
+      orow[kx] = in[i];
+    }
+  }
+}
+
+// E[b][l] = 1/(2 theta_l) sum over full-plane modes of band l of |s|^2 (eq. el),
+// from a standard-layout spectrum: half-plane weight 1 on kx = 0, n/2, else 2.
+template <typename T>
+__global__ void __launch_bounds__(WF_THREADS)
+k_band_energy(WfGeo g, const V2<T>* s, const int16_t* band, const double* theta, int n_bands,
+              double* E) {
+  extern __shared__ double s_bins[];
+  const int b = blockIdx.y, n = g.n, h = g.h;
+  const size_t nsp = (size_t)g.C * n * (h + 1);
+  for (int i = threadIdx.x; i < n_bands; i += blockDim.x) s_bins[i] = 0.0;
+  __syncthreads();
+  const V2<T>* sb = s + (size_t)b * nsp;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsp; i += stride) {
+    const int l = band[i];
+    if (l < 0 || l >= n_bands) continue;
+    const int kx = (int)(i % (h + 1));
+    const V2<T> v = sb[i];
+    const double m2 = (double)v.x * v.x + (double)v.y * v.y;
+    atomicAdd(&s_bins[l], (kx == 0 || kx == h) ? m2 : 2.0 * m2);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_bands; i += blockDim.x)
+    atomicAdd(&E[(size_t)b * n_bands + i], 0.5 * s_bins[i] / theta[i]);
+}

@@ -1,0 +1,211 @@
+// Host-side launchers of the operator kernels, instantiated once per working
+// type by wf_ops_f32.cu and wf_ops_f64.cu.
+#pragma once
+#include "wf_ops.cuh"
+
+namespace wfimpl {
+
+template <typename T> inline size_t col_smem(const WfGeo& g) {
+  return (WF_NT + (size_t)g.C * g.TC * g.n) * sizeof(V2<T>);
+}
+template <typename T> inline size_t row_smem(const WfGeo& g) {
+  return (WF_NT + (size_t)g.RB * g.h) * sizeof(V2<T>);
+}
+
+// Raise the dynamic shared-memory limit of a kernel once per device.
+template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes, int* done_mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && (*done_mask >> dev) & 1) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((WF_NT + WF_TILE) * sizeof(double2)));
+  if (e == cudaSuccess && dev < 32) *done_mask |= 1 << dev;
+  (void)bytes;
+  return e;
+}
+
+template <typename T, int C, int IN>
+cudaError_t col_inv(const WfGeo& g, const WfBufs& b, const void* src, cudaStream_t st) {
+  static int done = 0;
+  auto k = k_col_inv<T, C, IN>;
+  const size_t sm = col_smem<T>(g);
+  cudaError_t e = ensure_smem(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, b.tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int C, int IN>
+cudaError_t col_fwd(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st) {
+  static int done = 0;
+  auto k = k_col_fwd<T, C, IN>;
+  const size_t sm = col_smem<T>(g);
+  cudaError_t e = ensure_smem(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, dst,
+                                                b.part, b.tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int C>
+cudaError_t col_sim(const WfGeo& g, const WfBufs& b, cudaStream_t st) {
+  static int done = 0;
+  auto k = k_col_sim<T, C>;
+  const size_t sm = col_smem<T>(g);
+  cudaError_t e = ensure_smem(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t row(const WfGeo& g, const WfBufs& b, const void* aux, void* out, cudaStream_t st) {
+  static int done = 0;
+  auto k = k_row<T, MODE>;
+  const size_t sm = row_smem<T>(g);
+  cudaError_t e = ensure_smem(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.nrb, b.B), WF_THREADS, sm, st>>>(g, b.scratch, b.d, b.w, aux, out, b.part, b.tw);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t row_any(int mode, const WfGeo& g, const WfBufs& b, const void* aux, void* out,
+                    cudaStream_t st) {
+  switch (mode) {
+    case WF_ROW_DATA: return row<T, WF_ROW_DATA>(g, b, aux, out, st);
+    case WF_ROW_NODATA: return row<T, WF_ROW_NODATA>(g, b, aux, out, st);
+    case WF_ROW_SIGNAL: return row<T, WF_ROW_SIGNAL>(g, b, aux, out, st);
+    case WF_ROW_SIM: return row<T, WF_ROW_SIM>(g, b, aux, out, st);
+    case WF_ROW_RFFT: return row<T, WF_ROW_RFFT>(g, b, aux, out, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t col_inv_any(const WfGeo& g, const WfBufs& b, int in, const void* src, cudaStream_t st) {
+  if (g.C == 1) return in == WF_IN_PK ? col_inv<T, 1, WF_IN_PK>(g, b, src, st) : col_inv<T, 1, WF_IN_STD>(g, b, src, st);
+  return in == WF_IN_PK ? col_inv<T, 2, WF_IN_PK>(g, b, src, st) : col_inv<T, 2, WF_IN_STD>(g, b, src, st);
+}
+
+template <typename T>
+cudaError_t col_fwd_any(const WfGeo& g, const WfBufs& b, int in, const void* src, void* dst,
+                        cudaStream_t st) {
+  if (g.C == 1)
+    return in == WF_IN_PK ? col_fwd<T, 1, WF_IN_PK>(g, b, src, dst, st) : col_fwd<T, 1, WF_IN_STD>(g, b, src, dst, st);
+  return in == WF_IN_PK ? col_fwd<T, 2, WF_IN_PK>(g, b, src, dst, st) : col_fwd<T, 2, WF_IN_STD>(g, b, src, dst, st);
+}
+
+inline int grid1d(size_t total, int cap) {
+  size_t blocks = (total + 255) / 256;
+  if (blocks > (size_t)cap) blocks = cap;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
+}  // namespace wfimpl
+
+// Launcher definitions (explicitly instantiated per working type).
+  template <typename T>
+  cudaError_t wf_launch_prep(const WfGeo& g, const void* const* dptr,
+                                const unsigned char* const* mptr, const void* const* nptr,
+                                const void* const* pptr, int in_f64, int B, void* d, void* w,
+                                void* sp, int sp_shared, int* flags, cudaStream_t st) {
+    WfMapPtrs* hm = (WfMapPtrs*)malloc(sizeof(WfMapPtrs) * (size_t)B);
+    if (!hm) return cudaErrorMemoryAllocation;
+    for (int i = 0; i < B; ++i) hm[i] = WfMapPtrs{dptr[i], mptr[i], nptr[i], pptr[i]};
+    WfMapPtrs* dm = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&dm, sizeof(WfMapPtrs) * (size_t)B, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dm, hm, sizeof(WfMapPtrs) * (size_t)B,
+                                              cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      const size_t npix = (size_t)g.C * g.n * g.n;
+      k_prep<T><<<dim3(wfimpl::grid1d(npix, 1024), B), 256, 0, st>>>(g, dm, in_f64, (T*)d, (T*)w,
+                                                                     (T*)sp, sp_shared, flags);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (dm) cudaFreeAsync(dm, st);
+    free(hm);
+    return e;
+  }
+  template <typename T>
+  cudaError_t wf_launch_set_data(const WfGeo& g, const void* src, int B, void* d,
+                                    cudaStream_t st) {
+    const size_t total = (size_t)B * g.C * g.n * g.n;
+    k_set_data<T><<<wfimpl::grid1d(total, 4096), 256, 0, st>>>(total, (const T*)src, (T*)d);
+    return cudaGetLastError();
+  }
+  template <typename T>
+  cudaError_t wf_launch_eval(const WfGeo& g, const WfBufs& b, int row_mode, int in_layout,
+                                const void* src, void* dst, double* chi2, cudaStream_t st) {
+    cudaError_t e = wfimpl::col_inv_any<T>(g, b, in_layout, src, st);
+    if (e == cudaSuccess) e = wfimpl::row_any<T>(row_mode, g, b, nullptr, nullptr, st);
+    if (e == cudaSuccess) e = wfimpl::col_fwd_any<T>(g, b, in_layout, src, dst, st);
+    if (e == cudaSuccess && chi2) {
+      k_finalize_chi2<<<b.B, WF_THREADS, 0, st>>>(b.part, g.maxblk, g.ntile,
+                                                  row_mode == WF_ROW_DATA ? g.nrb : 0, chi2);
+      e = cudaGetLastError();
+    }
+    return e;
+  }
+  template <typename T>
+  cudaError_t wf_launch_signal(const WfGeo& g, const WfBufs& b, int in_layout, const void* src,
+                                  void* xout, cudaStream_t st) {
+    cudaError_t e = wfimpl::col_inv_any<T>(g, b, in_layout, src, st);
+    if (e == cudaSuccess) e = wfimpl::row_any<T>(WF_ROW_SIGNAL, g, b, nullptr, xout, st);
+    return e;
+  }
+  template <typename T>
+  cudaError_t wf_launch_simulate(const WfGeo& g, const WfBufs& b, const void* z,
+                                    const void* noise, void* dout, cudaStream_t st) {
+    cudaError_t e = wfimpl::row_any<T>(WF_ROW_RFFT, g, b, z, nullptr, st);
+    if (e == cudaSuccess)
+      e = g.C == 1 ? wfimpl::col_sim<T, 1>(g, b, st) : wfimpl::col_sim<T, 2>(g, b, st);
+    if (e == cudaSuccess) e = wfimpl::row_any<T>(WF_ROW_SIM, g, b, noise, dout, st);
+    return e;
+  }
+  template <typename T>
+  cudaError_t wf_launch_band_energy(const WfGeo& g, int B, const void* s, const int16_t* band,
+                                       const double* theta, int n_bands, double* E,
+                                       cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(E, 0, sizeof(double) * (size_t)B * n_bands, st);
+    if (e != cudaSuccess) return e;
+    const size_t nsp = (size_t)g.C * g.n * (g.h + 1);
+    k_band_energy<T><<<dim3(wfimpl::grid1d(nsp, 256), B), WF_THREADS,
+                       sizeof(double) * (size_t)n_bands, st>>>(g, (const V2<T>*)s, band, theta,
+                                                               n_bands, E);
+    return cudaGetLastError();
+  }
+  template <typename T>
+  cudaError_t wf_launch_pack(const WfGeo& g, int B, const void* in, void* out,
+                                cudaStream_t st) {
+    const size_t total = (size_t)B * g.C * g.n * g.h;
+    k_pack<T><<<wfimpl::grid1d(total, 4096), 256, 0, st>>>(g, B, (const V2<T>*)in, (V2<T>*)out);
+    return cudaGetLastError();
+  }
+  template <typename T>
+  cudaError_t wf_launch_unpack(const WfGeo& g, int B, const void* in, void* out,
+                                  cudaStream_t st) {
+    const size_t total = (size_t)B * g.C * g.n * g.h;
+    k_unpack<T><<<wfimpl::grid1d(total, 4096), 256, 0, st>>>(g, B, (const V2<T>*)in,
+                                                             (V2<T>*)out);
+    return cudaGetLastError();
+  }
+
+#define WF_INSTANTIATE(T)                                                                          \
+  template cudaError_t wf_launch_prep<T>(const WfGeo&, const void* const*,                         \
+                                         const unsigned char* const*, const void* const*,          \
+                                         const void* const*, int, int, void*, void*, void*, int,   \
+                                         int*, cudaStream_t);                                      \
+  template cudaError_t wf_launch_set_data<T>(const WfGeo&, const void*, int, void*, cudaStream_t); \
+  template cudaError_t wf_launch_eval<T>(const WfGeo&, const WfBufs&, int, int, const void*,       \
+                                         void*, double*, cudaStream_t);                            \
+  template cudaError_t wf_launch_signal<T>(const WfGeo&, const WfBufs&, int, const void*, void*,   \
+                                           cudaStream_t);                                          \
+  template cudaError_t wf_launch_simulate<T>(const WfGeo&, const WfBufs&, const void*,             \
+                                             const void*, void*, cudaStream_t);                    \
+  template cudaError_t wf_launch_band_energy<T>(const WfGeo&, int, const void*, const int16_t*,    \
+                                                const double*, int, double*, cudaStream_t);        \
+  template cudaError_t wf_launch_pack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);     \
+  template cudaError_t wf_launch_unpack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);

@@ -55,15 +55,16 @@ def mode_modulus(n: int) -> np.ndarray:
 
 def _disk_mask(n: int, rng, count: int, radius: float) -> np.ndarray:
     """Boolean map of `count` periodic disks of the given radius (True = hole)."""
-    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     holes = np.zeros((n, n), dtype=bool)
     cy = rng.integers(0, n, size=count)
     cx = rng.integers(0, n, size=count)
-    r2 = radius * radius
+    r = int(np.ceil(radius))
+    off = np.arange(-r, r + 1)
+    oy, ox = np.meshgrid(off, off, indexing="ij")
+    inside = (oy * oy + ox * ox) <= radius * radius
+    oy, ox = oy[inside], ox[inside]
     for y0, x0 in zip(cy, cx):
-        dy = (yy - y0 + n // 2) % n - n // 2
-        dx = (xx - x0 + n // 2) % n - n // 2
-        holes |= (dy * dy + dx * dx) <= r2
+        holes[(y0 + oy) % n, (x0 + ox) % n] = True
     return holes
 
 

@@ -1,0 +1,265 @@
+"""Thin Python binding of the C ABI in include/wf.h (ctypes; argument
+marshalling only).  Device memory and streams come from PyTorch; every
+computation runs in libwf.so.  Importing works without a GPU; the first call
+that needs the library raises if libwf.so has not been built."""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwf.so")
+
+WF_FP64, WF_MIXED = 0, 1
+WF_F32, WF_F64 = 0, 1
+STATUS = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENONFINITE", 3: "WF_ENOMEM", 4: "WF_ECUDA",
+          5: "WF_ENOTCONVERGED", 6: "WF_ELINESEARCH", 7: "WF_ETIMEOUT"}
+
+# Names declared in include/wf.h (checked against the header by the tests).
+EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_problem_create",
+           "wf_problem_destroy", "wf_problem_set_data", "wf_eval", "wf_hess_vec",
+           "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy"]
+
+
+class WfMap(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("Ninv", ctypes.c_void_p), ("P", ctypes.c_void_p)]
+
+
+class WfOpts(ctypes.Structure):
+    _fields_ = [("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("gtol_rel", ctypes.c_double), ("dchi2_abs", ctypes.c_double),
+                ("refresh_every", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class WfSolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("evals", ctypes.c_int), ("status", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("chi2", ctypes.c_double), ("gnorm_rel", ctypes.c_double)]
+
+
+class WfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libwf.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run paper_1810_00503_gb300.build.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.wf_last_error.restype = ctypes.c_char_p
+    L.wf_create.argtypes = [ctypes.POINTER(vp)]
+    L.wf_destroy.argtypes = [vp]
+    L.wf_opts_default.argtypes = [ctypes.POINTER(WfOpts)]
+    L.wf_opts_default.restype = None
+    L.wf_problem_create.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, i, i, vp, ctypes.POINTER(vp)]
+    L.wf_problem_destroy.argtypes = [vp]
+    L.wf_problem_set_data.argtypes = [vp, vp, vp]
+    L.wf_eval.argtypes = [vp, vp, vp, vp, vp]
+    L.wf_hess_vec.argtypes = [vp, vp, vp, vp]
+    L.wf_signal_map.argtypes = [vp, vp, vp, vp]
+    L.wf_map_solve.argtypes = [vp, ctypes.POINTER(WfOpts), vp, vp, vp, ctypes.POINTER(WfSolveStats)]
+    L.wf_simulate_data.argtypes = [vp, vp, vp, vp, vp]
+    L.wf_band_energy.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    for name in EXPORTS:
+        if name not in ("wf_last_error", "wf_opts_default"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise WfError(status, lib().wf_last_error().decode())
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+class Handle:
+    """wf_create / wf_destroy."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().wf_create(ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().wf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_handle = None
+
+
+def default_handle() -> Handle:
+    global _default_handle
+    if _default_handle is None:
+        _default_handle = Handle()
+    return _default_handle
+
+
+@dataclass
+class SolveResult:
+    s: object
+    x: object
+    stats: list
+
+
+class Problem:
+    """A prepared batch of maps of one shape (wf_problem_create).
+
+    d, Ninv: (B, C, n, n) CUDA tensors; mask: (B, n, n) or (n, n) uint8;
+    P: (B, C, n, n/2+1) or (C, n, n/2+1).  Floating inputs must share one dtype
+    (float32 or float64).  precision: "fp64" or "mixed".  State arrays (s, grad,
+    z, noise, outputs) use the working type: float64 for fp64, float32 for mixed."""
+
+    def __init__(self, d, mask, Ninv, P, precision="fp64", lbfgs_m=10, handle=None, stream=None):
+        import torch
+        self.handle = handle or default_handle()
+        B, C, n, _ = Ninv.shape
+        self.B, self.C, self.n = B, C, n
+        dtype = Ninv.dtype
+        if dtype not in (torch.float32, torch.float64):
+            raise TypeError("inputs must be float32 or float64")
+        self.precision = WF_FP64 if precision == "fp64" else WF_MIXED
+        self.wdtype = torch.float64 if self.precision == WF_FP64 else torch.float32
+        masks = mask if mask.dim() == 3 else mask.unsqueeze(0).expand(B, n, n)
+        Ps = P if P.dim() == 4 else P.unsqueeze(0).expand(B, *P.shape)
+        self._keep = (d, masks, Ninv, Ps)
+        arr = (WfMap * B)()
+        for b in range(B):
+            arr[b].d = _ptr(d[b]) if d is not None else 0
+            arr[b].mask = _ptr(masks[b])
+            arr[b].Ninv = _ptr(Ninv[b])
+            arr[b].P = _ptr(Ps[b])
+        out = ctypes.c_void_p()
+        _check(lib().wf_problem_create(self.handle.ptr, arr, B, n, C,
+                                       WF_F64 if dtype == torch.float64 else WF_F32,
+                                       self.precision, lbfgs_m, _stream(stream), ctypes.byref(out)))
+        self._p = out
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_p", None):
+            lib().wf_problem_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shapes -----------------------------------------------------------------
+    def spec_shape(self):
+        return (self.B, self.C, self.n, self.n // 2 + 1)
+
+    def pix_shape(self):
+        return (self.B, self.C, self.n, self.n)
+
+    def _cplx(self):
+        import torch
+        return torch.complex128 if self.precision == WF_FP64 else torch.complex64
+
+    def _spec(self, t):
+        import torch
+        if t.dtype != self._cplx() or tuple(t.shape) != self.spec_shape() or not t.is_contiguous():
+            raise ValueError(f"spectrum must be contiguous {self._cplx()} of shape {self.spec_shape()}")
+        return t
+
+    # calls --------------------------------------------------------------------
+    def eval(self, s, grad=None, chi2=None, stream=None):
+        import torch
+        self._spec(s)
+        grad = torch.empty_like(s) if grad is None else grad
+        chi2 = torch.empty(self.B, dtype=torch.float64, device=s.device) if chi2 is None else chi2
+        _check(lib().wf_eval(self._p, _ptr(s), _ptr(grad), _ptr(chi2), _stream(stream)))
+        return chi2, grad
+
+    def hess_vec(self, v, out=None, stream=None):
+        import torch
+        self._spec(v)
+        out = torch.empty_like(v) if out is None else out
+        _check(lib().wf_hess_vec(self._p, _ptr(v), _ptr(out), _stream(stream)))
+        return out
+
+    def signal_map(self, s, out=None, stream=None):
+        import torch
+        self._spec(s)
+        out = torch.empty(self.pix_shape(), dtype=self.wdtype, device=s.device) if out is None else out
+        _check(lib().wf_signal_map(self._p, _ptr(s), _ptr(out), _stream(stream)))
+        return out
+
+    def simulate(self, z, noise, out=None, stream=None):
+        import torch
+        for t in (z, noise):
+            if t.dtype != self.wdtype or tuple(t.shape) != self.pix_shape():
+                raise ValueError("z and noise must be working-type pixel maps")
+        out = torch.empty_like(z) if out is None else out
+        _check(lib().wf_simulate_data(self._p, _ptr(z), _ptr(noise), _ptr(out), _stream(stream)))
+        return out
+
+    def set_data(self, d, stream=None):
+        if d.dtype != self.wdtype or tuple(d.shape) != self.pix_shape():
+            raise ValueError("d must be a working-type pixel map batch")
+        _check(lib().wf_problem_set_data(self._p, _ptr(d), _stream(stream)))
+
+    def band_energy(self, s, band, theta, out=None, stream=None):
+        import torch
+        self._spec(s)
+        nb = int(theta.numel())
+        out = torch.empty((self.B, nb), dtype=torch.float64, device=s.device) if out is None else out
+        _check(lib().wf_band_energy(self._p, _ptr(s), _ptr(band), _ptr(theta), nb, _ptr(out),
+                                    _stream(stream)))
+        return out
+
+    def solve(self, s0=None, x_out=False, stream=None, **opts):
+        import torch
+        o = WfOpts()
+        lib().wf_opts_default(ctypes.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        o.stream = _stream(stream)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        s = torch.empty(self.spec_shape(), dtype=self._cplx(), device=dev)
+        x = torch.empty(self.pix_shape(), dtype=self.wdtype, device=dev) if x_out else None
+        st = (WfSolveStats * self.B)()
+        status = lib().wf_map_solve(self._p, ctypes.byref(o), _ptr(s0), _ptr(s), _ptr(x), st)
+        stats = [dict(iters=e.iters, evals=e.evals, status=STATUS.get(e.status, e.status),
+                      chi2=e.chi2, gnorm_rel=e.gnorm_rel) for e in st]
+        if status not in (0, 5):
+            _check(status)
+        return SolveResult(s=s, x=x, stats=stats)
