@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the Wiener-filter MAP hot path on GB300.
+
+Workload (default ``cmb_1024``): the band-power simulation batch of a CMB
+temperature patch, 1024 x 1024 pixels of 2 arcmin, analytic C_l, scan-striped
+noise, 15% galactic band plus 500 point-source holes; 120 maps = 100 noise-bias
+simulations + 20 Fisher simulations, all solved together.  Mixed precision:
+FP32 fields and FFTs, FP64 reductions and L-BFGS scalars.
+
+One step = one device L-BFGS iteration (memory 10) on every map of the batch:
+the direction from the two-loop recursion, one objective+gradient evaluation
+in Hessian-vector form (inverse column stage, row stage, forward column stage,
+adjoint), the exact step and the state update.  The metric is objective+gradient
+evaluations per second = maps x steps / time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own batch (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "objective+grad evals/s"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=120)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--m", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def config(args, world):
+    return {"workload": f"cmb_{args.n}: {args.batch} maps of {args.n}x{args.n} (100 noise-bias + 20 Fisher "
+                        f"simulations), 20 log l-bands, mixed FP32/FP64",
+            "n": args.n, "maps_per_gpu": args.batch, "lbfgs_m": args.m, "precision": "mixed",
+            "step": "one L-BFGS iteration on every map (1 Hessian-vector evaluation each)",
+            "l2_policy": "working set per step (~20 GB) far exceeds the 126 MB L2; no flush needed",
+            "parallelism": f"independent batches per GPU x{world}"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_problem(args, rank, dev):
+    import numpy as np
+    import torch
+    from paper_1810_00503_gb300 import synth, wf
+    inp = synth.cmb_patch(args.n, seed=3)
+    B = args.batch
+    g = torch.Generator(device=dev)
+    g.manual_seed(1000 + rank)
+    Ninv1 = torch.as_tensor(inp.Ninv, dtype=torch.float32, device=dev)
+    Ninv = Ninv1.unsqueeze(0).expand(B, -1, -1, -1).contiguous()
+    mask = torch.as_tensor(inp.mask, dtype=torch.uint8, device=dev)
+    P = torch.as_tensor(inp.P_half, dtype=torch.float32, device=dev)
+    prob = wf.Problem(torch.zeros_like(Ninv), mask, Ninv, P, precision="mixed", lbfgs_m=args.m)
+    z = torch.randn(B, 1, args.n, args.n, generator=g, device=dev)
+    sig = torch.where(Ninv > 0, torch.rsqrt(torch.clamp(Ninv, min=1e-30)), torch.zeros_like(Ninv))
+    noise = torch.randn(B, 1, args.n, args.n, generator=g, device=dev) * sig
+    d = prob.simulate(z, noise)
+    prob.set_data(d)
+    torch.cuda.synchronize()
+    host = dict(mask=inp.mask, Ninv=inp.Ninv.astype(np.float32), P=inp.P_half.astype(np.float32),
+                d=d.cpu().numpy())
+    return prob, host
+
+
+def algorithmic_bytes(n, m, elt=4):
+    """Compulsory DRAM bytes per map of each kernel of one iteration.
+    Packed state vector V = n * n/2 complex = 2 n^2 values; sqrt(P) table n (n/2+1)
+    values; w map n^2 values.
+    k_lb1 reads 2m ring vectors + g + s, writes s, g, p; reads sqrt(P).
+    k_lb_row reads w (the Hessian-vector product needs no data map).
+    k_lb3 reads p, g and m-1 ring Q vectors, writes q; reads sqrt(P)."""
+    V = 2 * n * n * elt
+    sp = n * (n // 2 + 1) * elt
+    lb1 = (2 * m + 2 + 3) * V + sp
+    row = n * n * elt
+    lb3 = (2 + (m - 1) + 1) * V + sp
+    return {"lb1": lb1, "row": row, "lb3": lb3}
+
+
+def run_ours(args, rank, world, dev):
+    import torch
+    from paper_1810_00503_gb300 import wf
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        prob, host = make_problem(args, rank, dev)
+        prob.start(gtol_rel=0.0, dchi2_abs=0.0, max_iter=1 << 30, check_every=1, use_graphs=1,
+                   refresh_every=0)
+        prob.step(args.warmup, sync=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clk:
+        clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        prob.step(args.steps, sync=False)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop() if clk else None
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    # per-kernel durations of the same iterations, events on the working stream
+    with torch.cuda.stream(stream):
+        kms = prob.profile(max(3, min(args.steps, 10)))
+        active = prob.step(0, sync=True)
+        res = prob.finish()
+    torch.cuda.synchronize()
+    out = dict(ms=ms, kernel_ms=kms, active=active, stats0=res.stats[0], prob=prob, host=host, clocks=clocks)
+    return out
+
+
+def run_e2e(args, dev, host, iters):
+    """End to end through the public API from pinned host buffers: copy the
+    batch's inputs to the device, prepare, solve `iters` iterations, copy the
+    MAP spectra back."""
+    import numpy as np
+    import torch
+    from paper_1810_00503_gb300 import wf
+    B, n = args.batch, args.n
+    h_d = torch.from_numpy(np.ascontiguousarray(host["d"])).pin_memory()
+    h_N = torch.from_numpy(np.ascontiguousarray(host["Ninv"][None].repeat(B, 0))).pin_memory()
+    h_m = torch.from_numpy(np.ascontiguousarray(host["mask"])).pin_memory()
+    h_P = torch.from_numpy(np.ascontiguousarray(host["P"])).pin_memory()
+    h_s = torch.empty((B, 1, n, n // 2 + 1), dtype=torch.complex64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_d, h_N, h_m, h_P))
+    d2h = h_s.numel() * h_s.element_size()
+    stream = torch.cuda.Stream(device=dev)
+    times, evals = [], []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            d = h_d.to(dev, non_blocking=True)
+            N = h_N.to(dev, non_blocking=True)
+            msk = h_m.to(dev, non_blocking=True)
+            P = h_P.to(dev, non_blocking=True)
+            prob = wf.Problem(d, msk, N, P, precision="mixed", lbfgs_m=args.m)
+            res = prob.solve(gtol_rel=0.0, max_iter=iters, check_every=iters, use_graphs=1)
+            h_s.copy_(res.s, non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        prob.close()
+        times.append(dt)
+        evals.append(sum(s["evals"] for s in res.stats))
+    dt = min(times)
+    ev = evals[times.index(dt)]
+    return {"value": ev / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / iters, "d2h_bytes_per_step": d2h / iters,
+            "iterations": iters, "evals": ev, "seconds": dt,
+            "note": "one wf_map_solve job from pinned host inputs incl. preparation; bytes per step = job bytes / iterations"}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(args, budget_s=12.0, host=None):
+    """Textbook FP64 L-BFGS (the oracle) on one map of the same workload,
+    as many iterations as fit in about budget_s seconds; returns evals/s."""
+    import numpy as np
+    from oracle import wf_oracle as O
+    from paper_1810_00503_gb300 import synth
+    inp = synth.cmb_patch(args.n, seed=3)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    W = inp.mask[None] * inp.Ninv
+    count = [0]
+    t_end = [None]
+
+    def fg(z):
+        count[0] += 1
+        r = d - O.apply_A(z, inp.P)
+        return float(np.sum(z * z) + np.sum(r * W * r)), 2.0 * (z - O.apply_At(W * r, inp.P))
+
+    state = {"t0": None}
+
+    def cb(it, x, f, g):
+        if time.perf_counter() - state["t0"] > budget_s:
+            raise StopIteration
+
+    fg(np.zeros_like(d))  # warm-up of numpy's FFT plans
+    count[0] = 0
+    state["t0"] = time.perf_counter()
+    try:
+        O.lbfgs(fg, np.zeros_like(d), m=args.m, gtol_rel=0.0, max_iter=10 ** 6, callback=cb)
+    except StopIteration:
+        pass
+    dt = time.perf_counter() - state["t0"]
+    return count[0] / dt, count[0], dt
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    """The oracle as the reference arm: K steps of its textbook L-BFGS on one
+    1024^2 map of the same workload (bounded sample), on the host cores."""
+    import numpy as np
+    from oracle import wf_oracle as O
+    from paper_1810_00503_gb300 import synth
+    inp = synth.cmb_patch(args.n, seed=3)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    W = inp.mask[None] * inp.Ninv
+    count = [0]
+
+    def fg(z):
+        count[0] += 1
+        r = d - O.apply_A(z, inp.P)
+        return float(np.sum(z * z) + np.sum(r * W * r)), 2.0 * (z - O.apply_At(W * r, inp.P))
+
+    marks = []
+
+    def cb(it, x, f, g):
+        marks.append((time.perf_counter(), count[0]))
+        if it >= args.warmup + args.steps:
+            raise StopIteration
+
+    try:
+        O.lbfgs(fg, np.zeros_like(d), m=args.m, gtol_rel=0.0, max_iter=args.warmup + args.steps, callback=cb)
+    except StopIteration:
+        pass
+    (t0, c0), (t1, c1) = marks[args.warmup - 1], marks[-1]
+    dt = t1 - t0
+    steps = len(marks) - args.warmup
+    value = (c1 - c0) / dt
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, 1),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": f"one {args.n}^2 map of the batch, {steps} textbook L-BFGS iterations "
+                                       f"(numpy FP64, single-threaded pocketfft)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    from paper_1810_00503_gb300 import build, wf
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=dev)
+    if not os.path.exists(wf.LIB_PATH):
+        if rank == 0:
+            build.build()
+        if world > 1:
+            torch.distributed.barrier()
+    r = run_ours(args, rank, world, dev)
+    B, K = args.batch, args.steps
+    value = world * B * K / (r["ms"] / 1000.0)
+    ab = algorithmic_bytes(args.n, args.m)
+    names = ["lb1", "row", "lb3", "scalar"]
+    kms = dict(zip(names, r["kernel_ms"]))
+    dom = max(("lb1", "row", "lb3"), key=lambda k: kms[k])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    achieved = ab[dom] * B / (kms[dom] / 1000.0) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": r["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": config(args, world),
+            "gpu_launches": 4 * K,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": ab[dom] * B,
+                         "kernel_ms": kms,
+                         "iteration_frac": sum(ab[k] for k in ("lb1", "row", "lb3")) * B
+                         / (sum(kms.values()) / 1000.0) / 1e9 / hbm},
+            "solver": {"maps_active_after": r["active"], "chi2_map0": r["stats0"]["chi2"],
+                       "gnorm_rel_map0": r["stats0"]["gnorm_rel"]}}
+    if rank == 0:
+        line["clocks"] = r["clocks"]
+        if not args.no_e2e:
+            line["e2e"] = run_e2e(args, dev, r["host"], iters=max(K, 10))
+        if not args.no_cpu:
+            v, cnt, dt = oracle_sample(args)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"textbook FP64 L-BFGS on one {args.n}^2 map of the batch, "
+                                              f"{cnt} objective+gradient evaluations in {dt:.1f} s "
+                                              f"(single-threaded numpy), of {cores_used()} host cores"}
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -116,8 +116,10 @@ void wf_opts_default(wf_opts* o);
  * WF_ENONFINITE) and allocates the device workspace: about
  * (4 + 2 m) C n^2 values of the working type per map plus scratch.
  * maps: HOST array of `count` descriptors holding device pointers.
- * dtype: WF_F32 or WF_F64 for every floating array of the maps and of later
- * calls on this problem (s, grad, s_out, x_out, z, noise).
+ * dtype: WF_F32 or WF_F64, the type of the maps' d, Ninv and P.  Every state
+ * or output array of later calls (s, grad, v, hv, s0, s_out, x, x_out, z,
+ * noise, d_out and the d of wf_problem_set_data) uses the WORKING type:
+ * double for WF_FP64, float for WF_MIXED (complex = two of them).
  * precision: WF_FP64 computes everything in FP64; WF_MIXED keeps fields and
  * FFTs in FP32 and all reductions and L-BFGS scalars in FP64.
  * Synchronises the stream once (to read the input check).  Paper: Sec. 2
@@ -127,14 +129,14 @@ wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, 
                             wf_problem** out);
 wf_status wf_problem_destroy(wf_problem* p);
 
-/* Replace the data maps d of every map (device [count][C][n][n], problem
- * dtype); masked pixels are ignored.  Stream ordered, no synchronisation. */
+/* Replace the data maps d of every map (device [count][C][n][n], working
+ * type); masked pixels are ignored.  Stream ordered, no synchronisation. */
 wf_status wf_problem_set_data(wf_problem* p, const void* d, void* stream);
 
 /* One objective + gradient pass per map (Sec. 2.2, eq_chi and eq_cost):
  *   chi2[b] = |s_hat_b|^2 + (d_b - x_b)^T W_b (d_b - x_b)
  *   grad[b] = d chi2 / d s_hat = 2 (s_hat - sqrt P R^T U W (d - x))
- * s: device [count][C][n][n/2+1] complex of the problem dtype (whitened modes,
+ * s: device [count][C][n][n/2+1] complex of the working type (whitened modes,
  * Hermitian-consistent in the kx = 0 and kx = n/2 columns); grad: same shape,
  * written; chi2: device double [count], written; any may alias nothing else.
  * Stream ordered, no synchronisation. */
@@ -159,16 +161,39 @@ wf_status wf_signal_map(wf_problem* p, const void* s, void* x, void* stream);
 wf_status wf_map_solve(wf_problem* p, const wf_opts* opts, const void* s0, void* s_out,
                        void* x_out, wf_solve_stats* stats);
 
+/* The same solve in three calls, for callers that drive the iterations
+ * themselves (benchmarks, checkpoints, time-sliced serving):
+ *   wf_solver_start  prepares the state at s0 (NULL = 0) with the true gradient;
+ *   wf_solver_step   runs exactly n_iter more iterations on every map still
+ *                    active; if n_active is not NULL it synchronises once and
+ *                    stores the number of maps still iterating (HOST int);
+ *   wf_solver_finish applies the last step, evaluates the true chi^2 and
+ *                    gradient, writes s_out / x_out (either may be NULL) and
+ *                    stats (HOST, may be NULL), and synchronises.
+ * opts are copied at start; stepping is stream ordered on opts->stream.
+ * Paper: Sec. 2.2 (L-BFGS minimisation of eq_chi). */
+wf_status wf_solver_start(wf_problem* p, const wf_opts* opts, const void* s0);
+wf_status wf_solver_step(wf_problem* p, int n_iter, int* n_active);
+wf_status wf_solver_finish(wf_problem* p, void* s_out, void* x_out, wf_solve_stats* stats);
+
+/* Diagnostic: run n_iter more iterations of a started solve with plain
+ * launches and CUDA events around each kernel on the working stream, and
+ * store the average duration in milliseconds of the four kernels of an
+ * iteration in ms (HOST float[4]): direction + inverse column stage, row
+ * stage, forward column stage + dot products, scalar step.  Synchronises
+ * after every iteration.  Not part of the method; used for roofline reports. */
+wf_status wf_solver_profile(wf_problem* p, int n_iter, float* ms);
+
 /* Data synthesis for simulations (Sec. 2.5, steps 1-2; eq. blmv):
  * d_b = mask * (A z_b + noise_b), z and noise device [count][C][n][n] of the
- * problem dtype (z white N(0,1), noise with variance 1/Ninv), d_out the same
+ * working type (z white N(0,1), noise with variance 1/Ninv), d_out the same
  * shape.  Uses each map's mask and P.  Stream ordered. */
 wf_status wf_simulate_data(wf_problem* p, const void* z, const void* noise, void* d_out,
                            void* stream);
 
 /* Band powers of the MAP fields (Sec. 2.4, eq. el):
  *   E[b][l] = 1/(2 Theta_l) sum over full-plane modes k in band l of |s_hat_k|^2
- * s: device spectra [count][C][n][n/2+1] (problem dtype); band: device int16
+ * s: device spectra [count][C][n][n/2+1] (working type); band: device int16
  * [C][n][n/2+1] band id per half-plane mode (-1 = none), ids < n_bands;
  * theta: device double [n_bands]; E: device double [count][n_bands], written.
  * Stream ordered. */

@@ -16,11 +16,43 @@
 #define WF_TILE (WF_THREADS * WF_EMAX)
 
 // Partial-sum slots per map (one FP64 value per block and slot).
-#define WF_SLOT_PRIOR 0
-#define WF_SLOT_DATA 1
-#define WF_SLOT_DOT0 2   // first of the L-BFGS dot-product slots
 #define WF_MAXM 32
-#define WF_NSLOT (WF_SLOT_DOT0 + 2 * WF_MAXM + 4)
+#define WF_SLOT_PRIOR 0                         // sum |s|^2 (half-plane weights)
+#define WF_SLOT_DATA 1                          // sum r W r
+#define WF_SLOT_OUT2 2                          // sum |out|^2 of the column-forward output
+#define WF_SLOT_GP 3                            // <g, P_i>, i < WF_MAXM
+#define WF_SLOT_GQ (WF_SLOT_GP + WF_MAXM)       // <g, Q_i>
+#define WF_SLOT_GG (WF_SLOT_GQ + WF_MAXM)       // <g, g>
+#define WF_SLOT_QQI (WF_SLOT_GG + 1)            // <q, Q_i>
+#define WF_SLOT_QQ (WF_SLOT_QQI + WF_MAXM)      // <q, q>
+#define WF_SLOT_PQ (WF_SLOT_QQ + 1)             // <p, q>
+#define WF_SLOT_GQN (WF_SLOT_PQ + 1)            // <g, q>
+#define WF_SLOT_GPN (WF_SLOT_GQN + 1)           // <g, p>
+#define WF_SLOT_PP (WF_SLOT_GPN + 1)            // <p, p>
+#define WF_NSLOT (WF_SLOT_PP + 1)
+
+// Per-map L-BFGS state, FP64, resident on the device.  The history holds m
+// pairs as unscaled directions P_i and their Hessian products Q_i = H P_i;
+// the curvature pair is (s_i, y_i) = (alpha_i P_i, alpha_i Q_i).  Dot products
+// among the stored vectors are kept as Gram matrices so that the two-loop
+// recursion runs on scalars.
+struct WfLbMap {
+  int k;            // iterations completed
+  int npairs;       // valid pairs in the ring (<= m)
+  int head;         // slot of the newest pair (-1: none)
+  int next;         // slot receiving the next direction
+  int active;       // 1 while iterating
+  int status;       // wf_status of this map
+  int evals;        // operator applications
+  int pend_slot;    // slot of the pending update
+  double pend_alpha;  // pending update s += a P[pend_slot], g += a Q[pend_slot]
+  double chi2, chi2_prev, gg, gg0;
+  double dg;                    // direction p = dg g + sum dP_i P_i + dQ_i Q_i
+  double dP[WF_MAXM], dQ[WF_MAXM];
+  double alpha[WF_MAXM];        // step of pair i
+  double gP[WF_MAXM], gQ[WF_MAXM];
+  double PP[WF_MAXM * WF_MAXM], PQ[WF_MAXM * WF_MAXM], QQ[WF_MAXM * WF_MAXM];
+};
 
 // Launch geometry of one (n, C) shape.
 struct WfGeo {
@@ -68,6 +100,24 @@ cudaError_t wf_launch_simulate(const WfGeo& g, const WfBufs& b, const void* z, c
 template <typename T>
 cudaError_t wf_launch_band_energy(const WfGeo& g, int B, const void* s, const int16_t* band,
                                   const double* theta, int n_bands, double* E, cudaStream_t st);
+// L-BFGS column kernels.  lb1 modes: full iteration, materialise only, dots only.
+enum { WF_LB1_FULL = 0, WF_LB1_MATERIALIZE = 1, WF_LB1_DOTS = 2 };
+struct WfLbBufs {
+  WfLbMap* st;      // [B]
+  void* s;          // packed state [B][C][n][h]
+  void* g;          // packed gradient
+  void* ring;       // [2m][B][C][n][h]: P slots then Q slots
+  int m;
+};
+template <typename T>
+cudaError_t wf_launch_lb1(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_lb3(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st);
+// Full objective+gradient pass on packed vectors (src -> dst), all maps.
+template <typename T>
+cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st);
 template <typename T>
 cudaError_t wf_launch_pack(const WfGeo& g, int B, const void* std_in, void* pk_out, cudaStream_t st);
 template <typename T>

@@ -216,7 +216,7 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
   const V2<T>* src = (const V2<T>*)src_ + (size_t)b * sstride;
   V2<T>* dst = (V2<T>*)dst_ + (size_t)b * sstride;
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
     const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
     const int kx = kx0 + t;
@@ -224,7 +224,9 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
     const V2<T> a = buf[j * CT + c * TC + t];
     const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
     const T m2 = sv.x * sv.x + sv.y * sv.y;
+    const T o2 = o.x * o.x + o.y * o.y;
     acc += (kx == 0) ? (double)m2 : 2.0 * (double)m2;
+    acc2 += (kx == 0) ? (double)o2 : 2.0 * (double)o2;
     if constexpr (IN == WF_IN_PK) {
       dst[((size_t)c * n + j) * h + kx] = o;
     } else {
@@ -250,6 +252,8 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   }
   const double tot = wf_block_sum(acc);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_PRIOR) * g.maxblk + blockIdx.x] = tot;
+  const double tot2 = wf_block_sum(acc2);
+  if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_OUT2) * g.maxblk + blockIdx.x] = tot2;
 }
 
 // ---------------------------------------------------------------------------
@@ -288,9 +292,8 @@ k_col_sim(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void
 //   MODE RFFT: r2c of the pixel rows of aux (a white field), store to scratch.
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void __launch_bounds__(WF_THREADS)
-k_row(WfGeo g, void* scratch_, const void* d_, const void* w_, const void* aux_, void* out_,
-      double* part, const void* tw_) {
+__device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* d_, const void* w_,
+                                           const void* aux_, void* out_, double* part, const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
@@ -391,6 +394,13 @@ k_row(WfGeo g, void* scratch_, const void* d_, const void* w_, const void* aux_,
     const double s = wf_block_sum(acc);
     if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;
   }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(WF_THREADS)
+k_row(WfGeo g, void* scratch_, const void* d_, const void* w_, const void* aux_, void* out_,
+      double* part, const void* tw_) {
+  k_row_body<T, MODE>(g, scratch_, d_, w_, aux_, out_, part, tw_);
 }
 
 // chi2[b] = sum of the prior and data partial sums, in a fixed order.

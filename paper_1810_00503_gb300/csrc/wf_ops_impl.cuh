@@ -1,7 +1,7 @@
 // Host-side launchers of the operator kernels, instantiated once per working
 // type by wf_ops_f32.cu and wf_ops_f64.cu.
 #pragma once
-#include "wf_ops.cuh"
+#include "wf_lbfgs.cuh"
 
 namespace wfimpl {
 
@@ -95,6 +95,48 @@ cudaError_t col_fwd_any(const WfGeo& g, const WfBufs& b, int in, const void* src
   if (g.C == 1)
     return in == WF_IN_PK ? col_fwd<T, 1, WF_IN_PK>(g, b, src, dst, st) : col_fwd<T, 1, WF_IN_STD>(g, b, src, dst, st);
   return in == WF_IN_PK ? col_fwd<T, 2, WF_IN_PK>(g, b, src, dst, st) : col_fwd<T, 2, WF_IN_STD>(g, b, src, dst, st);
+}
+
+template <typename T> inline size_t lb1_smem() {
+  return (WF_NT + 2 * (size_t)WF_TILE) * sizeof(V2<T>) + (2 * WF_MAXM + 1) * (WF_THREADS / 32) * sizeof(double) +
+         (2 * WF_MAXM + 1) * sizeof(int);
+}
+template <typename T> inline size_t lb3_smem() {
+  return (WF_NT + (size_t)WF_TILE) * sizeof(V2<T>) + (WF_MAXM + 5) * (WF_THREADS / 32) * sizeof(double) +
+         (WF_MAXM + 5) * sizeof(int);
+}
+
+template <typename K> inline cudaError_t ensure_smem_n(K kernel, size_t bytes, int* done_mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && (*done_mask >> dev) & 1) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev < 32) *done_mask |= 1 << dev;
+  return e;
+}
+
+template <typename T, int C>
+cudaError_t lb1(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st) {
+  static int done = 0;
+  auto k = k_lb1<T, C>;
+  const size_t sm = lb1_smem<T>();
+  cudaError_t e = ensure_smem_n(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb, b.part,
+                                                mode);
+  return cudaGetLastError();
+}
+
+template <typename T, int C>
+cudaError_t lb3(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  static int done = 0;
+  auto k = k_lb3<T, C>;
+  const size_t sm = lb3_smem<T>();
+  cudaError_t e = ensure_smem_n(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb, b.part);
+  return cudaGetLastError();
 }
 
 inline int grid1d(size_t total, int cap) {
@@ -193,6 +235,32 @@ inline int grid1d(size_t total, int cap) {
     return cudaGetLastError();
   }
 
+template <typename T>
+cudaError_t wf_launch_lb1(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st) {
+  return g.C == 1 ? wfimpl::lb1<T, 1>(g, b, lb, mode, st) : wfimpl::lb1<T, 2>(g, b, lb, mode, st);
+}
+template <typename T>
+cudaError_t wf_launch_lb3(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  return g.C == 1 ? wfimpl::lb3<T, 1>(g, b, lb, st) : wfimpl::lb3<T, 2>(g, b, lb, st);
+}
+template <typename T>
+cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  static int done = 0;
+  auto k = k_lb_row<T>;
+  const size_t sm = wfimpl::row_smem<T>(g);
+  cudaError_t e = wfimpl::ensure_smem(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.nrb, b.B), WF_THREADS, sm, st>>>(g, b.scratch, b.w, b.part, b.tw, lb.st);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st) {
+  cudaError_t e = wfimpl::col_inv_any<T>(g, b, WF_IN_PK, src, st);
+  if (e == cudaSuccess) e = wfimpl::row_any<T>(WF_ROW_DATA, g, b, nullptr, nullptr, st);
+  if (e == cudaSuccess) e = wfimpl::col_fwd_any<T>(g, b, WF_IN_PK, src, dst, st);
+  return e;
+}
+
 #define WF_INSTANTIATE(T)                                                                          \
   template cudaError_t wf_launch_prep<T>(const WfGeo&, const void* const*,                         \
                                          const unsigned char* const*, const void* const*,          \
@@ -208,4 +276,11 @@ inline int grid1d(size_t total, int cap) {
   template cudaError_t wf_launch_band_energy<T>(const WfGeo&, int, const void*, const int16_t*,    \
                                                 const double*, int, double*, cudaStream_t);        \
   template cudaError_t wf_launch_pack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);     \
-  template cudaError_t wf_launch_unpack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);
+  template cudaError_t wf_launch_unpack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);    \
+  template cudaError_t wf_launch_lb1<T>(const WfGeo&, const WfBufs&, const WfLbBufs&, int,          \
+                                        cudaStream_t);                                             \
+  template cudaError_t wf_launch_lb3<T>(const WfGeo&, const WfBufs&, const WfLbBufs&, cudaStream_t);\
+  template cudaError_t wf_launch_lb_row<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,           \
+                                           cudaStream_t);                                          \
+  template cudaError_t wf_launch_eval_pk<T>(const WfGeo&, const WfBufs&, const void*, void*,       \
+                                            cudaStream_t);

@@ -1,10 +1,610 @@
-// L-BFGS MAP driver (placeholder until the device solver lands).
+// Device-resident L-BFGS MAP driver (Sec. 2.2: the MAP field minimises chi^2;
+// L-BFGS builds a low-rank model of the curvature D, eq_curv, never forming it).
+//
+// One iteration for every map still active:
+//   k_lb1     s, g += a (P, Q) of the previous step; p = direction; <g, .>
+//   k_lb_row  row stage of H p (no data term)
+//   k_lb3     q = H p; <q, .>
+//   k_lb_scalar (one warp per map) exact step a = -g.p / p.Hp along p (the
+//             objective is quadratic, so this is the point a Wolfe line search
+//             converges to), chi^2 update, Gram-matrix update of the new pair
+//             (s, y) = (a p, a q), convergence test, and the two-loop recursion
+//             (Nocedal & Wright, Numerical Optimization, Alg. 7.4) evaluated on
+//             the Gram matrices to give the next direction's coefficients.
+// Iterations are captured in CUDA graphs, `check_every` per graph; the host
+// reads one counter of active maps per graph launch.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
 #include "wf_api_internal.h"
 
-void wf_solver_free(wf_problem* p) { (void)p; }
+struct WfScalarArgs {
+  double gtol2, dchi2;
+  int max_iter, m, ntile, nrb, maxblk, phase, init;
+};
+// Legacy and per-thread default stream handles cannot be captured; the solver
+// then runs on its own stream, ordered after the caller's with events.
+static inline bool wf_capturable(cudaStream_t s) {
+  return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
+struct WfSolver {
+  int m;
+  int B;
+  void* s;
+  void* g;
+  void* ring;
+  WfLbMap* st;
+  int* nact;          // device counter of active maps
+  int* nact_host;     // pinned
+  double* stats_dev;  // [B][4]: k, evals, status, chi2 ... see k_lb_final
+  double* stats_host; // pinned
+  cudaStream_t stream;
+  cudaEvent_t ev_in, ev_out;
+  cudaGraphExec_t exec;
+  int g_chunk, g_maxit, g_m;
+  double g_gtol2, g_dchi2;
+  int started;
+  cudaStream_t work, g_stream;  // stream in use; stream the graph was captured on
+  long long iters;     // iterations launched since the last start
+  wf_opts o;
+  WfScalarArgs A;
+};
+
+enum { WF_PH_ITER = 0, WF_PH_REFRESH = 1 };
+
+#define WF_SW 4  // warps (maps) per block of the scalar kernel
+
+__device__ __forceinline__ double wf_warp_slot(const double* pb, int slot, int nb, int maxblk) {
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int i = lane; i < nb; i += 32) v += pb[(size_t)slot * maxblk + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Two-loop recursion on coefficients: r = H_k g expressed over the basis
+// {g, P_i, Q_i}; the direction is p = -r.
+__device__ void wf_two_loop(WfLbMap& M, int m) {
+  const int np = M.npairs, head = M.head;
+  double cP[WF_MAXM], cQ[WF_MAXM], aa[WF_MAXM];
+  int W[WF_MAXM];
+  for (int i = 0; i < m; ++i) { cP[i] = 0.0; cQ[i] = 0.0; }
+  for (int q = 0; q < np; ++q) W[q] = (head - q + m) % m;
+  double cg = 1.0;
+  for (int q = 0; q < np; ++q) {  // newest to oldest
+    const int i = W[q];
+    double d = cg * M.gP[i];
+    for (int u = 0; u < np; ++u) {
+      const int l = W[u];
+      d += cP[l] * M.PP[i * WF_MAXM + l] + cQ[l] * M.PQ[i * WF_MAXM + l];
+    }
+    const double ai = M.alpha[i];
+    const double rho = 1.0 / (ai * ai * M.PQ[i * WF_MAXM + i]);
+    const double a = rho * ai * d;
+    aa[q] = a;
+    cQ[i] -= a * ai;
+  }
+  double gamma = 1.0;
+  if (np > 0) gamma = M.PQ[head * WF_MAXM + head] / M.QQ[head * WF_MAXM + head];
+  cg *= gamma;
+  for (int q = 0; q < np; ++q) { cP[W[q]] *= gamma; cQ[W[q]] *= gamma; }
+  for (int q = np - 1; q >= 0; --q) {  // oldest to newest
+    const int i = W[q];
+    double d = cg * M.gQ[i];
+    for (int u = 0; u < np; ++u) {
+      const int l = W[u];
+      d += cP[l] * M.PQ[l * WF_MAXM + i] + cQ[l] * M.QQ[i * WF_MAXM + l];
+    }
+    const double ai = M.alpha[i];
+    const double rho = 1.0 / (ai * ai * M.PQ[i * WF_MAXM + i]);
+    const double beta = rho * ai * d;
+    cP[i] += ai * (aa[q] - beta);
+  }
+  M.dg = -cg;
+  for (int i = 0; i < m; ++i) { M.dP[i] = -cP[i]; M.dQ[i] = -cQ[i]; }
+  M.next = (head + 1) % m;
+}
+
+__global__ void __launch_bounds__(32 * WF_SW)
+k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
+  __shared__ double S[WF_SW][WF_NSLOT];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * WF_SW + w;
+  if (b >= B) return;
+  WfLbMap& M = st[b];
+  const double* pb = part + (size_t)b * WF_NSLOT * A.maxblk;
+  const int m = A.m;
+  if (A.phase == WF_PH_ITER) {
+    if (!M.active) {
+      if (lane == 0) M.pend_alpha = 0.0;
+      return;
+    }
+    const int np = M.npairs, head = M.head;
+    S[w][WF_SLOT_GG] = wf_warp_slot(pb, WF_SLOT_GG, A.ntile, A.maxblk);
+    S[w][WF_SLOT_QQ] = wf_warp_slot(pb, WF_SLOT_QQ, A.ntile, A.maxblk);
+    S[w][WF_SLOT_PQ] = wf_warp_slot(pb, WF_SLOT_PQ, A.ntile, A.maxblk);
+    S[w][WF_SLOT_GQN] = wf_warp_slot(pb, WF_SLOT_GQN, A.ntile, A.maxblk);
+    S[w][WF_SLOT_GPN] = wf_warp_slot(pb, WF_SLOT_GPN, A.ntile, A.maxblk);
+    S[w][WF_SLOT_PP] = wf_warp_slot(pb, WF_SLOT_PP, A.ntile, A.maxblk);
+    for (int q = 0; q < np; ++q) {
+      const int sl = (head - q + m) % m;
+      S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ntile, A.maxblk);
+      S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ntile, A.maxblk);
+      S[w][WF_SLOT_QQI + sl] = wf_warp_slot(pb, WF_SLOT_QQI + sl, A.ntile, A.maxblk);
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    const double* Sw = S[w];
+    const int nx = M.next;
+    const double pq = Sw[WF_SLOT_PQ], qq = Sw[WF_SLOT_QQ], gq = Sw[WF_SLOT_GQN];
+    const double gp = Sw[WF_SLOT_GPN], pp = Sw[WF_SLOT_PP], ggk = Sw[WF_SLOT_GG];
+    M.evals += 1;
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(gp) || !isfinite(ggk)) {
+      M.status = (isfinite(pq) && isfinite(gp) && isfinite(ggk)) ? WF_ELINESEARCH : WF_ENONFINITE;
+      M.active = 0;
+      M.pend_alpha = 0.0;
+      return;
+    }
+    const double alpha = -gp / pq;
+    M.chi2_prev = M.chi2;
+    M.chi2 = M.chi2 + alpha * gp + 0.5 * alpha * alpha * pq;
+    int W[WF_MAXM];
+    double gPk[WF_MAXM], gQk[WF_MAXM], rowPP[WF_MAXM], rowPQ[WF_MAXM];
+    for (int q = 0; q < np; ++q) {
+      W[q] = (head - q + m) % m;
+      gPk[W[q]] = Sw[WF_SLOT_GP + W[q]];
+      gQk[W[q]] = Sw[WF_SLOT_GQ + W[q]];
+    }
+    // Gram row of the new direction p = dg g + sum (dP_l P_l + dQ_l Q_l), from the old entries.
+    for (int q = 0; q < np; ++q) {
+      const int i = W[q];
+      if (i == nx) continue;
+      double a = M.dg * gPk[i], c = M.dg * gQk[i];
+      for (int u = 0; u < np; ++u) {
+        const int l = W[u];
+        a += M.dP[l] * M.PP[l * WF_MAXM + i] + M.dQ[l] * M.PQ[i * WF_MAXM + l];
+        c += M.dP[l] * M.PQ[l * WF_MAXM + i] + M.dQ[l] * M.QQ[l * WF_MAXM + i];
+      }
+      rowPP[i] = a;
+      rowPQ[i] = c;
+    }
+    for (int q = 0; q < np; ++q) {
+      const int i = W[q];
+      if (i == nx) continue;
+      M.PP[nx * WF_MAXM + i] = M.PP[i * WF_MAXM + nx] = rowPP[i];
+      M.PQ[nx * WF_MAXM + i] = rowPQ[i];  // <p, Q_i>
+      M.PQ[i * WF_MAXM + nx] = rowPQ[i];  // <P_i, H p> = <H P_i, p>
+      M.QQ[nx * WF_MAXM + i] = M.QQ[i * WF_MAXM + nx] = Sw[WF_SLOT_QQI + i];
+    }
+    M.PP[nx * WF_MAXM + nx] = pp;
+    M.PQ[nx * WF_MAXM + nx] = pq;
+    M.QQ[nx * WF_MAXM + nx] = qq;
+    // dot products of g_{k+1} = g_k + alpha q with the stored vectors
+    for (int q = 0; q < np; ++q) {
+      const int i = W[q];
+      if (i == nx) continue;
+      M.gP[i] = gPk[i] + alpha * M.PQ[i * WF_MAXM + nx];
+      M.gQ[i] = gQk[i] + alpha * M.QQ[nx * WF_MAXM + i];
+    }
+    M.gP[nx] = gp + alpha * pq;
+    M.gQ[nx] = gq + alpha * qq;
+    double gg = ggk + 2.0 * alpha * gq + alpha * alpha * qq;
+    if (gg < 0.0) gg = 0.0;
+    M.gg = gg;
+    M.alpha[nx] = alpha;
+    M.pend_alpha = alpha;
+    M.pend_slot = nx;
+    M.head = nx;
+    M.npairs = np + 1 < m ? np + 1 : m;
+    M.next = (nx + 1) % m;
+    M.k += 1;
+    bool done = false;
+    if (!isfinite(M.chi2) || !isfinite(gg)) { done = true; M.status = WF_ENONFINITE; }
+    else if (gg <= A.gtol2 * M.gg0) { done = true; }
+    else if (A.dchi2 > 0.0 && fabs(M.chi2 - M.chi2_prev) < A.dchi2) { done = true; }
+    else if (M.k >= A.max_iter) { done = true; M.status = WF_ENOTCONVERGED; }
+    if (done) {
+      M.active = 0;
+    } else {
+      wf_two_loop(M, m);
+      atomicAdd(nact, 1);
+    }
+    return;
+  }
+  // WF_PH_REFRESH: true chi^2 and gradient at the current state, exact dots.
+  const int np = A.init ? 0 : M.npairs, head = M.head;
+  const double prior = wf_warp_slot(pb, WF_SLOT_PRIOR, A.ntile, A.maxblk);
+  const double data = wf_warp_slot(pb, WF_SLOT_DATA, A.nrb, A.maxblk);
+  const double gg = wf_warp_slot(pb, WF_SLOT_GG, A.ntile, A.maxblk);
+  for (int q = 0; q < np; ++q) {
+    const int sl = (head - q + m) % m;
+    S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ntile, A.maxblk);
+    S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ntile, A.maxblk);
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  if (A.init) {
+    M.k = 0;
+    M.npairs = 0;
+    M.head = -1;
+    M.next = 0;
+    M.status = WF_OK;
+    M.evals = 1;
+    M.gg0 = gg;
+    M.active = 1;
+    M.chi2_prev = prior + data;
+  } else {
+    M.evals += 1;
+  }
+  M.chi2 = prior + data;
+  M.gg = gg;
+  M.pend_alpha = 0.0;
+  if (!M.active) return;
+  for (int q = 0; q < np; ++q) {
+    const int sl = (head - q + m) % m;
+    M.gP[sl] = S[w][WF_SLOT_GP + sl];
+    M.gQ[sl] = S[w][WF_SLOT_GQ + sl];
+  }
+  bool done = false;
+  if (!isfinite(M.chi2) || !isfinite(gg)) { done = true; M.status = WF_ENONFINITE; }
+  else if (gg <= A.gtol2 * M.gg0) { done = true; M.status = WF_OK; }
+  else if (M.k >= A.max_iter) { done = true; M.status = WF_ENOTCONVERGED; }
+  if (done) {
+    M.active = 0;
+  } else {
+    wf_two_loop(M, m);
+    atomicAdd(nact, 1);
+  }
+}
+
+// Final statistics from the closing true evaluation: [k, evals, status, chi2, gnorm_rel].
+__global__ void k_lb_final(const WfLbMap* st, const double* part, int ntile, int nrb, int maxblk, int B,
+                           double* out) {
+  const int w = threadIdx.x >> 5;
+  const int b = blockIdx.x * WF_SW + w;
+  if (b >= B) return;
+  const double* pb = part + (size_t)b * WF_NSLOT * maxblk;
+  const double prior = wf_warp_slot(pb, WF_SLOT_PRIOR, ntile, maxblk);
+  const double data = wf_warp_slot(pb, WF_SLOT_DATA, nrb, maxblk);
+  const double g2 = wf_warp_slot(pb, WF_SLOT_OUT2, ntile, maxblk);
+  if ((threadIdx.x & 31) != 0) return;
+  const WfLbMap& M = st[b];
+  out[b * 5 + 0] = M.k;
+  out[b * 5 + 1] = M.evals + 1;
+  out[b * 5 + 2] = M.status;
+  out[b * 5 + 3] = prior + data;
+  out[b * 5 + 4] = M.gg0 > 0.0 ? sqrt(g2 / M.gg0) : 0.0;
+}
+
+void wf_solver_free(wf_problem* p) {
+  WfSolver* S = p->solver;
+  if (!S) return;
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  void* ptrs[] = {S->s, S->g, S->ring, S->st, S->nact, S->stats_dev};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (S->nact_host) cudaFreeHost(S->nact_host);
+  if (S->stats_host) cudaFreeHost(S->stats_host);
+  if (S->stream) cudaStreamDestroy(S->stream);
+  if (S->ev_in) cudaEventDestroy(S->ev_in);
+  if (S->ev_out) cudaEventDestroy(S->ev_out);
+  free(S);
+  p->solver = nullptr;
+}
+
+static wf_status ensure_solver(wf_problem* p, int m) {
+  if (p->solver && p->solver->m >= m) return WF_OK;
+  wf_solver_free(p);
+  WfSolver* S = (WfSolver*)calloc(1, sizeof(WfSolver));
+  if (!S) return wf_fail(WF_ENOMEM, "wf_map_solve: host allocation failed");
+  p->solver = S;
+  S->m = m;
+  S->B = p->count;
+  const size_t vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;  // packed complex = n^2 reals
+  wf_status s = wf_alloc(&S->s, vbytes, "L-BFGS state");
+  if (s == WF_OK) s = wf_alloc(&S->g, vbytes, "L-BFGS gradient");
+  if (s == WF_OK) s = wf_alloc(&S->ring, vbytes * 2 * m, "L-BFGS history");
+  if (s == WF_OK) s = wf_alloc((void**)&S->st, sizeof(WfLbMap) * p->count, "L-BFGS scalars");
+  if (s == WF_OK) s = wf_alloc((void**)&S->nact, sizeof(int), "active counter");
+  if (s == WF_OK) s = wf_alloc((void**)&S->stats_dev, sizeof(double) * 5 * p->count, "statistics");
+  cudaError_t e = cudaSuccess;
+  if (s == WF_OK) e = cudaMallocHost((void**)&S->nact_host, sizeof(int));
+  if (s == WF_OK && e == cudaSuccess) e = cudaMallocHost((void**)&S->stats_host, sizeof(double) * 5 * p->count);
+  if (s == WF_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (s == WF_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming);
+  if (s == WF_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming);
+  if (s == WF_OK && e != cudaSuccess) s = wf_cuda_fail(e, "wf_map_solve: solver set-up");
+  if (s != WF_OK) wf_solver_free(p);
+  return s;
+}
+
+#define WF_TRY(expr)                                    \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) return wf_cuda_fail(e_, #expr); \
+  } while (0)
+
+template <typename T>
+static cudaError_t iteration(const wf_problem* p, const WfBufs& b, const WfLbBufs& lb, const WfScalarArgs& A,
+                             WfSolver* S, cudaStream_t st) {
+  cudaError_t e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_FULL, st);
+  if (e == cudaSuccess) e = wf_launch_lb_row<T>(p->g, b, lb, st);
+  if (e == cudaSuccess) e = wf_launch_lb3<T>(p->g, b, lb, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S->nact, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_lb_scalar<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, A, p->count, S->nact);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <typename T>
+static cudaError_t refresh(const wf_problem* p, const WfBufs& b, const WfLbBufs& lb, WfScalarArgs A, int init,
+                           WfSolver* S, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (!init) e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_MATERIALIZE, st);
+  if (e == cudaSuccess) e = wf_launch_eval_pk<T>(p->g, b, lb.s, lb.g, st);
+  if (e == cudaSuccess) e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_DOTS, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S->nact, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    A.phase = WF_PH_REFRESH;
+    A.init = init;
+    k_lb_scalar<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, A, p->count, S->nact);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <typename T>
+static WfLbBufs lb_bufs(WfSolver* S) {
+  WfLbBufs lb;
+  lb.st = S->st;
+  lb.s = S->s;
+  lb.g = S->g;
+  lb.ring = S->ring;
+  lb.m = S->o.lbfgs_m;
+  return lb;
+}
+
+// Set up the state at s0 (or 0): true gradient, chi^2, first direction.
+template <typename T>
+static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
+  const int m = o->lbfgs_m;
+  wf_status rs = ensure_solver(p, m);
+  if (rs != WF_OK) return rs;
+  WfSolver* S = p->solver;
+  S->o = *o;
+  S->iters = 0;
+  cudaStream_t us = (cudaStream_t)o->stream;
+  cudaStream_t st = wf_capturable(us) ? us : S->stream;
+  if (S->exec && S->g_stream != st) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
+  S->work = st;
+  WfBufs b = wf_bufs(p);
+  WfLbBufs lb = lb_bufs<T>(S);
+  WfScalarArgs& A = S->A;
+  A.gtol2 = o->gtol_rel * o->gtol_rel;
+  A.dchi2 = o->dchi2_abs;
+  A.max_iter = o->max_iter;
+  A.m = m;
+  A.ntile = p->g.ntile;
+  A.nrb = p->g.nrb;
+  A.maxblk = p->g.maxblk;
+  A.phase = WF_PH_ITER;
+  A.init = 0;
+  WF_TRY(cudaEventRecord(S->ev_in, us));
+  WF_TRY(cudaStreamWaitEvent(st, S->ev_in, 0));
+  if (s0) WF_TRY(wf_launch_pack<T>(p->g, p->count, s0, S->s, st));
+  else WF_TRY(cudaMemsetAsync(S->s, 0, (size_t)p->count * p->C * p->n * p->n * p->elt, st));
+  WF_TRY(cudaMemsetAsync(S->st, 0, sizeof(WfLbMap) * p->count, st));
+  WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
+  const int chunk = o->check_every > 0 ? o->check_every : 16;
+  if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
+                         S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m)) {
+    if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
+    // Set every kernel's attributes outside capture: one iteration, then undo
+    // nothing (it is a genuine iteration of the solve).
+    WF_TRY(iteration<T>(p, b, lb, A, S, st));
+    S->iters += 1;
+    cudaGraph_t graph;
+    WF_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    cudaError_t ce = cudaSuccess;
+    for (int i = 0; i < chunk && ce == cudaSuccess; ++i) ce = iteration<T>(p, b, lb, A, S, st);
+    cudaError_t ee = cudaStreamEndCapture(st, &graph);
+    if (ce != cudaSuccess) return wf_cuda_fail(ce, "wf_solver_start: capture");
+    if (ee != cudaSuccess) return wf_cuda_fail(ee, "wf_solver_start: end capture");
+    ce = cudaGraphInstantiate(&S->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { S->exec = nullptr; return wf_cuda_fail(ce, "wf_solver_start: graph instantiate"); }
+    S->g_chunk = chunk;
+    S->g_maxit = o->max_iter;
+    S->g_gtol2 = A.gtol2;
+    S->g_dchi2 = A.dchi2;
+    S->g_m = m;
+    S->g_stream = st;
+  }
+  S->started = 1;
+  return WF_OK;
+}
+
+// Run n iterations (graph chunks plus plain launches for the remainder);
+// optionally read the number of maps still active (one synchronisation).
+template <typename T>
+static wf_status step_impl(wf_problem* p, int n_iter, int* n_active) {
+  WfSolver* S = p->solver;
+  const wf_opts* o = &S->o;
+  cudaStream_t st = S->work;
+  WfBufs b = wf_bufs(p);
+  WfLbBufs lb = lb_bufs<T>(S);
+  const int chunk = S->g_chunk > 0 ? S->g_chunk : 16;
+  int done = 0;
+  while (done < n_iter) {
+    if (o->refresh_every > 0 && S->iters > 0 && S->iters % o->refresh_every == 0)
+      WF_TRY(refresh<T>(p, b, lb, S->A, 0, S, st));
+    int left = n_iter - done;
+    if (o->refresh_every > 0) {
+      const int to_refresh = o->refresh_every - (int)(S->iters % o->refresh_every);
+      if (to_refresh < left) left = to_refresh;
+    }
+    if (o->use_graphs && S->exec && left >= chunk) {
+      WF_TRY(cudaGraphLaunch(S->exec, st));
+      done += chunk;
+      S->iters += chunk;
+    } else {
+      WF_TRY(iteration<T>(p, b, lb, S->A, S, st));
+      done += 1;
+      S->iters += 1;
+    }
+  }
+  if (n_active) {
+    WF_TRY(cudaMemcpyAsync(S->nact_host, S->nact, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WF_TRY(cudaStreamSynchronize(st));
+    *n_active = *S->nact_host;
+  }
+  return WF_OK;
+}
+
+// Apply the last step, evaluate the true chi^2 and gradient, write outputs.
+template <typename T>
+static wf_status finish_impl(wf_problem* p, void* s_out, void* x_out, wf_solve_stats* stats) {
+  WfSolver* S = p->solver;
+  cudaStream_t us = (cudaStream_t)S->o.stream, st = S->work;
+  WfBufs b = wf_bufs(p);
+  WfLbBufs lb = lb_bufs<T>(S);
+  WF_TRY(wf_launch_lb1<T>(p->g, b, lb, WF_LB1_MATERIALIZE, st));
+  WF_TRY(wf_launch_eval_pk<T>(p->g, b, lb.s, lb.g, st));
+  k_lb_final<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, p->g.ntile, p->g.nrb,
+                                                                    p->g.maxblk, p->count, S->stats_dev);
+  WF_TRY(cudaGetLastError());
+  if (s_out) WF_TRY(wf_launch_unpack<T>(p->g, p->count, S->s, s_out, st));
+  if (x_out) WF_TRY(wf_launch_signal<T>(p->g, b, WF_IN_PK, S->s, x_out, st));
+  WF_TRY(cudaMemcpyAsync(S->stats_host, S->stats_dev, sizeof(double) * 5 * p->count, cudaMemcpyDeviceToHost, st));
+  WF_TRY(cudaEventRecord(S->ev_out, st));
+  WF_TRY(cudaStreamWaitEvent(us, S->ev_out, 0));
+  WF_TRY(cudaStreamSynchronize(st));
+  S->started = 0;
+  int worst = WF_OK;
+  auto rank = [](int s) { return s == WF_ENONFINITE ? 3 : s == WF_ELINESEARCH ? 2 : s == WF_ENOTCONVERGED ? 1 : 0; };
+  for (int i = 0; i < p->count; ++i) {
+    const double* r = S->stats_host + 5 * i;
+    const int status = (int)r[2];
+    if (stats) {
+      stats[i].iters = (int)r[0];
+      stats[i].evals = (int)r[1];
+      stats[i].status = status;
+      stats[i].pad_ = 0;
+      stats[i].chi2 = r[3];
+      stats[i].gnorm_rel = r[4];
+    }
+    if (rank(status) > rank(worst)) worst = status;
+  }
+  if (worst != WF_OK) {
+    if (worst == WF_ENOTCONVERGED) wf_fail((wf_status)worst, "wf_map_solve: iteration limit reached");
+    else wf_fail((wf_status)worst, "wf_map_solve: a map stopped with status %d", worst);
+  }
+  return (wf_status)worst;
+}
+
+// Run n iterations with plain launches and CUDA events around each kernel on
+// the working stream; ms[0..3] = average duration of k_lb1, the row stage,
+// k_lb3 and the scalar step.
+template <typename T>
+static wf_status profile_impl(wf_problem* p, int n_iter, float* ms) {
+  WfSolver* S = p->solver;
+  cudaStream_t st = S->work;
+  WfBufs b = wf_bufs(p);
+  WfLbBufs lb = lb_bufs<T>(S);
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) WF_TRY(cudaEventCreate(&ev[i]));
+  double acc[4] = {0, 0, 0, 0};
+  wf_status rs = WF_OK;
+  for (int it = 0; it < n_iter && rs == WF_OK; ++it) {
+    cudaError_t e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_FULL, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = wf_launch_lb_row<T>(p->g, b, lb, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+    if (e == cudaSuccess) e = wf_launch_lb3<T>(p->g, b, lb, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->nact, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+      k_lb_scalar<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, S->A, p->count, S->nact);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+    if (e != cudaSuccess) rs = wf_cuda_fail(e, "wf_solver_profile");
+    S->iters += 1;
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  for (int k = 0; k < 4; ++k) ms[k] = n_iter > 0 ? (float)(acc[k] / n_iter) : 0.f;
+  return rs;
+}
+
+static wf_status check_opts(const wf_problem* p, const wf_opts* o) {
+  if (o->lbfgs_m < 1 || o->lbfgs_m > WF_MAXM)
+    return wf_fail(WF_EINVAL, "lbfgs_m = %d outside [1, %d]", o->lbfgs_m, WF_MAXM);
+  if (o->max_iter < 1) return wf_fail(WF_EINVAL, "max_iter must be >= 1");
+  if (!(o->gtol_rel >= 0.0) || !(o->dchi2_abs >= 0.0)) return wf_fail(WF_EINVAL, "tolerances must be >= 0");
+  if (o->check_every < 0 || o->check_every > 4096) return wf_fail(WF_EINVAL, "bad check_every");
+  if (o->refresh_every < 0) return wf_fail(WF_EINVAL, "bad refresh_every");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->h->device) return wf_fail(WF_EINVAL, "current device differs from the problem's");
+  return WF_OK;
+}
+
+extern "C" wf_status wf_solver_start(wf_problem* p, const wf_opts* opts, const void* s0) {
+  if (!p) return wf_fail(WF_EINVAL, "wf_solver_start: null problem");
+  wf_opts o;
+  if (opts) o = *opts;
+  else wf_opts_default(&o);
+  wf_status s = check_opts(p, &o);
+  if (s != WF_OK) return s;
+  return p->precision == WF_FP64 ? start_impl<double>(p, &o, s0) : start_impl<float>(p, &o, s0);
+}
+
+extern "C" wf_status wf_solver_step(wf_problem* p, int n_iter, int* n_active) {
+  if (!p || !p->solver || !p->solver->started) return wf_fail(WF_EINVAL, "wf_solver_step: no solve started");
+  if (n_iter < 0) return wf_fail(WF_EINVAL, "wf_solver_step: n_iter < 0");
+  return p->precision == WF_FP64 ? step_impl<double>(p, n_iter, n_active) : step_impl<float>(p, n_iter, n_active);
+}
+
+extern "C" wf_status wf_solver_profile(wf_problem* p, int n_iter, float* ms) {
+  if (!p || !p->solver || !p->solver->started || !ms)
+    return wf_fail(WF_EINVAL, "wf_solver_profile: no solve started or null output");
+  if (n_iter < 1) return wf_fail(WF_EINVAL, "wf_solver_profile: n_iter < 1");
+  return p->precision == WF_FP64 ? profile_impl<double>(p, n_iter, ms) : profile_impl<float>(p, n_iter, ms);
+}
+
+extern "C" wf_status wf_solver_finish(wf_problem* p, void* s_out, void* x_out, wf_solve_stats* stats) {
+  if (!p || !p->solver || !p->solver->started) return wf_fail(WF_EINVAL, "wf_solver_finish: no solve started");
+  return p->precision == WF_FP64 ? finish_impl<double>(p, s_out, x_out, stats)
+                                 : finish_impl<float>(p, s_out, x_out, stats);
+}
 
 extern "C" wf_status wf_map_solve(wf_problem* p, const wf_opts* opts, const void* s0, void* s_out,
                                   void* x_out, wf_solve_stats* stats) {
-  (void)p; (void)opts; (void)s0; (void)s_out; (void)x_out; (void)stats;
-  return wf_fail(WF_EINVAL, "wf_map_solve: not built yet");
+  if (!p || !s_out) return wf_fail(WF_EINVAL, "wf_map_solve: null problem or output");
+  wf_opts o;
+  if (opts) o = *opts;
+  else wf_opts_default(&o);
+  wf_status s = wf_solver_start(p, &o, s0);
+  if (s != WF_OK) return s;
+  const int chunk = o.check_every > 0 ? o.check_every : 16;
+  const long long max_chunks = (long long)o.max_iter / chunk + 2;
+  for (long long c = 0; c < max_chunks; ++c) {
+    int nact = 0;
+    s = wf_solver_step(p, chunk, &nact);
+    if (s != WF_OK) return s;
+    if (nact == 0) break;
+  }
+  return wf_solver_finish(p, s_out, x_out, stats);
 }

@@ -21,7 +21,8 @@ STATUS = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENONFINITE", 3: "WF_ENOMEM", 4: "WF
 # Names declared in include/wf.h (checked against the header by the tests).
 EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_problem_create",
            "wf_problem_destroy", "wf_problem_set_data", "wf_eval", "wf_hess_vec",
-           "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy"]
+           "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy",
+           "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile"]
 
 
 class WfMap(ctypes.Structure):
@@ -73,6 +74,10 @@ def lib() -> ctypes.CDLL:
     L.wf_map_solve.argtypes = [vp, ctypes.POINTER(WfOpts), vp, vp, vp, ctypes.POINTER(WfSolveStats)]
     L.wf_simulate_data.argtypes = [vp, vp, vp, vp, vp]
     L.wf_band_energy.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    L.wf_solver_start.argtypes = [vp, ctypes.POINTER(WfOpts), vp]
+    L.wf_solver_step.argtypes = [vp, i, ctypes.POINTER(i)]
+    L.wf_solver_finish.argtypes = [vp, vp, vp, ctypes.POINTER(WfSolveStats)]
+    L.wf_solver_profile.argtypes = [vp, i, ctypes.POINTER(ctypes.c_float)]
     for name in EXPORTS:
         if name not in ("wf_last_error", "wf_opts_default"):
             getattr(L, name).restype = ctypes.c_int
@@ -243,6 +248,50 @@ class Problem:
         _check(lib().wf_band_energy(self._p, _ptr(s), _ptr(band), _ptr(theta), nb, _ptr(out),
                                     _stream(stream)))
         return out
+
+    def _opts(self, stream, opts):
+        o = WfOpts()
+        lib().wf_opts_default(ctypes.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        o.stream = _stream(stream)
+        return o
+
+    def start(self, s0=None, stream=None, **opts):
+        """wf_solver_start: prepare an L-BFGS solve from s0 (None = 0)."""
+        self._o = self._opts(stream, opts)
+        _check(lib().wf_solver_start(self._p, ctypes.byref(self._o), _ptr(s0)))
+
+    def step(self, n_iter, sync=True):
+        """wf_solver_step: run n_iter iterations; returns the active count if sync."""
+        na = ctypes.c_int(-1)
+        _check(lib().wf_solver_step(self._p, int(n_iter), ctypes.byref(na) if sync else None))
+        return na.value if sync else None
+
+    def profile(self, n_iter):
+        """wf_solver_profile: average ms of the four kernels of one iteration."""
+        ms = (ctypes.c_float * 4)()
+        _check(lib().wf_solver_profile(self._p, int(n_iter), ms))
+        return list(ms)
+
+    def finish(self, x_out=False):
+        """wf_solver_finish: returns SolveResult."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        s = torch.empty(self.spec_shape(), dtype=self._cplx(), device=dev)
+        x = torch.empty(self.pix_shape(), dtype=self.wdtype, device=dev) if x_out else None
+        st = (WfSolveStats * self.B)()
+        status = lib().wf_solver_finish(self._p, _ptr(s), _ptr(x), st)
+        if status not in (0, 5):
+            _check(status)
+        return SolveResult(s=s, x=x, stats=self._stats(st))
+
+    @staticmethod
+    def _stats(st):
+        return [dict(iters=e.iters, evals=e.evals, status=STATUS.get(e.status, e.status),
+                     chi2=e.chi2, gnorm_rel=e.gnorm_rel) for e in st]
 
     def solve(self, s0=None, x_out=False, stream=None, **opts):
         import torch
