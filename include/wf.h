@@ -200,6 +200,33 @@ wf_status wf_simulate_data(wf_problem* p, const void* z, const void* noise, void
 wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
                          const double* theta, int n_bands, double* E, void* stream);
 
+/* Objective + gradient pass that allocates nothing (no counterpart in the
+ * paper; an interface for callers that cannot allocate device memory, for
+ * example because a framework's caching allocator or a pool reserved at
+ * start-up owns it, or because their real-time rules forbid allocation after
+ * initialisation - wf_problem_create allocates, this call does not).
+ * Computes the same chi2 and grad as wf_eval for `count` maps of one shape,
+ * from inputs the caller has already prepared, all DEVICE pointers of the
+ * working type (double for WF_FP64, float for WF_MIXED):
+ *   s    [count][C][n][n/2+1] complex   whitened state
+ *   d    [count][C][n][n]               data (any value where w = 0)
+ *   w    [count][C][n][n]               mask * Ninv, >= 0
+ *   P    [C][n][n/2+1]                  signal power per mode, shared by the maps
+ *   chi2 double [count], grad like s    outputs
+ * Scratch lives in a static device array of 16 MiB per GPU that loads the
+ * library (held until the process exits).  A call whose scratch would not fit
+ * (it needs about (C n^2 + C n (n/2+1)) working-type values per map plus
+ * 24 KiB) returns WF_EINVAL; FP32 fits up to three 1024^2 maps per call.
+ * The first call on a device resolves the array's address and writes the
+ * twiddle tables with blocking copies; make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites what it
+ * uses before reading it, so nothing needs clearing between calls, but calls
+ * that overlap on the GPU (different streams, or different host threads)
+ * race on it: order them on one stream.  Inputs are not checked for
+ * non-finite values.  Stream ordered, no synchronisation after the first call. */
+wf_status wf_eval_noalloc(const void* s, const void* d, const void* w, const void* P, int n, int C,
+                          int count, int precision, double* chi2, void* grad, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

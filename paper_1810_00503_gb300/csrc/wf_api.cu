@@ -61,7 +61,7 @@ WfGeo wf_make_geo(int n, int C) {
 
 // Roots of unity exp(-2 pi i k / WF_NT), computed in long double; the values
 // at multiples of pi/2 are set exactly.
-static void make_twiddles(double2* out) {
+void wf_make_twiddles(double2* out) {
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int k = 0; k < WF_NT; ++k) {
     long double a = -two_pi * (long double)k / (long double)WF_NT;
@@ -85,7 +85,7 @@ extern "C" wf_status wf_create(wf_handle** out) {
   if (e != cudaSuccess) { free(h); return wf_cuda_fail(e, "wf_create: cudaGetDevice"); }
   double2 tw64[WF_NT];
   float2 tw32[WF_NT];
-  make_twiddles(tw64);
+  wf_make_twiddles(tw64);
   for (int k = 0; k < WF_NT; ++k) { tw32[k].x = (float)tw64[k].x; tw32[k].y = (float)tw64[k].y; }
   e = cudaMalloc(&h->tw64, sizeof tw64);
   if (e == cudaSuccess) e = cudaMalloc(&h->tw32, sizeof tw32);

@@ -31,3 +31,4 @@ wf_status wf_cuda_fail(cudaError_t e, const char* what);
 wf_status wf_alloc(void** ptr, size_t bytes, const char* what);
 WfBufs wf_bufs(const wf_problem* p);
 void wf_solver_free(wf_problem* p);
+void wf_make_twiddles(double2* out);  // WF_NT roots of unity exp(-2 pi i k / WF_NT)

@@ -22,7 +22,8 @@ STATUS = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENONFINITE", 3: "WF_ENOMEM", 4: "WF
 EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_problem_create",
            "wf_problem_destroy", "wf_problem_set_data", "wf_eval", "wf_hess_vec",
            "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy",
-           "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile"]
+           "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
+           "wf_eval_noalloc"]
 
 
 class WfMap(ctypes.Structure):
@@ -78,6 +79,7 @@ def lib() -> ctypes.CDLL:
     L.wf_solver_step.argtypes = [vp, i, ctypes.POINTER(i)]
     L.wf_solver_finish.argtypes = [vp, vp, vp, ctypes.POINTER(WfSolveStats)]
     L.wf_solver_profile.argtypes = [vp, i, ctypes.POINTER(ctypes.c_float)]
+    L.wf_eval_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("wf_last_error", "wf_opts_default"):
             getattr(L, name).restype = ctypes.c_int
@@ -139,6 +141,22 @@ class SolveResult:
     s: object
     x: object
     stats: list
+
+
+def eval_noalloc(s, d, w, P, chi2=None, grad=None, stream=None):
+    """wf_eval_noalloc: objective + gradient without any device allocation in
+    the library (scratch in a static device array).  s (B, C, n, n/2+1)
+    complex, d and w (B, C, n, n), P (C, n, n/2+1), all CUDA tensors of the
+    working type; chi2 and grad are written (allocated here by torch if not
+    given, which is the caller's allocation, not the library's)."""
+    import torch
+    B, C, n, _ = d.shape
+    precision = WF_FP64 if d.dtype == torch.float64 else WF_MIXED
+    grad = torch.empty_like(s) if grad is None else grad
+    chi2 = torch.empty(B, dtype=torch.float64, device=d.device) if chi2 is None else chi2
+    _check(lib().wf_eval_noalloc(_ptr(s), _ptr(d), _ptr(w), _ptr(P), n, C, B, precision, _ptr(chi2),
+                                 _ptr(grad), _stream(stream)))
+    return chi2, grad
 
 
 class Problem:
