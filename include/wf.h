@@ -178,10 +178,11 @@ wf_status wf_solver_finish(wf_problem* p, void* s_out, void* x_out, wf_solve_sta
 
 /* Diagnostic: run n_iter more iterations of a started solve with plain
  * launches and CUDA events around each kernel on the working stream, and
- * store the average duration in milliseconds of the four kernels of an
- * iteration in ms (HOST float[4]): direction + inverse column stage, row
- * stage, forward column stage + dot products, scalar step.  Synchronises
- * after every iteration.  Not part of the method; used for roofline reports. */
+ * store the average duration in milliseconds of the six kernels of an
+ * iteration in ms (HOST float[6]): direction / state update / dot products,
+ * inverse column stage, row stage, forward column stage, q dot products,
+ * scalar step.  Synchronises after every iteration.  Not part of the method;
+ * used for roofline reports. */
 wf_status wf_solver_profile(wf_problem* p, int n_iter, float* ms);
 
 /* Data synthesis for simulations (Sec. 2.5, steps 1-2; eq. blmv):

@@ -59,7 +59,8 @@ struct WfGeo {
   int n, h, lgn, lgh, C;
   int TC, ntile;   // packed columns per column tile, tiles per map
   int RB, nrb;     // rows per row block (over the C*n rows), row blocks per map
-  int maxblk;      // max(ntile, nrb): stride of the partial-sum slots
+  int ncomb;       // blocks per map of the streaming L-BFGS kernels
+  int maxblk;      // max(ntile, nrb, ncomb): stride of the partial-sum slots
 };
 
 WfGeo wf_make_geo(int n, int C);
@@ -100,7 +101,7 @@ cudaError_t wf_launch_simulate(const WfGeo& g, const WfBufs& b, const void* z, c
 template <typename T>
 cudaError_t wf_launch_band_energy(const WfGeo& g, int B, const void* s, const int16_t* band,
                                   const double* theta, int n_bands, double* E, cudaStream_t st);
-// L-BFGS column kernels.  lb1 modes: full iteration, materialise only, dots only.
+// L-BFGS kernels.  Streaming-kernel modes: full iteration, materialise only, dots only.
 enum { WF_LB1_FULL = 0, WF_LB1_MATERIALIZE = 1, WF_LB1_DOTS = 2 };
 struct WfLbBufs {
   WfLbMap* st;      // [B]
@@ -110,11 +111,15 @@ struct WfLbBufs {
   int m;
 };
 template <typename T>
-cudaError_t wf_launch_lb1(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st);
+cudaError_t wf_launch_lb_comb(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st);
 template <typename T>
 cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st);
 template <typename T>
-cudaError_t wf_launch_lb3(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st);
+cudaError_t wf_launch_lb_colfwd(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_lb_qdots(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st);
 // Full objective+gradient pass on packed vectors (src -> dst), all maps.
 template <typename T>
 cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st);

@@ -1,34 +1,40 @@
-// Column kernels of one device L-BFGS iteration (Sec. 2.2: L-BFGS on chi^2).
+// Kernels of one device L-BFGS iteration (Sec. 2.2: L-BFGS on chi^2).
 //
-// Per iteration and map:
-//   k_lb1  applies the pending update s += a P, g += a Q of the previous step,
-//          forms the new direction p = dg g + sum_i (dP_i P_i + dQ_i Q_i) from
-//          the coefficients the scalar two-loop produced, stores p into the
-//          ring, accumulates the exact dot products of g with every stored
-//          vector, then runs the inverse-transform column stage on p;
-//   (row stage without data: the Hessian-vector product needs no d)
-//   k_lb3  finishes q = H p = 2 (p + A^T W A p) (forward column stage and the
-//          adjoint), stores q into the ring and accumulates <q, Q_i>, <q, q>,
-//          <p, q>, <g, q>, <g, p>, <p, p>.
-// Dot products use the half-plane weights of the packed layout (1 on the
-// packed column 0, 2 elsewhere), which equal the full-plane real inner product.
+// Per iteration and map (all maps of a batch in each launch):
+//   k_lb_comb   streaming: applies the pending update s += a P, g += a Q of the
+//               previous step, forms the new direction
+//               p = dg g + sum_i (dP_i P_i + dQ_i Q_i) from the coefficients of
+//               the scalar two-loop, stores p into the ring, and accumulates the
+//               dot products of g with every stored vector;
+//   k_lb_colinv inverse-transform column stage on p (A1, first half of A2);
+//   k_lb_row    row stage of the Hessian-vector product (no data term);
+//   k_lb_colfwd forward column stage and adjoint, q = H p = 2 (p + A^T W A p),
+//               stores q into the ring, <q,q>, <p,q>, <g,q>, <g,p>, <p,p>;
+//   k_lb_qdots  streaming: <q, Q_i> for the stored Q_i.
+// The streaming kernels run at high occupancy with 16-byte loads; the column
+// kernels keep only the transform work.  Dot products use the weights of the
+// packed half plane (1 on the packed column 0, 2 elsewhere), which equal the
+// full-plane real inner product.
 #pragma once
 #include "wf_ops.cuh"
 
-// Stage per-warp partial dot products: red[slot * NW + warp].
-__device__ __forceinline__ void wf_warp_stash(double v, double* red, int slot) {
+#define WF_COMB_THREADS 256
+#define WF_COMB_EPT 8                                   // complex values per thread per vector
+#define WF_COMB_CHUNK (WF_COMB_THREADS * WF_COMB_EPT)   // complex values per block
+
+// Stage per-warp partial dot products: red[slot * NW + warp] (NW = warps of the block).
+__device__ __forceinline__ void wf_warp_stash(double v, double* red, int slot, int nw) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[slot * (WF_THREADS / 32) + (threadIdx.x >> 5)] = v;
+  if ((threadIdx.x & 31) == 0) red[slot * nw + (threadIdx.x >> 5)] = v;
 }
 
-// Sum the staged warp partials of slots [0, nslot) into part[slot_id(i)].
-__device__ __forceinline__ void wf_flush_slots(const double* red, int nslot, const int* ids, double* part_b,
-                                               int maxblk) {
+// Sum the staged warp partials of slots [0, nslot) into part_b[ids[i] * maxblk + blockIdx.x].
+__device__ __forceinline__ void wf_flush_slots(const double* red, int nslot, int nw, const int* ids,
+                                               double* part_b, int maxblk) {
   for (int i = threadIdx.x; i < nslot; i += blockDim.x) {
     double acc = 0.0;
-#pragma unroll
-    for (int w = 0; w < WF_THREADS / 32; ++w) acc += red[i * (WF_THREADS / 32) + w];
+    for (int w = 0; w < nw; ++w) acc += red[i * nw + w];
     part_b[(size_t)ids[i] * maxblk + blockIdx.x] = acc;
   }
 }
@@ -39,230 +45,301 @@ __device__ __forceinline__ double wf_wdot(V2<T> a, V2<T> b, int kx) {
   return kx == 0 ? (double)d : 2.0 * (double)d;
 }
 
-template <typename T>
-__device__ __forceinline__ V2<T> wf_axpy(V2<T> y, double a, V2<T> x) {
-  const T s = (T)a;
-  return mk<T>(y.x + s * x.x, y.y + s * x.y);
-}
-
-// Element e of a column tile: vector offset, shared-memory index, column kx.
-struct WfTileIdx {
-  int off, sidx, kx;
+// A thread's share of a streaming chunk: WF_COMB_EPT complex values as
+// NV = WF_COMB_EPT / VW vector loads of VW complex values each (16 bytes).
+template <typename T> struct WfVec;
+template <> struct WfVec<float> {
+  typedef float4 type;
+  static constexpr int VW = 2;
 };
-__device__ __forceinline__ WfTileIdx wf_tile_idx(int e, int n, int h, int lgn, int lgTC, int C, int kx0) {
-  const int TC = 1 << lgTC;
-  const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-  WfTileIdx x;
-  x.kx = kx0 + t;
-  x.off = (c * n + j) * h + kx0 + t;
-  x.sidx = j * C * TC + c * TC + t;
-  return x;
+template <> struct WfVec<double> {
+  typedef double2 type;
+  static constexpr int VW = 1;
+};
+
+template <typename T>
+__device__ __forceinline__ typename WfVec<T>::type wf_vaxpy(typename WfVec<T>::type y, T a,
+                                                            typename WfVec<T>::type x) {
+  typename WfVec<T>::type r;
+  if constexpr (sizeof(T) == 4) {
+    r.x = y.x + a * x.x; r.y = y.y + a * x.y; r.z = y.z + a * x.z; r.w = y.w + a * x.w;
+  } else {
+    r.x = y.x + a * x.x; r.y = y.y + a * x.y;
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ typename WfVec<T>::type wf_vscale(typename WfVec<T>::type x, T a) {
+  typename WfVec<T>::type r;
+  if constexpr (sizeof(T) == 4) {
+    r.x = a * x.x; r.y = a * x.y; r.z = a * x.z; r.w = a * x.w;
+  } else {
+    r.x = a * x.x; r.y = a * x.y;
+  }
+  return r;
+}
+// Weighted dot of two vector loads starting at complex index `off` of a map
+// vector whose rows hold h packed columns (weight 1 on column 0, 2 elsewhere).
+template <typename T>
+__device__ __forceinline__ float wf_vdotf(typename WfVec<T>::type a, typename WfVec<T>::type b, int kx) {
+  if constexpr (sizeof(T) == 4) {
+    const float d0 = a.x * b.x + a.y * b.y, d1 = a.z * b.z + a.w * b.w;
+    return (kx == 0 ? d0 : 2.f * d0) + 2.f * d1;  // kx even, so kx + 1 >= 1
+  } else {
+    return 0.f;
+  }
+}
+template <typename T>
+__device__ __forceinline__ double wf_vdotd(typename WfVec<T>::type a, typename WfVec<T>::type b, int kx) {
+  if constexpr (sizeof(T) == 8) {
+    const double d0 = a.x * b.x + a.y * b.y;
+    return kx == 0 ? d0 : 2.0 * d0;
+  } else {
+    return (double)wf_vdotf<T>(a, b, kx);
+  }
 }
 
-template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS)
-k_lb1(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb,
-      double* part, int mode) {
-  extern __shared__ __align__(16) unsigned char wf_smem[];
+// ---------------------------------------------------------------------------
+// k_lb_comb: grid (ncomb, B).  Block chunk = WF_COMB_CHUNK complex values of
+// the map's packed vectors (fewer for small maps).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(WF_COMB_THREADS)
+k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
+  typedef typename WfVec<T>::type VT;
+  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32;
+  __shared__ double red[(2 * WF_MAXM + 1) * NW];
+  __shared__ int ids[2 * WF_MAXM + 1];
   const int b = blockIdx.y;
   const WfLbMap* M = lb.st + b;
   const int active = M->active;
   const double pa = M->pend_alpha;
   if (mode == WF_LB1_FULL && !active && pa == 0.0) return;
   if (mode == WF_LB1_MATERIALIZE && pa == 0.0) return;
-  V2<T>* s_tw = (V2<T>*)wf_smem;
-  V2<T>* buf = s_tw + WF_NT;
-  V2<T>* gb = buf + WF_TILE;
-  double* red = (double*)(gb + WF_TILE);
-  int* ids = (int*)(red + (2 * WF_MAXM + 1) * (WF_THREADS / 32));
-  const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1;
-  const int kx0 = blockIdx.x * TC, tot = C * n * TC;
-  const size_t vsz = (size_t)C * n * h;
-  const int B = gridDim.y, m = lb.m;
-  V2<T>* sv = (V2<T>*)lb.s + (size_t)b * vsz;
-  V2<T>* gv = (V2<T>*)lb.g + (size_t)b * vsz;
+  const size_t vsz = (size_t)g.C * g.n * g.h;  // complex values per map vector
+  const int h = g.h, B = gridDim.y, m = lb.m;
+  const size_t c0 = (size_t)blockIdx.x * WF_COMB_CHUNK;
+  size_t cend = c0 + WF_COMB_CHUNK;
+  if (cend > vsz) cend = vsz;
+  VT* sv = (VT*)((V2<T>*)lb.s + (size_t)b * vsz);
+  VT* gv = (VT*)((V2<T>*)lb.g + (size_t)b * vsz);
   V2<T>* ring = (V2<T>*)lb.ring;
-  auto Pv = [&](int i) { return ring + ((size_t)i * B + b) * vsz; };
-  auto Qv = [&](int i) { return ring + ((size_t)(m + i) * B + b) * vsz; };
-
-  // 1. state update of the previous step (or plain load of g)
-  if (pa != 0.0 && mode != WF_LB1_DOTS) {
-    const V2<T>* Pp = Pv(M->pend_slot);
-    const V2<T>* Qp = Qv(M->pend_slot);
+  auto Pv = [&](int i) { return (VT*)(ring + ((size_t)i * B + b) * vsz); };
+  auto Qv = [&](int i) { return (VT*)(ring + ((size_t)(m + i) * B + b) * vsz); };
+  // vector-load index u (in units of VW complex values) and column of its first value
+  size_t u[NV];
+  int kx[NV];
+  bool ok[NV];
 #pragma unroll
-    for (int i = 0; i < WF_EMAX; ++i) {
-      const int e = threadIdx.x + i * WF_THREADS;
-      if (e < tot) {
-        const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-        const V2<T> s1 = wf_axpy<T>(sv[x.off], pa, Pp[x.off]);
-        const V2<T> g1 = wf_axpy<T>(gv[x.off], pa, Qp[x.off]);
-        sv[x.off] = s1;
-        gv[x.off] = g1;
-        gb[x.sidx] = g1;
+  for (int i = 0; i < NV; ++i) {
+    const size_t c = c0 + ((size_t)threadIdx.x + (size_t)i * WF_COMB_THREADS) * VW;
+    ok[i] = c < cend;
+    u[i] = c / VW;
+    kx[i] = (int)(c % h);
+  }
+  VT gr[NV];
+  if (pa != 0.0 && mode != WF_LB1_DOTS) {
+    const VT* Pp = Pv(M->pend_slot);
+    const VT* Qp = Qv(M->pend_slot);
+    VT s1[NV], p1[NV], q1[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) { s1[i] = sv[u[i]]; gr[i] = gv[u[i]]; p1[i] = Pp[u[i]]; q1[i] = Qp[u[i]]; }
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) {
+        s1[i] = wf_vaxpy<T>(s1[i], (T)pa, p1[i]);
+        gr[i] = wf_vaxpy<T>(gr[i], (T)pa, q1[i]);
+        sv[u[i]] = s1[i];
+        gv[u[i]] = gr[i];
       }
-    }
   } else if (mode != WF_LB1_MATERIALIZE) {
 #pragma unroll
-    for (int i = 0; i < WF_EMAX; ++i) {
-      const int e = threadIdx.x + i * WF_THREADS;
-      if (e < tot) {
-        const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-        gb[x.sidx] = gv[x.off];
-      }
-    }
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) gr[i] = gv[u[i]];
   }
   if (mode == WF_LB1_MATERIALIZE) return;
   if (mode == WF_LB1_FULL && !active) return;
   const bool full = (mode == WF_LB1_FULL);
-
-  // 2. direction and dot products of g with the stored vectors
   const int np = M->npairs, head = M->head;
-  const double dg = M->dg;
-  double acc = 0.0;
+  VT pr[NV];
+  {
+    double acc = 0.0;
+    const T dg = (T)M->dg;
 #pragma unroll
-  for (int i = 0; i < WF_EMAX; ++i) {
-    const int e = threadIdx.x + i * WF_THREADS;
-    if (e < tot) {
-      const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-      const V2<T> gg = gb[x.sidx];
-      acc += wf_wdot<T>(gg, gg, x.kx);
-      if (full) buf[x.sidx] = mk<T>((T)dg * gg.x, (T)dg * gg.y);
-    }
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) {
+        acc += wf_vdotd<T>(gr[i], gr[i], kx[i]);
+        if (full) pr[i] = wf_vscale<T>(gr[i], dg);
+      }
+    wf_warp_stash(acc, red, 0, NW);
+    if (threadIdx.x == 0) ids[0] = WF_SLOT_GG;
   }
-  wf_warp_stash(acc, red, 0);
-  if (threadIdx.x == 0) ids[0] = WF_SLOT_GG;
   for (int q = 0; q < np; ++q) {
     const int sl = (head - q + m) % m;
-    for (int half = 0; half < 2; ++half) {
-      const V2<T>* vp = half == 0 ? Pv(sl) : Qv(sl);
-      const double coef = half == 0 ? M->dP[sl] : M->dQ[sl];
-      V2<T> v[WF_EMAX];
+    const VT* Pq = Pv(sl);
+    const VT* Qq = Qv(sl);
+    VT vp[NV], vq[NV];
 #pragma unroll
-      for (int i = 0; i < WF_EMAX; ++i) {
-        const int e = threadIdx.x + i * WF_THREADS;
-        if (e < tot) v[i] = vp[wf_tile_idx(e, n, h, lgn, lgTC, C, kx0).off];
-      }
-      double a2 = 0.0;
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) { vp[i] = Pq[u[i]]; vq[i] = Qq[u[i]]; }
+    const T cp = (T)M->dP[sl], cq = (T)M->dQ[sl];
+    double ap = 0.0, aq = 0.0;
 #pragma unroll
-      for (int i = 0; i < WF_EMAX; ++i) {
-        const int e = threadIdx.x + i * WF_THREADS;
-        if (e < tot) {
-          const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-          a2 += wf_wdot<T>(gb[x.sidx], v[i], x.kx);
-          if (full) buf[x.sidx] = wf_axpy<T>(buf[x.sidx], coef, v[i]);
-        }
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) {
+        ap += wf_vdotd<T>(gr[i], vp[i], kx[i]);
+        aq += wf_vdotd<T>(gr[i], vq[i], kx[i]);
+        if (full) pr[i] = wf_vaxpy<T>(wf_vaxpy<T>(pr[i], cp, vp[i]), cq, vq[i]);
       }
-      const int k = 1 + 2 * q + half;
-      wf_warp_stash(a2, red, k);
-      if (threadIdx.x == 0) ids[k] = (half == 0 ? WF_SLOT_GP : WF_SLOT_GQ) + sl;
+    wf_warp_stash(ap, red, 1 + 2 * q, NW);
+    wf_warp_stash(aq, red, 2 + 2 * q, NW);
+    if (threadIdx.x == 0) {
+      ids[1 + 2 * q] = WF_SLOT_GP + sl;
+      ids[2 + 2 * q] = WF_SLOT_GQ + sl;
     }
   }
+  if (full) {
+    VT* Pn = Pv(M->next);
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) Pn[u[i]] = pr[i];
+  }
   __syncthreads();
-  wf_flush_slots(red, 1 + 2 * np, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
-  if (!full) return;
+  wf_flush_slots(red, 1 + 2 * np, NW, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+}
 
-  // 3. store p into its ring slot, then the inverse-transform column stage
-  V2<T>* Pn = Pv(M->next);
+// ---------------------------------------------------------------------------
+// k_lb_qdots: grid (ncomb, B).  <q, Q_i> for the stored Q_i other than q.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(WF_COMB_THREADS)
+k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
+  typedef typename WfVec<T>::type VT;
+  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32;
+  __shared__ double red[WF_MAXM * NW];
+  __shared__ int ids[WF_MAXM];
+  const int b = blockIdx.y;
+  const WfLbMap* M = lb.st + b;
+  if (!M->active) return;
+  const size_t vsz = (size_t)g.C * g.n * g.h;
+  const int h = g.h, B = gridDim.y, m = lb.m;
+  const size_t c0 = (size_t)blockIdx.x * WF_COMB_CHUNK;
+  size_t cend = c0 + WF_COMB_CHUNK;
+  if (cend > vsz) cend = vsz;
+  V2<T>* ring = (V2<T>*)lb.ring;
+  auto Qv = [&](int i) { return (const VT*)(ring + ((size_t)(m + i) * B + b) * vsz); };
+  size_t u[NV];
+  int kx[NV];
+  bool ok[NV];
 #pragma unroll
-  for (int i = 0; i < WF_EMAX; ++i) {
-    const int e = threadIdx.x + i * WF_THREADS;
-    if (e < tot) {
-      const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-      Pn[x.off] = buf[x.sidx];
-    }
+  for (int i = 0; i < NV; ++i) {
+    const size_t c = c0 + ((size_t)threadIdx.x + (size_t)i * WF_COMB_THREADS) * VW;
+    ok[i] = c < cend;
+    u[i] = c / VW;
+    kx[i] = (int)(c % h);
   }
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  const int nx = M->next, np = M->npairs, head = M->head;
+  const VT* Qn = Qv(nx);
+  VT qr[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (ok[i]) qr[i] = Qn[u[i]];
+  int k = 0;
+  for (int q = 0; q < np; ++q) {
+    const int sl = (head - q + m) % m;
+    if (sl == nx) continue;
+    const VT* Qq = Qv(sl);
+    VT v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) v[i] = Qq[u[i]];
+    double a = 0.0;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) a += wf_vdotd<T>(qr[i], v[i], kx[i]);
+    wf_warp_stash(a, red, k, NW);
+    if (threadIdx.x == 0) ids[k] = WF_SLOT_QQI + sl;
+    ++k;
+  }
   __syncthreads();
-  wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
-  __syncthreads();
-  fft_smem<T, +1, WF_EMAX>(buf, lgn, C * TC, 1, C * TC, s_tw);
-  wf_tile_store_pk<T, C>((V2<T>*)scratch_ + (size_t)b * vsz, buf, n, lgTC, kx0);
+  wf_flush_slots(red, k, NW, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+}
+
+// ---------------------------------------------------------------------------
+// Column stages of the Hessian-vector product on p = P[next] of each map.
+// ---------------------------------------------------------------------------
+template <typename T, int C>
+__global__ void __launch_bounds__(WF_THREADS)
+k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb) {
+  const int b = blockIdx.y;
+  const WfLbMap* M = lb.st + b;
+  if (!M->active) return;
+  const size_t vsz = (size_t)C * g.n * g.h;
+  const V2<T>* p = (const V2<T>*)lb.ring + ((size_t)M->next * gridDim.y + b) * vsz;
+  wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
 }
 
 template <typename T, int C>
 __global__ void __launch_bounds__(WF_THREADS)
-k_lb3(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, const void* tw_, WfLbBufs lb,
-      double* part) {
+k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, const void* tw_, WfLbBufs lb,
+            double* part) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   const int b = blockIdx.y;
   const WfLbMap* M = lb.st + b;
   if (!M->active) return;
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
-  double* red = (double*)(buf + WF_TILE);
-  int* ids = (int*)(red + (WF_MAXM + 5) * (WF_THREADS / 32));
   const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC;
   const int kx0 = blockIdx.x * TC, tot = C * n * TC;
   const size_t vsz = (size_t)C * n * h;
-  const int B = gridDim.y, m = lb.m;
-  V2<T>* ring = (V2<T>*)lb.ring;
-  auto Pv = [&](int i) { return ring + ((size_t)i * B + b) * vsz; };
-  auto Qv = [&](int i) { return ring + ((size_t)(m + i) * B + b) * vsz; };
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
-  const V2<T>* sc = (const V2<T>*)scratch_ + (size_t)b * vsz;
-#pragma unroll
-  for (int i = 0; i < WF_EMAX; ++i) {
-    const int e = threadIdx.x + i * WF_THREADS;
-    if (e < tot) {
-      const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-      buf[x.sidx] = sc[x.off];
-    }
-  }
-  __syncthreads();
-  fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
-  wf_col_scale<T, C, true>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
-  __syncthreads();
-  const int nx = M->next;
-  const V2<T>* Pn = Pv(nx);
-  V2<T>* Qn = Qv(nx);
+  const int B = gridDim.y, m = lb.m, nx = M->next;
+  wf_col_fwd_front<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, sp_ + (size_t)b * sp_stride, buf, s_tw,
+                         tw_);
+  const V2<T>* Pn = (const V2<T>*)lb.ring + ((size_t)nx * B + b) * vsz;
+  V2<T>* Qn = (V2<T>*)lb.ring + ((size_t)(m + nx) * B + b) * vsz;
   const V2<T>* gv = (const V2<T>*)lb.g + (size_t)b * vsz;
   double qq = 0, pq = 0, pp = 0, gq = 0, gp = 0;
-  V2<T> qr[WF_EMAX];
+  V2<T> pl[WF_EMAX], gl[WF_EMAX];
 #pragma unroll
   for (int i = 0; i < WF_EMAX; ++i) {
     const int e = threadIdx.x + i * WF_THREADS;
     if (e < tot) {
-      const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-      const V2<T> p = Pn[x.off], a = buf[x.sidx], gg = gv[x.off];
-      const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
-      Qn[x.off] = q;
-      qr[i] = q;
-      qq += wf_wdot<T>(q, q, x.kx);
-      pq += wf_wdot<T>(p, q, x.kx);
-      pp += wf_wdot<T>(p, p, x.kx);
-      gq += wf_wdot<T>(gg, q, x.kx);
-      gp += wf_wdot<T>(gg, p, x.kx);
+      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+      const size_t off = ((size_t)c * n + j) * h + kx0 + t;
+      pl[i] = Pn[off];
+      gl[i] = gv[off];
     }
   }
-  wf_warp_stash(qq, red, 0);
-  wf_warp_stash(pq, red, 1);
-  wf_warp_stash(pp, red, 2);
-  wf_warp_stash(gq, red, 3);
-  wf_warp_stash(gp, red, 4);
+#pragma unroll
+  for (int i = 0; i < WF_EMAX; ++i) {
+    const int e = threadIdx.x + i * WF_THREADS;
+    if (e < tot) {
+      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+      const int kx = kx0 + t;
+      const size_t off = ((size_t)c * n + j) * h + kx;
+      const V2<T> a = buf[j * CT + c * TC + t], p = pl[i], gg = gl[i];
+      const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
+      Qn[off] = q;
+      qq += wf_wdot<T>(q, q, kx);
+      pq += wf_wdot<T>(p, q, kx);
+      pp += wf_wdot<T>(p, p, kx);
+      gq += wf_wdot<T>(gg, q, kx);
+      gp += wf_wdot<T>(gg, p, kx);
+    }
+  }
+  __shared__ double red[5 * (WF_THREADS / 32)];
+  __shared__ int ids[5];
+  wf_warp_stash(qq, red, 0, WF_THREADS / 32);
+  wf_warp_stash(pq, red, 1, WF_THREADS / 32);
+  wf_warp_stash(pp, red, 2, WF_THREADS / 32);
+  wf_warp_stash(gq, red, 3, WF_THREADS / 32);
+  wf_warp_stash(gp, red, 4, WF_THREADS / 32);
   if (threadIdx.x == 0) {
     ids[0] = WF_SLOT_QQ; ids[1] = WF_SLOT_PQ; ids[2] = WF_SLOT_PP; ids[3] = WF_SLOT_GQN; ids[4] = WF_SLOT_GPN;
   }
-  const int np = M->npairs, head = M->head;
-  int k = 5;
-  for (int q = 0; q < np; ++q) {
-    const int sl = (head - q + m) % m;
-    if (sl == nx) continue;
-    const V2<T>* vq = Qv(sl);
-    double a2 = 0.0;
-#pragma unroll
-    for (int i = 0; i < WF_EMAX; ++i) {
-      const int e = threadIdx.x + i * WF_THREADS;
-      if (e < tot) {
-        const WfTileIdx x = wf_tile_idx(e, n, h, lgn, lgTC, C, kx0);
-        a2 += wf_wdot<T>(qr[i], vq[x.off], x.kx);
-      }
-    }
-    wf_warp_stash(a2, red, k);
-    if (threadIdx.x == 0) ids[k] = WF_SLOT_QQI + sl;
-    ++k;
-  }
   __syncthreads();
-  wf_flush_slots(red, k, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_flush_slots(red, 5, WF_THREADS / 32, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
 }
 
 // Row stage of the Hessian-vector product for the maps still iterating.

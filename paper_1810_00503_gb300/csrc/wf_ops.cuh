@@ -148,21 +148,134 @@ __device__ __forceinline__ V2<T> wf_load_spec(const V2<T>* src, int c, int j, in
   }
 }
 
+// Position of element e of a column tile: pairs (FP32, 16-byte loads) or
+// single complex values.  Tile element (row j, channel c, column t) lives at
+// buf[j*C*TC + c*TC + t]; in the packed vector at ((c*n + j)*h + kx0 + t).
 template <typename T, int C, int IN>
 __device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n, int lgTC, int kx0) {
-  const int TC = 1 << lgTC, CT = C * TC, lgn = __ffs(n) - 1;
-  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
-    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-    buf[j * CT + c * TC + t] = wf_load_spec<T, C, IN>(src, c, j, kx0 + t, n);
+  const int TC = 1 << lgTC, CT = C * TC, lgn = __ffs(n) - 1, tot = C * n * TC, h = n >> 1;
+  if constexpr (IN == WF_IN_PK && sizeof(T) == 4) {
+    if (TC >= 2) {
+      const int lgP = lgTC - 1, tot2 = tot >> 1;
+      float4 v[WF_EMAX / 2];
+#pragma unroll
+      for (int i = 0; i < WF_EMAX / 2; ++i) {
+        const int e = threadIdx.x + i * WF_THREADS;
+        if (e < tot2) {
+          const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
+          v[i] = *(const float4*)(src + ((size_t)c * n + j) * h + kx0 + t);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < WF_EMAX / 2; ++i) {
+        const int e = threadIdx.x + i * WF_THREADS;
+        if (e < tot2) {
+          const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
+          V2<T>* d = buf + j * CT + c * TC + t;
+          d[0] = mk<T>(v[i].x, v[i].y);
+          d[1] = mk<T>(v[i].z, v[i].w);
+        }
+      }
+      return;
+    }
+  }
+  V2<T> v[WF_EMAX];
+#pragma unroll
+  for (int i = 0; i < WF_EMAX; ++i) {
+    const int e = threadIdx.x + i * WF_THREADS;
+    if (e < tot) {
+      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+      v[i] = wf_load_spec<T, C, IN>(src, c, j, kx0 + t, n);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < WF_EMAX; ++i) {
+    const int e = threadIdx.x + i * WF_THREADS;
+    if (e < tot) {
+      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+      buf[j * CT + c * TC + t] = v[i];
+    }
   }
 }
 
 template <typename T, int C>
 __device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, int n, int lgTC, int kx0) {
-  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, lgn = __ffs(n) - 1;
-  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
-    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-    dst[((size_t)c * n + j) * h + kx0 + t] = buf[j * CT + c * TC + t];
+  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, lgn = __ffs(n) - 1, tot = C * n * TC;
+  if constexpr (sizeof(T) == 4) {
+    if (TC >= 2) {
+      const int lgP = lgTC - 1, tot2 = tot >> 1;
+#pragma unroll
+      for (int i = 0; i < WF_EMAX / 2; ++i) {
+        const int e = threadIdx.x + i * WF_THREADS;
+        if (e < tot2) {
+          const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
+          const V2<T>* q = buf + j * CT + c * TC + t;
+          *(float4*)(dst + ((size_t)c * n + j) * h + kx0 + t) = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+        }
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < WF_EMAX; ++i) {
+    const int e = threadIdx.x + i * WF_THREADS;
+    if (e < tot) {
+      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+      dst[((size_t)c * n + j) * h + kx0 + t] = buf[j * CT + c * TC + t];
+    }
+  }
+}
+
+// Contiguous copies of up to WF_TILE complex values between global and shared
+// memory, every load of a thread issued before its stores (16-byte accesses).
+template <typename T>
+__device__ __forceinline__ void wf_g2s(V2<T>* dst, const V2<T>* src, int tot) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = (const float4*)src;
+    float4* d4 = (float4*)dst;
+    const int t2 = tot >> 1;
+    float4 v[WF_EMAX / 2];
+#pragma unroll
+    for (int i = 0; i < WF_EMAX / 2; ++i) {
+      const int e = threadIdx.x + i * WF_THREADS;
+      if (e < t2) v[i] = s4[e];
+    }
+#pragma unroll
+    for (int i = 0; i < WF_EMAX / 2; ++i) {
+      const int e = threadIdx.x + i * WF_THREADS;
+      if (e < t2) d4[e] = v[i];
+    }
+  } else {
+    V2<T> v[WF_EMAX];
+#pragma unroll
+    for (int i = 0; i < WF_EMAX; ++i) {
+      const int e = threadIdx.x + i * WF_THREADS;
+      if (e < tot) v[i] = src[e];
+    }
+#pragma unroll
+    for (int i = 0; i < WF_EMAX; ++i) {
+      const int e = threadIdx.x + i * WF_THREADS;
+      if (e < tot) dst[e] = v[i];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void wf_s2g(V2<T>* dst, const V2<T>* src, int tot) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* s4 = (const float4*)src;
+    float4* d4 = (float4*)dst;
+#pragma unroll
+    for (int i = 0; i < WF_EMAX / 2; ++i) {
+      const int e = threadIdx.x + i * WF_THREADS;
+      if (e < (tot >> 1)) d4[e] = s4[e];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < WF_EMAX; ++i) {
+      const int e = threadIdx.x + i * WF_THREADS;
+      if (e < tot) dst[e] = src[e];
+    }
   }
 }
 
@@ -170,21 +283,42 @@ __device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, i
 // k_col_inv: spectrum tile -> R sqrt(P)/n -> inverse FFT along y -> scratch
 // ---------------------------------------------------------------------------
 template <typename T, int C, int IN>
-__global__ void __launch_bounds__(WF_THREADS)
-k_col_inv(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
+__device__ __forceinline__ void wf_col_inv_body(const WfGeo& g, const V2<T>* src, const T* sp, V2<T>* scr,
+                                                const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
-  const int b = blockIdx.y, n = g.n, h = g.h;
-  const int lgTC = __ffs(g.TC) - 1, kx0 = blockIdx.x * g.TC;
+  const int n = g.n, lgTC = __ffs(g.TC) - 1, kx0 = blockIdx.x * g.TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
-  const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
-  wf_tile_load<T, C, IN>(buf, (const V2<T>*)src_ + (size_t)b * sstride, n, lgTC, kx0);
+  wf_tile_load<T, C, IN>(buf, src, n, lgTC, kx0);
   __syncthreads();
-  wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
+  wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp, (T)1);
   __syncthreads();
   fft_smem<T, +1, WF_EMAX>(buf, g.lgn, C * g.TC, 1, C * g.TC, s_tw);
-  wf_tile_store_pk<T, C>((V2<T>*)scratch_ + (size_t)b * C * n * h, buf, n, lgTC, kx0);
+  wf_tile_store_pk<T, C>(scr, buf, n, lgTC, kx0);
+}
+
+template <typename T, int C, int IN>
+__global__ void __launch_bounds__(WF_THREADS)
+k_col_inv(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
+  const int b = blockIdx.y, n = g.n, h = g.h;
+  const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
+  wf_col_inv_body<T, C, IN>(g, (const V2<T>*)src_ + (size_t)b * sstride, sp_ + (size_t)b * sp_stride,
+                            (V2<T>*)scratch_ + (size_t)b * C * n * h, tw_);
+}
+
+// Forward column stage shared by the gradient and Hessian-vector epilogues:
+// scratch tile -> forward FFT along y -> sqrt(P) R^T / n, left in buf.
+template <typename T, int C>
+__device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* scr, const T* sp, V2<T>* buf,
+                                                 V2<T>* s_tw, const void* tw_) {
+  const int n = g.n, lgTC = __ffs(g.TC) - 1, CT = C * g.TC, kx0 = blockIdx.x * g.TC;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  wf_tile_load<T, C, WF_IN_PK>(buf, scr, n, lgTC, kx0);
+  __syncthreads();
+  fft_smem<T, -1, WF_EMAX>(buf, g.lgn, CT, 1, CT, s_tw);
+  wf_col_scale<T, C, true>(buf, n, lgTC, kx0, sp, (T)1);
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -202,13 +336,7 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   const int b = blockIdx.y, n = g.n, h = g.h, lgn = g.lgn;
   const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
-  {
-    const V2<T>* sc = (const V2<T>*)scratch_ + (size_t)b * C * n * h;
-    for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
-      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-      buf[j * CT + c * TC + t] = sc[((size_t)c * n + j) * h + kx0 + t];
-    }
-  }
+  wf_tile_load<T, C, WF_IN_PK>(buf, (const V2<T>*)scratch_ + (size_t)b * C * n * h, n, lgTC, kx0);
   __syncthreads();
   fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
   wf_col_scale<T, C, true>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
@@ -271,10 +399,7 @@ k_col_sim(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void
   const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
   V2<T>* sc = (V2<T>*)scratch_ + (size_t)b * C * n * h;
-  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
-    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-    buf[j * CT + c * TC + t] = sc[((size_t)c * n + j) * h + kx0 + t];
-  }
+  wf_tile_load<T, C, WF_IN_PK>(buf, sc, n, lgTC, kx0);
   __syncthreads();
   fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
   wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1 / (T)n);
@@ -308,10 +433,10 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
 
   if constexpr (MODE == WF_ROW_RFFT) {
     const V2<T>* z = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * n);
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) buf[e] = z[e];
+    wf_g2s<T>(buf, z, tot);
     __syncthreads();
   } else {
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) buf[e] = sc[e];
+    wf_g2s<T>(buf, sc, tot);
     __syncthreads();
     // c2r pre-processing: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]),
     // w = exp(+2 pi i / n), X[0], X[h] the real parts packed in Y[0].
@@ -338,7 +463,7 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
     const V2<T>* wv = (const V2<T>*)((const T*)w_ + (size_t)b * npix + (size_t)row0 * n);
     if constexpr (MODE == WF_ROW_SIGNAL) {
       V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * n);
-      for (int e = threadIdx.x; e < tot; e += blockDim.x) ov[e] = buf[e];
+      wf_s2g<T>(ov, buf, tot);
       return;
     } else if constexpr (MODE == WF_ROW_SIM) {
       V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * n);
@@ -350,19 +475,28 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
       return;
     } else {
       float accf = 0.f;
-      for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const V2<T> x = buf[e], w = wv[e];
-        V2<T> r;
-        if constexpr (MODE == WF_ROW_DATA) {
-          const V2<T> dd = dv[e];
-          r = mk<T>(dd.x - x.x, dd.y - x.y);
-        } else {
-          r = mk<T>(-x.x, -x.y);
+      V2<T> wl[WF_EMAX], dl[WF_EMAX];
+#pragma unroll
+      for (int i = 0; i < WF_EMAX; ++i) {
+        const int e = threadIdx.x + i * WF_THREADS;
+        if (e < tot) {
+          wl[i] = wv[e];
+          if constexpr (MODE == WF_ROW_DATA) dl[i] = dv[e];
         }
-        const V2<T> wr = mk<T>(w.x * r.x, w.y * r.y);
-        if constexpr (sizeof(T) == 4) accf += r.x * wr.x + r.y * wr.y;
-        else acc += (double)(r.x * wr.x) + (double)(r.y * wr.y);
-        buf[e] = wr;
+      }
+#pragma unroll
+      for (int i = 0; i < WF_EMAX; ++i) {
+        const int e = threadIdx.x + i * WF_THREADS;
+        if (e < tot) {
+          const V2<T> x = buf[e], w = wl[i];
+          V2<T> r;
+          if constexpr (MODE == WF_ROW_DATA) r = mk<T>(dl[i].x - x.x, dl[i].y - x.y);
+          else r = mk<T>(-x.x, -x.y);
+          const V2<T> wr = mk<T>(w.x * r.x, w.y * r.y);
+          if constexpr (sizeof(T) == 4) accf += r.x * wr.x + r.y * wr.y;
+          else acc += (double)(r.x * wr.x) + (double)(r.y * wr.y);
+          buf[e] = wr;
+        }
       }
       acc += (double)accf;
       __syncthreads();
@@ -389,7 +523,7 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) sc[e] = buf[e];
+  wf_s2g<T>(sc, buf, tot);
   if constexpr (MODE == WF_ROW_DATA || MODE == WF_ROW_NODATA) {
     const double s = wf_block_sum(acc);
     if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;

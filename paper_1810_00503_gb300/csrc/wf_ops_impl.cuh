@@ -97,15 +97,6 @@ cudaError_t col_fwd_any(const WfGeo& g, const WfBufs& b, int in, const void* src
   return in == WF_IN_PK ? col_fwd<T, 2, WF_IN_PK>(g, b, src, dst, st) : col_fwd<T, 2, WF_IN_STD>(g, b, src, dst, st);
 }
 
-template <typename T> inline size_t lb1_smem() {
-  return (WF_NT + 2 * (size_t)WF_TILE) * sizeof(V2<T>) + (2 * WF_MAXM + 1) * (WF_THREADS / 32) * sizeof(double) +
-         (2 * WF_MAXM + 1) * sizeof(int);
-}
-template <typename T> inline size_t lb3_smem() {
-  return (WF_NT + (size_t)WF_TILE) * sizeof(V2<T>) + (WF_MAXM + 5) * (WF_THREADS / 32) * sizeof(double) +
-         (WF_MAXM + 5) * sizeof(int);
-}
-
 template <typename K> inline cudaError_t ensure_smem_n(K kernel, size_t bytes, int* done_mask) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -117,23 +108,22 @@ template <typename K> inline cudaError_t ensure_smem_n(K kernel, size_t bytes, i
 }
 
 template <typename T, int C>
-cudaError_t lb1(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st) {
+cudaError_t lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
-  auto k = k_lb1<T, C>;
-  const size_t sm = lb1_smem<T>();
-  cudaError_t e = ensure_smem_n(k, sm, &done);
+  auto k = k_lb_colinv<T, C>;
+  const size_t sm = col_smem<T>(g);
+  cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
-  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb, b.part,
-                                                mode);
+  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb);
   return cudaGetLastError();
 }
 
 template <typename T, int C>
-cudaError_t lb3(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+cudaError_t lb_colfwd(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
-  auto k = k_lb3<T, C>;
-  const size_t sm = lb3_smem<T>();
-  cudaError_t e = ensure_smem_n(k, sm, &done);
+  auto k = k_lb_colfwd<T, C>;
+  const size_t sm = col_smem<T>(g);
+  cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb, b.part);
   return cudaGetLastError();
@@ -236,12 +226,22 @@ inline int grid1d(size_t total, int cap) {
   }
 
 template <typename T>
-cudaError_t wf_launch_lb1(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st) {
-  return g.C == 1 ? wfimpl::lb1<T, 1>(g, b, lb, mode, st) : wfimpl::lb1<T, 2>(g, b, lb, mode, st);
+cudaError_t wf_launch_lb_comb(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st) {
+  k_lb_comb<T><<<dim3(g.ncomb, b.B), WF_COMB_THREADS, 0, st>>>(g, lb, b.part, mode);
+  return cudaGetLastError();
 }
 template <typename T>
-cudaError_t wf_launch_lb3(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
-  return g.C == 1 ? wfimpl::lb3<T, 1>(g, b, lb, st) : wfimpl::lb3<T, 2>(g, b, lb, st);
+cudaError_t wf_launch_lb_qdots(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  k_lb_qdots<T><<<dim3(g.ncomb, b.B), WF_COMB_THREADS, 0, st>>>(g, lb, b.part);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t wf_launch_lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  return g.C == 1 ? wfimpl::lb_colinv<T, 1>(g, b, lb, st) : wfimpl::lb_colinv<T, 2>(g, b, lb, st);
+}
+template <typename T>
+cudaError_t wf_launch_lb_colfwd(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  return g.C == 1 ? wfimpl::lb_colfwd<T, 1>(g, b, lb, st) : wfimpl::lb_colfwd<T, 2>(g, b, lb, st);
 }
 template <typename T>
 cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
@@ -277,9 +277,14 @@ cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, 
                                                 const double*, int, double*, cudaStream_t);        \
   template cudaError_t wf_launch_pack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);     \
   template cudaError_t wf_launch_unpack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);    \
-  template cudaError_t wf_launch_lb1<T>(const WfGeo&, const WfBufs&, const WfLbBufs&, int,          \
-                                        cudaStream_t);                                             \
-  template cudaError_t wf_launch_lb3<T>(const WfGeo&, const WfBufs&, const WfLbBufs&, cudaStream_t);\
+  template cudaError_t wf_launch_lb_comb<T>(const WfGeo&, const WfBufs&, const WfLbBufs&, int,      \
+                                            cudaStream_t);                                         \
+  template cudaError_t wf_launch_lb_qdots<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,         \
+                                             cudaStream_t);                                        \
+  template cudaError_t wf_launch_lb_colinv<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,        \
+                                              cudaStream_t);                                       \
+  template cudaError_t wf_launch_lb_colfwd<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,        \
+                                              cudaStream_t);                                       \
   template cudaError_t wf_launch_lb_row<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,           \
                                            cudaStream_t);                                          \
   template cudaError_t wf_launch_eval_pk<T>(const WfGeo&, const WfBufs&, const void*, void*,       \

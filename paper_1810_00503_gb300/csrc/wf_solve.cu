@@ -2,9 +2,9 @@
 // L-BFGS builds a low-rank model of the curvature D, eq_curv, never forming it).
 //
 // One iteration for every map still active:
-//   k_lb1     s, g += a (P, Q) of the previous step; p = direction; <g, .>
-//   k_lb_row  row stage of H p (no data term)
-//   k_lb3     q = H p; <q, .>
+//   k_lb_comb   s, g += a (P, Q) of the previous step; p = direction; <g, .>
+//   k_lb_colinv, k_lb_row, k_lb_colfwd   q = H p and <q,q>, <p,q>, <g,q>, <g,p>
+//   k_lb_qdots  <q, Q_i>
 //   k_lb_scalar (one warp per map) exact step a = -g.p / p.Hp along p (the
 //             objective is quadratic, so this is the point a Wolfe line search
 //             converges to), chi^2 update, Gram-matrix update of the new pair
@@ -21,7 +21,7 @@
 
 struct WfScalarArgs {
   double gtol2, dchi2;
-  int max_iter, m, ntile, nrb, maxblk, phase, init;
+  int max_iter, m, ntile, nrb, ncomb, maxblk, phase, init;
 };
 // Legacy and per-thread default stream handles cannot be captured; the solver
 // then runs on its own stream, ordered after the caller's with events.
@@ -123,7 +123,7 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
       return;
     }
     const int np = M.npairs, head = M.head;
-    S[w][WF_SLOT_GG] = wf_warp_slot(pb, WF_SLOT_GG, A.ntile, A.maxblk);
+    S[w][WF_SLOT_GG] = wf_warp_slot(pb, WF_SLOT_GG, A.ncomb, A.maxblk);
     S[w][WF_SLOT_QQ] = wf_warp_slot(pb, WF_SLOT_QQ, A.ntile, A.maxblk);
     S[w][WF_SLOT_PQ] = wf_warp_slot(pb, WF_SLOT_PQ, A.ntile, A.maxblk);
     S[w][WF_SLOT_GQN] = wf_warp_slot(pb, WF_SLOT_GQN, A.ntile, A.maxblk);
@@ -131,9 +131,9 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
     S[w][WF_SLOT_PP] = wf_warp_slot(pb, WF_SLOT_PP, A.ntile, A.maxblk);
     for (int q = 0; q < np; ++q) {
       const int sl = (head - q + m) % m;
-      S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ntile, A.maxblk);
-      S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ntile, A.maxblk);
-      S[w][WF_SLOT_QQI + sl] = wf_warp_slot(pb, WF_SLOT_QQI + sl, A.ntile, A.maxblk);
+      S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ncomb, A.maxblk);
+      S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ncomb, A.maxblk);
+      S[w][WF_SLOT_QQI + sl] = wf_warp_slot(pb, WF_SLOT_QQI + sl, A.ncomb, A.maxblk);
     }
     __syncwarp();
     if (lane != 0) return;
@@ -218,11 +218,11 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
   const int np = A.init ? 0 : M.npairs, head = M.head;
   const double prior = wf_warp_slot(pb, WF_SLOT_PRIOR, A.ntile, A.maxblk);
   const double data = wf_warp_slot(pb, WF_SLOT_DATA, A.nrb, A.maxblk);
-  const double gg = wf_warp_slot(pb, WF_SLOT_GG, A.ntile, A.maxblk);
+  const double gg = wf_warp_slot(pb, WF_SLOT_GG, A.ncomb, A.maxblk);
   for (int q = 0; q < np; ++q) {
     const int sl = (head - q + m) % m;
-    S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ntile, A.maxblk);
-    S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ntile, A.maxblk);
+    S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ncomb, A.maxblk);
+    S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ncomb, A.maxblk);
   }
   __syncwarp();
   if (lane != 0) return;
@@ -330,9 +330,11 @@ static wf_status ensure_solver(wf_problem* p, int m) {
 template <typename T>
 static cudaError_t iteration(const wf_problem* p, const WfBufs& b, const WfLbBufs& lb, const WfScalarArgs& A,
                              WfSolver* S, cudaStream_t st) {
-  cudaError_t e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_FULL, st);
+  cudaError_t e = wf_launch_lb_comb<T>(p->g, b, lb, WF_LB1_FULL, st);
+  if (e == cudaSuccess) e = wf_launch_lb_colinv<T>(p->g, b, lb, st);
   if (e == cudaSuccess) e = wf_launch_lb_row<T>(p->g, b, lb, st);
-  if (e == cudaSuccess) e = wf_launch_lb3<T>(p->g, b, lb, st);
+  if (e == cudaSuccess) e = wf_launch_lb_colfwd<T>(p->g, b, lb, st);
+  if (e == cudaSuccess) e = wf_launch_lb_qdots<T>(p->g, b, lb, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S->nact, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     k_lb_scalar<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, A, p->count, S->nact);
@@ -345,9 +347,9 @@ template <typename T>
 static cudaError_t refresh(const wf_problem* p, const WfBufs& b, const WfLbBufs& lb, WfScalarArgs A, int init,
                            WfSolver* S, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  if (!init) e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_MATERIALIZE, st);
+  if (!init) e = wf_launch_lb_comb<T>(p->g, b, lb, WF_LB1_MATERIALIZE, st);
   if (e == cudaSuccess) e = wf_launch_eval_pk<T>(p->g, b, lb.s, lb.g, st);
-  if (e == cudaSuccess) e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_DOTS, st);
+  if (e == cudaSuccess) e = wf_launch_lb_comb<T>(p->g, b, lb, WF_LB1_DOTS, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(S->nact, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     A.phase = WF_PH_REFRESH;
@@ -391,6 +393,7 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   A.m = m;
   A.ntile = p->g.ntile;
   A.nrb = p->g.nrb;
+  A.ncomb = p->g.ncomb;
   A.maxblk = p->g.maxblk;
   A.phase = WF_PH_ITER;
   A.init = 0;
@@ -473,7 +476,7 @@ static wf_status finish_impl(wf_problem* p, void* s_out, void* x_out, wf_solve_s
   cudaStream_t us = (cudaStream_t)S->o.stream, st = S->work;
   WfBufs b = wf_bufs(p);
   WfLbBufs lb = lb_bufs<T>(S);
-  WF_TRY(wf_launch_lb1<T>(p->g, b, lb, WF_LB1_MATERIALIZE, st));
+  WF_TRY(wf_launch_lb_comb<T>(p->g, b, lb, WF_LB1_MATERIALIZE, st));
   WF_TRY(wf_launch_eval_pk<T>(p->g, b, lb.s, lb.g, st));
   k_lb_final<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, p->g.ntile, p->g.nrb,
                                                                     p->g.maxblk, p->count, S->stats_dev);
@@ -510,32 +513,39 @@ static wf_status finish_impl(wf_problem* p, void* s_out, void* x_out, wf_solve_s
 // Run n iterations with plain launches and CUDA events around each kernel on
 // the working stream; ms[0..3] = average duration of k_lb1, the row stage,
 // k_lb3 and the scalar step.
+// Run n iterations with plain launches and CUDA events around each kernel on
+// the working stream; ms[0..5] = average duration of k_lb_comb, k_lb_colinv,
+// the row stage, k_lb_colfwd, k_lb_qdots and the scalar step.
 template <typename T>
 static wf_status profile_impl(wf_problem* p, int n_iter, float* ms) {
   WfSolver* S = p->solver;
   cudaStream_t st = S->work;
   WfBufs b = wf_bufs(p);
   WfLbBufs lb = lb_bufs<T>(S);
-  cudaEvent_t ev[5];
-  for (int i = 0; i < 5; ++i) WF_TRY(cudaEventCreate(&ev[i]));
-  double acc[4] = {0, 0, 0, 0};
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) WF_TRY(cudaEventCreate(&ev[i]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
   wf_status rs = WF_OK;
   for (int it = 0; it < n_iter && rs == WF_OK; ++it) {
     cudaError_t e = cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess) e = wf_launch_lb1<T>(p->g, b, lb, WF_LB1_FULL, st);
+    if (e == cudaSuccess) e = wf_launch_lb_comb<T>(p->g, b, lb, WF_LB1_FULL, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess) e = wf_launch_lb_row<T>(p->g, b, lb, st);
+    if (e == cudaSuccess) e = wf_launch_lb_colinv<T>(p->g, b, lb, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-    if (e == cudaSuccess) e = wf_launch_lb3<T>(p->g, b, lb, st);
+    if (e == cudaSuccess) e = wf_launch_lb_row<T>(p->g, b, lb, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = wf_launch_lb_colfwd<T>(p->g, b, lb, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
+    if (e == cudaSuccess) e = wf_launch_lb_qdots<T>(p->g, b, lb, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[5], st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->nact, 0, sizeof(int), st);
     if (e == cudaSuccess) {
       k_lb_scalar<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, S->A, p->count, S->nact);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    if (e == cudaSuccess) e = cudaEventRecord(ev[6], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
       float t = 0.f;
       e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
       acc[k] += t;
@@ -543,8 +553,8 @@ static wf_status profile_impl(wf_problem* p, int n_iter, float* ms) {
     if (e != cudaSuccess) rs = wf_cuda_fail(e, "wf_solver_profile");
     S->iters += 1;
   }
-  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
-  for (int k = 0; k < 4; ++k) ms[k] = n_iter > 0 ? (float)(acc[k] / n_iter) : 0.f;
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+  for (int k = 0; k < 6; ++k) ms[k] = n_iter > 0 ? (float)(acc[k] / n_iter) : 0.f;
   return rs;
 }
 

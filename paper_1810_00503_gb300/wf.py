@@ -289,8 +289,8 @@ class Problem:
         return na.value if sync else None
 
     def profile(self, n_iter):
-        """wf_solver_profile: average ms of the four kernels of one iteration."""
-        ms = (ctypes.c_float * 4)()
+        """wf_solver_profile: average ms of the six kernels of one iteration."""
+        ms = (ctypes.c_float * 6)()
         _check(lib().wf_solver_profile(self._p, int(n_iter), ms))
         return list(ms)
 
