@@ -140,14 +140,15 @@ def make_problem(args, rank, dev):
 
 def algorithmic_bytes(n, m, elt=4):
     """Compulsory DRAM bytes per map of each kernel of one iteration (ring full).
-    Packed vector V = n * n/2 complex = 2 n^2 values; sqrt(P) table n (n/2+1)
+    Packed vector V = n * n/2 complex = n^2 values; sqrt(P) table n (n/2+1)
     values; weight map n^2 values.
-    comb:   reads the 2m stored vectors, s and g; writes s, g and p.
+    comb:   reads the 2m stored vectors (the newest pair once: it also carries the
+            pending update), s and g; writes s, g and p.
     colinv: reads p and sqrt(P).        row: reads W (Hp needs no data map).
     colfwd: reads g, writes q (p is re-read there only because the column
             stages are split; the re-read and the scratch traffic are not counted).
     qdots:  reads q and the m - 1 other stored Q."""
-    V = 2 * n * n * elt
+    V = n * n * elt
     sp = n * (n // 2 + 1) * elt
     return {"comb": (2 * m + 5) * V, "colinv": V + sp, "row": n * n * elt, "colfwd": 2 * V,
             "qdots": m * V}

@@ -108,6 +108,24 @@ __device__ __forceinline__ void dft_reg(V2<T>* v) {
   dit_stages<T, R, DIR, 2>(v);
 }
 
+// Shared-memory position of flat tile index x.  The low bits are XORed with
+// higher bits so that the strided accesses of the Stockham passes (stride R
+// in the first pass, stride C*TC in column tiles) spread over all banks:
+// 8-byte values fill 16 bank pairs, 16-byte values 8 bank quads.  A bijection
+// within each aligned block of 16 (8) values.
+#ifndef WF_SWIZZLE
+#define WF_SWIZZLE 1
+#endif
+template <typename T>
+__device__ __forceinline__ int wf_sw(int x) {
+#if WF_SWIZZLE
+  if constexpr (sizeof(T) == 4) return x ^ (((x >> 4) ^ (x >> 8)) & 15);
+  else return x ^ (((x >> 3) ^ (x >> 6)) & 7);
+#else
+  return x;
+#endif
+}
+
 // Twiddle exp(DIR * 2 pi i * k / WF_NT) from the shared table (k < WF_NT).
 template <typename T, int DIR>
 __device__ __forceinline__ V2<T> twid(const V2<T>* tw, int k) {
@@ -131,9 +149,8 @@ __device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, in
     const int b = threadIdx.x + i * blockDim.x;
     if (b < nbf) {
       const int t = b >> lgLR, j = b & (LR - 1);
-      const V2<T>* base = buf + t * ts;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = base[(j + r * LR) * js];
+      for (int r = 0; r < R; ++r) v[i][r] = buf[wf_sw<T>(t * ts + (j + r * LR) * js)];
     }
   }
   __syncthreads();
@@ -151,9 +168,8 @@ __device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, in
       }
       dft_reg<T, R, DIR>(v[i]);
       const int o = ((j - k) << lgR) + k;
-      V2<T>* base = buf + t * ts;
 #pragma unroll
-      for (int r = 0; r < R; ++r) base[(o + r * Ns) * js] = v[i][r];
+      for (int r = 0; r < R; ++r) buf[wf_sw<T>(t * ts + (o + r * Ns) * js)] = v[i][r];
     }
   }
   __syncthreads();

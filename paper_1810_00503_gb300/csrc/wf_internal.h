@@ -14,6 +14,12 @@
 #define WF_THREADS 256
 #define WF_EMAX 16
 #define WF_TILE (WF_THREADS * WF_EMAX)
+// Resident blocks per SM requested from the compiler for the FFT-stage kernels
+// (FP32 fits two blocks of 256 threads in the register file; FP64 one).
+#ifndef WF_MINB32
+#define WF_MINB32 2
+#endif
+#define WF_MINB(T) (sizeof(T) == 4 ? WF_MINB32 : 1)
 
 // Partial-sum slots per map (one FP64 value per block and slot).
 #define WF_MAXM 32

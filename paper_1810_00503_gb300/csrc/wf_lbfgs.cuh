@@ -99,178 +99,267 @@ __device__ __forceinline__ double wf_vdotd(typename WfVec<T>::type a, typename W
   }
 }
 
+// Asynchronous 16-byte global -> shared copies (each thread consumes only the
+// values it copied itself, so no block barrier is needed between stages).
+__device__ __forceinline__ void wf_cp16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void wf_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void wf_cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Block sums of per-thread partial dot products pdot[slot][thread], one warp
+// per slot, accumulated in FP64 in a fixed order.
+__device__ __forceinline__ void wf_reduce_pdots(const float* pdot, int nslot, const int* ids, double* part_b,
+                                                int maxblk) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = wid; k < nslot; k += nw) {
+    double v = 0.0;
+    for (int i = lane; i < (int)blockDim.x; i += 32) v += (double)pdot[k * blockDim.x + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part_b[(size_t)ids[k] * maxblk + blockIdx.x] = v;
+  }
+}
+
+// Pipeline depth of the streaming kernels: stored vectors in flight per thread.
+// Sized so that two blocks fit on an SM with m = 10 (5 x 16 KB stages + 21 KB
+// of partial dots in FP32; 2 x 32 KB stages in FP64).
+template <typename T> struct WfStages { static constexpr int v = sizeof(T) == 4 ? 5 : 2; };
+template <typename T>
+constexpr size_t wf_comb_smem(int m) {
+  return (size_t)WfStages<T>::v * (WF_COMB_EPT / WfVec<T>::VW) * WF_COMB_THREADS * 16 +
+         (size_t)(2 * m + 1) * WF_COMB_THREADS * sizeof(float);
+}
+
 // ---------------------------------------------------------------------------
 // k_lb_comb: grid (ncomb, B).  Block chunk = WF_COMB_CHUNK complex values of
-// the map's packed vectors (fewer for small maps).
+// the map's packed vectors (fewer for small maps).  The stored vectors stream
+// through a per-thread shared-memory ring, newest pair first (Q before P, so
+// that g is updated before the first dot product uses it).  The pending update
+// always belongs to the newest pair, whose slot is `head`.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(WF_COMB_THREADS)
+__global__ void __launch_bounds__(WF_COMB_THREADS, 2)
 k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   typedef typename WfVec<T>::type VT;
-  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32;
-  __shared__ double red[(2 * WF_MAXM + 1) * NW];
+  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32, S = WfStages<T>::v;
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  VT* stage = (VT*)wf_smem;  // [S][NV][threads]
+  float* pdot = (float*)(stage + S * NV * WF_COMB_THREADS);  // [2m + 1][threads] per-thread partial dots
   __shared__ int ids[2 * WF_MAXM + 1];
-  const int b = blockIdx.y;
+  const int b = blockIdx.y, tid = threadIdx.x;
   const WfLbMap* M = lb.st + b;
   const int active = M->active;
   const double pa = M->pend_alpha;
   if (mode == WF_LB1_FULL && !active && pa == 0.0) return;
   if (mode == WF_LB1_MATERIALIZE && pa == 0.0) return;
+  if (mode == WF_LB1_FULL && !active) mode = WF_LB1_MATERIALIZE;  // deactivated: apply its last step only
+  const bool mat = (pa != 0.0 && mode != WF_LB1_DOTS);
+  const bool full = (mode == WF_LB1_FULL);
   const size_t vsz = (size_t)g.C * g.n * g.h;  // complex values per map vector
   const int h = g.h, B = gridDim.y, m = lb.m;
   const size_t c0 = (size_t)blockIdx.x * WF_COMB_CHUNK;
-  size_t cend = c0 + WF_COMB_CHUNK;
-  if (cend > vsz) cend = vsz;
-  VT* sv = (VT*)((V2<T>*)lb.s + (size_t)b * vsz);
-  VT* gv = (VT*)((V2<T>*)lb.g + (size_t)b * vsz);
-  V2<T>* ring = (V2<T>*)lb.ring;
-  auto Pv = [&](int i) { return (VT*)(ring + ((size_t)i * B + b) * vsz); };
-  auto Qv = [&](int i) { return (VT*)(ring + ((size_t)(m + i) * B + b) * vsz); };
-  // vector-load index u (in units of VW complex values) and column of its first value
-  size_t u[NV];
-  int kx[NV];
-  bool ok[NV];
+  const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
+  VT* sv = (VT*)((V2<T>*)lb.s + (size_t)b * vsz + c0);
+  VT* gv = (VT*)((V2<T>*)lb.g + (size_t)b * vsz + c0);
+  const V2<T>* ring = (const V2<T>*)lb.ring;
+  const int np = (mode == WF_LB1_MATERIALIZE) ? 1 : M->npairs;
+  const int head = (mode == WF_LB1_MATERIALIZE) ? M->pend_slot : M->head;
+  const int nvec = 2 * np;
+  // vector-load index within the chunk and whether its first value is on column 0
+  int u[NV];
+  bool ok[NV], col0[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    const size_t c = c0 + ((size_t)threadIdx.x + (size_t)i * WF_COMB_THREADS) * VW;
-    ok[i] = c < cend;
+    const int c = (tid + i * WF_COMB_THREADS) * VW;
+    ok[i] = c < clen;
     u[i] = c / VW;
-    kx[i] = (int)(c % h);
+    col0[i] = ((c0 + c) % h) == 0;
   }
-  VT gr[NV];
-  if (pa != 0.0 && mode != WF_LB1_DOTS) {
-    const VT* Pp = Pv(M->pend_slot);
-    const VT* Qp = Qv(M->pend_slot);
-    VT s1[NV], p1[NV], q1[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) { s1[i] = sv[u[i]]; gr[i] = gv[u[i]]; p1[i] = Pp[u[i]]; q1[i] = Qp[u[i]]; }
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) {
-        s1[i] = wf_vaxpy<T>(s1[i], (T)pa, p1[i]);
-        gr[i] = wf_vaxpy<T>(gr[i], (T)pa, q1[i]);
-        sv[u[i]] = s1[i];
-        gv[u[i]] = gr[i];
-      }
-  } else if (mode != WF_LB1_MATERIALIZE) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) gr[i] = gv[u[i]];
-  }
-  if (mode == WF_LB1_MATERIALIZE) return;
-  if (mode == WF_LB1_FULL && !active) return;
-  const bool full = (mode == WF_LB1_FULL);
-  const int np = M->npairs, head = M->head;
-  VT pr[NV];
-  {
-    double acc = 0.0;
-    const T dg = (T)M->dg;
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) {
-        acc += wf_vdotd<T>(gr[i], gr[i], kx[i]);
-        if (full) pr[i] = wf_vscale<T>(gr[i], dg);
-      }
-    wf_warp_stash(acc, red, 0, NW);
-    if (threadIdx.x == 0) ids[0] = WF_SLOT_GG;
-  }
-  for (int q = 0; q < np; ++q) {
-    const int sl = (head - q + m) % m;
-    const VT* Pq = Pv(sl);
-    const VT* Qq = Qv(sl);
-    VT vp[NV], vq[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) { vp[i] = Pq[u[i]]; vq[i] = Qq[u[i]]; }
-    const T cp = (T)M->dP[sl], cq = (T)M->dQ[sl];
-    double ap = 0.0, aq = 0.0;
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) {
-        ap += wf_vdotd<T>(gr[i], vp[i], kx[i]);
-        aq += wf_vdotd<T>(gr[i], vq[i], kx[i]);
-        if (full) pr[i] = wf_vaxpy<T>(wf_vaxpy<T>(pr[i], cp, vp[i]), cq, vq[i]);
-      }
-    wf_warp_stash(ap, red, 1 + 2 * q, NW);
-    wf_warp_stash(aq, red, 2 + 2 * q, NW);
-    if (threadIdx.x == 0) {
-      ids[1 + 2 * q] = WF_SLOT_GP + sl;
-      ids[2 + 2 * q] = WF_SLOT_GQ + sl;
+  auto vec = [&](int v) {  // v = 2 q + (0: Q, 1: P) of the q-th newest pair
+    const int sl = (head - (v >> 1) + m) % m;
+    const int slot = (v & 1) ? sl : m + sl;
+    return (const VT*)(ring + ((size_t)slot * B + b) * vsz + c0);
+  };
+  auto wdot = [&](VT a, VT c, int i) -> double {
+    if constexpr (sizeof(T) == 4) {
+      const float d0 = a.x * c.x + a.y * c.y, d1 = a.z * c.z + a.w * c.w;
+      return (double)((col0[i] ? d0 : 2.f * d0) + 2.f * d1);
+    } else {
+      const double d0 = a.x * c.x + a.y * c.y;
+      return col0[i] ? d0 : 2.0 * d0;
     }
+  };
+  VT gr[NV], sr[NV], pr[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (ok[i]) {
+      gr[i] = gv[u[i]];
+      if (mat) sr[i] = sv[u[i]];
+      if (full) pr[i] = wf_vscale<T>(gr[i], (T)0);
+    }
+  // prologue: S - 1 vectors in flight
+#pragma unroll
+  for (int v = 0; v < S - 1; ++v) {
+    if (v < nvec) {
+      const VT* src = vec(v);
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
+    }
+    wf_cp_commit();
   }
+  for (int w = 0; w < nvec; ++w) {
+    const int v = w + S - 1;
+    if (v < nvec) {
+      const VT* src = vec(v);
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
+    }
+    wf_cp_commit();
+    wf_cp_wait<S - 1>();
+    VT x[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) x[i] = stage[((w % S) * NV + i) * WF_COMB_THREADS + tid];
+    const bool isP = (w & 1) != 0;
+    const int sl = (head - (w >> 1) + m) % m;
+    if (mat && w < 2) {  // the newest pair carries the pending update
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) {
+          if (isP) { sr[i] = wf_vaxpy<T>(sr[i], (T)pa, x[i]); sv[u[i]] = sr[i]; }
+          else { gr[i] = wf_vaxpy<T>(gr[i], (T)pa, x[i]); gv[u[i]] = gr[i]; }
+        }
+    }
+    if (mode == WF_LB1_MATERIALIZE) continue;
+    const T coef = (T)(isP ? M->dP[sl] : M->dQ[sl]);
+    double a = 0.0;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) {
+        a += wdot(gr[i], x[i], i);
+        if (full) pr[i] = wf_vaxpy<T>(pr[i], coef, x[i]);
+      }
+    pdot[(1 + w) * WF_COMB_THREADS + tid] = (float)a;
+    if (tid == 0) ids[1 + w] = (isP ? WF_SLOT_GP : WF_SLOT_GQ) + sl;
+  }
+  wf_cp_wait<0>();
+  if (mode == WF_LB1_MATERIALIZE) return;
+  double acc = 0.0;
+  const T dg = (T)M->dg;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (ok[i]) {
+      acc += wdot(gr[i], gr[i], i);
+      if (full) pr[i] = wf_vaxpy<T>(pr[i], dg, gr[i]);
+    }
+  pdot[tid] = (float)acc;
+  if (tid == 0) ids[0] = WF_SLOT_GG;
   if (full) {
-    VT* Pn = Pv(M->next);
+    VT* Pn = (VT*)((V2<T>*)ring + ((size_t)M->next * B + b) * vsz + c0);
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (ok[i]) Pn[u[i]] = pr[i];
   }
   __syncthreads();
-  wf_flush_slots(red, 1 + 2 * np, NW, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_reduce_pdots(pdot, 1 + nvec, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
 }
 
 // ---------------------------------------------------------------------------
-// k_lb_qdots: grid (ncomb, B).  <q, Q_i> for the stored Q_i other than q.
+// k_lb_qdots: grid (ncomb, B).  <q, Q_i> for the stored Q_i other than q,
+// streamed through the same per-thread shared-memory ring.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(WF_COMB_THREADS)
+__global__ void __launch_bounds__(WF_COMB_THREADS, 2)
 k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
   typedef typename WfVec<T>::type VT;
-  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32;
-  __shared__ double red[WF_MAXM * NW];
+  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32, S = WfStages<T>::v;
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  VT* stage = (VT*)wf_smem;
+  float* pdot = (float*)(stage + S * NV * WF_COMB_THREADS);
   __shared__ int ids[WF_MAXM];
-  const int b = blockIdx.y;
+  const int b = blockIdx.y, tid = threadIdx.x;
   const WfLbMap* M = lb.st + b;
   if (!M->active) return;
   const size_t vsz = (size_t)g.C * g.n * g.h;
   const int h = g.h, B = gridDim.y, m = lb.m;
   const size_t c0 = (size_t)blockIdx.x * WF_COMB_CHUNK;
-  size_t cend = c0 + WF_COMB_CHUNK;
-  if (cend > vsz) cend = vsz;
-  V2<T>* ring = (V2<T>*)lb.ring;
-  auto Qv = [&](int i) { return (const VT*)(ring + ((size_t)(m + i) * B + b) * vsz); };
-  size_t u[NV];
-  int kx[NV];
-  bool ok[NV];
+  const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
+  const V2<T>* ring = (const V2<T>*)lb.ring;
+  const int nx = M->next, np = M->npairs, head = M->head;
+  int sls[WF_MAXM];
+  int nvec = 0;
+  for (int q = 0; q < np; ++q) {
+    const int sl = (head - q + m) % m;
+    if (sl != nx) sls[nvec++] = sl;
+  }
+  int u[NV];
+  bool ok[NV], col0[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    const size_t c = c0 + ((size_t)threadIdx.x + (size_t)i * WF_COMB_THREADS) * VW;
-    ok[i] = c < cend;
+    const int c = (tid + i * WF_COMB_THREADS) * VW;
+    ok[i] = c < clen;
     u[i] = c / VW;
-    kx[i] = (int)(c % h);
+    col0[i] = ((c0 + c) % h) == 0;
   }
-  const int nx = M->next, np = M->npairs, head = M->head;
-  const VT* Qn = Qv(nx);
+  auto qvec = [&](int sl) { return (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0); };
+  const VT* Qn = qvec(nx);
   VT qr[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i)
     if (ok[i]) qr[i] = Qn[u[i]];
-  int k = 0;
-  for (int q = 0; q < np; ++q) {
-    const int sl = (head - q + m) % m;
-    if (sl == nx) continue;
-    const VT* Qq = Qv(sl);
-    VT v[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) v[i] = Qq[u[i]];
+  for (int v = 0; v < S - 1; ++v) {
+    if (v < nvec) {
+      const VT* src = qvec(sls[v]);
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
+    }
+    wf_cp_commit();
+  }
+  for (int w = 0; w < nvec; ++w) {
+    const int v = w + S - 1;
+    if (v < nvec) {
+      const VT* src = qvec(sls[v]);
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
+    }
+    wf_cp_commit();
+    wf_cp_wait<S - 1>();
     double a = 0.0;
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      if (ok[i]) a += wf_vdotd<T>(qr[i], v[i], kx[i]);
-    wf_warp_stash(a, red, k, NW);
-    if (threadIdx.x == 0) ids[k] = WF_SLOT_QQI + sl;
-    ++k;
+      if (ok[i]) {
+        const VT x = stage[((w % S) * NV + i) * WF_COMB_THREADS + tid];
+        if constexpr (sizeof(T) == 4) {
+          const float d0 = qr[i].x * x.x + qr[i].y * x.y, d1 = qr[i].z * x.z + qr[i].w * x.w;
+          a += (double)((col0[i] ? d0 : 2.f * d0) + 2.f * d1);
+        } else {
+          const double d0 = qr[i].x * x.x + qr[i].y * x.y;
+          a += col0[i] ? d0 : 2.0 * d0;
+        }
+      }
+    pdot[w * WF_COMB_THREADS + tid] = (float)a;
+    if (tid == 0) ids[w] = WF_SLOT_QQI + sls[w];
   }
+  wf_cp_wait<0>();
   __syncthreads();
-  wf_flush_slots(red, k, NW, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_reduce_pdots(pdot, nvec, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
 }
 
 // ---------------------------------------------------------------------------
 // Column stages of the Hessian-vector product on p = P[next] of each map.
 // ---------------------------------------------------------------------------
 template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS)
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb) {
   const int b = blockIdx.y;
   const WfLbMap* M = lb.st + b;
@@ -281,7 +370,7 @@ k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const vo
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS)
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, const void* tw_, WfLbBufs lb,
             double* part) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
@@ -318,7 +407,7 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
       const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
       const int kx = kx0 + t;
       const size_t off = ((size_t)c * n + j) * h + kx;
-      const V2<T> a = buf[j * CT + c * TC + t], p = pl[i], gg = gl[i];
+      const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)], p = pl[i], gg = gl[i];
       const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
       Qn[off] = q;
       qq += wf_wdot<T>(q, q, kx);
@@ -344,7 +433,7 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
 
 // Row stage of the Hessian-vector product for the maps still iterating.
 template <typename T>
-__global__ void __launch_bounds__(WF_THREADS)
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_lb_row(WfGeo g, void* scratch_, const void* w_, double* part, const void* tw_, const WfLbMap* st) {
   if (!st[blockIdx.y].active) return;
   k_row_body<T, WF_ROW_NODATA>(g, scratch_, nullptr, w_, nullptr, nullptr, part, tw_);

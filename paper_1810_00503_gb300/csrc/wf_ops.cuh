@@ -106,10 +106,10 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
     if (kx == 0) continue;
     V2<T> v[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) v[c] = buf[j * CT + c * TC + t];
+    for (int c = 0; c < C; ++c) v[c] = buf[wf_sw<T>(j * CT + c * TC + t)];
     wf_mode_op<T, C, ADJ>(v, j, kx, n, sp, extra);
 #pragma unroll
-    for (int c = 0; c < C; ++c) buf[j * CT + c * TC + t] = v[c];
+    for (int c = 0; c < C; ++c) buf[wf_sw<T>(j * CT + c * TC + t)] = v[c];
   }
   if (kx0 == 0) {
     for (int j = threadIdx.x; j <= h; j += blockDim.x) {
@@ -117,7 +117,7 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
       V2<T> X0[C], Xh[C], X0m[C], Xhm[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const V2<T> Y = buf[j * CT + c * TC], Ym = buf[jm * CT + c * TC];
+        const V2<T> Y = buf[wf_sw<T>(j * CT + c * TC)], Ym = buf[wf_sw<T>(jm * CT + c * TC)];
         wf_unpack0<T>(Y, Ym, X0[c], Xh[c]);
         wf_unpack0<T>(Ym, Y, X0m[c], Xhm[c]);
       }
@@ -127,8 +127,8 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
       wf_mode_op<T, C, ADJ>(Xhm, jm, h, n, sp, extra);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        buf[j * CT + c * TC] = wf_pack0<T>(X0[c], Xh[c]);
-        buf[jm * CT + c * TC] = wf_pack0<T>(X0m[c], Xhm[c]);
+        buf[wf_sw<T>(j * CT + c * TC)] = wf_pack0<T>(X0[c], Xh[c]);
+        buf[wf_sw<T>(jm * CT + c * TC)] = wf_pack0<T>(X0m[c], Xhm[c]);
       }
     }
   }
@@ -171,9 +171,9 @@ __device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n
         const int e = threadIdx.x + i * WF_THREADS;
         if (e < tot2) {
           const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
-          V2<T>* d = buf + j * CT + c * TC + t;
-          d[0] = mk<T>(v[i].x, v[i].y);
-          d[1] = mk<T>(v[i].z, v[i].w);
+          const int x = j * CT + c * TC + t;
+          buf[wf_sw<T>(x)] = mk<T>(v[i].x, v[i].y);
+          buf[wf_sw<T>(x + 1)] = mk<T>(v[i].z, v[i].w);
         }
       }
       return;
@@ -193,7 +193,7 @@ __device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n
     const int e = threadIdx.x + i * WF_THREADS;
     if (e < tot) {
       const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-      buf[j * CT + c * TC + t] = v[i];
+      buf[wf_sw<T>(j * CT + c * TC + t)] = v[i];
     }
   }
 }
@@ -209,8 +209,9 @@ __device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, i
         const int e = threadIdx.x + i * WF_THREADS;
         if (e < tot2) {
           const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
-          const V2<T>* q = buf + j * CT + c * TC + t;
-          *(float4*)(dst + ((size_t)c * n + j) * h + kx0 + t) = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+          const int x = j * CT + c * TC + t;
+          const V2<T> q0 = buf[wf_sw<T>(x)], q1 = buf[wf_sw<T>(x + 1)];
+          *(float4*)(dst + ((size_t)c * n + j) * h + kx0 + t) = make_float4(q0.x, q0.y, q1.x, q1.y);
         }
       }
       return;
@@ -221,7 +222,7 @@ __device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, i
     const int e = threadIdx.x + i * WF_THREADS;
     if (e < tot) {
       const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-      dst[((size_t)c * n + j) * h + kx0 + t] = buf[j * CT + c * TC + t];
+      dst[((size_t)c * n + j) * h + kx0 + t] = buf[wf_sw<T>(j * CT + c * TC + t)];
     }
   }
 }
@@ -232,7 +233,6 @@ template <typename T>
 __device__ __forceinline__ void wf_g2s(V2<T>* dst, const V2<T>* src, int tot) {
   if constexpr (sizeof(T) == 4) {
     const float4* s4 = (const float4*)src;
-    float4* d4 = (float4*)dst;
     const int t2 = tot >> 1;
     float4 v[WF_EMAX / 2];
 #pragma unroll
@@ -243,7 +243,10 @@ __device__ __forceinline__ void wf_g2s(V2<T>* dst, const V2<T>* src, int tot) {
 #pragma unroll
     for (int i = 0; i < WF_EMAX / 2; ++i) {
       const int e = threadIdx.x + i * WF_THREADS;
-      if (e < t2) d4[e] = v[i];
+      if (e < t2) {
+        dst[wf_sw<T>(2 * e)] = mk<T>(v[i].x, v[i].y);
+        dst[wf_sw<T>(2 * e + 1)] = mk<T>(v[i].z, v[i].w);
+      }
     }
   } else {
     V2<T> v[WF_EMAX];
@@ -255,7 +258,7 @@ __device__ __forceinline__ void wf_g2s(V2<T>* dst, const V2<T>* src, int tot) {
 #pragma unroll
     for (int i = 0; i < WF_EMAX; ++i) {
       const int e = threadIdx.x + i * WF_THREADS;
-      if (e < tot) dst[e] = v[i];
+      if (e < tot) dst[wf_sw<T>(e)] = v[i];
     }
   }
 }
@@ -263,18 +266,20 @@ __device__ __forceinline__ void wf_g2s(V2<T>* dst, const V2<T>* src, int tot) {
 template <typename T>
 __device__ __forceinline__ void wf_s2g(V2<T>* dst, const V2<T>* src, int tot) {
   if constexpr (sizeof(T) == 4) {
-    const float4* s4 = (const float4*)src;
     float4* d4 = (float4*)dst;
 #pragma unroll
     for (int i = 0; i < WF_EMAX / 2; ++i) {
       const int e = threadIdx.x + i * WF_THREADS;
-      if (e < (tot >> 1)) d4[e] = s4[e];
+      if (e < (tot >> 1)) {
+        const V2<T> a = src[wf_sw<T>(2 * e)], b = src[wf_sw<T>(2 * e + 1)];
+        d4[e] = make_float4(a.x, a.y, b.x, b.y);
+      }
     }
   } else {
 #pragma unroll
     for (int i = 0; i < WF_EMAX; ++i) {
       const int e = threadIdx.x + i * WF_THREADS;
-      if (e < tot) dst[e] = src[e];
+      if (e < tot) dst[e] = src[wf_sw<T>(e)];
     }
   }
 }
@@ -299,7 +304,7 @@ __device__ __forceinline__ void wf_col_inv_body(const WfGeo& g, const V2<T>* src
 }
 
 template <typename T, int C, int IN>
-__global__ void __launch_bounds__(WF_THREADS)
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_col_inv(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
   const int b = blockIdx.y, n = g.n, h = g.h;
   const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
@@ -327,7 +332,7 @@ __device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* sc
 // stage ran without data); prior partial sum |src|^2 with half-plane weights.
 // ---------------------------------------------------------------------------
 template <typename T, int C, int IN>
-__global__ void __launch_bounds__(WF_THREADS)
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const void* scratch_,
           void* dst_, double* part, const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
@@ -349,7 +354,7 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
     const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
     const int kx = kx0 + t;
     const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n);
-    const V2<T> a = buf[j * CT + c * TC + t];
+    const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
     const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
     const T m2 = sv.x * sv.x + sv.y * sv.y;
     const T o2 = o.x * o.x + o.y * o.y;
@@ -358,7 +363,7 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
     if constexpr (IN == WF_IN_PK) {
       dst[((size_t)c * n + j) * h + kx] = o;
     } else {
-      if (kx == 0) buf[j * CT + c * TC + t] = o;
+      if (kx == 0) buf[wf_sw<T>(j * CT + c * TC + t)] = o;
       else dst[((size_t)c * n + j) * (h + 1) + kx] = o;
     }
   }
@@ -370,7 +375,7 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           V2<T> X0, Xh;
-          wf_unpack0<T>(buf[j * CT + c * TC], buf[jm * CT + c * TC], X0, Xh);
+          wf_unpack0<T>(buf[wf_sw<T>(j * CT + c * TC)], buf[wf_sw<T>(jm * CT + c * TC)], X0, Xh);
           V2<T>* row = dst + ((size_t)c * n + j) * (h + 1);
           row[0] = X0;
           row[h] = Xh;
@@ -390,7 +395,7 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
 // along y -> scratch.  Used to synthesise A z for simulations.
 // ---------------------------------------------------------------------------
 template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS)
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_col_sim(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   V2<T>* s_tw = (V2<T>*)wf_smem;
@@ -442,18 +447,18 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
     // w = exp(+2 pi i / n), X[0], X[h] the real parts packed in Y[0].
     for (int e = threadIdx.x; e < RB * (h / 2 + 1); e += blockDim.x) {
       const int t = e / (h / 2 + 1), k = e - t * (h / 2 + 1);
-      V2<T>* row = buf + t * h;
+      const int r0 = t * h;
       if (k == 0) {
-        const V2<T> Y = row[0];
-        row[0] = mk<T>(Y.x + Y.y, Y.x - Y.y);
+        const V2<T> Y = buf[wf_sw<T>(r0)];
+        buf[wf_sw<T>(r0)] = mk<T>(Y.x + Y.y, Y.x - Y.y);
       } else {
         const int km = h - k;
-        const V2<T> Xk = row[k], Xm = row[km];
+        const V2<T> Xk = buf[wf_sw<T>(r0 + k)], Xm = buf[wf_sw<T>(r0 + km)];
         const V2<T> w1 = twid<T, +1>(s_tw, k << lgNTn), w2 = twid<T, +1>(s_tw, km << lgNTn);
         const V2<T> s1 = mk<T>(Xk.x + Xm.x, Xk.y - Xm.y), d1 = mk<T>(Xk.x - Xm.x, Xk.y + Xm.y);
         const V2<T> s2 = mk<T>(Xm.x + Xk.x, Xm.y - Xk.y), d2 = mk<T>(Xm.x - Xk.x, Xm.y + Xk.y);
-        row[k] = cadd<T>(s1, mul_i<T>(cmul<T>(w1, d1)));
-        row[km] = cadd<T>(s2, mul_i<T>(cmul<T>(w2, d2)));
+        buf[wf_sw<T>(r0 + k)] = cadd<T>(s1, mul_i<T>(cmul<T>(w1, d1)));
+        buf[wf_sw<T>(r0 + km)] = cadd<T>(s2, mul_i<T>(cmul<T>(w2, d2)));
       }
     }
     __syncthreads();
@@ -469,7 +474,7 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
       V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * n);
       const V2<T>* nz = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * n);
       for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        const V2<T> x = buf[e], w = wv[e], q = nz[e];
+        const V2<T> x = buf[wf_sw<T>(e)], w = wv[e], q = nz[e];
         ov[e] = mk<T>(w.x > (T)0 ? x.x + q.x : (T)0, w.y > (T)0 ? x.y + q.y : (T)0);
       }
       return;
@@ -488,14 +493,14 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
       for (int i = 0; i < WF_EMAX; ++i) {
         const int e = threadIdx.x + i * WF_THREADS;
         if (e < tot) {
-          const V2<T> x = buf[e], w = wl[i];
+          const V2<T> x = buf[wf_sw<T>(e)], w = wl[i];
           V2<T> r;
           if constexpr (MODE == WF_ROW_DATA) r = mk<T>(dl[i].x - x.x, dl[i].y - x.y);
           else r = mk<T>(-x.x, -x.y);
           const V2<T> wr = mk<T>(w.x * r.x, w.y * r.y);
           if constexpr (sizeof(T) == 4) accf += r.x * wr.x + r.y * wr.y;
           else acc += (double)(r.x * wr.x) + (double)(r.y * wr.y);
-          buf[e] = wr;
+          buf[wf_sw<T>(e)] = wr;
         }
       }
       acc += (double)accf;
@@ -507,19 +512,19 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
   fft_smem<T, -1, WF_EMAX>(buf, lgh, RB, h, 1, s_tw);
   for (int e = threadIdx.x; e < RB * (h / 2 + 1); e += blockDim.x) {
     const int t = e / (h / 2 + 1), k = e - t * (h / 2 + 1);
-    V2<T>* row = buf + t * h;
+    const int r0 = t * h;
     if (k == 0) {
-      const V2<T> Z = row[0];
-      row[0] = mk<T>(Z.x + Z.y, Z.x - Z.y);
+      const V2<T> Z = buf[wf_sw<T>(r0)];
+      buf[wf_sw<T>(r0)] = mk<T>(Z.x + Z.y, Z.x - Z.y);
     } else {
       const int km = h - k;
-      const V2<T> Zk = row[k], Zm = row[km];
+      const V2<T> Zk = buf[wf_sw<T>(r0 + k)], Zm = buf[wf_sw<T>(r0 + km)];
       const V2<T> w1 = twid<T, -1>(s_tw, k << lgNTn), w2 = twid<T, -1>(s_tw, km << lgNTn);
       const V2<T> s1 = mk<T>(Zk.x + Zm.x, Zk.y - Zm.y), d1 = mk<T>(Zk.x - Zm.x, Zk.y + Zm.y);
       const V2<T> s2 = mk<T>(Zm.x + Zk.x, Zm.y - Zk.y), d2 = mk<T>(Zm.x - Zk.x, Zm.y + Zk.y);
       const V2<T> i1 = mul_i<T>(cmul<T>(w1, d1)), i2 = mul_i<T>(cmul<T>(w2, d2));
-      row[k] = mk<T>((T)0.5 * (s1.x - i1.x), (T)0.5 * (s1.y - i1.y));
-      row[km] = mk<T>((T)0.5 * (s2.x - i2.x), (T)0.5 * (s2.y - i2.y));
+      buf[wf_sw<T>(r0 + k)] = mk<T>((T)0.5 * (s1.x - i1.x), (T)0.5 * (s1.y - i1.y));
+      buf[wf_sw<T>(r0 + km)] = mk<T>((T)0.5 * (s2.x - i2.x), (T)0.5 * (s2.y - i2.y));
     }
   }
   __syncthreads();
@@ -531,7 +536,7 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(WF_THREADS)
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_row(WfGeo g, void* scratch_, const void* d_, const void* w_, const void* aux_, void* out_,
       double* part, const void* tw_) {
   k_row_body<T, MODE>(g, scratch_, d_, w_, aux_, out_, part, tw_);

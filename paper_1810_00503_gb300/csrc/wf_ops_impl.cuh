@@ -227,12 +227,22 @@ inline int grid1d(size_t total, int cap) {
 
 template <typename T>
 cudaError_t wf_launch_lb_comb(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st) {
-  k_lb_comb<T><<<dim3(g.ncomb, b.B), WF_COMB_THREADS, 0, st>>>(g, lb, b.part, mode);
+  static int done = 0;
+  auto k = k_lb_comb<T>;
+  const size_t sm = wf_comb_smem<T>(lb.m);
+  cudaError_t e = wfimpl::ensure_smem_n(k, wf_comb_smem<T>(WF_MAXM), &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.ncomb, b.B), WF_COMB_THREADS, sm, st>>>(g, lb, b.part, mode);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t wf_launch_lb_qdots(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
-  k_lb_qdots<T><<<dim3(g.ncomb, b.B), WF_COMB_THREADS, 0, st>>>(g, lb, b.part);
+  static int done = 0;
+  auto k = k_lb_qdots<T>;
+  const size_t sm = wf_comb_smem<T>(lb.m);
+  cudaError_t e = wfimpl::ensure_smem_n(k, wf_comb_smem<T>(WF_MAXM), &done);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.ncomb, b.B), WF_COMB_THREADS, sm, st>>>(g, lb, b.part);
   return cudaGetLastError();
 }
 template <typename T>
