@@ -201,6 +201,48 @@ wf_status wf_simulate_data(wf_problem* p, const void* z, const void* noise, void
 wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
                          const double* theta, int n_bands, double* E, void* stream);
 
+/* Inputs of the band-power estimator.  All pointers are DEVICE pointers; the
+ * random fields are supplied by the caller (any generator), in the working type. */
+typedef struct {
+  int n_bands;            /* bands, ids 0 .. n_bands-1 (1..64) */
+  int n_sim;              /* noise-bias simulations (>= 2) */
+  int n_fd;               /* Fisher simulations per band, 1..n_sim; the j-th reuses simulation j */
+  int pad_;
+  const int16_t* band;    /* [C][n][n/2+1] band id of each half-plane mode, -1 = none */
+  const void* z;          /* [n_sim][C][n][n] white signal fields, N(0, 1) */
+  const void* noise;      /* [n_sim][C][n][n] noise realisations with variance 1/Ninv */
+  const void* u;          /* [n_bands][n_fd][C][n][n] white fields for the Fisher signals */
+} wf_bandpower_in;
+
+/* Outputs of the band-power estimator: HOST arrays, written. */
+typedef struct {
+  double* theta_fid;      /* [n_bands] mean of P over each band's modes */
+  double* E;              /* [n_bands] E_l of the data's MAP field (eq. el) */
+  double* bias;           /* [n_bands] noise bias b_l (eq. blmv) */
+  double* fisher;         /* [n_bands * n_bands] F[l][l'] by finite differences (eq. fisher) */
+  double* cov;            /* [n_bands * n_bands] F^-1 (eq. var) */
+  double* theta_hat;      /* [n_bands] Theta_fid + F^-1 (E - b) (eq. eq:wfmv) */
+  double* cov_E;          /* [n_bands * n_bands] sample covariance of E over the simulations */
+} wf_bandpower_out;
+
+/* Band powers, noise bias, Fisher matrix and covariance from simulations, for
+ * one data map (Sec. 2.4-2.5; procedure of Sec. 2.5):
+ *   d_j   = M (A z_j + n_j)                         noise-bias simulations
+ *   d_lj  = d_j + M A_l u_lj  (j < n_fd)            Fisher simulations, A_l = A
+ *           restricted to band l, Delta Theta_l = Theta_fid,l
+ *   every map is solved for its MAP field in one batched L-BFGS run (opts), then
+ *   E_l per map (eq. el), b = mean_j E(d_j), F[l][l'] = mean_j (E_l(d_l'j) -
+ *   E_l(d_j)) / Theta_fid,l', cov = F^-1, Theta_hat = Theta_fid + F^-1 (E - b).
+ * data: HOST descriptor of the data map with DEVICE pointers (its P is the
+ * fiducial spectrum); n, C, dtype, precision as for wf_problem_create.
+ * stats: HOST array of 1 + n_sim + n_bands * n_fd entries (data, simulations,
+ * Fisher maps in that order) or NULL.  Allocates its working memory and frees it
+ * before returning; synchronises opts->stream.  Returns WF_ENOTCONVERGED when a
+ * solve hit max_iter (outputs still written), WF_ENONFINITE if F is singular. */
+wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
+                             const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
+                             wf_solve_stats* stats);
+
 /* Objective + gradient pass that allocates nothing (no counterpart in the
  * paper; an interface for callers that cannot allocate device memory, for
  * example because a framework's caching allocator or a pool reserved at

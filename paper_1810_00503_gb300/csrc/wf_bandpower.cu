@@ -1,0 +1,299 @@
+// Band powers from simulations (Sec. 2.4-2.5 of the paper):
+//   E_l  = 1/2 sum_{k in l} |s_hat_k|^2 / Theta_fid,l           (eq. el, whitened)
+//   b_l  = mean over simulations j of E_l(MAP(d_j)),
+//          d_j = M (A z_j + n_j)                               (eq. blmv)
+//   F_ll' Delta Theta_l' = mean_j [E_l(MAP(d_j + delta_l'j)) - E_l(MAP(d_j))],
+//          delta_l'j = M A_l' u_l'j, Delta Theta_l' = Theta_fid,l' (eq. fisher)
+//   Theta_hat = Theta_fid + F^-1 (E - b),  cov = F^-1         (eq. eq:wfmv, eq:var)
+// Theta_fid,l is the mean of P over the band's full-plane modes.  The data,
+// noise-bias and Fisher maps are solved together in one batched L-BFGS run.
+// Random fields are inputs, so a run is reproducible and testable.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "wf_api_internal.h"
+
+// Theta_fid,l: full-plane mean of P over band l (half-plane multiplicity 1 on
+// the kx = 0 and kx = n/2 columns, 2 elsewhere).  One block.
+template <typename S>
+__global__ void k_theta_fid(const S* P, const int16_t* band, int n, int C, int nb, double* theta) {
+  extern __shared__ double sh[];  // [2 nb]: sums, counts
+  for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) sh[i] = 0.0;
+  __syncthreads();
+  const int h = n / 2;
+  const size_t tot = (size_t)C * n * (h + 1);
+  for (size_t i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int l = band[i];
+    if (l < 0 || l >= nb) continue;
+    const int kx = (int)(i % (h + 1));
+    const double w = (kx == 0 || kx == h) ? 1.0 : 2.0;
+    atomicAdd(&sh[l], w * (double)P[i]);
+    atomicAdd(&sh[nb + l], w);
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nb; l += blockDim.x) theta[l] = sh[nb + l] > 0.0 ? sh[l] / sh[nb + l] : 0.0;
+}
+
+// P restricted to each band: out[l][i] = band[i] == l ? P[i] : 0.
+template <typename S>
+__global__ void k_band_P(const S* P, const int16_t* band, size_t tot, int nb, S* out) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += stride) {
+    const int l = band[i];
+    const S p = P[i];
+    for (int k = 0; k < nb; ++k) out[(size_t)k * tot + i] = (l == k) ? p : (S)0;
+  }
+}
+
+// Estimator from the band energies of all solved maps.  Rows of Eall: 0 = data,
+// 1..J = noise-bias simulations, 1+J+l*nfd+j = Fisher map of band l, sim j.
+// out = [theta | E | b | F | Finv | theta_hat | covE] (sizes nb, nb, nb, nb^2,
+// nb^2, nb, nb^2); flag[0] = 1 if F is singular.  One block, nb <= 64.
+__global__ void k_bp_final(const double* Eall, const double* theta, int nb, int J, int nfd, double* out, int* flag) {
+  extern __shared__ double M[];  // [nb][2 nb] augmented matrix for Gauss-Jordan
+  __shared__ double piv_val;
+  __shared__ int piv_row;
+  double* o_theta = out;
+  double* o_E = out + nb;
+  double* o_b = out + 2 * nb;
+  double* o_F = out + 3 * nb;
+  double* o_Fi = o_F + nb * nb;
+  double* o_th = o_Fi + nb * nb;
+  double* o_cE = o_th + nb;
+  const int t = threadIdx.x;
+  for (int l = t; l < nb; l += blockDim.x) {
+    o_theta[l] = theta[l];
+    o_E[l] = Eall[l];
+    double s = 0.0;
+    for (int j = 0; j < J; ++j) s += Eall[(size_t)(1 + j) * nb + l];
+    o_b[l] = s / J;
+  }
+  __syncthreads();
+  for (int idx = t; idx < nb * nb; idx += blockDim.x) {
+    const int l = idx / nb, lp = idx % nb;
+    double s = 0.0;
+    for (int j = 0; j < nfd; ++j)
+      s += Eall[(size_t)(1 + J + lp * nfd + j) * nb + l] - Eall[(size_t)(1 + j) * nb + l];
+    o_F[idx] = s / nfd / theta[lp];
+    double c = 0.0;
+    for (int j = 0; j < J; ++j)
+      c += (Eall[(size_t)(1 + j) * nb + l] - o_b[l]) * (Eall[(size_t)(1 + j) * nb + lp] - o_b[lp]);
+    o_cE[idx] = J > 1 ? c / (J - 1) : 0.0;
+  }
+  __syncthreads();
+  // Gauss-Jordan elimination with partial pivoting on [F | I]
+  const int w2 = 2 * nb;
+  for (int idx = t; idx < nb * w2; idx += blockDim.x) {
+    const int r = idx / w2, c = idx % w2;
+    M[idx] = c < nb ? o_F[r * nb + c] : (c - nb == r ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int col = 0; col < nb; ++col) {
+    if (t == 0) {
+      int best = col;
+      double bv = fabs(M[col * w2 + col]);
+      for (int r = col + 1; r < nb; ++r)
+        if (fabs(M[r * w2 + col]) > bv) { bv = fabs(M[r * w2 + col]); best = r; }
+      piv_row = best;
+      piv_val = M[best * w2 + col];
+      if (!(bv > 0.0) || !isfinite(bv)) flag[0] = 1;
+    }
+    __syncthreads();
+    if (piv_row != col)
+      for (int c = t; c < w2; c += blockDim.x) {
+        const double a = M[col * w2 + c];
+        M[col * w2 + c] = M[piv_row * w2 + c];
+        M[piv_row * w2 + c] = a;
+      }
+    __syncthreads();
+    const double pv = piv_val;
+    for (int c = t; c < w2; c += blockDim.x) M[col * w2 + c] /= pv;
+    __syncthreads();
+    for (int idx = t; idx < nb * w2; idx += blockDim.x) {
+      const int r = idx / w2, c = idx % w2;
+      if (r != col && c != col) M[idx] -= M[r * w2 + col] * M[col * w2 + c];
+    }
+    __syncthreads();
+    for (int r = t; r < nb; r += blockDim.x)
+      if (r != col) M[r * w2 + col] = 0.0;
+    __syncthreads();
+  }
+  for (int idx = t; idx < nb * nb; idx += blockDim.x) o_Fi[idx] = M[(idx / nb) * w2 + nb + idx % nb];
+  __syncthreads();
+  for (int l = t; l < nb; l += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nb; ++k) s += o_Fi[l * nb + k] * (o_E[k] - o_b[k]);
+    o_th[l] = o_theta[l] + s;
+  }
+}
+
+namespace {
+struct Scope {  // frees what the estimator allocates, on every return path
+  void* ptrs[16] = {};
+  int n = 0;
+  wf_problem* probs[4] = {};
+  int np = 0;
+  void* add(void* p) { ptrs[n++] = p; return p; }
+  void addp(wf_problem* p) { probs[np++] = p; }
+  ~Scope() {
+    for (int i = 0; i < np; ++i) wf_problem_destroy(probs[i]);
+    for (int i = 0; i < n; ++i) cudaFree(ptrs[i]);
+  }
+};
+}  // namespace
+
+#define BP_TRY(expr)                                                      \
+  do {                                                                    \
+    cudaError_t e_ = (expr);                                              \
+    if (e_ != cudaSuccess) return wf_cuda_fail(e_, "bandpower_estimate: " #expr); \
+  } while (0)
+#define BP_OK(expr)                        \
+  do {                                     \
+    wf_status s_ = (expr);                 \
+    if (s_ != WF_OK) return s_;            \
+  } while (0)
+
+extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
+                                        const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
+                                        wf_solve_stats* stats) {
+  if (!h || !data || !in || !out) return wf_fail(WF_EINVAL, "bandpower_estimate: null argument");
+  if (!data->d || !data->mask || !data->Ninv || !data->P)
+    return wf_fail(WF_EINVAL, "bandpower_estimate: the data map needs d, mask, Ninv and P");
+  const int nb = in->n_bands, J = in->n_sim, nfd = in->n_fd;
+  if (nb < 1 || nb > 64) return wf_fail(WF_EINVAL, "bandpower_estimate: n_bands = %d outside [1, 64]", nb);
+  if (J < 2) return wf_fail(WF_EINVAL, "bandpower_estimate: n_sim = %d (need >= 2)", J);
+  if (nfd < 1 || nfd > J) return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd = %d outside [1, n_sim]", nfd);
+  if (!in->band || !in->z || !in->noise || !in->u)
+    return wf_fail(WF_EINVAL, "bandpower_estimate: null band table or random fields");
+  if (!out->theta_fid || !out->E || !out->bias || !out->fisher || !out->cov || !out->theta_hat || !out->cov_E)
+    return wf_fail(WF_EINVAL, "bandpower_estimate: null output array");
+  if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "bandpower_estimate: bad dtype");
+  wf_opts o;
+  if (opts) o = *opts;
+  else wf_opts_default(&o);
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const size_t delt = dtype == WF_F64 ? 8 : 4;
+  const size_t welt = precision == WF_FP64 ? 8 : 4;
+  const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
+  const int nF = nb * nfd, Btot = 1 + J + nF;
+  Scope sc;
+  // Theta_fid and the band-restricted power tables
+  double* theta = nullptr;
+  BP_OK(wf_alloc((void**)&theta, sizeof(double) * nb, "theta_fid"));
+  sc.add(theta);
+  if (dtype == WF_F64)
+    k_theta_fid<double><<<1, 1024, 2 * nb * sizeof(double), st>>>((const double*)data->P, in->band, n, C, nb, theta);
+  else
+    k_theta_fid<float><<<1, 1024, 2 * nb * sizeof(double), st>>>((const float*)data->P, in->band, n, C, nb, theta);
+  BP_TRY(cudaGetLastError());
+  void* Pl = nullptr;
+  BP_OK(wf_alloc(&Pl, nsp * nb * delt, "band-restricted power"));
+  sc.add(Pl);
+  const int gblk = (int)((nsp + 255) / 256 < 4096 ? (nsp + 255) / 256 : 4096);
+  if (dtype == WF_F64)
+    k_band_P<double><<<gblk, 256, 0, st>>>((const double*)data->P, in->band, nsp, nb, (double*)Pl);
+  else
+    k_band_P<float><<<gblk, 256, 0, st>>>((const float*)data->P, in->band, nsp, nb, (float*)Pl);
+  BP_TRY(cudaGetLastError());
+
+  // noise-bias simulations d_j = M (A z_j + n_j)
+  wf_map* maps = (wf_map*)calloc((size_t)Btot, sizeof(wf_map));
+  if (!maps) return wf_fail(WF_ENOMEM, "bandpower_estimate: host allocation");
+  for (int i = 0; i < Btot; ++i) {
+    maps[i].d = nullptr;
+    maps[i].mask = data->mask;
+    maps[i].Ninv = data->Ninv;
+    maps[i].P = data->P;
+  }
+  wf_problem* psim = nullptr;
+  wf_status rs = wf_problem_create(h, maps, J, n, C, dtype, precision, 1, (void*)st, &psim);
+  if (rs != WF_OK) { free(maps); return rs; }
+  sc.addp(psim);
+  void* dsim = nullptr;
+  rs = wf_alloc(&dsim, npix * J * welt, "simulated data");
+  if (rs != WF_OK) { free(maps); return rs; }
+  sc.add(dsim);
+  rs = wf_simulate_data(psim, in->z, in->noise, dsim, st);
+  if (rs != WF_OK) { free(maps); return rs; }
+
+  // Fisher maps: d_j + M A_l u_lj, synthesised with the band-restricted power as
+  // signal and the simulation's data as "noise" (M d_j = d_j)
+  for (int l = 0; l < nb; ++l)
+    for (int j = 0; j < nfd; ++j) maps[l * nfd + j].P = (const char*)Pl + (size_t)l * nsp * delt;
+  wf_problem* pfd = nullptr;
+  rs = wf_problem_create(h, maps, nF, n, C, dtype, precision, 1, (void*)st, &pfd);
+  if (rs != WF_OK) { free(maps); return rs; }
+  sc.addp(pfd);
+  void* nfd_in = nullptr;
+  void* dfd = nullptr;
+  rs = wf_alloc(&nfd_in, npix * nF * welt, "Fisher base data");
+  if (rs == WF_OK) { sc.add(nfd_in); rs = wf_alloc(&dfd, npix * nF * welt, "Fisher data"); }
+  if (rs != WF_OK) { free(maps); return rs; }
+  sc.add(dfd);
+  for (int l = 0; l < nb; ++l)
+    for (int j = 0; j < nfd; ++j) {
+      cudaError_t e = cudaMemcpyAsync((char*)nfd_in + (size_t)(l * nfd + j) * npix * welt,
+                                      (const char*)dsim + (size_t)j * npix * welt, npix * welt,
+                                      cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) { free(maps); return wf_cuda_fail(e, "bandpower_estimate: Fisher base copy"); }
+    }
+  rs = wf_simulate_data(pfd, in->u, nfd_in, dfd, st);
+  if (rs != WF_OK) { free(maps); return rs; }
+
+  // one batched MAP solve: data, simulations, Fisher maps
+  for (int i = 0; i < Btot; ++i) maps[i].P = data->P;
+  maps[0].d = data->d;
+  wf_problem* ps = nullptr;
+  rs = wf_problem_create(h, maps, Btot, n, C, dtype, precision, o.lbfgs_m, (void*)st, &ps);
+  free(maps);
+  if (rs != WF_OK) return rs;
+  sc.addp(ps);
+  BP_TRY(cudaMemcpyAsync((char*)ps->d + npix * welt, dsim, npix * J * welt, cudaMemcpyDeviceToDevice, st));
+  BP_TRY(cudaMemcpyAsync((char*)ps->d + (size_t)(1 + J) * npix * welt, dfd, npix * nF * welt,
+                         cudaMemcpyDeviceToDevice, st));
+  void* sall = nullptr;
+  BP_OK(wf_alloc(&sall, nsp * Btot * 2 * welt, "MAP spectra"));
+  sc.add(sall);
+  wf_solve_stats* hst = (wf_solve_stats*)calloc((size_t)Btot, sizeof(wf_solve_stats));
+  if (!hst) return wf_fail(WF_ENOMEM, "bandpower_estimate: host allocation");
+  rs = wf_map_solve(ps, &o, nullptr, sall, nullptr, hst);
+  if (stats) memcpy(stats, hst, sizeof(wf_solve_stats) * Btot);
+  free(hst);
+  if (rs != WF_OK && rs != WF_ENOTCONVERGED) return rs;
+  const wf_status solve_status = rs;
+  double* Eall = nullptr;
+  BP_OK(wf_alloc((void**)&Eall, sizeof(double) * Btot * nb, "band energies"));
+  sc.add(Eall);
+  BP_OK(wf_band_energy(ps, sall, in->band, theta, nb, Eall, st));
+  const size_t nout = 4 * (size_t)nb + 3 * (size_t)nb * nb;
+  double* dout = nullptr;
+  int* dflag = nullptr;
+  BP_OK(wf_alloc((void**)&dout, sizeof(double) * nout, "estimator output"));
+  sc.add(dout);
+  BP_OK(wf_alloc((void**)&dflag, sizeof(int), "flag"));
+  sc.add(dflag);
+  BP_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), st));
+  const size_t gj_smem = sizeof(double) * 2 * nb * nb;
+  BP_TRY(cudaFuncSetAttribute(k_bp_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 64 * 64 * 8)));
+  k_bp_final<<<1, 256, gj_smem, st>>>(Eall, theta, nb, J, nfd, dout, dflag);
+  BP_TRY(cudaGetLastError());
+  double* hout = (double*)malloc(sizeof(double) * nout);
+  if (!hout) return wf_fail(WF_ENOMEM, "bandpower_estimate: host allocation");
+  int hflag = 0;
+  cudaError_t e = cudaMemcpyAsync(hout, dout, sizeof(double) * nout, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { free(hout); return wf_cuda_fail(e, "bandpower_estimate: reading results"); }
+  const size_t nb2 = (size_t)nb * nb;
+  memcpy(out->theta_fid, hout, sizeof(double) * nb);
+  memcpy(out->E, hout + nb, sizeof(double) * nb);
+  memcpy(out->bias, hout + 2 * nb, sizeof(double) * nb);
+  memcpy(out->fisher, hout + 3 * nb, sizeof(double) * nb2);
+  memcpy(out->cov, hout + 3 * nb + nb2, sizeof(double) * nb2);
+  memcpy(out->theta_hat, hout + 3 * nb + 2 * nb2, sizeof(double) * nb);
+  memcpy(out->cov_E, hout + 4 * nb + 2 * nb2, sizeof(double) * nb2);
+  free(hout);
+  if (hflag) return wf_fail(WF_ENONFINITE, "bandpower_estimate: the Fisher matrix is singular");
+  return solve_status;
+}

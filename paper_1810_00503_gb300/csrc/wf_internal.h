@@ -14,6 +14,12 @@
 #define WF_THREADS 256
 #define WF_EMAX 16
 #define WF_TILE (WF_THREADS * WF_EMAX)
+// Streaming L-BFGS kernels: threads per block, complex values per thread per
+// vector, and the resulting chunk of each map vector a block owns.
+#define WF_COMB_THREADS 256
+#define WF_COMB_EPT 4
+#define WF_COMB_CHUNK (WF_COMB_THREADS * WF_COMB_EPT)
+
 // Resident blocks per SM requested from the compiler for the FFT-stage kernels
 // (FP32 fits two blocks of 256 threads in the register file; FP64 one).
 #ifndef WF_MINB32

@@ -18,9 +18,6 @@
 #pragma once
 #include "wf_ops.cuh"
 
-#define WF_COMB_THREADS 256
-#define WF_COMB_EPT 8                                   // complex values per thread per vector
-#define WF_COMB_CHUNK (WF_COMB_THREADS * WF_COMB_EPT)   // complex values per block
 
 // Stage per-warp partial dot products: red[slot * NW + warp] (NW = warps of the block).
 __device__ __forceinline__ void wf_warp_stash(double v, double* red, int slot, int nw) {
@@ -99,18 +96,6 @@ __device__ __forceinline__ double wf_vdotd(typename WfVec<T>::type a, typename W
   }
 }
 
-// Asynchronous 16-byte global -> shared copies (each thread consumes only the
-// values it copied itself, so no block barrier is needed between stages).
-__device__ __forceinline__ void wf_cp16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void wf_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void wf_cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // Block sums of per-thread partial dot products pdot[slot][thread], one warp
 // per slot, accumulated in FP64 in a fixed order.
 __device__ __forceinline__ void wf_reduce_pdots(const float* pdot, int nslot, const int* ids, double* part_b,
@@ -125,31 +110,28 @@ __device__ __forceinline__ void wf_reduce_pdots(const float* pdot, int nslot, co
   }
 }
 
-// Pipeline depth of the streaming kernels: stored vectors in flight per thread.
-// Sized so that two blocks fit on an SM with m = 10 (5 x 16 KB stages + 21 KB
-// of partial dots in FP32; 2 x 32 KB stages in FP64).
-template <typename T> struct WfStages { static constexpr int v = sizeof(T) == 4 ? 5 : 2; };
+// Shared memory of the streaming kernels: per-thread partial dot products,
+// [2m + 1][threads] floats.
 template <typename T>
 constexpr size_t wf_comb_smem(int m) {
-  return (size_t)WfStages<T>::v * (WF_COMB_EPT / WfVec<T>::VW) * WF_COMB_THREADS * 16 +
-         (size_t)(2 * m + 1) * WF_COMB_THREADS * sizeof(float);
+  return (size_t)(2 * m + 1) * WF_COMB_THREADS * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
 // k_lb_comb: grid (ncomb, B).  Block chunk = WF_COMB_CHUNK complex values of
-// the map's packed vectors (fewer for small maps).  The stored vectors stream
-// through a per-thread shared-memory ring, newest pair first (Q before P, so
-// that g is updated before the first dot product uses it).  The pending update
-// always belongs to the newest pair, whose slot is `head`.
+// the map's packed vectors (fewer for small maps).  Each thread owns
+// WF_COMB_EPT complex values of the chunk; the stored vectors are read with
+// plain 16-byte loads, one pair (Q, P) per trip, newest first, at the
+// occupancy needed to keep HBM busy.  The pending update always belongs to the
+// newest pair, whose slot is `head`.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(WF_COMB_THREADS, 2)
+__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? 4 : 2)
 k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   typedef typename WfVec<T>::type VT;
-  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32, S = WfStages<T>::v;
+  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW;
   extern __shared__ __align__(16) unsigned char wf_smem[];
-  VT* stage = (VT*)wf_smem;  // [S][NV][threads]
-  float* pdot = (float*)(stage + S * NV * WF_COMB_THREADS);  // [2m + 1][threads] per-thread partial dots
+  float* pdot = (float*)wf_smem;  // [2m + 1][threads]
   __shared__ int ids[2 * WF_MAXM + 1];
   const int b = blockIdx.y, tid = threadIdx.x;
   const WfLbMap* M = lb.st + b;
@@ -169,8 +151,6 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   const V2<T>* ring = (const V2<T>*)lb.ring;
   const int np = (mode == WF_LB1_MATERIALIZE) ? 1 : M->npairs;
   const int head = (mode == WF_LB1_MATERIALIZE) ? M->pend_slot : M->head;
-  const int nvec = 2 * np;
-  // vector-load index within the chunk and whether its first value is on column 0
   int u[NV];
   bool ok[NV], col0[NV];
 #pragma unroll
@@ -180,18 +160,13 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
     u[i] = c / VW;
     col0[i] = ((c0 + c) % h) == 0;
   }
-  auto vec = [&](int v) {  // v = 2 q + (0: Q, 1: P) of the q-th newest pair
-    const int sl = (head - (v >> 1) + m) % m;
-    const int slot = (v & 1) ? sl : m + sl;
-    return (const VT*)(ring + ((size_t)slot * B + b) * vsz + c0);
-  };
-  auto wdot = [&](VT a, VT c, int i) -> double {
+  auto wdot = [&](VT a, VT c, int i) -> float {
     if constexpr (sizeof(T) == 4) {
       const float d0 = a.x * c.x + a.y * c.y, d1 = a.z * c.z + a.w * c.w;
-      return (double)((col0[i] ? d0 : 2.f * d0) + 2.f * d1);
+      return (col0[i] ? d0 : 2.f * d0) + 2.f * d1;
     } else {
       const double d0 = a.x * c.x + a.y * c.y;
-      return col0[i] ? d0 : 2.0 * d0;
+      return (float)(col0[i] ? d0 : 2.0 * d0);
     }
   };
   VT gr[NV], sr[NV], pr[NV];
@@ -202,56 +177,43 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
       if (mat) sr[i] = sv[u[i]];
       if (full) pr[i] = wf_vscale<T>(gr[i], (T)0);
     }
-  // prologue: S - 1 vectors in flight
-#pragma unroll
-  for (int v = 0; v < S - 1; ++v) {
-    if (v < nvec) {
-      const VT* src = vec(v);
-#pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
-    }
-    wf_cp_commit();
-  }
-  for (int w = 0; w < nvec; ++w) {
-    const int v = w + S - 1;
-    if (v < nvec) {
-      const VT* src = vec(v);
-#pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
-    }
-    wf_cp_commit();
-    wf_cp_wait<S - 1>();
-    VT x[NV];
+  for (int q = 0; q < np; ++q) {
+    const int sl = (head - q + m) % m;
+    const VT* Pq = (const VT*)(ring + ((size_t)sl * B + b) * vsz + c0);
+    const VT* Qq = (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0);
+    VT xp[NV], xq[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      if (ok[i]) x[i] = stage[((w % S) * NV + i) * WF_COMB_THREADS + tid];
-    const bool isP = (w & 1) != 0;
-    const int sl = (head - (w >> 1) + m) % m;
-    if (mat && w < 2) {  // the newest pair carries the pending update
+      if (ok[i]) { xq[i] = Qq[u[i]]; xp[i] = Pq[u[i]]; }
+    if (mat && q == 0) {  // the newest pair carries the pending update
 #pragma unroll
       for (int i = 0; i < NV; ++i)
         if (ok[i]) {
-          if (isP) { sr[i] = wf_vaxpy<T>(sr[i], (T)pa, x[i]); sv[u[i]] = sr[i]; }
-          else { gr[i] = wf_vaxpy<T>(gr[i], (T)pa, x[i]); gv[u[i]] = gr[i]; }
+          gr[i] = wf_vaxpy<T>(gr[i], (T)pa, xq[i]);
+          sr[i] = wf_vaxpy<T>(sr[i], (T)pa, xp[i]);
+          gv[u[i]] = gr[i];
+          sv[u[i]] = sr[i];
         }
     }
-    if (mode == WF_LB1_MATERIALIZE) continue;
-    const T coef = (T)(isP ? M->dP[sl] : M->dQ[sl]);
-    double a = 0.0;
+    if (mode == WF_LB1_MATERIALIZE) break;
+    const T cq = (T)M->dQ[sl], cp = (T)M->dP[sl];
+    float aq = 0.f, ap = 0.f;
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (ok[i]) {
-        a += wdot(gr[i], x[i], i);
-        if (full) pr[i] = wf_vaxpy<T>(pr[i], coef, x[i]);
+        aq += wdot(gr[i], xq[i], i);
+        ap += wdot(gr[i], xp[i], i);
+        if (full) pr[i] = wf_vaxpy<T>(wf_vaxpy<T>(pr[i], cq, xq[i]), cp, xp[i]);
       }
-    pdot[(1 + w) * WF_COMB_THREADS + tid] = (float)a;
-    if (tid == 0) ids[1 + w] = (isP ? WF_SLOT_GP : WF_SLOT_GQ) + sl;
+    pdot[(1 + 2 * q) * WF_COMB_THREADS + tid] = aq;
+    pdot[(2 + 2 * q) * WF_COMB_THREADS + tid] = ap;
+    if (tid == 0) {
+      ids[1 + 2 * q] = WF_SLOT_GQ + sl;
+      ids[2 + 2 * q] = WF_SLOT_GP + sl;
+    }
   }
-  wf_cp_wait<0>();
   if (mode == WF_LB1_MATERIALIZE) return;
-  double acc = 0.0;
+  float acc = 0.f;
   const T dg = (T)M->dg;
 #pragma unroll
   for (int i = 0; i < NV; ++i)
@@ -259,7 +221,7 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
       acc += wdot(gr[i], gr[i], i);
       if (full) pr[i] = wf_vaxpy<T>(pr[i], dg, gr[i]);
     }
-  pdot[tid] = (float)acc;
+  pdot[tid] = acc;
   if (tid == 0) ids[0] = WF_SLOT_GG;
   if (full) {
     VT* Pn = (VT*)((V2<T>*)ring + ((size_t)M->next * B + b) * vsz + c0);
@@ -268,21 +230,20 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
       if (ok[i]) Pn[u[i]] = pr[i];
   }
   __syncthreads();
-  wf_reduce_pdots(pdot, 1 + nvec, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_reduce_pdots(pdot, 1 + 2 * np, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
 }
 
 // ---------------------------------------------------------------------------
-// k_lb_qdots: grid (ncomb, B).  <q, Q_i> for the stored Q_i other than q,
-// streamed through the same per-thread shared-memory ring.
+// k_lb_qdots: grid (ncomb, B).  <q, Q_i> for the stored Q_i other than q, two
+// stored vectors per trip.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(WF_COMB_THREADS, 2)
+__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? 4 : 2)
 k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
   typedef typename WfVec<T>::type VT;
-  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW, NW = WF_COMB_THREADS / 32, S = WfStages<T>::v;
+  constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW;
   extern __shared__ __align__(16) unsigned char wf_smem[];
-  VT* stage = (VT*)wf_smem;
-  float* pdot = (float*)(stage + S * NV * WF_COMB_THREADS);
+  float* pdot = (float*)wf_smem;
   __shared__ int ids[WF_MAXM];
   const int b = blockIdx.y, tid = threadIdx.x;
   const WfLbMap* M = lb.st + b;
@@ -309,48 +270,39 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
     col0[i] = ((c0 + c) % h) == 0;
   }
   auto qvec = [&](int sl) { return (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0); };
+  auto wdot = [&](VT a, VT c, int i) -> float {
+    if constexpr (sizeof(T) == 4) {
+      const float d0 = a.x * c.x + a.y * c.y, d1 = a.z * c.z + a.w * c.w;
+      return (col0[i] ? d0 : 2.f * d0) + 2.f * d1;
+    } else {
+      const double d0 = a.x * c.x + a.y * c.y;
+      return (float)(col0[i] ? d0 : 2.0 * d0);
+    }
+  };
   const VT* Qn = qvec(nx);
   VT qr[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i)
     if (ok[i]) qr[i] = Qn[u[i]];
-#pragma unroll
-  for (int v = 0; v < S - 1; ++v) {
-    if (v < nvec) {
-      const VT* src = qvec(sls[v]);
-#pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
-    }
-    wf_cp_commit();
-  }
-  for (int w = 0; w < nvec; ++w) {
-    const int v = w + S - 1;
-    if (v < nvec) {
-      const VT* src = qvec(sls[v]);
-#pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (ok[i]) wf_cp16(&stage[((v % S) * NV + i) * WF_COMB_THREADS + tid], src + u[i]);
-    }
-    wf_cp_commit();
-    wf_cp_wait<S - 1>();
-    double a = 0.0;
+  for (int w = 0; w < nvec; w += 2) {
+    const bool two = w + 1 < nvec;
+    const VT* Qa = qvec(sls[w]);
+    const VT* Qb = qvec(two ? sls[w + 1] : sls[w]);
+    VT xa[NV], xb[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      if (ok[i]) {
-        const VT x = stage[((w % S) * NV + i) * WF_COMB_THREADS + tid];
-        if constexpr (sizeof(T) == 4) {
-          const float d0 = qr[i].x * x.x + qr[i].y * x.y, d1 = qr[i].z * x.z + qr[i].w * x.w;
-          a += (double)((col0[i] ? d0 : 2.f * d0) + 2.f * d1);
-        } else {
-          const double d0 = qr[i].x * x.x + qr[i].y * x.y;
-          a += col0[i] ? d0 : 2.0 * d0;
-        }
-      }
-    pdot[w * WF_COMB_THREADS + tid] = (float)a;
-    if (tid == 0) ids[w] = WF_SLOT_QQI + sls[w];
+      if (ok[i]) { xa[i] = Qa[u[i]]; xb[i] = Qb[u[i]]; }
+    float a = 0.f, c = 0.f;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) { a += wdot(qr[i], xa[i], i); c += wdot(qr[i], xb[i], i); }
+    pdot[w * WF_COMB_THREADS + tid] = a;
+    if (two) pdot[(w + 1) * WF_COMB_THREADS + tid] = c;
+    if (tid == 0) {
+      ids[w] = WF_SLOT_QQI + sls[w];
+      if (two) ids[w + 1] = WF_SLOT_QQI + sls[w + 1];
+    }
   }
-  wf_cp_wait<0>();
   __syncthreads();
   wf_reduce_pdots(pdot, nvec, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
 }

@@ -23,7 +23,7 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_problem_destroy", "wf_problem_set_data", "wf_eval", "wf_hess_vec",
            "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy",
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
-           "wf_eval_noalloc"]
+           "wf_eval_noalloc", "bandpower_estimate"]
 
 
 class WfMap(ctypes.Structure):
@@ -41,6 +41,17 @@ class WfOpts(ctypes.Structure):
 class WfSolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("evals", ctypes.c_int), ("status", ctypes.c_int),
                 ("pad_", ctypes.c_int), ("chi2", ctypes.c_double), ("gnorm_rel", ctypes.c_double)]
+
+
+class WfBandpowerIn(ctypes.Structure):
+    _fields_ = [("n_bands", ctypes.c_int), ("n_sim", ctypes.c_int), ("n_fd", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("band", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("noise", ctypes.c_void_p), ("u", ctypes.c_void_p)]
+
+
+class WfBandpowerOut(ctypes.Structure):
+    _fields_ = [(k, ctypes.POINTER(ctypes.c_double)) for k in
+                ("theta_fid", "E", "bias", "fisher", "cov", "theta_hat", "cov_E")]
 
 
 class WfError(RuntimeError):
@@ -80,6 +91,9 @@ def lib() -> ctypes.CDLL:
     L.wf_solver_finish.argtypes = [vp, vp, vp, ctypes.POINTER(WfSolveStats)]
     L.wf_solver_profile.argtypes = [vp, i, ctypes.POINTER(ctypes.c_float)]
     L.wf_eval_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, vp]
+    L.bandpower_estimate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
+                                     ctypes.POINTER(WfOpts), ctypes.POINTER(WfBandpowerOut),
+                                     ctypes.POINTER(WfSolveStats)]
     for name in EXPORTS:
         if name not in ("wf_last_error", "wf_opts_default"):
             getattr(L, name).restype = ctypes.c_int
@@ -157,6 +171,41 @@ def eval_noalloc(s, d, w, P, chi2=None, grad=None, stream=None):
     _check(lib().wf_eval_noalloc(_ptr(s), _ptr(d), _ptr(w), _ptr(P), n, C, B, precision, _ptr(chi2),
                                  _ptr(grad), _stream(stream)))
     return chi2, grad
+
+
+def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",
+                       handle=None, stream=None, **opts):
+    """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
+    of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
+    (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
+    (C, n, n/2+1) int16; z, noise (n_sim, C, n, n), u (n_bands, n_fd, C, n, n)
+    in the working type.  Returns (dict of numpy arrays, per-map stats)."""
+    import torch
+    handle = handle or default_handle()
+    C, n, _ = Ninv.shape
+    m = WfMap(d=_ptr(d), mask=_ptr(mask), Ninv=_ptr(Ninv), P=_ptr(P))
+    nb = int(n_bands)
+    bi = WfBandpowerIn(n_bands=nb, n_sim=int(z.shape[0]), n_fd=int(u.shape[1]), pad_=0,
+                       band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u))
+    arrs = {k: np.zeros(sz) for k, sz in (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb),
+                                          ("cov", nb * nb), ("theta_hat", nb), ("cov_E", nb * nb))}
+    bo = WfBandpowerOut(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in arrs.items()})
+    o = WfOpts()
+    lib().wf_opts_default(ctypes.byref(o))
+    for k, v in opts.items():
+        setattr(o, k, v)
+    o.stream = _stream(stream)
+    nmaps = 1 + bi.n_sim + nb * bi.n_fd
+    st = (WfSolveStats * nmaps)()
+    prec = WF_FP64 if precision == "fp64" else WF_MIXED
+    status = lib().bandpower_estimate(handle.ptr, ctypes.byref(m), n, C,
+                                      WF_F64 if Ninv.dtype == torch.float64 else WF_F32, prec,
+                                      ctypes.byref(bi), ctypes.byref(o), ctypes.byref(bo), st)
+    if status not in (0, 5):
+        _check(status)
+    for k in ("fisher", "cov", "cov_E"):
+        arrs[k] = arrs[k].reshape(nb, nb)
+    return arrs, Problem._stats(st)
 
 
 class Problem:

@@ -1,0 +1,76 @@
+"""GPU band-power estimator (bandpower_estimate) against the oracle's
+simulation band powers (Sec. 2.4-2.5) on the same seeded random fields.
+
+Both sides solve every map to a tight gradient tolerance, so the comparison is
+a numerics check.  Tolerances: FP64 1e-7 relative (the MAP error of 1e-10 is
+squared into E and differenced in F), mixed 1e-3 (the stated band-power
+tolerance)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import wf_oracle as O  # noqa: E402
+from paper_1810_00503_gb300 import synth, wf  # noqa: E402
+from tests.helpers import ensure_lib, to_dev  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    ensure_lib()
+
+
+def _run(n, nb, J, nfd, precision, seed, masked_frac=0.25):
+    inp = synth.density_small(n, seed=seed, masked_frac=masked_frac)
+    npdt = np.float64 if precision == "fp64" else np.float32
+    wdt = torch.float64 if precision == "fp64" else torch.float32
+    P = inp.P.astype(npdt).astype(np.float64)
+    Ninv = inp.Ninv.astype(npdt).astype(np.float64)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, P).astype(npdt).astype(np.float64)
+    bands = synth.log_bands(n, nb)
+    rng = np.random.default_rng(seed + 100)
+    sig = np.where(Ninv > 0, 1.0 / np.sqrt(np.where(Ninv > 0, Ninv, 1.0)), 0.0)
+    z = rng.standard_normal((J, 1, n, n)).astype(npdt).astype(np.float64)
+    nz = (rng.standard_normal((J, 1, n, n)) * sig).astype(npdt).astype(np.float64)
+    u = rng.standard_normal((nb, nfd, 1, n, n)).astype(npdt).astype(np.float64)
+    res, stats = wf.bandpower_estimate(
+        to_dev(d, wdt), to_dev(inp.mask, torch.uint8), to_dev(Ninv, wdt), to_dev(P[..., : n // 2 + 1], wdt),
+        to_dev(bands[..., : n // 2 + 1], torch.int16), nb, to_dev(z, wdt), to_dev(nz, wdt), to_dev(u, wdt),
+        precision=precision, gtol_rel=1e-12 if precision == "fp64" else 1e-7, max_iter=20000,
+        refresh_every=0 if precision == "fp64" else 50)
+    ref = O.bandpower_sims(d, inp.mask, Ninv, P, bands, nb, z, nz, u, gtol_rel=1e-12, max_iter=20000)
+    return res, ref, stats
+
+
+def _close(a, b, tol):
+    a = np.asarray(a); b = np.asarray(b)
+    return np.abs(a - b).max() <= tol * np.abs(b).max()
+
+
+def test_bandpower_fp64_matches_oracle():
+    res, ref, stats = _run(16, 3, 8, 4, "fp64", seed=31)
+    assert all(s["status"] == "WF_OK" for s in stats)
+    for k in ("theta_fid", "E", "b", "F", "cov_E", "theta_hat", "cov"):
+        kk = {"b": "bias", "F": "fisher"}.get(k, k)
+        assert _close(res[kk], ref[k], 1e-7), (k, res[kk], ref[k])
+
+
+def test_bandpower_mixed_matches_oracle_to_1e3():
+    res, ref, stats = _run(64, 4, 12, 3, "mixed", seed=5)
+    for k in ("E", "b", "F", "theta_hat"):
+        kk = {"b": "bias", "F": "fisher"}.get(k, k)
+        assert _close(res[kk], ref[k], 1e-3), (k, res[kk], ref[k])
+
+
+def test_bandpower_rejects_bad_counts():
+    n = 16
+    dt = torch.float64
+    z = torch.zeros((1, 1, n, n), dtype=dt, device="cuda")
+    with pytest.raises(wf.WfError, match="EINVAL"):
+        wf.bandpower_estimate(z[0], torch.ones((n, n), dtype=torch.uint8, device="cuda"), z[0] + 1,
+                              torch.ones((1, n, n // 2 + 1), dtype=dt, device="cuda"),
+                              torch.zeros((1, n, n // 2 + 1), dtype=torch.int16, device="cuda"), 2,
+                              z, z, torch.zeros((2, 1, 1, n, n), dtype=dt, device="cuda"))
