@@ -142,6 +142,24 @@ wf_status wf_problem_set_data(wf_problem* p, const void* d, void* stream);
  * Stream ordered, no synchronisation. */
 wf_status wf_eval(wf_problem* p, const void* s, void* grad, double* chi2, void* stream);
 
+/* Band-amplitude form of the prior (Sec. 2.3, eq. pilin: S = sum_l q_l S_fid
+ * restricted to band l, q_l = Theta_l / Theta_fid,l).  Scales the problem's
+ * signal power by q[band(k)] on every mode (modes with band id -1 keep their
+ * power); the original P is kept, so later calls replace the scale.
+ * band: device int16 [C][n][n/2+1], ids < n_b; q: device double [n_b] > 0,
+ * shared by all maps.  Stream ordered. */
+wf_status wf_problem_set_band_scale(wf_problem* p, const int16_t* band, const double* q, int n_b,
+                                    void* stream);
+
+/* wf_eval plus the derivative of chi^2 with respect to the band amplitudes,
+ * computed in the adjoint stage: dlogq[b][l] = d chi2_b / d log q_l
+ *   = -sum over the full-plane modes k of band l of Re(conj(a_k) s_k),
+ * a = sqrt(P) R^T U W (d - x) at the current scale (divide by q_l for
+ * d chi2 / d q_l).  band: device int16 [C][n][n/2+1]; dlogq: device double
+ * [count][n_b], written.  Other arguments as wf_eval.  Stream ordered. */
+wf_status wf_eval_bands(wf_problem* p, const void* s, void* grad, double* chi2, const int16_t* band, int n_b,
+                        double* dlogq, void* stream);
+
 /* Hessian-vector product of chi^2 (twice eq_curv): hv = 2 (v + A^T W A v),
  * same layouts as wf_eval.  Stream ordered. */
 wf_status wf_hess_vec(wf_problem* p, const void* v, void* hv, void* stream);
@@ -259,7 +277,8 @@ wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int
  * Scratch lives in a static device array of 16 MiB per GPU that loads the
  * library (held until the process exits).  A call whose scratch would not fit
  * (it needs about (C n^2 + C n (n/2+1)) working-type values per map plus
- * 24 KiB) returns WF_EINVAL; FP32 fits up to three 1024^2 maps per call.
+ * 264 KiB of twiddle tables) returns WF_EINVAL; FP32 fits up to three 1024^2
+ * maps per call.
  * The first call on a device resolves the array's address and writes the
  * twiddle tables with blocking copies; make that first call before any stream
  * capture.  All calls share the one array and each call overwrites what it

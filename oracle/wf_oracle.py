@@ -131,6 +131,19 @@ def grad(z, d, W, P) -> np.ndarray:
     return 2.0 * (z - apply_At(W * r, P))
 
 
+def chi2_dlogq(z, d, W, P, bands, n_bands):
+    """d chi^2 / d log q_l when band l's power is scaled by q_l (S = sum_l q_l
+    S_fid on band l, Sec. 2.3 eq. pilin), at the scale already folded into P:
+    d sqrt(q P) / d log q = sqrt(q P) / 2 on band l, so dA/dlog q_l is A built
+    with P/4 on band l and 0 elsewhere, and d chi^2 = -2 (W r).(dA z)."""
+    r = d - apply_A(z, P)
+    out = np.zeros(n_bands)
+    for l in range(n_bands):
+        dA_z = apply_A(z, np.where(bands == l, 0.25 * P, 0.0))
+        out[l] = -2.0 * float(np.sum(W * r * dA_z))
+    return out
+
+
 def hess_vec(v, W, P) -> np.ndarray:
     """Full Hessian of chi^2 times v: 2 (I + A^T W A) v (twice eq_curv)."""
     return 2.0 * (v + apply_At(W * apply_A(v, P), P))

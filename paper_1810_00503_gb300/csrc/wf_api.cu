@@ -62,8 +62,11 @@ WfGeo wf_make_geo(int n, int C) {
   return g;
 }
 
-// Roots of unity exp(-2 pi i k / WF_NT), computed in long double; the values
-// at multiples of pi/2 are set exactly.
+// Twiddle buffer of WF_TWTAB entries (layout in wf_internal.h).  Roots of unity
+// exp(-2 pi i k / WF_NT) are computed in long double, with the values at
+// multiples of pi/2 set exactly.  The pass table of length L = 2^lgL follows the
+// radix plan of fft_smem: the pass with span Ns and radix R holds
+// exp(-2 pi i k r / (Ns R)) at (Ns - R1) + (r - 1) Ns + k, R1 the first radix.
 void wf_make_twiddles(double2* out) {
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int k = 0; k < WF_NT; ++k) {
@@ -77,6 +80,23 @@ void wf_make_twiddles(double2* out) {
     out[k].x = c;
     out[k].y = s;
   }
+  for (int lgL = 1; lgL <= WF_LOG2_NT; ++lgL) {
+    double2* tab = out + (size_t)WF_NT * lgL;
+    for (int i = 0; i < WF_NT; ++i) { tab[i].x = 0.0; tab[i].y = 0.0; }
+    const int np = (lgL + 3) >> 2;
+    int rem = lgL, lgNs = 0, R1 = 1;
+    for (int p = 0; p < np; ++p) {
+      const int left = np - p, bits = (rem + left - 1) / left, R = 1 << bits, Ns = 1 << lgNs;
+      if (p == 0) R1 = R;
+      if (Ns > 1) {
+        const int sh = WF_LOG2_NT - lgNs - bits;
+        for (int r = 1; r < R; ++r)
+          for (int k = 0; k < Ns; ++k) tab[(Ns - R1) + (r - 1) * Ns + k] = out[(k * r) << sh];
+      }
+      rem -= bits;
+      lgNs += bits;
+    }
+  }
 }
 
 extern "C" wf_status wf_create(wf_handle** out) {
@@ -86,14 +106,22 @@ extern "C" wf_status wf_create(wf_handle** out) {
   if (!h) return wf_fail(WF_ENOMEM, "wf_create: host allocation failed");
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) { free(h); return wf_cuda_fail(e, "wf_create: cudaGetDevice"); }
-  double2 tw64[WF_NT];
-  float2 tw32[WF_NT];
+  double2* tw64 = (double2*)malloc(sizeof(double2) * WF_TWTAB);
+  float2* tw32 = (float2*)malloc(sizeof(float2) * WF_TWTAB);
+  if (!tw64 || !tw32) {
+    free(tw64);
+    free(tw32);
+    free(h);
+    return wf_fail(WF_ENOMEM, "wf_create: host allocation failed");
+  }
   wf_make_twiddles(tw64);
-  for (int k = 0; k < WF_NT; ++k) { tw32[k].x = (float)tw64[k].x; tw32[k].y = (float)tw64[k].y; }
-  e = cudaMalloc(&h->tw64, sizeof tw64);
-  if (e == cudaSuccess) e = cudaMalloc(&h->tw32, sizeof tw32);
-  if (e == cudaSuccess) e = cudaMemcpy(h->tw64, tw64, sizeof tw64, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->tw32, tw32, sizeof tw32, cudaMemcpyHostToDevice);
+  for (int k = 0; k < WF_TWTAB; ++k) { tw32[k].x = (float)tw64[k].x; tw32[k].y = (float)tw64[k].y; }
+  e = cudaMalloc(&h->tw64, sizeof(double2) * WF_TWTAB);
+  if (e == cudaSuccess) e = cudaMalloc(&h->tw32, sizeof(float2) * WF_TWTAB);
+  if (e == cudaSuccess) e = cudaMemcpy(h->tw64, tw64, sizeof(double2) * WF_TWTAB, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->tw32, tw32, sizeof(float2) * WF_TWTAB, cudaMemcpyHostToDevice);
+  free(tw64);
+  free(tw32);
   if (e != cudaSuccess) {
     if (h->tw64) cudaFree(h->tw64);
     if (h->tw32) cudaFree(h->tw32);
@@ -114,7 +142,7 @@ extern "C" wf_status wf_destroy(wf_handle* h) {
 
 static void free_problem(wf_problem* p) {
   if (!p) return;
-  void* ptrs[] = {p->d, p->w, p->sp, p->scratch, p->part, p->flags};
+  void* ptrs[] = {p->d, p->w, p->sp, p->sp0, p->scratch, p->part, p->flags};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   wf_solver_free(p);
@@ -290,4 +318,32 @@ extern "C" wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t*
   cudaError_t e = WF_DISPATCH(p, wf_launch_band_energy)(p->g, p->count, s, band, theta, n_bands, E,
                                                         (cudaStream_t)stream);
   return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_band_energy");
+}
+
+extern "C" wf_status wf_problem_set_band_scale(wf_problem* p, const int16_t* band, const double* q, int n_b,
+                                               void* stream) {
+  if (!p || !band || !q) return wf_fail(WF_EINVAL, "wf_problem_set_band_scale: null argument");
+  if (n_b < 1 || n_b > 1024) return wf_fail(WF_EINVAL, "wf_problem_set_band_scale: n_b = %d", n_b);
+  const size_t nsp = (size_t)p->C * p->n * (p->n / 2 + 1);
+  const int ntab = p->sp_shared ? 1 : p->count;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!p->sp0) {
+    wf_status s = wf_alloc(&p->sp0, nsp * ntab * p->elt, "unscaled sqrt(P) table");
+    if (s != WF_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(p->sp0, p->sp, nsp * ntab * p->elt, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return wf_cuda_fail(e, "wf_problem_set_band_scale: copy");
+  }
+  cudaError_t e = WF_DISPATCH(p, wf_launch_band_scale)(p->g, p->sp0, p->sp, ntab, band, q, n_b, st);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_problem_set_band_scale");
+}
+
+extern "C" wf_status wf_eval_bands(wf_problem* p, const void* s, void* grad, double* chi2, const int16_t* band,
+                                   int n_b, double* dlogq, void* stream) {
+  if (!p || !s || !grad || !chi2 || !band || !dlogq) return wf_fail(WF_EINVAL, "wf_eval_bands: null argument");
+  if (s == grad) return wf_fail(WF_EINVAL, "wf_eval_bands: s and grad must not alias");
+  if (n_b < 1 || n_b > 1024) return wf_fail(WF_EINVAL, "wf_eval_bands: n_b = %d outside [1, 1024]", n_b);
+  WfBufs b = wf_bufs(p);
+  cudaError_t e = WF_DISPATCH(p, wf_launch_eval_bands)(p->g, b, s, grad, chi2, band, n_b, dlogq,
+                                                       (cudaStream_t)stream);
+  return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_eval_bands");
 }

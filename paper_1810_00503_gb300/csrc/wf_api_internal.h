@@ -4,8 +4,8 @@
 
 struct wf_handle {
   int device;
-  void* tw64;   // WF_NT double2 roots of unity
-  void* tw32;   // WF_NT float2 roots of unity
+  void* tw64;   // WF_TWTAB double2 twiddles (roots of unity, pass tables)
+  void* tw32;   // WF_TWTAB float2 twiddles
 };
 
 struct WfSolver;  // L-BFGS state, allocated on the first solve (wf_solve.cu)
@@ -19,7 +19,8 @@ struct wf_problem {
   long long sp_stride;   // elements between maps' sqrt(P) tables
   void* d;               // [count][C][n][n] working type
   void* w;               // [count][C][n][n] mask * Ninv
-  void* sp;              // [1 or count][C][n][n/2+1] sqrt(P)/n
+  void* sp;              // [1 or count][C][n][n/2+1] sqrt(P)/n (band-scaled if set)
+  void* sp0;             // unscaled copy, kept once a band scale has been set
   void* scratch;         // [count][C][n][n/2] complex
   double* part;          // [count][WF_NSLOT][maxblk]
   int* flags;            // device status words
@@ -31,4 +32,4 @@ wf_status wf_cuda_fail(cudaError_t e, const char* what);
 wf_status wf_alloc(void** ptr, size_t bytes, const char* what);
 WfBufs wf_bufs(const wf_problem* p);
 void wf_solver_free(wf_problem* p);
-void wf_make_twiddles(double2* out);  // WF_NT roots of unity exp(-2 pi i k / WF_NT)
+void wf_make_twiddles(double2* out);  // WF_TWTAB entries: roots of unity and pass tables

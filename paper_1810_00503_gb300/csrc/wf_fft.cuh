@@ -9,12 +9,16 @@
 // butterflies in registers between two barriers, so a pass is in place.
 //
 // Sign convention: DIR = -1 is the forward transform sum_j x_j e^{-2 pi i jk/L},
-// DIR = +1 the unnormalised inverse.  Twiddles come from a table of the WF_NT-th
-// roots of unity, tw[k] = exp(-2 pi i k / WF_NT), computed on the host in long
-// double and staged in shared memory by the caller.
+// DIR = +1 the unnormalised inverse.  Twiddles come from tables computed on the
+// host in long double (see wf_make_twiddles): the WF_NT-th roots of unity
+// tw[k] = exp(-2 pi i k / WF_NT) and, for each length L, a pass table ordered so
+// that consecutive butterflies read consecutive entries.  Kernels stage the
+// tables they use in shared memory.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "wf_internal.h"
 
@@ -24,6 +28,11 @@ template <> struct V2t<float>  { typedef float2  type; };
 template <> struct V2t<double> { typedef double2 type; };
 
 template <typename T> using V2 = typename V2t<T>::type;
+
+// Per-thread accumulator of a dot product over a thread's few elements: FP32
+// in the mixed path (each partial then continues in FP64 across the block),
+// FP64 in the FP64 path.
+template <typename T> using WfAcc = typename std::conditional<sizeof(T) == 4, float, double>::type;
 
 template <typename T> __device__ __forceinline__ V2<T> mk(T x, T y) { V2<T> r; r.x = x; r.y = y; return r; }
 template <typename T> __device__ __forceinline__ V2<T> cadd(V2<T> a, V2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
@@ -135,9 +144,12 @@ __device__ __forceinline__ V2<T> twid(const V2<T>* tw, int k) {
 }
 
 // One Stockham pass.  EMAX = most samples a thread holds (compile time).
+// ptab is the length-L pass table: the twiddles of the pass with span Ns sit at
+// ptab[(Ns - R1) + (r - 1) Ns + k] = exp(-2 pi i k r / (Ns R)) (R1 = radix of the
+// first pass), so butterflies with consecutive k read consecutive entries.
 template <typename T, int R, int DIR, int EMAX>
 __device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, int ts, int js,
-                                         int Ns, int lgNs, const V2<T>* tw) {
+                                         int Ns, int lgNs, const V2<T>* ptab, int R1) {
   constexpr int NB = (EMAX / R) > 0 ? (EMAX / R) : 1;
   constexpr int lgR = Log2R<R>::v;
   const int lgLR = lgL - lgR;
@@ -161,10 +173,9 @@ __device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, in
       const int t = b >> lgLR, j = b & (LR - 1);
       const int k = j & (Ns - 1);
       if (Ns > 1) {
-        // w_{Ns R}^{k r} = table[k r WF_NT / (Ns R)]
-        const int sh = WF_LOG2_NT - lgNs - lgR;
+        const V2<T>* pt = ptab + (Ns - R1) + k;
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[i][r] = cmul<T>(v[i][r], twid<T, DIR>(tw, (k * r) << sh));
+        for (int r = 1; r < R; ++r) v[i][r] = cmul<T>(v[i][r], twid<T, DIR>(pt, (r - 1) * Ns));
       }
       dft_reg<T, R, DIR>(v[i]);
       const int o = ((j - k) << lgR) + k;
@@ -178,20 +189,22 @@ __device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, in
 // Full transform of `cnt` sequences of length L = 2^lgL (1 <= lgL <= 10).
 // Radix plan: ceil(lgL / 4) passes with the bits spread as evenly as possible,
 // larger radices first.  Requires cnt * L <= EMAX * blockDim.x.
+// ptab: the length-L pass table (see fft_pass), staged in shared memory.
 template <typename T, int DIR, int EMAX>
-__device__ __forceinline__ void fft_smem(V2<T>* buf, int lgL, int cnt, int ts, int js, const V2<T>* tw) {
+__device__ __forceinline__ void fft_smem(V2<T>* buf, int lgL, int cnt, int ts, int js, const V2<T>* ptab) {
   const int L = 1 << lgL;
   const int np = (lgL + 3) >> 2;
-  int rem = lgL, lgNs = 0;
+  int rem = lgL, lgNs = 0, R1 = 1;
   for (int p = 0; p < np; ++p) {
     const int left = np - p;
     const int bits = (rem + left - 1) / left;  // ceil(rem / left)
     const int Ns = 1 << lgNs;
+    if (p == 0) R1 = 1 << bits;
     switch (bits) {
-      case 4: fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
-      case 3: fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
-      case 2: fft_pass<T, 4, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
-      default: fft_pass<T, 2, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, tw); break;
+      case 4: fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
+      case 3: fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
+      case 2: fft_pass<T, 4, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
+      default: fft_pass<T, 2, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
     }
     rem -= bits;
     lgNs += bits;

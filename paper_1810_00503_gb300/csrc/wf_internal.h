@@ -8,6 +8,9 @@
 
 #define WF_NT 1024          // largest transform length and twiddle-table size
 #define WF_LOG2_NT 10
+// Twiddle buffer: [0, WF_NT) roots of unity exp(-2 pi i k / WF_NT); then for
+// lgL = 1..10 the pass table of length 2^lgL at WF_NT * lgL (2^lgL - 1 entries).
+#define WF_TWTAB ((WF_LOG2_NT + 1) * WF_NT)
 
 // Threads per block of every operator kernel and the most samples one thread
 // stages in registers during an FFT pass; a tile holds at most their product.
@@ -135,6 +138,12 @@ cudaError_t wf_launch_lb_qdots(const WfGeo& g, const WfBufs& b, const WfLbBufs& 
 // Full objective+gradient pass on packed vectors (src -> dst), all maps.
 template <typename T>
 cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_eval_bands(const WfGeo& g, const WfBufs& b, const void* src, void* dst, double* chi2,
+                                 const int16_t* band, int n_b, double* dq, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_band_scale(const WfGeo& g, const void* sp0, void* sp, int ntab, const int16_t* band,
+                                 const double* q, int n_b, cudaStream_t st);
 template <typename T>
 cudaError_t wf_launch_pack(const WfGeo& g, int B, const void* std_in, void* pk_out, cudaStream_t st);
 template <typename T>

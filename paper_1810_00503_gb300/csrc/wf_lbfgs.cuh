@@ -125,8 +125,11 @@ constexpr size_t wf_comb_smem(int m) {
 // occupancy needed to keep HBM busy.  The pending update always belongs to the
 // newest pair, whose slot is `head`.
 // ---------------------------------------------------------------------------
+#ifndef WF_COMB_MINB
+#define WF_COMB_MINB 4
+#endif
 template <typename T>
-__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? WF_COMB_MINB : 2)
 k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   typedef typename WfVec<T>::type VT;
   constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW;
@@ -284,23 +287,25 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
 #pragma unroll
   for (int i = 0; i < NV; ++i)
     if (ok[i]) qr[i] = Qn[u[i]];
-  for (int w = 0; w < nvec; w += 2) {
-    const bool two = w + 1 < nvec;
-    const VT* Qa = qvec(sls[w]);
-    const VT* Qb = qvec(two ? sls[w + 1] : sls[w]);
-    VT xa[NV], xb[NV];
+  constexpr int U = 4;  // stored vectors per trip
+  for (int w = 0; w < nvec; w += U) {
+    VT x[U][NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) { xa[i] = Qa[u[i]]; xb[i] = Qb[u[i]]; }
-    float a = 0.f, c = 0.f;
+    for (int v = 0; v < U; ++v) {
+      const VT* Qv = qvec(sls[w + v < nvec ? w + v : w]);
 #pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) { a += wdot(qr[i], xa[i], i); c += wdot(qr[i], xb[i], i); }
-    pdot[w * WF_COMB_THREADS + tid] = a;
-    if (two) pdot[(w + 1) * WF_COMB_THREADS + tid] = c;
-    if (tid == 0) {
-      ids[w] = WF_SLOT_QQI + sls[w];
-      if (two) ids[w + 1] = WF_SLOT_QQI + sls[w + 1];
+      for (int i = 0; i < NV; ++i)
+        if (ok[i] && w + v < nvec) x[v][i] = Qv[u[i]];
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      if (w + v >= nvec) break;
+      float a = 0.f;
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) a += wdot(qr[i], x[v][i], i);
+      pdot[(w + v) * WF_COMB_THREADS + tid] = a;
+      if (tid == 0) ids[w + v] = WF_SLOT_QQI + sls[w + v];
     }
   }
   __syncthreads();
@@ -340,7 +345,8 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
   const V2<T>* Pn = (const V2<T>*)lb.ring + ((size_t)nx * B + b) * vsz;
   V2<T>* Qn = (V2<T>*)lb.ring + ((size_t)(m + nx) * B + b) * vsz;
   const V2<T>* gv = (const V2<T>*)lb.g + (size_t)b * vsz;
-  double qq = 0, pq = 0, pp = 0, gq = 0, gp = 0;
+  typedef WfAcc<T> A;
+  A qq = 0, pq = 0, pp = 0, gq = 0, gp = 0;
   V2<T> pl[WF_EMAX], gl[WF_EMAX];
 #pragma unroll
   for (int i = 0; i < WF_EMAX; ++i) {
@@ -362,20 +368,21 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
       const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)], p = pl[i], gg = gl[i];
       const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
       Qn[off] = q;
-      qq += wf_wdot<T>(q, q, kx);
-      pq += wf_wdot<T>(p, q, kx);
-      pp += wf_wdot<T>(p, p, kx);
-      gq += wf_wdot<T>(gg, q, kx);
-      gp += wf_wdot<T>(gg, p, kx);
+      const A wk = kx == 0 ? (A)1 : (A)2;
+      qq += wk * (A)(q.x * q.x + q.y * q.y);
+      pq += wk * (A)(p.x * q.x + p.y * q.y);
+      pp += wk * (A)(p.x * p.x + p.y * p.y);
+      gq += wk * (A)(gg.x * q.x + gg.y * q.y);
+      gp += wk * (A)(gg.x * p.x + gg.y * p.y);
     }
   }
   __shared__ double red[5 * (WF_THREADS / 32)];
   __shared__ int ids[5];
-  wf_warp_stash(qq, red, 0, WF_THREADS / 32);
-  wf_warp_stash(pq, red, 1, WF_THREADS / 32);
-  wf_warp_stash(pp, red, 2, WF_THREADS / 32);
-  wf_warp_stash(gq, red, 3, WF_THREADS / 32);
-  wf_warp_stash(gp, red, 4, WF_THREADS / 32);
+  wf_warp_stash((double)qq, red, 0, WF_THREADS / 32);
+  wf_warp_stash((double)pq, red, 1, WF_THREADS / 32);
+  wf_warp_stash((double)pp, red, 2, WF_THREADS / 32);
+  wf_warp_stash((double)gq, red, 3, WF_THREADS / 32);
+  wf_warp_stash((double)gp, red, 4, WF_THREADS / 32);
   if (threadIdx.x == 0) {
     ids[0] = WF_SLOT_QQ; ids[1] = WF_SLOT_PQ; ids[2] = WF_SLOT_PP; ids[3] = WF_SLOT_GQN; ids[4] = WF_SLOT_GPN;
   }

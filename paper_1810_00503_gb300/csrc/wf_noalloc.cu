@@ -9,17 +9,17 @@
 // partial sums and the intermediate spectra) in the file-scope device array
 // below, which every GPU that loads the library holds until the process exits.
 //
-// Layout of the array: [0, 16 KiB) FP64 twiddles, [16, 24 KiB) FP32 twiddles,
-// then the sqrt(P)/n table, the partial sums and the intermediate spectra,
-// each starting on a 256-byte boundary.
+// Layout of the array: FP64 twiddle tables (176 KiB), FP32 twiddle tables
+// (88 KiB), then the sqrt(P)/n table, the partial sums and the intermediate
+// spectra, each starting on a 256-byte boundary.
 #include <mutex>
 
 #include "wf_api_internal.h"
 
 #define WF_NOALLOC_BYTES (16u << 20)  // 16 MiB per device
 #define WF_NOALLOC_TW64 0
-#define WF_NOALLOC_TW32 (WF_NT * sizeof(double2))
-#define WF_NOALLOC_DATA (WF_NOALLOC_TW32 + WF_NT * sizeof(float2))
+#define WF_NOALLOC_TW32 (WF_TWTAB * sizeof(double2))
+#define WF_NOALLOC_DATA (WF_NOALLOC_TW32 + WF_TWTAB * sizeof(float2))
 #define WF_NOALLOC_MAXDEV 64
 
 static __device__ __align__(256) unsigned char wf_noalloc_scratch[WF_NOALLOC_BYTES];
@@ -38,10 +38,10 @@ static wf_status noalloc_setup(int dev, unsigned char** out) {
   void* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&ptr, wf_noalloc_scratch);
   if (e != cudaSuccess) return wf_cuda_fail(e, "wf_eval_noalloc: cudaGetSymbolAddress of the static scratch");
-  double2 tw64[WF_NT];
-  float2 tw32[WF_NT];
+  static double2 tw64[WF_TWTAB];  // host staging (guarded by the mutex)
+  static float2 tw32[WF_TWTAB];
   wf_make_twiddles(tw64);
-  for (int k = 0; k < WF_NT; ++k) {
+  for (int k = 0; k < WF_TWTAB; ++k) {
     tw32[k].x = (float)tw64[k].x;
     tw32[k].y = (float)tw64[k].y;
   }

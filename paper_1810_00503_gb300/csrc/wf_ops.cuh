@@ -37,9 +37,11 @@ __device__ __forceinline__ double wf_block_sum(double v) {
   return r;
 }
 
+// Stage the roots of unity (lgL = 0) or the pass table of length 2^lgL.
 template <typename T>
-__device__ __forceinline__ void wf_stage_tw(V2<T>* s_tw, const V2<T>* g_tw) {
-  for (int i = threadIdx.x; i < WF_NT; i += blockDim.x) s_tw[i] = g_tw[i];
+__device__ __forceinline__ void wf_stage_tw(V2<T>* s_tw, const V2<T>* g_tw, int lgL = 0) {
+  const V2<T>* src = g_tw + (size_t)WF_NT * lgL;
+  for (int i = threadIdx.x; i < WF_NT; i += blockDim.x) s_tw[i] = src[i];
 }
 
 // Kaiser-Squires cosine / sine of half-plane mode (row j, column kx), kx in
@@ -294,7 +296,7 @@ __device__ __forceinline__ void wf_col_inv_body(const WfGeo& g, const V2<T>* src
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
   const int n = g.n, lgTC = __ffs(g.TC) - 1, kx0 = blockIdx.x * g.TC;
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, g.lgn);
   wf_tile_load<T, C, IN>(buf, src, n, lgTC, kx0);
   __syncthreads();
   wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp, (T)1);
@@ -318,7 +320,7 @@ template <typename T, int C>
 __device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* scr, const T* sp, V2<T>* buf,
                                                  V2<T>* s_tw, const void* tw_) {
   const int n = g.n, lgTC = __ffs(g.TC) - 1, CT = C * g.TC, kx0 = blockIdx.x * g.TC;
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, g.lgn);
   wf_tile_load<T, C, WF_IN_PK>(buf, scr, n, lgTC, kx0);
   __syncthreads();
   fft_smem<T, -1, WF_EMAX>(buf, g.lgn, CT, 1, CT, s_tw);
@@ -334,13 +336,14 @@ __device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* sc
 template <typename T, int C, int IN>
 __global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const void* scratch_,
-          void* dst_, double* part, const void* tw_) {
+          void* dst_, double* part, const void* tw_, const int16_t* band, int n_b, double* dq) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
+  double* bins = (double*)(buf + WF_TILE);  // [n_b] band sums of the optional epilogue
   const int b = blockIdx.y, n = g.n, h = g.h, lgn = g.lgn;
   const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
   wf_tile_load<T, C, WF_IN_PK>(buf, (const V2<T>*)scratch_ + (size_t)b * C * n * h, n, lgTC, kx0);
   __syncthreads();
   fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
@@ -349,17 +352,46 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
   const V2<T>* src = (const V2<T>*)src_ + (size_t)b * sstride;
   V2<T>* dst = (V2<T>*)dst_ + (size_t)b * sstride;
-  double acc = 0.0, acc2 = 0.0;
+  // Optional band epilogue (standard-layout input only): D_l = -sum over the
+  // full-plane modes of band l of Re(conj(a) s), a = sqrt(P) R^T U W r, which is
+  // d chi^2 / d log q_l when band l's power is scaled by q_l.
+  const bool bands = (IN == WF_IN_STD) && band != nullptr;
+  if (bands) {
+    for (int i = threadIdx.x; i < n_b; i += blockDim.x) bins[i] = 0.0;
+    __syncthreads();
+    if (kx0 == 0) {  // packed column 0: unpack a, then kx = 0 and kx = n/2 modes
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int jm = (n - j) & (n - 1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          V2<T> A0, Ah;
+          wf_unpack0<T>(buf[wf_sw<T>(j * CT + c * TC)], buf[wf_sw<T>(jm * CT + c * TC)], A0, Ah);
+          const V2<T>* row = src + ((size_t)c * n + j) * (h + 1);
+          const V2<T> S0 = row[0], Sh = row[h];
+          const int16_t* brow = band + ((size_t)c * n + j) * (h + 1);
+          const int l0 = brow[0], lh = brow[h];
+          if (l0 >= 0 && l0 < n_b) atomicAdd(&bins[l0], -(double)(A0.x * S0.x + A0.y * S0.y));
+          if (lh >= 0 && lh < n_b) atomicAdd(&bins[lh], -(double)(Ah.x * Sh.x + Ah.y * Sh.y));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  WfAcc<T> acc = 0, acc2 = 0;  // per-thread partials; FP64 from the block sum on
   for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
     const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
     const int kx = kx0 + t;
     const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n);
     const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
+    if (bands && kx > 0) {
+      const int l = band[((size_t)c * n + j) * (h + 1) + kx];
+      if (l >= 0 && l < n_b) atomicAdd(&bins[l], -2.0 * (double)(a.x * sv.x + a.y * sv.y));
+    }
     const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
     const T m2 = sv.x * sv.x + sv.y * sv.y;
     const T o2 = o.x * o.x + o.y * o.y;
-    acc += (kx == 0) ? (double)m2 : 2.0 * (double)m2;
-    acc2 += (kx == 0) ? (double)o2 : 2.0 * (double)o2;
+    acc += (kx == 0) ? m2 : (T)2 * m2;
+    acc2 += (kx == 0) ? o2 : (T)2 * o2;
     if constexpr (IN == WF_IN_PK) {
       dst[((size_t)c * n + j) * h + kx] = o;
     } else {
@@ -383,10 +415,29 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
       }
     }
   }
-  const double tot = wf_block_sum(acc);
+  const double tot = wf_block_sum((double)acc);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_PRIOR) * g.maxblk + blockIdx.x] = tot;
-  const double tot2 = wf_block_sum(acc2);
+  const double tot2 = wf_block_sum((double)acc2);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_OUT2) * g.maxblk + blockIdx.x] = tot2;
+  if (bands) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_b; i += blockDim.x)
+      if (bins[i] != 0.0) atomicAdd(&dq[(size_t)b * n_b + i], bins[i]);
+  }
+}
+
+// Scale the sqrt(P)/n table by sqrt(q_l) on the modes of band l (others 1):
+// sp = sp0 * sqrt(q[band]); q has n_b entries shared by all maps.
+template <typename T>
+__global__ void k_band_scale(const T* sp0, T* sp, size_t nsp, int ntab, const int16_t* band, const double* q,
+                             int n_b) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t tot = nsp * (size_t)ntab;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += stride) {
+    const int l = band[i % nsp];
+    const double f = (l >= 0 && l < n_b) ? sqrt(q[l]) : 1.0;
+    sp[i] = (T)((double)sp0[i] * f);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -402,7 +453,7 @@ k_col_sim(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void
   V2<T>* buf = s_tw + WF_NT;
   const int b = blockIdx.y, n = g.n, h = g.h, lgn = g.lgn;
   const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
   V2<T>* sc = (V2<T>*)scratch_ + (size_t)b * C * n * h;
   wf_tile_load<T, C, WF_IN_PK>(buf, sc, n, lgTC, kx0);
   __syncthreads();
@@ -425,12 +476,14 @@ template <typename T, int MODE>
 __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* d_, const void* w_,
                                            const void* aux_, void* out_, double* part, const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
-  V2<T>* s_tw = (V2<T>*)wf_smem;
-  V2<T>* buf = s_tw + WF_NT;
+  V2<T>* s_tw = (V2<T>*)wf_smem;   // roots of unity (real-FFT pre/post twiddles)
+  V2<T>* s_pt = s_tw + WF_NT;       // pass table of length n/2
+  V2<T>* buf = s_pt + WF_NT;
   const int b = blockIdx.y, n = g.n, h = g.h, lgh = g.lgh, RB = g.RB;
   const int row0 = blockIdx.x * RB;
   const size_t npix = (size_t)g.C * n * n;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
+  wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, lgh);
   V2<T>* sc = (V2<T>*)scratch_ + (size_t)b * g.C * n * h + (size_t)row0 * h;
   const int tot = RB * h;
   const int lgNTn = WF_LOG2_NT - g.lgn;  // table stride of the n-th roots
@@ -462,7 +515,7 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
       }
     }
     __syncthreads();
-    fft_smem<T, +1, WF_EMAX>(buf, lgh, RB, h, 1, s_tw);
+    fft_smem<T, +1, WF_EMAX>(buf, lgh, RB, h, 1, s_pt);
     // pixel stage: buf[t][m] holds pixels (2m, 2m+1) of row row0 + t
     const V2<T>* dv = (const V2<T>*)((const T*)d_ + (size_t)b * npix + (size_t)row0 * n);
     const V2<T>* wv = (const V2<T>*)((const T*)w_ + (size_t)b * npix + (size_t)row0 * n);
@@ -509,7 +562,7 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
   }
   // r2c: forward FFT of the packed pairs, then
   // X[k] = (Z[k] + conj Z[h-k])/2 - i w^-k (Z[k] - conj Z[h-k])/2, X[0], X[h] packed.
-  fft_smem<T, -1, WF_EMAX>(buf, lgh, RB, h, 1, s_tw);
+  fft_smem<T, -1, WF_EMAX>(buf, lgh, RB, h, 1, s_pt);
   for (int e = threadIdx.x; e < RB * (h / 2 + 1); e += blockDim.x) {
     const int t = e / (h / 2 + 1), k = e - t * (h / 2 + 1);
     const int r0 = t * h;

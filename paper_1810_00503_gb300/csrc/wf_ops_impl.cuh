@@ -9,7 +9,7 @@ template <typename T> inline size_t col_smem(const WfGeo& g) {
   return (WF_NT + (size_t)g.C * g.TC * g.n) * sizeof(V2<T>);
 }
 template <typename T> inline size_t row_smem(const WfGeo& g) {
-  return (WF_NT + (size_t)g.RB * g.h) * sizeof(V2<T>);
+  return (2 * WF_NT + (size_t)g.RB * g.h) * sizeof(V2<T>);
 }
 
 // Raise the dynamic shared-memory limit of a kernel once per device.
@@ -19,7 +19,7 @@ template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes, int
   if (e != cudaSuccess) return e;
   if (dev < 32 && (*done_mask >> dev) & 1) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)((WF_NT + WF_TILE) * sizeof(double2)));
+                           (int)((2 * WF_NT + WF_TILE) * sizeof(double2)));
   if (e == cudaSuccess && dev < 32) *done_mask |= 1 << dev;
   (void)bytes;
   return e;
@@ -37,14 +37,15 @@ cudaError_t col_inv(const WfGeo& g, const WfBufs& b, const void* src, cudaStream
 }
 
 template <typename T, int C, int IN>
-cudaError_t col_fwd(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st) {
+cudaError_t col_fwd(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st,
+                    const int16_t* band = nullptr, int n_b = 0, double* dq = nullptr) {
   static int done = 0;
   auto k = k_col_fwd<T, C, IN>;
-  const size_t sm = col_smem<T>(g);
+  const size_t sm = band ? (WF_NT + (size_t)WF_TILE) * sizeof(V2<T>) + sizeof(double) * n_b : col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, dst,
-                                                b.part, b.tw);
+                                                b.part, b.tw, band, n_b, dq);
   return cudaGetLastError();
 }
 
@@ -226,6 +227,29 @@ inline int grid1d(size_t total, int cap) {
   }
 
 template <typename T>
+cudaError_t wf_launch_eval_bands(const WfGeo& g, const WfBufs& b, const void* src, void* dst, double* chi2,
+                                 const int16_t* band, int n_b, double* dq, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(dq, 0, sizeof(double) * (size_t)b.B * n_b, st);
+  if (e == cudaSuccess) e = wfimpl::col_inv_any<T>(g, b, WF_IN_STD, src, st);
+  if (e == cudaSuccess) e = wfimpl::row_any<T>(WF_ROW_DATA, g, b, nullptr, nullptr, st);
+  if (e == cudaSuccess)
+    e = g.C == 1 ? wfimpl::col_fwd<T, 1, WF_IN_STD>(g, b, src, dst, st, band, n_b, dq)
+                 : wfimpl::col_fwd<T, 2, WF_IN_STD>(g, b, src, dst, st, band, n_b, dq);
+  if (e == cudaSuccess && chi2) {
+    k_finalize_chi2<<<b.B, WF_THREADS, 0, st>>>(b.part, g.maxblk, g.ntile, g.nrb, chi2);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+template <typename T>
+cudaError_t wf_launch_band_scale(const WfGeo& g, const void* sp0, void* sp, int ntab, const int16_t* band,
+                                 const double* q, int n_b, cudaStream_t st) {
+  const size_t nsp = (size_t)g.C * g.n * (g.h + 1);
+  k_band_scale<T><<<wfimpl::grid1d(nsp * ntab, 4096), 256, 0, st>>>((const T*)sp0, (T*)sp, nsp, ntab, band, q,
+                                                                     n_b);
+  return cudaGetLastError();
+}
+template <typename T>
 cudaError_t wf_launch_lb_comb(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st) {
   static int done = 0;
   auto k = k_lb_comb<T>;
@@ -298,4 +322,8 @@ cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, 
   template cudaError_t wf_launch_lb_row<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,           \
                                            cudaStream_t);                                          \
   template cudaError_t wf_launch_eval_pk<T>(const WfGeo&, const WfBufs&, const void*, void*,       \
-                                            cudaStream_t);
+                                            cudaStream_t);                                         \
+  template cudaError_t wf_launch_eval_bands<T>(const WfGeo&, const WfBufs&, const void*, void*,    \
+                                               double*, const int16_t*, int, double*, cudaStream_t);\
+  template cudaError_t wf_launch_band_scale<T>(const WfGeo&, const void*, void*, int,               \
+                                               const int16_t*, const double*, int, cudaStream_t);

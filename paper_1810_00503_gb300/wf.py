@@ -23,7 +23,7 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_problem_destroy", "wf_problem_set_data", "wf_eval", "wf_hess_vec",
            "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy",
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
-           "wf_eval_noalloc", "bandpower_estimate"]
+           "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands"]
 
 
 class WfMap(ctypes.Structure):
@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
     L.wf_solver_finish.argtypes = [vp, vp, vp, ctypes.POINTER(WfSolveStats)]
     L.wf_solver_profile.argtypes = [vp, i, ctypes.POINTER(ctypes.c_float)]
     L.wf_eval_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, vp]
+    L.wf_problem_set_band_scale.argtypes = [vp, vp, vp, i, vp]
+    L.wf_eval_bands.argtypes = [vp, vp, vp, vp, vp, i, vp, vp]
     L.bandpower_estimate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
                                      ctypes.POINTER(WfOpts), ctypes.POINTER(WfBandpowerOut),
                                      ctypes.POINTER(WfSolveStats)]
@@ -278,6 +280,22 @@ class Problem:
         chi2 = torch.empty(self.B, dtype=torch.float64, device=s.device) if chi2 is None else chi2
         _check(lib().wf_eval(self._p, _ptr(s), _ptr(grad), _ptr(chi2), _stream(stream)))
         return chi2, grad
+
+    def set_band_scale(self, band, q, stream=None):
+        """wf_problem_set_band_scale: P <- q[band] P (band int16 (C, n, n/2+1),
+        q float64 (n_b,) CUDA tensors)."""
+        _check(lib().wf_problem_set_band_scale(self._p, _ptr(band), _ptr(q), int(q.numel()), _stream(stream)))
+
+    def eval_bands(self, s, band, n_b, stream=None):
+        """wf_eval_bands: (chi2, grad, d chi2 / d log q) at the current band scale."""
+        import torch
+        self._spec(s)
+        grad = torch.empty_like(s)
+        chi2 = torch.empty(self.B, dtype=torch.float64, device=s.device)
+        dq = torch.empty((self.B, int(n_b)), dtype=torch.float64, device=s.device)
+        _check(lib().wf_eval_bands(self._p, _ptr(s), _ptr(grad), _ptr(chi2), _ptr(band), int(n_b), _ptr(dq),
+                                   _stream(stream)))
+        return chi2, grad, dq
 
     def hess_vec(self, v, out=None, stream=None):
         import torch

@@ -1,0 +1,67 @@
+"""Band-amplitude derivatives from the adjoint stage (wf_eval_bands) against
+the oracle, and the torch.autograd.Function against central finite
+differences on random directions (Hermitian-consistent for s)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import wf_oracle as O  # noqa: E402
+from paper_1810_00503_gb300 import synth  # noqa: E402
+from tests.helpers import ensure_lib, make_problem, rel, rfft_u, to_dev  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    ensure_lib()
+
+
+@pytest.mark.parametrize("n,C", [(32, 1), (64, 2), (256, 1)])
+def test_eval_bands_matches_oracle(n, C):
+    nb = 4
+    inp = synth.density_small(n, seed=12) if C == 1 else synth.shear_eb(n, seed=12)
+    prob, host = make_problem([inp], "fp64")
+    bands = synth.log_bands(n, nb, C=C)
+    nbt = nb * C
+    band_t = to_dev(bands[..., : n // 2 + 1], torch.int16)
+    rng = np.random.default_rng(1)
+    q = rng.uniform(0.5, 2.0, size=nbt)
+    prob.set_band_scale(band_t, to_dev(q, torch.float64))
+    Pq = host["P"][0] * np.where(bands >= 0, q[np.maximum(bands, 0)], 1.0)
+    z = synth.random_state(n, C, seed=2)
+    s = to_dev(rfft_u(z)[None], torch.complex128)
+    chi2, g, dq = prob.eval_bands(s, band_t, nbt)
+    torch.cuda.synchronize()
+    ref = O.chi2_dlogq(z, host["d"][0], host["W"][0], Pq, bands, nbt)
+    assert np.allclose(dq[0].cpu().numpy(), ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    assert abs(chi2[0].item() - O.chi2(z, host["d"][0], host["W"][0], Pq)) <= 1e-12 * chi2[0].item()
+    assert rel(g[0].cpu().numpy(), rfft_u(O.grad(z, host["d"][0], host["W"][0], Pq))) <= 1e-12
+
+
+def test_autograd_function_matches_finite_differences():
+    from paper_1810_00503_gb300.autograd import chi2 as wf_chi2
+    n, nb = 64, 5
+    inp = synth.density_small(n, seed=3)
+    prob, host = make_problem([inp], "fp64")
+    bands = synth.log_bands(n, nb)
+    band_t = to_dev(bands[..., : n // 2 + 1], torch.int16)
+    rng = np.random.default_rng(9)
+    s = to_dev(rfft_u(synth.random_state(n, 1, seed=5))[None], torch.complex128).requires_grad_(True)
+    q = to_dev(rng.uniform(0.5, 1.5, size=nb), torch.float64).requires_grad_(True)
+    f = wf_chi2(s, q, prob, band_t).sum()
+    f.backward()
+    gs, gq = s.grad.clone(), q.grad.clone()
+    h = 1e-4
+    with torch.no_grad():
+        for k in range(20):
+            dirs = to_dev(rfft_u(np.random.default_rng(100 + k).standard_normal((1, n, n)))[None],
+                          torch.complex128)
+            dq = to_dev(np.random.default_rng(200 + k).standard_normal(nb), torch.float64)
+            fp = wf_chi2(s + h * dirs, q + h * dq, prob, band_t).sum().item()
+            fm = wf_chi2(s - h * dirs, q - h * dq, prob, band_t).sum().item()
+            fd = (fp - fm) / (2 * h)
+            an = float((gs.real * dirs.real + gs.imag * dirs.imag).sum() + (gq * dq).sum())
+            assert abs(fd - an) <= 1e-6 * abs(f.item()) / 1e3 + 1e-6 * abs(an), (k, fd, an)

@@ -216,3 +216,22 @@ def test_simulated_band_terms_match_exact_traces():
     # finite-difference F: each entry is a mean of J cross terms; loose 5-sigma-ish bound
     assert np.allclose(res["F"], F_ex, rtol=0.25, atol=0.1 * np.abs(F_ex).max())
     assert np.allclose(res["cov_E"], F_ex, rtol=0.3, atol=0.1 * np.abs(F_ex).max())
+
+
+@pytest.mark.parametrize("C", [1, 2])
+def test_band_amplitude_derivative_matches_finite_differences(C):
+    # chi^2(log q) is smooth; central differences with step 1e-4 agree to O(h^2).
+    n, nb = 16, 3
+    inp = synth.density_small(n, seed=8) if C == 1 else synth.shear_eb(n, seed=8)
+    W = inp.mask[None] * inp.Ninv
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb, C=C)
+    rng = np.random.default_rng(4)
+    z = rng.standard_normal(d.shape)
+    an = O.chi2_dlogq(z, d, W, inp.P, bands, nb * C)
+    h = 1e-4
+    for l in range(nb * C):
+        up = np.where(bands == l, np.exp(h), 1.0) * inp.P
+        dn = np.where(bands == l, np.exp(-h), 1.0) * inp.P
+        fd = (O.chi2(z, d, W, up) - O.chi2(z, d, W, dn)) / (2 * h)
+        assert abs(fd - an[l]) <= 1e-6 * max(abs(an).max(), 1.0), (l, fd, an[l])
