@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--m", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-bandpower", action="store_true")
     return ap.parse_args()
 
 
@@ -234,6 +235,45 @@ def run_e2e(args, dev, host, iters):
             "note": "one wf_map_solve job from pinned host inputs incl. preparation; bytes per step = job bytes / iterations"}
 
 
+def run_bandpower(args, dev, n_sim=100, n_bands=20, n_fd=1):
+    """One complete band-power estimate (Sec. 2.4-2.5) on the same CMB patch:
+    n_sim noise-bias simulations and n_bands * n_fd Fisher simulations, all
+    solved with the paper's stopping rule (Delta chi^2 < 0.1), on the device."""
+    import numpy as np
+    import torch
+    from paper_1810_00503_gb300 import synth, wf
+    n = args.n
+    inp = synth.cmb_patch(n, seed=3)
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    Ninv = torch.as_tensor(inp.Ninv, dtype=torch.float32, device=dev)
+    mask = torch.as_tensor(inp.mask, dtype=torch.uint8, device=dev)
+    P = torch.as_tensor(inp.P_half, dtype=torch.float32, device=dev)
+    sig = torch.where(Ninv > 0, torch.rsqrt(torch.clamp(Ninv, min=1e-30)), torch.zeros_like(Ninv))
+    one = wf.Problem(torch.zeros_like(Ninv)[None], mask, Ninv[None], P, precision="mixed")
+    d = one.simulate(torch.randn(1, 1, n, n, generator=g, device=dev),
+                     torch.randn(1, 1, n, n, generator=g, device=dev) * sig)[0]
+    one.close()
+    bands = torch.as_tensor(synth.log_bands(n, n_bands)[..., : n // 2 + 1], dtype=torch.int16, device=dev)
+    z = torch.randn(n_sim, 1, n, n, generator=g, device=dev)
+    nz = torch.randn(n_sim, 1, n, n, generator=g, device=dev) * sig
+    u = torch.randn(n_bands, n_fd, 1, n, n, generator=g, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, stats = wf.bandpower_estimate(d, mask, Ninv, P, bands, n_bands, z, nz, u, precision="mixed",
+                                       gtol_rel=0.0, dchi2_abs=0.1, max_iter=20000, check_every=32,
+                                       refresh_every=200)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nsim = n_sim + n_bands * n_fd
+    its = [st["iters"] for st in stats]
+    return {"sims_per_s": nsim / dt, "map_solves_per_s": (nsim + 1) / dt, "seconds": dt,
+            "n_sim": n_sim, "n_fisher": n_bands * n_fd, "n_bands": n_bands, "stop": "Delta chi^2 < 0.1",
+            "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
+            "statuses": sorted(set(st["status"] for st in stats)),
+            "theta_hat_over_fid_median": float(np.median(res["theta_hat"] / res["theta_fid"]))}
+
+
 # ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -371,6 +411,9 @@ def main():
                        "gnorm_rel_map0": r["stats0"]["gnorm_rel"]}}
     if rank == 0:
         line["clocks"] = r["clocks"]
+        r["prob"].close()
+        if not args.no_bandpower:
+            line["bandpower"] = run_bandpower(args, dev)
         if not args.no_e2e:
             line["e2e"] = run_e2e(args, dev, r["host"], iters=max(K, 10))
         if not args.no_cpu:

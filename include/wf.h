@@ -203,6 +203,18 @@ wf_status wf_solver_finish(wf_problem* p, void* s_out, void* x_out, wf_solve_sta
  * used for roofline reports. */
 wf_status wf_solver_profile(wf_problem* p, int n_iter, float* ms);
 
+/* MAP solves of several prepared problems at once, typically one per map
+ * shape of a heterogeneous batch (Sec. 2.2).  Each problem runs on its own
+ * internal stream, ordered after opts->stream, so the shapes' launches overlap
+ * on the device; iterations advance round-robin, opts->check_every per
+ * problem per round, until every map of every problem has stopped.
+ * ps: HOST array of np problems; s_out: HOST array of np device outputs
+ * (each [count][C][n][n/2+1] in its problem's working type); stats: HOST array
+ * of np HOST arrays (each of its problem's count) or NULL.  Starts from 0.
+ * Returns the worst status over all maps; synchronises. */
+wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_opts* opts, void* const* s_out,
+                            wf_solve_stats* const* stats);
+
 /* Data synthesis for simulations (Sec. 2.5, steps 1-2; eq. blmv):
  * d_b = mask * (A z_b + noise_b), z and noise device [count][C][n][n] of the
  * working type (z white N(0,1), noise with variance 1/Ninv), d_out the same

@@ -618,3 +618,63 @@ extern "C" wf_status wf_map_solve(wf_problem* p, const wf_opts* opts, const void
   }
   return wf_solver_finish(p, s_out, x_out, stats);
 }
+
+// Several problems (typically one per map shape of a heterogeneous batch),
+// each solved on its own stream so that their launches overlap on the device;
+// iterations advance round-robin, check_every per problem per round.
+extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_opts* opts, void* const* s_out,
+                                       wf_solve_stats* const* stats) {
+  if (!ps || np < 1 || !s_out) return wf_fail(WF_EINVAL, "wf_map_solve_many: null or empty arguments");
+  for (int i = 0; i < np; ++i)
+    if (!ps[i] || !s_out[i]) return wf_fail(WF_EINVAL, "wf_map_solve_many: problem %d or its output is null", i);
+  wf_opts o;
+  if (opts) o = *opts;
+  else wf_opts_default(&o);
+  cudaStream_t us = (cudaStream_t)o.stream;
+  cudaEvent_t ready;
+  cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (e != cudaSuccess) return wf_cuda_fail(e, "wf_map_solve_many: event");
+  e = cudaEventRecord(ready, us);
+  wf_opts oi = o;
+  oi.stream = nullptr;  // every problem on its own internal stream
+  wf_status rs = WF_OK;
+  for (int i = 0; i < np && rs == WF_OK && e == cudaSuccess; ++i) {
+    rs = check_opts(ps[i], &oi);
+    if (rs != WF_OK) break;
+    rs = ensure_solver(ps[i], oi.lbfgs_m);
+    if (rs != WF_OK) break;
+    e = cudaStreamWaitEvent(ps[i]->solver->stream, ready, 0);
+    if (e == cudaSuccess)
+      rs = ps[i]->precision == WF_FP64 ? start_impl<double>(ps[i], &oi, nullptr) : start_impl<float>(ps[i], &oi, nullptr);
+  }
+  cudaEventDestroy(ready);
+  if (e != cudaSuccess) return wf_cuda_fail(e, "wf_map_solve_many: ordering");
+  if (rs != WF_OK) return rs;
+  const int chunk = o.check_every > 0 ? o.check_every : 16;
+  int* live = (int*)calloc((size_t)np, sizeof(int));
+  if (!live) return wf_fail(WF_ENOMEM, "wf_map_solve_many: host allocation");
+  for (int i = 0; i < np; ++i) live[i] = 1;
+  const long long max_rounds = (long long)o.max_iter / chunk + 2;
+  for (long long r = 0; r < max_rounds && rs == WF_OK; ++r) {
+    int any = 0;
+    for (int i = 0; i < np && rs == WF_OK; ++i)
+      if (live[i]) rs = wf_solver_step(ps[i], chunk, nullptr);
+    for (int i = 0; i < np && rs == WF_OK; ++i)
+      if (live[i]) {
+        int na = 0;
+        rs = wf_solver_step(ps[i], 0, &na);
+        live[i] = na > 0;
+        any |= live[i];
+      }
+    if (!any) break;
+  }
+  free(live);
+  if (rs != WF_OK) return rs;
+  wf_status worst = WF_OK;
+  for (int i = 0; i < np; ++i) {
+    const wf_status si = wf_solver_finish(ps[i], s_out[i], nullptr, stats ? stats[i] : nullptr);
+    if (si != WF_OK && (worst == WF_OK || worst == WF_ENOTCONVERGED)) worst = si;
+  }
+  if (us) cudaStreamSynchronize(us);
+  return worst;
+}

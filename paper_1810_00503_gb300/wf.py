@@ -23,7 +23,8 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_problem_destroy", "wf_problem_set_data", "wf_eval", "wf_hess_vec",
            "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy",
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
-           "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands"]
+           "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
+           "wf_map_solve_many"]
 
 
 class WfMap(ctypes.Structure):
@@ -93,6 +94,8 @@ def lib() -> ctypes.CDLL:
     L.wf_eval_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, vp]
     L.wf_problem_set_band_scale.argtypes = [vp, vp, vp, i, vp]
     L.wf_eval_bands.argtypes = [vp, vp, vp, vp, vp, i, vp, vp]
+    L.wf_map_solve_many.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(WfOpts), ctypes.POINTER(vp),
+                                    ctypes.POINTER(ctypes.POINTER(WfSolveStats))]
     L.bandpower_estimate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
                                      ctypes.POINTER(WfOpts), ctypes.POINTER(WfBandpowerOut),
                                      ctypes.POINTER(WfSolveStats)]
@@ -173,6 +176,28 @@ def eval_noalloc(s, d, w, P, chi2=None, grad=None, stream=None):
     _check(lib().wf_eval_noalloc(_ptr(s), _ptr(d), _ptr(w), _ptr(P), n, C, B, precision, _ptr(chi2),
                                  _ptr(grad), _stream(stream)))
     return chi2, grad
+
+
+def solve_many(problems, stream=None, **opts):
+    """wf_map_solve_many: solve several problems (one per map shape) at once.
+    Returns one SolveResult per problem."""
+    import torch
+    o = WfOpts()
+    lib().wf_opts_default(ctypes.byref(o))
+    for k, v in opts.items():
+        setattr(o, k, v)
+    o.stream = _stream(stream)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    outs = [torch.empty(p.spec_shape(), dtype=p._cplx(), device=dev) for p in problems]
+    sts = [(WfSolveStats * p.B)() for p in problems]
+    np_ = len(problems)
+    parr = (ctypes.c_void_p * np_)(*[p._p.value for p in problems])
+    oarr = (ctypes.c_void_p * np_)(*[_ptr(t) for t in outs])
+    sarr = (ctypes.POINTER(WfSolveStats) * np_)(*[ctypes.cast(st, ctypes.POINTER(WfSolveStats)) for st in sts])
+    status = lib().wf_map_solve_many(parr, np_, ctypes.byref(o), oarr, sarr)
+    if status not in (0, 5):
+        _check(status)
+    return [SolveResult(s=t, x=None, stats=Problem._stats(st)) for t, st in zip(outs, sts)]
 
 
 def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",

@@ -114,3 +114,23 @@ def test_graphs_and_plain_launches_agree():
     b = prob.solve(gtol_rel=1e-10, max_iter=2000, use_graphs=0, check_every=8)
     assert a.stats[0]["iters"] == b.stats[0]["iters"]
     assert rel(a.s[0].cpu().numpy(), b.s[0].cpu().numpy()) <= 1e-13
+
+
+def test_heterogeneous_batch_solved_together():
+    # maps of uneven size (one problem per shape), solved concurrently; each map
+    # agrees with the oracle's own L-BFGS minimiser.
+    from paper_1810_00503_gb300 import wf
+    maps = synth.hetero_batch(count=9, seed=4, sizes=(64, 128, 256))
+    groups = {}
+    for m in maps:
+        groups.setdefault(m.n, []).append(m)
+    probs, hosts, order = [], [], []
+    for n in sorted(groups):
+        pr, ho = make_problem(groups[n], "fp64", shared_P=False)
+        probs.append(pr); hosts.append(ho); order.append(n)
+    res = wf.solve_many(probs, gtol_rel=1e-11, max_iter=20000)
+    for r, ho, n in zip(res, hosts, order):
+        assert all(s["status"] == "WF_OK" for s in r.stats), r.stats
+        b = 0
+        zs, info = O.map_solve(ho["d"][b], ho["W"][b], ho["P"][b], gtol_rel=1e-12, max_iter=20000)
+        assert rel(r.s[b].cpu().numpy(), rfft_u(zs)) <= 1e-9, n
