@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bandpower", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     return ap.parse_args()
 
 
@@ -227,7 +228,9 @@ def run_e2e(args, dev, host, iters):
         dt = time.perf_counter() - t0
         prob.close()
         times.append(dt)
-        evals.append(sum(s["evals"] for s in res.stats))
+        # one operator pass per map per L-BFGS iteration, as in the device-timed value
+        # (the start-up gradient and the final chi^2 pass are not counted)
+        evals.append(sum(s["iters"] for s in res.stats))
     dt = min(times)
     ev = evals[times.index(dt)]
     return {"value": ev / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / iters, "d2h_bytes_per_step": d2h / iters,
@@ -272,6 +275,59 @@ def run_bandpower(args, dev, n_sim=100, n_bands=20, n_fd=1):
             "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
             "statuses": sorted(set(st["status"] for st in stats)),
             "theta_hat_over_fid_median": float(np.median(res["theta_hat"] / res["theta_fid"]))}
+
+
+def run_fp64_reference(args, dev, gtol=1e-6):
+    """The plain single-map FP64 GPU path on map 0 of the workload: iteration
+    throughput, and one solve to ||g|| / ||g0|| < gtol compared with the mixed
+    batched path's solution of the same map to the same tolerance."""
+    import numpy as np
+    import torch
+    from paper_1810_00503_gb300 import synth, wf
+    n = args.n
+    inp = synth.cmb_patch(n, seed=3)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1000)
+    Ninv64 = torch.as_tensor(inp.Ninv, dtype=torch.float64, device=dev)
+    mask = torch.as_tensor(inp.mask, dtype=torch.uint8, device=dev)
+    P64 = torch.as_tensor(inp.P_half, dtype=torch.float64, device=dev)
+    sig = torch.where(Ninv64 > 0, torch.rsqrt(torch.clamp(Ninv64, min=1e-30)), torch.zeros_like(Ninv64))
+    z = torch.randn(1, 1, n, n, generator=g, device=dev, dtype=torch.float64)
+    nz = torch.randn(1, 1, n, n, generator=g, device=dev, dtype=torch.float64) * sig
+    p64 = wf.Problem(torch.zeros_like(Ninv64)[None], mask, Ninv64[None], P64, precision="fp64", lbfgs_m=args.m)
+    d64 = p64.simulate(z, nz)
+    p64.set_data(d64)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        p64.start(gtol_rel=0.0, max_iter=1 << 30, check_every=1)
+        p64.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p64.step(args.steps, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        it_ms = e0.elapsed_time(e1) / args.steps
+        p64.finish()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r64 = p64.solve(gtol_rel=gtol, max_iter=50000, check_every=64)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    p32 = wf.Problem(d64.float(), mask, Ninv64.float()[None], P64.float(), precision="mixed", lbfgs_m=args.m)
+    t0 = time.perf_counter()
+    r32 = p32.solve(gtol_rel=gtol, max_iter=50000, check_every=64, refresh_every=200)
+    torch.cuda.synchronize()
+    t32 = time.perf_counter() - t0
+    a = r64.s[0].cpu().numpy()
+    b = r32.s[0].cpu().numpy().astype(np.complex128)
+    err = float(np.linalg.norm(a - b) / np.linalg.norm(a))
+    p64.close()
+    p32.close()
+    return {"fp64_single_map_evals_per_s": 1000.0 / it_ms, "fp64_single_map_ms_per_iteration": it_ms,
+            "fp64_single_map_solve_s": t64, "fp64_iterations": r64.stats[0]["iters"],
+            "mixed_single_map_solve_s": t32, "mixed_iterations": r32.stats[0]["iters"],
+            "gtol_rel": gtol, "mixed_vs_fp64_rel_l2": err,
+            "note": "map 0 of the workload; the batched mixed path's per-map cost is ms_per_step / maps"}
 
 
 # ---------------------------------------------------------------------------
@@ -414,6 +470,8 @@ def main():
         r["prob"].close()
         if not args.no_bandpower:
             line["bandpower"] = run_bandpower(args, dev)
+        if not args.no_fp64:
+            line["fp64_reference"] = run_fp64_reference(args, dev)
         if not args.no_e2e:
             line["e2e"] = run_e2e(args, dev, r["host"], iters=max(K, 10))
         if not args.no_cpu:

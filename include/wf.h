@@ -236,7 +236,9 @@ wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
 typedef struct {
   int n_bands;            /* bands, ids 0 .. n_bands-1 (1..64) */
   int n_sim;              /* noise-bias simulations (>= 2) */
-  int n_fd;               /* Fisher simulations per band, 1..n_sim; the j-th reuses simulation j */
+  int n_fd;               /* Fisher simulations per band, 0..n_sim; the j-th reuses simulation j.
+                             0 (a rank of a multi-GPU run that owns no Fisher map) leaves
+                             fisher, cov and theta_hat as NaN */
   int pad_;
   const int16_t* band;    /* [C][n][n/2+1] band id of each half-plane mode, -1 = none */
   const void* z;          /* [n_sim][C][n][n] white signal fields, N(0, 1) */
@@ -253,6 +255,9 @@ typedef struct {
   double* cov;            /* [n_bands * n_bands] F^-1 (eq. var) */
   double* theta_hat;      /* [n_bands] Theta_fid + F^-1 (E - b) (eq. eq:wfmv) */
   double* cov_E;          /* [n_bands * n_bands] sample covariance of E over the simulations */
+  double* E_maps;         /* optional (NULL = not written): [1 + n_sim + n_bands * n_fd][n_bands]
+                             E of every solved map (data, simulations, Fisher maps), for callers
+                             that combine simulations from several GPUs */
 } wf_bandpower_out;
 
 /* Band powers, noise bias, Fisher matrix and covariance from simulations, for

@@ -75,7 +75,7 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
     double s = 0.0;
     for (int j = 0; j < nfd; ++j)
       s += Eall[(size_t)(1 + J + lp * nfd + j) * nb + l] - Eall[(size_t)(1 + j) * nb + l];
-    o_F[idx] = s / nfd / theta[lp];
+    o_F[idx] = nfd > 0 ? s / nfd / theta[lp] : 0.0;
     double c = 0.0;
     for (int j = 0; j < J; ++j)
       c += (Eall[(size_t)(1 + j) * nb + l] - o_b[l]) * (Eall[(size_t)(1 + j) * nb + lp] - o_b[lp]);
@@ -163,8 +163,8 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   const int nb = in->n_bands, J = in->n_sim, nfd = in->n_fd;
   if (nb < 1 || nb > 64) return wf_fail(WF_EINVAL, "bandpower_estimate: n_bands = %d outside [1, 64]", nb);
   if (J < 2) return wf_fail(WF_EINVAL, "bandpower_estimate: n_sim = %d (need >= 2)", J);
-  if (nfd < 1 || nfd > J) return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd = %d outside [1, n_sim]", nfd);
-  if (!in->band || !in->z || !in->noise || !in->u)
+  if (nfd < 0 || nfd > J) return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd = %d outside [0, n_sim]", nfd);
+  if (!in->band || !in->z || !in->noise || (nfd > 0 && !in->u))
     return wf_fail(WF_EINVAL, "bandpower_estimate: null band table or random fields");
   if (!out->theta_fid || !out->E || !out->bias || !out->fisher || !out->cov || !out->theta_hat || !out->cov_E)
     return wf_fail(WF_EINVAL, "bandpower_estimate: null output array");
@@ -221,25 +221,27 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   // signal and the simulation's data as "noise" (M d_j = d_j)
   for (int l = 0; l < nb; ++l)
     for (int j = 0; j < nfd; ++j) maps[l * nfd + j].P = (const char*)Pl + (size_t)l * nsp * delt;
-  wf_problem* pfd = nullptr;
-  rs = wf_problem_create(h, maps, nF, n, C, dtype, precision, 1, (void*)st, &pfd);
-  if (rs != WF_OK) { free(maps); return rs; }
-  sc.addp(pfd);
-  void* nfd_in = nullptr;
   void* dfd = nullptr;
-  rs = wf_alloc(&nfd_in, npix * nF * welt, "Fisher base data");
-  if (rs == WF_OK) { sc.add(nfd_in); rs = wf_alloc(&dfd, npix * nF * welt, "Fisher data"); }
-  if (rs != WF_OK) { free(maps); return rs; }
-  sc.add(dfd);
-  for (int l = 0; l < nb; ++l)
-    for (int j = 0; j < nfd; ++j) {
-      cudaError_t e = cudaMemcpyAsync((char*)nfd_in + (size_t)(l * nfd + j) * npix * welt,
-                                      (const char*)dsim + (size_t)j * npix * welt, npix * welt,
-                                      cudaMemcpyDeviceToDevice, st);
-      if (e != cudaSuccess) { free(maps); return wf_cuda_fail(e, "bandpower_estimate: Fisher base copy"); }
-    }
-  rs = wf_simulate_data(pfd, in->u, nfd_in, dfd, st);
-  if (rs != WF_OK) { free(maps); return rs; }
+  if (nF > 0) {
+    wf_problem* pfd = nullptr;
+    rs = wf_problem_create(h, maps, nF, n, C, dtype, precision, 1, (void*)st, &pfd);
+    if (rs != WF_OK) { free(maps); return rs; }
+    sc.addp(pfd);
+    void* nfd_in = nullptr;
+    rs = wf_alloc(&nfd_in, npix * nF * welt, "Fisher base data");
+    if (rs == WF_OK) { sc.add(nfd_in); rs = wf_alloc(&dfd, npix * nF * welt, "Fisher data"); }
+    if (rs != WF_OK) { free(maps); return rs; }
+    sc.add(dfd);
+    for (int l = 0; l < nb; ++l)
+      for (int j = 0; j < nfd; ++j) {
+        cudaError_t e = cudaMemcpyAsync((char*)nfd_in + (size_t)(l * nfd + j) * npix * welt,
+                                        (const char*)dsim + (size_t)j * npix * welt, npix * welt,
+                                        cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { free(maps); return wf_cuda_fail(e, "bandpower_estimate: Fisher base copy"); }
+      }
+    rs = wf_simulate_data(pfd, in->u, nfd_in, dfd, st);
+    if (rs != WF_OK) { free(maps); return rs; }
+  }
 
   // one batched MAP solve: data, simulations, Fisher maps
   for (int i = 0; i < Btot; ++i) maps[i].P = data->P;
@@ -250,8 +252,9 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (rs != WF_OK) return rs;
   sc.addp(ps);
   BP_TRY(cudaMemcpyAsync((char*)ps->d + npix * welt, dsim, npix * J * welt, cudaMemcpyDeviceToDevice, st));
-  BP_TRY(cudaMemcpyAsync((char*)ps->d + (size_t)(1 + J) * npix * welt, dfd, npix * nF * welt,
-                         cudaMemcpyDeviceToDevice, st));
+  if (nF > 0)
+    BP_TRY(cudaMemcpyAsync((char*)ps->d + (size_t)(1 + J) * npix * welt, dfd, npix * nF * welt,
+                           cudaMemcpyDeviceToDevice, st));
   void* sall = nullptr;
   BP_OK(wf_alloc(&sall, nsp * Btot * 2 * welt, "MAP spectra"));
   sc.add(sall);
@@ -294,6 +297,15 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   memcpy(out->theta_hat, hout + 3 * nb + 2 * nb2, sizeof(double) * nb);
   memcpy(out->cov_E, hout + 4 * nb + 2 * nb2, sizeof(double) * nb2);
   free(hout);
+  if (out->E_maps) {
+    e = cudaMemcpy(out->E_maps, Eall, sizeof(double) * (size_t)Btot * nb, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return wf_cuda_fail(e, "bandpower_estimate: reading E_maps");
+  }
+  if (nfd == 0) {  // no Fisher maps on this call: F, F^-1 and Theta_hat are undefined
+    for (size_t i = 0; i < nb2; ++i) out->fisher[i] = out->cov[i] = NAN;
+    for (int l = 0; l < nb; ++l) out->theta_hat[l] = NAN;
+    return solve_status;
+  }
   if (hflag) return wf_fail(WF_ENONFINITE, "bandpower_estimate: the Fisher matrix is singular");
   return solve_status;
 }

@@ -1,0 +1,75 @@
+"""Band powers from simulations spread over several GPUs (one process each).
+
+Each rank solves its own contiguous range of noise-bias simulations, and the
+Fisher simulations that reuse them, with bandpower_estimate on its GPU.  The
+ranks then combine (3 n_b + n_b^2) FP64 sums in one all-reduce (Sec. 2.5,
+eq. blmv, fisher, eq:wfmv):
+    b      = sum_j E_j / J
+    F_ll'  = sum_j (E_l(d_l'j) - E_l(d_j)) / J_fd / Theta_fid,l'
+    cov_E  = (sum_j E_j E_j^T - J b b^T) / (J - 1)
+    Theta  = Theta_fid + F^-1 (E - b)
+No data path crosses GPUs; only these sums do.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def shard(n_total: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous [start, stop) range of simulation indices owned by `rank`."""
+    base, extra = divmod(n_total, world)
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
+
+
+def assignment(n_sim: int, n_fd: int, world: int, rank: int):
+    """Simulations owned by `rank`, in the local order bandpower_estimate needs:
+    the Fisher simulation j reuses simulation j, so the simulations paired with
+    Fisher maps (global 0 .. n_fd-1) are split evenly and listed first, then the
+    rank's share of the others.  Returns (global simulation indices, (fd_lo, fd_hi))."""
+    fd_lo, fd_hi = shard(n_fd, world, rank)
+    o_lo, o_hi = shard(n_sim - n_fd, world, rank)
+    sims = list(range(fd_lo, fd_hi)) + list(range(n_fd + o_lo, n_fd + o_hi))
+    return sims, (fd_lo, fd_hi)
+
+
+def local_sums(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int) -> np.ndarray:
+    """Partial sums of one rank from its per-map band energies, rows ordered as
+    bandpower_estimate writes them: data, n_sim simulations, then n_bands x n_fd
+    Fisher maps (the j-th reusing simulation j).  Returns one FP64 vector:
+    [J, J_fd, sum E_j (nb), sum E_j E_j^T (nb^2), sum_j (E(d_l'j) - E(d_j)) (nb^2, [l][l'])]."""
+    nb = n_bands
+    Es = E_maps[1:1 + n_sim]
+    Ef = E_maps[1 + n_sim:].reshape(nb, n_fd, nb)  # [l'][j][l]
+    diff = (Ef - Es[None, :n_fd, :]).sum(axis=1)      # [l'][l]
+    return np.concatenate([[float(n_sim), float(n_fd)], Es.sum(axis=0), (Es.T @ Es).ravel(), diff.T.ravel()])
+
+
+def combine(total: np.ndarray, E_data: np.ndarray, theta_fid: np.ndarray) -> dict:
+    """Band-power estimate from the all-reduced sums of `local_sums`."""
+    nb = theta_fid.size
+    J, Jfd = total[0], total[1]
+    S1 = total[2:2 + nb]
+    S2 = total[2 + nb:2 + nb + nb * nb].reshape(nb, nb)
+    D = total[2 + nb + nb * nb:].reshape(nb, nb)
+    b = S1 / J
+    F = D / Jfd / theta_fid[None, :]
+    covE = (S2 - J * np.outer(b, b)) / (J - 1)
+    cov = np.linalg.inv(F)
+    return dict(bias=b, fisher=F, cov=cov, cov_E=covE, theta_hat=theta_fid + cov @ (E_data - b),
+                theta_fid=theta_fid, E=E_data)
+
+
+def reduce_bandpower(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int, theta_fid: np.ndarray,
+                     group=None) -> dict:
+    """All-reduce the rank's partial sums (torch.distributed, any backend) and
+    combine them.  E_maps: this rank's per-map energies; the data map's row 0
+    is taken from rank 0."""
+    import torch
+    import torch.distributed as dist
+    part = torch.as_tensor(local_sums(E_maps, n_sim, n_bands, n_fd), dtype=torch.float64)
+    e0 = torch.as_tensor(E_maps[0], dtype=torch.float64).clone()
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(part, group=group)
+        dist.broadcast(e0, src=0, group=group)
+    return combine(part.numpy(), e0.numpy(), np.asarray(theta_fid, dtype=np.float64))

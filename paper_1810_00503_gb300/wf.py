@@ -52,7 +52,7 @@ class WfBandpowerIn(ctypes.Structure):
 
 class WfBandpowerOut(ctypes.Structure):
     _fields_ = [(k, ctypes.POINTER(ctypes.c_double)) for k in
-                ("theta_fid", "E", "bias", "fisher", "cov", "theta_hat", "cov_E")]
+                ("theta_fid", "E", "bias", "fisher", "cov", "theta_hat", "cov_E", "E_maps")]
 
 
 class WfError(RuntimeError):
@@ -214,8 +214,10 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
     nb = int(n_bands)
     bi = WfBandpowerIn(n_bands=nb, n_sim=int(z.shape[0]), n_fd=int(u.shape[1]), pad_=0,
                        band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u))
+    nmaps = 1 + int(z.shape[0]) + nb * int(u.shape[1])
     arrs = {k: np.zeros(sz) for k, sz in (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb),
-                                          ("cov", nb * nb), ("theta_hat", nb), ("cov_E", nb * nb))}
+                                          ("cov", nb * nb), ("theta_hat", nb), ("cov_E", nb * nb),
+                                          ("E_maps", nmaps * nb))}
     bo = WfBandpowerOut(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in arrs.items()})
     o = WfOpts()
     lib().wf_opts_default(ctypes.byref(o))
@@ -232,6 +234,7 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
         _check(status)
     for k in ("fisher", "cov", "cov_E"):
         arrs[k] = arrs[k].reshape(nb, nb)
+    arrs["E_maps"] = arrs["E_maps"].reshape(nmaps, nb)
     return arrs, Problem._stats(st)
 
 

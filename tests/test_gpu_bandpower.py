@@ -74,3 +74,37 @@ def test_bandpower_rejects_bad_counts():
                               torch.ones((1, n, n // 2 + 1), dtype=dt, device="cuda"),
                               torch.zeros((1, n, n // 2 + 1), dtype=torch.int16, device="cuda"), 2,
                               z, z, torch.zeros((2, 1, 1, n, n), dtype=dt, device="cuda"))
+
+
+def test_sharded_calls_reduce_to_the_single_call():
+    """The multi-GPU split run as two sequential shards on one GPU: shard 0 owns
+    every Fisher map, shard 1 none (n_fd = 0); their summed partial sums give
+    the single call's estimate (the maps are solved independently)."""
+    from paper_1810_00503_gb300 import dist as D
+    n, nb, J, nfd, seed = 16, 3, 8, 4, 31
+    inp = synth.density_small(n, seed=seed, masked_frac=0.25)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb)
+    rng = np.random.default_rng(seed + 100)
+    sig = np.where(inp.Ninv > 0, 1.0 / np.sqrt(np.where(inp.Ninv > 0, inp.Ninv, 1.0)), 0.0)
+    z = rng.standard_normal((J, 1, n, n))
+    nz = rng.standard_normal((J, 1, n, n)) * sig
+    u = rng.standard_normal((nb, nfd, 1, n, n))
+    dt = torch.float64
+    common = (to_dev(d, dt), to_dev(inp.mask, torch.uint8), to_dev(inp.Ninv, dt), to_dev(inp.P[..., : n // 2 + 1], dt),
+              to_dev(bands[..., : n // 2 + 1], torch.int16), nb)
+    kw = dict(precision="fp64", gtol_rel=1e-12, max_iter=20000, refresh_every=0)
+    full, _ = wf.bandpower_estimate(*common, to_dev(z, dt), to_dev(nz, dt), to_dev(u, dt), **kw)
+    total = np.zeros(2 + nb + 2 * nb * nb)
+    for sims, (lo, hi) in ((list(range(0, 5)), (0, 4)), (list(range(5, 8)), (4, 4))):
+        res, stats = wf.bandpower_estimate(*common, to_dev(z[sims], dt), to_dev(nz[sims], dt),
+                                           to_dev(u[:, lo:hi], dt), **kw)
+        assert all(s["status"] == "WF_OK" for s in stats)
+        assert np.allclose(res["E_maps"][0], full["E"], rtol=1e-9)
+        if hi == lo:
+            assert np.isnan(res["theta_hat"]).all() and np.isnan(res["fisher"]).all()
+        total += D.local_sums(res["E_maps"], len(sims), nb, hi - lo)
+    red = D.combine(total, full["E"], full["theta_fid"])
+    for k in ("bias", "fisher", "cov_E", "theta_hat", "cov"):
+        assert _close(red[k], full[k], 1e-9), (k, red[k], full[k])
+    assert np.allclose(full["E_maps"][1:1 + J].mean(axis=0), full["bias"], rtol=1e-12)

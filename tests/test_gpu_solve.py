@@ -134,3 +134,45 @@ def test_heterogeneous_batch_solved_together():
         b = 0
         zs, info = O.map_solve(ho["d"][b], ho["W"][b], ho["P"][b], gtol_rel=1e-12, max_iter=20000)
         assert rel(r.s[b].cpu().numpy(), rfft_u(zs)) <= 1e-9, n
+
+
+@pytest.mark.parametrize("case", ["all_masked", "zero_data", "zero_power"])
+def test_degenerate_problems(case):
+    # Degenerate cases of the method: with no observed pixel, no data or no
+    # signal power the MAP field is 0 and the solver stops at once.
+    n = 32
+    inp = synth.density_small(n, seed=2)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    if case == "all_masked":
+        inp.mask[:] = 0
+        inp.Ninv[:] = 0.0
+        d = d * 0.0
+    elif case == "zero_data":
+        d = d * 0.0
+    else:
+        inp.P[:] = 0.0
+    prob, host = make_problem([inp], "fp64", d_list=[d])
+    res = prob.solve(gtol_rel=1e-10, max_iter=100)
+    assert res.stats[0]["status"] == "WF_OK"
+    assert res.stats[0]["iters"] == 0
+    assert np.abs(res.s[0].cpu().numpy()).max() == 0.0
+
+
+def test_mixed_cmb_256_within_1e4():
+    # CMB-like red spectrum (the paper's hardest conditioning) in FP32 fields with
+    # FP64 reductions and periodic true-gradient refresh.
+    inp = synth.cmb_patch(256, seed=3)
+    prob, host = make_problem([inp], "mixed")
+    res = prob.solve(gtol_rel=1e-7, max_iter=20000, refresh_every=100)
+    zs, info = O.map_solve(host["d"][0], host["W"][0], host["P"][0], gtol_rel=1e-11, max_iter=20000)
+    err = rel(res.s[0].cpu().numpy(), rfft_u(zs))
+    assert err <= 1e-4, (err, res.stats)
+
+
+def test_mixed_shear_eb_256_within_1e4():
+    inp = synth.shear_eb(256, seed=2)
+    prob, host = make_problem([inp], "mixed")
+    res = prob.solve(gtol_rel=1e-7, max_iter=20000, refresh_every=100)
+    zs, info = O.map_solve(host["d"][0], host["W"][0], host["P"][0], gtol_rel=1e-11, max_iter=20000)
+    err = rel(res.s[0].cpu().numpy(), rfft_u(zs))
+    assert err <= 1e-4, (err, res.stats)
