@@ -57,6 +57,7 @@ WfGeo wf_make_geo(int n, int C) {
   g.nrb = C * n / rb;
   const long long vsz = (long long)C * n * (n / 2);
   g.ncomb = (int)((vsz + WF_COMB_CHUNK - 1) / WF_COMB_CHUNK);
+  g.ncomb = (g.ncomb + WF_STREAM_GROUP - 1) / WF_STREAM_GROUP;
   g.maxblk = g.ntile > g.nrb ? g.ntile : g.nrb;
   if (g.ncomb > g.maxblk) g.maxblk = g.ncomb;
   return g;

@@ -22,6 +22,21 @@
 #define WF_COMB_THREADS 256
 #define WF_COMB_EPT 4
 #define WF_COMB_CHUNK (WF_COMB_THREADS * WF_COMB_EPT)
+// Chunks a streaming block walks in turn; one partial-sum entry per group.
+#ifndef WF_STREAM_GROUP
+#define WF_STREAM_GROUP 4
+#endif
+// FFT stages of the L-BFGS iteration on ping-pong passes with direct global
+// input/output (1) or on in-place shared-memory passes (0).
+#ifndef WF_FFT_PP
+#define WF_FFT_PP 1
+#endif
+#ifndef WF_COLFWD_PP
+#define WF_COLFWD_PP WF_FFT_PP
+#endif
+#ifndef WF_COLFWD_PF
+#define WF_COLFWD_PF 1
+#endif
 
 // Resident blocks per SM requested from the compiler for the FFT-stage kernels.
 // FP32: three blocks of 256 threads (85 registers a thread; the radix-16 passes
@@ -76,7 +91,7 @@ struct WfGeo {
   int n, h, lgn, lgh, C;
   int TC, ntile;   // packed columns per column tile, tiles per map
   int RB, nrb;     // rows per row block (over the C*n rows), row blocks per map
-  int ncomb;       // blocks per map of the streaming L-BFGS kernels
+  int ncomb;       // partial sums per map and slot of the streaming L-BFGS kernels
   int maxblk;      // max(ntile, nrb, ncomb): stride of the partial-sum slots
 };
 

@@ -17,6 +17,7 @@
 // full-plane real inner product.
 #pragma once
 #include "wf_ops.cuh"
+#include "wf_stage_pp.cuh"
 
 
 // Stage per-warp partial dot products: red[slot * NW + warp] (NW = warps of the block).
@@ -118,8 +119,9 @@ constexpr size_t wf_comb_smem(int m) {
 }
 
 // ---------------------------------------------------------------------------
-// k_lb_comb: grid (ncomb, B).  Block chunk = WF_COMB_CHUNK complex values of
-// the map's packed vectors (fewer for small maps).  Each thread owns
+// k_lb_comb: grid (ncomb, B).  A block walks WF_STREAM_GROUP consecutive
+// chunks of WF_COMB_CHUNK complex values of the map's packed vectors (fewer for
+// small maps), summing its partial dot products once at the end.  Each thread owns
 // WF_COMB_EPT complex values of the chunk; the stored vectors are read with
 // plain 16-byte loads, one pair (Q, P) per trip, newest first, at the
 // occupancy needed to keep HBM busy.  The pending update always belongs to the
@@ -134,7 +136,7 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   typedef typename WfVec<T>::type VT;
   constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW;
   extern __shared__ __align__(16) unsigned char wf_smem[];
-  float* pdot = (float*)wf_smem;  // [2m + 1][threads]
+  float* pdot = (float*)wf_smem;  // [2m + 1][threads], this thread's column only until the final sums
   __shared__ int ids[2 * WF_MAXM + 1];
   const int b = blockIdx.y, tid = threadIdx.x;
   const WfLbMap* M = lb.st + b;
@@ -147,98 +149,109 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   const bool full = (mode == WF_LB1_FULL);
   const size_t vsz = (size_t)g.C * g.n * g.h;  // complex values per map vector
   const int h = g.h, B = gridDim.y, m = lb.m;
-  const size_t c0 = (size_t)blockIdx.x * WF_COMB_CHUNK;
-  const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
-  VT* sv = (VT*)((V2<T>*)lb.s + (size_t)b * vsz + c0);
-  VT* gv = (VT*)((V2<T>*)lb.g + (size_t)b * vsz + c0);
   const V2<T>* ring = (const V2<T>*)lb.ring;
   const int np = (mode == WF_LB1_MATERIALIZE) ? 1 : M->npairs;
   const int head = (mode == WF_LB1_MATERIALIZE) ? M->pend_slot : M->head;
-  int u[NV];
-  bool ok[NV], col0[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const int c = (tid + i * WF_COMB_THREADS) * VW;
-    ok[i] = c < clen;
-    u[i] = c / VW;
-    col0[i] = ((c0 + c) % h) == 0;
+  const int nslot = 1 + 2 * np;
+  if (mode != WF_LB1_MATERIALIZE) {
+    for (int k = 0; k < nslot; ++k) pdot[k * WF_COMB_THREADS + tid] = 0.f;
+    if (tid == 0) {
+      ids[0] = WF_SLOT_GG;
+      for (int q = 0; q < np; ++q) {
+        const int sl = (head - q + m) % m;
+        ids[1 + 2 * q] = WF_SLOT_GQ + sl;
+        ids[2 + 2 * q] = WF_SLOT_GP + sl;
+      }
+    }
   }
-  auto wdot = [&](VT a, VT c, int i) -> float {
-    if constexpr (sizeof(T) == 4) {
-      const float d0 = a.x * c.x + a.y * c.y, d1 = a.z * c.z + a.w * c.w;
-      return (col0[i] ? d0 : 2.f * d0) + 2.f * d1;
-    } else {
-      const double d0 = a.x * c.x + a.y * c.y;
-      return (float)(col0[i] ? d0 : 2.0 * d0);
-    }
-  };
-  VT gr[NV], sr[NV], pr[NV];
+  const T dg = (T)M->dg;
+  for (int cg = 0; cg < WF_STREAM_GROUP; ++cg) {
+    const size_t c0 = ((size_t)blockIdx.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
+    if (c0 >= vsz) break;
+    const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
+    VT* sv = (VT*)((V2<T>*)lb.s + (size_t)b * vsz + c0);
+    VT* gv = (VT*)((V2<T>*)lb.g + (size_t)b * vsz + c0);
+    int u[NV];
+    bool ok[NV], col0[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i)
-    if (ok[i]) {
-      gr[i] = gv[u[i]];
-      if (mat) sr[i] = sv[u[i]];
-      if (full) pr[i] = wf_vscale<T>(gr[i], (T)0);
+    for (int i = 0; i < NV; ++i) {
+      const int c = (tid + i * WF_COMB_THREADS) * VW;
+      ok[i] = c < clen;
+      u[i] = c / VW;
+      col0[i] = ((c0 + c) % h) == 0;
     }
-  for (int q = 0; q < np; ++q) {
-    const int sl = (head - q + m) % m;
-    const VT* Pq = (const VT*)(ring + ((size_t)sl * B + b) * vsz + c0);
-    const VT* Qq = (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0);
-    VT xp[NV], xq[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) { xq[i] = Qq[u[i]]; xp[i] = Pq[u[i]]; }
-    if (mat && q == 0) {  // the newest pair carries the pending update
-#pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (ok[i]) {
-          gr[i] = wf_vaxpy<T>(gr[i], (T)pa, xq[i]);
-          sr[i] = wf_vaxpy<T>(sr[i], (T)pa, xp[i]);
-          gv[u[i]] = gr[i];
-          sv[u[i]] = sr[i];
-        }
-    }
-    if (mode == WF_LB1_MATERIALIZE) break;
-    const T cq = (T)M->dQ[sl], cp = (T)M->dP[sl];
-    float aq = 0.f, ap = 0.f;
+    auto wdot = [&](VT a, VT c, int i) -> float {
+      if constexpr (sizeof(T) == 4) {
+        const float d0 = a.x * c.x + a.y * c.y, d1 = a.z * c.z + a.w * c.w;
+        return (col0[i] ? d0 : 2.f * d0) + 2.f * d1;
+      } else {
+        const double d0 = a.x * c.x + a.y * c.y;
+        return (float)(col0[i] ? d0 : 2.0 * d0);
+      }
+    };
+    VT gr[NV], sr[NV], pr[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (ok[i]) {
-        aq += wdot(gr[i], xq[i], i);
-        ap += wdot(gr[i], xp[i], i);
-        if (full) pr[i] = wf_vaxpy<T>(wf_vaxpy<T>(pr[i], cq, xq[i]), cp, xp[i]);
+        gr[i] = gv[u[i]];
+        if (mat) sr[i] = sv[u[i]];
+        if (full) pr[i] = wf_vscale<T>(gr[i], (T)0);
       }
-    pdot[(1 + 2 * q) * WF_COMB_THREADS + tid] = aq;
-    pdot[(2 + 2 * q) * WF_COMB_THREADS + tid] = ap;
-    if (tid == 0) {
-      ids[1 + 2 * q] = WF_SLOT_GQ + sl;
-      ids[2 + 2 * q] = WF_SLOT_GP + sl;
+    for (int q = 0; q < np; ++q) {
+      const int sl = (head - q + m) % m;
+      const VT* Pq = (const VT*)(ring + ((size_t)sl * B + b) * vsz + c0);
+      const VT* Qq = (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0);
+      VT xp[NV], xq[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) { xq[i] = Qq[u[i]]; xp[i] = Pq[u[i]]; }
+      if (mat && q == 0) {  // the newest pair carries the pending update
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+          if (ok[i]) {
+            gr[i] = wf_vaxpy<T>(gr[i], (T)pa, xq[i]);
+            sr[i] = wf_vaxpy<T>(sr[i], (T)pa, xp[i]);
+            gv[u[i]] = gr[i];
+            sv[u[i]] = sr[i];
+          }
+      }
+      if (mode == WF_LB1_MATERIALIZE) break;
+      const T cq = (T)M->dQ[sl], cp = (T)M->dP[sl];
+      float aq = 0.f, ap = 0.f;
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) {
+          aq += wdot(gr[i], xq[i], i);
+          ap += wdot(gr[i], xp[i], i);
+          if (full) pr[i] = wf_vaxpy<T>(wf_vaxpy<T>(pr[i], cq, xq[i]), cp, xp[i]);
+        }
+      pdot[(1 + 2 * q) * WF_COMB_THREADS + tid] += aq;
+      pdot[(2 + 2 * q) * WF_COMB_THREADS + tid] += ap;
+    }
+    if (mode == WF_LB1_MATERIALIZE) continue;
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) {
+        acc += wdot(gr[i], gr[i], i);
+        if (full) pr[i] = wf_vaxpy<T>(pr[i], dg, gr[i]);
+      }
+    pdot[tid] += acc;
+    if (full) {
+      VT* Pn = (VT*)((V2<T>*)ring + ((size_t)M->next * B + b) * vsz + c0);
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) Pn[u[i]] = pr[i];
     }
   }
   if (mode == WF_LB1_MATERIALIZE) return;
-  float acc = 0.f;
-  const T dg = (T)M->dg;
-#pragma unroll
-  for (int i = 0; i < NV; ++i)
-    if (ok[i]) {
-      acc += wdot(gr[i], gr[i], i);
-      if (full) pr[i] = wf_vaxpy<T>(pr[i], dg, gr[i]);
-    }
-  pdot[tid] = acc;
-  if (tid == 0) ids[0] = WF_SLOT_GG;
-  if (full) {
-    VT* Pn = (VT*)((V2<T>*)ring + ((size_t)M->next * B + b) * vsz + c0);
-#pragma unroll
-    for (int i = 0; i < NV; ++i)
-      if (ok[i]) Pn[u[i]] = pr[i];
-  }
   __syncthreads();
-  wf_reduce_pdots(pdot, 1 + 2 * np, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_reduce_pdots(pdot, nslot, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
 }
 
 // ---------------------------------------------------------------------------
-// k_lb_qdots: grid (ncomb, B).  <q, Q_i> for the stored Q_i other than q, two
-// stored vectors per trip.
+// k_lb_qdots: grid (ncomb, B).  <q, Q_i> for the stored Q_i other than q, four
+// stored vectors per trip, over the same chunk groups as k_lb_comb.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? 4 : 2)
@@ -253,8 +266,6 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
   if (!M->active) return;
   const size_t vsz = (size_t)g.C * g.n * g.h;
   const int h = g.h, B = gridDim.y, m = lb.m;
-  const size_t c0 = (size_t)blockIdx.x * WF_COMB_CHUNK;
-  const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
   const V2<T>* ring = (const V2<T>*)lb.ring;
   const int nx = M->next, np = M->npairs, head = M->head;
   int sls[WF_MAXM];
@@ -263,49 +274,56 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
     const int sl = (head - q + m) % m;
     if (sl != nx) sls[nvec++] = sl;
   }
-  int u[NV];
-  bool ok[NV], col0[NV];
+  for (int v = 0; v < nvec; ++v) pdot[v * WF_COMB_THREADS + tid] = 0.f;
+  if (tid == 0)
+    for (int v = 0; v < nvec; ++v) ids[v] = WF_SLOT_QQI + sls[v];
+  auto qvec = [&](int sl, size_t c0) { return (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0); };
+  for (int cg = 0; cg < WF_STREAM_GROUP; ++cg) {
+    const size_t c0 = ((size_t)blockIdx.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
+    if (c0 >= vsz) break;
+    const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
+    int u[NV];
+    bool ok[NV], col0[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const int c = (tid + i * WF_COMB_THREADS) * VW;
-    ok[i] = c < clen;
-    u[i] = c / VW;
-    col0[i] = ((c0 + c) % h) == 0;
-  }
-  auto qvec = [&](int sl) { return (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0); };
-  auto wdot = [&](VT a, VT c, int i) -> float {
-    if constexpr (sizeof(T) == 4) {
-      const float d0 = a.x * c.x + a.y * c.y, d1 = a.z * c.z + a.w * c.w;
-      return (col0[i] ? d0 : 2.f * d0) + 2.f * d1;
-    } else {
-      const double d0 = a.x * c.x + a.y * c.y;
-      return (float)(col0[i] ? d0 : 2.0 * d0);
+    for (int i = 0; i < NV; ++i) {
+      const int c = (tid + i * WF_COMB_THREADS) * VW;
+      ok[i] = c < clen;
+      u[i] = c / VW;
+      col0[i] = ((c0 + c) % h) == 0;
     }
-  };
-  const VT* Qn = qvec(nx);
-  VT qr[NV];
+    auto wdot = [&](VT a, VT c, int i) -> float {
+      if constexpr (sizeof(T) == 4) {
+        const float d0 = a.x * c.x + a.y * c.y, d1 = a.z * c.z + a.w * c.w;
+        return (col0[i] ? d0 : 2.f * d0) + 2.f * d1;
+      } else {
+        const double d0 = a.x * c.x + a.y * c.y;
+        return (float)(col0[i] ? d0 : 2.0 * d0);
+      }
+    };
+    const VT* Qn = qvec(nx, c0);
+    VT qr[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i)
-    if (ok[i]) qr[i] = Qn[u[i]];
-  constexpr int U = 4;  // stored vectors per trip
-  for (int w = 0; w < nvec; w += U) {
-    VT x[U][NV];
+    for (int i = 0; i < NV; ++i)
+      if (ok[i]) qr[i] = Qn[u[i]];
+    constexpr int U = 4;  // stored vectors per trip
+    for (int w = 0; w < nvec; w += U) {
+      VT x[U][NV];
 #pragma unroll
-    for (int v = 0; v < U; ++v) {
-      const VT* Qv = qvec(sls[w + v < nvec ? w + v : w]);
+      for (int v = 0; v < U; ++v) {
+        const VT* Qv = qvec(sls[w + v < nvec ? w + v : w], c0);
 #pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (ok[i] && w + v < nvec) x[v][i] = Qv[u[i]];
-    }
+        for (int i = 0; i < NV; ++i)
+          if (ok[i] && w + v < nvec) x[v][i] = Qv[u[i]];
+      }
 #pragma unroll
-    for (int v = 0; v < U; ++v) {
-      if (w + v >= nvec) break;
-      float a = 0.f;
+      for (int v = 0; v < U; ++v) {
+        if (w + v >= nvec) break;
+        float a = 0.f;
 #pragma unroll
-      for (int i = 0; i < NV; ++i)
-        if (ok[i]) a += wdot(qr[i], x[v][i], i);
-      pdot[(w + v) * WF_COMB_THREADS + tid] = a;
-      if (tid == 0) ids[w + v] = WF_SLOT_QQI + sls[w + v];
+        for (int i = 0; i < NV; ++i)
+          if (ok[i]) a += wdot(qr[i], x[v][i], i);
+        pdot[(w + v) * WF_COMB_THREADS + tid] += a;
+      }
     }
   }
   __syncthreads();
@@ -323,7 +341,11 @@ k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const vo
   if (!M->active) return;
   const size_t vsz = (size_t)C * g.n * g.h;
   const V2<T>* p = (const V2<T>*)lb.ring + ((size_t)M->next * gridDim.y + b) * vsz;
+#if WF_FFT_PP
+  wf_col_inv_pp<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
+#else
   wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
+#endif
 }
 
 template <typename T, int C>
@@ -340,40 +362,69 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
   const int kx0 = blockIdx.x * TC, tot = C * n * TC;
   const size_t vsz = (size_t)C * n * h;
   const int B = gridDim.y, m = lb.m, nx = M->next;
-  wf_col_fwd_front<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, sp_ + (size_t)b * sp_stride, buf, s_tw,
-                         tw_);
   const V2<T>* Pn = (const V2<T>*)lb.ring + ((size_t)nx * B + b) * vsz;
   V2<T>* Qn = (V2<T>*)lb.ring + ((size_t)(m + nx) * B + b) * vsz;
   const V2<T>* gv = (const V2<T>*)lb.g + (size_t)b * vsz;
   typedef WfAcc<T> A;
   A qq = 0, pq = 0, pp = 0, gq = 0, gp = 0;
-  V2<T> pl[WF_EMAX], gl[WF_EMAX];
+#if WF_COLFWD_PP
+  (void)buf;
+  (void)s_tw;
+  // p and g of this tile are read after the transform: start their trip to L2 now
 #pragma unroll
-  for (int i = 0; i < WF_EMAX; ++i) {
+  for (int i = 0; i < (WF_COLFWD_PF ? WF_EMAX : 0); ++i) {
     const int e = threadIdx.x + i * WF_THREADS;
     if (e < tot) {
       const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
       const size_t off = ((size_t)c * n + j) * h + kx0 + t;
-      pl[i] = Pn[off];
-      gl[i] = gv[off];
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(Pn + off));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(gv + off));
     }
   }
+  const V2<T>* O = wf_col_fwd_pp<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, tw_);
+  const T* sp = sp_ + (size_t)b * sp_stride;
+  constexpr int EB = 4;  // elements per batch of loads
+#else
+  wf_col_fwd_front<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, sp_ + (size_t)b * sp_stride, buf, s_tw,
+                         tw_);
+  constexpr int EB = WF_EMAX;
+#endif
 #pragma unroll
-  for (int i = 0; i < WF_EMAX; ++i) {
-    const int e = threadIdx.x + i * WF_THREADS;
-    if (e < tot) {
-      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-      const int kx = kx0 + t;
-      const size_t off = ((size_t)c * n + j) * h + kx;
-      const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)], p = pl[i], gg = gl[i];
-      const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
-      Qn[off] = q;
-      const A wk = kx == 0 ? (A)1 : (A)2;
-      qq += wk * (A)(q.x * q.x + q.y * q.y);
-      pq += wk * (A)(p.x * q.x + p.y * q.y);
-      pp += wk * (A)(p.x * p.x + p.y * p.y);
-      gq += wk * (A)(gg.x * q.x + gg.y * q.y);
-      gp += wk * (A)(gg.x * p.x + gg.y * p.y);
+  for (int i0 = 0; i0 < WF_EMAX; i0 += EB) {
+    V2<T> pl[EB], gl[EB];
+#pragma unroll
+    for (int ii = 0; ii < EB; ++ii) {
+      const int e = threadIdx.x + (i0 + ii) * WF_THREADS;
+      if (e < tot) {
+        const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+        const size_t off = ((size_t)c * n + j) * h + kx0 + t;
+        pl[ii] = Pn[off];
+        gl[ii] = gv[off];
+      }
+    }
+#pragma unroll
+    for (int ii = 0; ii < EB; ++ii) {
+      const int e = threadIdx.x + (i0 + ii) * WF_THREADS;
+      if (e < tot) {
+        const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+        const int kx = kx0 + t;
+        const size_t off = ((size_t)c * n + j) * h + kx;
+#if WF_COLFWD_PP
+        auto lds = [&](int cc, int rr) { return O[wf_sw<T>(rr * CT + cc * TC + t)]; };
+        const V2<T> a = wf_mode_packed<T, C, true>(lds, j, c, kx, n, sp);
+#else
+        const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
+#endif
+        const V2<T> p = pl[ii], gg = gl[ii];
+        const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
+        Qn[off] = q;
+        const A wk = kx == 0 ? (A)1 : (A)2;
+        qq += wk * (A)(q.x * q.x + q.y * q.y);
+        pq += wk * (A)(p.x * q.x + p.y * q.y);
+        pp += wk * (A)(p.x * p.x + p.y * p.y);
+        gq += wk * (A)(gg.x * q.x + gg.y * q.y);
+        gp += wk * (A)(gg.x * p.x + gg.y * p.y);
+      }
     }
   }
   __shared__ double red[5 * (WF_THREADS / 32)];
@@ -395,5 +446,9 @@ template <typename T>
 __global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_lb_row(WfGeo g, void* scratch_, const void* w_, double* part, const void* tw_, const WfLbMap* st) {
   if (!st[blockIdx.y].active) return;
+#if WF_FFT_PP
+  wf_row_pp<T, WF_ROW_NODATA>(g, (V2<T>*)scratch_, nullptr, (const T*)w_, part, tw_);
+#else
   k_row_body<T, WF_ROW_NODATA>(g, scratch_, nullptr, w_, nullptr, nullptr, part, tw_);
+#endif
 }

@@ -18,8 +18,7 @@ template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes, int
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 32 && (*done_mask >> dev) & 1) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)((2 * WF_NT + WF_TILE) * sizeof(double2)));
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wf_pp_smem<double>());
   if (e == cudaSuccess && dev < 32) *done_mask |= 1 << dev;
   (void)bytes;
   return e;
@@ -112,7 +111,7 @@ template <typename T, int C>
 cudaError_t lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
   auto k = k_lb_colinv<T, C>;
-  const size_t sm = col_smem<T>(g);
+  const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb);
@@ -123,7 +122,7 @@ template <typename T, int C>
 cudaError_t lb_colfwd(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
   auto k = k_lb_colfwd<T, C>;
-  const size_t sm = col_smem<T>(g);
+  const size_t sm = WF_COLFWD_PP ? wf_pp_smem<T>() : col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb, b.part);
@@ -281,7 +280,7 @@ template <typename T>
 cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
   auto k = k_lb_row<T>;
-  const size_t sm = wfimpl::row_smem<T>(g);
+  const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : wfimpl::row_smem<T>(g);
   cudaError_t e = wfimpl::ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.nrb, b.B), WF_THREADS, sm, st>>>(g, b.scratch, b.w, b.part, b.tw, lb.st);

@@ -489,7 +489,9 @@ static wf_status finish_impl(wf_problem* p, void* s_out, void* x_out, wf_solve_s
   WF_TRY(cudaStreamSynchronize(st));
   S->started = 0;
   int worst = WF_OK;
-  auto rank = [](int s) { return s == WF_ENONFINITE ? 3 : s == WF_ELINESEARCH ? 2 : s == WF_ENOTCONVERGED ? 1 : 0; };
+  auto rank = [](int s) {
+    return s == WF_ETIMEOUT ? 4 : s == WF_ENONFINITE ? 3 : s == WF_ELINESEARCH ? 2 : s == WF_ENOTCONVERGED ? 1 : 0;
+  };
   for (int i = 0; i < p->count; ++i) {
     const double* r = S->stats_host + 5 * i;
     const int status = (int)r[2];

@@ -1,0 +1,175 @@
+// Operator stages on the ping-pong passes of wf_fft_pp.cuh (the same three
+// steps as the kernels of wf_ops.cuh; the first FFT pass reads global memory
+// with the per-mode operator or the real-FFT pre-step applied on the way in).
+//
+// Shared memory of every stage: the length-L pass table (WF_NT entries) and
+// two tiles A, B of WF_TILE values.
+#pragma once
+#include "wf_fft_pp.cuh"
+#include "wf_ops.cuh"
+
+template <typename T>
+__host__ __device__ constexpr size_t wf_pp_smem() {
+  return ((size_t)WF_NT + 2 * (size_t)WF_TILE) * sizeof(V2<T>);
+}
+
+// Packed value of column tile element (row j, channel c, column kx) after the
+// per-mode operator (R(k) sqrt(P)/n, or its adjoint), read through `ld(cc, row)`
+// (channel cc's packed value at row `row` of this column).  Column 0 is
+// unpacked with row n - j, the operator applied at kx = 0 and kx = n/2, and
+// packed again.
+template <typename T, int C, bool ADJ, class LD>
+__device__ __forceinline__ V2<T> wf_mode_packed(LD& ld, int j, int c, int kx, int n, const T* sp) {
+  V2<T> v[C];
+  if (kx != 0) {
+#pragma unroll
+    for (int cc = 0; cc < C; ++cc) v[cc] = ld(cc, j);
+    wf_mode_op<T, C, ADJ>(v, j, kx, n, sp, (T)1);
+    return v[c];
+  }
+  const int jm = (n - j) & (n - 1);
+  V2<T> X0[C], Xh[C];
+#pragma unroll
+  for (int cc = 0; cc < C; ++cc) wf_unpack0<T>(ld(cc, j), ld(cc, jm), X0[cc], Xh[cc]);
+  wf_mode_op<T, C, ADJ>(X0, j, 0, n, sp, (T)1);
+  wf_mode_op<T, C, ADJ>(Xh, j, n >> 1, n, sp, (T)1);
+  return wf_pack0<T>(X0[c], Xh[c]);
+}
+
+// Inverse column stage: spectrum (packed [C][n][h], or standard [C][n][h+1])
+// -> R sqrt(P)/n -> inverse FFT along y -> scratch (packed).
+template <typename T, int C, int IN>
+__device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, const T* sp, V2<T>* scr,
+                                              const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_tw = (V2<T>*)wf_smem;
+  V2<T>* A = s_tw + WF_NT;
+  V2<T>* Bf = A + WF_TILE;
+  const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1;
+  const int lgCT = lgTC + (C == 2 ? 1 : 0), kx0 = blockIdx.x * TC;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);  // first read after the first barrier
+  auto ld0 = [&](int t, int row) -> V2<T> {
+    const int c = t >> lgTC, kx = kx0 + (t & (TC - 1));
+    if constexpr (IN == WF_IN_STD) {
+      if (kx == 0) {  // kx = 0 and kx = n/2 stored separately
+        V2<T> X0[C], Xh[C];
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) {
+          const V2<T>* r = src + ((size_t)cc * n + row) * (h + 1);
+          X0[cc] = r[0];
+          Xh[cc] = r[h];
+        }
+        wf_mode_op<T, C, false>(X0, row, 0, n, sp, (T)1);
+        wf_mode_op<T, C, false>(Xh, row, h, n, sp, (T)1);
+        return wf_pack0<T>(X0[c], Xh[c]);
+      }
+      auto ldg = [&](int cc, int rr) { return src[((size_t)cc * n + rr) * (h + 1) + kx]; };
+      return wf_mode_packed<T, C, false>(ldg, row, c, kx, n, sp);
+    } else {
+      auto ldg = [&](int cc, int rr) { return src[((size_t)cc * n + rr) * h + kx]; };
+      return wf_mode_packed<T, C, false>(ldg, row, c, kx, n, sp);
+    }
+  };
+  auto stl = [&](int t, int row, V2<T> v) {
+    scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))] = v;
+  };
+  wf_pp_fft<T, +1, true>(lgn, lgCT, 1, C * TC, A, Bf, s_tw, ld0, stl);
+}
+
+// Forward column stage: scratch -> forward FFT along y -> shared tile O
+// (returned), synchronised; element (row j, channel c, column t) at
+// wf_sw(j * C * TC + c * TC + t), before the adjoint operator.
+template <typename T, int C>
+__device__ __forceinline__ V2<T>* wf_col_fwd_pp(const WfGeo& g, const V2<T>* scr, const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_tw = (V2<T>*)wf_smem;
+  V2<T>* A = s_tw + WF_NT;
+  V2<T>* Bf = A + WF_TILE;
+  const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1;
+  const int CT = C * TC, lgCT = lgTC + (C == 2 ? 1 : 0), kx0 = blockIdx.x * TC;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
+  auto ld0 = [&](int t, int row) { return scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))]; };
+  V2<T>* O = wf_pp_out<T>(lgn, A, Bf);
+  auto stl = [&](int t, int row, V2<T> v) { O[wf_sw<T>(row * CT + t)] = v; };
+  wf_pp_fft<T, -1, true>(lgn, lgCT, 1, CT, A, Bf, s_tw, ld0, stl);
+  __syncthreads();
+  return O;
+}
+
+// Row stage of the objective (MODE DATA: r = d - x) or of the Hessian-vector
+// product (MODE NODATA: r = -x): c2r along x, wr = w r, partial sum r.wr, r2c
+// of wr along x, back to scratch.  The c2r pre-step pairs X[k] with X[h-k] of
+// the same row and is applied as the first pass loads; the r2c post-step runs
+// from the last pass's shared output.
+template <typename T, int MODE>
+__device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const T* d, const T* w, double* part,
+                                          const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_pt = (V2<T>*)wf_smem;
+  V2<T>* A = s_pt + WF_NT;
+  V2<T>* Bf = A + WF_TILE;
+  const V2<T>* roots = (const V2<T>*)tw_;  // exp(-2 pi i k / WF_NT), read through the cache
+  const int b = blockIdx.y, n = g.n, h = g.h, lgh = g.lgh, RB = g.RB, lgRB = __ffs(RB) - 1;
+  const int row0 = blockIdx.x * RB;
+  const size_t npix = (size_t)g.C * n * n;
+  const int lgNTn = WF_LOG2_NT - g.lgn;
+  wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, lgh);
+  V2<T>* sc = scratch + (size_t)b * g.C * n * h + (size_t)row0 * h;
+  const V2<T>* dv = (const V2<T>*)(d + (size_t)b * npix + (size_t)row0 * n);
+  const V2<T>* wv = (const V2<T>*)(w + (size_t)b * npix + (size_t)row0 * n);
+  // c2r pre-step: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]), w = exp(+2 pi i / n);
+  // Z[0] from the packed X[0] + i X[h].
+  auto ld0 = [&](int t, int k) -> V2<T> {
+    const V2<T>* row = sc + (size_t)t * h;
+    const V2<T> Xk = row[k];
+    if (k == 0) return mk<T>(Xk.x + Xk.y, Xk.x - Xk.y);
+    const V2<T> Xm = row[h - k];
+    const V2<T> w1 = twid<T, +1>(roots, k << lgNTn);
+    const V2<T> s1 = mk<T>(Xk.x + Xm.x, Xk.y - Xm.y), d1 = mk<T>(Xk.x - Xm.x, Xk.y + Xm.y);
+    return cadd<T>(s1, mul_i<T>(cmul<T>(w1, d1)));
+  };
+  // pixel step on the c2r output (pixels 2m, 2m+1 of row t): wr = w (d - x)
+  V2<T>* O = wf_pp_out<T>(lgh, A, Bf);
+  WfAcc<T> acc = 0;
+  auto stpix = [&](int t, int m, V2<T> x) {
+    const size_t e = (size_t)t * n / 2 + m;
+    const V2<T> wl = wv[e];
+    V2<T> r;
+    if constexpr (MODE == WF_ROW_DATA) {
+      const V2<T> dl = dv[e];
+      r = mk<T>(dl.x - x.x, dl.y - x.y);
+    } else {
+      r = mk<T>(-x.x, -x.y);
+    }
+    const V2<T> wr = mk<T>(wl.x * r.x, wl.y * r.y);
+    acc += (WfAcc<T>)(r.x * wr.x + r.y * wr.y);
+    O[wf_sw<T>(t * h + m)] = wr;
+  };
+  wf_pp_fft<T, +1, false>(lgh, lgRB, h, 1, A, Bf, s_pt, ld0, stpix);
+  __syncthreads();
+  // r2c of wr: the input is O, so the passes start from the other buffer
+  V2<T>* A2 = (O == A) ? Bf : A;
+  auto ldO = [&](int t, int e) { return O[wf_sw<T>(t * h + e)]; };
+  V2<T>* Z = wf_pp_out<T>(lgh, A2, O);
+  auto stZ = [&](int t, int e, V2<T> v) { Z[wf_sw<T>(t * h + e)] = v; };
+  wf_pp_fft<T, -1, false>(lgh, lgRB, h, 1, A2, O, s_pt, ldO, stZ);
+  __syncthreads();
+  // r2c post-step: X[k] = (Z[k] + conj Z[h-k])/2 - i w^-k (Z[k] - conj Z[h-k])/2, X[0], X[h] packed
+  for (int e = threadIdx.x; e < RB * h; e += blockDim.x) {
+    const int t = e >> lgh, k = e & (h - 1);
+    const V2<T> Zk = Z[wf_sw<T>(t * h + k)];
+    V2<T> X;
+    if (k == 0) {
+      X = mk<T>(Zk.x + Zk.y, Zk.x - Zk.y);
+    } else {
+      const V2<T> Zm = Z[wf_sw<T>(t * h + h - k)];
+      const V2<T> w1 = twid<T, -1>(roots, k << lgNTn);
+      const V2<T> s1 = mk<T>(Zk.x + Zm.x, Zk.y - Zm.y), d1 = mk<T>(Zk.x - Zm.x, Zk.y + Zm.y);
+      const V2<T> i1 = mul_i<T>(cmul<T>(w1, d1));
+      X = mk<T>((T)0.5 * (s1.x - i1.x), (T)0.5 * (s1.y - i1.y));
+    }
+    sc[e] = X;
+  }
+  const double s = wf_block_sum((double)acc);
+  if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;
+}
