@@ -60,6 +60,14 @@ typedef enum {
 } wf_status;
 
 typedef enum { WF_FP64 = 0, WF_MIXED = 1 } wf_precision;  /* MIXED: FP32 fields, FP64 sums */
+/* Step length along each L-BFGS direction p (Sec. 2.2 uses a generic L-BFGS).
+ * chi^2 is quadratic, so one Hessian-vector pass q = H p gives chi^2 and its
+ * slope along p in closed form: phi(a) = chi2 + a g.p + a^2 p.Hp / 2.
+ *   WF_LS_EXACT: the minimiser a = -g.p / p.Hp.
+ *   WF_LS_WOLFE: the strong Wolfe search of Nocedal & Wright (Alg. 3.5 with
+ *     zoom, Alg. 3.6): trial a = 1, doubling, safeguarded quadratic
+ *     interpolation, constants c1 and c2, run on phi. */
+typedef enum { WF_LS_EXACT = 0, WF_LS_WOLFE = 1 } wf_line_search;
 typedef enum { WF_F32 = 0, WF_F64 = 1 } wf_dtype;
 
 typedef struct wf_handle wf_handle;
@@ -87,6 +95,11 @@ typedef struct {
                          (one synchronisation each); default 16 */
   int use_graphs;     /* capture check_every iterations in one CUDA graph; default 1 */
   void* stream;       /* cudaStream_t for all work of the call; NULL = default stream */
+  int line_search;    /* wf_line_search; default WF_LS_EXACT */
+  int pad_;
+  double c1, c2;      /* strong Wolfe constants, 0 < c1 < c2 < 1; default 1e-4, 0.9 */
+  unsigned long long seed;  /* Philox key of draws made on the device (bandpower_estimate
+                               with no caller-supplied fields); default 0 */
 } wf_opts;
 
 typedef struct {
@@ -98,10 +111,18 @@ typedef struct {
   double gnorm_rel;   /* final |g| / |g0| (true gradient) */
 } wf_solve_stats;
 
-/* Library handle: owns the twiddle tables for the current device.  Create one
- * per device and thread of use.  Returns WF_ECUDA if no device is usable. */
-wf_status wf_create(wf_handle** out);
+/* Library handle: owns the twiddle tables for the current device and charges
+ * every device allocation of its problems, solvers and band-power runs to one
+ * workspace.  workspace_limit: most device bytes the handle may hold at once
+ * (0 = no limit); an allocation beyond it fails with WF_ENOMEM and the call
+ * returns without side effects.  Create one per device and thread of use.
+ * Returns WF_ECUDA if no device is usable.  wf_destroy does not free the
+ * handle's problems: destroy those first. */
+wf_status wf_create(wf_handle** out, size_t workspace_limit);
 wf_status wf_destroy(wf_handle* h);
+
+/* Device bytes the handle holds now (twiddle tables, problems, solver state). */
+wf_status wf_workspace_used(const wf_handle* h, size_t* bytes);
 
 /* Message for the last failing call on this thread ("" if none).  The pointer
  * stays valid until the next call from the same thread. */
@@ -231,8 +252,23 @@ wf_status wf_simulate_data(wf_problem* p, const void* z, const void* noise, void
 wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
                          const double* theta, int n_bands, double* E, void* stream);
 
-/* Inputs of the band-power estimator.  All pointers are DEVICE pointers; the
- * random fields are supplied by the caller (any generator), in the working type. */
+/* Band table from edges in |k| (the bands of Sec. 2.4, Pi_l = 1 on the modes
+ * of band l).  Mode (row j, column kx) of the half plane has the signed row
+ * frequency ky = j for j < n/2 and j - n otherwise, and |k| = kscale *
+ * sqrt(kx^2 + ky^2) (kscale = 1: units of the fundamental 2 pi / L; 2 pi / L
+ * for physical k, or 360 / (patch side in degrees) for multipoles l).  Band
+ * l = 0..n_bands-1 holds the modes with edges[l] <= |k| < edges[l+1]; other
+ * modes get -1.  edges: HOST, n_bands + 1 increasing values; out: HOST
+ * [C][n][n/2+1], the same table for every channel.  Host only (no device
+ * work); WF_EINVAL for bad sizes or edges that do not increase. */
+wf_status wf_band_table(int n, int C, const double* edges, int n_bands, double kscale, int16_t* out);
+
+/* Inputs of the band-power estimator.  All pointers are DEVICE pointers.  The
+ * random fields z, noise and u are either all supplied by the caller (any
+ * generator, working type) or all NULL: then the call draws them on the device
+ * with wf_normal_draw's generator from opts->seed, z from stream 0, noise
+ * from stream 1 (scaled by Ninv^-1/2 on observed pixels) and u from stream 2,
+ * deviate i of each being element i of the flattened array. */
 typedef struct {
   int n_bands;            /* bands, ids 0 .. n_bands-1 (1..64) */
   int n_sim;              /* noise-bias simulations (>= 2) */
@@ -277,6 +313,19 @@ typedef struct {
 wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
                              const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
                              wf_solve_stats* stats);
+
+/* Standard normal deviates on the device: out[k] = deviate offset + k of
+ * (seed, stream_id), k < count, in dtype WF_F32 or WF_F64 (computed in FP64).
+ * Generator: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).  Deviate i
+ * comes from block j = i / 2: counter (j mod 2^32, j div 2^32, stream_id, 0),
+ * key (seed mod 2^32, seed div 2^32); output words x0..x3 give
+ * u1 = (2^26 (x0 >> 5) + (x1 >> 6) + 1/2) 2^-53, u2 likewise from x2, x3, and
+ * the Box-Muller pair sqrt(-2 ln u1) (cos, sin)(2 pi u2): deviate 2j is the
+ * cosine, 2j + 1 the sine.  The draws of the simulations of Sec. 2.5 (white
+ * fields and noise) when the caller supplies none.  out: DEVICE pointer.
+ * Stream ordered; WF_EINVAL for a null output or a bad dtype. */
+wf_status wf_normal_draw(unsigned long long seed, unsigned int stream_id, unsigned long long offset,
+                         size_t count, int dtype, void* out, void* stream);
 
 /* Objective + gradient pass that allocates nothing (no counterpart in the
  * paper; an interface for callers that cannot allocate device memory, for

@@ -36,6 +36,10 @@ extern "C" void wf_opts_default(wf_opts* o) {
   o->check_every = 16;
   o->use_graphs = 1;
   o->stream = nullptr;
+  o->line_search = WF_LS_EXACT;
+  o->c1 = 1e-4;
+  o->c2 = 0.9;
+  o->seed = 0;
 }
 
 WfGeo wf_make_geo(int n, int C) {
@@ -100,34 +104,37 @@ void wf_make_twiddles(double2* out) {
   }
 }
 
-extern "C" wf_status wf_create(wf_handle** out) {
+extern "C" wf_status wf_create(wf_handle** out, size_t workspace_limit) {
   if (!out) return wf_fail(WF_EINVAL, "wf_create: null output pointer");
   *out = nullptr;
-  wf_handle* h = (wf_handle*)calloc(1, sizeof(wf_handle));
+  wf_handle* h = new (std::nothrow) wf_handle();
   if (!h) return wf_fail(WF_ENOMEM, "wf_create: host allocation failed");
+  h->limit = workspace_limit;
+  h->used = 0;
   cudaError_t e = cudaGetDevice(&h->device);
-  if (e != cudaSuccess) { free(h); return wf_cuda_fail(e, "wf_create: cudaGetDevice"); }
+  if (e != cudaSuccess) { delete h; return wf_cuda_fail(e, "wf_create: cudaGetDevice"); }
   double2* tw64 = (double2*)malloc(sizeof(double2) * WF_TWTAB);
   float2* tw32 = (float2*)malloc(sizeof(float2) * WF_TWTAB);
   if (!tw64 || !tw32) {
     free(tw64);
     free(tw32);
-    free(h);
+    delete h;
     return wf_fail(WF_ENOMEM, "wf_create: host allocation failed");
   }
   wf_make_twiddles(tw64);
   for (int k = 0; k < WF_TWTAB; ++k) { tw32[k].x = (float)tw64[k].x; tw32[k].y = (float)tw64[k].y; }
-  e = cudaMalloc(&h->tw64, sizeof(double2) * WF_TWTAB);
-  if (e == cudaSuccess) e = cudaMalloc(&h->tw32, sizeof(float2) * WF_TWTAB);
-  if (e == cudaSuccess) e = cudaMemcpy(h->tw64, tw64, sizeof(double2) * WF_TWTAB, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->tw32, tw32, sizeof(float2) * WF_TWTAB, cudaMemcpyHostToDevice);
+  wf_status s = wf_alloc(h, &h->tw64, sizeof(double2) * WF_TWTAB, "twiddle tables");
+  if (s == WF_OK) s = wf_alloc(h, &h->tw32, sizeof(float2) * WF_TWTAB, "twiddle tables");
+  e = cudaSuccess;
+  if (s == WF_OK) e = cudaMemcpy(h->tw64, tw64, sizeof(double2) * WF_TWTAB, cudaMemcpyHostToDevice);
+  if (s == WF_OK && e == cudaSuccess) e = cudaMemcpy(h->tw32, tw32, sizeof(float2) * WF_TWTAB, cudaMemcpyHostToDevice);
   free(tw64);
   free(tw32);
-  if (e != cudaSuccess) {
-    if (h->tw64) cudaFree(h->tw64);
-    if (h->tw32) cudaFree(h->tw32);
-    free(h);
-    return wf_cuda_fail(e, "wf_create: twiddle tables");
+  if (s != WF_OK || e != cudaSuccess) {
+    wf_free(h, h->tw64);
+    wf_free(h, h->tw32);
+    delete h;
+    return s != WF_OK ? s : wf_cuda_fail(e, "wf_create: twiddle tables");
   }
   *out = h;
   return WF_OK;
@@ -135,32 +142,60 @@ extern "C" wf_status wf_create(wf_handle** out) {
 
 extern "C" wf_status wf_destroy(wf_handle* h) {
   if (!h) return WF_OK;
-  cudaFree(h->tw64);
-  cudaFree(h->tw32);
-  free(h);
+  wf_free(h, h->tw64);
+  wf_free(h, h->tw32);
+  delete h;
+  return WF_OK;
+}
+
+extern "C" wf_status wf_workspace_used(const wf_handle* h, size_t* bytes) {
+  if (!h || !bytes) return wf_fail(WF_EINVAL, "wf_workspace_used: null argument");
+  std::lock_guard<std::mutex> lock(const_cast<wf_handle*>(h)->mu);
+  *bytes = h->used;
   return WF_OK;
 }
 
 static void free_problem(wf_problem* p) {
   if (!p) return;
   void* ptrs[] = {p->d, p->w, p->sp, p->sp0, p->scratch, p->part, p->flags};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  for (void* q : ptrs) wf_free(p->h, q);
   wf_solver_free(p);
   free(p);
 }
 
-wf_status wf_alloc(void** ptr, size_t bytes, const char* what) {
+wf_status wf_alloc(wf_handle* h, void** ptr, size_t bytes, const char* what) {
   *ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(h->mu);
+    if (h->limit && h->used + bytes > h->limit)
+      return wf_fail(WF_ENOMEM, "%s: %zu more bytes would exceed the workspace limit (%zu of %zu in use)", what,
+                     bytes, h->used, h->limit);
+    h->used += bytes;  // reserved before the allocation, so concurrent callers cannot overshoot
+  }
   cudaError_t e = cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
     cudaGetLastError();
+    std::lock_guard<std::mutex> lock(h->mu);
+    h->used -= bytes;
     return wf_fail(e == cudaErrorMemoryAllocation ? WF_ENOMEM : WF_ECUDA,
                    "device allocation of %zu bytes for %s failed: %s", bytes, what,
                    cudaGetErrorString(e));
   }
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->live[*ptr] = bytes;
   return WF_OK;
+}
+
+void wf_free(wf_handle* h, void* ptr) {
+  if (!ptr) return;
+  cudaFree(ptr);
+  std::lock_guard<std::mutex> lock(h->mu);
+  auto it = h->live.find(ptr);
+  if (it != h->live.end()) {
+    h->used -= it->second;
+    h->live.erase(it);
+  }
 }
 
 extern "C" wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, int C,
@@ -204,12 +239,12 @@ extern "C" wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int cou
   const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
   p->sp_stride = shared ? 0 : (long long)nsp;
   wf_status s = WF_OK;
-  if (s == WF_OK) s = wf_alloc(&p->d, npix * count * p->elt, "data maps");
-  if (s == WF_OK) s = wf_alloc(&p->w, npix * count * p->elt, "weights");
-  if (s == WF_OK) s = wf_alloc(&p->sp, nsp * (shared ? 1 : count) * p->elt, "sqrt(P) tables");
-  if (s == WF_OK) s = wf_alloc(&p->scratch, npix * count * p->elt, "scratch");
-  if (s == WF_OK) s = wf_alloc((void**)&p->part, sizeof(double) * WF_NSLOT * p->g.maxblk * count, "partial sums");
-  if (s == WF_OK) s = wf_alloc((void**)&p->flags, sizeof(int) * 4, "flags");
+  if (s == WF_OK) s = wf_alloc(h, &p->d, npix * count * p->elt, "data maps");
+  if (s == WF_OK) s = wf_alloc(h, &p->w, npix * count * p->elt, "weights");
+  if (s == WF_OK) s = wf_alloc(h, &p->sp, nsp * (shared ? 1 : count) * p->elt, "sqrt(P) tables");
+  if (s == WF_OK) s = wf_alloc(h, &p->scratch, npix * count * p->elt, "scratch");
+  if (s == WF_OK) s = wf_alloc(h, (void**)&p->part, sizeof(double) * WF_NSLOT * p->g.maxblk * count, "partial sums");
+  if (s == WF_OK) s = wf_alloc(h, (void**)&p->flags, sizeof(int) * 4, "flags");
   if (s != WF_OK) { free_problem(p); return s; }
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(p->flags, 0, sizeof(int) * 4, st);
@@ -329,7 +364,7 @@ extern "C" wf_status wf_problem_set_band_scale(wf_problem* p, const int16_t* ban
   const int ntab = p->sp_shared ? 1 : p->count;
   cudaStream_t st = (cudaStream_t)stream;
   if (!p->sp0) {
-    wf_status s = wf_alloc(&p->sp0, nsp * ntab * p->elt, "unscaled sqrt(P) table");
+    wf_status s = wf_alloc(p->h, &p->sp0, nsp * ntab * p->elt, "unscaled sqrt(P) table");
     if (s != WF_OK) return s;
     cudaError_t e = cudaMemcpyAsync(p->sp0, p->sp, nsp * ntab * p->elt, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return wf_cuda_fail(e, "wf_problem_set_band_scale: copy");
@@ -347,4 +382,32 @@ extern "C" wf_status wf_eval_bands(wf_problem* p, const void* s, void* grad, dou
   cudaError_t e = WF_DISPATCH(p, wf_launch_eval_bands)(p->g, b, s, grad, chi2, band, n_b, dlogq,
                                                        (cudaStream_t)stream);
   return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_eval_bands");
+}
+
+extern "C" wf_status wf_band_table(int n, int C, const double* edges, int n_bands, double kscale, int16_t* out) {
+  if (!edges || !out) return wf_fail(WF_EINVAL, "wf_band_table: null argument");
+  if (n < 2 || (n & 1) || (C != 1 && C != 2)) return wf_fail(WF_EINVAL, "wf_band_table: n = %d, C = %d", n, C);
+  if (n_bands < 1 || n_bands > 32767) return wf_fail(WF_EINVAL, "wf_band_table: n_bands = %d", n_bands);
+  if (!(kscale > 0.0)) return wf_fail(WF_EINVAL, "wf_band_table: kscale must be > 0");
+  for (int l = 0; l < n_bands; ++l)
+    if (!(edges[l] < edges[l + 1])) return wf_fail(WF_EINVAL, "wf_band_table: edges must increase");
+  const int h = n / 2;
+  for (int j = 0; j < n; ++j) {
+    const int ky = j < h ? j : j - n;
+    for (int kx = 0; kx <= h; ++kx) {
+      const double k = kscale * sqrt((double)kx * kx + (double)ky * ky);
+      int band = -1;
+      if (k >= edges[0] && k < edges[n_bands]) {
+        int lo = 0, hi = n_bands;  // edges[lo] <= k < edges[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) / 2;
+          if (k >= edges[mid]) lo = mid;
+          else hi = mid;
+        }
+        band = lo;
+      }
+      for (int c = 0; c < C; ++c) out[((size_t)c * n + j) * (h + 1) + kx] = (int16_t)band;
+    }
+  }
+  return WF_OK;
 }

@@ -1,11 +1,17 @@
 // Host-side structures of the C ABI (handle, prepared problem, solver state).
 #pragma once
+#include <mutex>
+#include <unordered_map>
 #include "wf_internal.h"
 
 struct wf_handle {
   int device;
   void* tw64;   // WF_TWTAB double2 twiddles (roots of unity, pass tables)
   void* tw32;   // WF_TWTAB float2 twiddles
+  size_t limit;  // workspace limit in bytes (0 = none)
+  size_t used;   // device bytes held by this handle's allocations
+  std::mutex mu;
+  std::unordered_map<void*, size_t> live;  // allocation -> bytes
 };
 
 struct WfSolver;  // L-BFGS state, allocated on the first solve (wf_solve.cu)
@@ -29,7 +35,14 @@ struct wf_problem {
 
 wf_status wf_fail(wf_status s, const char* fmt, ...);
 wf_status wf_cuda_fail(cudaError_t e, const char* what);
-wf_status wf_alloc(void** ptr, size_t bytes, const char* what);
+// Device allocation charged to the handle's workspace (WF_ENOMEM beyond its
+// limit), and its release; wf_free(h, nullptr) does nothing.
+wf_status wf_alloc(wf_handle* h, void** ptr, size_t bytes, const char* what);
+void wf_free(wf_handle* h, void* ptr);
 WfBufs wf_bufs(const wf_problem* p);
 void wf_solver_free(wf_problem* p);
 void wf_make_twiddles(double2* out);  // WF_TWTAB entries: roots of unity and pass tables
+// Normal deviates offset .. offset + count - 1 of (seed, stream_id) into out
+// (working type); scaled by w^-1/2 where w > 0 and zeroed elsewhere if w given.
+wf_status wf_draw_normal(unsigned long long seed, unsigned stream_id, unsigned long long offset, size_t count,
+                         int working_f64, void* out, const void* w, cudaStream_t st);

@@ -7,7 +7,8 @@
 //   Theta_hat = Theta_fid + F^-1 (E - b),  cov = F^-1         (eq. eq:wfmv, eq:var)
 // Theta_fid,l is the mean of P over the band's full-plane modes.  The data,
 // noise-bias and Fisher maps are solved together in one batched L-BFGS run.
-// Random fields are inputs, so a run is reproducible and testable.
+// Random fields are inputs, or drawn here from a counter-based generator with
+// a caller-given seed, so a run is reproducible and testable.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -130,15 +131,17 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
 
 namespace {
 struct Scope {  // frees what the estimator allocates, on every return path
+  wf_handle* h;
   void* ptrs[16] = {};
   int n = 0;
   wf_problem* probs[4] = {};
   int np = 0;
+  explicit Scope(wf_handle* hh) : h(hh) {}
   void* add(void* p) { ptrs[n++] = p; return p; }
   void addp(wf_problem* p) { probs[np++] = p; }
   ~Scope() {
     for (int i = 0; i < np; ++i) wf_problem_destroy(probs[i]);
-    for (int i = 0; i < n; ++i) cudaFree(ptrs[i]);
+    for (int i = 0; i < n; ++i) wf_free(h, ptrs[i]);
   }
 };
 }  // namespace
@@ -164,8 +167,10 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (nb < 1 || nb > 64) return wf_fail(WF_EINVAL, "bandpower_estimate: n_bands = %d outside [1, 64]", nb);
   if (J < 2) return wf_fail(WF_EINVAL, "bandpower_estimate: n_sim = %d (need >= 2)", J);
   if (nfd < 0 || nfd > J) return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd = %d outside [0, n_sim]", nfd);
-  if (!in->band || !in->z || !in->noise || (nfd > 0 && !in->u))
-    return wf_fail(WF_EINVAL, "bandpower_estimate: null band table or random fields");
+  if (!in->band) return wf_fail(WF_EINVAL, "bandpower_estimate: null band table");
+  const bool draw = !in->z && !in->noise && !in->u;  // fields drawn here from opts->seed
+  if (!draw && (!in->z || !in->noise || (nfd > 0 && !in->u)))
+    return wf_fail(WF_EINVAL, "bandpower_estimate: supply all random fields (z, noise, u) or none");
   if (!out->theta_fid || !out->E || !out->bias || !out->fisher || !out->cov || !out->theta_hat || !out->cov_E)
     return wf_fail(WF_EINVAL, "bandpower_estimate: null output array");
   if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "bandpower_estimate: bad dtype");
@@ -177,10 +182,10 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   const size_t welt = precision == WF_FP64 ? 8 : 4;
   const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
   const int nF = nb * nfd, Btot = 1 + J + nF;
-  Scope sc;
+  Scope sc(h);
   // Theta_fid and the band-restricted power tables
   double* theta = nullptr;
-  BP_OK(wf_alloc((void**)&theta, sizeof(double) * nb, "theta_fid"));
+  BP_OK(wf_alloc(h, (void**)&theta, sizeof(double) * nb, "theta_fid"));
   sc.add(theta);
   if (dtype == WF_F64)
     k_theta_fid<double><<<1, 1024, 2 * nb * sizeof(double), st>>>((const double*)data->P, in->band, n, C, nb, theta);
@@ -188,7 +193,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     k_theta_fid<float><<<1, 1024, 2 * nb * sizeof(double), st>>>((const float*)data->P, in->band, n, C, nb, theta);
   BP_TRY(cudaGetLastError());
   void* Pl = nullptr;
-  BP_OK(wf_alloc(&Pl, nsp * nb * delt, "band-restricted power"));
+  BP_OK(wf_alloc(h, &Pl, nsp * nb * delt, "band-restricted power"));
   sc.add(Pl);
   const int gblk = (int)((nsp + 255) / 256 < 4096 ? (nsp + 255) / 256 : 4096);
   if (dtype == WF_F64)
@@ -210,11 +215,28 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   wf_status rs = wf_problem_create(h, maps, J, n, C, dtype, precision, 1, (void*)st, &psim);
   if (rs != WF_OK) { free(maps); return rs; }
   sc.addp(psim);
+  const void* zin = in->z;
+  const void* nzin = in->noise;
+  const void* uin = in->u;
+  if (draw) {  // streams 0, 1, 2 of opts->seed; noise scaled by the simulations' W = M Ninv
+    void *zb = nullptr, *nb_ = nullptr, *ub = nullptr;
+    rs = wf_alloc(h, &zb, npix * J * welt, "drawn signal fields");
+    if (rs == WF_OK) { sc.add(zb); rs = wf_alloc(h, &nb_, npix * J * welt, "drawn noise"); }
+    if (rs == WF_OK) { sc.add(nb_); if (nF > 0) rs = wf_alloc(h, &ub, npix * nF * welt, "drawn Fisher fields"); }
+    if (rs == WF_OK && ub) sc.add(ub);
+    if (rs == WF_OK) rs = wf_draw_normal(o.seed, 0, 0, npix * J, precision == WF_FP64, zb, nullptr, st);
+    if (rs == WF_OK) rs = wf_draw_normal(o.seed, 1, 0, npix * J, precision == WF_FP64, nb_, psim->w, st);
+    if (rs == WF_OK && nF > 0) rs = wf_draw_normal(o.seed, 2, 0, npix * nF, precision == WF_FP64, ub, nullptr, st);
+    if (rs != WF_OK) { free(maps); return rs; }
+    zin = zb;
+    nzin = nb_;
+    uin = ub;
+  }
   void* dsim = nullptr;
-  rs = wf_alloc(&dsim, npix * J * welt, "simulated data");
+  rs = wf_alloc(h, &dsim, npix * J * welt, "simulated data");
   if (rs != WF_OK) { free(maps); return rs; }
   sc.add(dsim);
-  rs = wf_simulate_data(psim, in->z, in->noise, dsim, st);
+  rs = wf_simulate_data(psim, zin, nzin, dsim, st);
   if (rs != WF_OK) { free(maps); return rs; }
 
   // Fisher maps: d_j + M A_l u_lj, synthesised with the band-restricted power as
@@ -228,8 +250,8 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     if (rs != WF_OK) { free(maps); return rs; }
     sc.addp(pfd);
     void* nfd_in = nullptr;
-    rs = wf_alloc(&nfd_in, npix * nF * welt, "Fisher base data");
-    if (rs == WF_OK) { sc.add(nfd_in); rs = wf_alloc(&dfd, npix * nF * welt, "Fisher data"); }
+    rs = wf_alloc(h, &nfd_in, npix * nF * welt, "Fisher base data");
+    if (rs == WF_OK) { sc.add(nfd_in); rs = wf_alloc(h, &dfd, npix * nF * welt, "Fisher data"); }
     if (rs != WF_OK) { free(maps); return rs; }
     sc.add(dfd);
     for (int l = 0; l < nb; ++l)
@@ -239,7 +261,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
                                         cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) { free(maps); return wf_cuda_fail(e, "bandpower_estimate: Fisher base copy"); }
       }
-    rs = wf_simulate_data(pfd, in->u, nfd_in, dfd, st);
+    rs = wf_simulate_data(pfd, uin, nfd_in, dfd, st);
     if (rs != WF_OK) { free(maps); return rs; }
   }
 
@@ -256,7 +278,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     BP_TRY(cudaMemcpyAsync((char*)ps->d + (size_t)(1 + J) * npix * welt, dfd, npix * nF * welt,
                            cudaMemcpyDeviceToDevice, st));
   void* sall = nullptr;
-  BP_OK(wf_alloc(&sall, nsp * Btot * 2 * welt, "MAP spectra"));
+  BP_OK(wf_alloc(h, &sall, nsp * Btot * 2 * welt, "MAP spectra"));
   sc.add(sall);
   wf_solve_stats* hst = (wf_solve_stats*)calloc((size_t)Btot, sizeof(wf_solve_stats));
   if (!hst) return wf_fail(WF_ENOMEM, "bandpower_estimate: host allocation");
@@ -266,15 +288,15 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (rs != WF_OK && rs != WF_ENOTCONVERGED) return rs;
   const wf_status solve_status = rs;
   double* Eall = nullptr;
-  BP_OK(wf_alloc((void**)&Eall, sizeof(double) * Btot * nb, "band energies"));
+  BP_OK(wf_alloc(h, (void**)&Eall, sizeof(double) * Btot * nb, "band energies"));
   sc.add(Eall);
   BP_OK(wf_band_energy(ps, sall, in->band, theta, nb, Eall, st));
   const size_t nout = 4 * (size_t)nb + 3 * (size_t)nb * nb;
   double* dout = nullptr;
   int* dflag = nullptr;
-  BP_OK(wf_alloc((void**)&dout, sizeof(double) * nout, "estimator output"));
+  BP_OK(wf_alloc(h, (void**)&dout, sizeof(double) * nout, "estimator output"));
   sc.add(dout);
-  BP_OK(wf_alloc((void**)&dflag, sizeof(int), "flag"));
+  BP_OK(wf_alloc(h, (void**)&dflag, sizeof(int), "flag"));
   sc.add(dflag);
   BP_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), st));
   const size_t gj_smem = sizeof(double) * 2 * nb * nb;

@@ -20,8 +20,8 @@
 #include "wf_api_internal.h"
 
 struct WfScalarArgs {
-  double gtol2, dchi2;
-  int max_iter, m, ntile, nrb, ncomb, maxblk, phase, init;
+  double gtol2, dchi2, c1, c2;
+  int max_iter, m, ntile, nrb, ncomb, maxblk, phase, init, ls;
 };
 // Legacy and per-thread default stream handles cannot be captured; the solver
 // then runs on its own stream, ordered after the caller's with events.
@@ -43,8 +43,8 @@ struct WfSolver {
   cudaStream_t stream;
   cudaEvent_t ev_in, ev_out;
   cudaGraphExec_t exec;
-  int g_chunk, g_maxit, g_m;
-  double g_gtol2, g_dchi2;
+  int g_chunk, g_maxit, g_m, g_ls;
+  double g_gtol2, g_dchi2, g_c1, g_c2;
   int started;
   cudaStream_t work, g_stream;  // stream in use; stream the graph was captured on
   long long iters;     // iterations launched since the last start
@@ -108,6 +108,50 @@ __device__ void wf_two_loop(WfLbMap& M, int m) {
   M.next = (head + 1) % m;
 }
 
+// Strong Wolfe step along p (Nocedal & Wright, Alg. 3.5, zoom Alg. 3.6) on the
+// exact quadratic model of chi^2: f(a) = phi(a) - phi(0) = a d0 + a^2 c / 2 and
+// phi'(a) = d0 + a c, with d0 = g.p < 0 and c = p.Hp > 0.  Trial a = 1, then
+// doubling up to 1e6; zoom by quadratic interpolation of f(lo), phi'(lo), f(hi),
+// kept inside the middle 80% of the bracket (else bisection).
+__device__ double wf_wolfe_zoom(double lo, double f_lo, double d_lo, double hi, double f_hi, double d0, double c,
+                                double c1, double c2) {
+  for (int it = 0; it < 60; ++it) {
+    const double da = hi - lo, den = 2.0 * (f_hi - f_lo - d_lo * da);
+    double a = den > 0.0 ? lo - d_lo * da * da / den : 0.5 * (lo + hi);
+    const double bl = fmin(lo, hi), bh = fmax(lo, hi);
+    if (!(a >= bl + 0.1 * (bh - bl) && a <= bh - 0.1 * (bh - bl))) a = 0.5 * (lo + hi);
+    const double f = a * d0 + 0.5 * a * a * c, d = d0 + a * c;
+    if (f > c1 * a * d0 || f >= f_lo) {
+      hi = a;
+      f_hi = f;
+    } else {
+      if (fabs(d) <= -c2 * d0) return a;
+      if (d * (hi - lo) >= 0.0) {
+        hi = lo;
+        f_hi = f_lo;
+      }
+      lo = a;
+      f_lo = f;
+      d_lo = d;
+    }
+  }
+  return lo;
+}
+__device__ double wf_wolfe_step(double d0, double c, double c1, double c2) {
+  double a_prev = 0.0, f_prev = 0.0, d_prev = d0, a = 1.0;
+  for (int i = 0; i < 40; ++i) {
+    const double f = a * d0 + 0.5 * a * a * c, d = d0 + a * c;
+    if (f > c1 * a * d0 || (i > 0 && f >= f_prev)) return wf_wolfe_zoom(a_prev, f_prev, d_prev, a, f, d0, c, c1, c2);
+    if (fabs(d) <= -c2 * d0) return a;
+    if (d >= 0.0) return wf_wolfe_zoom(a, f, d, a_prev, f_prev, d0, c, c1, c2);
+    a_prev = a;
+    f_prev = f;
+    d_prev = d;
+    a = fmin(2.0 * a, 1e6);
+  }
+  return a;
+}
+
 __global__ void __launch_bounds__(32 * WF_SW)
 k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
   __shared__ double S[WF_SW][WF_NSLOT];
@@ -148,7 +192,16 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
       M.pend_alpha = 0.0;
       return;
     }
-    const double alpha = -gp / pq;
+    // A8's curvature test s.y > 1e-12 |s| |y| with (s, y) = a (p, q): the pair
+    // would be unusable, and on this positive definite objective that only
+    // happens when rounding has taken over, so the map stops.
+    if (!(pq > 1e-12 * sqrt(pp * Sw[WF_SLOT_QQ]))) {
+      M.status = WF_ELINESEARCH;
+      M.active = 0;
+      M.pend_alpha = 0.0;
+      return;
+    }
+    const double alpha = A.ls == WF_LS_WOLFE ? wf_wolfe_step(gp, pq, A.c1, A.c2) : -gp / pq;
     M.chi2_prev = M.chi2;
     M.chi2 = M.chi2 + alpha * gp + 0.5 * alpha * alpha * pq;
     int W[WF_MAXM];
@@ -284,8 +337,7 @@ void wf_solver_free(wf_problem* p) {
   if (!S) return;
   if (S->exec) cudaGraphExecDestroy(S->exec);
   void* ptrs[] = {S->s, S->g, S->ring, S->st, S->nact, S->stats_dev};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  for (void* q : ptrs) wf_free(p->h, q);
   if (S->nact_host) cudaFreeHost(S->nact_host);
   if (S->stats_host) cudaFreeHost(S->stats_host);
   if (S->stream) cudaStreamDestroy(S->stream);
@@ -304,12 +356,12 @@ static wf_status ensure_solver(wf_problem* p, int m) {
   S->m = m;
   S->B = p->count;
   const size_t vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;  // packed complex = n^2 reals
-  wf_status s = wf_alloc(&S->s, vbytes, "L-BFGS state");
-  if (s == WF_OK) s = wf_alloc(&S->g, vbytes, "L-BFGS gradient");
-  if (s == WF_OK) s = wf_alloc(&S->ring, vbytes * 2 * m, "L-BFGS history");
-  if (s == WF_OK) s = wf_alloc((void**)&S->st, sizeof(WfLbMap) * p->count, "L-BFGS scalars");
-  if (s == WF_OK) s = wf_alloc((void**)&S->nact, sizeof(int), "active counter");
-  if (s == WF_OK) s = wf_alloc((void**)&S->stats_dev, sizeof(double) * 5 * p->count, "statistics");
+  wf_status s = wf_alloc(p->h, &S->s, vbytes, "L-BFGS state");
+  if (s == WF_OK) s = wf_alloc(p->h, &S->g, vbytes, "L-BFGS gradient");
+  if (s == WF_OK) s = wf_alloc(p->h, &S->ring, vbytes * 2 * m, "L-BFGS history");
+  if (s == WF_OK) s = wf_alloc(p->h, (void**)&S->st, sizeof(WfLbMap) * p->count, "L-BFGS scalars");
+  if (s == WF_OK) s = wf_alloc(p->h, (void**)&S->nact, sizeof(int), "active counter");
+  if (s == WF_OK) s = wf_alloc(p->h, (void**)&S->stats_dev, sizeof(double) * 5 * p->count, "statistics");
   cudaError_t e = cudaSuccess;
   if (s == WF_OK) e = cudaMallocHost((void**)&S->nact_host, sizeof(int));
   if (s == WF_OK && e == cudaSuccess) e = cudaMallocHost((void**)&S->stats_host, sizeof(double) * 5 * p->count);
@@ -391,6 +443,9 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   A.dchi2 = o->dchi2_abs;
   A.max_iter = o->max_iter;
   A.m = m;
+  A.ls = o->line_search;
+  A.c1 = o->c1;
+  A.c2 = o->c2;
   A.ntile = p->g.ntile;
   A.nrb = p->g.nrb;
   A.ncomb = p->g.ncomb;
@@ -405,7 +460,8 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
   const int chunk = o->check_every > 0 ? o->check_every : 16;
   if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
-                         S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m)) {
+                         S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m && S->g_ls == A.ls &&
+                         S->g_c1 == A.c1 && S->g_c2 == A.c2)) {
     if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
     // Set every kernel's attributes outside capture: one iteration, then undo
     // nothing (it is a genuine iteration of the solve).
@@ -426,6 +482,9 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
     S->g_gtol2 = A.gtol2;
     S->g_dchi2 = A.dchi2;
     S->g_m = m;
+    S->g_ls = A.ls;
+    S->g_c1 = A.c1;
+    S->g_c2 = A.c2;
     S->g_stream = st;
   }
   S->started = 1;
@@ -567,6 +626,10 @@ static wf_status check_opts(const wf_problem* p, const wf_opts* o) {
   if (!(o->gtol_rel >= 0.0) || !(o->dchi2_abs >= 0.0)) return wf_fail(WF_EINVAL, "tolerances must be >= 0");
   if (o->check_every < 0 || o->check_every > 4096) return wf_fail(WF_EINVAL, "bad check_every");
   if (o->refresh_every < 0) return wf_fail(WF_EINVAL, "bad refresh_every");
+  if (o->line_search != WF_LS_EXACT && o->line_search != WF_LS_WOLFE)
+    return wf_fail(WF_EINVAL, "line_search = %d is not WF_LS_EXACT or WF_LS_WOLFE", o->line_search);
+  if (o->line_search == WF_LS_WOLFE && !(0.0 < o->c1 && o->c1 < o->c2 && o->c2 < 1.0))
+    return wf_fail(WF_EINVAL, "Wolfe constants need 0 < c1 < c2 < 1 (c1 = %g, c2 = %g)", o->c1, o->c2);
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != p->h->device) return wf_fail(WF_EINVAL, "current device differs from the problem's");

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libwf.so")
 
 WF_FP64, WF_MIXED = 0, 1
 WF_F32, WF_F64 = 0, 1
+WF_LS_EXACT, WF_LS_WOLFE = 0, 1
 STATUS = {0: "WF_OK", 1: "WF_EINVAL", 2: "WF_ENONFINITE", 3: "WF_ENOMEM", 4: "WF_ECUDA",
           5: "WF_ENOTCONVERGED", 6: "WF_ELINESEARCH", 7: "WF_ETIMEOUT"}
 
@@ -24,7 +25,7 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy",
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
            "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
-           "wf_map_solve_many"]
+           "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table"]
 
 
 class WfMap(ctypes.Structure):
@@ -36,7 +37,9 @@ class WfOpts(ctypes.Structure):
     _fields_ = [("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("gtol_rel", ctypes.c_double), ("dchi2_abs", ctypes.c_double),
                 ("refresh_every", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("use_graphs", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("line_search", ctypes.c_int), ("pad_", ctypes.c_int), ("c1", ctypes.c_double),
+                ("c2", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
 
 
 class WfSolveStats(ctypes.Structure):
@@ -74,7 +77,9 @@ def lib() -> ctypes.CDLL:
     L = ctypes.CDLL(LIB_PATH)
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     L.wf_last_error.restype = ctypes.c_char_p
-    L.wf_create.argtypes = [ctypes.POINTER(vp)]
+    L.wf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
+    L.wf_workspace_used.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.wf_band_table.argtypes = [i, i, ctypes.POINTER(d), i, d, vp]
     L.wf_destroy.argtypes = [vp]
     L.wf_opts_default.argtypes = [ctypes.POINTER(WfOpts)]
     L.wf_opts_default.restype = None
@@ -99,6 +104,7 @@ def lib() -> ctypes.CDLL:
     L.bandpower_estimate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
                                      ctypes.POINTER(WfOpts), ctypes.POINTER(WfBandpowerOut),
                                      ctypes.POINTER(WfSolveStats)]
+    L.wf_normal_draw.argtypes = [ctypes.c_ulonglong, ctypes.c_uint, ctypes.c_ulonglong, ctypes.c_size_t, i, vp, vp]
     for name in EXPORTS:
         if name not in ("wf_last_error", "wf_opts_default"):
             getattr(L, name).restype = ctypes.c_int
@@ -122,12 +128,18 @@ def _stream(stream) -> int:
 
 
 class Handle:
-    """wf_create / wf_destroy."""
+    """wf_create / wf_destroy.  workspace_limit: most device bytes the handle's
+    problems and solvers may hold (0 = no limit)."""
 
-    def __init__(self):
+    def __init__(self, workspace_limit=0):
         h = ctypes.c_void_p()
-        _check(lib().wf_create(ctypes.byref(h)))
+        _check(lib().wf_create(ctypes.byref(h), int(workspace_limit)))
         self._h = h
+
+    def workspace_used(self):
+        v = ctypes.c_size_t()
+        _check(lib().wf_workspace_used(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     @property
     def ptr(self):
@@ -200,21 +212,45 @@ def solve_many(problems, stream=None, **opts):
     return [SolveResult(s=t, x=None, stats=Problem._stats(st)) for t, st in zip(outs, sts)]
 
 
+def band_table(n, edges, C=1, kscale=1.0):
+    """wf_band_table: int16 numpy array (C, n, n/2+1) of band ids from |k| edges."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    out = np.empty((C, n, n // 2 + 1), dtype=np.int16)
+    _check(lib().wf_band_table(int(n), int(C), e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(e) - 1,
+                               float(kscale), out.ctypes.data))
+    return out
+
+
+def normal_draw(seed, count, stream_id=0, offset=0, dtype=None, out=None, stream=None):
+    """wf_normal_draw: `count` standard normal deviates of (seed, stream_id)
+    starting at deviate `offset`, as a CUDA tensor (float64 by default)."""
+    import torch
+    if out is None:
+        out = torch.empty(int(count), dtype=dtype or torch.float64, device="cuda")
+    _check(lib().wf_normal_draw(int(seed), int(stream_id), int(offset), int(count),
+                                WF_F64 if out.dtype == torch.float64 else WF_F32, _ptr(out), _stream(stream)))
+    return out
+
+
 def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",
-                       handle=None, stream=None, **opts):
+                       handle=None, stream=None, n_sim=None, n_fd=None, **opts):
     """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
     of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
     (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
     (C, n, n/2+1) int16; z, noise (n_sim, C, n, n), u (n_bands, n_fd, C, n, n)
-    in the working type.  Returns (dict of numpy arrays, per-map stats)."""
+    in the working type, or all three None with n_sim and n_fd given (the
+    library then draws them from opts `seed`).  Returns (dict of numpy arrays,
+    per-map stats)."""
     import torch
     handle = handle or default_handle()
     C, n, _ = Ninv.shape
     m = WfMap(d=_ptr(d), mask=_ptr(mask), Ninv=_ptr(Ninv), P=_ptr(P))
     nb = int(n_bands)
-    bi = WfBandpowerIn(n_bands=nb, n_sim=int(z.shape[0]), n_fd=int(u.shape[1]), pad_=0,
+    J = int(z.shape[0]) if z is not None else int(n_sim)
+    F = int(u.shape[1]) if u is not None else int(n_fd)
+    bi = WfBandpowerIn(n_bands=nb, n_sim=J, n_fd=F, pad_=0,
                        band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u))
-    nmaps = 1 + int(z.shape[0]) + nb * int(u.shape[1])
+    nmaps = 1 + J + nb * F
     arrs = {k: np.zeros(sz) for k, sz in (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb),
                                           ("cov", nb * nb), ("theta_hat", nb), ("cov_E", nb * nb),
                                           ("E_maps", nmaps * nb))}

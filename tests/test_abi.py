@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_1810_00503_gb300 import wf
 from tests.helpers import ensure_lib
 
@@ -30,14 +32,62 @@ def test_opts_default_and_last_error_need_no_gpu():
     o = wf.WfOpts()
     L.wf_opts_default(ctypes.byref(o))
     assert (o.lbfgs_m, o.max_iter, o.gtol_rel, o.check_every, o.use_graphs) == (10, 10000, 1e-6, 16, 1)
+    assert (o.line_search, o.c1, o.c2, o.seed) == (wf.WF_LS_EXACT, 1e-4, 0.9, 0)
+    assert ctypes.sizeof(o) == 80  # layout of wf_opts in include/wf.h
     assert isinstance(L.wf_last_error(), bytes)
 
 
 def test_null_arguments_are_rejected_without_touching_the_device():
     L = ensure_lib()
-    assert L.wf_create(None) == 1
+    assert L.wf_create(None, 0) == 1
     assert b"null" in L.wf_last_error()
     out = ctypes.c_void_p()
     # null handle is rejected before any CUDA call
     assert L.wf_problem_create(None, None, 1, 32, 1, 1, 0, 10, None, ctypes.byref(out)) == 1
     assert L.wf_eval(None, None, None, None, None) == 1
+
+
+def test_wf_opts_layout_matches_the_header():
+    """Compile a tiny C program against include/wf.h and compare the field
+    offsets of wf_opts with the binding's."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    fields = [f[0] for f in wf.WfOpts._fields_]
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"wf.h\"\nint main(void){\n"
+    src += 'printf("%zu\\n", sizeof(wf_opts));\n'
+    for f in fields:
+        src += f'printf("%zu\\n", offsetof(wf_opts, {f}));\n'
+    src += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call([cc, "-I", os.path.join(root, "include"), "-I", "/usr/local/cuda/include", c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert out[0] == ctypes.sizeof(wf.WfOpts)
+    assert out[1:] == [getattr(wf.WfOpts, f).offset for f in fields]
+
+
+def test_band_table_from_edges_matches_brute_force():
+    """wf_band_table (host code in the library) against a loop over modes."""
+    ensure_lib()
+    import numpy as np
+    for n, C, kscale in ((16, 1, 1.0), (32, 2, 0.5), (64, 1, 3.0)):
+        edges = np.array([1.0, 2.5, 4.0, 7.5, 11.0, 20.0])
+        got = wf.band_table(n, edges, C=C, kscale=kscale)
+        want = np.full((C, n, n // 2 + 1), -1, dtype=np.int16)
+        for j in range(n):
+            ky = j if j < n // 2 else j - n
+            for kx in range(n // 2 + 1):
+                k = kscale * np.hypot(kx, ky)
+                for lb in range(len(edges) - 1):
+                    if edges[lb] <= k < edges[lb + 1]:
+                        want[:, j, kx] = lb
+        assert np.array_equal(got, want)
+    with pytest.raises(wf.WfError, match="EINVAL"):
+        wf.band_table(16, [2.0, 1.0])

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import wf_oracle as O  # noqa: E402
-from paper_1810_00503_gb300 import synth  # noqa: E402
+from paper_1810_00503_gb300 import synth, wf  # noqa: E402
 from tests.helpers import ensure_lib, make_problem, rel, rfft_u, to_dev  # noqa: E402
 
 
@@ -176,3 +176,45 @@ def test_mixed_shear_eb_256_within_1e4():
     zs, info = O.map_solve(host["d"][0], host["W"][0], host["P"][0], gtol_rel=1e-11, max_iter=20000)
     err = rel(res.s[0].cpu().numpy(), rfft_u(zs))
     assert err <= 1e-4, (err, res.stats)
+
+
+def test_wolfe_fp64_density_32_matches_dense_wiener_filter():
+    inp = synth.density_small(32, seed=0)
+    prob, host = make_problem([inp], "fp64")
+    res = prob.solve(gtol_rel=1e-12, max_iter=5000, line_search=wf.WF_LS_WOLFE)
+    assert res.stats[0]["status"] == "WF_OK", res.stats
+    zs = O.dense_wf_whitened(host["d"][0], host["W"][0], host["P"][0])
+    assert rel(res.s[0].cpu().numpy(), rfft_u(zs)) <= 1e-10
+
+
+def test_wolfe_iterates_follow_the_textbook_search():
+    """Five L-BFGS iterations with the strong Wolfe search: the device runs
+    Alg. 3.5/3.6 on the closed-form line model, the oracle on true objective
+    evaluations.  Both accept the same trial steps; inside a zoom the oracle's
+    interpolated step carries the rounding of chi^2 differences (chi^2 ~ 1e3
+    against changes a few orders smaller), so the iterates agree to ~1e-8,
+    while one different accept/reject decision would move them by ~1e-2."""
+    inp = synth.shear_eb(32, seed=4)
+    prob, host = make_problem([inp], "fp64")
+    for k in (1, 2, 5):
+        res = prob.solve(gtol_rel=0.0, max_iter=k, line_search=wf.WF_LS_WOLFE, use_graphs=0)
+        zk, info = O.map_solve(host["d"][0], host["W"][0], host["P"][0], gtol_rel=0.0, max_iter=k)
+        assert info["iters"] == k and res.stats[0]["iters"] == k
+        assert rel(res.s[0].cpu().numpy(), rfft_u(zk)) <= 1e-7, k
+
+
+def test_wolfe_mixed_shear_eb_256_within_1e4():
+    inp = synth.shear_eb(256, seed=2)
+    prob, host = make_problem([inp], "mixed")
+    res = prob.solve(gtol_rel=1e-6, max_iter=4000, refresh_every=64, line_search=wf.WF_LS_WOLFE)
+    zs, info = O.map_solve(host["d"][0], host["W"][0], host["P"][0], gtol_rel=1e-11, max_iter=6000)
+    assert rel(res.s[0].cpu().numpy(), rfft_u(zs)) <= 1e-4, res.stats
+
+
+@pytest.mark.parametrize("bad", [dict(line_search=2), dict(line_search=1, c1=0.5, c2=0.4),
+                                 dict(line_search=1, c1=0.0), dict(line_search=1, c2=1.0)])
+def test_bad_line_search_options_rejected(bad):
+    inp = synth.density_small(16, seed=1)
+    prob, host = make_problem([inp], "fp64")
+    with pytest.raises(wf.WfError, match="EINVAL"):
+        prob.solve(max_iter=3, **bad)

@@ -2,6 +2,8 @@
 textbook DFT definitions and closed forms, exact identities of a quadratic,
 Woodbury agreement of two independent dense Wiener-filter forms, and analytic
 band terms for an unmasked map with homogeneous noise."""
+import os
+
 import numpy as np
 import pytest
 
@@ -235,3 +237,45 @@ def test_band_amplitude_derivative_matches_finite_differences(C):
         dn = np.where(bands == l, np.exp(-h), 1.0) * inp.P
         fd = (O.chi2(z, d, W, up) - O.chi2(z, d, W, dn)) / (2 * h)
         assert abs(fd - an[l]) <= 1e-6 * max(abs(an).max(), 1.0), (l, fd, an[l])
+
+
+# ---------------------------------------------------------------------------
+# Counter-based normal deviates (oracle/philox.py)
+# ---------------------------------------------------------------------------
+def _kat_rows():
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append([int(w, 16) for w in line.split()])
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    from oracle.philox import philox4x32_10
+    rows = _kat_rows()
+    assert len(rows) == 3
+    for r in rows:
+        out = philox4x32_10([np.array([c]) for c in r[:4]], r[4:6])
+        assert [int(o[0]) for o in out] == r[6:10]
+
+
+def test_philox_normals_box_muller_pairs_and_moments():
+    from oracle.philox import MASK32, normals, philox4x32_10
+    z = normals(11, 3, 400000)
+    # moments of N(0, 1) within 6 sigma of their sampling error
+    n = z.size
+    assert abs(z.mean()) < 6 / np.sqrt(n)
+    assert abs(z.var() - 1) < 6 * np.sqrt(2 / n)
+    assert abs(np.mean(z ** 4) - 3) < 6 * np.sqrt(96 / n)
+    # a pair (2j, 2j+1) lies on the circle of radius sqrt(-2 ln u1) of block j
+    j = 12345
+    x = philox4x32_10((np.array([j]), np.array([0]), np.array([3]), np.array([0])), (11, 0))
+    u1 = ((int(x[0][0]) >> 5) * 67108864.0 + (int(x[1][0]) >> 6) + 0.5) * 2.0 ** -53
+    assert abs(z[2 * j] ** 2 + z[2 * j + 1] ** 2 + 2 * np.log(u1)) < 1e-12
+    # offsets address the same stream; streams and seeds differ
+    assert np.array_equal(normals(11, 3, 10, offset=2 * j), z[2 * j: 2 * j + 10])
+    assert not np.allclose(normals(11, 4, 10), z[:10])
+    assert not np.allclose(normals(12, 3, 10), z[:10])
+    assert MASK32 == 2 ** 32 - 1
