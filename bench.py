@@ -156,6 +156,37 @@ def algorithmic_bytes(n, m, elt=4):
             "qdots": m * V}
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_lb_comb_dram_traffic.txt")
+TRAFFIC_SOURCES = ["paper_1810_00503_gb300/csrc/wf_lbfgs.cuh", "paper_1810_00503_gb300/csrc/wf_internal.h"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, maps):
+    """DRAM bytes of one launch of `kernel` over `maps` maps, from the committed
+    ncu capture (dram__bytes_read.sum + dram__bytes_write.sum per map of a
+    smaller batch; the kernel streams every vector once, so traffic scales with
+    the maps).  None when no capture exists for this kernel or the kernel's
+    source has changed since it was taken."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                kv[k] = v
+        if kv.get("kernel") != kernel or kv.get("source_sha256") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_map"]) * maps
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def run_ours(args, rank, world, dev):
     import torch
     from paper_1810_00503_gb300 import wf
@@ -458,7 +489,7 @@ def main():
             "dtype": "f32", "data": "synthetic", "config": config(args, world),
             "gpu_launches": 6 * K,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                         "frac": achieved / hbm, "traffic": measured_traffic(dom, B), "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": ab[dom] * B,
                          "kernel_ms": kms,
                          "iteration_frac": sum(ab[k] for k in names[:5]) * B
