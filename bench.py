@@ -308,6 +308,24 @@ def run_bandpower(args, dev, n_sim=100, n_bands=20, n_fd=1):
             "theta_hat_over_fid_median": float(np.median(res["theta_hat"] / res["theta_fid"]))}
 
 
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64
+
+
+def iteration_flops(n, m):
+    """FP64 arithmetic of one L-BFGS iteration on one n x n map (C = 1), counted
+    as 5 L log2 L per complex FFT of length L: two real 2-D transforms (n/2
+    column FFTs of length n and n row FFTs of length n/2 each); 5m + 9 complex
+    dot products or real-coefficient axpys per packed value, 4 flops each
+    (comb: 2m + 1 dots and 2m + 3 axpys; qdots: m - 1 dots; forward column
+    stage: 5 dots and q = 2 (p - a)); about 10 flops per value for the per-mode
+    and per-pixel steps."""
+    import math
+    h = n // 2
+    fft = 5 * (h * n * math.log2(n) + n * h * math.log2(h))
+    vals = n * h
+    return 2 * fft + vals * (4 * (5 * m + 9) + 10)
+
+
 def run_fp64_reference(args, dev, gtol=1e-6):
     """The plain single-map FP64 GPU path on map 0 of the workload: iteration
     throughput, and one solve to ||g|| / ||g0|| < gtol compared with the mixed
@@ -354,10 +372,15 @@ def run_fp64_reference(args, dev, gtol=1e-6):
     err = float(np.linalg.norm(a - b) / np.linalg.norm(a))
     p64.close()
     p32.close()
+    flops = iteration_flops(n, args.m)
+    achieved = flops / (it_ms / 1000.0) / 1e12
     return {"fp64_single_map_evals_per_s": 1000.0 / it_ms, "fp64_single_map_ms_per_iteration": it_ms,
             "fp64_single_map_solve_s": t64, "fp64_iterations": r64.stats[0]["iters"],
             "mixed_single_map_solve_s": t32, "mixed_iterations": r32.stats[0]["iters"],
             "gtol_rel": gtol, "mixed_vs_fp64_rel_l2": err,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_iteration": flops,
+                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)"},
             "note": "map 0 of the workload; the batched mixed path's per-map cost is ms_per_step / maps"}
 
 

@@ -263,15 +263,21 @@ wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
  * work); WF_EINVAL for bad sizes or edges that do not increase. */
 wf_status wf_band_table(int n, int C, const double* edges, int n_bands, double kscale, int16_t* out);
 
-/* Inputs of the band-power estimator.  All pointers are DEVICE pointers.  The
- * random fields z, noise and u are either all supplied by the caller (any
- * generator, working type) or all NULL: then the call draws them on the device
- * with wf_normal_draw's generator from opts->seed, z from stream 0, noise
- * from stream 1 (scaled by Ninv^-1/2 on observed pixels) and u from stream 2,
- * deviate i of each being element i of the flattened array. */
+/* Inputs of the band-power estimator.  Pointers are DEVICE pointers except
+ * sim_index.  The random fields z, noise and u are either all supplied by the
+ * caller (any generator, working type) or all NULL: then the call draws them
+ * on the device with wf_normal_draw's generator from opts->seed.  With
+ * npix = C n^2 and g the global index of a simulation (sim_index[j], or j):
+ *   z of simulation g:      stream 0, deviates g npix .. (g + 1) npix - 1
+ *   noise of simulation g:  stream 1, the same deviates times Ninv^-1/2 on
+ *                           observed pixels (0 on masked ones)
+ *   u of band l for the Fisher map reusing simulation g: stream 2, deviates
+ *                           (g n_bands + l) npix .. + npix - 1
+ * so a simulation's fields do not depend on how simulations are split over
+ * calls or GPUs. */
 typedef struct {
   int n_bands;            /* bands, ids 0 .. n_bands-1 (1..64) */
-  int n_sim;              /* noise-bias simulations (>= 2) */
+  int n_sim;              /* noise-bias simulations (>= 1; cov_E needs >= 2, else NaN) */
   int n_fd;               /* Fisher simulations per band, 0..n_sim; the j-th reuses simulation j.
                              0 (a rank of a multi-GPU run that owns no Fisher map) leaves
                              fisher, cov and theta_hat as NaN */
@@ -280,6 +286,8 @@ typedef struct {
   const void* z;          /* [n_sim][C][n][n] white signal fields, N(0, 1) */
   const void* noise;      /* [n_sim][C][n][n] noise realisations with variance 1/Ninv */
   const void* u;          /* [n_bands][n_fd][C][n][n] white fields for the Fisher signals */
+  const long long* sim_index;  /* HOST [n_sim] global index (>= 0) of each simulation, used by
+                                  the device draws; NULL = 0 .. n_sim-1 */
 } wf_bandpower_in;
 
 /* Outputs of the band-power estimator: HOST arrays, written. */

@@ -80,7 +80,7 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
     double c = 0.0;
     for (int j = 0; j < J; ++j)
       c += (Eall[(size_t)(1 + j) * nb + l] - o_b[l]) * (Eall[(size_t)(1 + j) * nb + lp] - o_b[lp]);
-    o_cE[idx] = J > 1 ? c / (J - 1) : 0.0;
+    o_cE[idx] = J > 1 ? c / (J - 1) : NAN;
   }
   __syncthreads();
   // Gauss-Jordan elimination with partial pivoting on [F | I]
@@ -165,12 +165,18 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     return wf_fail(WF_EINVAL, "bandpower_estimate: the data map needs d, mask, Ninv and P");
   const int nb = in->n_bands, J = in->n_sim, nfd = in->n_fd;
   if (nb < 1 || nb > 64) return wf_fail(WF_EINVAL, "bandpower_estimate: n_bands = %d outside [1, 64]", nb);
-  if (J < 2) return wf_fail(WF_EINVAL, "bandpower_estimate: n_sim = %d (need >= 2)", J);
+  if (J < 1) return wf_fail(WF_EINVAL, "bandpower_estimate: n_sim = %d (need >= 1)", J);
   if (nfd < 0 || nfd > J) return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd = %d outside [0, n_sim]", nfd);
   if (!in->band) return wf_fail(WF_EINVAL, "bandpower_estimate: null band table");
   const bool draw = !in->z && !in->noise && !in->u;  // fields drawn here from opts->seed
   if (!draw && (!in->z || !in->noise || (nfd > 0 && !in->u)))
     return wf_fail(WF_EINVAL, "bandpower_estimate: supply all random fields (z, noise, u) or none");
+  if (in->sim_index) {
+    const unsigned long long lim = (1ull << 62) / ((unsigned long long)C * n * n * (nb + 1));
+    for (int j = 0; j < J; ++j)
+      if (in->sim_index[j] < 0 || (unsigned long long)in->sim_index[j] >= lim)
+        return wf_fail(WF_EINVAL, "bandpower_estimate: sim_index[%d] = %lld out of range", j, in->sim_index[j]);
+  }
   if (!out->theta_fid || !out->E || !out->bias || !out->fisher || !out->cov || !out->theta_hat || !out->cov_E)
     return wf_fail(WF_EINVAL, "bandpower_estimate: null output array");
   if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "bandpower_estimate: bad dtype");
@@ -224,9 +230,17 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     if (rs == WF_OK) { sc.add(zb); rs = wf_alloc(h, &nb_, npix * J * welt, "drawn noise"); }
     if (rs == WF_OK) { sc.add(nb_); if (nF > 0) rs = wf_alloc(h, &ub, npix * nF * welt, "drawn Fisher fields"); }
     if (rs == WF_OK && ub) sc.add(ub);
-    if (rs == WF_OK) rs = wf_draw_normal(o.seed, 0, 0, npix * J, precision == WF_FP64, zb, nullptr, st);
-    if (rs == WF_OK) rs = wf_draw_normal(o.seed, 1, 0, npix * J, precision == WF_FP64, nb_, psim->w, st);
-    if (rs == WF_OK && nF > 0) rs = wf_draw_normal(o.seed, 2, 0, npix * nF, precision == WF_FP64, ub, nullptr, st);
+    const int f64 = precision == WF_FP64;
+    for (int j = 0; j < J && rs == WF_OK; ++j) {  // simulation j: global index g, deviates g npix ..
+      const unsigned long long g = in->sim_index ? (unsigned long long)in->sim_index[j] : (unsigned long long)j;
+      rs = wf_draw_normal(o.seed, 0, g * npix, npix, f64, (char*)zb + j * npix * welt, nullptr, st);
+      if (rs == WF_OK)
+        rs = wf_draw_normal(o.seed, 1, g * npix, npix, f64, (char*)nb_ + j * npix * welt,
+                            (const char*)psim->w + j * npix * welt, st);
+      for (int l = 0; l < nb && j < nfd && rs == WF_OK; ++l)  // Fisher map (l, j) reuses simulation j
+        rs = wf_draw_normal(o.seed, 2, (g * nb + l) * npix, npix, f64, (char*)ub + ((size_t)l * nfd + j) * npix * welt,
+                            nullptr, st);
+    }
     if (rs != WF_OK) { free(maps); return rs; }
     zin = zb;
     nzin = nb_;

@@ -39,6 +39,10 @@
 #ifndef WF_COLFWD_PF
 #define WF_COLFWD_PF 1
 #endif
+// p and g values the forward column stage loads per batch in its epilogue.
+#ifndef WF_COLFWD_EB
+#define WF_COLFWD_EB 16
+#endif
 
 // Resident blocks per SM requested from the compiler for the FFT-stage kernels.
 // FP32: three blocks of 256 threads (85 registers a thread; the radix-16 passes

@@ -268,16 +268,19 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
   const int h = g.h, B = gridDim.y, m = lb.m;
   const V2<T>* ring = (const V2<T>*)lb.ring;
   const int nx = M->next, np = M->npairs, head = M->head;
-  int sls[WF_MAXM];
-  int nvec = 0;
-  for (int q = 0; q < np; ++q) {
-    const int sl = (head - q + m) % m;
-    if (sl != nx) sls[nvec++] = sl;
+  __shared__ const VT* qv[WF_MAXM];  // the stored Q other than q, newest first
+  const int nvec = np - ((head - nx + m) % m < np ? 1 : 0);
+  if (tid == 0) {
+    int v = 0;
+    for (int q = 0; q < np; ++q) {
+      const int sl = (head - q + m) % m;
+      if (sl == nx) continue;
+      qv[v] = (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz);
+      ids[v++] = WF_SLOT_QQI + sl;
+    }
   }
   for (int v = 0; v < nvec; ++v) pdot[v * WF_COMB_THREADS + tid] = 0.f;
-  if (tid == 0)
-    for (int v = 0; v < nvec; ++v) ids[v] = WF_SLOT_QQI + sls[v];
-  auto qvec = [&](int sl, size_t c0) { return (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0); };
+  __syncthreads();
   for (int cg = 0; cg < WF_STREAM_GROUP; ++cg) {
     const size_t c0 = ((size_t)blockIdx.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
     if (c0 >= vsz) break;
@@ -300,7 +303,7 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
         return (float)(col0[i] ? d0 : 2.0 * d0);
       }
     };
-    const VT* Qn = qvec(nx, c0);
+    const VT* Qn = (const VT*)(ring + ((size_t)(m + nx) * B + b) * vsz + c0);
     VT qr[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
@@ -310,7 +313,7 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
       VT x[U][NV];
 #pragma unroll
       for (int v = 0; v < U; ++v) {
-        const VT* Qv = qvec(sls[w + v < nvec ? w + v : w], c0);
+        const VT* Qv = qv[w + v < nvec ? w + v : w] + c0 / VW;
 #pragma unroll
         for (int i = 0; i < NV; ++i)
           if (ok[i] && w + v < nvec) x[v][i] = Qv[u[i]];
@@ -387,7 +390,7 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
 #else
   wf_col_fwd_front<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, sp_ + (size_t)b * sp_stride, buf, s_tw,
                          tw_);
-  constexpr int EB = WF_EMAX;
+  constexpr int EB = WF_COLFWD_EB;
 #endif
 #pragma unroll
   for (int i0 = 0; i0 < WF_EMAX; i0 += EB) {

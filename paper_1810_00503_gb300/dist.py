@@ -73,3 +73,18 @@ def reduce_bandpower(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int, th
         dist.all_reduce(part, group=group)
         dist.broadcast(e0, src=0, group=group)
     return combine(part.numpy(), e0.numpy(), np.asarray(theta_fid, dtype=np.float64))
+
+
+def estimate_on_rank(d, mask, Ninv, P, band, n_bands, n_sim, n_fd, world, rank, seed, group=None, **opts):
+    """One band-power estimate spread over `world` ranks, this rank's part:
+    bandpower_estimate on the rank's simulations with fields drawn on its GPU
+    (Philox keyed by each simulation's global index, so every simulation has
+    the same fields whatever the split), then the all-reduce of the partial
+    sums.  Returns (estimate, this rank's per-map stats); the estimate is the
+    same on every rank and equals the single-process one."""
+    from . import wf
+    sims, (fd_lo, fd_hi) = assignment(n_sim, n_fd, world, rank)
+    res, stats = wf.bandpower_estimate(d, mask, Ninv, P, band, n_bands, None, None, None, n_sim=len(sims),
+                                       n_fd=fd_hi - fd_lo, sim_index=sims, seed=seed, **opts)
+    est = reduce_bandpower(res["E_maps"], len(sims), n_bands, fd_hi - fd_lo, res["theta_fid"], group)
+    return est, stats

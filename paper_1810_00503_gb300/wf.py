@@ -50,7 +50,7 @@ class WfSolveStats(ctypes.Structure):
 class WfBandpowerIn(ctypes.Structure):
     _fields_ = [("n_bands", ctypes.c_int), ("n_sim", ctypes.c_int), ("n_fd", ctypes.c_int),
                 ("pad_", ctypes.c_int), ("band", ctypes.c_void_p), ("z", ctypes.c_void_p),
-                ("noise", ctypes.c_void_p), ("u", ctypes.c_void_p)]
+                ("noise", ctypes.c_void_p), ("u", ctypes.c_void_p), ("sim_index", ctypes.c_void_p)]
 
 
 class WfBandpowerOut(ctypes.Structure):
@@ -233,14 +233,15 @@ def normal_draw(seed, count, stream_id=0, offset=0, dtype=None, out=None, stream
 
 
 def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",
-                       handle=None, stream=None, n_sim=None, n_fd=None, **opts):
+                       handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None, **opts):
     """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
     of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
     (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
     (C, n, n/2+1) int16; z, noise (n_sim, C, n, n), u (n_bands, n_fd, C, n, n)
     in the working type, or all three None with n_sim and n_fd given (the
-    library then draws them from opts `seed`).  Returns (dict of numpy arrays,
-    per-map stats)."""
+    library then draws them from opts `seed`; sim_index gives the global index
+    of each simulation, so that the draws do not depend on how simulations are
+    split over calls).  Returns (dict of numpy arrays, per-map stats)."""
     import torch
     handle = handle or default_handle()
     C, n, _ = Ninv.shape
@@ -248,8 +249,14 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
     nb = int(n_bands)
     J = int(z.shape[0]) if z is not None else int(n_sim)
     F = int(u.shape[1]) if u is not None else int(n_fd)
+    idx = None
+    if sim_index is not None:
+        idx = np.ascontiguousarray(sim_index, dtype=np.int64)
+        if idx.shape != (J,):
+            raise ValueError("sim_index needs one entry per simulation")
     bi = WfBandpowerIn(n_bands=nb, n_sim=J, n_fd=F, pad_=0,
-                       band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u))
+                       band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u),
+                       sim_index=None if idx is None else idx.ctypes.data)
     nmaps = 1 + J + nb * F
     arrs = {k: np.zeros(sz) for k, sz in (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb),
                                           ("cov", nb * nb), ("theta_hat", nb), ("cov_E", nb * nb),

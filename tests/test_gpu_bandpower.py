@@ -73,7 +73,7 @@ def test_bandpower_rejects_bad_counts():
         wf.bandpower_estimate(z[0], torch.ones((n, n), dtype=torch.uint8, device="cuda"), z[0] + 1,
                               torch.ones((1, n, n // 2 + 1), dtype=dt, device="cuda"),
                               torch.zeros((1, n, n // 2 + 1), dtype=torch.int16, device="cuda"), 2,
-                              z, z, torch.zeros((2, 1, 1, n, n), dtype=dt, device="cuda"))
+                              z, z, torch.zeros((2, 2, 1, n, n), dtype=dt, device="cuda"))  # n_fd > n_sim
 
 
 def test_sharded_calls_reduce_to_the_single_call():
