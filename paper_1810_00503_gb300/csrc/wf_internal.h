@@ -24,7 +24,7 @@
 #define WF_COMB_CHUNK (WF_COMB_THREADS * WF_COMB_EPT)
 // Chunks a streaming block walks in turn; one partial-sum entry per group.
 #ifndef WF_STREAM_GROUP
-#define WF_STREAM_GROUP 4
+#define WF_STREAM_GROUP 8
 #endif
 // FFT stages of the L-BFGS iteration on ping-pong passes with direct global
 // input/output (1) or on in-place shared-memory passes (0).

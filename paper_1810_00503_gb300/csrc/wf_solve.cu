@@ -54,8 +54,10 @@ struct WfSolver {
 
 enum { WF_PH_ITER = 0, WF_PH_REFRESH = 1 };
 
-#define WF_SW 4  // warps (maps) per block of the scalar kernel
+#define WF_SW 1                        // warps (maps) per block of the scalar kernel
+#define WF_SCAL_SLOTS (6 + 3 * WF_MAXM)  // partial-sum slots one scalar step reads at most
 
+// Sum over the nb block partials of one slot (every lane gets the total).
 __device__ __forceinline__ double wf_warp_slot(const double* pb, int slot, int nb, int maxblk) {
   const int lane = threadIdx.x & 31;
   double v = 0.0;
@@ -65,47 +67,78 @@ __device__ __forceinline__ double wf_warp_slot(const double* pb, int slot, int n
   return v;
 }
 
-// Two-loop recursion on coefficients: r = H_k g expressed over the basis
-// {g, P_i, Q_i}; the direction is p = -r.
-__device__ void wf_two_loop(WfLbMap& M, int m) {
+__device__ __forceinline__ double wf_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block partials of ns slots: out[k] = sum_i pb[slots[k] * maxblk + i], i < cnt[k].
+// Every lane first sums its stride-32 share of every slot (independent loads),
+// then lane k adds the 32 shares of slot k in lane order: a fixed order, so
+// the result is deterministic.
+__device__ void wf_gather_slots(const double* pb, int maxblk, const int* slots, const int* cnt, int ns,
+                                double (*red)[33], double* out) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < ns; ++k) {
+    const double* src = pb + (size_t)slots[k] * maxblk;
+    double v = 0.0;
+    for (int i = lane; i < cnt[k]; i += 32) v += src[i];
+    red[k][lane] = v;
+  }
+  __syncwarp();
+  for (int k = lane; k < ns; k += 32) {
+    double v = 0.0;
+    for (int l = 0; l < 32; ++l) v += red[k][l];
+    out[k] = v;
+  }
+  __syncwarp();
+}
+
+// Two-loop recursion on coefficients (Nocedal & Wright, Alg. 7.4): r = H_k g
+// expressed over the basis {g, P_i, Q_i}; the direction is p = -r.  Lane l
+// holds the coefficients of history slot l (m <= 32); each step of the two
+// loops is one warp sum over the stored pairs.  Called by all 32 lanes.
+__device__ void wf_two_loop(WfLbMap& M, int m, int lane) {
   const int np = M.npairs, head = M.head;
-  double cP[WF_MAXM], cQ[WF_MAXM], aa[WF_MAXM];
-  int W[WF_MAXM];
-  for (int i = 0; i < m; ++i) { cP[i] = 0.0; cQ[i] = 0.0; }
-  for (int q = 0; q < np; ++q) W[q] = (head - q + m) % m;
-  double cg = 1.0;
+  const bool act = np > 0 && lane < m && (head - lane + m) % m < np;  // slot `lane` holds a stored pair
+  double cP = 0.0, cQ = 0.0, aa = 0.0, cg = 1.0;
   for (int q = 0; q < np; ++q) {  // newest to oldest
-    const int i = W[q];
-    double d = cg * M.gP[i];
-    for (int u = 0; u < np; ++u) {
-      const int l = W[u];
-      d += cP[l] * M.PP[i * WF_MAXM + l] + cQ[l] * M.PQ[i * WF_MAXM + l];
-    }
+    const int i = (head - q + m) % m;
+    const double t = act ? cP * M.PP[i * WF_MAXM + lane] + cQ * M.PQ[i * WF_MAXM + lane] : 0.0;
+    const double d = cg * M.gP[i] + wf_warp_sum(t);
     const double ai = M.alpha[i];
     const double rho = 1.0 / (ai * ai * M.PQ[i * WF_MAXM + i]);
     const double a = rho * ai * d;
-    aa[q] = a;
-    cQ[i] -= a * ai;
+    if (lane == i) {
+      aa = a;
+      cQ -= a * ai;
+    }
   }
   double gamma = 1.0;
   if (np > 0) gamma = M.PQ[head * WF_MAXM + head] / M.QQ[head * WF_MAXM + head];
   cg *= gamma;
-  for (int q = 0; q < np; ++q) { cP[W[q]] *= gamma; cQ[W[q]] *= gamma; }
+  cP *= gamma;
+  cQ *= gamma;
   for (int q = np - 1; q >= 0; --q) {  // oldest to newest
-    const int i = W[q];
-    double d = cg * M.gQ[i];
-    for (int u = 0; u < np; ++u) {
-      const int l = W[u];
-      d += cP[l] * M.PQ[l * WF_MAXM + i] + cQ[l] * M.QQ[i * WF_MAXM + l];
-    }
+    const int i = (head - q + m) % m;
+    const double t = act ? cP * M.PQ[lane * WF_MAXM + i] + cQ * M.QQ[i * WF_MAXM + lane] : 0.0;
+    const double d = cg * M.gQ[i] + wf_warp_sum(t);
     const double ai = M.alpha[i];
     const double rho = 1.0 / (ai * ai * M.PQ[i * WF_MAXM + i]);
     const double beta = rho * ai * d;
-    cP[i] += ai * (aa[q] - beta);
+    if (lane == i) cP += ai * (aa - beta);
   }
-  M.dg = -cg;
-  for (int i = 0; i < m; ++i) { M.dP[i] = -cP[i]; M.dQ[i] = -cQ[i]; }
-  M.next = (head + 1) % m;
+  __syncwarp();  // every lane has read the old coefficients' Gram entries
+  if (lane == 0) {
+    M.dg = -cg;
+    M.next = (head + 1) % m;
+  }
+  if (lane < m) {
+    M.dP[lane] = -cP;
+    M.dQ[lane] = -cQ;
+  }
+  __syncwarp();
 }
 
 // Strong Wolfe step along p (Nocedal & Wright, Alg. 3.5, zoom Alg. 3.6) on the
@@ -152,11 +185,16 @@ __device__ double wf_wolfe_step(double d0, double c, double c1, double c2) {
   return a;
 }
 
+// One warp per map.  ITER: exact or Wolfe step along p, chi^2 and Gram-matrix
+// update of the new pair, convergence test, two-loop for the next direction.
+// REFRESH: true chi^2 and gradient dots after a full evaluation.
 __global__ void __launch_bounds__(32 * WF_SW)
 k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
-  __shared__ double S[WF_SW][WF_NSLOT];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x * WF_SW + w;
+  __shared__ double red[WF_SCAL_SLOTS][33];
+  __shared__ double S[WF_SCAL_SLOTS];
+  __shared__ int slots[WF_SCAL_SLOTS], cnt[WF_SCAL_SLOTS];
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x;
   if (b >= B) return;
   WfLbMap& M = st[b];
   const double* pb = part + (size_t)b * WF_NSLOT * A.maxblk;
@@ -166,150 +204,163 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
       if (lane == 0) M.pend_alpha = 0.0;
       return;
     }
-    const int np = M.npairs, head = M.head;
-    S[w][WF_SLOT_GG] = wf_warp_slot(pb, WF_SLOT_GG, A.ncomb, A.maxblk);
-    S[w][WF_SLOT_QQ] = wf_warp_slot(pb, WF_SLOT_QQ, A.ntile, A.maxblk);
-    S[w][WF_SLOT_PQ] = wf_warp_slot(pb, WF_SLOT_PQ, A.ntile, A.maxblk);
-    S[w][WF_SLOT_GQN] = wf_warp_slot(pb, WF_SLOT_GQN, A.ntile, A.maxblk);
-    S[w][WF_SLOT_GPN] = wf_warp_slot(pb, WF_SLOT_GPN, A.ntile, A.maxblk);
-    S[w][WF_SLOT_PP] = wf_warp_slot(pb, WF_SLOT_PP, A.ntile, A.maxblk);
-    for (int q = 0; q < np; ++q) {
-      const int sl = (head - q + m) % m;
-      S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ncomb, A.maxblk);
-      S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ncomb, A.maxblk);
-      S[w][WF_SLOT_QQI + sl] = wf_warp_slot(pb, WF_SLOT_QQI + sl, A.ncomb, A.maxblk);
+    const int np = M.npairs, head = M.head, nx = M.next;
+    // slot list: 0 GG, 1 QQ, 2 PQ, 3 GQN, 4 GPN, 5 PP, then per stored pair q:
+    // 6 + 3q GP, 7 + 3q GQ, 8 + 3q QQI (of slot (head - q) mod m)
+    if (lane == 0) {
+      const int fixed[6] = {WF_SLOT_GG, WF_SLOT_QQ, WF_SLOT_PQ, WF_SLOT_GQN, WF_SLOT_GPN, WF_SLOT_PP};
+      for (int k = 0; k < 6; ++k) {
+        slots[k] = fixed[k];
+        cnt[k] = k == 0 ? A.ncomb : A.ntile;
+      }
+      for (int q = 0; q < np; ++q) {
+        const int sl = (head - q + m) % m;
+        slots[6 + 3 * q] = WF_SLOT_GP + sl;
+        slots[7 + 3 * q] = WF_SLOT_GQ + sl;
+        slots[8 + 3 * q] = WF_SLOT_QQI + sl;
+        cnt[6 + 3 * q] = cnt[7 + 3 * q] = cnt[8 + 3 * q] = A.ncomb;
+      }
     }
     __syncwarp();
-    if (lane != 0) return;
-    const double* Sw = S[w];
-    const int nx = M.next;
-    const double pq = Sw[WF_SLOT_PQ], qq = Sw[WF_SLOT_QQ], gq = Sw[WF_SLOT_GQN];
-    const double gp = Sw[WF_SLOT_GPN], pp = Sw[WF_SLOT_PP], ggk = Sw[WF_SLOT_GG];
-    M.evals += 1;
-    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(gp) || !isfinite(ggk)) {
-      M.status = (isfinite(pq) && isfinite(gp) && isfinite(ggk)) ? WF_ELINESEARCH : WF_ENONFINITE;
-      M.active = 0;
-      M.pend_alpha = 0.0;
-      return;
-    }
-    // A8's curvature test s.y > 1e-12 |s| |y| with (s, y) = a (p, q): the pair
-    // would be unusable, and on this positive definite objective that only
-    // happens when rounding has taken over, so the map stops.
-    if (!(pq > 1e-12 * sqrt(pp * Sw[WF_SLOT_QQ]))) {
-      M.status = WF_ELINESEARCH;
-      M.active = 0;
-      M.pend_alpha = 0.0;
+    wf_gather_slots(pb, A.maxblk, slots, cnt, 6 + 3 * np, red, S);
+    const double ggk = S[0], qq = S[1], pq = S[2], gq = S[3], gp = S[4], pp = S[5];
+    // position of slot `lane` among the stored pairs (newest first), if stored
+    const int ql = (head - lane + m) % m;
+    const bool act = np > 0 && lane < m && ql < np;
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(gp) || !isfinite(ggk) ||
+        !(pq > 1e-12 * sqrt(pp * qq))) {
+      // no decrease along p, a non-finite value, or A8's curvature test
+      // s.y > 1e-12 |s| |y| failing (on this positive definite objective only
+      // when rounding has taken over): the map stops
+      if (lane == 0) {
+        M.evals += 1;
+        M.status = (isfinite(pq) && isfinite(gp) && isfinite(ggk)) ? WF_ELINESEARCH : WF_ENONFINITE;
+        M.active = 0;
+        M.pend_alpha = 0.0;
+      }
       return;
     }
     const double alpha = A.ls == WF_LS_WOLFE ? wf_wolfe_step(gp, pq, A.c1, A.c2) : -gp / pq;
-    M.chi2_prev = M.chi2;
-    M.chi2 = M.chi2 + alpha * gp + 0.5 * alpha * alpha * pq;
-    int W[WF_MAXM];
-    double gPk[WF_MAXM], gQk[WF_MAXM], rowPP[WF_MAXM], rowPQ[WF_MAXM];
-    for (int q = 0; q < np; ++q) {
-      W[q] = (head - q + m) % m;
-      gPk[W[q]] = Sw[WF_SLOT_GP + W[q]];
-      gQk[W[q]] = Sw[WF_SLOT_GQ + W[q]];
+    // Gram row of the new direction p = dg g + sum (dP_l P_l + dQ_l Q_l), from the old
+    // entries: lane i computes <p, P_i> and <p, Q_i> = <P_i, H p> for its stored slot i
+    double rowPP = 0.0, rowPQ = 0.0, gPk = 0.0, gQk = 0.0;
+    if (act) {
+      gPk = S[6 + 3 * ql];
+      gQk = S[7 + 3 * ql];
     }
-    // Gram row of the new direction p = dg g + sum (dP_l P_l + dQ_l Q_l), from the old entries.
-    for (int q = 0; q < np; ++q) {
-      const int i = W[q];
-      if (i == nx) continue;
-      double a = M.dg * gPk[i], c = M.dg * gQk[i];
+    if (act && lane != nx) {
+      const int i = lane;
+      double a = M.dg * gPk, c = M.dg * gQk;
       for (int u = 0; u < np; ++u) {
-        const int l = W[u];
+        const int l = (head - u + m) % m;
         a += M.dP[l] * M.PP[l * WF_MAXM + i] + M.dQ[l] * M.PQ[i * WF_MAXM + l];
         c += M.dP[l] * M.PQ[l * WF_MAXM + i] + M.dQ[l] * M.QQ[l * WF_MAXM + i];
       }
-      rowPP[i] = a;
-      rowPQ[i] = c;
+      rowPP = a;
+      rowPQ = c;
     }
-    for (int q = 0; q < np; ++q) {
-      const int i = W[q];
-      if (i == nx) continue;
-      M.PP[nx * WF_MAXM + i] = M.PP[i * WF_MAXM + nx] = rowPP[i];
-      M.PQ[nx * WF_MAXM + i] = rowPQ[i];  // <p, Q_i>
-      M.PQ[i * WF_MAXM + nx] = rowPQ[i];  // <P_i, H p> = <H P_i, p>
-      M.QQ[nx * WF_MAXM + i] = M.QQ[i * WF_MAXM + nx] = Sw[WF_SLOT_QQI + i];
+    __syncwarp();  // all reads of the old Gram entries are done
+    if (act && lane != nx) {
+      const int i = lane;
+      M.PP[nx * WF_MAXM + i] = M.PP[i * WF_MAXM + nx] = rowPP;
+      M.PQ[nx * WF_MAXM + i] = rowPQ;  // <p, Q_i>
+      M.PQ[i * WF_MAXM + nx] = rowPQ;  // <P_i, H p> = <H P_i, p>
+      const double qqi = S[8 + 3 * ql];
+      M.QQ[nx * WF_MAXM + i] = M.QQ[i * WF_MAXM + nx] = qqi;
+      // dot products of g_{k+1} = g_k + alpha q with the stored vectors
+      M.gP[i] = gPk + alpha * rowPQ;
+      M.gQ[i] = gQk + alpha * qqi;
     }
-    M.PP[nx * WF_MAXM + nx] = pp;
-    M.PQ[nx * WF_MAXM + nx] = pq;
-    M.QQ[nx * WF_MAXM + nx] = qq;
-    // dot products of g_{k+1} = g_k + alpha q with the stored vectors
-    for (int q = 0; q < np; ++q) {
-      const int i = W[q];
-      if (i == nx) continue;
-      M.gP[i] = gPk[i] + alpha * M.PQ[i * WF_MAXM + nx];
-      M.gQ[i] = gQk[i] + alpha * M.QQ[nx * WF_MAXM + i];
-    }
-    M.gP[nx] = gp + alpha * pq;
-    M.gQ[nx] = gq + alpha * qq;
-    double gg = ggk + 2.0 * alpha * gq + alpha * alpha * qq;
-    if (gg < 0.0) gg = 0.0;
-    M.gg = gg;
-    M.alpha[nx] = alpha;
-    M.pend_alpha = alpha;
-    M.pend_slot = nx;
-    M.head = nx;
-    M.npairs = np + 1 < m ? np + 1 : m;
-    M.next = (nx + 1) % m;
-    M.k += 1;
     bool done = false;
-    if (!isfinite(M.chi2) || !isfinite(gg)) { done = true; M.status = WF_ENONFINITE; }
-    else if (gg <= A.gtol2 * M.gg0) { done = true; }
-    else if (A.dchi2 > 0.0 && fabs(M.chi2 - M.chi2_prev) < A.dchi2) { done = true; }
-    else if (M.k >= A.max_iter) { done = true; M.status = WF_ENOTCONVERGED; }
-    if (done) {
-      M.active = 0;
-    } else {
-      wf_two_loop(M, m);
-      atomicAdd(nact, 1);
+    if (lane == 0) {
+      M.evals += 1;
+      M.chi2_prev = M.chi2;
+      M.chi2 = M.chi2 + alpha * gp + 0.5 * alpha * alpha * pq;
+      M.PP[nx * WF_MAXM + nx] = pp;
+      M.PQ[nx * WF_MAXM + nx] = pq;
+      M.QQ[nx * WF_MAXM + nx] = qq;
+      M.gP[nx] = gp + alpha * pq;
+      M.gQ[nx] = gq + alpha * qq;
+      double gg = ggk + 2.0 * alpha * gq + alpha * alpha * qq;
+      if (gg < 0.0) gg = 0.0;
+      M.gg = gg;
+      M.alpha[nx] = alpha;
+      M.pend_alpha = alpha;
+      M.pend_slot = nx;
+      M.head = nx;
+      M.npairs = np + 1 < m ? np + 1 : m;
+      M.next = (nx + 1) % m;
+      M.k += 1;
+      if (!isfinite(M.chi2) || !isfinite(gg)) { done = true; M.status = WF_ENONFINITE; }
+      else if (gg <= A.gtol2 * M.gg0) { done = true; }
+      else if (A.dchi2 > 0.0 && fabs(M.chi2 - M.chi2_prev) < A.dchi2) { done = true; }
+      else if (M.k >= A.max_iter) { done = true; M.status = WF_ENOTCONVERGED; }
+      if (done) M.active = 0;
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    __syncwarp();
+    if (!done) {
+      wf_two_loop(M, m, lane);
+      if (lane == 0) atomicAdd(nact, 1);
     }
     return;
   }
   // WF_PH_REFRESH: true chi^2 and gradient at the current state, exact dots.
   const int np = A.init ? 0 : M.npairs, head = M.head;
-  const double prior = wf_warp_slot(pb, WF_SLOT_PRIOR, A.ntile, A.maxblk);
-  const double data = wf_warp_slot(pb, WF_SLOT_DATA, A.nrb, A.maxblk);
-  const double gg = wf_warp_slot(pb, WF_SLOT_GG, A.ncomb, A.maxblk);
-  for (int q = 0; q < np; ++q) {
-    const int sl = (head - q + m) % m;
-    S[w][WF_SLOT_GP + sl] = wf_warp_slot(pb, WF_SLOT_GP + sl, A.ncomb, A.maxblk);
-    S[w][WF_SLOT_GQ + sl] = wf_warp_slot(pb, WF_SLOT_GQ + sl, A.ncomb, A.maxblk);
+  if (lane == 0) {
+    slots[0] = WF_SLOT_PRIOR;
+    cnt[0] = A.ntile;
+    slots[1] = WF_SLOT_DATA;
+    cnt[1] = A.nrb;
+    slots[2] = WF_SLOT_GG;
+    cnt[2] = A.ncomb;
+    for (int q = 0; q < np; ++q) {
+      const int sl = (head - q + m) % m;
+      slots[3 + 2 * q] = WF_SLOT_GP + sl;
+      slots[4 + 2 * q] = WF_SLOT_GQ + sl;
+      cnt[3 + 2 * q] = cnt[4 + 2 * q] = A.ncomb;
+    }
   }
   __syncwarp();
-  if (lane != 0) return;
-  if (A.init) {
-    M.k = 0;
-    M.npairs = 0;
-    M.head = -1;
-    M.next = 0;
-    M.status = WF_OK;
-    M.evals = 1;
-    M.gg0 = gg;
-    M.active = 1;
-    M.chi2_prev = prior + data;
-  } else {
-    M.evals += 1;
+  wf_gather_slots(pb, A.maxblk, slots, cnt, 3 + 2 * np, red, S);
+  const double prior = S[0], data = S[1], gg = S[2];
+  bool go = false;
+  if (lane == 0) {
+    if (A.init) {
+      M.k = 0;
+      M.npairs = 0;
+      M.head = -1;
+      M.next = 0;
+      M.status = WF_OK;
+      M.evals = 1;
+      M.gg0 = gg;
+      M.active = 1;
+      M.chi2_prev = prior + data;
+    } else {
+      M.evals += 1;
+    }
+    M.chi2 = prior + data;
+    M.gg = gg;
+    M.pend_alpha = 0.0;
+    if (M.active) {
+      for (int q = 0; q < np; ++q) {
+        const int sl = (head - q + m) % m;
+        M.gP[sl] = S[3 + 2 * q];
+        M.gQ[sl] = S[4 + 2 * q];
+      }
+      bool done = false;
+      if (!isfinite(M.chi2) || !isfinite(gg)) { done = true; M.status = WF_ENONFINITE; }
+      else if (gg <= A.gtol2 * M.gg0) { done = true; M.status = WF_OK; }
+      else if (M.k >= A.max_iter) { done = true; M.status = WF_ENOTCONVERGED; }
+      if (done) M.active = 0;
+      go = !done;
+    }
   }
-  M.chi2 = prior + data;
-  M.gg = gg;
-  M.pend_alpha = 0.0;
-  if (!M.active) return;
-  for (int q = 0; q < np; ++q) {
-    const int sl = (head - q + m) % m;
-    M.gP[sl] = S[w][WF_SLOT_GP + sl];
-    M.gQ[sl] = S[w][WF_SLOT_GQ + sl];
-  }
-  bool done = false;
-  if (!isfinite(M.chi2) || !isfinite(gg)) { done = true; M.status = WF_ENONFINITE; }
-  else if (gg <= A.gtol2 * M.gg0) { done = true; M.status = WF_OK; }
-  else if (M.k >= A.max_iter) { done = true; M.status = WF_ENOTCONVERGED; }
-  if (done) {
-    M.active = 0;
-  } else {
-    wf_two_loop(M, m);
-    atomicAdd(nact, 1);
+  go = __shfl_sync(0xffffffffu, go, 0);
+  __syncwarp();
+  if (go) {
+    wf_two_loop(M, m, lane);
+    if (lane == 0) atomicAdd(nact, 1);
   }
 }
 
