@@ -285,9 +285,20 @@ typedef struct {
   const int16_t* band;    /* [C][n][n/2+1] band id of each half-plane mode, -1 = none */
   const void* z;          /* [n_sim][C][n][n] white signal fields, N(0, 1) */
   const void* noise;      /* [n_sim][C][n][n] noise realisations with variance 1/Ninv */
-  const void* u;          /* [n_bands][n_fd][C][n][n] white fields for the Fisher signals */
+  const void* u;          /* [n_bands or n_fd_bands][n_fd][C][n][n] white fields for the Fisher signals */
   const long long* sim_index;  /* HOST [n_sim] global index (>= 0) of each simulation, used by
                                   the device draws; NULL = 0 .. n_sim-1 */
+  const int* fd_bands;    /* HOST [n_fd_bands] ascending band ids that get Fisher maps (NULL =
+                             every band).  The other bands' Fisher columns are interpolated
+                             (Sec. 3.1: the matrix is smooth and nearly translation invariant):
+                             between sampled s0 < l' < s1, F[l'+o][l'] = (1-t) F[s0+o][s0] +
+                             t F[s1+o][s1], t = (l'-s0)/(s1-s0), a term whose row leaves the
+                             matrix dropped; beyond the first or last sampled band the nearest
+                             sampled column is shifted.  u then has n_fd_bands rows. */
+  int n_fd_bands;
+  int trunc_bands;        /* zero F[l][l'] for l, l' < trunc_bands with |l - l'| > trunc_width */
+  int trunc_width;        /* (App. C: far off-diagonal EE terms, E bands first); 0, 0 = off */
+  int pad2_;
 } wf_bandpower_in;
 
 /* Outputs of the band-power estimator: HOST arrays, written. */
@@ -299,7 +310,8 @@ typedef struct {
   double* cov;            /* [n_bands * n_bands] F^-1 (eq. var) */
   double* theta_hat;      /* [n_bands] Theta_fid + F^-1 (E - b) (eq. eq:wfmv) */
   double* cov_E;          /* [n_bands * n_bands] sample covariance of E over the simulations */
-  double* E_maps;         /* optional (NULL = not written): [1 + n_sim + n_bands * n_fd][n_bands]
+  double* E_maps;         /* optional (NULL = not written): [1 + n_sim + n_F * n_fd][n_bands], n_F
+                             the bands with Fisher maps (n_bands or n_fd_bands),
                              E of every solved map (data, simulations, Fisher maps), for callers
                              that combine simulations from several GPUs */
 } wf_bandpower_out;
@@ -321,6 +333,22 @@ typedef struct {
 wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
                              const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
                              wf_solve_stats* stats);
+
+/* Iterated fiducial (Sec. 2.3, after eq. pilin): n_iter band-power estimates
+ * with the same random fields; between two, the fiducial P moves to the
+ * estimate band by band, P <- P q_l on the modes of band l with
+ * q_l = Theta_hat_l / Theta_fid,l kept in [q_min, q_max] (0 < q_min <= 1 <=
+ * q_max: the regularisation, no band power becomes zero or negative).  The
+ * paper starts from the true spectrum with every band scaled by U[0.01, 1] and
+ * finds one re-estimate enough (n_iter = 2).  data->P is the starting
+ * fiducial and is not modified; P_out (DEVICE, [C][n][n/2+1] in dtype, or
+ * NULL) receives the fiducial of the last estimate; theta_hat_hist (HOST
+ * [n_iter][n_bands] or NULL) every estimate's Theta_hat; out and stats are
+ * those of the last estimate.  Needs in->n_fd >= 1.  Synchronises. */
+wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
+                            const wf_bandpower_in* in, const wf_opts* opts, int n_iter, double q_min,
+                            double q_max, void* P_out, double* theta_hat_hist, wf_bandpower_out* out,
+                            wf_solve_stats* stats);
 
 /* Standard normal deviates on the device: out[k] = deviate offset + k of
  * (seed, stream_id), k < count, in dtype WF_F32 or WF_F64 (computed in FP64).

@@ -392,9 +392,54 @@ def band_signal(u, P, bands, band):
     return apply_A(u, Pl)
 
 
+def fisher_fill_columns(F, sampled):
+    """Fisher columns of unsampled bands from the sampled ones (Sec. 3.1: the
+    matrix is smooth and nearly translation invariant, so a few rows suffice and
+    the rest are interpolated).  Reading: column l' between sampled s0 < l' < s1
+    is F[l' + o][l'] = (1 - t) F[s0 + o][s0] + t F[s1 + o][s1] at every offset o,
+    t = (l' - s0) / (s1 - s0); a term whose row s + o falls outside the matrix is
+    dropped and the other weighted alone; before the first or after the last
+    sampled column the nearest one is shifted.  sampled: ascending band ids."""
+    nb = F.shape[0]
+    G = F.copy()
+    S = list(sampled)
+    for lp in range(nb):
+        if lp in S:
+            continue
+        lo = [s for s in S if s < lp]
+        hi = [s for s in S if s > lp]
+        if lo and hi:
+            s0, s1 = lo[-1], hi[0]
+            t = (lp - s0) / (s1 - s0)
+            terms = [(1.0 - t, s0), (t, s1)]
+        else:
+            terms = [(1.0, lo[-1] if lo else hi[0])]
+        for l in range(nb):
+            o = l - lp
+            acc, wsum = 0.0, 0.0
+            for wt, sc in terms:
+                if 0 <= sc + o < nb and wt > 0.0:
+                    acc += wt * F[sc + o, sc]
+                    wsum += wt
+            G[l, lp] = acc / wsum if wsum > 0.0 else 0.0
+    return G
+
+
+def fisher_truncate(F, n_trunc, width):
+    """Zero the Fisher terms far from the diagonal inside the leading n_trunc
+    bands (App. C: the EE block, E bands first), |l - l'| > width."""
+    G = F.copy()
+    for l in range(min(n_trunc, F.shape[0])):
+        for lp in range(min(n_trunc, F.shape[0])):
+            if abs(l - lp) > width:
+                G[l, lp] = 0.0
+    return G
+
+
 def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
-                   m=10, gtol_rel=1e-10, max_iter=20000):
-    """Simulation estimates of Sec. 2.5 on one data map (C = 1).
+                   m=10, gtol_rel=1e-10, max_iter=20000, fd_bands=None, trunc=(0, 0)):
+    """Simulation estimates of Sec. 2.5 on one data map (C = 1, or C = 2 for the
+    joint E/B case of App. C with separate band ids for the two channels).
 
     * E(d): eq. el on the MAP of the data.
     * b_l = mean_j E_l(MAP(d_j)), d_j = M (A z_j + n_j)        (eq. blmv)
@@ -405,7 +450,10 @@ def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
     * cov = F^-1 (eq. eq:var), and the sample covariance of E over the sims.
     z_sims, n_sims: (J, C, n, n) white signal fields and noise realisations.
     u_fd: (n_bands, J_fd, C, n, n) white fields for the Fisher perturbations;
-    J_fd <= J, and the j-th perturbation is added to sim j.
+    J_fd <= J, and the j-th perturbation is added to sim j.  fd_bands: the bands
+    given Fisher simulations (default all; u_fd then holds one row per listed
+    band), the other columns from fisher_fill_columns.  trunc = (n_trunc,
+    width): fisher_truncate before the inversion ((0, 0) = off).
     """
     W = mask[None] * Ninv
     theta = theta_fid(P, bands, n_bands)
@@ -420,18 +468,43 @@ def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
     E_s = np.array([E_of(sd) for sd in sims])
     b = E_s.mean(axis=0)
     J_fd = u_fd.shape[1]
+    fdb = list(range(n_bands)) if fd_bands is None else list(fd_bands)
     F = np.zeros((n_bands, n_bands))
-    for lp in range(n_bands):
+    for k, lp in enumerate(fdb):
         acc = np.zeros(n_bands)
         for j in range(J_fd):
-            delta = band_signal(u_fd[lp, j], P, bands, lp) * mask[None]
+            delta = band_signal(u_fd[k, j], P, bands, lp) * mask[None]
             acc += E_of(sims[j] + delta) - E_s[j]
         F[:, lp] = acc / J_fd / theta[lp]
+    if len(fdb) < n_bands:
+        F = fisher_fill_columns(F, fdb)
+    if trunc[0] > 0:
+        F = fisher_truncate(F, trunc[0], trunc[1])
     Finv = np.linalg.inv(F)
     theta_hat = theta + Finv @ (E_d - b)
     covE = np.cov(E_s.T, ddof=1) if J > 1 else np.zeros((n_bands, n_bands))
     return dict(E=E_d, b=b, F=F, cov=Finv, theta_hat=theta_hat, theta_fid=theta,
                 E_sims=E_s, cov_E=covE)
+
+
+def bandpower_iterate(d, mask, Ninv, P0, bands, n_bands, z_sims, n_sims, u_fd, n_iter,
+                      q_min=0.01, q_max=100.0, **kw):
+    """Iterated fiducial (Sec. 2.3, after eq. pilin): estimate the band powers
+    with the fiducial S_fid, move each band of S_fid to its estimate, S_fid <-
+    S_fid * q_l on the modes of band l with q_l = Theta_hat_l / Theta_fid,l kept
+    in [q_min, q_max] (the regularisation: no band power becomes zero or
+    negative), and estimate again; n_iter estimates with the same random fields.
+    Returns (list of the n_iter estimates, final fiducial P)."""
+    P = np.array(P0, dtype=np.float64, copy=True)
+    out = []
+    for it in range(n_iter):
+        r = bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd, **kw)
+        out.append(r)
+        if it + 1 < n_iter:
+            q = np.clip(r["theta_hat"] / r["theta_fid"], q_min, q_max)
+            for l in range(n_bands):
+                P = np.where(bands == l, P * q[l], P)
+    return out, P
 
 
 def exact_band_terms(mask, Ninv, P, bands, n_bands, A=None):

@@ -48,10 +48,19 @@ __global__ void k_band_P(const S* P, const int16_t* band, size_t tot, int nb, S*
 }
 
 // Estimator from the band energies of all solved maps.  Rows of Eall: 0 = data,
-// 1..J = noise-bias simulations, 1+J+l*nfd+j = Fisher map of band l, sim j.
-// out = [theta | E | b | F | Finv | theta_hat | covE] (sizes nb, nb, nb, nb^2,
-// nb^2, nb, nb^2); flag[0] = 1 if F is singular.  One block, nb <= 64.
-__global__ void k_bp_final(const double* Eall, const double* theta, int nb, int J, int nfd, double* out, int* flag) {
+// 1..J = noise-bias simulations, 1+J+k*nfd+j = Fisher map k (of band fdb[k]),
+// sim j.  fdk[l] = k for a band with Fisher maps, -1 for one without: its
+// column is interpolated from the sampled ones (Sec. 3.1: the Fisher matrix is
+// smooth and nearly translation invariant): between sampled s0 < l' < s1,
+// F[l'+o][l'] = (1-t) F[s0+o][s0] + t F[s1+o][s1], t = (l'-s0)/(s1-s0), a term
+// whose row leaves the matrix dropped and the other weighted alone; beyond the
+// first or last sampled column the nearest one is shifted.  Then the terms
+// |l - l'| > trunc_w with l, l' < trunc_n are zeroed (App. C: far off-diagonal
+// EE terms).  out = [theta | E | b | F | Finv | theta_hat | covE] (sizes nb,
+// nb, nb, nb^2, nb^2, nb, nb^2); flag[0] = 1 if F is singular.  One block,
+// nb <= 64.
+__global__ void k_bp_final(const double* Eall, const double* theta, int nb, int J, int nfd, const int* fdk,
+                           int trunc_n, int trunc_w, double* out, int* flag) {
   extern __shared__ double M[];  // [nb][2 nb] augmented matrix for Gauss-Jordan
   __shared__ double piv_val;
   __shared__ int piv_row;
@@ -72,15 +81,50 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
   }
   __syncthreads();
   for (int idx = t; idx < nb * nb; idx += blockDim.x) {
-    const int l = idx / nb, lp = idx % nb;
+    const int l = idx / nb, lp = idx % nb, k = fdk[lp];
     double s = 0.0;
-    for (int j = 0; j < nfd; ++j)
-      s += Eall[(size_t)(1 + J + lp * nfd + j) * nb + l] - Eall[(size_t)(1 + j) * nb + l];
-    o_F[idx] = nfd > 0 ? s / nfd / theta[lp] : 0.0;
+    for (int j = 0; j < nfd && k >= 0; ++j)
+      s += Eall[(size_t)(1 + J + k * nfd + j) * nb + l] - Eall[(size_t)(1 + j) * nb + l];
+    o_F[idx] = (nfd > 0 && k >= 0) ? s / nfd / theta[lp] : 0.0;
     double c = 0.0;
     for (int j = 0; j < J; ++j)
       c += (Eall[(size_t)(1 + j) * nb + l] - o_b[l]) * (Eall[(size_t)(1 + j) * nb + lp] - o_b[lp]);
     o_cE[idx] = J > 1 ? c / (J - 1) : NAN;
+  }
+  __syncthreads();
+  for (int idx = t; idx < nb * nb; idx += blockDim.x) {  // columns without Fisher maps
+    const int l = idx / nb, lp = idx % nb;
+    if (fdk[lp] >= 0 || nfd == 0) continue;
+    int s0 = -1, s1 = -1;
+    for (int q = lp - 1; q >= 0 && s0 < 0; --q)
+      if (fdk[q] >= 0) s0 = q;
+    for (int q = lp + 1; q < nb && s1 < 0; ++q)
+      if (fdk[q] >= 0) s1 = q;
+    double w0 = 0.0, w1 = 0.0;
+    if (s0 >= 0 && s1 >= 0) {
+      w1 = (double)(lp - s0) / (double)(s1 - s0);
+      w0 = 1.0 - w1;
+    } else if (s0 >= 0) {
+      w0 = 1.0;
+    } else {
+      w1 = 1.0;
+    }
+    const int o = l - lp;
+    double acc = 0.0, ws = 0.0;
+    if (s0 >= 0 && w0 > 0.0 && s0 + o >= 0 && s0 + o < nb) {
+      acc += w0 * o_F[(s0 + o) * nb + s0];
+      ws += w0;
+    }
+    if (s1 >= 0 && w1 > 0.0 && s1 + o >= 0 && s1 + o < nb) {
+      acc += w1 * o_F[(s1 + o) * nb + s1];
+      ws += w1;
+    }
+    o_F[idx] = ws > 0.0 ? acc / ws : 0.0;
+  }
+  __syncthreads();
+  for (int idx = t; idx < nb * nb; idx += blockDim.x) {
+    const int l = idx / nb, lp = idx % nb;
+    if (l < trunc_n && lp < trunc_n && abs(l - lp) > trunc_w) o_F[idx] = 0.0;
   }
   __syncthreads();
   // Gauss-Jordan elimination with partial pivoting on [F | I]
@@ -171,6 +215,11 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   const bool draw = !in->z && !in->noise && !in->u;  // fields drawn here from opts->seed
   if (!draw && (!in->z || !in->noise || (nfd > 0 && !in->u)))
     return wf_fail(WF_EINVAL, "bandpower_estimate: supply all random fields (z, noise, u) or none");
+  if (in->trunc_bands < 0 || in->trunc_bands > nb || in->trunc_width < 0)
+    return wf_fail(WF_EINVAL, "bandpower_estimate: trunc_bands = %d, trunc_width = %d", in->trunc_bands,
+                   in->trunc_width);
+  if (in->fd_bands && (in->n_fd_bands < 1 || in->n_fd_bands > nb))
+    return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd_bands = %d", in->n_fd_bands);
   if (in->sim_index) {
     const unsigned long long lim = (1ull << 62) / ((unsigned long long)C * n * n * (nb + 1));
     for (int j = 0; j < J; ++j)
@@ -187,7 +236,21 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   const size_t delt = dtype == WF_F64 ? 8 : 4;
   const size_t welt = precision == WF_FP64 ? 8 : 4;
   const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
-  const int nF = nb * nfd, Btot = 1 + J + nF;
+  // bands given Fisher maps (all by default) and each band's Fisher-map row
+  int fdb[64], fdk[64], nbF = 0;
+  for (int l = 0; l < nb; ++l) fdk[l] = -1;
+  if (in->fd_bands) {
+    for (int k = 0; k < in->n_fd_bands; ++k) {
+      const int l = in->fd_bands[k];
+      if (l < 0 || l >= nb || (k > 0 && l <= fdb[k - 1]))
+        return wf_fail(WF_EINVAL, "bandpower_estimate: fd_bands must be ascending band ids in [0, n_bands)");
+      fdb[nbF] = l;
+      fdk[l] = nbF++;
+    }
+  } else {
+    for (int l = 0; l < nb; ++l) fdb[nbF] = l, fdk[l] = nbF++;
+  }
+  const int nF = nbF * nfd, Btot = 1 + J + nF;
   Scope sc(h);
   // Theta_fid and the band-restricted power tables
   double* theta = nullptr;
@@ -237,9 +300,9 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
       if (rs == WF_OK)
         rs = wf_draw_normal(o.seed, 1, g * npix, npix, f64, (char*)nb_ + j * npix * welt,
                             (const char*)psim->w + j * npix * welt, st);
-      for (int l = 0; l < nb && j < nfd && rs == WF_OK; ++l)  // Fisher map (l, j) reuses simulation j
-        rs = wf_draw_normal(o.seed, 2, (g * nb + l) * npix, npix, f64, (char*)ub + ((size_t)l * nfd + j) * npix * welt,
-                            nullptr, st);
+      for (int k = 0; k < nbF && j < nfd && rs == WF_OK; ++k)  // Fisher map (band fdb[k], j) reuses simulation j
+        rs = wf_draw_normal(o.seed, 2, (g * nb + fdb[k]) * npix, npix, f64,
+                            (char*)ub + ((size_t)k * nfd + j) * npix * welt, nullptr, st);
     }
     if (rs != WF_OK) { free(maps); return rs; }
     zin = zb;
@@ -255,8 +318,8 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
 
   // Fisher maps: d_j + M A_l u_lj, synthesised with the band-restricted power as
   // signal and the simulation's data as "noise" (M d_j = d_j)
-  for (int l = 0; l < nb; ++l)
-    for (int j = 0; j < nfd; ++j) maps[l * nfd + j].P = (const char*)Pl + (size_t)l * nsp * delt;
+  for (int k = 0; k < nbF; ++k)
+    for (int j = 0; j < nfd; ++j) maps[k * nfd + j].P = (const char*)Pl + (size_t)fdb[k] * nsp * delt;
   void* dfd = nullptr;
   if (nF > 0) {
     wf_problem* pfd = nullptr;
@@ -268,9 +331,9 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     if (rs == WF_OK) { sc.add(nfd_in); rs = wf_alloc(h, &dfd, npix * nF * welt, "Fisher data"); }
     if (rs != WF_OK) { free(maps); return rs; }
     sc.add(dfd);
-    for (int l = 0; l < nb; ++l)
+    for (int k = 0; k < nbF; ++k)
       for (int j = 0; j < nfd; ++j) {
-        cudaError_t e = cudaMemcpyAsync((char*)nfd_in + (size_t)(l * nfd + j) * npix * welt,
+        cudaError_t e = cudaMemcpyAsync((char*)nfd_in + (size_t)(k * nfd + j) * npix * welt,
                                         (const char*)dsim + (size_t)j * npix * welt, npix * welt,
                                         cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) { free(maps); return wf_cuda_fail(e, "bandpower_estimate: Fisher base copy"); }
@@ -313,9 +376,13 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   BP_OK(wf_alloc(h, (void**)&dflag, sizeof(int), "flag"));
   sc.add(dflag);
   BP_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), st));
+  int* dfdk = nullptr;
+  BP_OK(wf_alloc(h, (void**)&dfdk, sizeof(int) * 64, "Fisher rows"));
+  sc.add(dfdk);
+  BP_TRY(cudaMemcpyAsync(dfdk, fdk, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
   const size_t gj_smem = sizeof(double) * 2 * nb * nb;
   BP_TRY(cudaFuncSetAttribute(k_bp_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 64 * 64 * 8)));
-  k_bp_final<<<1, 256, gj_smem, st>>>(Eall, theta, nb, J, nfd, dout, dflag);
+  k_bp_final<<<1, 256, gj_smem, st>>>(Eall, theta, nb, J, nfd, dfdk, in->trunc_bands, in->trunc_width, dout, dflag);
   BP_TRY(cudaGetLastError());
   double* hout = (double*)malloc(sizeof(double) * nout);
   if (!hout) return wf_fail(WF_ENOMEM, "bandpower_estimate: host allocation");
@@ -344,4 +411,66 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   }
   if (hflag) return wf_fail(WF_ENONFINITE, "bandpower_estimate: the Fisher matrix is singular");
   return solve_status;
+}
+
+// P <- P * q[l] on the modes of band l (others unchanged), in the input dtype.
+template <typename S>
+__global__ void k_scale_bands(S* P, const int16_t* band, size_t tot, const double* q, int nb) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += stride) {
+    const int l = band[i];
+    if (l >= 0 && l < nb) P[i] = (S)((double)P[i] * q[l]);
+  }
+}
+
+extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
+                                       const wf_bandpower_in* in, const wf_opts* opts, int n_iter, double q_min,
+                                       double q_max, void* P_out, double* theta_hat_hist, wf_bandpower_out* out,
+                                       wf_solve_stats* stats) {
+  if (!h || !data || !in || !out) return wf_fail(WF_EINVAL, "bandpower_iterate: null argument");
+  if (n_iter < 1 || n_iter > 100) return wf_fail(WF_EINVAL, "bandpower_iterate: n_iter = %d outside [1, 100]", n_iter);
+  if (!(q_min > 0.0 && q_min <= 1.0 && q_max >= 1.0 && isfinite(q_max)))
+    return wf_fail(WF_EINVAL, "bandpower_iterate: need 0 < q_min <= 1 <= q_max (got %g, %g)", q_min, q_max);
+  if (in->n_fd < 1) return wf_fail(WF_EINVAL, "bandpower_iterate: needs n_fd >= 1 (the Fisher matrix)");
+  if (!data->P || !in->band) return wf_fail(WF_EINVAL, "bandpower_iterate: null P or band table");
+  if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "bandpower_iterate: bad dtype");
+  wf_opts o;
+  if (opts) o = *opts;
+  else wf_opts_default(&o);
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int nb = in->n_bands;
+  const size_t delt = dtype == WF_F64 ? 8 : 4;
+  const size_t nsp = (size_t)C * n * (n / 2 + 1);
+  Scope sc(h);
+  void* Pc = nullptr;
+  double* qd = nullptr;
+  BP_OK(wf_alloc(h, &Pc, nsp * delt, "iterated fiducial power"));
+  sc.add(Pc);
+  BP_OK(wf_alloc(h, (void**)&qd, sizeof(double) * (nb > 0 ? nb : 1), "band factors"));
+  sc.add(qd);
+  BP_TRY(cudaMemcpyAsync(Pc, data->P, nsp * delt, cudaMemcpyDeviceToDevice, st));
+  wf_map m = *data;
+  m.P = Pc;
+  wf_status worst = WF_OK;
+  double q[64];
+  for (int it = 0; it < n_iter; ++it) {
+    const wf_status rs = bandpower_estimate(h, &m, n, C, dtype, precision, in, &o, out, stats);
+    if (rs != WF_OK && rs != WF_ENOTCONVERGED) return rs;
+    if (rs != WF_OK) worst = rs;
+    if (theta_hat_hist) memcpy(theta_hat_hist + (size_t)it * nb, out->theta_hat, sizeof(double) * nb);
+    if (it + 1 == n_iter) break;
+    for (int l = 0; l < nb; ++l) {  // regularised move of each band: ratio kept in [q_min, q_max]
+      const double r = out->theta_hat[l] / out->theta_fid[l];
+      q[l] = isfinite(r) ? fmin(fmax(r, q_min), q_max) : 1.0;
+    }
+    BP_TRY(cudaMemcpyAsync(qd, q, sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+    const int gblk = (int)((nsp + 255) / 256 < 4096 ? (nsp + 255) / 256 : 4096);
+    if (dtype == WF_F64) k_scale_bands<double><<<gblk, 256, 0, st>>>((double*)Pc, in->band, nsp, qd, nb);
+    else k_scale_bands<float><<<gblk, 256, 0, st>>>((float*)Pc, in->band, nsp, qd, nb);
+    BP_TRY(cudaGetLastError());
+  }
+  if (P_out) BP_TRY(cudaMemcpyAsync(P_out, Pc, nsp * delt, cudaMemcpyDeviceToDevice, st));
+  BP_TRY(cudaStreamSynchronize(st));
+  if (worst != WF_OK) wf_fail(worst, "bandpower_iterate: a solve hit its iteration limit");
+  return worst;
 }

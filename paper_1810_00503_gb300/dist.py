@@ -83,6 +83,8 @@ def estimate_on_rank(d, mask, Ninv, P, band, n_bands, n_sim, n_fd, world, rank, 
     sums.  Returns (estimate, this rank's per-map stats); the estimate is the
     same on every rank and equals the single-process one."""
     from . import wf
+    if opts.get("fd_bands") is not None:
+        raise ValueError("estimate_on_rank: every band needs Fisher maps (fd_bands is not supported)")
     sims, (fd_lo, fd_hi) = assignment(n_sim, n_fd, world, rank)
     res, stats = wf.bandpower_estimate(d, mask, Ninv, P, band, n_bands, None, None, None, n_sim=len(sims),
                                        n_fd=fd_hi - fd_lo, sim_index=sims, seed=seed, **opts)

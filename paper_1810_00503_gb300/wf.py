@@ -25,7 +25,8 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_signal_map", "wf_map_solve", "wf_simulate_data", "wf_band_energy",
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
            "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
-           "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table"]
+           "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table",
+           "bandpower_iterate"]
 
 
 class WfMap(ctypes.Structure):
@@ -50,7 +51,9 @@ class WfSolveStats(ctypes.Structure):
 class WfBandpowerIn(ctypes.Structure):
     _fields_ = [("n_bands", ctypes.c_int), ("n_sim", ctypes.c_int), ("n_fd", ctypes.c_int),
                 ("pad_", ctypes.c_int), ("band", ctypes.c_void_p), ("z", ctypes.c_void_p),
-                ("noise", ctypes.c_void_p), ("u", ctypes.c_void_p), ("sim_index", ctypes.c_void_p)]
+                ("noise", ctypes.c_void_p), ("u", ctypes.c_void_p), ("sim_index", ctypes.c_void_p),
+                ("fd_bands", ctypes.c_void_p), ("n_fd_bands", ctypes.c_int), ("trunc_bands", ctypes.c_int),
+                ("trunc_width", ctypes.c_int), ("pad2_", ctypes.c_int)]
 
 
 class WfBandpowerOut(ctypes.Structure):
@@ -105,6 +108,9 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(WfOpts), ctypes.POINTER(WfBandpowerOut),
                                      ctypes.POINTER(WfSolveStats)]
     L.wf_normal_draw.argtypes = [ctypes.c_ulonglong, ctypes.c_uint, ctypes.c_ulonglong, ctypes.c_size_t, i, vp, vp]
+    L.bandpower_iterate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
+                                    ctypes.POINTER(WfOpts), i, d, d, vp, ctypes.POINTER(d),
+                                    ctypes.POINTER(WfBandpowerOut), ctypes.POINTER(WfSolveStats)]
     for name in EXPORTS:
         if name not in ("wf_last_error", "wf_opts_default"):
             getattr(L, name).restype = ctypes.c_int
@@ -232,18 +238,10 @@ def normal_draw(seed, count, stream_id=0, offset=0, dtype=None, out=None, stream
     return out
 
 
-def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",
-                       handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None, **opts):
-    """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
-    of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
-    (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
-    (C, n, n/2+1) int16; z, noise (n_sim, C, n, n), u (n_bands, n_fd, C, n, n)
-    in the working type, or all three None with n_sim and n_fd given (the
-    library then draws them from opts `seed`; sim_index gives the global index
-    of each simulation, so that the draws do not depend on how simulations are
-    split over calls).  Returns (dict of numpy arrays, per-map stats)."""
+def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
+                    opts, fd_bands=None, trunc=(0, 0)):
+    """ctypes arguments shared by bandpower_estimate and bandpower_iterate."""
     import torch
-    handle = handle or default_handle()
     C, n, _ = Ninv.shape
     m = WfMap(d=_ptr(d), mask=_ptr(mask), Ninv=_ptr(Ninv), P=_ptr(P))
     nb = int(n_bands)
@@ -254,10 +252,14 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
         idx = np.ascontiguousarray(sim_index, dtype=np.int64)
         if idx.shape != (J,):
             raise ValueError("sim_index needs one entry per simulation")
+    fdb = None if fd_bands is None else np.ascontiguousarray(fd_bands, dtype=np.int32)
+    nbF = nb if fdb is None else int(fdb.size)
     bi = WfBandpowerIn(n_bands=nb, n_sim=J, n_fd=F, pad_=0,
                        band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u),
-                       sim_index=None if idx is None else idx.ctypes.data)
-    nmaps = 1 + J + nb * F
+                       sim_index=None if idx is None else idx.ctypes.data,
+                       fd_bands=None if fdb is None else fdb.ctypes.data, n_fd_bands=0 if fdb is None else nbF,
+                       trunc_bands=int(trunc[0]), trunc_width=int(trunc[1]))
+    nmaps = 1 + J + nbF * F
     arrs = {k: np.zeros(sz) for k, sz in (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb),
                                           ("cov", nb * nb), ("theta_hat", nb), ("cov_E", nb * nb),
                                           ("E_maps", nmaps * nb))}
@@ -267,18 +269,67 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
     for k, v in opts.items():
         setattr(o, k, v)
     o.stream = _stream(stream)
-    nmaps = 1 + bi.n_sim + nb * bi.n_fd
     st = (WfSolveStats * nmaps)()
     prec = WF_FP64 if precision == "fp64" else WF_MIXED
-    status = lib().bandpower_estimate(handle.ptr, ctypes.byref(m), n, C,
-                                      WF_F64 if Ninv.dtype == torch.float64 else WF_F32, prec,
-                                      ctypes.byref(bi), ctypes.byref(o), ctypes.byref(bo), st)
-    if status not in (0, 5):
-        _check(status)
+    dt = WF_F64 if Ninv.dtype == torch.float64 else WF_F32
+    return dict(m=m, bi=bi, bo=bo, o=o, st=st, arrs=arrs, n=n, C=C, nb=nb, nmaps=nmaps, prec=prec, dt=dt,
+                keep=(idx, fdb))
+
+
+def _bandpower_result(a):
+    arrs, nb = a["arrs"], a["nb"]
     for k in ("fisher", "cov", "cov_E"):
         arrs[k] = arrs[k].reshape(nb, nb)
-    arrs["E_maps"] = arrs["E_maps"].reshape(nmaps, nb)
-    return arrs, Problem._stats(st)
+    arrs["E_maps"] = arrs["E_maps"].reshape(a["nmaps"], nb)
+    return arrs, Problem._stats(a["st"])
+
+
+def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",
+                       handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None, fd_bands=None,
+                       trunc=(0, 0), **opts):
+    """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
+    of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
+    (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
+    (C, n, n/2+1) int16; z, noise (n_sim, C, n, n), u (n_bands, n_fd, C, n, n)
+    in the working type, or all three None with n_sim and n_fd given (the
+    library then draws them from opts `seed`; sim_index gives the global index
+    of each simulation, so that the draws do not depend on how simulations are
+    split over calls).  fd_bands: the bands given Fisher maps (default all;
+    the others' Fisher columns are interpolated, u then has one row per listed
+    band); trunc = (n, w): zero F[l][l'] for l, l' < n with |l - l'| > w.
+    Returns (dict of numpy arrays, per-map stats)."""
+    handle = handle or default_handle()
+    a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
+                        opts, fd_bands, trunc)
+    status = lib().bandpower_estimate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
+                                      ctypes.byref(a["bi"]), ctypes.byref(a["o"]), ctypes.byref(a["bo"]), a["st"])
+    if status not in (0, 5):
+        _check(status)
+    return _bandpower_result(a)
+
+
+def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_min=0.01, q_max=100.0,
+                      precision="fp64", handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None,
+                      fd_bands=None, trunc=(0, 0), **opts):
+    """bandpower_iterate: n_iter estimates, the fiducial P moved to each estimate
+    in between (Sec. 2.3).  Arguments as bandpower_estimate.  Returns (last
+    estimate, per-map stats of the last run, Theta_hat of every estimate
+    (n_iter, n_bands), final fiducial P as a CUDA tensor like P)."""
+    import torch
+    handle = handle or default_handle()
+    a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
+                        opts, fd_bands, trunc)
+    hist = np.zeros((int(n_iter), a["nb"]))
+    P_out = torch.empty_like(P)
+    status = lib().bandpower_iterate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
+                                     ctypes.byref(a["bi"]), ctypes.byref(a["o"]), int(n_iter), float(q_min),
+                                     float(q_max), _ptr(P_out),
+                                     hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(a["bo"]),
+                                     a["st"])
+    if status not in (0, 5):
+        _check(status)
+    res, stats = _bandpower_result(a)
+    return res, stats, hist, P_out
 
 
 class Problem:

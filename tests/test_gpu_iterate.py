@@ -1,0 +1,163 @@
+"""Iterated fiducial (bandpower_iterate) and the joint E/B band powers (C = 2)
+against the oracle, and the iteration's behaviour from a distorted start."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import wf_oracle as O  # noqa: E402
+from paper_1810_00503_gb300 import synth, wf  # noqa: E402
+from tests.helpers import ensure_lib, to_dev  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    ensure_lib()
+
+
+def _fields(inp, J, nb, nfd, C, seed):
+    rng = np.random.default_rng(seed)
+    n = inp.n
+    sig = np.where(inp.Ninv > 0, 1.0 / np.sqrt(np.where(inp.Ninv > 0, inp.Ninv, 1.0)), 0.0)
+    z = rng.standard_normal((J, C, n, n))
+    nz = rng.standard_normal((J, C, n, n)) * sig
+    u = rng.standard_normal((nb, nfd, C, n, n))
+    return z, nz, u
+
+
+def _dev(inp, d, P, bands, dt=torch.float64):
+    n = inp.n
+    return (to_dev(d, dt), to_dev(inp.mask, torch.uint8), to_dev(inp.Ninv, dt), to_dev(P[..., : n // 2 + 1], dt),
+            to_dev(bands[..., : n // 2 + 1], torch.int16))
+
+
+def test_iterate_matches_oracle_iteration():
+    n, nb, J, nfd, n_iter = 16, 3, 6, 3, 3
+    inp = synth.density_small(n, seed=12, masked_frac=0.2)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb)
+    r = np.array([0.2, 1.0, 3.0])
+    P0 = inp.P.copy()
+    for lb in range(nb):
+        P0[bands == lb] *= r[lb]
+    z, nz, u = _fields(inp, J, nb, nfd, 1, 5)
+    dd, mk, Nv, Pv, bv = _dev(inp, d, P0, bands)
+    res, stats, hist, Pf = wf.bandpower_iterate(dd, mk, Nv, Pv, bv, nb, to_dev(z, torch.float64),
+                                                to_dev(nz, torch.float64), to_dev(u, torch.float64),
+                                                n_iter=n_iter, q_min=0.05, q_max=20.0, precision="fp64",
+                                                gtol_rel=1e-12, max_iter=20000)
+    ref, Pref = O.bandpower_iterate(d, inp.mask, inp.Ninv, P0, bands, nb, z, nz, u, n_iter, q_min=0.05, q_max=20.0,
+                                    gtol_rel=1e-12, max_iter=20000)
+    for it in range(n_iter):
+        th = ref[it]["theta_hat"]
+        assert np.abs(hist[it] - th).max() <= 1e-7 * np.abs(th).max(), (it, hist[it], th)
+    assert np.abs(res["theta_fid"] - ref[-1]["theta_fid"]).max() <= 1e-7 * np.abs(ref[-1]["theta_fid"]).max()
+    Ph = Pf.cpu().numpy()
+    assert np.abs(Ph - Pref[..., : n // 2 + 1]).max() <= 1e-7 * np.abs(Pref).max()
+    assert all(s["status"] == "WF_OK" for s in stats)
+
+
+def test_iteration_from_a_distorted_start_reaches_the_truth():
+    """The paper's scheme: the true spectrum with every band scaled by a random
+    factor in [0.01, 1], then re-estimation.  The re-estimated band powers lie
+    near the truth although the start was off by up to 100x."""
+    n, nb, J, nfd = 64, 4, 24, 6
+    inp = synth.density_small(n, seed=21, masked_frac=0.15)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb, kmin=2.0)
+    th_true = O.theta_fid(inp.P, bands, nb)
+    r = np.random.default_rng(3).uniform(0.01, 1.0, nb)
+    P0 = inp.P.copy()
+    for lb in range(nb):
+        P0[bands == lb] *= r[lb]
+    dd, mk, Nv, Pv, bv = _dev(inp, d, P0, bands)
+    res, stats, hist, Pf = wf.bandpower_iterate(dd, mk, Nv, Pv, bv, nb, None, None, None, n_sim=J, n_fd=nfd,
+                                                n_iter=3, q_min=0.01, q_max=100.0, precision="fp64",
+                                                gtol_rel=1e-10, max_iter=20000, seed=8)
+    err0 = np.abs(np.log(r))
+    err = np.abs(np.log(np.clip(hist[-1], 1e-30, None) / th_true))
+    assert np.all(err < 0.35), (r, hist / th_true)
+    assert err.mean() < 0.2 * err0.mean(), (err, err0)
+
+
+def test_joint_eb_bandpowers_match_oracle():
+    n, nb, J, nfd = 16, 2, 5, 2
+    inp = synth.shear_eb(n, seed=6)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb, C=2)  # E bands 0, 1; B bands 2, 3
+    z, nz, u = _fields(inp, J, 2 * nb, nfd, 2, 17)
+    dd, mk, Nv, Pv, bv = _dev(inp, d, inp.P, bands)
+    res, stats = wf.bandpower_estimate(dd, mk, Nv, Pv, bv, 2 * nb, to_dev(z, torch.float64),
+                                       to_dev(nz, torch.float64), to_dev(u, torch.float64), precision="fp64",
+                                       gtol_rel=1e-12, max_iter=20000)
+    ref = O.bandpower_sims(d, inp.mask, inp.Ninv, inp.P, bands, 2 * nb, z, nz, u, gtol_rel=1e-12, max_iter=20000)
+    for k in ("E", "b", "F", "theta_hat"):
+        kk = {"b": "bias", "F": "fisher"}.get(k, k)
+        a, b = np.asarray(res[kk]), np.asarray(ref[k])
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(b).max(), (k, a, b)
+    # the leakage blocks EB / BE of the Fisher matrix are non-zero under the mask
+    F = np.asarray(res["fisher"])
+    assert np.abs(F[:nb, nb:]).max() > 1e-6 * np.abs(F).max()
+
+
+def test_sampled_fisher_columns_match_oracle():
+    """Fisher maps for bands 0, 2, 3 only; column 1 interpolated (Sec. 3.1)."""
+    n, nb, J, nfd = 16, 4, 6, 3
+    inp = synth.density_small(n, seed=14, masked_frac=0.2)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb)
+    fdb = [0, 2, 3]
+    z, nz, u = _fields(inp, J, len(fdb), nfd, 1, 23)
+    dd, mk, Nv, Pv, bv = _dev(inp, d, inp.P, bands)
+    res, stats = wf.bandpower_estimate(dd, mk, Nv, Pv, bv, nb, to_dev(z, torch.float64), to_dev(nz, torch.float64),
+                                       to_dev(u, torch.float64), precision="fp64", gtol_rel=1e-12, max_iter=20000,
+                                       fd_bands=fdb)
+    assert len(stats) == 1 + J + len(fdb) * nfd
+    ref = O.bandpower_sims(d, inp.mask, inp.Ninv, inp.P, bands, nb, z, nz, u, gtol_rel=1e-12, max_iter=20000,
+                           fd_bands=fdb)
+    for k in ("F", "theta_hat", "b"):
+        kk = {"b": "bias", "F": "fisher"}.get(k, k)
+        a, b = np.asarray(res[kk]), np.asarray(ref[k])
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(b).max(), (k, a, b)
+
+
+def test_truncated_eb_fisher_matches_oracle():
+    """Joint E/B with 3 + 3 bands and the EE block truncated beyond one band
+    off the diagonal (App. C)."""
+    n, nb, J, nfd = 16, 3, 5, 2
+    inp = synth.shear_eb(n, seed=9)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb, C=2)
+    z, nz, u = _fields(inp, J, 2 * nb, nfd, 2, 29)
+    dd, mk, Nv, Pv, bv = _dev(inp, d, inp.P, bands)
+    res, _ = wf.bandpower_estimate(dd, mk, Nv, Pv, bv, 2 * nb, to_dev(z, torch.float64), to_dev(nz, torch.float64),
+                                   to_dev(u, torch.float64), precision="fp64", gtol_rel=1e-12, max_iter=20000,
+                                   trunc=(nb, 1))
+    ref = O.bandpower_sims(d, inp.mask, inp.Ninv, inp.P, bands, 2 * nb, z, nz, u, gtol_rel=1e-12, max_iter=20000,
+                           trunc=(nb, 1))
+    F = np.asarray(res["fisher"])
+    assert F[0, 2] == 0.0 and F[2, 0] == 0.0 and F[0, 1] != 0.0 and F[0, 5] != 0.0
+    for k in ("F", "theta_hat"):
+        kk = {"F": "fisher"}.get(k, k)
+        a, b = np.asarray(res[kk]), np.asarray(ref[k])
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(b).max(), (k, a, b)
+
+
+def test_device_draws_of_sampled_bands_agree_with_the_full_run():
+    """Fisher fields drawn on the device are keyed by band id, so the sampled
+    bands' Fisher columns equal those of the run over every band."""
+    n, nb, J, nfd = 16, 4, 5, 2
+    inp = synth.density_small(n, seed=15, masked_frac=0.2)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb)
+    args = _dev(inp, d, inp.P, bands)
+    kw = dict(n_sim=J, n_fd=nfd, precision="fp64", gtol_rel=1e-12, max_iter=20000, seed=4)
+    full, _ = wf.bandpower_estimate(*args, nb, None, None, None, **kw)
+    part, _ = wf.bandpower_estimate(*args, nb, None, None, None, fd_bands=[1, 3], **kw)
+    F, G = np.asarray(full["fisher"]), np.asarray(part["fisher"])
+    for lp in (1, 3):
+        assert np.abs(F[:, lp] - G[:, lp]).max() <= 1e-9 * np.abs(F).max()
+    assert np.allclose(full["bias"], part["bias"], rtol=1e-12)

@@ -279,3 +279,89 @@ def test_philox_normals_box_muller_pairs_and_moments():
     assert not np.allclose(normals(11, 4, 10), z[:10])
     assert not np.allclose(normals(12, 3, 10), z[:10])
     assert MASK32 == 2 ** 32 - 1
+
+
+def test_exact_band_terms_unmasked_closed_form_eb():
+    """Joint E/B (C = 2) with separate E and B band ids, no mask, isotropic
+    noise: the rotation R(k) is orthogonal off the Nyquist lines and c I on them,
+    so each channel is filtered on its own with effective power P_eff = P (c^2 P
+    on the Nyquist lines) and the band terms take the C = 1 closed forms."""
+    n, s2, nb = 8, 0.5, 2
+    inp = synth.shear_eb(n, seed=4)
+    mask = np.ones((n, n), np.uint8)
+    Ninv = np.full((2, n, n), 1.0 / s2)
+    b1 = synth.log_bands(n, nb)[0]
+    bands = np.stack([b1, np.where(b1 >= 0, b1 + nb, -1)])
+    b, F, th = O.exact_band_terms(mask, Ninv, inp.P, bands, 2 * nb)
+    c, _ = O.ks_rotation(n)
+    my, mx = O.signed_modes(n)
+    nyq = (np.abs(mx) == n // 2) | (np.abs(my) == n // 2)
+    Peff = inp.P * np.where(nyq, c * c, 1.0)[None]
+    for l in range(2 * nb):
+        sel = bands == l
+        assert np.isclose(th[l], inp.P[sel].mean(), rtol=1e-12)
+        assert np.isclose(b[l], 0.5 / th[l] * np.sum(Peff[sel] / (Peff[sel] + s2)), rtol=1e-10)
+        assert np.isclose(F[l, l], 0.5 / th[l] ** 2 * np.sum(Peff[sel] ** 2 / (Peff[sel] + s2) ** 2), rtol=1e-10)
+    off = F - np.diag(np.diag(F))
+    assert np.abs(off).max() <= 1e-11 * np.abs(F).max()
+
+
+def test_iterated_fiducial_update_rule():
+    """Each re-estimate starts from the previous fiducial times the clamped ratio
+    of estimate to fiducial on every band's modes; modes outside the bands keep
+    their power."""
+    n, nb, J, nfd = 8, 2, 3, 2
+    inp = synth.density_small(n, seed=3)
+    bands = synth.log_bands(n, nb)
+    rng = np.random.default_rng(4)
+    sig = np.where(inp.Ninv > 0, 1.0 / np.sqrt(np.where(inp.Ninv > 0, inp.Ninv, 1.0)), 0.0)
+    z = rng.standard_normal((J, 1, n, n))
+    nz = rng.standard_normal((J, 1, n, n)) * sig
+    u = rng.standard_normal((nb, nfd, 1, n, n))
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    P0 = inp.P * 0.3
+    res, Pf = O.bandpower_iterate(d, inp.mask, inp.Ninv, P0, bands, nb, z, nz, u, 2, q_min=0.5, q_max=2.0,
+                                  gtol_rel=1e-12)
+    assert len(res) == 2
+    q = np.clip(res[0]["theta_hat"] / res[0]["theta_fid"], 0.5, 2.0)
+    want = P0.copy()
+    for l in range(nb):
+        want[bands == l] *= q[l]
+    assert np.array_equal(Pf, want)
+    assert np.allclose(res[1]["theta_fid"], res[0]["theta_fid"] * q, rtol=1e-12)
+    outside = bands < 0
+    assert np.array_equal(Pf[outside], P0[outside])
+
+
+def test_fisher_column_interpolation_rule():
+    """fisher_fill_columns: sampled columns are kept; on a matrix that is exactly
+    translation invariant with a factor linear in the column, F[l][l'] =
+    f(l - l') (a + b l'), interpolated columns are exact where both shifted rows
+    exist; with every band sampled nothing changes."""
+    nb = 9
+    f = lambda o: np.exp(-abs(o) / 1.5) * (1.0 if o >= 0 else 0.7)
+    F = np.array([[f(l - lp) * (2.0 + 0.3 * lp) for lp in range(nb)] for l in range(nb)])
+    S = [0, 2, 5, 8]
+    G = O.fisher_fill_columns(F * np.isin(np.arange(nb), S)[None, :], S)
+    for lp in S:
+        assert np.array_equal(G[:, lp], F[:, lp])
+    for lp in (1, 3, 4, 6, 7):
+        s0 = max(s for s in S if s < lp)
+        s1 = min(s for s in S if s > lp)
+        for l in range(nb):
+            o = l - lp
+            if 0 <= s0 + o < nb and 0 <= s1 + o < nb:
+                assert np.isclose(G[l, lp], F[l, lp], rtol=1e-12), (l, lp)
+    assert np.array_equal(O.fisher_fill_columns(F, list(range(nb))), F)
+    # outside the sampled range the nearest column is shifted
+    G2 = O.fisher_fill_columns(F * np.isin(np.arange(nb), [2, 5])[None, :], [2, 5])
+    assert np.isclose(G2[1, 0], F[3, 2]) and np.isclose(G2[8, 7], F[6, 5])
+
+
+def test_fisher_truncation_rule():
+    F = np.arange(1.0, 37.0).reshape(6, 6)
+    G = O.fisher_truncate(F, 4, 1)
+    for l in range(6):
+        for lp in range(6):
+            zeroed = l < 4 and lp < 4 and abs(l - lp) > 1
+            assert G[l, lp] == (0.0 if zeroed else F[l, lp])
