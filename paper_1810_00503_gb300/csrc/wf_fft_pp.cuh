@@ -53,13 +53,19 @@ __device__ __forceinline__ V2<T>* wf_pp_out(int lgL, V2<T>* A, V2<T>* B) {
   return wf_pp_np(lgL) == 2 ? B : A;
 }
 
+struct WfNoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // Full transform.  Element e of sequence t sits at t * ts + e * js in the
 // shared buffers A and B (swizzled).  ld0 feeds the first pass, stl takes the
-// last pass's outputs; a barrier separates consecutive passes.  The caller
-// synchronises before anything reads what stl wrote to shared memory.
-template <typename T, int DIR, bool SEQF, class LD0, class STL>
+// last pass's outputs; a barrier separates consecutive passes.  after1 runs
+// once every thread has finished the first pass (after a barrier), when
+// whatever ld0 read may be overwritten.  The caller synchronises before
+// anything reads what stl wrote to shared memory.
+template <typename T, int DIR, bool SEQF, class LD0, class STL, class H = WfNoHook>
 __device__ __forceinline__ void wf_pp_fft(int lgL, int lgcnt, int ts, int js, V2<T>* A, V2<T>* B,
-                                          const V2<T>* ptab, LD0& ld0, STL& stl) {
+                                          const V2<T>* ptab, LD0& ld0, STL& stl, H after1 = H()) {
   auto ldA = [&](int t, int e) { return A[wf_sw<T>(t * ts + e * js)]; };
   auto ldB = [&](int t, int e) { return B[wf_sw<T>(t * ts + e * js)]; };
   auto stA = [&](int t, int e, V2<T> v) { A[wf_sw<T>(t * ts + e * js)] = v; };
@@ -72,11 +78,14 @@ __device__ __forceinline__ void wf_pp_fft(int lgL, int lgcnt, int ts, int js, V2
       case 3: wf_pp_pass<T, 8, DIR, SEQF>(lgL, lgcnt, 0, ptab, 8, ld0, stl); break;
       default: wf_pp_pass<T, 16, DIR, SEQF>(lgL, lgcnt, 0, ptab, 16, ld0, stl); break;
     }
+    __syncthreads();
+    after1();
   } else if (np == 2) {  // lgL 5..8: bits (3,2) (3,3) (4,3) (4,4)
     const int b1 = (lgL + 1) >> 1, b2 = lgL - b1, R1 = 1 << b1;
     if (b1 == 3) wf_pp_pass<T, 8, DIR, SEQF>(lgL, lgcnt, 0, ptab, R1, ld0, stA);
     else wf_pp_pass<T, 16, DIR, SEQF>(lgL, lgcnt, 0, ptab, R1, ld0, stA);
     __syncthreads();
+    after1();
     if (b2 == 2) wf_pp_pass<T, 4, DIR, SEQF>(lgL, lgcnt, b1, ptab, R1, ldA, stl);
     else if (b2 == 3) wf_pp_pass<T, 8, DIR, SEQF>(lgL, lgcnt, b1, ptab, R1, ldA, stl);
     else wf_pp_pass<T, 16, DIR, SEQF>(lgL, lgcnt, b1, ptab, R1, ldA, stl);
@@ -85,6 +94,7 @@ __device__ __forceinline__ void wf_pp_fft(int lgL, int lgcnt, int ts, int js, V2
     if (b1 == 3) wf_pp_pass<T, 8, DIR, SEQF>(lgL, lgcnt, 0, ptab, R1, ld0, stA);
     else wf_pp_pass<T, 16, DIR, SEQF>(lgL, lgcnt, 0, ptab, R1, ld0, stA);
     __syncthreads();
+    after1();
     wf_pp_pass<T, 8, DIR, SEQF>(lgL, lgcnt, b1, ptab, R1, ldA, stB);
     __syncthreads();
     wf_pp_pass<T, 8, DIR, SEQF>(lgL, lgcnt, b1 + 3, ptab, R1, ldB, stl);

@@ -39,6 +39,11 @@
 #ifndef WF_COLFWD_PF
 #define WF_COLFWD_PF 1
 #endif
+// Inverse column stage of the iteration as a persistent kernel fed by TMA (1)
+// or one block per tile (0).
+#ifndef WF_COLINV_TMA
+#define WF_COLINV_TMA 1
+#endif
 // p and g values the forward column stage loads per batch in its epilogue.
 #ifndef WF_COLFWD_EB
 #define WF_COLFWD_EB 16

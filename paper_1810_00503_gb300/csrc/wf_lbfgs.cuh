@@ -18,6 +18,7 @@
 #pragma once
 #include "wf_ops.cuh"
 #include "wf_stage_pp.cuh"
+#include "wf_tma.cuh"
 
 
 // Stage per-warp partial dot products: red[slot * NW + warp] (NW = warps of the block).
@@ -349,6 +350,87 @@ k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const vo
 #else
   wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
 #endif
+}
+
+// Persistent inverse column stage with the next tile prefetched by TMA.
+// Shared memory: the TMA tile Ct ([C n][TC] packed values), the ping-pong
+// tiles A and B, the pass table.  Work items (map, column tile) are taken
+// round-robin by the resident blocks; while a block runs the second and third
+// FFT passes of one tile, the copy engine brings in the next tile, whose first
+// pass then reads shared memory (the per-mode operator R sqrt(P)/n applied on
+// the way in, as in wf_col_inv_pp).  tm: 2-D view of the whole history ring,
+// rows of n/2 packed values; the map's direction P[next] is rows
+// ((next B + b) C n + r).
+template <typename T>
+__host__ __device__ constexpr size_t wf_colinv_tma_smem() {
+  return (3 * (size_t)WF_TILE + WF_NT) * sizeof(V2<T>) + 128;  // + room to align the TMA tile to 128 B
+}
+template <typename T, int C>
+__global__ void __launch_bounds__(WF_THREADS, sizeof(T) == 4 ? 2 : 1)
+k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb, int B,
+                const __grid_constant__ CUtensorMap tm) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* Ct = (V2<T>*)(wf_smem + ((128u - (wf_smem_u32(wf_smem) & 127u)) & 127u));  // TMA destination, 128 B aligned
+  V2<T>* A = Ct + WF_TILE;
+  V2<T>* Bf = A + WF_TILE;
+  V2<T>* s_tw = Bf + WF_TILE;
+  __shared__ uint64_t full;
+  const int tid = threadIdx.x;
+  const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1;
+  const int CT = C * TC, lgCT = lgTC + (C == 2 ? 1 : 0);
+  const int nitems = B * g.ntile;
+  const int rows = C * n, boxr = rows < 256 ? rows : 256;
+  const uint32_t tile_bytes = (uint32_t)(rows * TC * sizeof(V2<T>));
+  const size_t vsz = (size_t)C * n * h;
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
+  if (tid == 0) {
+    wf_mbar_init(&full, 1);
+    wf_mbar_fence_init();
+  }
+  __syncthreads();
+  auto next_active = [&](int it) {
+    while (it < nitems && !lb.st[it / g.ntile].active) it += gridDim.x;
+    return it;
+  };
+  auto issue = [&](int it) {  // thread 0: the tile of work item `it` into Ct
+    const int b = it / g.ntile, tile = it - b * g.ntile;
+    const int row0 = (lb.st[b].next * B + b) * rows;
+    wf_mbar_expect_tx(&full, tile_bytes);
+    for (int r = 0; r < rows; r += boxr) wf_tma_load_2d(Ct + (size_t)r * TC, &tm, 2 * tile * TC, row0 + r, &full);
+  };
+  int it = next_active(blockIdx.x);
+  uint32_t parity = 0;
+  bool pending = false;  // a copy into Ct is in flight
+  if (tid == 0 && it < nitems) {
+    issue(it);
+    pending = true;
+  }
+  while (it < nitems) {
+    const int b = it / g.ntile, tile = it - b * g.ntile, kx0 = tile * TC;
+    const T* sp = sp_ + (size_t)b * sp_stride;
+    V2<T>* scr = (V2<T>*)scratch_ + (size_t)b * vsz;
+    if (!wf_mbar_wait(&full, parity)) lb.st[b].status = WF_ETIMEOUT;  // the tile is garbage then
+    parity ^= 1u;
+    auto ld0 = [&](int t, int row) -> V2<T> {
+      const int c = t >> lgTC, col = t & (TC - 1);
+      auto lds = [&](int cc, int rr) { return Ct[(size_t)(cc * n + rr) * TC + col]; };
+      return wf_mode_packed<T, C, false>(lds, row, c, kx0 + col, n, sp);
+    };
+    auto stl = [&](int t, int row, V2<T> v) { scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))] = v; };
+    const int itn = next_active(it + gridDim.x);
+    auto after1 = [&]() {  // every thread is done with Ct: bring in the next tile
+      if (tid == 0) {
+        pending = false;
+        if (itn < nitems) {
+          issue(itn);
+          pending = true;
+        }
+      }
+    };
+    wf_pp_fft<T, +1, true>(lgn, lgCT, 1, CT, A, Bf, s_tw, ld0, stl, after1);
+    it = itn;
+  }
+  if (tid == 0 && pending) wf_mbar_wait(&full, parity);  // only if a wait above gave up: let the copy land
 }
 
 template <typename T, int C>

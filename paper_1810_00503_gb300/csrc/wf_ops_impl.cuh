@@ -107,8 +107,66 @@ template <typename K> inline cudaError_t ensure_smem_n(K kernel, size_t bytes, i
   return e;
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver once (no link to libcuda).
+typedef CUresult (*WfEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline WfEncodeTiled wf_encode_fn() {
+  static WfEncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (WfEncodeTiled)p;
+  }
+  return fn;
+}
+
+// Persistent TMA-fed inverse column stage (k_lb_colinv_tma).
+template <typename T, int C>
+cudaError_t lb_colinv_tma(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  static int done = 0;
+  static int occ[32] = {0}, nsm[32] = {0};
+  auto k = k_lb_colinv_tma<T, C>;
+  const size_t sm = wf_colinv_tma_smem<T>();
+  cudaError_t e = ensure_smem_n(k, sm, &done);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int di = dev & 31;
+  if (!occ[di]) {
+    int o = 0, ns = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, WF_THREADS, sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    occ[di] = o > 0 ? o : 1;
+    nsm[di] = ns;
+  }
+  WfEncodeTiled enc = wf_encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  const int rows = C * g.n;
+  CUtensorMap tm;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * g.h, (cuuint64_t)2 * lb.m * b.B * rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * g.h * sizeof(T)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * g.TC), (cuuint32_t)(rows < 256 ? rows : 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(&tm, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                         lb.ring, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  int grid = nsm[di] * occ[di];
+  const int nitems = b.B * g.ntile;
+  if (grid > nitems) grid = nitems;
+  k<<<grid, WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb, b.B, tm);
+  return cudaGetLastError();
+}
+
 template <typename T, int C>
 cudaError_t lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  if (WF_COLINV_TMA) return lb_colinv_tma<T, C>(g, b, lb, st);
   static int done = 0;
   auto k = k_lb_colinv<T, C>;
   const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : col_smem<T>(g);

@@ -199,6 +199,13 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
   WfLbMap& M = st[b];
   const double* pb = part + (size_t)b * WF_NSLOT * A.maxblk;
   const int m = A.m;
+  if (M.status == WF_ETIMEOUT) {  // a bounded device wait gave up on this map's data
+    if (lane == 0) {
+      M.active = 0;
+      M.pend_alpha = 0.0;
+    }
+    return;
+  }
   if (A.phase == WF_PH_ITER) {
     if (!M.active) {
       if (lane == 0) M.pend_alpha = 0.0;
