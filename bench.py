@@ -157,15 +157,19 @@ def algorithmic_bytes(n, m, elt=4):
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_lb_comb_dram_traffic.txt")
-TRAFFIC_SOURCES = ["paper_1810_00503_gb300/csrc/wf_lbfgs.cuh", "paper_1810_00503_gb300/csrc/wf_internal.h"]
 
 
 def kernel_source_hash():
+    """Hash of what decides k_lb_comb's memory traffic: the kernel's own source
+    text and the streaming constants it is compiled with."""
     import hashlib
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    return h.hexdigest()
+    import re
+    src = open(os.path.join(ROOT, "paper_1810_00503_gb300/csrc/wf_lbfgs.cuh")).read()
+    a = src.index("k_lb_comb(WfGeo g")
+    b = src.index("// ----", a)
+    consts = open(os.path.join(ROOT, "paper_1810_00503_gb300/csrc/wf_internal.h")).read()
+    keep = "\n".join(re.findall(r"#define WF_(?:COMB_\w+|STREAM_GROUP|MAXM)\b.*", consts))
+    return hashlib.sha256((src[a:b] + keep).encode()).hexdigest()
 
 
 def measured_traffic(kernel, maps):

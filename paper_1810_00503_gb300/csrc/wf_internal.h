@@ -31,22 +31,13 @@
 #ifndef WF_FFT_PP
 #define WF_FFT_PP 1
 #endif
-// The forward column stage keeps the in-place passes: with the ping-pong tile
-// pair it measured 0.91 ms against 0.80 ms on the 120 x 1024^2 batch.
-#ifndef WF_COLFWD_PP
-#define WF_COLFWD_PP 0
-#endif
-#ifndef WF_COLFWD_PF
-#define WF_COLFWD_PF 1
-#endif
 // Inverse column stage of the iteration as a persistent kernel fed by TMA (1)
-// or one block per tile (0).
+// or one block per tile (0, also used when the driver lacks the tensor-map
+// encoder).  The row and forward column stages stay one block per tile: their
+// persistent TMA-fed forms measured slower (0.66 vs 0.59 ms, 0.93 vs 0.80 ms
+// on the 120 x 1024^2 batch).
 #ifndef WF_COLINV_TMA
 #define WF_COLINV_TMA 1
-#endif
-// p and g values the forward column stage loads per batch in its epilogue.
-#ifndef WF_COLFWD_EB
-#define WF_COLFWD_EB 16
 #endif
 
 // Resident blocks per SM requested from the compiler for the FFT-stage kernels.

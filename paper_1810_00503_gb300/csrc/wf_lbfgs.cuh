@@ -452,28 +452,9 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
   const V2<T>* gv = (const V2<T>*)lb.g + (size_t)b * vsz;
   typedef WfAcc<T> A;
   A qq = 0, pq = 0, pp = 0, gq = 0, gp = 0;
-#if WF_COLFWD_PP
-  (void)buf;
-  (void)s_tw;
-  // p and g of this tile are read after the transform: start their trip to L2 now
-#pragma unroll
-  for (int i = 0; i < (WF_COLFWD_PF ? WF_EMAX : 0); ++i) {
-    const int e = threadIdx.x + i * WF_THREADS;
-    if (e < tot) {
-      const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-      const size_t off = ((size_t)c * n + j) * h + kx0 + t;
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(Pn + off));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(gv + off));
-    }
-  }
-  const V2<T>* O = wf_col_fwd_pp<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, tw_);
-  const T* sp = sp_ + (size_t)b * sp_stride;
-  constexpr int EB = 4;  // elements per batch of loads
-#else
   wf_col_fwd_front<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, sp_ + (size_t)b * sp_stride, buf, s_tw,
                          tw_);
-  constexpr int EB = WF_COLFWD_EB;
-#endif
+  constexpr int EB = WF_EMAX;
 #pragma unroll
   for (int i0 = 0; i0 < WF_EMAX; i0 += EB) {
     V2<T> pl[EB], gl[EB];
@@ -494,12 +475,7 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
         const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
         const int kx = kx0 + t;
         const size_t off = ((size_t)c * n + j) * h + kx;
-#if WF_COLFWD_PP
-        auto lds = [&](int cc, int rr) { return O[wf_sw<T>(rr * CT + cc * TC + t)]; };
-        const V2<T> a = wf_mode_packed<T, C, true>(lds, j, c, kx, n, sp);
-#else
         const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
-#endif
         const V2<T> p = pl[ii], gg = gl[ii];
         const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
         Qn[off] = q;

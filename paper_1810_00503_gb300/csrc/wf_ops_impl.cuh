@@ -164,9 +164,45 @@ cudaError_t lb_colinv_tma(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, c
   return cudaGetLastError();
 }
 
+// Resident blocks of a persistent kernel: SMs x blocks per SM (cached per device).
+template <typename K>
+inline cudaError_t persistent_grid(K k, size_t smem, int* occ, int* nsm, int* grid) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int di = dev & 31;
+  if (!occ[di]) {
+    int o = 0, ns = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, WF_THREADS, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    occ[di] = o > 0 ? o : 1;
+    nsm[di] = ns;
+  }
+  *grid = occ[di] * nsm[di];
+  return cudaSuccess;
+}
+
+// 2-D tensor map of [rows][2 h] values of type T (packed spectra), boxes of
+// 2 TC values by min(C n, 256) rows.
+template <typename T>
+inline cudaError_t spectra_map(const WfGeo& g, void* base, long long rows, CUtensorMap* tm) {
+  WfEncodeTiled enc = wf_encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  const int crow = g.C * g.n;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * g.h, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * g.h * sizeof(T)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * g.TC), (cuuint32_t)(crow < 256 ? crow : 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(tm, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                         base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename T, int C>
 cudaError_t lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
-  if (WF_COLINV_TMA) return lb_colinv_tma<T, C>(g, b, lb, st);
+  if (WF_COLINV_TMA && wf_encode_fn()) return lb_colinv_tma<T, C>(g, b, lb, st);
   static int done = 0;
   auto k = k_lb_colinv<T, C>;
   const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : col_smem<T>(g);
@@ -180,7 +216,7 @@ template <typename T, int C>
 cudaError_t lb_colfwd(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
   auto k = k_lb_colfwd<T, C>;
-  const size_t sm = WF_COLFWD_PP ? wf_pp_smem<T>() : col_smem<T>(g);
+  const size_t sm = col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb, b.part);

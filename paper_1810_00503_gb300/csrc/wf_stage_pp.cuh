@@ -76,51 +76,27 @@ __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, 
   wf_pp_fft<T, +1, true>(lgn, lgCT, 1, C * TC, A, Bf, s_tw, ld0, stl);
 }
 
-// Forward column stage: scratch -> forward FFT along y -> shared tile O
-// (returned), synchronised; element (row j, channel c, column t) at
-// wf_sw(j * C * TC + c * TC + t), before the adjoint operator.
-template <typename T, int C>
-__device__ __forceinline__ V2<T>* wf_col_fwd_pp(const WfGeo& g, const V2<T>* scr, const void* tw_) {
-  extern __shared__ __align__(16) unsigned char wf_smem[];
-  V2<T>* s_tw = (V2<T>*)wf_smem;
-  V2<T>* A = s_tw + WF_NT;
-  V2<T>* Bf = A + WF_TILE;
-  const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1;
-  const int CT = C * TC, lgCT = lgTC + (C == 2 ? 1 : 0), kx0 = blockIdx.x * TC;
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
-  auto ld0 = [&](int t, int row) { return scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))]; };
-  V2<T>* O = wf_pp_out<T>(lgn, A, Bf);
-  auto stl = [&](int t, int row, V2<T> v) { O[wf_sw<T>(row * CT + t)] = v; };
-  wf_pp_fft<T, -1, true>(lgn, lgCT, 1, CT, A, Bf, s_tw, ld0, stl);
-  __syncthreads();
-  return O;
-}
-
 // Row stage of the objective (MODE DATA: r = d - x) or of the Hessian-vector
 // product (MODE NODATA: r = -x): c2r along x, wr = w r, partial sum r.wr, r2c
 // of wr along x, back to scratch.  The c2r pre-step pairs X[k] with X[h-k] of
 // the same row and is applied as the first pass loads; the r2c post-step runs
-// from the last pass's shared output.
-template <typename T, int MODE>
-__device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const T* d, const T* w, double* part,
-                                          const void* tw_) {
-  extern __shared__ __align__(16) unsigned char wf_smem[];
-  V2<T>* s_pt = (V2<T>*)wf_smem;
-  V2<T>* A = s_pt + WF_NT;
-  V2<T>* Bf = A + WF_TILE;
-  const V2<T>* roots = (const V2<T>*)tw_;  // exp(-2 pi i k / WF_NT), read through the cache
-  const int b = blockIdx.y, n = g.n, h = g.h, lgh = g.lgh, RB = g.RB, lgRB = __ffs(RB) - 1;
-  const int row0 = blockIdx.x * RB;
-  const size_t npix = (size_t)g.C * n * n;
+// from the last pass's shared output.  src: the RB rows of packed spectra (h
+// values each, global or shared memory); sc: where the result rows go
+// (global); d, w: the pixel rows (RB n values from the block's first row).
+// Returns this thread's part of sum r.wr.  after1 runs once the first pass has
+// finished reading src.
+template <typename T, int MODE, class H = WfNoHook>
+__device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* src, V2<T>* sc, const T* d,
+                                                   const T* w, const V2<T>* roots, const V2<T>* s_pt, V2<T>* A,
+                                                   V2<T>* Bf, H after1 = H()) {
+  const int n = g.n, h = g.h, lgh = g.lgh, RB = g.RB, lgRB = __ffs(RB) - 1;
   const int lgNTn = WF_LOG2_NT - g.lgn;
-  wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, lgh);
-  V2<T>* sc = scratch + (size_t)b * g.C * n * h + (size_t)row0 * h;
-  const V2<T>* dv = (const V2<T>*)(d + (size_t)b * npix + (size_t)row0 * n);
-  const V2<T>* wv = (const V2<T>*)(w + (size_t)b * npix + (size_t)row0 * n);
+  const V2<T>* dv = (const V2<T>*)d;
+  const V2<T>* wv = (const V2<T>*)w;
   // c2r pre-step: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]), w = exp(+2 pi i / n);
   // Z[0] from the packed X[0] + i X[h].
   auto ld0 = [&](int t, int k) -> V2<T> {
-    const V2<T>* row = sc + (size_t)t * h;
+    const V2<T>* row = src + (size_t)t * h;
     const V2<T> Xk = row[k];
     if (k == 0) return mk<T>(Xk.x + Xk.y, Xk.x - Xk.y);
     const V2<T> Xm = row[h - k];
@@ -145,7 +121,7 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
     acc += (WfAcc<T>)(r.x * wr.x + r.y * wr.y);
     O[wf_sw<T>(t * h + m)] = wr;
   };
-  wf_pp_fft<T, +1, false>(lgh, lgRB, h, 1, A, Bf, s_pt, ld0, stpix);
+  wf_pp_fft<T, +1, false>(lgh, lgRB, h, 1, A, Bf, s_pt, ld0, stpix, after1);
   __syncthreads();
   // r2c of wr: the input is O, so the passes start from the other buffer
   V2<T>* A2 = (O == A) ? Bf : A;
@@ -170,6 +146,24 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
     }
     sc[e] = X;
   }
+  return acc;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const T* d, const T* w, double* part,
+                                          const void* tw_) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  V2<T>* s_pt = (V2<T>*)wf_smem;
+  V2<T>* A = s_pt + WF_NT;
+  V2<T>* Bf = A + WF_TILE;
+  const int b = blockIdx.y, n = g.n, h = g.h;
+  const int row0 = blockIdx.x * g.RB;
+  const size_t npix = (size_t)g.C * n * n;
+  wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, g.lgh);
+  V2<T>* sc = scratch + (size_t)b * g.C * n * h + (size_t)row0 * h;
+  const size_t poff = (size_t)b * npix + (size_t)row0 * n;
+  const WfAcc<T> acc = wf_row_pp_core<T, MODE>(g, sc, sc, MODE == WF_ROW_DATA ? d + poff : nullptr, w + poff,
+                                               (const V2<T>*)tw_, s_pt, A, Bf);
   const double s = wf_block_sum((double)acc);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;
 }

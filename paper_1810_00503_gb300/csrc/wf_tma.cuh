@@ -48,3 +48,4 @@ __device__ __forceinline__ void wf_tma_load_2d(void* dst, const CUtensorMap* tm,
       "l"((uint64_t)tm), "r"(x), "r"(y), "r"(wf_smem_u32(bar))
       : "memory");
 }
+
