@@ -100,6 +100,14 @@ typedef struct {
   double c1, c2;      /* strong Wolfe constants, 0 < c1 < c2 < 1; default 1e-4, 0.9 */
   unsigned long long seed;  /* Philox key of draws made on the device (bandpower_estimate
                                with no caller-supplied fields); default 0 */
+  long long spin_limit;     /* bound of every device-side wait (the TMA-fed inverse column
+                               stage's copies), in SM clock cycles; 0 = default (4e9, about
+                               2 s at the maximum clock).  A wait that runs out stops the maps
+                               of that block with WF_ETIMEOUT; the context stays usable. */
+  int inject_timeout_map;   /* diagnostic, 0 = off (default).  k > 0: the inverse column stage
+                               never issues the copies of map k-1's tiles, so the bounded wait
+                               runs out: exercises the timeout path without a GPU fault. */
+  int pad2_;
 } wf_opts;
 
 typedef struct {

@@ -40,6 +40,8 @@ extern "C" void wf_opts_default(wf_opts* o) {
   o->c1 = 1e-4;
   o->c2 = 0.9;
   o->seed = 0;
+  o->spin_limit = 0;
+  o->inject_timeout_map = 0;
 }
 
 WfGeo wf_make_geo(int n, int C) {

@@ -137,12 +137,16 @@ cudaError_t wf_launch_band_energy(const WfGeo& g, int B, const void* s, const in
                                   const double* theta, int n_bands, double* E, cudaStream_t st);
 // L-BFGS kernels.  Streaming-kernel modes: full iteration, materialise only, dots only.
 enum { WF_LB1_FULL = 0, WF_LB1_MATERIALIZE = 1, WF_LB1_DOTS = 2 };
+// Default bound of a device-side wait, SM clock cycles (about 2 s at 2.07 GHz).
+#define WF_WAIT_CYCLES_DEFAULT 4000000000ll
 struct WfLbBufs {
   WfLbMap* st;      // [B]
   void* s;          // packed state [B][C][n][h]
   void* g;          // packed gradient
   void* ring;       // [2m][B][C][n][h]: P slots then Q slots
   int m;
+  int inject_map;   // map whose tile copies are never issued (-1: none), see wf_opts
+  long long spin_limit;  // bound of device waits, SM cycles
 };
 template <typename T>
 cudaError_t wf_launch_lb_comb(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st);

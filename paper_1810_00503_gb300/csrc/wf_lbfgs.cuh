@@ -392,24 +392,36 @@ k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, cons
     while (it < nitems && !lb.st[it / g.ntile].active) it += gridDim.x;
     return it;
   };
-  auto issue = [&](int it) {  // thread 0: the tile of work item `it` into Ct
+  // thread 0: the tile of work item `it` into Ct.  Returns whether a copy was
+  // issued (never for the map a diagnostic run names in inject_map).
+  auto issue = [&](int it) -> bool {
     const int b = it / g.ntile, tile = it - b * g.ntile;
+    if (b == lb.inject_map) return false;
     const int row0 = (lb.st[b].next * B + b) * rows;
     wf_mbar_expect_tx(&full, tile_bytes);
     for (int r = 0; r < rows; r += boxr) wf_tma_load_2d(Ct + (size_t)r * TC, &tm, 2 * tile * TC, row0 + r, &full);
+    return true;
   };
   int it = next_active(blockIdx.x);
   uint32_t parity = 0;
-  bool pending = false;  // a copy into Ct is in flight
-  if (tid == 0 && it < nitems) {
-    issue(it);
-    pending = true;
-  }
+  bool pending = false;  // a copy into Ct is in flight (thread 0's view)
+  if (tid == 0 && it < nitems) pending = issue(it);
   while (it < nitems) {
     const int b = it / g.ntile, tile = it - b * g.ntile, kx0 = tile * TC;
     const T* sp = sp_ + (size_t)b * sp_stride;
     V2<T>* scr = (V2<T>*)scratch_ + (size_t)b * vsz;
-    if (!wf_mbar_wait(&full, parity)) lb.st[b].status = WF_ETIMEOUT;  // the tile is garbage then
+    // A block-wide decision: every thread waits (bounded); if any gave up, the
+    // tile never arrived and the block stops.  Its current and remaining maps
+    // are marked WF_ETIMEOUT (none of them computes on missing data), and it
+    // returns after letting a copy it issued land (bounded again).
+    const bool late = !wf_mbar_wait(&full, parity, lb.spin_limit);
+    if (__syncthreads_or(late)) {
+      if (tid == 0) {
+        for (int r = it; r < nitems; r = next_active(r + gridDim.x)) lb.st[r / g.ntile].status = WF_ETIMEOUT;
+        if (pending) wf_mbar_wait(&full, parity, lb.spin_limit);
+      }
+      return;
+    }
     parity ^= 1u;
     auto ld0 = [&](int t, int row) -> V2<T> {
       const int c = t >> lgTC, col = t & (TC - 1);
@@ -419,18 +431,11 @@ k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, cons
     auto stl = [&](int t, int row, V2<T> v) { scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))] = v; };
     const int itn = next_active(it + gridDim.x);
     auto after1 = [&]() {  // every thread is done with Ct: bring in the next tile
-      if (tid == 0) {
-        pending = false;
-        if (itn < nitems) {
-          issue(itn);
-          pending = true;
-        }
-      }
+      if (tid == 0) pending = itn < nitems ? issue(itn) : false;
     };
     wf_pp_fft<T, +1, true>(lgn, lgCT, 1, CT, A, Bf, s_tw, ld0, stl, after1);
     it = itn;
   }
-  if (tid == 0 && pending) wf_mbar_wait(&full, parity);  // only if a wait above gave up: let the copy land
 }
 
 template <typename T, int C>

@@ -43,8 +43,9 @@ struct WfSolver {
   cudaStream_t stream;
   cudaEvent_t ev_in, ev_out;
   cudaGraphExec_t exec;
-  int g_chunk, g_maxit, g_m, g_ls;
+  int g_chunk, g_maxit, g_m, g_ls, g_inject;
   double g_gtol2, g_dchi2, g_c1, g_c2;
+  long long g_spin;
   int started;
   cudaStream_t work, g_stream;  // stream in use; stream the graph was captured on
   long long iters;     // iterations launched since the last start
@@ -478,6 +479,8 @@ static WfLbBufs lb_bufs(WfSolver* S) {
   lb.g = S->g;
   lb.ring = S->ring;
   lb.m = S->o.lbfgs_m;
+  lb.inject_map = S->o.inject_timeout_map - 1;
+  lb.spin_limit = S->o.spin_limit > 0 ? S->o.spin_limit : WF_WAIT_CYCLES_DEFAULT;
   return lb;
 }
 
@@ -519,7 +522,8 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   const int chunk = o->check_every > 0 ? o->check_every : 16;
   if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
                          S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m && S->g_ls == A.ls &&
-                         S->g_c1 == A.c1 && S->g_c2 == A.c2)) {
+                         S->g_c1 == A.c1 && S->g_c2 == A.c2 && S->g_inject == o->inject_timeout_map &&
+                         S->g_spin == o->spin_limit)) {
     if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
     // Set every kernel's attributes outside capture: one iteration, then undo
     // nothing (it is a genuine iteration of the solve).
@@ -543,6 +547,8 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
     S->g_ls = A.ls;
     S->g_c1 = A.c1;
     S->g_c2 = A.c2;
+    S->g_inject = o->inject_timeout_map;
+    S->g_spin = o->spin_limit;
     S->g_stream = st;
   }
   S->started = 1;
@@ -684,6 +690,9 @@ static wf_status check_opts(const wf_problem* p, const wf_opts* o) {
   if (!(o->gtol_rel >= 0.0) || !(o->dchi2_abs >= 0.0)) return wf_fail(WF_EINVAL, "tolerances must be >= 0");
   if (o->check_every < 0 || o->check_every > 4096) return wf_fail(WF_EINVAL, "bad check_every");
   if (o->refresh_every < 0) return wf_fail(WF_EINVAL, "bad refresh_every");
+  if (o->spin_limit < 0) return wf_fail(WF_EINVAL, "spin_limit must be >= 0");
+  if (o->inject_timeout_map < 0 || o->inject_timeout_map > p->count)
+    return wf_fail(WF_EINVAL, "inject_timeout_map = %d outside [0, %d]", o->inject_timeout_map, p->count);
   if (o->line_search != WF_LS_EXACT && o->line_search != WF_LS_WOLFE)
     return wf_fail(WF_EINVAL, "line_search = %d is not WF_LS_EXACT or WF_LS_WOLFE", o->line_search);
   if (o->line_search == WF_LS_WOLFE && !(0.0 < o->c1 && o->c1 < o->c2 && o->c2 < 1.0))

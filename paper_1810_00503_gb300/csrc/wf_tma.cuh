@@ -1,14 +1,11 @@
 // Tensor-memory-accelerator (TMA) copies and mbarriers for the persistent
 // FFT-stage kernels.  One thread issues a tile's 2-D copies; the block waits
-// on the mbarrier's transaction count.  Every wait is bounded (WF_WAIT_CYCLES
-// of the SM clock, about 2 s at the maximum clock): a wait that gives up
-// reports it to the caller, which records WF_ETIMEOUT for the map and lets the
-// block finish without waiting again.
+// on the mbarrier's transaction count.  Every wait is bounded by a limit in SM
+// clock cycles (wf_opts.spin_limit, by default WF_WAIT_CYCLES_DEFAULT, about
+// 2 s at the maximum clock): a wait that gives up reports it to the caller.
 #pragma once
 #include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)
 #include <stdint.h>
-
-#define WF_WAIT_CYCLES 4000000000ll
 
 __device__ __forceinline__ uint32_t wf_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void wf_mbar_init(uint64_t* bar, uint32_t count) {
@@ -31,12 +28,12 @@ __device__ __forceinline__ bool wf_mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Wait for the phase of parity `parity`; false if it did not complete within
-// WF_WAIT_CYCLES.
-__device__ __forceinline__ bool wf_mbar_wait(uint64_t* bar, uint32_t parity) {
+// `limit` SM clock cycles.
+__device__ __forceinline__ bool wf_mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   if (wf_mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!wf_mbar_try(bar, parity))
-    if (clock64() - t0 > WF_WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 // 2-D tiled copy global -> shared of one box at element coordinates (x, y);

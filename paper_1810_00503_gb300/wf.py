@@ -40,7 +40,8 @@ class WfOpts(ctypes.Structure):
                 ("refresh_every", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("line_search", ctypes.c_int), ("pad_", ctypes.c_int), ("c1", ctypes.c_double),
-                ("c2", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+                ("c2", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("spin_limit", ctypes.c_longlong),
+                ("inject_timeout_map", ctypes.c_int), ("pad2_", ctypes.c_int)]
 
 
 class WfSolveStats(ctypes.Structure):
@@ -62,9 +63,13 @@ class WfBandpowerOut(ctypes.Structure):
 
 
 class WfError(RuntimeError):
-    def __init__(self, status, msg):
+    """A failing call.  `result` holds the per-map outcome when the call still
+    produced one (a solve in which some maps stopped with an error)."""
+
+    def __init__(self, status, msg, result=None):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+        self.result = result
 
 
 _lib = None
@@ -491,9 +496,10 @@ class Problem:
         x = torch.empty(self.pix_shape(), dtype=self.wdtype, device=dev) if x_out else None
         st = (WfSolveStats * self.B)()
         status = lib().wf_solver_finish(self._p, _ptr(s), _ptr(x), st)
+        res = SolveResult(s=s, x=x, stats=self._stats(st))
         if status not in (0, 5):
-            _check(status)
-        return SolveResult(s=s, x=x, stats=self._stats(st))
+            raise WfError(status, lib().wf_last_error().decode(), res)
+        return res
 
     @staticmethod
     def _stats(st):
@@ -514,8 +520,7 @@ class Problem:
         x = torch.empty(self.pix_shape(), dtype=self.wdtype, device=dev) if x_out else None
         st = (WfSolveStats * self.B)()
         status = lib().wf_map_solve(self._p, ctypes.byref(o), _ptr(s0), _ptr(s), _ptr(x), st)
-        stats = [dict(iters=e.iters, evals=e.evals, status=STATUS.get(e.status, e.status),
-                      chi2=e.chi2, gnorm_rel=e.gnorm_rel) for e in st]
+        res = SolveResult(s=s, x=x, stats=self._stats(st))
         if status not in (0, 5):
-            _check(status)
-        return SolveResult(s=s, x=x, stats=stats)
+            raise WfError(status, lib().wf_last_error().decode(), res)
+        return res
