@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bandpower", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-solves", action="store_true")
     return ap.parse_args()
 
 
@@ -271,6 +272,67 @@ def run_e2e(args, dev, host, iters):
     return {"value": ev / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / iters, "d2h_bytes_per_step": d2h / iters,
             "iterations": iters, "evals": ev, "seconds": dt,
             "note": "one wf_map_solve job from pinned host inputs incl. preparation; bytes per step = job bytes / iterations"}
+
+
+def run_eval_pass(args, dev, prob, hbm, reps=20):
+    """The objective + gradient pass itself (wf_eval: steps A1-A5, no L-BFGS)
+    over the whole batch, device-timed on its stream.  Algorithmic bytes per
+    pass: read s, d and W, write the gradient, and the sqrt(P) table once
+    (shared by the maps); the scratch round trips between the three stages are
+    not counted."""
+    import torch
+    B, n = args.batch, args.n
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    s = torch.randn((B, 1, n, n // 2 + 1), generator=g, device=dev, dtype=torch.complex64)
+    grad = torch.empty_like(s)
+    chi2 = torch.empty(B, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            prob.eval(s, grad, chi2, stream=stream)
+        e0.record(stream)
+        for _ in range(reps):
+            prob.eval(s, grad, chi2, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nh = n * (n // 2 + 1)
+    alg = B * (8 * nh + 4 * n * n + 4 * n * n + 8 * nh) + 4 * nh
+    achieved = alg / (ms / 1000.0) / 1e9
+    return {"evals_per_s": B * 1000.0 / ms, "ms_per_pass": ms, "maps": B,
+            "algorithmic_bytes_per_pass": alg, "achieved_GBps": achieved, "peak_GBps": hbm, "frac": achieved / hbm,
+            "note": "wf_eval on the whole batch (A1-A5: inverse column, row and forward column stages)"}
+
+
+def run_map_solves(args, dev, n=512, maps=120):
+    """MAP solves/s: `maps` simulated CMB maps of n^2 solved together to the
+    paper's stopping rule (Delta chi^2 < 0.1), mixed precision."""
+    import torch
+    from paper_1810_00503_gb300 import synth, wf
+    inp = synth.cmb_patch(n, seed=3)
+    g = torch.Generator(device=dev)
+    g.manual_seed(91)
+    Ninv = torch.as_tensor(inp.Ninv, dtype=torch.float32, device=dev)
+    mask = torch.as_tensor(inp.mask, dtype=torch.uint8, device=dev)
+    P = torch.as_tensor(inp.P_half, dtype=torch.float32, device=dev)
+    sig = torch.where(Ninv > 0, torch.rsqrt(torch.clamp(Ninv, min=1e-30)), torch.zeros_like(Ninv))
+    Nb = Ninv[None].expand(maps, 1, n, n).contiguous()
+    prob = wf.Problem(torch.zeros_like(Nb), mask, Nb, P, precision="mixed", lbfgs_m=args.m)
+    d = prob.simulate(torch.randn(maps, 1, n, n, generator=g, device=dev),
+                      torch.randn(maps, 1, n, n, generator=g, device=dev) * sig)
+    prob.set_data(d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = prob.solve(gtol_rel=0.0, dchi2_abs=0.1, max_iter=20000, check_every=32, refresh_every=200)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    its = [st["iters"] for st in res.stats]
+    prob.close()
+    return {"map_solves_per_s": maps / dt, "seconds": dt, "n": n, "maps": maps, "stop": "Delta chi^2 < 0.1",
+            "iterations_mean": float(sum(its) / len(its)), "iterations_max": max(its),
+            "statuses": sorted({st["status"] for st in res.stats})}
 
 
 def run_bandpower(args, dev, n_sim=100, n_bands=20, n_fd=1):
@@ -525,7 +587,10 @@ def main():
                        "gnorm_rel_map0": r["stats0"]["gnorm_rel"]}}
     if rank == 0:
         line["clocks"] = r["clocks"]
+        line["eval_pass"] = run_eval_pass(args, dev, r["prob"], hbm)
         r["prob"].close()
+        if not args.no_solves:
+            line["map_solves"] = run_map_solves(args, dev)
         if not args.no_bandpower:
             line["bandpower"] = run_bandpower(args, dev)
         if not args.no_fp64:

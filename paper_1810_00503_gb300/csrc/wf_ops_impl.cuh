@@ -27,8 +27,8 @@ template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes, int
 template <typename T, int C, int IN>
 cudaError_t col_inv(const WfGeo& g, const WfBufs& b, const void* src, cudaStream_t st) {
   static int done = 0;
-  auto k = k_col_inv<T, C, IN>;
-  const size_t sm = col_smem<T>(g);
+  auto k = WF_FFT_PP ? k_col_inv_pp<T, C, IN> : k_col_inv<T, C, IN>;
+  const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, b.tw);
@@ -62,6 +62,15 @@ cudaError_t col_sim(const WfGeo& g, const WfBufs& b, cudaStream_t st) {
 template <typename T, int MODE>
 cudaError_t row(const WfGeo& g, const WfBufs& b, const void* aux, void* out, cudaStream_t st) {
   static int done = 0;
+  if constexpr (WF_FFT_PP && (MODE == WF_ROW_DATA || MODE == WF_ROW_NODATA)) {
+    static int done_pp = 0;
+    auto k = k_row_pp<T, MODE>;
+    const size_t sm = wf_pp_smem<T>();
+    cudaError_t e = ensure_smem(k, sm, &done_pp);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(g.nrb, b.B), WF_THREADS, sm, st>>>(g, b.scratch, b.d, b.w, b.part, b.tw);
+    return cudaGetLastError();
+  }
   auto k = k_row<T, MODE>;
   const size_t sm = row_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);

@@ -167,3 +167,19 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
   const double s = wf_block_sum((double)acc);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;
 }
+
+// Kernels of the objective + gradient pass on the ping-pong stages (one block
+// per column tile or row block, as k_col_inv and k_row).
+template <typename T, int C, int IN>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+k_col_inv_pp(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
+  const int b = blockIdx.y, n = g.n, h = g.h;
+  const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
+  wf_col_inv_pp<T, C, IN>(g, (const V2<T>*)src_ + (size_t)b * sstride, sp_ + (size_t)b * sp_stride,
+                          (V2<T>*)scratch_ + (size_t)b * C * n * h, tw_);
+}
+template <typename T, int MODE>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+k_row_pp(WfGeo g, void* scratch_, const void* d_, const void* w_, double* part, const void* tw_) {
+  wf_row_pp<T, MODE>(g, (V2<T>*)scratch_, (const T*)d_, (const T*)w_, part, tw_);
+}
