@@ -584,7 +584,8 @@ def main():
                          "iteration_frac": sum(ab[k] for k in names[:5]) * B
                          / (sum(kms.values()) / 1000.0) / 1e9 / hbm},
             "solver": {"maps_active_after": r["active"], "chi2_map0": r["stats0"]["chi2"],
-                       "gnorm_rel_map0": r["stats0"]["gnorm_rel"]}}
+                       "gnorm_rel_map0": r["stats0"]["gnorm_rel"],
+                       "fft_variant": r["prob"].variant(), "fft_variant_source": "autotuned"}}
     if rank == 0:
         line["clocks"] = r["clocks"]
         line["eval_pass"] = run_eval_pass(args, dev, r["prob"], hbm)

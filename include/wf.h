@@ -107,7 +107,16 @@ typedef struct {
   int inject_timeout_map;   /* diagnostic, 0 = off (default).  k > 0: the inverse column stage
                                never issues the copies of map k-1's tiles, so the bounded wait
                                runs out: exercises the timeout path without a GPU fault. */
-  int pad2_;
+  int autotune;             /* 1 (default): the first solve of each shape (n, C, precision,
+                               batch size) on a handle times the FFT-stage variants on the
+                               problem's own buffers and keeps the fastest (cached in the
+                               handle); 0: the built-in defaults */
+  int fft_variant;          /* 0 (default): as autotune says.  Otherwise a forced variant,
+                               1000 a + 100 b + 10 c + d: a = inverse column stage (1 persistent,
+                               TMA-fed; 2 ping-pong; 3 in-place), b = row stage (1 ping-pong;
+                               2 in-place), c, d = column and row tiles 1, 2 or 4 times narrower
+                               than the widest.  wf_problem_variant reports the one in use. */
+  int pad3_;
 } wf_opts;
 
 typedef struct {
@@ -128,6 +137,10 @@ typedef struct {
  * handle's problems: destroy those first. */
 wf_status wf_create(wf_handle** out, size_t workspace_limit);
 wf_status wf_destroy(wf_handle* h);
+
+/* FFT-stage variant the problem's last solver start chose (wf_opts.fft_variant
+ * encoding); before any start, the defaults. */
+wf_status wf_problem_variant(const wf_problem* p, int* variant);
 
 /* Device bytes the handle holds now (twiddle tables, problems, solver state). */
 wf_status wf_workspace_used(const wf_handle* h, size_t* bytes);

@@ -42,6 +42,25 @@ extern "C" void wf_opts_default(wf_opts* o) {
   o->seed = 0;
   o->spin_limit = 0;
   o->inject_timeout_map = 0;
+  o->autotune = 1;
+  o->fft_variant = 0;
+}
+
+static void wf_geo_tiles(WfGeo& g, int tc_div, int rb_div) {
+  int tc = WF_TILE / (g.C * g.n);
+  if (tc > g.h) tc = g.h;
+  tc /= tc_div;
+  if (tc < 2) tc = g.h < 2 ? g.h : 2;
+  g.TC = tc;
+  g.ntile = g.h / tc;
+  int rb = WF_TILE / g.h;
+  if (rb > g.C * g.n) rb = g.C * g.n;
+  rb /= rb_div;
+  if (rb < 1) rb = 1;
+  g.RB = rb;
+  g.nrb = g.C * g.n / rb;
+  g.tc_div = tc_div;
+  g.rb_div = rb_div;
 }
 
 WfGeo wf_make_geo(int n, int C) {
@@ -52,20 +71,23 @@ WfGeo wf_make_geo(int n, int C) {
   g.lgn = 0;
   while ((1 << g.lgn) < n) ++g.lgn;
   g.lgh = g.lgn - 1;
-  int tc = WF_TILE / (C * n);
-  if (tc > g.h) tc = g.h;
-  if (tc < 1) tc = 1;
-  g.TC = tc;
-  g.ntile = g.h / tc;
-  int rb = WF_TILE / g.h;
-  if (rb > C * n) rb = C * n;
-  g.RB = rb;
-  g.nrb = C * n / rb;
   const long long vsz = (long long)C * n * (n / 2);
   g.ncomb = (int)((vsz + WF_COMB_CHUNK - 1) / WF_COMB_CHUNK);
   g.ncomb = (g.ncomb + WF_STREAM_GROUP - 1) / WF_STREAM_GROUP;
+  wf_geo_tiles(g, WF_TUNE_MAXDIV, WF_TUNE_MAXDIV);  // the narrowest tiles set the stride
   g.maxblk = g.ntile > g.nrb ? g.ntile : g.nrb;
   if (g.ncomb > g.maxblk) g.maxblk = g.ncomb;
+  wf_geo_tiles(g, 1, 1);
+  g.colinv_kind = WF_COLINV_TMA ? WF_COLINV_TMA_K : WF_COLINV_PP_K;
+  g.row_kind = WF_ROW_PP_K;
+  return g;
+}
+
+WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_div, int rb_div) {
+  WfGeo g = base;
+  wf_geo_tiles(g, tc_div, rb_div);
+  g.colinv_kind = colinv_kind;
+  g.row_kind = row_kind;
   return g;
 }
 

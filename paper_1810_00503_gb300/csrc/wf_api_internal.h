@@ -12,6 +12,7 @@ struct wf_handle {
   size_t used;   // device bytes held by this handle's allocations
   std::mutex mu;
   std::unordered_map<void*, size_t> live;  // allocation -> bytes
+  std::unordered_map<long long, int> tuned;  // (n, C, precision, maps) -> FFT-stage variant
 };
 
 struct WfSolver;  // L-BFGS state, allocated on the first solve (wf_solve.cu)

@@ -89,15 +89,26 @@ struct WfLbMap {
 };
 
 // Launch geometry of one (n, C) shape.
+// Kernel variants of the L-BFGS FFT stages, chosen per shape by the autotuner
+// (wf_solve.cu) or forced through wf_opts.fft_variant.
+enum { WF_COLINV_TMA_K = 1, WF_COLINV_PP_K = 2, WF_COLINV_INPLACE_K = 3 };
+enum { WF_ROW_PP_K = 1, WF_ROW_INPLACE_K = 2 };
+#define WF_TUNE_MAXDIV 4  // tiles may be 1, 2 or 4 times narrower than the widest
+
 struct WfGeo {
   int n, h, lgn, lgh, C;
   int TC, ntile;   // packed columns per column tile, tiles per map
   int RB, nrb;     // rows per row block (over the C*n rows), row blocks per map
   int ncomb;       // partial sums per map and slot of the streaming L-BFGS kernels
-  int maxblk;      // max(ntile, nrb, ncomb): stride of the partial-sum slots
+  int maxblk;      // stride of the partial-sum slots: covers every tile choice
+  int colinv_kind, row_kind;  // WF_COLINV_*_K, WF_ROW_*_K
+  int tc_div, rb_div;         // TC and RB are the widest tile divided by these (1, 2, 4)
 };
 
+// Widest tiles and the default kernel variants.
 WfGeo wf_make_geo(int n, int C);
+// Tiles tc_div / rb_div times narrower (TC >= 2, RB >= 1), the same stride.
+WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_div, int rb_div);
 
 // Device pointers of one problem, in the working type T (float or double).
 struct WfBufs {

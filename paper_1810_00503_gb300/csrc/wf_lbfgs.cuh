@@ -337,7 +337,9 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
 // ---------------------------------------------------------------------------
 // Column stages of the Hessian-vector product on p = P[next] of each map.
 // ---------------------------------------------------------------------------
-template <typename T, int C>
+// One block per column tile; KIND WF_COLINV_PP_K (ping-pong passes) or
+// WF_COLINV_INPLACE_K (in-place passes).
+template <typename T, int C, int KIND>
 __global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb) {
   const int b = blockIdx.y;
@@ -345,11 +347,10 @@ k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const vo
   if (!M->active) return;
   const size_t vsz = (size_t)C * g.n * g.h;
   const V2<T>* p = (const V2<T>*)lb.ring + ((size_t)M->next * gridDim.y + b) * vsz;
-#if WF_FFT_PP
-  wf_col_inv_pp<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
-#else
-  wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
-#endif
+  if constexpr (KIND == WF_COLINV_PP_K)
+    wf_col_inv_pp<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
+  else
+    wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
 }
 
 // Persistent inverse column stage with the next tile prefetched by TMA.
@@ -508,13 +509,13 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
 }
 
 // Row stage of the Hessian-vector product for the maps still iterating.
-template <typename T>
+// KIND WF_ROW_PP_K (ping-pong passes) or WF_ROW_INPLACE_K (in-place passes).
+template <typename T, int KIND>
 __global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_lb_row(WfGeo g, void* scratch_, const void* w_, double* part, const void* tw_, const WfLbMap* st) {
   if (!st[blockIdx.y].active) return;
-#if WF_FFT_PP
-  wf_row_pp<T, WF_ROW_NODATA>(g, (V2<T>*)scratch_, nullptr, (const T*)w_, part, tw_);
-#else
-  k_row_body<T, WF_ROW_NODATA>(g, scratch_, nullptr, w_, nullptr, nullptr, part, tw_);
-#endif
+  if constexpr (KIND == WF_ROW_PP_K)
+    wf_row_pp<T, WF_ROW_NODATA>(g, (V2<T>*)scratch_, nullptr, (const T*)w_, part, tw_);
+  else
+    k_row_body<T, WF_ROW_NODATA>(g, scratch_, nullptr, w_, nullptr, nullptr, part, tw_);
 }

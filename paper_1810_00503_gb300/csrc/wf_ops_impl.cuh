@@ -209,16 +209,24 @@ inline cudaError_t spectra_map(const WfGeo& g, void* base, long long rows, CUten
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <typename T, int C>
-cudaError_t lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
-  if (WF_COLINV_TMA && wf_encode_fn()) return lb_colinv_tma<T, C>(g, b, lb, st);
+template <typename T, int C, int KIND>
+cudaError_t lb_colinv_tile(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
-  auto k = k_lb_colinv<T, C>;
-  const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : col_smem<T>(g);
+  auto k = k_lb_colinv<T, C, KIND>;
+  const size_t sm = KIND == WF_COLINV_PP_K ? wf_pp_smem<T>() : col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, lb);
   return cudaGetLastError();
+}
+
+// The variant in g.colinv_kind (the TMA form needs the driver's tensor-map
+// encoder; without it the ping-pong form runs).
+template <typename T, int C>
+cudaError_t lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  if (g.colinv_kind == WF_COLINV_TMA_K && wf_encode_fn()) return lb_colinv_tma<T, C>(g, b, lb, st);
+  if (g.colinv_kind == WF_COLINV_INPLACE_K) return lb_colinv_tile<T, C, WF_COLINV_INPLACE_K>(g, b, lb, st);
+  return lb_colinv_tile<T, C, WF_COLINV_PP_K>(g, b, lb, st);
 }
 
 template <typename T, int C>
@@ -379,15 +387,22 @@ template <typename T>
 cudaError_t wf_launch_lb_colfwd(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   return g.C == 1 ? wfimpl::lb_colfwd<T, 1>(g, b, lb, st) : wfimpl::lb_colfwd<T, 2>(g, b, lb, st);
 }
-template <typename T>
-cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+namespace wfimpl {
+template <typename T, int KIND>
+cudaError_t lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
-  auto k = k_lb_row<T>;
-  const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : wfimpl::row_smem<T>(g);
-  cudaError_t e = wfimpl::ensure_smem(k, sm, &done);
+  auto k = k_lb_row<T, KIND>;
+  const size_t sm = KIND == WF_ROW_PP_K ? wf_pp_smem<T>() : row_smem<T>(g);
+  cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.nrb, b.B), WF_THREADS, sm, st>>>(g, b.scratch, b.w, b.part, b.tw, lb.st);
   return cudaGetLastError();
+}
+}  // namespace wfimpl
+template <typename T>
+cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
+  return g.row_kind == WF_ROW_INPLACE_K ? wfimpl::lb_row<T, WF_ROW_INPLACE_K>(g, b, lb, st)
+                                        : wfimpl::lb_row<T, WF_ROW_PP_K>(g, b, lb, st);
 }
 template <typename T>
 cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st) {

@@ -43,7 +43,7 @@ struct WfSolver {
   cudaStream_t stream;
   cudaEvent_t ev_in, ev_out;
   cudaGraphExec_t exec;
-  int g_chunk, g_maxit, g_m, g_ls, g_inject;
+  int g_chunk, g_maxit, g_m, g_ls, g_inject, g_variant;
   double g_gtol2, g_dchi2, g_c1, g_c2;
   long long g_spin;
   int started;
@@ -484,6 +484,107 @@ static WfLbBufs lb_bufs(WfSolver* S) {
   return lb;
 }
 
+// FFT-stage variants (wf_opts.fft_variant encoding: 1000 a + 100 b + 10 c + d).
+static int variant_code(const WfGeo& g) {
+  return 1000 * g.colinv_kind + 100 * g.row_kind + 10 * g.tc_div + g.rb_div;
+}
+static bool variant_valid(int v) {
+  const int a = v / 1000, b = (v / 100) % 10, c = (v / 10) % 10, d = v % 10;
+  auto div_ok = [](int x) { return x == 1 || x == 2 || x == 4; };
+  return v >= 1000 && v < 10000 && a >= WF_COLINV_TMA_K && a <= WF_COLINV_INPLACE_K && b >= WF_ROW_PP_K &&
+         b <= WF_ROW_INPLACE_K && div_ok(c) && div_ok(d);
+}
+static WfGeo variant_geo(const WfGeo& base, int v) {
+  return wf_geo_variant(base, v / 1000, (v / 100) % 10, (v / 10) % 10, v % 10);
+}
+
+// Autotuner: times the FFT-stage variants of the Hessian-vector pass on the
+// problem's own buffers (the maps must be active; the outputs - scratch, the
+// ring slot Q[next] and the partial sums - are rewritten by the first
+// iteration) and keeps the fastest.  Column choices (inverse column stage
+// variant and column tile width) are timed with the forward column stage, then
+// the row choices (row stage variant and row block height) with those fixed.
+// Results are cached in the handle per (n, C, precision, maps).
+template <typename T>
+static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
+  const wf_opts* o = &S->o;
+  const WfGeo base = wf_make_geo(p->n, p->C);
+  if (o->fft_variant) {
+    p->g = variant_geo(base, o->fft_variant);
+    return WF_OK;
+  }
+  if (!o->autotune) {
+    p->g = base;
+    return WF_OK;
+  }
+  const long long key = (((long long)p->n * 4 + p->C) * 2 + p->precision) * 1000000LL + p->count;
+  {
+    std::lock_guard<std::mutex> lock(p->h->mu);
+    auto it = p->h->tuned.find(key);
+    if (it != p->h->tuned.end()) {
+      p->g = variant_geo(base, it->second);
+      return WF_OK;
+    }
+  }
+  const WfBufs b = wf_bufs(p);
+  const WfLbBufs lb = lb_bufs<T>(S);
+  // time on real values: the gradient as the direction P[0] (every map has
+  // next = 0 after the first refresh; the first iteration rewrites P[0])
+  WF_TRY(cudaMemcpyAsync(S->ring, S->g, (size_t)p->count * p->C * p->n * p->n * p->elt, cudaMemcpyDeviceToDevice, st));
+  cudaEvent_t e0, e1;
+  WF_TRY(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) { cudaEventDestroy(e0); return wf_cuda_fail(ce, "autotune: event"); }
+  auto timed = [&](auto&& run) -> float {  // ms of 3 runs after 2 warm-up runs; inf on failure
+    for (int i = 0; i < 2; ++i)
+      if (run() != cudaSuccess) return INFINITY;
+    if (cudaEventRecord(e0, st) != cudaSuccess) return INFINITY;
+    for (int i = 0; i < 3; ++i)
+      if (run() != cudaSuccess) return INFINITY;
+    float ms = INFINITY;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return INFINITY;
+    return ms;
+  };
+  WfGeo best = base;
+  float best_ms = INFINITY;
+  const int divs[3] = {1, 2, 4};
+  for (int ck = WF_COLINV_TMA_K; ck <= WF_COLINV_INPLACE_K; ++ck) {
+    int last_tc = -1;
+    for (int di : divs) {
+      const WfGeo g = wf_geo_variant(base, ck, base.row_kind, di, 1);
+      if (g.TC == last_tc) continue;  // no narrower tile possible
+      last_tc = g.TC;
+      const float ms = timed([&]() {
+        cudaError_t e = wf_launch_lb_colinv<T>(g, b, lb, st);
+        if (e == cudaSuccess) e = wf_launch_lb_colfwd<T>(g, b, lb, st);
+        return e;
+      });
+      if (ms < best_ms) { best_ms = ms; best = g; }
+    }
+  }
+  best_ms = INFINITY;
+  WfGeo bestr = best;
+  for (int rk = WF_ROW_PP_K; rk <= WF_ROW_INPLACE_K; ++rk) {
+    int last_rb = -1;
+    for (int di : divs) {
+      const WfGeo g = wf_geo_variant(base, best.colinv_kind, rk, best.tc_div, di);
+      if (g.RB == last_rb) continue;
+      last_rb = g.RB;
+      const float ms = timed([&]() { return wf_launch_lb_row<T>(g, b, lb, st); });
+      if (ms < best_ms) { best_ms = ms; bestr = g; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  p->g = bestr;
+  std::lock_guard<std::mutex> lock(p->h->mu);
+  p->h->tuned[key] = variant_code(bestr);
+  return WF_OK;
+}
+
 // Set up the state at s0 (or 0): true gradient, chi^2, first direction.
 template <typename T>
 static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
@@ -519,11 +620,15 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   else WF_TRY(cudaMemsetAsync(S->s, 0, (size_t)p->count * p->C * p->n * p->n * p->elt, st));
   WF_TRY(cudaMemsetAsync(S->st, 0, sizeof(WfLbMap) * p->count, st));
   WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
+  rs = choose_variant<T>(p, S, st);  // after the refresh: the maps are active
+  if (rs != WF_OK) return rs;
+  A.ntile = p->g.ntile;
+  A.nrb = p->g.nrb;
   const int chunk = o->check_every > 0 ? o->check_every : 16;
   if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
                          S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m && S->g_ls == A.ls &&
                          S->g_c1 == A.c1 && S->g_c2 == A.c2 && S->g_inject == o->inject_timeout_map &&
-                         S->g_spin == o->spin_limit)) {
+                         S->g_spin == o->spin_limit && S->g_variant == variant_code(p->g))) {
     if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
     // Set every kernel's attributes outside capture: one iteration, then undo
     // nothing (it is a genuine iteration of the solve).
@@ -548,6 +653,7 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
     S->g_c1 = A.c1;
     S->g_c2 = A.c2;
     S->g_inject = o->inject_timeout_map;
+    S->g_variant = variant_code(p->g);
     S->g_spin = o->spin_limit;
     S->g_stream = st;
   }
@@ -691,6 +797,8 @@ static wf_status check_opts(const wf_problem* p, const wf_opts* o) {
   if (o->check_every < 0 || o->check_every > 4096) return wf_fail(WF_EINVAL, "bad check_every");
   if (o->refresh_every < 0) return wf_fail(WF_EINVAL, "bad refresh_every");
   if (o->spin_limit < 0) return wf_fail(WF_EINVAL, "spin_limit must be >= 0");
+  if (o->fft_variant != 0 && !variant_valid(o->fft_variant))
+    return wf_fail(WF_EINVAL, "fft_variant = %d is not a valid variant code", o->fft_variant);
   if (o->inject_timeout_map < 0 || o->inject_timeout_map > p->count)
     return wf_fail(WF_EINVAL, "inject_timeout_map = %d outside [0, %d]", o->inject_timeout_map, p->count);
   if (o->line_search != WF_LS_EXACT && o->line_search != WF_LS_WOLFE)
@@ -809,4 +917,10 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
   }
   if (us) cudaStreamSynchronize(us);
   return worst;
+}
+
+extern "C" wf_status wf_problem_variant(const wf_problem* p, int* variant) {
+  if (!p || !variant) return wf_fail(WF_EINVAL, "wf_problem_variant: null argument");
+  *variant = variant_code(p->g);
+  return WF_OK;
 }

@@ -26,7 +26,7 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
            "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
            "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table",
-           "bandpower_iterate"]
+           "bandpower_iterate", "wf_problem_variant"]
 
 
 class WfMap(ctypes.Structure):
@@ -41,7 +41,8 @@ class WfOpts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("line_search", ctypes.c_int), ("pad_", ctypes.c_int), ("c1", ctypes.c_double),
                 ("c2", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("spin_limit", ctypes.c_longlong),
-                ("inject_timeout_map", ctypes.c_int), ("pad2_", ctypes.c_int)]
+                ("inject_timeout_map", ctypes.c_int), ("autotune", ctypes.c_int), ("fft_variant", ctypes.c_int),
+                ("pad3_", ctypes.c_int)]
 
 
 class WfSolveStats(ctypes.Structure):
@@ -87,6 +88,7 @@ def lib() -> ctypes.CDLL:
     L.wf_last_error.restype = ctypes.c_char_p
     L.wf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
     L.wf_workspace_used.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.wf_problem_variant.argtypes = [vp, ctypes.POINTER(i)]
     L.wf_band_table.argtypes = [i, i, ctypes.POINTER(d), i, d, vp]
     L.wf_destroy.argtypes = [vp]
     L.wf_opts_default.argtypes = [ctypes.POINTER(WfOpts)]
@@ -398,6 +400,12 @@ class Problem:
         if t.dtype != self._cplx() or tuple(t.shape) != self.spec_shape() or not t.is_contiguous():
             raise ValueError(f"spectrum must be contiguous {self._cplx()} of shape {self.spec_shape()}")
         return t
+
+    def variant(self):
+        """FFT-stage variant in use (wf_opts.fft_variant encoding: 1000 a + 100 b + 10 c + d)."""
+        v = ctypes.c_int()
+        _check(lib().wf_problem_variant(self._p, ctypes.byref(v)))
+        return v.value
 
     # calls --------------------------------------------------------------------
     def eval(self, s, grad=None, chi2=None, stream=None):

@@ -33,8 +33,8 @@ def test_opts_default_and_last_error_need_no_gpu():
     L.wf_opts_default(ctypes.byref(o))
     assert (o.lbfgs_m, o.max_iter, o.gtol_rel, o.check_every, o.use_graphs) == (10, 10000, 1e-6, 16, 1)
     assert (o.line_search, o.c1, o.c2, o.seed) == (wf.WF_LS_EXACT, 1e-4, 0.9, 0)
-    assert (o.spin_limit, o.inject_timeout_map) == (0, 0)
-    assert ctypes.sizeof(o) == 96  # layout of wf_opts in include/wf.h
+    assert (o.spin_limit, o.inject_timeout_map, o.autotune, o.fft_variant) == (0, 0, 1, 0)
+    assert ctypes.sizeof(o) == 104  # layout of wf_opts in include/wf.h
     assert isinstance(L.wf_last_error(), bytes)
 
 
