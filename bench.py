@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-bandpower", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-solves", action="store_true")
+    ap.add_argument("--fft-variant", type=int, default=0,
+                    help="force an FFT-stage variant (wf_opts.fft_variant code); 0 = autotune")
     return ap.parse_args()
 
 
@@ -199,7 +201,7 @@ def run_ours(args, rank, world, dev):
     with torch.cuda.stream(stream):
         prob, host = make_problem(args, rank, dev)
         prob.start(gtol_rel=0.0, dchi2_abs=0.0, max_iter=1 << 30, check_every=1, use_graphs=1,
-                   refresh_every=0)
+                   refresh_every=0, fft_variant=args.fft_variant)
         prob.step(args.warmup, sync=True)
     torch.cuda.synchronize()
     if world > 1:
@@ -585,7 +587,8 @@ def main():
                          / (sum(kms.values()) / 1000.0) / 1e9 / hbm},
             "solver": {"maps_active_after": r["active"], "chi2_map0": r["stats0"]["chi2"],
                        "gnorm_rel_map0": r["stats0"]["gnorm_rel"],
-                       "fft_variant": r["prob"].variant(), "fft_variant_source": "autotuned"}}
+                       "fft_variant": r["prob"].variant(),
+                       "fft_variant_source": "forced" if args.fft_variant else "autotuned"}}
     if rank == 0:
         line["clocks"] = r["clocks"]
         line["eval_pass"] = run_eval_pass(args, dev, r["prob"], hbm)

@@ -106,11 +106,13 @@ typedef struct {
                                of that block with WF_ETIMEOUT; the context stays usable. */
   int inject_timeout_map;   /* diagnostic, 0 = off (default).  k > 0: the inverse column stage
                                never issues the copies of map k-1's tiles, so the bounded wait
-                               runs out: exercises the timeout path without a GPU fault. */
+                               runs out: exercises the timeout path without a GPU fault.  The
+                               solve then uses the TMA-fed inverse column stage, untuned
+                               (WF_EINVAL with a forced variant that does not). */
   int autotune;             /* 1 (default): the first solve of each shape (n, C, precision,
-                               batch size) on a handle times the FFT-stage variants on the
-                               problem's own buffers and keeps the fastest (cached in the
-                               handle); 0: the built-in defaults */
+                               lbfgs_m, batch size) on a handle times the FFT-stage variants on
+                               the problem's own buffers, with a full history ring, and keeps
+                               the fastest (cached in the handle); 0: the built-in defaults */
   int fft_variant;          /* 0 (default): as autotune says.  Otherwise a forced variant,
                                1000 a + 100 b + 10 c + d: a = inverse column stage (1 persistent,
                                TMA-fed; 2 ping-pong; 3 in-place), b = row stage (1 ping-pong;

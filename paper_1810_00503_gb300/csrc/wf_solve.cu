@@ -498,6 +498,18 @@ static WfGeo variant_geo(const WfGeo& base, int v) {
   return wf_geo_variant(base, v / 1000, (v / 100) % 10, (v / 10) % 10, v % 10);
 }
 
+// Timing state for the autotuner: every map active with a full history ring
+// (npairs = m, newest pair in slot m - 1, next = 0), so that the candidates
+// stream what a steady-state iteration streams.
+__global__ void k_tune_state(WfLbMap* st, int B, int m) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  st[b].active = 1;
+  st[b].npairs = m;
+  st[b].head = m - 1;
+  st[b].next = 0;
+}
+
 // Autotuner: times the FFT-stage variants of the Hessian-vector pass on the
 // problem's own buffers (the maps must be active; the outputs - scratch, the
 // ring slot Q[next] and the partial sums - are rewritten by the first
@@ -513,11 +525,12 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
     p->g = variant_geo(base, o->fft_variant);
     return WF_OK;
   }
-  if (!o->autotune) {
+  if (!o->autotune || o->inject_timeout_map > 0) {  // the injected wait lives in the TMA-fed stage
     p->g = base;
     return WF_OK;
   }
-  const long long key = (((long long)p->n * 4 + p->C) * 2 + p->precision) * 1000000LL + p->count;
+  const int m = S->o.lbfgs_m;
+  const long long key = ((((long long)p->n * 4 + p->C) * 2 + p->precision) * 64 + m) * 1000000LL + p->count;
   {
     std::lock_guard<std::mutex> lock(p->h->mu);
     auto it = p->h->tuned.find(key);
@@ -527,14 +540,34 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
     }
   }
   const WfBufs b = wf_bufs(p);
-  const WfLbBufs lb = lb_bufs<T>(S);
-  // time on real values: the gradient as the direction P[0] (every map has
-  // next = 0 after the first refresh; the first iteration rewrites P[0])
-  WF_TRY(cudaMemcpyAsync(S->ring, S->g, (size_t)p->count * p->C * p->n * p->n * p->elt, cudaMemcpyDeviceToDevice, st));
-  cudaEvent_t e0, e1;
-  WF_TRY(cudaEventCreate(&e0));
-  cudaError_t ce = cudaEventCreate(&e1);
-  if (ce != cudaSuccess) { cudaEventDestroy(e0); return wf_cuda_fail(ce, "autotune: event"); }
+  WfLbBufs lb = lb_bufs<T>(S);
+  // Candidates run on a copy of the map states set to a full history ring and
+  // on real values: the gradient as the direction P[0].  The first iteration
+  // rewrites P[0], Q[0], the scratch and the partial sums they write.
+  WfLbMap* tst = nullptr;
+  if (wf_alloc(p->h, (void**)&tst, sizeof(WfLbMap) * p->count, "autotune state") != WF_OK) {
+    p->g = base;  // no room to time the candidates: the defaults, not cached
+    return WF_OK;
+  }
+  cudaError_t ce = cudaMemcpyAsync(S->ring, S->g, (size_t)p->count * p->C * p->n * p->n * p->elt,
+                                   cudaMemcpyDeviceToDevice, st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(tst, S->st, sizeof(WfLbMap) * p->count, cudaMemcpyDeviceToDevice, st);
+  if (ce == cudaSuccess) {
+    k_tune_state<<<(p->count + 127) / 128, 128, 0, st>>>(tst, p->count, m);
+    ce = cudaGetLastError();
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaStreamSynchronize(st);
+    wf_free(p->h, tst);
+    return wf_cuda_fail(ce, "autotune: set-up");
+  }
+  lb.st = tst;
+  lb.inject_map = -1;
   auto timed = [&](auto&& run) -> float {  // ms of 3 runs after 2 warm-up runs; inf on failure
     for (int i = 0; i < 2; ++i)
       if (run() != cudaSuccess) return INFINITY;
@@ -547,6 +580,8 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
       return INFINITY;
     return ms;
   };
+  // column choices (inverse and forward column stage together), then the row
+  // choices with the column choice fixed
   WfGeo best = base;
   float best_ms = INFINITY;
   const int divs[3] = {1, 2, 4};
@@ -576,8 +611,10 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
       if (ms < best_ms) { best_ms = ms; bestr = g; }
     }
   }
+  cudaStreamSynchronize(st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  wf_free(p->h, tst);
   cudaGetLastError();
   p->g = bestr;
   std::lock_guard<std::mutex> lock(p->h->mu);
@@ -799,6 +836,9 @@ static wf_status check_opts(const wf_problem* p, const wf_opts* o) {
   if (o->spin_limit < 0) return wf_fail(WF_EINVAL, "spin_limit must be >= 0");
   if (o->fft_variant != 0 && !variant_valid(o->fft_variant))
     return wf_fail(WF_EINVAL, "fft_variant = %d is not a valid variant code", o->fft_variant);
+  if (o->inject_timeout_map > 0 && o->fft_variant != 0 && (o->fft_variant / 1000) % 10 != WF_COLINV_TMA_K)
+    return wf_fail(WF_EINVAL, "inject_timeout_map needs the TMA-fed inverse column stage (fft_variant %d)",
+                   o->fft_variant);
   if (o->inject_timeout_map < 0 || o->inject_timeout_map > p->count)
     return wf_fail(WF_EINVAL, "inject_timeout_map = %d outside [0, %d]", o->inject_timeout_map, p->count);
   if (o->line_search != WF_LS_EXACT && o->line_search != WF_LS_WOLFE)

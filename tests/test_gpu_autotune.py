@@ -81,6 +81,12 @@ def test_autotune_picks_a_valid_variant_and_caches_it(shear64):
     prob, _ = _on_handle(h, [inp])
     prob.solve(gtol_rel=1e-8, max_iter=2000, autotune=0)
     assert prob.variant() in (1111, 2111), prob.variant()
+    # the history length is part of the tuned shape
+    prob, _ = _on_handle(h, [inp, inp, inp])
+    res = prob.solve(gtol_rel=1e-12, max_iter=5000, lbfgs_m=5)
+    assert _valid(prob.variant()), prob.variant()
+    for b in range(3):
+        assert rel(res.s[b].cpu().numpy(), rfft_u(zs)) <= 1e-10
 
 
 def _on_handle(h, inputs):
@@ -94,7 +100,7 @@ def _on_handle(h, inputs):
     return prob, ds
 
 
-@pytest.mark.parametrize("bad", [5, 999, 4111, 1311, 1131, 1113, 10111, -1111])
+@pytest.mark.parametrize("bad", [5, 999, 4111, 1311, 1131, 1113, 10111, 11111, -1111])
 def test_bad_variant_codes_rejected(bad):
     inp = synth.density_small(32, seed=0)
     prob, _ = make_problem([inp], "fp64")

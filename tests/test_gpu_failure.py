@@ -46,3 +46,5 @@ def test_bad_diagnostic_options_rejected():
         prob.solve(max_iter=3, inject_timeout_map=5)
     with pytest.raises(wf.WfError, match="EINVAL"):
         prob.solve(max_iter=3, spin_limit=-1)
+    with pytest.raises(wf.WfError, match="EINVAL"):  # the injected wait needs the TMA-fed stage
+        prob.solve(max_iter=3, inject_timeout_map=1, fft_variant=2111)
