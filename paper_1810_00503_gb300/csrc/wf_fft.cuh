@@ -23,6 +23,11 @@
 #include "wf_internal.h"
 
 
+// A hook that does nothing (default of the optional callbacks of the stages).
+struct WfNoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 template <typename T> struct V2t;
 template <> struct V2t<float>  { typedef float2  type; };
 template <> struct V2t<double> { typedef double2 type; };

@@ -53,10 +53,6 @@ __device__ __forceinline__ V2<T>* wf_pp_out(int lgL, V2<T>* A, V2<T>* B) {
   return wf_pp_np(lgL) == 2 ? B : A;
 }
 
-struct WfNoHook {
-  __device__ __forceinline__ void operator()() const {}
-};
-
 // Full transform.  Element e of sequence t sits at t * ts + e * js in the
 // shared buffers A and B (swizzled).  ld0 feeds the first pass, stl takes the
 // last pass's outputs; a barrier separates consecutive passes.  after1 runs

@@ -37,6 +37,18 @@ __device__ __forceinline__ double wf_block_sum(double v) {
   return r;
 }
 
+// Ask L2 to fetch `rows` segments of `seg` bytes, `stride` bytes apart, from
+// `base` (one request per 128-byte line, spread over the block's threads), so
+// that loads issued later in the kernel find them there.
+__device__ __forceinline__ void wf_prefetch_rows(const void* base, int rows, size_t stride, int seg) {
+  const int lpr = (seg + 127) >> 7, tot = rows * lpr;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int r = i / lpr, l = i - r * lpr;
+    const char* a = (const char*)base + (size_t)r * stride + ((size_t)l << 7);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+  }
+}
+
 // Stage the roots of unity (lgL = 0) or the pass table of length 2^lgL.
 template <typename T>
 __device__ __forceinline__ void wf_stage_tw(V2<T>* s_tw, const V2<T>* g_tw, int lgL = 0) {
@@ -62,15 +74,14 @@ __device__ __forceinline__ void wf_ks(int kx, int j, int n, T& c, T& s) {
 // Per-mode operator on the C channel values of one mode.
 //   forward (ADJ = false): v <- R(k) diag(sp) v * extra        (step A1)
 //   adjoint (ADJ = true):  v <- diag(sp) R(k)^T v * extra      (step A5)
-// sp points at this map's [C][n][n/2+1] table of sqrt(P)/n.
+// wf_mode_op_pre takes a0, a1 = the two channels' sqrt(P)/n times extra (a1
+// unused for C = 1); wf_mode_op reads them from sp, this map's [C][n][n/2+1]
+// table of sqrt(P)/n.
 template <typename T, int C, bool ADJ>
-__device__ __forceinline__ void wf_mode_op(V2<T>* v, int j, int kx, int n, const T* sp, T extra) {
-  const int pitch = (n >> 1) + 1;
-  const T a0 = sp[j * pitch + kx] * extra;
+__device__ __forceinline__ void wf_mode_op_pre(V2<T>* v, int j, int kx, int n, T a0, T a1) {
   if constexpr (C == 1) {
     v[0] = cscale<T>(v[0], a0);
   } else {
-    const T a1 = sp[(size_t)n * pitch + j * pitch + kx] * extra;
     T c, s;
     wf_ks<T>(kx, j, n, c, s);
     if constexpr (!ADJ) {
@@ -83,6 +94,14 @@ __device__ __forceinline__ void wf_mode_op(V2<T>* v, int j, int kx, int n, const
       v[1] = cscale<T>(mk<T>(-s * e.x + c * b.x, -s * e.y + c * b.y), a1);
     }
   }
+}
+
+template <typename T, int C, bool ADJ>
+__device__ __forceinline__ void wf_mode_op(V2<T>* v, int j, int kx, int n, const T* sp, T extra) {
+  const int pitch = (n >> 1) + 1;
+  const T a0 = sp[j * pitch + kx] * extra;
+  const T a1 = C == 2 ? sp[(size_t)n * pitch + j * pitch + kx] * extra : (T)0;
+  wf_mode_op_pre<T, C, ADJ>(v, j, kx, n, a0, a1);
 }
 
 // Unpack the packed column value pair (Y[j], Y[n-j]) into the kx = 0 and
@@ -102,16 +121,30 @@ __device__ __forceinline__ V2<T> wf_pack0(V2<T> X0, V2<T> Xh) { return mk<T>(X0.
 // starting at packed column kx0.  The packed column 0 is unpacked in pairs.
 template <typename T, int C, bool ADJ>
 __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx0, const T* sp, T extra) {
-  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1;
-  for (int e = threadIdx.x; e < n * TC; e += blockDim.x) {
-    const int t = e & (TC - 1), j = e >> lgTC, kx = kx0 + t;
-    if (kx == 0) continue;
-    V2<T> v[C];
+  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, pitch = h + 1;
+  // U elements per trip, their sqrt(P) values loaded before any is used
+  constexpr int U = 8;
+  for (int e0 = threadIdx.x; e0 < n * TC; e0 += U * blockDim.x) {
+    T a0[U], a1[U];
 #pragma unroll
-    for (int c = 0; c < C; ++c) v[c] = buf[wf_sw<T>(j * CT + c * TC + t)];
-    wf_mode_op<T, C, ADJ>(v, j, kx, n, sp, extra);
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x, t = e & (TC - 1), j = e >> lgTC;
+      if (e < n * TC) {
+        a0[u] = sp[j * pitch + kx0 + t];
+        if constexpr (C == 2) a1[u] = sp[(size_t)n * pitch + j * pitch + kx0 + t];
+      }
+    }
 #pragma unroll
-    for (int c = 0; c < C; ++c) buf[wf_sw<T>(j * CT + c * TC + t)] = v[c];
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x, t = e & (TC - 1), j = e >> lgTC, kx = kx0 + t;
+      if (e >= n * TC || kx == 0) continue;
+      V2<T> v[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = buf[wf_sw<T>(j * CT + c * TC + t)];
+      wf_mode_op_pre<T, C, ADJ>(v, j, kx, n, a0[u] * extra, C == 2 ? a1[u] * extra : (T)0);
+#pragma unroll
+      for (int c = 0; c < C; ++c) buf[wf_sw<T>(j * CT + c * TC + t)] = v[c];
+    }
   }
   if (kx0 == 0) {
     for (int j = threadIdx.x; j <= h; j += blockDim.x) {

@@ -159,6 +159,11 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
   const int b = blockIdx.y, n = g.n, h = g.h;
   const int row0 = blockIdx.x * g.RB;
   const size_t npix = (size_t)g.C * n * n;
+  {  // the pixel rows are read by the last pass: start them towards L2
+    const size_t off = (size_t)b * npix + (size_t)row0 * n;
+    wf_prefetch_rows(w + off, 1, 0, g.RB * n * (int)sizeof(T));
+    if (MODE == WF_ROW_DATA) wf_prefetch_rows(d + off, 1, 0, g.RB * n * (int)sizeof(T));
+  }
   wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, g.lgh);
   V2<T>* sc = scratch + (size_t)b * g.C * n * h + (size_t)row0 * h;
   const size_t poff = (size_t)b * npix + (size_t)row0 * n;
