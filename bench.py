@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-bandpower", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-solves", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the single-map and 512^2 eval loops, the heterogeneous batch and the ALU peaks")
     ap.add_argument("--fft-variant", type=int, default=0,
                     help="force an FFT-stage variant (wf_opts.fft_variant code); 0 = autotune")
     return ap.parse_args()
@@ -276,14 +278,15 @@ def run_e2e(args, dev, host, iters):
             "note": "one wf_map_solve job from pinned host inputs incl. preparation; bytes per step = job bytes / iterations"}
 
 
-def run_eval_pass(args, dev, prob, hbm, reps=20):
+def run_eval_pass(args, dev, prob, hbm, reps=20, B=None, n=None):
     """The objective + gradient pass itself (wf_eval: steps A1-A5, no L-BFGS)
     over the whole batch, device-timed on its stream.  Algorithmic bytes per
     pass: read s, d and W, write the gradient, and the sqrt(P) table once
     (shared by the maps); the scratch round trips between the three stages are
     not counted."""
     import torch
-    B, n = args.batch, args.n
+    B = args.batch if B is None else B
+    n = args.n if n is None else n
     g = torch.Generator(device=dev)
     g.manual_seed(5)
     s = torch.randn((B, 1, n, n // 2 + 1), generator=g, device=dev, dtype=torch.complex64)
@@ -306,6 +309,84 @@ def run_eval_pass(args, dev, prob, hbm, reps=20):
     return {"evals_per_s": B * 1000.0 / ms, "ms_per_pass": ms, "maps": B,
             "algorithmic_bytes_per_pass": alg, "achieved_GBps": achieved, "peak_GBps": hbm, "frac": achieved / hbm,
             "note": "wf_eval on the whole batch (A1-A5: inverse column, row and forward column stages)"}
+
+
+def run_eval_shapes(args, dev, hbm):
+    """The objective + gradient pass on two more workloads: one 1024^2 map
+    alone (latency-bound: one map cannot fill the GPU) and 256 maps of 512^2."""
+    import types
+    out = {}
+    for key, n, B, reps in (("single_1024", 1024, 1, 200), ("batch_256x512", 512, 256, 20)):
+        prob, _ = make_problem(types.SimpleNamespace(n=n, batch=B, m=args.m), 0, dev)
+        out[key] = run_eval_pass(args, dev, prob, hbm, reps=reps, B=B, n=n)
+        out[key].pop("note", None)
+        prob.close()
+    return out
+
+
+def run_hetero(args, dev, count=256, n_bands=10):
+    """Heterogeneous batch: `count` independent maps of n in {64, 128, 256,
+    512} (uneven masks, noise levels and spectral slopes), one problem per
+    size solved together by wf_map_solve_many to ||g|| / ||g0|| < 1e-6 in
+    mixed precision; then d chi^2 / d log q for n_bands log-spaced bands at the
+    solutions through the adjoint stage (wf_eval_bands)."""
+    import numpy as np
+    import torch
+    from paper_1810_00503_gb300 import synth, wf
+    maps = synth.hetero_batch(count=count, seed=4)
+    groups = {}
+    for mp in maps:
+        groups.setdefault(mp.n, []).append(mp)
+    probs, sizes = [], []
+    for n in sorted(groups):
+        ms = groups[n]
+        B = len(ms)
+        f32 = lambda a: torch.as_tensor(np.stack(a), dtype=torch.float32, device=dev).contiguous()
+        Ninv = f32([mp.Ninv for mp in ms])
+        mask = torch.as_tensor(np.stack([mp.mask for mp in ms]), dtype=torch.uint8, device=dev)
+        P = f32([mp.P_half for mp in ms])
+        prob = wf.Problem(torch.zeros_like(Ninv), mask, Ninv, P, precision="mixed", lbfgs_m=args.m)
+        prob.set_data(prob.simulate(f32([mp.z for mp in ms]), f32([mp.noise for mp in ms])))
+        probs.append(prob)
+        sizes.append((n, B))
+    torch.cuda.synchronize()
+    wf.solve_many(probs, gtol_rel=1e-6, max_iter=2)  # tunes each shape, builds the graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = wf.solve_many(probs, gtol_rel=1e-6, max_iter=20000, check_every=32, refresh_every=200)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    evals = sum(st["evals"] for r in res for st in r.stats)
+    per = {str(n): {"maps": B, "iterations_mean": float(np.mean([st["iters"] for st in r.stats])),
+                    "fft_variant": p.variant()} for (n, B), r, p in zip(sizes, res, probs)}
+    statuses = sorted({st["status"] for r in res for st in r.stats})
+    # d chi^2 / d log q at the solutions
+    bands = [torch.as_tensor(wf.band_table(n, np.geomspace(1.0, n / 2, n_bands + 1)), device=dev)
+             for n, _ in sizes]
+    reps = 10
+    for p, r, bt in zip(probs, res, bands):
+        p.eval_bands(r.s, bt, n_bands)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for p, r, bt in zip(probs, res, bands):
+            p.eval_bands(r.s, bt, n_bands)
+    torch.cuda.synchronize()
+    dq_dt = (time.perf_counter() - t0) / reps
+    for p in probs:
+        p.close()
+    return {"maps": count, "sizes": per, "seconds": dt, "map_solves_per_s": count / dt,
+            "evals_per_s": evals / dt, "stop": "||g||/||g0|| < 1e-6", "statuses": statuses,
+            "dchi2_dlogq": {"bands": n_bands, "ms_per_batch": dq_dt * 1e3, "maps_per_s": count / dq_dt},
+            "note": "one problem per size, all sizes solved together by wf_map_solve_many (one stream each); "
+                    "a 2-iteration solve first tunes each shape and captures its graphs"}
+
+
+def run_alu_peaks():
+    """Measured FMA throughput (wf_alu_peak), TFLOP/s."""
+    from paper_1810_00503_gb300 import wf
+    return {"fp32_tflops": wf.alu_peak("f32") / 1e12, "fp64_tflops": wf.alu_peak("f64") / 1e12,
+            "how": "independent FMA chains on every SM's resident blocks, about 40 ms each"}
 
 
 def run_map_solves(args, dev, n=512, maps=120):
@@ -394,7 +475,7 @@ def iteration_flops(n, m):
     return 2 * fft + vals * (4 * (5 * m + 9) + 10)
 
 
-def run_fp64_reference(args, dev, gtol=1e-6):
+def run_fp64_reference(args, dev, gtol=1e-6, fp64_peak=None):
     """The plain single-map FP64 GPU path on map 0 of the workload: iteration
     throughput, and one solve to ||g|| / ||g0|| < gtol compared with the mixed
     batched path's solution of the same map to the same tolerance."""
@@ -442,13 +523,15 @@ def run_fp64_reference(args, dev, gtol=1e-6):
     p32.close()
     flops = iteration_flops(n, args.m)
     achieved = flops / (it_ms / 1000.0) / 1e12
+    peak = fp64_peak or FP64_PEAK_TFLOPS
+    src = ("measured on this GPU (wf_alu_peak, FP64 FMA chains)" if fp64_peak
+           else "nominal GB300 FP64 rate (no measured FP64 peak)")
     return {"fp64_single_map_evals_per_s": 1000.0 / it_ms, "fp64_single_map_ms_per_iteration": it_ms,
             "fp64_single_map_solve_s": t64, "fp64_iterations": r64.stats[0]["iters"],
             "mixed_single_map_solve_s": t32, "mixed_iterations": r32.stats[0]["iters"],
             "gtol_rel": gtol, "mixed_vs_fp64_rel_l2": err,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_iteration": flops,
-                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "flops_per_iteration": flops, "peak_source": src},
             "note": "map 0 of the workload; the batched mixed path's per-map cost is ms_per_step / maps"}
 
 
@@ -593,12 +676,19 @@ def main():
         line["clocks"] = r["clocks"]
         line["eval_pass"] = run_eval_pass(args, dev, r["prob"], hbm)
         r["prob"].close()
+        if not args.no_extra:
+            line["eval_shapes"] = run_eval_shapes(args, dev, hbm)
         if not args.no_solves:
             line["map_solves"] = run_map_solves(args, dev)
+        if not args.no_extra:
+            line["hetero"] = run_hetero(args, dev)
+        alu = run_alu_peaks() if not args.no_extra else {}
+        if alu:
+            line["alu_peaks"] = alu
         if not args.no_bandpower:
             line["bandpower"] = run_bandpower(args, dev)
         if not args.no_fp64:
-            line["fp64_reference"] = run_fp64_reference(args, dev)
+            line["fp64_reference"] = run_fp64_reference(args, dev, fp64_peak=alu.get("fp64_tflops"))
         if not args.no_e2e:
             line["e2e"] = run_e2e(args, dev, r["host"], iters=max(K, 10))
         if not args.no_cpu:

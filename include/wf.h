@@ -414,6 +414,13 @@ wf_status wf_normal_draw(unsigned long long seed, unsigned int stream_id, unsign
 wf_status wf_eval_noalloc(const void* s, const void* d, const void* w, const void* P, int n, int C,
                           int count, int precision, double* chi2, void* grad, void* stream);
 
+/* Measured fused multiply-add throughput of the current device, in flop/s
+ * (2 per FMA), for dtype WF_F32 or WF_F64: every SM's resident blocks run
+ * independent FMA chains for about 40 ms.  Measurement support for the ALU
+ * roofline of the FP64 path; the paper has no counterpart.  Synchronises the
+ * device's work it launches (a private stream); allocates one value. */
+wf_status wf_alu_peak(int dtype, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
            "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
            "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table",
-           "bandpower_iterate", "wf_problem_variant"]
+           "bandpower_iterate", "wf_problem_variant", "wf_alu_peak"]
 
 
 class WfMap(ctypes.Structure):
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
     L.wf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
     L.wf_workspace_used.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.wf_problem_variant.argtypes = [vp, ctypes.POINTER(i)]
+    L.wf_alu_peak.argtypes = [i, ctypes.POINTER(d)]
     L.wf_band_table.argtypes = [i, i, ctypes.POINTER(d), i, d, vp]
     L.wf_destroy.argtypes = [vp]
     L.wf_opts_default.argtypes = [ctypes.POINTER(WfOpts)]
@@ -223,6 +224,13 @@ def solve_many(problems, stream=None, **opts):
     if status not in (0, 5):
         _check(status)
     return [SolveResult(s=t, x=None, stats=Problem._stats(st)) for t, st in zip(outs, sts)]
+
+
+def alu_peak(dtype="f32"):
+    """wf_alu_peak: measured FMA throughput of the current device, flop/s."""
+    v = ctypes.c_double()
+    _check(lib().wf_alu_peak(WF_F64 if dtype in ("f64", "fp64") else WF_F32, ctypes.byref(v)))
+    return v.value
 
 
 def band_table(n, edges, C=1, kscale=1.0):
