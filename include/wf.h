@@ -110,14 +110,19 @@ typedef struct {
                                solve then uses the TMA-fed inverse column stage, untuned
                                (WF_EINVAL with a forced variant that does not). */
   int autotune;             /* 1 (default): the first solve of each shape (n, C, precision,
-                               lbfgs_m, batch size) on a handle times the FFT-stage variants on
-                               the problem's own buffers, with a full history ring, and keeps
-                               the fastest (cached in the handle); 0: the built-in defaults */
+                               lbfgs_m, batch size) on a handle times the FFT-stage variants
+                               (kernels, radix plans, tile widths) on the problem's own buffers,
+                               with a full history ring, and keeps the fastest (cached in the
+                               handle); 0: the built-in defaults */
   int fft_variant;          /* 0 (default): as autotune says.  Otherwise a forced variant,
-                               1000 a + 100 b + 10 c + d: a = inverse column stage (1 persistent,
-                               TMA-fed; 2 ping-pong; 3 in-place), b = row stage (1 ping-pong;
-                               2 in-place), c, d = column and row tiles 1, 2 or 4 times narrower
-                               than the widest.  wf_problem_variant reports the one in use. */
+                               100000 f + 10000 e + 1000 a + 100 b + 10 c + d: a = inverse column
+                               stage (1 persistent, TMA-fed; 2 ping-pong; 3 in-place), b = row
+                               stage (1 ping-pong; 2 in-place), c, d = column and row tiles 1, 2
+                               or 4 times narrower than the widest, f, e = radix plans of the
+                               ping-pong column and row passes (0: larger radices first,
+                               1024 = 16 x 8 x 8; 1: ascending, 8 x 8 x 16; 2: radix 32 first
+                               for lengths 512 and 1024, 32 x 32).  wf_problem_variant reports
+                               the one in use. */
   int pad3_;
 } wf_opts;
 

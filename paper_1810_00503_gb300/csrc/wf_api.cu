@@ -80,22 +80,48 @@ WfGeo wf_make_geo(int n, int C) {
   wf_geo_tiles(g, 1, 1);
   g.colinv_kind = WF_COLINV_TMA ? WF_COLINV_TMA_K : WF_COLINV_PP_K;
   g.row_kind = WF_ROW_PP_K;
+  g.col_plan = g.row_plan = 0;
   return g;
 }
 
-WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_div, int rb_div) {
+WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_div, int rb_div, int col_plan,
+                     int row_plan) {
   WfGeo g = base;
   wf_geo_tiles(g, tc_div, rb_div);
   g.colinv_kind = colinv_kind;
   g.row_kind = row_kind;
+  g.col_plan = col_plan;
+  g.row_plan = row_plan;
   return g;
 }
 
-// Twiddle buffer of WF_TWTAB entries (layout in wf_internal.h).  Roots of unity
-// exp(-2 pi i k / WF_NT) are computed in long double, with the values at
-// multiples of pi/2 set exactly.  The pass table of length L = 2^lgL follows the
-// radix plan of fft_smem: the pass with span Ns and radix R holds
-// exp(-2 pi i k r / (Ns R)) at (Ns - R1) + (r - 1) Ns + k, R1 the first radix.
+// Pass tables of radix plan `plan` (layout in wf_internal.h) from the roots
+// of unity in roots[0, WF_NT): the pass with span Ns and radix R of the length
+// 2^lgL transform holds exp(-2 pi i k r / (Ns R)) at (Ns - R1) + (r - 1) Ns + k,
+// R1 the radix of the first pass, so consecutive butterflies read consecutive
+// entries.
+static void wf_plan_tables(const double2* roots, int plan, double2* block) {
+  for (int lgL = 1; lgL <= WF_LOG2_NT; ++lgL) {
+    double2* tab = block + (size_t)WF_NT * lgL;
+    for (int i = 0; i < WF_NT; ++i) { tab[i].x = 0.0; tab[i].y = 0.0; }
+    const int np = wf_plan_np(lgL, plan);
+    int lgNs = 0, R1 = 1;
+    for (int p = 0; p < np; ++p) {
+      const int bits = wf_plan_bits(lgL, plan, p), R = 1 << bits, Ns = 1 << lgNs;
+      if (p == 0) R1 = R;
+      if (Ns > 1) {
+        const int sh = WF_LOG2_NT - lgNs - bits;
+        for (int r = 1; r < R; ++r)
+          for (int k = 0; k < Ns; ++k) tab[(Ns - R1) + (r - 1) * Ns + k] = roots[(k * r) << sh];
+      }
+      lgNs += bits;
+    }
+  }
+}
+
+// Twiddle buffer of WF_TWTAB entries (plan 0; layout in wf_internal.h).  Roots
+// of unity exp(-2 pi i k / WF_NT) are computed in long double, with the values
+// at multiples of pi/2 set exactly.
 void wf_make_twiddles(double2* out) {
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int k = 0; k < WF_NT; ++k) {
@@ -109,22 +135,16 @@ void wf_make_twiddles(double2* out) {
     out[k].x = c;
     out[k].y = s;
   }
-  for (int lgL = 1; lgL <= WF_LOG2_NT; ++lgL) {
-    double2* tab = out + (size_t)WF_NT * lgL;
-    for (int i = 0; i < WF_NT; ++i) { tab[i].x = 0.0; tab[i].y = 0.0; }
-    const int np = (lgL + 3) >> 2;
-    int rem = lgL, lgNs = 0, R1 = 1;
-    for (int p = 0; p < np; ++p) {
-      const int left = np - p, bits = (rem + left - 1) / left, R = 1 << bits, Ns = 1 << lgNs;
-      if (p == 0) R1 = R;
-      if (Ns > 1) {
-        const int sh = WF_LOG2_NT - lgNs - bits;
-        for (int r = 1; r < R; ++r)
-          for (int k = 0; k < Ns; ++k) tab[(Ns - R1) + (r - 1) * Ns + k] = out[(k * r) << sh];
-      }
-      rem -= bits;
-      lgNs += bits;
-    }
+  wf_plan_tables(out, 0, out);
+}
+
+// All WF_NPLAN blocks (WF_TWTAB_ALL entries).
+static void wf_make_twiddles_all(double2* out) {
+  wf_make_twiddles(out);
+  for (int plan = 1; plan < WF_NPLAN; ++plan) {
+    double2* block = out + (size_t)WF_TWTAB * plan;
+    for (int k = 0; k < WF_NT; ++k) block[k] = out[k];
+    wf_plan_tables(out, plan, block);
   }
 }
 
@@ -137,21 +157,22 @@ extern "C" wf_status wf_create(wf_handle** out, size_t workspace_limit) {
   h->used = 0;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) { delete h; return wf_cuda_fail(e, "wf_create: cudaGetDevice"); }
-  double2* tw64 = (double2*)malloc(sizeof(double2) * WF_TWTAB);
-  float2* tw32 = (float2*)malloc(sizeof(float2) * WF_TWTAB);
+  double2* tw64 = (double2*)malloc(sizeof(double2) * WF_TWTAB_ALL);
+  float2* tw32 = (float2*)malloc(sizeof(float2) * WF_TWTAB_ALL);
   if (!tw64 || !tw32) {
     free(tw64);
     free(tw32);
     delete h;
     return wf_fail(WF_ENOMEM, "wf_create: host allocation failed");
   }
-  wf_make_twiddles(tw64);
-  for (int k = 0; k < WF_TWTAB; ++k) { tw32[k].x = (float)tw64[k].x; tw32[k].y = (float)tw64[k].y; }
-  wf_status s = wf_alloc(h, &h->tw64, sizeof(double2) * WF_TWTAB, "twiddle tables");
-  if (s == WF_OK) s = wf_alloc(h, &h->tw32, sizeof(float2) * WF_TWTAB, "twiddle tables");
+  wf_make_twiddles_all(tw64);
+  for (int k = 0; k < WF_TWTAB_ALL; ++k) { tw32[k].x = (float)tw64[k].x; tw32[k].y = (float)tw64[k].y; }
+  wf_status s = wf_alloc(h, &h->tw64, sizeof(double2) * WF_TWTAB_ALL, "twiddle tables");
+  if (s == WF_OK) s = wf_alloc(h, &h->tw32, sizeof(float2) * WF_TWTAB_ALL, "twiddle tables");
   e = cudaSuccess;
-  if (s == WF_OK) e = cudaMemcpy(h->tw64, tw64, sizeof(double2) * WF_TWTAB, cudaMemcpyHostToDevice);
-  if (s == WF_OK && e == cudaSuccess) e = cudaMemcpy(h->tw32, tw32, sizeof(float2) * WF_TWTAB, cudaMemcpyHostToDevice);
+  if (s == WF_OK) e = cudaMemcpy(h->tw64, tw64, sizeof(double2) * WF_TWTAB_ALL, cudaMemcpyHostToDevice);
+  if (s == WF_OK && e == cudaSuccess)
+    e = cudaMemcpy(h->tw32, tw32, sizeof(float2) * WF_TWTAB_ALL, cudaMemcpyHostToDevice);
   free(tw64);
   free(tw32);
   if (s != WF_OK || e != cudaSuccess) {

@@ -6,8 +6,8 @@
 
 struct wf_handle {
   int device;
-  void* tw64;   // WF_TWTAB double2 twiddles (roots of unity, pass tables)
-  void* tw32;   // WF_TWTAB float2 twiddles
+  void* tw64;   // WF_TWTAB_ALL double2 twiddles (roots of unity, pass tables of every plan)
+  void* tw32;   // WF_TWTAB_ALL float2 twiddles
   size_t limit;  // workspace limit in bytes (0 = none)
   size_t used;   // device bytes held by this handle's allocations
   std::mutex mu;

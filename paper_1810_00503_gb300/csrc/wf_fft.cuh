@@ -50,24 +50,31 @@ template <typename T> __device__ __forceinline__ V2<T> cscale(V2<T> a, T s) { re
 // multiply by i
 template <typename T> __device__ __forceinline__ V2<T> mul_i(V2<T> a) { return mk<T>(-a.y, a.x); }
 
-// Sixteenth roots of unity, cos and sin of 2 pi k / 16 for k = 0..7, to the
-// precision of the mathematics (values of cos(pi/8), sqrt(2)/2, sin(pi/8)).
-#define WF_C1 0.9238795325112867561281832
-#define WF_S1 0.3826834323650897717284600
-#define WF_R2 0.7071067811865475244008444
+// Thirty-second roots of unity: cos and sin of pi/16, pi/8, 3 pi/16 and
+// pi/4, to the precision of the mathematics; the other angles below pi follow
+// by symmetry.
+#define WF_C16 0.9807852804032304491261822  // cos(pi/16)
+#define WF_S16 0.1950903220161282678482849  // sin(pi/16)
+#define WF_C1 0.9238795325112867561281832   // cos(pi/8)
+#define WF_S1 0.3826834323650897717284600   // sin(pi/8)
+#define WF_C3 0.8314696123025452370787884   // cos(3 pi/16)
+#define WF_S3 0.5555702330196022247428308   // sin(3 pi/16)
+#define WF_R2 0.7071067811865475244008444   // cos(pi/4)
 
-// Multiply v by exp(DIR * 2 pi i q / 16) with q known at compile time.
+// Multiply v by exp(DIR * 2 pi i q / 32) with q known at compile time.
 template <typename T, int DIR, int Q>
-__device__ __forceinline__ V2<T> rot16(V2<T> v) {
-  static_assert(Q >= 0 && Q < 8, "root index");
+__device__ __forceinline__ V2<T> rot32(V2<T> v) {
+  static_assert(Q >= 0 && Q < 16, "root index");
   constexpr T s = (T)DIR;  // sign of the angle
   if constexpr (Q == 0) {
     return v;
-  } else if constexpr (Q == 4) {  // exp(DIR i pi/2) = DIR * i
+  } else if constexpr (Q == 8) {  // exp(DIR i pi/2) = DIR * i
     return (DIR > 0) ? mul_i<T>(v) : mk<T>(v.y, -v.x);
   } else {
-    constexpr double cs[8] = {1.0, WF_C1, WF_R2, WF_S1, 0.0, -WF_S1, -WF_R2, -WF_C1};
-    constexpr double sn[8] = {0.0, WF_S1, WF_R2, WF_C1, 1.0, WF_C1, WF_R2, WF_S1};
+    constexpr double cs[16] = {1.0,   WF_C16,  WF_C1,  WF_C3,  WF_R2,  WF_S3,  WF_S1,  WF_S16,
+                               0.0,  -WF_S16, -WF_S1, -WF_S3, -WF_R2, -WF_C3, -WF_C1, -WF_C16};
+    constexpr double sn[16] = {0.0,  WF_S16, WF_S1, WF_S3, WF_R2, WF_C3, WF_C1, WF_C16,
+                               1.0,  WF_C16, WF_C1, WF_C3, WF_R2, WF_S3, WF_S1, WF_S16};
     const T c = (T)cs[Q], sv = s * (T)sn[Q];
     return mk<T>(v.x * c - v.y * sv, v.x * sv + v.y * c);
   }
@@ -79,6 +86,7 @@ template <> struct Log2R<2> { static constexpr int v = 1; };
 template <> struct Log2R<4> { static constexpr int v = 2; };
 template <> struct Log2R<8> { static constexpr int v = 3; };
 template <> struct Log2R<16> { static constexpr int v = 4; };
+template <> struct Log2R<32> { static constexpr int v = 5; };
 
 __host__ __device__ constexpr int bitrev_c(int i, int bits) {
   int r = 0;
@@ -94,7 +102,7 @@ __device__ __forceinline__ void dit_q(V2<T>* v) {
 #pragma unroll
     for (int s = 0; s < R; s += LEN) {
       V2<T> a = v[s + Q];
-      V2<T> b = rot16<T, DIR, Q * (16 / LEN)>(v[s + Q + LEN / 2]);
+      V2<T> b = rot32<T, DIR, Q * (32 / LEN)>(v[s + Q + LEN / 2]);
       v[s + Q] = cadd<T>(a, b);
       v[s + Q + LEN / 2] = csub<T>(a, b);
     }

@@ -9,8 +9,38 @@
 #define WF_NT 1024          // largest transform length and twiddle-table size
 #define WF_LOG2_NT 10
 // Twiddle buffer: [0, WF_NT) roots of unity exp(-2 pi i k / WF_NT); then for
-// lgL = 1..10 the pass table of length 2^lgL at WF_NT * lgL (2^lgL - 1 entries).
+// lgL = 1..10 the pass table of length 2^lgL at WF_NT * lgL (2^lgL - 1 entries)
+// of radix plan 0.  A handle's buffer holds WF_NPLAN such blocks, plan p's
+// tables at WF_TWTAB * p + WF_NT * lgL (the roots only in block 0).
 #define WF_TWTAB ((WF_LOG2_NT + 1) * WF_NT)
+#define WF_NPLAN 3
+#define WF_TWTAB_ALL (WF_NPLAN * WF_TWTAB)
+
+// Radix plans of the ping-pong FFT passes (the in-place passes use plan 0):
+//   0: ceil(lgL / 4) passes, the bits spread evenly, larger radices first
+//      (1024 = 16 x 8 x 8, 512 = 8 x 8 x 8, 256 = 16 x 16, 128 = 16 x 8);
+//   1: the same radices in ascending order (1024 = 8 x 8 x 16, 128 = 8 x 16);
+//   2: for lgL >= 9 two passes, radix 32 first (1024 = 32 x 32, 512 = 32 x 16);
+//      otherwise plan 0.
+// wf_plan_np: passes; wf_plan_bits: log2 of the radix of pass p.
+__host__ __device__ inline int wf_plan_np(int lgL, int plan) {
+  return (plan == 2 && lgL >= 9) ? 2 : (lgL + 3) >> 2;
+}
+// Kernels are instantiated per plan; those with radix-32 passes (plan 2) are
+// compiled for two blocks per SM (FP32) to hold the 32 values.
+#define WF_MINB_PLAN(T, PLAN) ((PLAN) == 2 ? (sizeof(T) == 4 ? 2 : 1) : WF_MINB(T))
+__host__ __device__ inline int wf_plan_bits(int lgL, int plan, int p) {
+  if (plan == 2 && lgL >= 9) return p == 0 ? 5 : lgL - 5;
+  const int np = (lgL + 3) >> 2;
+  if (plan == 1) p = np - 1 - p;
+  int rem = lgL;
+  for (int q = 0; q < p; ++q) {
+    const int left = np - q;
+    rem -= (rem + left - 1) / left;
+  }
+  const int left = np - p;
+  return (rem + left - 1) / left;
+}
 
 // Threads per block of every operator kernel and the most samples one thread
 // stages in registers during an FFT pass; a tile holds at most their product.
@@ -88,6 +118,17 @@ struct WfLbMap {
   double PP[WF_MAXM * WF_MAXM], PQ[WF_MAXM * WF_MAXM], QQ[WF_MAXM * WF_MAXM];
 };
 
+// The lowest plan with the same passes as `plan` at length 2^lgL (the kernel
+// instantiation that runs it).
+__host__ __device__ inline int wf_plan_eff(int lgL, int plan) {
+  for (int q = 0; q < plan; ++q) {
+    bool same = wf_plan_np(lgL, q) == wf_plan_np(lgL, plan);
+    for (int i = 0; same && i < wf_plan_np(lgL, plan); ++i) same = wf_plan_bits(lgL, q, i) == wf_plan_bits(lgL, plan, i);
+    if (same) return q;
+  }
+  return plan;
+}
+
 // Launch geometry of one (n, C) shape.
 // Kernel variants of the L-BFGS FFT stages, chosen per shape by the autotuner
 // (wf_solve.cu) or forced through wf_opts.fft_variant.
@@ -103,12 +144,14 @@ struct WfGeo {
   int maxblk;      // stride of the partial-sum slots: covers every tile choice
   int colinv_kind, row_kind;  // WF_COLINV_*_K, WF_ROW_*_K
   int tc_div, rb_div;         // TC and RB are the widest tile divided by these (1, 2, 4)
+  int col_plan, row_plan;     // radix plans of the ping-pong column and row passes (0..WF_NPLAN-1)
 };
 
 // Widest tiles and the default kernel variants.
 WfGeo wf_make_geo(int n, int C);
 // Tiles tc_div / rb_div times narrower (TC >= 2, RB >= 1), the same stride.
-WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_div, int rb_div);
+WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_div, int rb_div, int col_plan = 0,
+                     int row_plan = 0);
 
 // Device pointers of one problem, in the working type T (float or double).
 struct WfBufs {

@@ -339,8 +339,8 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
 // ---------------------------------------------------------------------------
 // One block per column tile; KIND WF_COLINV_PP_K (ping-pong passes) or
 // WF_COLINV_INPLACE_K (in-place passes).
-template <typename T, int C, int KIND>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+template <typename T, int C, int KIND, int PLAN>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_PLAN(T, PLAN))
 k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb) {
   const int b = blockIdx.y;
   const WfLbMap* M = lb.st + b;
@@ -348,7 +348,7 @@ k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const vo
   const size_t vsz = (size_t)C * g.n * g.h;
   const V2<T>* p = (const V2<T>*)lb.ring + ((size_t)M->next * gridDim.y + b) * vsz;
   if constexpr (KIND == WF_COLINV_PP_K)
-    wf_col_inv_pp<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
+    wf_col_inv_pp<T, C, WF_IN_PK, PLAN>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
   else
     wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
 }
@@ -366,7 +366,7 @@ template <typename T>
 __host__ __device__ constexpr size_t wf_colinv_tma_smem() {
   return (3 * (size_t)WF_TILE + WF_NT) * sizeof(V2<T>) + 128;  // + room to align the TMA tile to 128 B
 }
-template <typename T, int C>
+template <typename T, int C, int PLAN>
 __global__ void __launch_bounds__(WF_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb, int B,
                 const __grid_constant__ CUtensorMap tm) {
@@ -383,7 +383,7 @@ k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, cons
   const int rows = C * n, boxr = rows < 256 ? rows : 256;
   const uint32_t tile_bytes = (uint32_t)(rows * TC * sizeof(V2<T>));
   const size_t vsz = (size_t)C * n * h;
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn, PLAN);
   if (tid == 0) {
     wf_mbar_init(&full, 1);
     wf_mbar_fence_init();
@@ -434,7 +434,7 @@ k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, cons
     auto after1 = [&]() {  // every thread is done with Ct: bring in the next tile
       if (tid == 0) pending = itn < nitems ? issue(itn) : false;
     };
-    wf_pp_fft<T, +1, true>(lgn, lgCT, 1, CT, A, Bf, s_tw, ld0, stl, after1);
+    wf_pp_fft<T, +1, true, PLAN>(lgn, lgCT, 1, CT, A, Bf, s_tw, ld0, stl, after1);
     it = itn;
   }
 }
@@ -510,12 +510,12 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
 
 // Row stage of the Hessian-vector product for the maps still iterating.
 // KIND WF_ROW_PP_K (ping-pong passes) or WF_ROW_INPLACE_K (in-place passes).
-template <typename T, int KIND>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+template <typename T, int KIND, int PLAN>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_PLAN(T, PLAN))
 k_lb_row(WfGeo g, void* scratch_, const void* w_, double* part, const void* tw_, const WfLbMap* st) {
   if (!st[blockIdx.y].active) return;
   if constexpr (KIND == WF_ROW_PP_K)
-    wf_row_pp<T, WF_ROW_NODATA>(g, (V2<T>*)scratch_, nullptr, (const T*)w_, part, tw_);
+    wf_row_pp<T, WF_ROW_NODATA, PLAN>(g, (V2<T>*)scratch_, nullptr, (const T*)w_, part, tw_);
   else
     k_row_body<T, WF_ROW_NODATA>(g, scratch_, nullptr, w_, nullptr, nullptr, part, tw_);
 }

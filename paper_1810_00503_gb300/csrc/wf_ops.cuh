@@ -49,10 +49,11 @@ __device__ __forceinline__ void wf_prefetch_rows(const void* base, int rows, siz
   }
 }
 
-// Stage the roots of unity (lgL = 0) or the pass table of length 2^lgL.
+// Stage the roots of unity (lgL = 0) or the pass table of length 2^lgL of
+// radix plan `plan`.
 template <typename T>
-__device__ __forceinline__ void wf_stage_tw(V2<T>* s_tw, const V2<T>* g_tw, int lgL = 0) {
-  const V2<T>* src = g_tw + (size_t)WF_NT * lgL;
+__device__ __forceinline__ void wf_stage_tw(V2<T>* s_tw, const V2<T>* g_tw, int lgL = 0, int plan = 0) {
+  const V2<T>* src = g_tw + (size_t)WF_TWTAB * plan + (size_t)WF_NT * lgL;
   for (int i = threadIdx.x; i < WF_NT; i += blockDim.x) s_tw[i] = src[i];
 }
 

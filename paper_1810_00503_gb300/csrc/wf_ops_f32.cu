@@ -1,4 +1,4 @@
 // Operator kernels and launchers instantiated for the float working type.
 #include "wf_ops_impl.cuh"
 
-WF_INSTANTIATE(float)
+WF_INSTANTIATE_OPS(float)

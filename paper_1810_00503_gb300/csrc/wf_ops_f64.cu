@@ -1,4 +1,4 @@
 // Operator kernels and launchers instantiated for the double working type.
 #include "wf_ops_impl.cuh"
 
-WF_INSTANTIATE(double)
+WF_INSTANTIATE_OPS(double)

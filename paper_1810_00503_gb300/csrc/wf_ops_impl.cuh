@@ -24,15 +24,24 @@ template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes, int
   return e;
 }
 
-template <typename T, int C, int IN>
-cudaError_t col_inv(const WfGeo& g, const WfBufs& b, const void* src, cudaStream_t st) {
+template <typename T, int C, int IN, int PLAN>
+cudaError_t col_inv_r(const WfGeo& g, const WfBufs& b, const void* src, cudaStream_t st) {
   static int done = 0;
-  auto k = WF_FFT_PP ? k_col_inv_pp<T, C, IN> : k_col_inv<T, C, IN>;
+  auto k = WF_FFT_PP ? k_col_inv_pp<T, C, IN, PLAN> : k_col_inv<T, C, IN>;
   const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, b.tw);
   return cudaGetLastError();
+}
+
+template <typename T, int C, int IN>
+cudaError_t col_inv(const WfGeo& g, const WfBufs& b, const void* src, cudaStream_t st) {
+  switch (wf_plan_eff(g.lgn, g.col_plan)) {
+    case 1: return col_inv_r<T, C, IN, 1>(g, b, src, st);
+    case 2: return col_inv_r<T, C, IN, 2>(g, b, src, st);
+    default: return col_inv_r<T, C, IN, 0>(g, b, src, st);
+  }
 }
 
 template <typename T, int C, int IN>
@@ -63,10 +72,11 @@ template <typename T, int MODE>
 cudaError_t row(const WfGeo& g, const WfBufs& b, const void* aux, void* out, cudaStream_t st) {
   static int done = 0;
   if constexpr (WF_FFT_PP && (MODE == WF_ROW_DATA || MODE == WF_ROW_NODATA)) {
-    static int done_pp = 0;
-    auto k = k_row_pp<T, MODE>;
+    static int done_pp[WF_NPLAN] = {0};
+    const int pl = wf_plan_eff(g.lgh, g.row_plan);
+    auto k = pl == 1 ? k_row_pp<T, MODE, 1> : pl == 2 ? k_row_pp<T, MODE, 2> : k_row_pp<T, MODE, 0>;
     const size_t sm = wf_pp_smem<T>();
-    cudaError_t e = ensure_smem(k, sm, &done_pp);
+    cudaError_t e = ensure_smem(k, sm, &done_pp[pl]);
     if (e != cudaSuccess) return e;
     k<<<dim3(g.nrb, b.B), WF_THREADS, sm, st>>>(g, b.scratch, b.d, b.w, b.part, b.tw);
     return cudaGetLastError();
@@ -134,11 +144,11 @@ inline WfEncodeTiled wf_encode_fn() {
 }
 
 // Persistent TMA-fed inverse column stage (k_lb_colinv_tma).
-template <typename T, int C>
+template <typename T, int C, int PLAN>
 cudaError_t lb_colinv_tma(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
   static int occ[32] = {0}, nsm[32] = {0};
-  auto k = k_lb_colinv_tma<T, C>;
+  auto k = k_lb_colinv_tma<T, C, PLAN>;
   const size_t sm = wf_colinv_tma_smem<T>();
   cudaError_t e = ensure_smem_n(k, sm, &done);
   if (e != cudaSuccess) return e;
@@ -209,10 +219,10 @@ inline cudaError_t spectra_map(const WfGeo& g, void* base, long long rows, CUten
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <typename T, int C, int KIND>
+template <typename T, int C, int KIND, int PLAN>
 cudaError_t lb_colinv_tile(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
-  auto k = k_lb_colinv<T, C, KIND>;
+  auto k = k_lb_colinv<T, C, KIND, PLAN>;
   const size_t sm = KIND == WF_COLINV_PP_K ? wf_pp_smem<T>() : col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
@@ -224,9 +234,14 @@ cudaError_t lb_colinv_tile(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, 
 // encoder; without it the ping-pong form runs).
 template <typename T, int C>
 cudaError_t lb_colinv(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
-  if (g.colinv_kind == WF_COLINV_TMA_K && wf_encode_fn()) return lb_colinv_tma<T, C>(g, b, lb, st);
-  if (g.colinv_kind == WF_COLINV_INPLACE_K) return lb_colinv_tile<T, C, WF_COLINV_INPLACE_K>(g, b, lb, st);
-  return lb_colinv_tile<T, C, WF_COLINV_PP_K>(g, b, lb, st);
+  const int pl = wf_plan_eff(g.lgn, g.col_plan);
+  if (g.colinv_kind == WF_COLINV_TMA_K && wf_encode_fn())
+    return pl == 1 ? lb_colinv_tma<T, C, 1>(g, b, lb, st)
+           : pl == 2 ? lb_colinv_tma<T, C, 2>(g, b, lb, st) : lb_colinv_tma<T, C, 0>(g, b, lb, st);
+  if (g.colinv_kind == WF_COLINV_INPLACE_K) return lb_colinv_tile<T, C, WF_COLINV_INPLACE_K, 0>(g, b, lb, st);
+  return pl == 1 ? lb_colinv_tile<T, C, WF_COLINV_PP_K, 1>(g, b, lb, st)
+         : pl == 2 ? lb_colinv_tile<T, C, WF_COLINV_PP_K, 2>(g, b, lb, st)
+                   : lb_colinv_tile<T, C, WF_COLINV_PP_K, 0>(g, b, lb, st);
 }
 
 template <typename T, int C>
@@ -388,10 +403,10 @@ cudaError_t wf_launch_lb_colfwd(const WfGeo& g, const WfBufs& b, const WfLbBufs&
   return g.C == 1 ? wfimpl::lb_colfwd<T, 1>(g, b, lb, st) : wfimpl::lb_colfwd<T, 2>(g, b, lb, st);
 }
 namespace wfimpl {
-template <typename T, int KIND>
+template <typename T, int KIND, int PLAN>
 cudaError_t lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
-  auto k = k_lb_row<T, KIND>;
+  auto k = k_lb_row<T, KIND, PLAN>;
   const size_t sm = KIND == WF_ROW_PP_K ? wf_pp_smem<T>() : row_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
@@ -401,8 +416,11 @@ cudaError_t lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStre
 }  // namespace wfimpl
 template <typename T>
 cudaError_t wf_launch_lb_row(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
-  return g.row_kind == WF_ROW_INPLACE_K ? wfimpl::lb_row<T, WF_ROW_INPLACE_K>(g, b, lb, st)
-                                        : wfimpl::lb_row<T, WF_ROW_PP_K>(g, b, lb, st);
+  if (g.row_kind == WF_ROW_INPLACE_K) return wfimpl::lb_row<T, WF_ROW_INPLACE_K, 0>(g, b, lb, st);
+  const int pl = wf_plan_eff(g.lgh, g.row_plan);
+  return pl == 1 ? wfimpl::lb_row<T, WF_ROW_PP_K, 1>(g, b, lb, st)
+         : pl == 2 ? wfimpl::lb_row<T, WF_ROW_PP_K, 2>(g, b, lb, st)
+                   : wfimpl::lb_row<T, WF_ROW_PP_K, 0>(g, b, lb, st);
 }
 template <typename T>
 cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st) {
@@ -412,7 +430,10 @@ cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, 
   return e;
 }
 
-#define WF_INSTANTIATE(T)                                                                          \
+// Explicit instantiations, split over translation units that compile in
+// parallel: the operator calls, the L-BFGS column stages, the L-BFGS row stage
+// and streaming kernels.
+#define WF_INSTANTIATE_OPS(T)                                                                      \
   template cudaError_t wf_launch_prep<T>(const WfGeo&, const void* const*,                         \
                                          const unsigned char* const*, const void* const*,          \
                                          const void* const*, int, int, void*, void*, void*, int,   \
@@ -428,19 +449,21 @@ cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, 
                                                 const double*, int, double*, cudaStream_t);        \
   template cudaError_t wf_launch_pack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);     \
   template cudaError_t wf_launch_unpack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);    \
-  template cudaError_t wf_launch_lb_comb<T>(const WfGeo&, const WfBufs&, const WfLbBufs&, int,      \
-                                            cudaStream_t);                                         \
-  template cudaError_t wf_launch_lb_qdots<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,         \
-                                             cudaStream_t);                                        \
-  template cudaError_t wf_launch_lb_colinv<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,        \
-                                              cudaStream_t);                                       \
-  template cudaError_t wf_launch_lb_colfwd<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,        \
-                                              cudaStream_t);                                       \
-  template cudaError_t wf_launch_lb_row<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,           \
-                                           cudaStream_t);                                          \
   template cudaError_t wf_launch_eval_pk<T>(const WfGeo&, const WfBufs&, const void*, void*,       \
                                             cudaStream_t);                                         \
   template cudaError_t wf_launch_eval_bands<T>(const WfGeo&, const WfBufs&, const void*, void*,    \
                                                double*, const int16_t*, int, double*, cudaStream_t);\
   template cudaError_t wf_launch_band_scale<T>(const WfGeo&, const void*, void*, int,               \
                                                const int16_t*, const double*, int, cudaStream_t);
+#define WF_INSTANTIATE_LBCOL(T)                                                                    \
+  template cudaError_t wf_launch_lb_colinv<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,        \
+                                              cudaStream_t);                                       \
+  template cudaError_t wf_launch_lb_colfwd<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,        \
+                                              cudaStream_t);
+#define WF_INSTANTIATE_LBROW(T)                                                                    \
+  template cudaError_t wf_launch_lb_comb<T>(const WfGeo&, const WfBufs&, const WfLbBufs&, int,      \
+                                            cudaStream_t);                                         \
+  template cudaError_t wf_launch_lb_qdots<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,         \
+                                             cudaStream_t);                                        \
+  template cudaError_t wf_launch_lb_row<T>(const WfGeo&, const WfBufs&, const WfLbBufs&,           \
+                                           cudaStream_t);

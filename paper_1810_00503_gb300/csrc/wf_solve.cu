@@ -484,18 +484,34 @@ static WfLbBufs lb_bufs(WfSolver* S) {
   return lb;
 }
 
-// FFT-stage variants (wf_opts.fft_variant encoding: 1000 a + 100 b + 10 c + d).
+// FFT-stage variants (wf_opts.fft_variant encoding:
+// 100000 f + 10000 e + 1000 a + 100 b + 10 c + d, f / e the column / row radix plans).
 static int variant_code(const WfGeo& g) {
-  return 1000 * g.colinv_kind + 100 * g.row_kind + 10 * g.tc_div + g.rb_div;
+  return 100000 * g.col_plan + 10000 * g.row_plan + 1000 * g.colinv_kind + 100 * g.row_kind + 10 * g.tc_div +
+         g.rb_div;
 }
 static bool variant_valid(int v) {
-  const int a = v / 1000, b = (v / 100) % 10, c = (v / 10) % 10, d = v % 10;
+  const int f = v / 100000, e = (v / 10000) % 10, a = (v / 1000) % 10, b = (v / 100) % 10, c = (v / 10) % 10,
+            d = v % 10;
   auto div_ok = [](int x) { return x == 1 || x == 2 || x == 4; };
-  return v >= 1000 && v < 10000 && a >= WF_COLINV_TMA_K && a <= WF_COLINV_INPLACE_K && b >= WF_ROW_PP_K &&
-         b <= WF_ROW_INPLACE_K && div_ok(c) && div_ok(d);
+  return v >= 1000 && f < WF_NPLAN && e < WF_NPLAN && a >= WF_COLINV_TMA_K && a <= WF_COLINV_INPLACE_K &&
+         b >= WF_ROW_PP_K && b <= WF_ROW_INPLACE_K && div_ok(c) && div_ok(d);
 }
 static WfGeo variant_geo(const WfGeo& base, int v) {
-  return wf_geo_variant(base, v / 1000, (v / 100) % 10, (v / 10) % 10, v % 10);
+  return wf_geo_variant(base, (v / 1000) % 10, (v / 100) % 10, (v / 10) % 10, v % 10, v / 100000,
+                        (v / 10000) % 10);
+}
+// Radix plans q and p give the same passes for length 2^lgL.
+static bool plan_same(int lgL, int p, int q) {
+  if (wf_plan_np(lgL, p) != wf_plan_np(lgL, q)) return false;
+  for (int i = 0; i < wf_plan_np(lgL, p); ++i)
+    if (wf_plan_bits(lgL, p, i) != wf_plan_bits(lgL, q, i)) return false;
+  return true;
+}
+static bool plan_new(int lgL, int p) {  // p differs from every lower plan
+  for (int q = 0; q < p; ++q)
+    if (plan_same(lgL, p, q)) return false;
+  return true;
 }
 
 // Timing state for the autotuner: every map active with a full history ring
@@ -511,12 +527,13 @@ __global__ void k_tune_state(WfLbMap* st, int B, int m) {
 }
 
 // Autotuner: times the FFT-stage variants of the Hessian-vector pass on the
-// problem's own buffers (the maps must be active; the outputs - scratch, the
-// ring slot Q[next] and the partial sums - are rewritten by the first
-// iteration) and keeps the fastest.  Column choices (inverse column stage
-// variant and column tile width) are timed with the forward column stage, then
-// the row choices (row stage variant and row block height) with those fixed.
-// Results are cached in the handle per (n, C, precision, maps).
+// problem's own buffers, before the solve's first refresh (whose outputs and
+// the first iteration's rewrite what the timing runs write), and keeps the
+// fastest.  Column choices (inverse column stage variant, radix plan and
+// column tile width) are timed with the forward column stage, then the row
+// choices (row stage variant, radix plan and row block height) with those
+// fixed.  Results are cached in the handle per (n, C, precision, history
+// length, maps).
 template <typename T>
 static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   const wf_opts* o = &S->o;
@@ -541,18 +558,17 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   }
   const WfBufs b = wf_bufs(p);
   WfLbBufs lb = lb_bufs<T>(S);
-  // Candidates run on a copy of the map states set to a full history ring and
-  // on real values: the gradient as the direction P[0].  The first iteration
-  // rewrites P[0], Q[0], the scratch and the partial sums they write.
+  // Candidates run against map states set to a full history ring, with the
+  // start state as the direction P[0].  The first refresh and iteration
+  // rewrite P[0], Q[0], the scratch and the partial sums they write.
   WfLbMap* tst = nullptr;
   if (wf_alloc(p->h, (void**)&tst, sizeof(WfLbMap) * p->count, "autotune state") != WF_OK) {
     p->g = base;  // no room to time the candidates: the defaults, not cached
     return WF_OK;
   }
-  cudaError_t ce = cudaMemcpyAsync(S->ring, S->g, (size_t)p->count * p->C * p->n * p->n * p->elt,
+  cudaError_t ce = cudaMemcpyAsync(S->ring, S->s, (size_t)p->count * p->C * p->n * p->n * p->elt,
                                    cudaMemcpyDeviceToDevice, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(tst, S->st, sizeof(WfLbMap) * p->count, cudaMemcpyDeviceToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(tst, 0, sizeof(WfLbMap) * p->count, st);
   if (ce == cudaSuccess) {
     k_tune_state<<<(p->count + 127) / 128, 128, 0, st>>>(tst, p->count, m);
     ce = cudaGetLastError();
@@ -581,36 +597,41 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
     return ms;
   };
   // column choices (inverse and forward column stage together), then the row
-  // choices with the column choice fixed
+  // choices with the column choice fixed; radix plans only for the ping-pong
+  // passes, and only those that differ at this length
   WfGeo best = base;
   float best_ms = INFINITY;
   const int divs[3] = {1, 2, 4};
-  for (int ck = WF_COLINV_TMA_K; ck <= WF_COLINV_INPLACE_K; ++ck) {
-    int last_tc = -1;
-    for (int di : divs) {
-      const WfGeo g = wf_geo_variant(base, ck, base.row_kind, di, 1);
-      if (g.TC == last_tc) continue;  // no narrower tile possible
-      last_tc = g.TC;
-      const float ms = timed([&]() {
-        cudaError_t e = wf_launch_lb_colinv<T>(g, b, lb, st);
-        if (e == cudaSuccess) e = wf_launch_lb_colfwd<T>(g, b, lb, st);
-        return e;
-      });
-      if (ms < best_ms) { best_ms = ms; best = g; }
+  for (int ck = WF_COLINV_TMA_K; ck <= WF_COLINV_INPLACE_K; ++ck)
+    for (int cp = 0; cp < (ck == WF_COLINV_INPLACE_K ? 1 : WF_NPLAN); ++cp) {
+      if (!plan_new(p->g.lgn, cp)) continue;
+      int last_tc = -1;
+      for (int di : divs) {
+        const WfGeo g = wf_geo_variant(base, ck, base.row_kind, di, 1, cp, 0);
+        if (g.TC == last_tc) continue;  // no narrower tile possible
+        last_tc = g.TC;
+        const float ms = timed([&]() {
+          cudaError_t e = wf_launch_lb_colinv<T>(g, b, lb, st);
+          if (e == cudaSuccess) e = wf_launch_lb_colfwd<T>(g, b, lb, st);
+          return e;
+        });
+        if (ms < best_ms) { best_ms = ms; best = g; }
+      }
     }
-  }
   best_ms = INFINITY;
   WfGeo bestr = best;
-  for (int rk = WF_ROW_PP_K; rk <= WF_ROW_INPLACE_K; ++rk) {
-    int last_rb = -1;
-    for (int di : divs) {
-      const WfGeo g = wf_geo_variant(base, best.colinv_kind, rk, best.tc_div, di);
-      if (g.RB == last_rb) continue;
-      last_rb = g.RB;
-      const float ms = timed([&]() { return wf_launch_lb_row<T>(g, b, lb, st); });
-      if (ms < best_ms) { best_ms = ms; bestr = g; }
+  for (int rk = WF_ROW_PP_K; rk <= WF_ROW_INPLACE_K; ++rk)
+    for (int rp = 0; rp < (rk == WF_ROW_INPLACE_K ? 1 : WF_NPLAN); ++rp) {
+      if (!plan_new(p->g.lgh, rp)) continue;
+      int last_rb = -1;
+      for (int di : divs) {
+        const WfGeo g = wf_geo_variant(base, best.colinv_kind, rk, best.tc_div, di, best.col_plan, rp);
+        if (g.RB == last_rb) continue;
+        last_rb = g.RB;
+        const float ms = timed([&]() { return wf_launch_lb_row<T>(g, b, lb, st); });
+        if (ms < best_ms) { best_ms = ms; bestr = g; }
+      }
     }
-  }
   cudaStreamSynchronize(st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -656,11 +677,11 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   if (s0) WF_TRY(wf_launch_pack<T>(p->g, p->count, s0, S->s, st));
   else WF_TRY(cudaMemsetAsync(S->s, 0, (size_t)p->count * p->C * p->n * p->n * p->elt, st));
   WF_TRY(cudaMemsetAsync(S->st, 0, sizeof(WfLbMap) * p->count, st));
-  WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
-  rs = choose_variant<T>(p, S, st);  // after the refresh: the maps are active
+  rs = choose_variant<T>(p, S, st);  // before the first refresh: one variant for the whole solve
   if (rs != WF_OK) return rs;
   A.ntile = p->g.ntile;
   A.nrb = p->g.nrb;
+  WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
   const int chunk = o->check_every > 0 ? o->check_every : 16;
   if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
                          S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m && S->g_ls == A.ls &&

@@ -38,7 +38,7 @@ __device__ __forceinline__ V2<T> wf_mode_packed(LD& ld, int j, int c, int kx, in
 
 // Inverse column stage: spectrum (packed [C][n][h], or standard [C][n][h+1])
 // -> R sqrt(P)/n -> inverse FFT along y -> scratch (packed).
-template <typename T, int C, int IN>
+template <typename T, int C, int IN, int PLAN>
 __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, const T* sp, V2<T>* scr,
                                               const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
@@ -47,7 +47,7 @@ __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, 
   V2<T>* Bf = A + WF_TILE;
   const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1;
   const int lgCT = lgTC + (C == 2 ? 1 : 0), kx0 = blockIdx.x * TC;
-  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);  // first read after the first barrier
+  wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn, PLAN);  // first read after the first barrier
   auto ld0 = [&](int t, int row) -> V2<T> {
     const int c = t >> lgTC, kx = kx0 + (t & (TC - 1));
     if constexpr (IN == WF_IN_STD) {
@@ -73,7 +73,7 @@ __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, 
   auto stl = [&](int t, int row, V2<T> v) {
     scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))] = v;
   };
-  wf_pp_fft<T, +1, true>(lgn, lgCT, 1, C * TC, A, Bf, s_tw, ld0, stl);
+  wf_pp_fft<T, +1, true, PLAN>(lgn, lgCT, 1, C * TC, A, Bf, s_tw, ld0, stl);
 }
 
 // Row stage of the objective (MODE DATA: r = d - x) or of the Hessian-vector
@@ -85,7 +85,7 @@ __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, 
 // (global); d, w: the pixel rows (RB n values from the block's first row).
 // Returns this thread's part of sum r.wr.  after1 runs once the first pass has
 // finished reading src.
-template <typename T, int MODE, class H = WfNoHook>
+template <typename T, int MODE, int PLAN, class H = WfNoHook>
 __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* src, V2<T>* sc, const T* d,
                                                    const T* w, const V2<T>* roots, const V2<T>* s_pt, V2<T>* A,
                                                    V2<T>* Bf, H after1 = H()) {
@@ -105,7 +105,7 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
     return cadd<T>(s1, mul_i<T>(cmul<T>(w1, d1)));
   };
   // pixel step on the c2r output (pixels 2m, 2m+1 of row t): wr = w (d - x)
-  V2<T>* O = wf_pp_out<T>(lgh, A, Bf);
+  V2<T>* O = wf_pp_out<T>(lgh, PLAN, A, Bf);
   WfAcc<T> acc = 0;
   auto stpix = [&](int t, int m, V2<T> x) {
     const size_t e = (size_t)t * n / 2 + m;
@@ -121,14 +121,14 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
     acc += (WfAcc<T>)(r.x * wr.x + r.y * wr.y);
     O[wf_sw<T>(t * h + m)] = wr;
   };
-  wf_pp_fft<T, +1, false>(lgh, lgRB, h, 1, A, Bf, s_pt, ld0, stpix, after1);
+  wf_pp_fft<T, +1, false, PLAN>(lgh, lgRB, h, 1, A, Bf, s_pt, ld0, stpix, after1);
   __syncthreads();
   // r2c of wr: the input is O, so the passes start from the other buffer
   V2<T>* A2 = (O == A) ? Bf : A;
   auto ldO = [&](int t, int e) { return O[wf_sw<T>(t * h + e)]; };
-  V2<T>* Z = wf_pp_out<T>(lgh, A2, O);
+  V2<T>* Z = wf_pp_out<T>(lgh, PLAN, A2, O);
   auto stZ = [&](int t, int e, V2<T> v) { Z[wf_sw<T>(t * h + e)] = v; };
-  wf_pp_fft<T, -1, false>(lgh, lgRB, h, 1, A2, O, s_pt, ldO, stZ);
+  wf_pp_fft<T, -1, false, PLAN>(lgh, lgRB, h, 1, A2, O, s_pt, ldO, stZ);
   __syncthreads();
   // r2c post-step: X[k] = (Z[k] + conj Z[h-k])/2 - i w^-k (Z[k] - conj Z[h-k])/2, X[0], X[h] packed
   for (int e = threadIdx.x; e < RB * h; e += blockDim.x) {
@@ -149,7 +149,7 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
   return acc;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int PLAN>
 __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const T* d, const T* w, double* part,
                                           const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
@@ -164,10 +164,10 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
     wf_prefetch_rows(w + off, 1, 0, g.RB * n * (int)sizeof(T));
     if (MODE == WF_ROW_DATA) wf_prefetch_rows(d + off, 1, 0, g.RB * n * (int)sizeof(T));
   }
-  wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, g.lgh);
+  wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, g.lgh, PLAN);
   V2<T>* sc = scratch + (size_t)b * g.C * n * h + (size_t)row0 * h;
   const size_t poff = (size_t)b * npix + (size_t)row0 * n;
-  const WfAcc<T> acc = wf_row_pp_core<T, MODE>(g, sc, sc, MODE == WF_ROW_DATA ? d + poff : nullptr, w + poff,
+  const WfAcc<T> acc = wf_row_pp_core<T, MODE, PLAN>(g, sc, sc, MODE == WF_ROW_DATA ? d + poff : nullptr, w + poff,
                                                (const V2<T>*)tw_, s_pt, A, Bf);
   const double s = wf_block_sum((double)acc);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;
@@ -175,16 +175,16 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
 
 // Kernels of the objective + gradient pass on the ping-pong stages (one block
 // per column tile or row block, as k_col_inv and k_row).
-template <typename T, int C, int IN>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+template <typename T, int C, int IN, int PLAN>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_PLAN(T, PLAN))
 k_col_inv_pp(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* scratch_, const void* tw_) {
   const int b = blockIdx.y, n = g.n, h = g.h;
   const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
-  wf_col_inv_pp<T, C, IN>(g, (const V2<T>*)src_ + (size_t)b * sstride, sp_ + (size_t)b * sp_stride,
+  wf_col_inv_pp<T, C, IN, PLAN>(g, (const V2<T>*)src_ + (size_t)b * sstride, sp_ + (size_t)b * sp_stride,
                           (V2<T>*)scratch_ + (size_t)b * C * n * h, tw_);
 }
-template <typename T, int MODE>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+template <typename T, int MODE, int PLAN>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_PLAN(T, PLAN))
 k_row_pp(WfGeo g, void* scratch_, const void* d_, const void* w_, double* part, const void* tw_) {
-  wf_row_pp<T, MODE>(g, (V2<T>*)scratch_, (const T*)d_, (const T*)w_, part, tw_);
+  wf_row_pp<T, MODE, PLAN>(g, (V2<T>*)scratch_, (const T*)d_, (const T*)w_, part, tw_);
 }
