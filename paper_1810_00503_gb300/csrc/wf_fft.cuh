@@ -134,18 +134,13 @@ __device__ __forceinline__ void dft_reg(V2<T>* v) {
 // higher bits so that the strided accesses of the Stockham passes (stride R
 // in the first pass, stride C*TC in column tiles) spread over all banks:
 // 8-byte values fill 16 bank pairs, 16-byte values 8 bank quads.  A bijection
-// within each aligned block of 16 (8) values.
-#ifndef WF_SWIZZLE
-#define WF_SWIZZLE 1
-#endif
+// within each aligned block of 16 (8) values.  For 8-byte values one shifted
+// copy of the index (a shift and one three-input logic operation) is
+// conflict-free on every pass of the plans used; 16-byte values need two.
 template <typename T>
 __device__ __forceinline__ int wf_sw(int x) {
-#if WF_SWIZZLE
-  if constexpr (sizeof(T) == 4) return x ^ (((x >> 4) ^ (x >> 8)) & 15);
+  if constexpr (sizeof(T) == 4) return x ^ ((x >> 4) & 15);
   else return x ^ (((x >> 3) ^ (x >> 6)) & 7);
-#else
-  return x;
-#endif
 }
 
 // Twiddle exp(DIR * 2 pi i * k / WF_NT) from the shared table (k < WF_NT).
