@@ -163,35 +163,43 @@ __device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, in
   const int lgLR = lgL - lgR;
   const int LR = 1 << lgLR;
   const int nbf = cnt << lgLR;
-  V2<T> v[NB][R];
+  // FULL: every thread has NB butterflies (a full tile), so no bounds tests
+  auto body = [&](auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    V2<T> v[NB][R];
 #pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    const int b = threadIdx.x + i * blockDim.x;
-    if (b < nbf) {
-      const int t = b >> lgLR, j = b & (LR - 1);
+    for (int i = 0; i < NB; ++i) {
+      const int b = threadIdx.x + i * blockDim.x;
+      if (FULL || b < nbf) {
+        const int t = b >> lgLR, j = b & (LR - 1);
+        const int x0 = t * ts + j * js, dx = LR * js;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = buf[wf_sw<T>(t * ts + (j + r * LR) * js)];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    const int b = threadIdx.x + i * blockDim.x;
-    if (b < nbf) {
-      const int t = b >> lgLR, j = b & (LR - 1);
-      const int k = j & (Ns - 1);
-      if (Ns > 1) {
-        const V2<T>* pt = ptab + (Ns - R1) + k;
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[i][r] = cmul<T>(v[i][r], twid<T, DIR>(pt, (r - 1) * Ns));
+        for (int r = 0; r < R; ++r) v[i][r] = buf[wf_sw<T>(x0 + r * dx)];
       }
-      dft_reg<T, R, DIR>(v[i]);
-      const int o = ((j - k) << lgR) + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) buf[wf_sw<T>(t * ts + (o + r * Ns) * js)] = v[i][r];
     }
-  }
-  __syncthreads();
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int b = threadIdx.x + i * blockDim.x;
+      if (FULL || b < nbf) {
+        const int t = b >> lgLR, j = b & (LR - 1);
+        const int k = j & (Ns - 1);
+        if (Ns > 1) {
+          const V2<T>* pt = ptab + (Ns - R1) + k;
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[i][r] = cmul<T>(v[i][r], twid<T, DIR>(pt, (r - 1) * Ns));
+        }
+        dft_reg<T, R, DIR>(v[i]);
+        const int o = ((j - k) << lgR) + k;
+        const int x0 = t * ts + o * js, dx = Ns * js;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[wf_sw<T>(x0 + r * dx)] = v[i][r];
+      }
+    }
+    __syncthreads();
+  };
+  if (nbf == NB * (int)blockDim.x) body(std::true_type());
+  else body(std::false_type());
 }
 
 // Full transform of `cnt` sequences of length L = 2^lgL (1 <= lgL <= 10).
@@ -201,20 +209,27 @@ __device__ __forceinline__ void fft_pass(V2<T>* buf, int L, int lgL, int cnt, in
 template <typename T, int DIR, int EMAX>
 __device__ __forceinline__ void fft_smem(V2<T>* buf, int lgL, int cnt, int ts, int js, const V2<T>* ptab) {
   const int L = 1 << lgL;
-  const int np = (lgL + 3) >> 2;
-  int rem = lgL, lgNs = 0, R1 = 1;
-  for (int p = 0; p < np; ++p) {
-    const int left = np - p;
-    const int bits = (rem + left - 1) / left;  // ceil(rem / left)
-    const int Ns = 1 << lgNs;
-    if (p == 0) R1 = 1 << bits;
-    switch (bits) {
-      case 4: fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
-      case 3: fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
-      case 2: fft_pass<T, 4, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
-      default: fft_pass<T, 2, DIR, EMAX>(buf, L, lgL, cnt, ts, js, Ns, lgNs, ptab, R1); break;
+  // the passes of plan 0 written out per length (bits (1..4), (3,2) (3,3)
+  // (4,3) (4,4), (3,3,3) (4,3,3)), so that each pass is compiled on its own
+  if (lgL <= 4) {
+    switch (lgL) {
+      case 1: fft_pass<T, 2, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, 2); break;
+      case 2: fft_pass<T, 4, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, 4); break;
+      case 3: fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, 8); break;
+      default: fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, 16); break;
     }
-    rem -= bits;
-    lgNs += bits;
+  } else if (lgL <= 8) {
+    const int b1 = (lgL + 1) >> 1, b2 = lgL - b1, R1 = 1 << b1;
+    if (b1 == 3) fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, R1);
+    else fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, R1);
+    if (b2 == 2) fft_pass<T, 4, DIR, EMAX>(buf, L, lgL, cnt, ts, js, R1, b1, ptab, R1);
+    else if (b2 == 3) fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, R1, b1, ptab, R1);
+    else fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, R1, b1, ptab, R1);
+  } else {
+    const int b1 = lgL - 6, R1 = 1 << b1;
+    if (b1 == 3) fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, R1);
+    else fft_pass<T, 16, DIR, EMAX>(buf, L, lgL, cnt, ts, js, 1, 0, ptab, R1);
+    fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, R1, b1, ptab, R1);
+    fft_pass<T, 8, DIR, EMAX>(buf, L, lgL, cnt, ts, js, R1 << 3, b1 + 3, ptab, R1);
   }
 }

@@ -123,30 +123,43 @@ __device__ __forceinline__ V2<T> wf_pack0(V2<T> X0, V2<T> Xh) { return mk<T>(X0.
 template <typename T, int C, bool ADJ>
 __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx0, const T* sp, T extra) {
   const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, pitch = h + 1;
-  // U elements per trip, their sqrt(P) values loaded before any is used
+  // U elements per trip, their sqrt(P) values loaded before any is used.  A
+  // thread's column t is fixed (blockDim is a multiple of TC); the packed
+  // column kx = 0 is not written here (its threads' stores are predicated
+  // off) and is done in pairs below.
   constexpr int U = 8;
-  for (int e0 = threadIdx.x; e0 < n * TC; e0 += U * blockDim.x) {
+  const int t = threadIdx.x & (TC - 1), kx = kx0 + t, jstep = blockDim.x >> lgTC;
+  const bool keep = kx == 0;
+  auto trip = [&](int j0, auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
     T a0[U], a1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * blockDim.x, t = e & (TC - 1), j = e >> lgTC;
-      if (e < n * TC) {
-        a0[u] = sp[j * pitch + kx0 + t];
-        if constexpr (C == 2) a1[u] = sp[(size_t)n * pitch + j * pitch + kx0 + t];
+      const int j = j0 + u * jstep;
+      if (FULL || j < n) {
+        a0[u] = sp[j * pitch + kx];
+        if constexpr (C == 2) a1[u] = sp[(size_t)n * pitch + j * pitch + kx];
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * blockDim.x, t = e & (TC - 1), j = e >> lgTC, kx = kx0 + t;
-      if (e >= n * TC || kx == 0) continue;
-      V2<T> v[C];
+      const int j = j0 + u * jstep;
+      if (FULL || j < n) {
+        V2<T> v[C];
 #pragma unroll
-      for (int c = 0; c < C; ++c) v[c] = buf[wf_sw<T>(j * CT + c * TC + t)];
-      wf_mode_op_pre<T, C, ADJ>(v, j, kx, n, a0[u] * extra, C == 2 ? a1[u] * extra : (T)0);
+        for (int c = 0; c < C; ++c) v[c] = buf[wf_sw<T>(j * CT + c * TC + t)];
+        wf_mode_op_pre<T, C, ADJ>(v, j, kx, n, a0[u] * extra, C == 2 ? a1[u] * extra : (T)0);
+        if (!keep) {
 #pragma unroll
-      for (int c = 0; c < C; ++c) buf[wf_sw<T>(j * CT + c * TC + t)] = v[c];
+          for (int c = 0; c < C; ++c) buf[wf_sw<T>(j * CT + c * TC + t)] = v[c];
+        }
+      }
     }
-  }
+  };
+  const int full_trips = n / (U * jstep);
+  int j0 = threadIdx.x >> lgTC;
+  for (int i = 0; i < full_trips; ++i, j0 += U * jstep) trip(j0, std::true_type());
+  if (j0 < n) trip(j0, std::false_type());
   if (kx0 == 0) {
     for (int j = threadIdx.x; j <= h; j += blockDim.x) {
       const int jm = (n - j) & (n - 1);
