@@ -150,14 +150,17 @@ def algorithmic_bytes(n, m, elt=4):
     Packed vector V = n * n/2 complex = n^2 values; sqrt(P) table n (n/2+1)
     values; weight map n^2 values.
     comb:   reads the 2m stored vectors (the newest pair once: it also carries the
-            pending update), s and g; writes s, g and p.
+            pending update) and g; writes g and p; reads and writes s once every
+            m - 1 launches, when the steps taken since are folded into it (the
+            average over that cycle is counted).
     colinv: reads p and sqrt(P).        row: reads W (Hp needs no data map).
     colfwd: reads g, writes q (p is re-read there only because the column
             stages are split; the re-read and the scratch traffic are not counted).
     qdots:  reads q and the m - 1 other stored Q."""
     V = n * n * elt
     sp = n * (n // 2 + 1) * elt
-    return {"comb": (2 * m + 5) * V, "colinv": V + sp, "row": n * n * elt, "colfwd": 2 * V,
+    fold = max(1, m - 1)
+    return {"comb": (2 * m + 3) * V + 2 * V / fold, "colinv": V + sp, "row": n * n * elt, "colfwd": 2 * V,
             "qdots": m * V}
 
 

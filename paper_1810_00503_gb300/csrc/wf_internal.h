@@ -109,7 +109,9 @@ struct WfLbMap {
   int status;       // wf_status of this map
   int evals;        // operator applications
   int pend_slot;    // slot of the pending update
-  double pend_alpha;  // pending update s += a P[pend_slot], g += a Q[pend_slot]
+  int s_k;          // steps folded into s: s = s0 + sum over steps i < s_k of alpha_i P_(i mod m)
+  int pad_;
+  double pend_alpha;  // pending update g += a Q[pend_slot] (s follows when the steps are folded)
   double chi2, chi2_prev, gg, gg0;
   double dg;                    // direction p = dg g + sum dP_i P_i + dQ_i Q_i
   double dP[WF_MAXM], dQ[WF_MAXM];
@@ -191,6 +193,10 @@ cudaError_t wf_launch_band_energy(const WfGeo& g, int B, const void* s, const in
                                   const double* theta, int n_bands, double* E, cudaStream_t st);
 // L-BFGS kernels.  Streaming-kernel modes: full iteration, materialise only, dots only.
 enum { WF_LB1_FULL = 0, WF_LB1_MATERIALIZE = 1, WF_LB1_DOTS = 2 };
+// The steps taken but not yet added to s are folded in one pass once this
+// many have gathered (their P slots are still in the ring: at most m - 1 of
+// them), or whenever s itself is needed.
+__host__ __device__ inline int wf_sfold(int m) { return m > 1 ? m - 1 : 1; }
 // Default bound of a device-side wait, SM clock cycles (about 2 s at 2.07 GHz).
 #define WF_WAIT_CYCLES_DEFAULT 4000000000ll
 struct WfLbBufs {

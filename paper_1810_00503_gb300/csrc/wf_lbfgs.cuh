@@ -143,16 +143,22 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   const WfLbMap* M = lb.st + b;
   const int active = M->active;
   const double pa = M->pend_alpha;
-  if (mode == WF_LB1_FULL && !active && pa == 0.0) return;
-  if (mode == WF_LB1_MATERIALIZE && pa == 0.0) return;
-  if (mode == WF_LB1_FULL && !active) mode = WF_LB1_MATERIALIZE;  // deactivated: apply its last step only
-  const bool mat = (pa != 0.0 && mode != WF_LB1_DOTS);
+  const int m = lb.m;
+  // steps taken but not in s yet: k - s_k of them, the newest in slot head
+  const int unfolded = M->k - M->s_k;
+  if (mode == WF_LB1_FULL && !active && pa == 0.0 && unfolded == 0) return;
+  if (mode == WF_LB1_MATERIALIZE && pa == 0.0 && unfolded == 0) return;
+  if (mode == WF_LB1_FULL && !active) mode = WF_LB1_MATERIALIZE;  // deactivated: finish its state only
+  const bool gup = (pa != 0.0 && mode != WF_LB1_DOTS);  // the pending step, into g
+  const int nfold = (mode == WF_LB1_DOTS) ? 0
+                    : (mode == WF_LB1_MATERIALIZE || unfolded >= wf_sfold(m)) ? unfolded : 0;  // into s now
   const bool full = (mode == WF_LB1_FULL);
   const size_t vsz = (size_t)g.C * g.n * g.h;  // complex values per map vector
-  const int h = g.h, B = gridDim.y, m = lb.m;
+  const int h = g.h, B = gridDim.y;
   const V2<T>* ring = (const V2<T>*)lb.ring;
-  const int np = (mode == WF_LB1_MATERIALIZE) ? 1 : M->npairs;
-  const int head = (mode == WF_LB1_MATERIALIZE) ? M->pend_slot : M->head;
+  const int head = M->head;
+  const int np = (mode == WF_LB1_MATERIALIZE) ? 0 : M->npairs;  // pairs of the direction and dots
+  const int nq = np > nfold ? np : nfold;  // slots streamed (newest first)
   const int nslot = 1 + 2 * np;
   if (mode != WF_LB1_MATERIALIZE) {
     for (int k = 0; k < nslot; ++k) pdot[k * WF_COMB_THREADS + tid] = 0.f;
@@ -194,29 +200,37 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (ok[i]) {
-        gr[i] = gv[u[i]];
-        if (mat) sr[i] = sv[u[i]];
+        if (mode != WF_LB1_MATERIALIZE || gup) gr[i] = gv[u[i]];
+        if (nfold) sr[i] = sv[u[i]];
         if (full) pr[i] = wf_vscale<T>(gr[i], (T)0);
       }
-    for (int q = 0; q < np; ++q) {
+    for (int q = 0; q < nq; ++q) {
       const int sl = (head - q + m) % m;
       const VT* Pq = (const VT*)(ring + ((size_t)sl * B + b) * vsz + c0);
       const VT* Qq = (const VT*)(ring + ((size_t)(m + sl) * B + b) * vsz + c0);
+      const bool useq = q < np || (gup && q == 0);
       VT xp[NV], xq[NV];
 #pragma unroll
       for (int i = 0; i < NV; ++i)
-        if (ok[i]) { xq[i] = Qq[u[i]]; xp[i] = Pq[u[i]]; }
-      if (mat && q == 0) {  // the newest pair carries the pending update
+        if (ok[i]) {
+          if (useq) xq[i] = Qq[u[i]];
+          xp[i] = Pq[u[i]];
+        }
+      if (gup && q == 0) {  // the newest pair carries the pending update of g
 #pragma unroll
         for (int i = 0; i < NV; ++i)
           if (ok[i]) {
             gr[i] = wf_vaxpy<T>(gr[i], (T)pa, xq[i]);
-            sr[i] = wf_vaxpy<T>(sr[i], (T)pa, xp[i]);
             gv[u[i]] = gr[i];
-            sv[u[i]] = sr[i];
           }
       }
-      if (mode == WF_LB1_MATERIALIZE) break;
+      if (q < nfold) {  // step of this pair into s
+        const T as = (T)M->alpha[sl];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+          if (ok[i]) sr[i] = wf_vaxpy<T>(sr[i], as, xp[i]);
+      }
+      if (q >= np) continue;
       const T cq = (T)M->dQ[sl], cp = (T)M->dP[sl];
       float aq = 0.f, ap = 0.f;
 #pragma unroll
@@ -228,6 +242,11 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
         }
       pdot[(1 + 2 * q) * WF_COMB_THREADS + tid] += aq;
       pdot[(2 + 2 * q) * WF_COMB_THREADS + tid] += ap;
+    }
+    if (nfold) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (ok[i]) sv[u[i]] = sr[i];
     }
     if (mode == WF_LB1_MATERIALIZE) continue;
     float acc = 0.f;

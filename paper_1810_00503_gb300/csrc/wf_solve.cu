@@ -200,6 +200,11 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
   WfLbMap& M = st[b];
   const double* pb = part + (size_t)b * WF_NSLOT * A.maxblk;
   const int m = A.m;
+  // Steps the streaming pass just folded into s (the rule of k_lb_comb): all of
+  // them before a refresh and for a map that had stopped, otherwise all once
+  // wf_sfold(m) have gathered.
+  if (lane == 0 && (A.phase != WF_PH_ITER || !M.active || M.k - M.s_k >= wf_sfold(m))) M.s_k = M.k;
+  __syncwarp();
   if (M.status == WF_ETIMEOUT) {  // a bounded device wait gave up on this map's data
     if (lane == 0) {
       M.active = 0;
