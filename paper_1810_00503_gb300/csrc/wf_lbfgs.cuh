@@ -1,8 +1,9 @@
 // Kernels of one device L-BFGS iteration (Sec. 2.2: L-BFGS on chi^2).
 //
 // Per iteration and map (all maps of a batch in each launch):
-//   k_lb_comb   streaming: applies the pending update s += a P, g += a Q of the
-//               previous step, forms the new direction
+//   k_lb_comb   streaming: applies the pending update g += a Q of the previous
+//               step (s += a P follows for the steps gathered, once every
+//               m - 1 iterations and whenever s is needed), forms the new direction
 //               p = dg g + sum_i (dP_i P_i + dQ_i Q_i) from the coefficients of
 //               the scalar two-loop, stores p into the ring, and accumulates the
 //               dot products of g with every stored vector;
@@ -480,31 +481,35 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
   wf_col_fwd_front<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, sp_ + (size_t)b * sp_stride, buf, s_tw,
                          tw_);
   constexpr int EB = WF_EMAX;
-#pragma unroll
-  for (int i0 = 0; i0 < WF_EMAX; i0 += EB) {
+  // element ii of this thread: packed row r = r0 + ii * rstep (rows c n + j of
+  // the C channels), column kx0 + t, fixed for the thread (blockDim is a
+  // multiple of TC); offsets fit 32 bits (C n h <= 2^20)
+  const int t = threadIdx.x & (TC - 1), r0 = threadIdx.x >> lgTC, rstep = WF_THREADS >> lgTC;
+  const int kx = kx0 + t;
+  const A wk = kx == 0 ? (A)1 : (A)2;
+  const V2<T>* Pb = Pn + kx;
+  const V2<T>* gb = gv + kx;
+  V2<T>* Qb = Qn + kx;
+  const int rows = C * n;
+  {
     V2<T> pl[EB], gl[EB];
 #pragma unroll
     for (int ii = 0; ii < EB; ++ii) {
-      const int e = threadIdx.x + (i0 + ii) * WF_THREADS;
-      if (e < tot) {
-        const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-        const size_t off = ((size_t)c * n + j) * h + kx0 + t;
-        pl[ii] = Pn[off];
-        gl[ii] = gv[off];
+      const int r = r0 + ii * rstep;
+      if (r < rows) {
+        pl[ii] = Pb[r * h];
+        gl[ii] = gb[r * h];
       }
     }
 #pragma unroll
     for (int ii = 0; ii < EB; ++ii) {
-      const int e = threadIdx.x + (i0 + ii) * WF_THREADS;
-      if (e < tot) {
-        const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-        const int kx = kx0 + t;
-        const size_t off = ((size_t)c * n + j) * h + kx;
+      const int r = r0 + ii * rstep;
+      if (r < rows) {
+        const int j = r & (n - 1), c = r >> lgn;
         const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
         const V2<T> p = pl[ii], gg = gl[ii];
         const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
-        Qn[off] = q;
-        const A wk = kx == 0 ? (A)1 : (A)2;
+        Qb[r * h] = q;
         qq += wk * (A)(q.x * q.x + q.y * q.y);
         pq += wk * (A)(p.x * q.x + p.y * q.y);
         pp += wk * (A)(p.x * p.x + p.y * p.y);
