@@ -205,22 +205,23 @@ __device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n
   const int TC = 1 << lgTC, CT = C * TC, lgn = __ffs(n) - 1, tot = C * n * TC, h = n >> 1;
   if constexpr (IN == WF_IN_PK && sizeof(T) == 4) {
     if (TC >= 2) {
-      const int lgP = lgTC - 1, tot2 = tot >> 1;
+      // a thread's column pair t is fixed (blockDim is a multiple of TC / 2);
+      // its rows r = r0 + i rstep (rows c n + j of the channels), packed
+      // offset r h + kx0 + t in 32 bits
+      const int lgP = lgTC - 1, rows = C * n;
+      const int t = (threadIdx.x & ((1 << lgP) - 1)) << 1, r0 = threadIdx.x >> lgP, rstep = WF_THREADS >> lgP;
+      const V2<T>* sb = src + kx0 + t;
       float4 v[WF_EMAX / 2];
 #pragma unroll
       for (int i = 0; i < WF_EMAX / 2; ++i) {
-        const int e = threadIdx.x + i * WF_THREADS;
-        if (e < tot2) {
-          const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
-          v[i] = *(const float4*)(src + ((size_t)c * n + j) * h + kx0 + t);
-        }
+        const int r = r0 + i * rstep;
+        if (r < rows) v[i] = *(const float4*)(sb + r * h);
       }
 #pragma unroll
       for (int i = 0; i < WF_EMAX / 2; ++i) {
-        const int e = threadIdx.x + i * WF_THREADS;
-        if (e < tot2) {
-          const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
-          const int x = j * CT + c * TC + t;
+        const int r = r0 + i * rstep;
+        if (r < rows) {
+          const int x = (r & (n - 1)) * CT + (r >> lgn) * TC + t;
           buf[wf_sw<T>(x)] = mk<T>(v[i].x, v[i].y);
           buf[wf_sw<T>(x + 1)] = mk<T>(v[i].z, v[i].w);
         }
@@ -252,15 +253,17 @@ __device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, i
   const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, lgn = __ffs(n) - 1, tot = C * n * TC;
   if constexpr (sizeof(T) == 4) {
     if (TC >= 2) {
-      const int lgP = lgTC - 1, tot2 = tot >> 1;
+      // as in wf_tile_load: fixed column pair t, rows r0 + i rstep
+      const int lgP = lgTC - 1, rows = C * n;
+      const int t = (threadIdx.x & ((1 << lgP) - 1)) << 1, r0 = threadIdx.x >> lgP, rstep = WF_THREADS >> lgP;
+      V2<T>* db = dst + kx0 + t;
 #pragma unroll
       for (int i = 0; i < WF_EMAX / 2; ++i) {
-        const int e = threadIdx.x + i * WF_THREADS;
-        if (e < tot2) {
-          const int t = (e & ((1 << lgP) - 1)) << 1, r = e >> lgP, j = r & (n - 1), c = r >> lgn;
-          const int x = j * CT + c * TC + t;
+        const int r = r0 + i * rstep;
+        if (r < rows) {
+          const int x = (r & (n - 1)) * CT + (r >> lgn) * TC + t;
           const V2<T> q0 = buf[wf_sw<T>(x)], q1 = buf[wf_sw<T>(x + 1)];
-          *(float4*)(dst + ((size_t)c * n + j) * h + kx0 + t) = make_float4(q0.x, q0.y, q1.x, q1.y);
+          *(float4*)(db + r * h) = make_float4(q0.x, q0.y, q1.x, q1.y);
         }
       }
       return;
