@@ -134,11 +134,19 @@ __device__ __forceinline__ void dft_reg(V2<T>* v) {
 // higher bits so that the strided accesses of the Stockham passes (stride R
 // in the first pass, stride C*TC in column tiles) spread over all banks:
 // 8-byte values fill 16 bank pairs, 16-byte values 8 bank quads.  A bijection
-// within each aligned block of 16 (8) values.  For 8-byte values one shifted
-// copy of the index (a shift and one three-input logic operation) is
-// conflict-free on every pass of the plans used; 16-byte values need two.
+// within each aligned block of 16 (8) values.  This form serves the in-place
+// passes, whose lanes walk the rows of one column of a column tile.
 template <typename T>
 __device__ __forceinline__ int wf_sw(int x) {
+  if constexpr (sizeof(T) == 4) return x ^ (((x >> 4) ^ (x >> 8)) & 15);
+  else return x ^ (((x >> 3) ^ (x >> 6)) & 7);
+}
+// The same for the ping-pong passes (wf_fft_pp.cuh), whose lanes walk the
+// columns of a tile first: there one shifted copy of the index (a shift and
+// one three-input logic operation) is conflict-free for 8-byte values on
+// every pass of the plans used; 16-byte values keep two.
+template <typename T>
+__device__ __forceinline__ int wf_swp(int x) {
   if constexpr (sizeof(T) == 4) return x ^ ((x >> 4) & 15);
   else return x ^ (((x >> 3) ^ (x >> 6)) & 7);
 }

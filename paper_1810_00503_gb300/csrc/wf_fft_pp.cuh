@@ -63,10 +63,10 @@ __device__ __forceinline__ V2<T>* wf_pp_out(int lgL, int plan, V2<T>* A, V2<T>* 
 template <typename T, int DIR, bool SEQF, int PLAN, class LD0, class STL, class H = WfNoHook>
 __device__ __forceinline__ void wf_pp_fft(int lgL, int lgcnt, int ts, int js, V2<T>* A, V2<T>* B,
                                           const V2<T>* ptab, LD0& ld0, STL& stl, H after1 = H()) {
-  auto ldA = [&](int t, int e) { return A[wf_sw<T>(t * ts + e * js)]; };
-  auto ldB = [&](int t, int e) { return B[wf_sw<T>(t * ts + e * js)]; };
-  auto stA = [&](int t, int e, V2<T> v) { A[wf_sw<T>(t * ts + e * js)] = v; };
-  auto stB = [&](int t, int e, V2<T> v) { B[wf_sw<T>(t * ts + e * js)] = v; };
+  auto ldA = [&](int t, int e) { return A[wf_swp<T>(t * ts + e * js)]; };
+  auto ldB = [&](int t, int e) { return B[wf_swp<T>(t * ts + e * js)]; };
+  auto stA = [&](int t, int e, V2<T> v) { A[wf_swp<T>(t * ts + e * js)] = v; };
+  auto stB = [&](int t, int e, V2<T> v) { B[wf_swp<T>(t * ts + e * js)] = v; };
   const int np = wf_plan_np(lgL, PLAN);
   if (np == 1) {
     switch (lgL) {

@@ -119,26 +119,26 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
     }
     const V2<T> wr = mk<T>(wl.x * r.x, wl.y * r.y);
     acc += (WfAcc<T>)(r.x * wr.x + r.y * wr.y);
-    O[wf_sw<T>(t * h + m)] = wr;
+    O[wf_swp<T>(t * h + m)] = wr;
   };
   wf_pp_fft<T, +1, false, PLAN>(lgh, lgRB, h, 1, A, Bf, s_pt, ld0, stpix, after1);
   __syncthreads();
   // r2c of wr: the input is O, so the passes start from the other buffer
   V2<T>* A2 = (O == A) ? Bf : A;
-  auto ldO = [&](int t, int e) { return O[wf_sw<T>(t * h + e)]; };
+  auto ldO = [&](int t, int e) { return O[wf_swp<T>(t * h + e)]; };
   V2<T>* Z = wf_pp_out<T>(lgh, PLAN, A2, O);
-  auto stZ = [&](int t, int e, V2<T> v) { Z[wf_sw<T>(t * h + e)] = v; };
+  auto stZ = [&](int t, int e, V2<T> v) { Z[wf_swp<T>(t * h + e)] = v; };
   wf_pp_fft<T, -1, false, PLAN>(lgh, lgRB, h, 1, A2, O, s_pt, ldO, stZ);
   __syncthreads();
   // r2c post-step: X[k] = (Z[k] + conj Z[h-k])/2 - i w^-k (Z[k] - conj Z[h-k])/2, X[0], X[h] packed
   for (int e = threadIdx.x; e < RB * h; e += blockDim.x) {
     const int t = e >> lgh, k = e & (h - 1);
-    const V2<T> Zk = Z[wf_sw<T>(t * h + k)];
+    const V2<T> Zk = Z[wf_swp<T>(t * h + k)];
     V2<T> X;
     if (k == 0) {
       X = mk<T>(Zk.x + Zk.y, Zk.x - Zk.y);
     } else {
-      const V2<T> Zm = Z[wf_sw<T>(t * h + h - k)];
+      const V2<T> Zm = Z[wf_swp<T>(t * h + h - k)];
       const V2<T> w1 = twid<T, -1>(roots, k << lgNTn);
       const V2<T> s1 = mk<T>(Zk.x + Zm.x, Zk.y - Zm.y), d1 = mk<T>(Zk.x - Zm.x, Zk.y + Zm.y);
       const V2<T> i1 = mul_i<T>(cmul<T>(w1, d1));
