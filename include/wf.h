@@ -123,7 +123,10 @@ typedef struct {
                                1024 = 16 x 8 x 8; 1: ascending, 8 x 8 x 16; 2: radix 32 first
                                for lengths 512 and 1024, 32 x 32).  wf_problem_variant reports
                                the one in use. */
-  int pad3_;
+  int history;              /* 0 (default): off.  k > 0: every map keeps a device ring of its
+                               last k iterations' records (k, chi2, |g|/|g0|, step, evals), the
+                               convergence trace the paper plots (Sec. 3, Fig. of chi2 against
+                               iteration); read with wf_solver_history.  40 k bytes per map. */
 } wf_opts;
 
 typedef struct {
@@ -251,6 +254,17 @@ wf_status wf_solver_finish(wf_problem* p, void* s_out, void* x_out, wf_solve_sta
  * scalar step.  Synchronises after every iteration.  Not part of the method;
  * used for roofline reports. */
 wf_status wf_solver_profile(wf_problem* p, int n_iter, float* ms);
+
+/* Convergence records of the solve started last on p with opts->history = cap
+ * > 0 (during the solve after a step, or after wf_solver_finish).  out: HOST
+ * double [count][cap][5]; map b's records are out[b][0 .. counts[b]-1], the
+ * last min(k_b, cap) iterations in order, each (k, chi2, |g|/|g0|, step length
+ * alpha, operator evaluations) as tracked by the solver (chi2 from the line
+ * model, |g|^2 from the dot products; the refreshes and the closing
+ * evaluation are exact); the rest is NaN.  counts: HOST int [count].
+ * Synchronises the solver's stream.  WF_EINVAL if no solve with a history was
+ * started. */
+wf_status wf_solver_history(const wf_problem* p, double* out, int* counts);
 
 /* MAP solves of several prepared problems at once, typically one per map
  * shape of a heterogeneous batch (Sec. 2.2).  Each problem runs on its own

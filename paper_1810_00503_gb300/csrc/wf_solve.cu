@@ -17,11 +17,15 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "wf_api_internal.h"
 
 struct WfScalarArgs {
   double gtol2, dchi2, c1, c2;
   int max_iter, m, ntile, nrb, ncomb, maxblk, phase, init, ls;
+  int hcap;      // convergence records kept per map (0: none)
+  double* hist;  // [B][hcap][5] ring of (k, chi2, |g|/|g0|, alpha, evals)
 };
 // Legacy and per-thread default stream handles cannot be captured; the solver
 // then runs on its own stream, ordered after the caller's with events.
@@ -51,6 +55,10 @@ struct WfSolver {
   long long iters;     // iterations launched since the last start
   wf_opts o;
   WfScalarArgs A;
+  double* hist;        // convergence ring, hist_cap records per map (allocated on demand)
+  int hist_cap;
+  double* g_hist;      // ring the graph was captured with
+  int g_hcap;
 };
 
 enum { WF_PH_ITER = 0, WF_PH_REFRESH = 1 };
@@ -304,6 +312,14 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
       M.npairs = np + 1 < m ? np + 1 : m;
       M.next = (nx + 1) % m;
       M.k += 1;
+      if (A.hcap > 0) {  // convergence record of iteration k
+        double* rec = A.hist + ((size_t)b * A.hcap + (M.k - 1) % A.hcap) * 5;
+        rec[0] = M.k;
+        rec[1] = M.chi2;
+        rec[2] = M.gg0 > 0.0 ? sqrt(gg / M.gg0) : 0.0;
+        rec[3] = alpha;
+        rec[4] = M.evals;
+      }
       if (!isfinite(M.chi2) || !isfinite(gg)) { done = true; M.status = WF_ENONFINITE; }
       else if (gg <= A.gtol2 * M.gg0) { done = true; }
       else if (A.dchi2 > 0.0 && fabs(M.chi2 - M.chi2_prev) < A.dchi2) { done = true; }
@@ -400,7 +416,7 @@ void wf_solver_free(wf_problem* p) {
   WfSolver* S = p->solver;
   if (!S) return;
   if (S->exec) cudaGraphExecDestroy(S->exec);
-  void* ptrs[] = {S->s, S->g, S->ring, S->st, S->nact, S->stats_dev};
+  void* ptrs[] = {S->s, S->g, S->ring, S->st, S->nact, S->stats_dev, S->hist};
   for (void* q : ptrs) wf_free(p->h, q);
   if (S->nact_host) cudaFreeHost(S->nact_host);
   if (S->stats_host) cudaFreeHost(S->stats_host);
@@ -677,6 +693,20 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   A.maxblk = p->g.maxblk;
   A.phase = WF_PH_ITER;
   A.init = 0;
+  A.hcap = 0;
+  A.hist = nullptr;
+  if (o->history > 0) {  // the convergence ring, kept (and grown) across solves
+    if (S->hist_cap < o->history) {
+      wf_free(p->h, S->hist);
+      S->hist = nullptr;
+      S->hist_cap = 0;
+      rs = wf_alloc(p->h, (void**)&S->hist, sizeof(double) * 5 * (size_t)o->history * p->count, "history ring");
+      if (rs != WF_OK) return rs;
+      S->hist_cap = o->history;
+    }
+    A.hcap = o->history;
+    A.hist = S->hist;
+  }
   WF_TRY(cudaEventRecord(S->ev_in, us));
   WF_TRY(cudaStreamWaitEvent(st, S->ev_in, 0));
   if (s0) WF_TRY(wf_launch_pack<T>(p->g, p->count, s0, S->s, st));
@@ -691,7 +721,8 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
                          S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m && S->g_ls == A.ls &&
                          S->g_c1 == A.c1 && S->g_c2 == A.c2 && S->g_inject == o->inject_timeout_map &&
-                         S->g_spin == o->spin_limit && S->g_variant == variant_code(p->g))) {
+                         S->g_spin == o->spin_limit && S->g_variant == variant_code(p->g) &&
+                         S->g_hist == A.hist && S->g_hcap == A.hcap)) {
     if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
     // Set every kernel's attributes outside capture: one iteration, then undo
     // nothing (it is a genuine iteration of the solve).
@@ -718,6 +749,8 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
     S->g_inject = o->inject_timeout_map;
     S->g_variant = variant_code(p->g);
     S->g_spin = o->spin_limit;
+    S->g_hist = A.hist;
+    S->g_hcap = A.hcap;
     S->g_stream = st;
   }
   S->started = 1;
@@ -860,6 +893,7 @@ static wf_status check_opts(const wf_problem* p, const wf_opts* o) {
   if (o->check_every < 0 || o->check_every > 4096) return wf_fail(WF_EINVAL, "bad check_every");
   if (o->refresh_every < 0) return wf_fail(WF_EINVAL, "bad refresh_every");
   if (o->spin_limit < 0) return wf_fail(WF_EINVAL, "spin_limit must be >= 0");
+  if (o->history < 0 || o->history > (1 << 20)) return wf_fail(WF_EINVAL, "history = %d outside [0, 2^20]", o->history);
   if (o->fft_variant != 0 && !variant_valid(o->fft_variant))
     return wf_fail(WF_EINVAL, "fft_variant = %d is not a valid variant code", o->fft_variant);
   if (o->inject_timeout_map > 0 && o->fft_variant != 0 && (o->fft_variant / 1000) % 10 != WF_COLINV_TMA_K)
@@ -988,5 +1022,31 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
 extern "C" wf_status wf_problem_variant(const wf_problem* p, int* variant) {
   if (!p || !variant) return wf_fail(WF_EINVAL, "wf_problem_variant: null argument");
   *variant = variant_code(p->g);
+  return WF_OK;
+}
+
+extern "C" wf_status wf_solver_history(const wf_problem* p, double* out, int* counts) {
+  if (!p || !out || !counts) return wf_fail(WF_EINVAL, "wf_solver_history: null argument");
+  const WfSolver* S = p->solver;
+  if (!S || !S->hist || S->A.hcap <= 0)
+    return wf_fail(WF_EINVAL, "wf_solver_history: no solve with a history was started");
+  const int cap = S->A.hcap, B = p->count;
+  std::vector<double> ring((size_t)B * cap * 5);
+  std::vector<WfLbMap> st(B);
+  cudaError_t e = cudaStreamSynchronize(S->work);
+  if (e == cudaSuccess) e = cudaMemcpy(ring.data(), S->hist, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(st.data(), S->st, sizeof(WfLbMap) * B, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return wf_cuda_fail(e, "wf_solver_history");
+  for (int b = 0; b < B; ++b) {
+    const int k = st[b].k, nrec = k < cap ? k : cap;
+    counts[b] = nrec;
+    double* ob = out + (size_t)b * cap * 5;
+    for (int i = 0; i < cap * 5; ++i) ob[i] = NAN;
+    for (int i = 0; i < nrec; ++i) {  // iterations k - nrec + 1 .. k, oldest first
+      const int it = k - nrec + 1 + i;
+      const double* r = ring.data() + ((size_t)b * cap + (it - 1) % cap) * 5;
+      for (int c = 0; c < 5; ++c) ob[(size_t)i * 5 + c] = r[c];
+    }
+  }
   return WF_OK;
 }

@@ -26,7 +26,7 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
            "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
            "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table",
-           "bandpower_iterate", "wf_problem_variant", "wf_alu_peak"]
+           "bandpower_iterate", "wf_problem_variant", "wf_alu_peak", "wf_solver_history"]
 
 
 class WfMap(ctypes.Structure):
@@ -42,7 +42,7 @@ class WfOpts(ctypes.Structure):
                 ("line_search", ctypes.c_int), ("pad_", ctypes.c_int), ("c1", ctypes.c_double),
                 ("c2", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("spin_limit", ctypes.c_longlong),
                 ("inject_timeout_map", ctypes.c_int), ("autotune", ctypes.c_int), ("fft_variant", ctypes.c_int),
-                ("pad3_", ctypes.c_int)]
+                ("history", ctypes.c_int)]
 
 
 class WfSolveStats(ctypes.Structure):
@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
     L.wf_workspace_used.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.wf_problem_variant.argtypes = [vp, ctypes.POINTER(i)]
     L.wf_alu_peak.argtypes = [i, ctypes.POINTER(d)]
+    L.wf_solver_history.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i)]
     L.wf_band_table.argtypes = [i, i, ctypes.POINTER(d), i, d, vp]
     L.wf_destroy.argtypes = [vp]
     L.wf_opts_default.argtypes = [ctypes.POINTER(WfOpts)]
@@ -408,6 +409,16 @@ class Problem:
         if t.dtype != self._cplx() or tuple(t.shape) != self.spec_shape() or not t.is_contiguous():
             raise ValueError(f"spectrum must be contiguous {self._cplx()} of shape {self.spec_shape()}")
         return t
+
+    def history(self, cap):
+        """wf_solver_history: per map a float64 array (n_b, 5) of (k, chi2,
+        |g|/|g0|, alpha, evals), the last iterations of the solve started with
+        history=cap."""
+        out = np.empty((self.B, cap, 5), dtype=np.float64)
+        counts = np.zeros(self.B, dtype=np.int32)
+        _check(lib().wf_solver_history(self._p, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return [out[b, : counts[b]].copy() for b in range(self.B)]
 
     def variant(self):
         """FFT-stage variant in use (wf_opts.fft_variant encoding: 1000 a + 100 b + 10 c + d)."""
