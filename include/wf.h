@@ -340,10 +340,11 @@ typedef struct {
   int n_fd_bands;
   int trunc_bands;        /* zero F[l][l'] for l, l' < trunc_bands with |l - l'| > trunc_width */
   int trunc_width;        /* (App. C: far off-diagonal EE terms, E bands first); 0, 0 = off */
-  int pad2_;
+  int out_on_device;      /* 0: the wf_bandpower_out arrays are HOST arrays; 1: DEVICE arrays */
 } wf_bandpower_in;
 
-/* Outputs of the band-power estimator: HOST arrays, written. */
+/* Outputs of the band-power estimator: HOST arrays, or DEVICE arrays when
+ * in->out_on_device, written. */
 typedef struct {
   double* theta_fid;      /* [n_bands] mean of P over each band's modes */
   double* E;              /* [n_bands] E_l of the data's MAP field (eq. el) */

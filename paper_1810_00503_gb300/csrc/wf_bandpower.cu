@@ -13,6 +13,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "wf_api_internal.h"
 
 // Theta_fid,l: full-plane mean of P over band l (half-plane multiplicity 1 on
@@ -228,6 +230,8 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   }
   if (!out->theta_fid || !out->E || !out->bias || !out->fisher || !out->cov || !out->theta_hat || !out->cov_E)
     return wf_fail(WF_EINVAL, "bandpower_estimate: null output array");
+  if (in->out_on_device != 0 && in->out_on_device != 1)
+    return wf_fail(WF_EINVAL, "bandpower_estimate: out_on_device = %d is not 0 or 1", in->out_on_device);
   if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "bandpower_estimate: bad dtype");
   wf_opts o;
   if (opts) o = *opts;
@@ -392,23 +396,24 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { free(hout); return wf_cuda_fail(e, "bandpower_estimate: reading results"); }
   const size_t nb2 = (size_t)nb * nb;
-  memcpy(out->theta_fid, hout, sizeof(double) * nb);
-  memcpy(out->E, hout + nb, sizeof(double) * nb);
-  memcpy(out->bias, hout + 2 * nb, sizeof(double) * nb);
-  memcpy(out->fisher, hout + 3 * nb, sizeof(double) * nb2);
-  memcpy(out->cov, hout + 3 * nb + nb2, sizeof(double) * nb2);
-  memcpy(out->theta_hat, hout + 3 * nb + 2 * nb2, sizeof(double) * nb);
-  memcpy(out->cov_E, hout + 4 * nb + 2 * nb2, sizeof(double) * nb2);
+  if (nfd == 0) {  // no Fisher maps on this call: F, F^-1 and Theta_hat are undefined
+    for (size_t i = 0; i < nb2; ++i) hout[3 * nb + i] = hout[3 * nb + nb2 + i] = NAN;
+    for (int l = 0; l < nb; ++l) hout[3 * nb + 2 * nb2 + l] = NAN;
+  }
+  // the outputs, host or device arrays
+  const cudaMemcpyKind kind = in->out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  double* dst[7] = {out->theta_fid, out->E, out->bias, out->fisher, out->cov, out->theta_hat, out->cov_E};
+  const size_t off[7] = {0, (size_t)nb, 2 * (size_t)nb, 3 * (size_t)nb, 3 * nb + nb2, 3 * nb + 2 * nb2, 4 * nb + 2 * nb2};
+  const size_t len[7] = {(size_t)nb, (size_t)nb, (size_t)nb, nb2, nb2, (size_t)nb, nb2};
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaMemcpy(dst[i], hout + off[i], sizeof(double) * len[i], kind);
   free(hout);
+  if (e != cudaSuccess) return wf_cuda_fail(e, "bandpower_estimate: writing results");
   if (out->E_maps) {
-    e = cudaMemcpy(out->E_maps, Eall, sizeof(double) * (size_t)Btot * nb, cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(out->E_maps, Eall, sizeof(double) * (size_t)Btot * nb,
+                   in->out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return wf_cuda_fail(e, "bandpower_estimate: reading E_maps");
   }
-  if (nfd == 0) {  // no Fisher maps on this call: F, F^-1 and Theta_hat are undefined
-    for (size_t i = 0; i < nb2; ++i) out->fisher[i] = out->cov[i] = NAN;
-    for (int l = 0; l < nb; ++l) out->theta_hat[l] = NAN;
-    return solve_status;
-  }
+  if (nfd == 0) return solve_status;
   if (hflag) return wf_fail(WF_ENONFINITE, "bandpower_estimate: the Fisher matrix is singular");
   return solve_status;
 }
@@ -453,14 +458,36 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
   m.P = Pc;
   wf_status worst = WF_OK;
   double q[64];
+  // device outputs: the estimates go to host arrays (the fiducial moves on the
+  // host between them) and the last one is copied out at the end
+  const bool dev = in->out_on_device != 0;
+  wf_bandpower_in inh = *in;
+  inh.out_on_device = 0;
+  const size_t nb2 = (size_t)nb * nb;
+  const int nF = in->n_fd_bands > 0 ? in->n_fd_bands : nb;
+  const size_t nEm = (size_t)(1 + in->n_sim + (size_t)nF * in->n_fd) * nb;
+  std::vector<double> hbuf(dev ? 4 * (size_t)nb + 3 * nb2 + (out->E_maps ? nEm : 0) : 0);
+  wf_bandpower_out hs = *out;
+  if (dev) {
+    double* p = hbuf.data();
+    hs.theta_fid = p; p += nb;
+    hs.E = p; p += nb;
+    hs.bias = p; p += nb;
+    hs.fisher = p; p += nb2;
+    hs.cov = p; p += nb2;
+    hs.theta_hat = p; p += nb;
+    hs.cov_E = p; p += nb2;
+    hs.E_maps = out->E_maps ? p : nullptr;
+  }
+  wf_bandpower_out* ob = dev ? &hs : out;
   for (int it = 0; it < n_iter; ++it) {
-    const wf_status rs = bandpower_estimate(h, &m, n, C, dtype, precision, in, &o, out, stats);
+    const wf_status rs = bandpower_estimate(h, &m, n, C, dtype, precision, &inh, &o, ob, stats);
     if (rs != WF_OK && rs != WF_ENOTCONVERGED) return rs;
     if (rs != WF_OK) worst = rs;
-    if (theta_hat_hist) memcpy(theta_hat_hist + (size_t)it * nb, out->theta_hat, sizeof(double) * nb);
+    if (theta_hat_hist) memcpy(theta_hat_hist + (size_t)it * nb, ob->theta_hat, sizeof(double) * nb);
     if (it + 1 == n_iter) break;
     for (int l = 0; l < nb; ++l) {  // regularised move of each band: ratio kept in [q_min, q_max]
-      const double r = out->theta_hat[l] / out->theta_fid[l];
+      const double r = ob->theta_hat[l] / ob->theta_fid[l];
       q[l] = isfinite(r) ? fmin(fmax(r, q_min), q_max) : 1.0;
     }
     BP_TRY(cudaMemcpyAsync(qd, q, sizeof(double) * nb, cudaMemcpyHostToDevice, st));
@@ -471,6 +498,13 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
   }
   if (P_out) BP_TRY(cudaMemcpyAsync(P_out, Pc, nsp * delt, cudaMemcpyDeviceToDevice, st));
   BP_TRY(cudaStreamSynchronize(st));
+  if (dev) {
+    double* dst[8] = {out->theta_fid, out->E, out->bias, out->fisher, out->cov, out->theta_hat, out->cov_E, out->E_maps};
+    const double* src[8] = {hs.theta_fid, hs.E, hs.bias, hs.fisher, hs.cov, hs.theta_hat, hs.cov_E, hs.E_maps};
+    const size_t len[8] = {(size_t)nb, (size_t)nb, (size_t)nb, nb2, nb2, (size_t)nb, nb2, nEm};
+    for (int i = 0; i < 8; ++i)
+      if (dst[i]) BP_TRY(cudaMemcpy(dst[i], src[i], sizeof(double) * len[i], cudaMemcpyHostToDevice));
+  }
   if (worst != WF_OK) wf_fail(worst, "bandpower_iterate: a solve hit its iteration limit");
   return worst;
 }

@@ -55,7 +55,7 @@ class WfBandpowerIn(ctypes.Structure):
                 ("pad_", ctypes.c_int), ("band", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("noise", ctypes.c_void_p), ("u", ctypes.c_void_p), ("sim_index", ctypes.c_void_p),
                 ("fd_bands", ctypes.c_void_p), ("n_fd_bands", ctypes.c_int), ("trunc_bands", ctypes.c_int),
-                ("trunc_width", ctypes.c_int), ("pad2_", ctypes.c_int)]
+                ("trunc_width", ctypes.c_int), ("out_on_device", ctypes.c_int)]
 
 
 class WfBandpowerOut(ctypes.Structure):
@@ -255,7 +255,7 @@ def normal_draw(seed, count, stream_id=0, offset=0, dtype=None, out=None, stream
 
 
 def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
-                    opts, fd_bands=None, trunc=(0, 0)):
+                    opts, fd_bands=None, trunc=(0, 0), out_on_device=False):
     """ctypes arguments shared by bandpower_estimate and bandpower_iterate."""
     import torch
     C, n, _ = Ninv.shape
@@ -274,12 +274,17 @@ def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, str
                        band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u),
                        sim_index=None if idx is None else idx.ctypes.data,
                        fd_bands=None if fdb is None else fdb.ctypes.data, n_fd_bands=0 if fdb is None else nbF,
-                       trunc_bands=int(trunc[0]), trunc_width=int(trunc[1]))
+                       trunc_bands=int(trunc[0]), trunc_width=int(trunc[1]), out_on_device=int(bool(out_on_device)))
     nmaps = 1 + J + nbF * F
-    arrs = {k: np.zeros(sz) for k, sz in (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb),
-                                          ("cov", nb * nb), ("theta_hat", nb), ("cov_E", nb * nb),
-                                          ("E_maps", nmaps * nb))}
-    bo = WfBandpowerOut(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in arrs.items()})
+    sizes = (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb), ("cov", nb * nb),
+             ("theta_hat", nb), ("cov_E", nb * nb), ("E_maps", nmaps * nb))
+    if out_on_device:  # float64 CUDA tensors on the current device
+        arrs = {k: torch.zeros(sz, dtype=torch.float64, device="cuda") for k, sz in sizes}
+        ptrs = {k: ctypes.cast(ctypes.c_void_p(v.data_ptr()), ctypes.POINTER(ctypes.c_double)) for k, v in arrs.items()}
+    else:
+        arrs = {k: np.zeros(sz) for k, sz in sizes}
+        ptrs = {k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in arrs.items()}
+    bo = WfBandpowerOut(**ptrs)
     o = WfOpts()
     lib().wf_opts_default(ctypes.byref(o))
     for k, v in opts.items():
@@ -302,7 +307,7 @@ def _bandpower_result(a):
 
 def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",
                        handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None, fd_bands=None,
-                       trunc=(0, 0), **opts):
+                       trunc=(0, 0), out_on_device=False, **opts):
     """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
     of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
     (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
@@ -313,10 +318,11 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
     split over calls).  fd_bands: the bands given Fisher maps (default all;
     the others' Fisher columns are interpolated, u then has one row per listed
     band); trunc = (n, w): zero F[l][l'] for l, l' < n with |l - l'| > w.
-    Returns (dict of numpy arrays, per-map stats)."""
+    Returns (dict of numpy arrays, or float64 CUDA tensors with out_on_device,
+    per-map stats)."""
     handle = handle or default_handle()
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
-                        opts, fd_bands, trunc)
+                        opts, fd_bands, trunc, out_on_device)
     status = lib().bandpower_estimate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
                                       ctypes.byref(a["bi"]), ctypes.byref(a["o"]), ctypes.byref(a["bo"]), a["st"])
     if status not in (0, 5):
@@ -326,7 +332,7 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
 
 def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_min=0.01, q_max=100.0,
                       precision="fp64", handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None,
-                      fd_bands=None, trunc=(0, 0), **opts):
+                      fd_bands=None, trunc=(0, 0), out_on_device=False, **opts):
     """bandpower_iterate: n_iter estimates, the fiducial P moved to each estimate
     in between (Sec. 2.3).  Arguments as bandpower_estimate.  Returns (last
     estimate, per-map stats of the last run, Theta_hat of every estimate
@@ -334,7 +340,7 @@ def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_
     import torch
     handle = handle or default_handle()
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
-                        opts, fd_bands, trunc)
+                        opts, fd_bands, trunc, out_on_device)
     hist = np.zeros((int(n_iter), a["nb"]))
     P_out = torch.empty_like(P)
     status = lib().bandpower_iterate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],

@@ -108,3 +108,29 @@ def test_sharded_calls_reduce_to_the_single_call():
     for k in ("bias", "fisher", "cov_E", "theta_hat", "cov"):
         assert _close(red[k], full[k], 1e-9), (k, red[k], full[k])
     assert np.allclose(full["E_maps"][1:1 + J].mean(axis=0), full["bias"], rtol=1e-12)
+
+
+def test_device_outputs_equal_host_outputs():
+    # in->out_on_device: the same estimate written to device arrays, single and
+    # iterated (whose fiducial moves on the host between estimates)
+    n, nb = 16, 3
+    inp = synth.density_small(n, seed=41)
+    dt = torch.float64
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    args = (to_dev(d, dt), to_dev(inp.mask, torch.uint8), to_dev(inp.Ninv, dt),
+            to_dev(inp.P[..., : n // 2 + 1], dt), to_dev(synth.log_bands(n, nb)[..., : n // 2 + 1], torch.int16),
+            nb, None, None, None)
+    kw = dict(precision="fp64", n_sim=4, n_fd=2, seed=9, gtol_rel=1e-12, max_iter=20000)
+    host, _ = wf.bandpower_estimate(*args, **kw)
+    dev, _ = wf.bandpower_estimate(*args, out_on_device=True, **kw)
+    # two runs agree to rounding (the band sums are accumulated with atomics,
+    # so their last bits depend on the order)
+    same = lambda a, b: np.allclose(a, b, rtol=1e-9, atol=1e-12 * np.abs(b).max(), equal_nan=True)
+    for k, v in host.items():
+        assert isinstance(dev[k], torch.Tensor) and dev[k].is_cuda
+        assert same(dev[k].cpu().numpy(), v), k
+    host_i, _, hist_h, _ = wf.bandpower_iterate(*args, n_iter=2, **kw)
+    dev_i, _, hist_d, _ = wf.bandpower_iterate(*args, n_iter=2, out_on_device=True, **kw)
+    assert same(hist_d, hist_h)
+    for k, v in host_i.items():
+        assert same(dev_i[k].cpu().numpy(), v), k
