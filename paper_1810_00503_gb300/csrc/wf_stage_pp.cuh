@@ -82,15 +82,15 @@ __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, 
 // the same row and is applied as the first pass loads; the r2c post-step runs
 // from the last pass's shared output.  src: the RB rows of packed spectra (h
 // values each, global or shared memory); sc: where the result rows go
-// (global); d, w: the pixel rows (RB n values from the block's first row).
-// Returns this thread's part of sum r.wr.  after1 runs once the first pass has
-// finished reading src.
+// (global); d, w: the pixel rows (RB n values from the block's first row);
+// roots: exp(-2 pi i k / n) for k < n/2, in shared memory.  Returns this
+// thread's part of sum r.wr.  after1 runs once the first pass has finished
+// reading src.
 template <typename T, int MODE, int PLAN, class H = WfNoHook>
 __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* src, V2<T>* sc, const T* d,
                                                    const T* w, const V2<T>* roots, const V2<T>* s_pt, V2<T>* A,
                                                    V2<T>* Bf, H after1 = H()) {
   const int n = g.n, h = g.h, lgh = g.lgh, RB = g.RB, lgRB = __ffs(RB) - 1;
-  const int lgNTn = WF_LOG2_NT - g.lgn;
   const V2<T>* dv = (const V2<T>*)d;
   const V2<T>* wv = (const V2<T>*)w;
   // c2r pre-step: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]), w = exp(+2 pi i / n);
@@ -100,7 +100,7 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
     const V2<T> Xk = row[k];
     if (k == 0) return mk<T>(Xk.x + Xk.y, Xk.x - Xk.y);
     const V2<T> Xm = row[h - k];
-    const V2<T> w1 = twid<T, +1>(roots, k << lgNTn);
+    const V2<T> w1 = twid<T, +1>(roots, k);
     const V2<T> s1 = mk<T>(Xk.x + Xm.x, Xk.y - Xm.y), d1 = mk<T>(Xk.x - Xm.x, Xk.y + Xm.y);
     return cadd<T>(s1, mul_i<T>(cmul<T>(w1, d1)));
   };
@@ -139,7 +139,7 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
       X = mk<T>(Zk.x + Zk.y, Zk.x - Zk.y);
     } else {
       const V2<T> Zm = Z[wf_swp<T>(t * h + h - k)];
-      const V2<T> w1 = twid<T, -1>(roots, k << lgNTn);
+      const V2<T> w1 = twid<T, -1>(roots, k);
       const V2<T> s1 = mk<T>(Zk.x + Zm.x, Zk.y - Zm.y), d1 = mk<T>(Zk.x - Zm.x, Zk.y + Zm.y);
       const V2<T> i1 = mul_i<T>(cmul<T>(w1, d1));
       X = mk<T>((T)0.5 * (s1.x - i1.x), (T)0.5 * (s1.y - i1.y));
@@ -164,11 +164,21 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
     wf_prefetch_rows(w + off, 1, 0, g.RB * n * (int)sizeof(T));
     if (MODE == WF_ROW_DATA) wf_prefetch_rows(d + off, 1, 0, g.RB * n * (int)sizeof(T));
   }
-  wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, g.lgh, PLAN);
+  {  // the length-h pass table (under WF_NT / 2 entries for h <= 512), then the
+     // n-th roots the real-FFT pre- and post-steps use
+    const V2<T>* gt = (const V2<T>*)tw_;
+    const V2<T>* src = gt + (size_t)WF_TWTAB * PLAN + (size_t)WF_NT * g.lgh;
+    const int lgNTn = WF_LOG2_NT - g.lgn;
+    for (int i = threadIdx.x; i < WF_NT / 2; i += blockDim.x) {
+      s_pt[i] = src[i];
+      if (i < h) s_pt[WF_NT / 2 + i] = gt[i << lgNTn];
+    }
+  }
+  __syncthreads();
   V2<T>* sc = scratch + (size_t)b * g.C * n * h + (size_t)row0 * h;
   const size_t poff = (size_t)b * npix + (size_t)row0 * n;
   const WfAcc<T> acc = wf_row_pp_core<T, MODE, PLAN>(g, sc, sc, MODE == WF_ROW_DATA ? d + poff : nullptr, w + poff,
-                                               (const V2<T>*)tw_, s_pt, A, Bf);
+                                                     s_pt + WF_NT / 2, s_pt, A, Bf);
   const double s = wf_block_sum((double)acc);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_DATA) * g.maxblk + blockIdx.x] = s;
 }
