@@ -29,7 +29,8 @@ Pins (what fixes this file independently of itself) live in
 tests/test_oracle_pins.py: naive O(n^4) DFT, Parseval, unmasked closed form
 S/(S+N), Woodbury agreement of the two dense Wiener-filter forms, exact central
 differences of a quadratic, the lambda_min >= 1 certificate, analytic band
-terms without a mask, and the Fisher identity Cov(E) = F.
+terms without a mask, the Fisher identity Cov(E) = F, and the leakage-bias form
+of App. C against the full Fisher run where E and B do not mix.
 Parity unpinned: iteration counts and chi^2-versus-iteration curves, because the
 paper gives them only as figures.
 """
@@ -437,7 +438,7 @@ def fisher_truncate(F, n_trunc, width):
 
 
 def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
-                   m=10, gtol_rel=1e-10, max_iter=20000, fd_bands=None, trunc=(0, 0)):
+                   m=10, gtol_rel=1e-10, max_iter=20000, fd_bands=None, trunc=(0, 0), leak_split=0):
     """Simulation estimates of Sec. 2.5 on one data map (C = 1, or C = 2 for the
     joint E/B case of App. C with separate band ids for the two channels).
 
@@ -454,6 +455,16 @@ def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
     given Fisher simulations (default all; u_fd then holds one row per listed
     band), the other columns from fisher_fill_columns.  trunc = (n_trunc,
     width): fisher_truncate before the inversion ((0, 0) = off).
+    leak_split = L > 0: the leakage-bias alternative of App. C (E bands
+    0..L-1, B bands L..n_bands-1).  The B power gets no per-band Fisher maps:
+    one map per simulation j < J_fd adds the fiducial power of every B band at
+    once, delta_Bj = M A_B u_Bj, and the B bands get only the diagonal response
+    F_ll = mean_j [E_l(MAP(d_j + delta_Bj)) - E_l(MAP(d_j))] / Theta_fid,l.
+    The cross blocks (E response to B power, B response to E power) are not
+    estimated: the E-to-B leakage enters through b alone, the mean over
+    simulations at the fiducial power, like the noise.  Per-band maps,
+    fd_bands (all < L), the interpolation and trunc then concern the E block;
+    u_fd holds one more row, the B fields, last.
     """
     W = mask[None] * Ninv
     theta = theta_fid(P, bands, n_bands)
@@ -468,7 +479,9 @@ def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
     E_s = np.array([E_of(sd) for sd in sims])
     b = E_s.mean(axis=0)
     J_fd = u_fd.shape[1]
-    fdb = list(range(n_bands)) if fd_bands is None else list(fd_bands)
+    L = int(leak_split)
+    nE = L if L > 0 else n_bands       # bands with per-band Fisher maps (all, or the E bands)
+    fdb = list(range(nE)) if fd_bands is None else list(fd_bands)
     F = np.zeros((n_bands, n_bands))
     for k, lp in enumerate(fdb):
         acc = np.zeros(n_bands)
@@ -476,8 +489,17 @@ def bandpower_sims(d, mask, Ninv, P, bands, n_bands, z_sims, n_sims, u_fd,
             delta = band_signal(u_fd[k, j], P, bands, lp) * mask[None]
             acc += E_of(sims[j] + delta) - E_s[j]
         F[:, lp] = acc / J_fd / theta[lp]
-    if len(fdb) < n_bands:
-        F = fisher_fill_columns(F, fdb)
+    if L > 0:
+        F[L:, :L] = 0.0                  # B response to E power: left to b
+        PB = np.where(bands >= L, P, 0.0)
+        acc = np.zeros(n_bands)
+        for j in range(J_fd):
+            delta = apply_A(u_fd[len(fdb), j], PB) * mask[None]
+            acc += E_of(sims[j] + delta) - E_s[j]
+        for l in range(L, n_bands):
+            F[l, l] = acc[l] / J_fd / theta[l]
+    if len(fdb) < nE:
+        F[:nE, :nE] = fisher_fill_columns(F[:nE, :nE], fdb)
     if trunc[0] > 0:
         F = fisher_truncate(F, trunc[0], trunc[1])
     Finv = np.linalg.inv(F)

@@ -365,3 +365,69 @@ def test_fisher_truncation_rule():
         for lp in range(6):
             zeroed = l < 4 and lp < 4 and abs(l - lp) > 1
             assert G[l, lp] == (0.0 if zeroed else F[l, lp])
+
+
+def _eb_leak_case(n, nb, J, nfd, seed, full_sky):
+    """E/B inputs with E bands 0..nb-1 and B bands nb..2nb-1, fields for the
+    full Fisher run (one row per band, every B band given the same field u_B)
+    and for the leakage-bias run (the E rows, then u_B)."""
+    inp = synth.shear_eb(n, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    if full_sky:
+        mask = np.ones((n, n), np.uint8)
+        Ninv = np.full((2, n, n), 2.0)
+    else:
+        mask, Ninv = inp.mask, inp.Ninv
+    sig = np.where(Ninv > 0, 1.0 / np.sqrt(np.where(Ninv > 0, Ninv, 1.0)), 0.0)
+    d = O.synthesize_data(inp.z, rng.standard_normal((2, n, n)) * sig, mask, inp.P)
+    b1 = synth.log_bands(n, nb)[0]
+    bands = np.stack([b1, np.where(b1 >= 0, b1 + nb, -1)])
+    z = rng.standard_normal((J, 2, n, n))
+    nz = rng.standard_normal((J, 2, n, n)) * sig
+    uE = rng.standard_normal((nb, nfd, 2, n, n))
+    uB = rng.standard_normal((1, nfd, 2, n, n))
+    u_full = np.concatenate([uE] + [uB] * nb)
+    u_leak = np.concatenate([uE, uB])
+    return d, mask, Ninv, inp.P, bands, z, nz, u_full, u_leak
+
+
+def test_leakage_bias_equals_full_fisher_when_nothing_leaks():
+    """App. C leakage-bias alternative.  Without a mask and with isotropic
+    noise, E and B do not mix (R(k) orthogonal, c I on the Nyquist lines) and
+    the Hessian is diagonal per mode, so a B injection moves only its own
+    band's modes: the joint B map's response in band l equals the per-band
+    map's when both use the same field, and the full Fisher matrix is diagonal
+    in its B block with empty cross blocks.  Both estimates must then agree."""
+    n, nb, J, nfd = 8, 2, 3, 2
+    d, mask, Ninv, P, bands, z, nz, u_full, u_leak = _eb_leak_case(n, nb, J, nfd, 31, True)
+    kw = dict(gtol_rel=1e-12, max_iter=20000)
+    full = O.bandpower_sims(d, mask, Ninv, P, bands, 2 * nb, z, nz, u_full, **kw)
+    leak = O.bandpower_sims(d, mask, Ninv, P, bands, 2 * nb, z, nz, u_leak, leak_split=nb, **kw)
+    F, G = full["F"], leak["F"]
+    scale = np.abs(F).max()
+    assert np.abs(F - G).max() <= 1e-8 * scale, (F, G)
+    assert np.all(np.diag(G)[nb:] > 0.0)
+    assert np.allclose(leak["theta_hat"], full["theta_hat"], rtol=1e-7, atol=0.0)
+    assert np.array_equal(leak["b"], full["b"])
+
+
+def test_leakage_bias_blocks_under_a_mask():
+    """Under a mask the full Fisher matrix has E-B cross terms; the
+    leakage-bias form keeps the full EE block, drops the cross blocks and the
+    BB off-diagonal, so the E estimates do not depend on the B fields."""
+    n, nb, J, nfd = 8, 2, 3, 2
+    d, mask, Ninv, P, bands, z, nz, u_full, u_leak = _eb_leak_case(n, nb, J, nfd, 32, False)
+    kw = dict(gtol_rel=1e-12, max_iter=20000)
+    full = O.bandpower_sims(d, mask, Ninv, P, bands, 2 * nb, z, nz, u_full, **kw)
+    leak = O.bandpower_sims(d, mask, Ninv, P, bands, 2 * nb, z, nz, u_leak, leak_split=nb, **kw)
+    F, G = full["F"], leak["F"]
+    assert np.abs(F[:nb, nb:]).max() > 1e-6 * np.abs(F).max()      # the mask mixes E and B
+    assert np.abs(F[nb:, :nb]).max() > 1e-6 * np.abs(F).max()
+    assert np.array_equal(G[:nb, :nb], F[:nb, :nb])
+    assert not G[:nb, nb:].any() and not G[nb:, :nb].any()
+    assert np.array_equal(G[nb:, nb:], np.diag(np.diag(G)[nb:]))
+    u2 = u_leak.copy()
+    u2[nb] = np.random.default_rng(5).standard_normal(u2[nb].shape)
+    leak2 = O.bandpower_sims(d, mask, Ninv, P, bands, 2 * nb, z, nz, u2, leak_split=nb, **kw)
+    assert np.array_equal(leak2["theta_hat"][:nb], leak["theta_hat"][:nb])
+    assert not np.allclose(leak2["theta_hat"][nb:], leak["theta_hat"][nb:], rtol=1e-6)
