@@ -323,11 +323,25 @@ typedef struct {
   int n_fd;               /* Fisher simulations per band, 0..n_sim; the j-th reuses simulation j.
                              0 (a rank of a multi-GPU run that owns no Fisher map) leaves
                              fisher, cov and theta_hat as NaN */
-  int pad_;
+  int leak_split;         /* 0 = off.  L in [1, n_bands): the leakage-bias alternative of App. C
+                             for the joint E/B case (C = 2), bands 0..L-1 the E bands and
+                             L..n_bands-1 the B bands.  Per-band Fisher maps are made for E
+                             bands only; for the B bands one Fisher map per simulation j < n_fd
+                             adds the fiducial power of every B band at once, d_j + M A_B u_Bj,
+                             and F[l][l] = mean_j (E_l(that map) - E_l(d_j)) / Theta_fid,l is
+                             their only Fisher term.  The cross blocks F[E][B] and F[B][E] and
+                             the BB off-diagonal are 0: the E-to-B leakage enters through b,
+                             the mean over the simulations at the fiducial power, as the noise
+                             does.  fd_bands (all < L) and trunc_bands (<= L) then concern the
+                             E block, a column's interpolation staying inside it; u holds one
+                             more row, u_B, after the E rows, drawn on the device as band L's
+                             row.  Saves (n_bands - L - 1) n_fd solves against the full form */
   const int16_t* band;    /* [C][n][n/2+1] band id of each half-plane mode, -1 = none */
   const void* z;          /* [n_sim][C][n][n] white signal fields, N(0, 1) */
   const void* noise;      /* [n_sim][C][n][n] noise realisations with variance 1/Ninv */
-  const void* u;          /* [n_bands or n_fd_bands][n_fd][C][n][n] white fields for the Fisher signals */
+  const void* u;          /* [n_R][n_fd][C][n][n] white fields for the Fisher signals: n_R = the
+                             bands with Fisher maps (n_bands, n_fd_bands, or L with leak_split),
+                             plus 1 with leak_split */
   const long long* sim_index;  /* HOST [n_sim] global index (>= 0) of each simulation, used by
                                   the device draws; NULL = 0 .. n_sim-1 */
   const int* fd_bands;    /* HOST [n_fd_bands] ascending band ids that get Fisher maps (NULL =
@@ -353,8 +367,8 @@ typedef struct {
   double* cov;            /* [n_bands * n_bands] F^-1 (eq. var) */
   double* theta_hat;      /* [n_bands] Theta_fid + F^-1 (E - b) (eq. eq:wfmv) */
   double* cov_E;          /* [n_bands * n_bands] sample covariance of E over the simulations */
-  double* E_maps;         /* optional (NULL = not written): [1 + n_sim + n_F * n_fd][n_bands], n_F
-                             the bands with Fisher maps (n_bands or n_fd_bands),
+  double* E_maps;         /* optional (NULL = not written): [1 + n_sim + n_R * n_fd][n_bands], n_R
+                             the Fisher rows of wf_bandpower_in.u,
                              E of every solved map (data, simulations, Fisher maps), for callers
                              that combine simulations from several GPUs */
 } wf_bandpower_out;
@@ -369,7 +383,7 @@ typedef struct {
  *   E_l(d_j)) / Theta_fid,l', cov = F^-1, Theta_hat = Theta_fid + F^-1 (E - b).
  * data: HOST descriptor of the data map with DEVICE pointers (its P is the
  * fiducial spectrum); n, C, dtype, precision as for wf_problem_create.
- * stats: HOST array of 1 + n_sim + n_bands * n_fd entries (data, simulations,
+ * stats: HOST array of 1 + n_sim + n_R * n_fd entries (data, simulations,
  * Fisher maps in that order) or NULL.  Allocates its working memory and frees it
  * before returning; synchronises opts->stream.  Returns WF_ENOTCONVERGED when a
  * solve hit max_iter (outputs still written), WF_ENONFINITE if F is singular. */

@@ -38,15 +38,26 @@ __global__ void k_theta_fid(const S* P, const int16_t* band, int n, int C, int n
   for (int l = threadIdx.x; l < nb; l += blockDim.x) theta[l] = sh[nb + l] > 0.0 ? sh[l] / sh[nb + l] : 0.0;
 }
 
-// P restricted to each band: out[l][i] = band[i] == l ? P[i] : 0.
+// P restricted to each band: out[l][i] = band[i] == l ? P[i] : 0; with lo > 0
+// one more table, P on the bands lo and above (the B bands of the
+// leakage-bias form): out[nb][i] = band[i] >= lo ? P[i] : 0.
 template <typename S>
-__global__ void k_band_P(const S* P, const int16_t* band, size_t tot, int nb, S* out) {
+__global__ void k_band_P(const S* P, const int16_t* band, size_t tot, int nb, int lo, S* out) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += stride) {
     const int l = band[i];
     const S p = P[i];
     for (int k = 0; k < nb; ++k) out[(size_t)k * tot + i] = (l == k) ? p : (S)0;
+    if (lo > 0) out[(size_t)nb * tot + i] = (l >= lo) ? p : (S)0;
   }
+}
+
+// Rows of wf_bandpower_in.u: the bands with per-band Fisher maps (every band,
+// the listed ones, or the E bands of the leakage-bias form), then with
+// leak_split the one row of joint B maps.
+static int bp_fisher_rows(const wf_bandpower_in* in) {
+  const int nE = in->leak_split > 0 ? in->leak_split : in->n_bands;
+  return (in->fd_bands ? in->n_fd_bands : nE) + (in->leak_split > 0 ? 1 : 0);
 }
 
 // Estimator from the band energies of all solved maps.  Rows of Eall: 0 = data,
@@ -58,11 +69,14 @@ __global__ void k_band_P(const S* P, const int16_t* band, size_t tot, int nb, S*
 // whose row leaves the matrix dropped and the other weighted alone; beyond the
 // first or last sampled column the nearest one is shifted.  Then the terms
 // |l - l'| > trunc_w with l, l' < trunc_n are zeroed (App. C: far off-diagonal
-// EE terms).  out = [theta | E | b | F | Finv | theta_hat | covE] (sizes nb,
+// EE terms).  leak > 0 (the leakage-bias form of App. C, B bands leak..nb-1):
+// fdk of every B band is the row of the joint B maps, a B band keeps only its
+// diagonal term, the E-B cross terms are zeroed, and the interpolation of an
+// E column stays inside the E block.  out = [theta | E | b | F | Finv | theta_hat | covE] (sizes nb,
 // nb, nb, nb^2, nb^2, nb, nb^2); flag[0] = 1 if F is singular.  One block,
 // nb <= 64.
 __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int J, int nfd, const int* fdk,
-                           int trunc_n, int trunc_w, double* out, int* flag) {
+                           int trunc_n, int trunc_w, int leak, double* out, int* flag) {
   extern __shared__ double M[];  // [nb][2 nb] augmented matrix for Gauss-Jordan
   __shared__ double piv_val;
   __shared__ int piv_row;
@@ -94,13 +108,18 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
     o_cE[idx] = J > 1 ? c / (J - 1) : NAN;
   }
   __syncthreads();
+  const int lim = leak > 0 ? leak : nb;  // bands an interpolated column draws on (its block)
   for (int idx = t; idx < nb * nb; idx += blockDim.x) {  // columns without Fisher maps
     const int l = idx / nb, lp = idx % nb;
     if (fdk[lp] >= 0 || nfd == 0) continue;
+    if (l >= lim) {
+      o_F[idx] = 0.0;
+      continue;
+    }
     int s0 = -1, s1 = -1;
     for (int q = lp - 1; q >= 0 && s0 < 0; --q)
       if (fdk[q] >= 0) s0 = q;
-    for (int q = lp + 1; q < nb && s1 < 0; ++q)
+    for (int q = lp + 1; q < lim && s1 < 0; ++q)
       if (fdk[q] >= 0) s1 = q;
     double w0 = 0.0, w1 = 0.0;
     if (s0 >= 0 && s1 >= 0) {
@@ -113,11 +132,11 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
     }
     const int o = l - lp;
     double acc = 0.0, ws = 0.0;
-    if (s0 >= 0 && w0 > 0.0 && s0 + o >= 0 && s0 + o < nb) {
+    if (s0 >= 0 && w0 > 0.0 && s0 + o >= 0 && s0 + o < lim) {
       acc += w0 * o_F[(s0 + o) * nb + s0];
       ws += w0;
     }
-    if (s1 >= 0 && w1 > 0.0 && s1 + o >= 0 && s1 + o < nb) {
+    if (s1 >= 0 && w1 > 0.0 && s1 + o >= 0 && s1 + o < lim) {
       acc += w1 * o_F[(s1 + o) * nb + s1];
       ws += w1;
     }
@@ -127,6 +146,7 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
   for (int idx = t; idx < nb * nb; idx += blockDim.x) {
     const int l = idx / nb, lp = idx % nb;
     if (l < trunc_n && lp < trunc_n && abs(l - lp) > trunc_w) o_F[idx] = 0.0;
+    if (leak > 0 && (l >= leak || lp >= leak) && l != lp) o_F[idx] = 0.0;  // cross blocks, BB off-diagonal
   }
   __syncthreads();
   // Gauss-Jordan elimination with partial pivoting on [F | I]
@@ -220,7 +240,14 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (in->trunc_bands < 0 || in->trunc_bands > nb || in->trunc_width < 0)
     return wf_fail(WF_EINVAL, "bandpower_estimate: trunc_bands = %d, trunc_width = %d", in->trunc_bands,
                    in->trunc_width);
-  if (in->fd_bands && (in->n_fd_bands < 1 || in->n_fd_bands > nb))
+  const int L = in->leak_split;  // > 0: leakage-bias form, B bands L..nb-1
+  if (L < 0 || L >= nb || (L > 0 && C != 2))
+    return wf_fail(WF_EINVAL, "bandpower_estimate: leak_split = %d (need 0, or 1..n_bands-1 with C = 2)", L);
+  if (L > 0 && in->trunc_bands > L)
+    return wf_fail(WF_EINVAL, "bandpower_estimate: trunc_bands = %d beyond the E bands (leak_split = %d)",
+                   in->trunc_bands, L);
+  const int nE = L > 0 ? L : nb;  // bands that may get per-band Fisher maps
+  if (in->fd_bands && (in->n_fd_bands < 1 || in->n_fd_bands > nE))
     return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd_bands = %d", in->n_fd_bands);
   if (in->sim_index) {
     const unsigned long long lim = (1ull << 62) / ((unsigned long long)C * n * n * (nb + 1));
@@ -240,21 +267,26 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   const size_t delt = dtype == WF_F64 ? 8 : 4;
   const size_t welt = precision == WF_FP64 ? 8 : 4;
   const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
-  // bands given Fisher maps (all by default) and each band's Fisher-map row
+  // bands given per-band Fisher maps (all, or all E bands, by default) and each
+  // band's Fisher-map row; with leak_split every B band points at the last row,
+  // the joint B maps
   int fdb[64], fdk[64], nbF = 0;
   for (int l = 0; l < nb; ++l) fdk[l] = -1;
   if (in->fd_bands) {
     for (int k = 0; k < in->n_fd_bands; ++k) {
       const int l = in->fd_bands[k];
-      if (l < 0 || l >= nb || (k > 0 && l <= fdb[k - 1]))
-        return wf_fail(WF_EINVAL, "bandpower_estimate: fd_bands must be ascending band ids in [0, n_bands)");
+      if (l < 0 || l >= nE || (k > 0 && l <= fdb[k - 1]))
+        return wf_fail(WF_EINVAL, "bandpower_estimate: fd_bands must be ascending band ids in [0, %s)",
+                       L > 0 ? "leak_split" : "n_bands");
       fdb[nbF] = l;
       fdk[l] = nbF++;
     }
   } else {
-    for (int l = 0; l < nb; ++l) fdb[nbF] = l, fdk[l] = nbF++;
+    for (int l = 0; l < nE; ++l) fdb[nbF] = l, fdk[l] = nbF++;
   }
-  const int nF = nbF * nfd, Btot = 1 + J + nF;
+  for (int l = nE; l < nb; ++l) fdk[l] = nbF;
+  const int nR = bp_fisher_rows(in);  // nbF, plus the joint B row
+  const int nF = nR * nfd, Btot = 1 + J + nF;
   Scope sc(h);
   // Theta_fid and the band-restricted power tables
   double* theta = nullptr;
@@ -266,13 +298,13 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     k_theta_fid<float><<<1, 1024, 2 * nb * sizeof(double), st>>>((const float*)data->P, in->band, n, C, nb, theta);
   BP_TRY(cudaGetLastError());
   void* Pl = nullptr;
-  BP_OK(wf_alloc(h, &Pl, nsp * nb * delt, "band-restricted power"));
+  BP_OK(wf_alloc(h, &Pl, nsp * (nb + (L > 0)) * delt, "band-restricted power"));
   sc.add(Pl);
   const int gblk = (int)((nsp + 255) / 256 < 4096 ? (nsp + 255) / 256 : 4096);
   if (dtype == WF_F64)
-    k_band_P<double><<<gblk, 256, 0, st>>>((const double*)data->P, in->band, nsp, nb, (double*)Pl);
+    k_band_P<double><<<gblk, 256, 0, st>>>((const double*)data->P, in->band, nsp, nb, L, (double*)Pl);
   else
-    k_band_P<float><<<gblk, 256, 0, st>>>((const float*)data->P, in->band, nsp, nb, (float*)Pl);
+    k_band_P<float><<<gblk, 256, 0, st>>>((const float*)data->P, in->band, nsp, nb, L, (float*)Pl);
   BP_TRY(cudaGetLastError());
 
   // noise-bias simulations d_j = M (A z_j + n_j)
@@ -304,8 +336,8 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
       if (rs == WF_OK)
         rs = wf_draw_normal(o.seed, 1, g * npix, npix, f64, (char*)nb_ + j * npix * welt,
                             (const char*)psim->w + j * npix * welt, st);
-      for (int k = 0; k < nbF && j < nfd && rs == WF_OK; ++k)  // Fisher map (band fdb[k], j) reuses simulation j
-        rs = wf_draw_normal(o.seed, 2, (g * nb + fdb[k]) * npix, npix, f64,
+      for (int k = 0; k < nR && j < nfd && rs == WF_OK; ++k)  // Fisher map (row k, j) reuses simulation j;
+        rs = wf_draw_normal(o.seed, 2, (g * nb + (k < nbF ? fdb[k] : L)) * npix, npix, f64,  // joint B: band L's
                             (char*)ub + ((size_t)k * nfd + j) * npix * welt, nullptr, st);
     }
     if (rs != WF_OK) { free(maps); return rs; }
@@ -321,9 +353,11 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (rs != WF_OK) { free(maps); return rs; }
 
   // Fisher maps: d_j + M A_l u_lj, synthesised with the band-restricted power as
-  // signal and the simulation's data as "noise" (M d_j = d_j)
-  for (int k = 0; k < nbF; ++k)
-    for (int j = 0; j < nfd; ++j) maps[k * nfd + j].P = (const char*)Pl + (size_t)fdb[k] * nsp * delt;
+  // signal and the simulation's data as "noise" (M d_j = d_j); the joint B maps
+  // with the power of every B band
+  for (int k = 0; k < nR; ++k)
+    for (int j = 0; j < nfd; ++j)
+      maps[k * nfd + j].P = (const char*)Pl + (size_t)(k < nbF ? fdb[k] : nb) * nsp * delt;
   void* dfd = nullptr;
   if (nF > 0) {
     wf_problem* pfd = nullptr;
@@ -335,7 +369,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     if (rs == WF_OK) { sc.add(nfd_in); rs = wf_alloc(h, &dfd, npix * nF * welt, "Fisher data"); }
     if (rs != WF_OK) { free(maps); return rs; }
     sc.add(dfd);
-    for (int k = 0; k < nbF; ++k)
+    for (int k = 0; k < nR; ++k)
       for (int j = 0; j < nfd; ++j) {
         cudaError_t e = cudaMemcpyAsync((char*)nfd_in + (size_t)(k * nfd + j) * npix * welt,
                                         (const char*)dsim + (size_t)j * npix * welt, npix * welt,
@@ -386,7 +420,8 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   BP_TRY(cudaMemcpyAsync(dfdk, fdk, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
   const size_t gj_smem = sizeof(double) * 2 * nb * nb;
   BP_TRY(cudaFuncSetAttribute(k_bp_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 64 * 64 * 8)));
-  k_bp_final<<<1, 256, gj_smem, st>>>(Eall, theta, nb, J, nfd, dfdk, in->trunc_bands, in->trunc_width, dout, dflag);
+  k_bp_final<<<1, 256, gj_smem, st>>>(Eall, theta, nb, J, nfd, dfdk, in->trunc_bands, in->trunc_width, L, dout,
+                                      dflag);
   BP_TRY(cudaGetLastError());
   double* hout = (double*)malloc(sizeof(double) * nout);
   if (!hout) return wf_fail(WF_ENOMEM, "bandpower_estimate: host allocation");
@@ -464,8 +499,7 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
   wf_bandpower_in inh = *in;
   inh.out_on_device = 0;
   const size_t nb2 = (size_t)nb * nb;
-  const int nF = in->n_fd_bands > 0 ? in->n_fd_bands : nb;
-  const size_t nEm = (size_t)(1 + in->n_sim + (size_t)nF * in->n_fd) * nb;
+  const size_t nEm = (size_t)(1 + in->n_sim + (size_t)bp_fisher_rows(in) * in->n_fd) * nb;
   std::vector<double> hbuf(dev ? 4 * (size_t)nb + 3 * nb2 + (out->E_maps ? nEm : 0) : 0);
   wf_bandpower_out hs = *out;
   if (dev) {

@@ -85,6 +85,8 @@ def estimate_on_rank(d, mask, Ninv, P, band, n_bands, n_sim, n_fd, world, rank, 
     from . import wf
     if opts.get("fd_bands") is not None:
         raise ValueError("estimate_on_rank: every band needs Fisher maps (fd_bands is not supported)")
+    if opts.get("leak_split"):
+        raise ValueError("estimate_on_rank: the leakage-bias form (leak_split) is not supported")
     sims, (fd_lo, fd_hi) = assignment(n_sim, n_fd, world, rank)
     res, stats = wf.bandpower_estimate(d, mask, Ninv, P, band, n_bands, None, None, None, n_sim=len(sims),
                                        n_fd=fd_hi - fd_lo, sim_index=sims, seed=seed, **opts)

@@ -52,7 +52,7 @@ class WfSolveStats(ctypes.Structure):
 
 class WfBandpowerIn(ctypes.Structure):
     _fields_ = [("n_bands", ctypes.c_int), ("n_sim", ctypes.c_int), ("n_fd", ctypes.c_int),
-                ("pad_", ctypes.c_int), ("band", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("leak_split", ctypes.c_int), ("band", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("noise", ctypes.c_void_p), ("u", ctypes.c_void_p), ("sim_index", ctypes.c_void_p),
                 ("fd_bands", ctypes.c_void_p), ("n_fd_bands", ctypes.c_int), ("trunc_bands", ctypes.c_int),
                 ("trunc_width", ctypes.c_int), ("out_on_device", ctypes.c_int)]
@@ -255,7 +255,7 @@ def normal_draw(seed, count, stream_id=0, offset=0, dtype=None, out=None, stream
 
 
 def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
-                    opts, fd_bands=None, trunc=(0, 0), out_on_device=False):
+                    opts, fd_bands=None, trunc=(0, 0), out_on_device=False, leak_split=0):
     """ctypes arguments shared by bandpower_estimate and bandpower_iterate."""
     import torch
     C, n, _ = Ninv.shape
@@ -269,13 +269,16 @@ def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, str
         if idx.shape != (J,):
             raise ValueError("sim_index needs one entry per simulation")
     fdb = None if fd_bands is None else np.ascontiguousarray(fd_bands, dtype=np.int32)
-    nbF = nb if fdb is None else int(fdb.size)
-    bi = WfBandpowerIn(n_bands=nb, n_sim=J, n_fd=F, pad_=0,
+    L = int(leak_split)
+    nR = ((L if L > 0 else nb) if fdb is None else int(fdb.size)) + (1 if L > 0 else 0)  # Fisher rows of u
+    if u is not None and int(u.shape[0]) != nR:
+        raise ValueError(f"u has {int(u.shape[0])} Fisher rows, the call needs {nR}")
+    bi = WfBandpowerIn(n_bands=nb, n_sim=J, n_fd=F, leak_split=L,
                        band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u),
                        sim_index=None if idx is None else idx.ctypes.data,
-                       fd_bands=None if fdb is None else fdb.ctypes.data, n_fd_bands=0 if fdb is None else nbF,
+                       fd_bands=None if fdb is None else fdb.ctypes.data, n_fd_bands=0 if fdb is None else int(fdb.size),
                        trunc_bands=int(trunc[0]), trunc_width=int(trunc[1]), out_on_device=int(bool(out_on_device)))
-    nmaps = 1 + J + nbF * F
+    nmaps = 1 + J + nR * F
     sizes = (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb), ("cov", nb * nb),
              ("theta_hat", nb), ("cov_E", nb * nb), ("E_maps", nmaps * nb))
     if out_on_device:  # float64 CUDA tensors on the current device
@@ -307,7 +310,7 @@ def _bandpower_result(a):
 
 def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="fp64",
                        handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None, fd_bands=None,
-                       trunc=(0, 0), out_on_device=False, **opts):
+                       trunc=(0, 0), out_on_device=False, leak_split=0, **opts):
     """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
     of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
     (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
@@ -318,11 +321,15 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
     split over calls).  fd_bands: the bands given Fisher maps (default all;
     the others' Fisher columns are interpolated, u then has one row per listed
     band); trunc = (n, w): zero F[l][l'] for l, l' < n with |l - l'| > w.
+    leak_split = L > 0 (C = 2, E bands 0..L-1, B bands L..): the leakage-bias
+    form of App. C, per-band Fisher maps for the E bands only, one joint map of
+    all B bands per Fisher simulation giving the B bands' diagonal, no E-B
+    cross terms; u then has the E rows and one more, the B fields.
     Returns (dict of numpy arrays, or float64 CUDA tensors with out_on_device,
     per-map stats)."""
     handle = handle or default_handle()
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
-                        opts, fd_bands, trunc, out_on_device)
+                        opts, fd_bands, trunc, out_on_device, leak_split)
     status = lib().bandpower_estimate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
                                       ctypes.byref(a["bi"]), ctypes.byref(a["o"]), ctypes.byref(a["bo"]), a["st"])
     if status not in (0, 5):
@@ -332,7 +339,7 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
 
 def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_min=0.01, q_max=100.0,
                       precision="fp64", handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None,
-                      fd_bands=None, trunc=(0, 0), out_on_device=False, **opts):
+                      fd_bands=None, trunc=(0, 0), out_on_device=False, leak_split=0, **opts):
     """bandpower_iterate: n_iter estimates, the fiducial P moved to each estimate
     in between (Sec. 2.3).  Arguments as bandpower_estimate.  Returns (last
     estimate, per-map stats of the last run, Theta_hat of every estimate
@@ -340,7 +347,7 @@ def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_
     import torch
     handle = handle or default_handle()
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
-                        opts, fd_bands, trunc, out_on_device)
+                        opts, fd_bands, trunc, out_on_device, leak_split)
     hist = np.zeros((int(n_iter), a["nb"]))
     P_out = torch.empty_like(P)
     status = lib().bandpower_iterate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],

@@ -161,3 +161,80 @@ def test_device_draws_of_sampled_bands_agree_with_the_full_run():
     for lp in (1, 3):
         assert np.abs(F[:, lp] - G[:, lp]).max() <= 1e-9 * np.abs(F).max()
     assert np.allclose(full["bias"], part["bias"], rtol=1e-12)
+
+
+def test_leakage_bias_eb_matches_oracle():
+    """Leakage-bias form of App. C: E bands 0, 1 with per-band Fisher maps, B
+    bands 2, 3 from one joint map per Fisher simulation, no E-B cross terms."""
+    n, nb, J, nfd = 16, 2, 5, 2
+    inp = synth.shear_eb(n, seed=6)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb, C=2)
+    z, nz, u = _fields(inp, J, nb + 1, nfd, 2, 19)
+    dd, mk, Nv, Pv, bv = _dev(inp, d, inp.P, bands)
+    res, stats = wf.bandpower_estimate(dd, mk, Nv, Pv, bv, 2 * nb, to_dev(z, torch.float64),
+                                       to_dev(nz, torch.float64), to_dev(u, torch.float64), precision="fp64",
+                                       gtol_rel=1e-12, max_iter=20000, leak_split=nb)
+    assert len(stats) == 1 + J + (nb + 1) * nfd
+    assert all(s["status"] == "WF_OK" for s in stats)
+    ref = O.bandpower_sims(d, inp.mask, inp.Ninv, inp.P, bands, 2 * nb, z, nz, u, gtol_rel=1e-12,
+                           max_iter=20000, leak_split=nb)
+    F = np.asarray(res["fisher"])
+    assert not F[:nb, nb:].any() and not F[nb:, :nb].any() and F[2, 3] == 0.0 and F[3, 2] == 0.0
+    for k in ("E", "b", "F", "theta_hat"):
+        kk = {"b": "bias", "F": "fisher"}.get(k, k)
+        a, b = np.asarray(res[kk]), np.asarray(ref[k])
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(b).max(), (k, a, b)
+
+
+def test_leakage_bias_with_device_draws_and_sampled_e_bands():
+    """Device-drawn fields (the joint B maps draw band L's row), Fisher maps for
+    E bands 0 and 2 only, column 1 interpolated inside the E block."""
+    from oracle import philox as PH
+    n, nb, J, nfd, seed = 16, 3, 4, 2, 12
+    inp = synth.shear_eb(n, seed=7)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb, C=2)
+    nbt, fdb = 2 * nb, [0, 2]
+    args = _dev(inp, d, inp.P, bands)
+    res, stats = wf.bandpower_estimate(*args, nbt, None, None, None, n_sim=J, n_fd=nfd, precision="fp64",
+                                       gtol_rel=1e-12, max_iter=20000, seed=seed, fd_bands=fdb, leak_split=nb)
+    assert len(stats) == 1 + J + (len(fdb) + 1) * nfd
+    npix = 2 * n * n
+    w = inp.mask[None] * inp.Ninv
+    sig = np.where(w > 0, 1.0 / np.sqrt(np.where(w > 0, w, 1.0)), 0.0)
+    z = PH.normals(seed, PH.STREAM_Z, J * npix).reshape(J, 2, n, n)
+    nz = PH.normals(seed, PH.STREAM_NOISE, J * npix).reshape(J, 2, n, n) * sig
+    rows = fdb + [nb]  # the joint B row draws as band L = nb
+    u = np.zeros((len(rows), nfd, 2, n, n))
+    for k, lb in enumerate(rows):
+        for j in range(nfd):
+            u[k, j] = PH.normals(seed, PH.STREAM_U, npix, offset=(j * nbt + lb) * npix).reshape(2, n, n)
+    ref = O.bandpower_sims(d, inp.mask, inp.Ninv, inp.P, bands, nbt, z, nz, u, gtol_rel=1e-12, max_iter=20000,
+                           fd_bands=fdb, leak_split=nb)
+    F = np.asarray(res["fisher"])
+    assert F[0, 1] != 0.0 and not F[:nb, nb:].any()
+    for k in ("E", "b", "F", "theta_hat"):
+        kk = {"b": "bias", "F": "fisher"}.get(k, k)
+        a, b = np.asarray(res[kk]), np.asarray(ref[k])
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(b).max(), (k, a, b)
+
+
+def test_leakage_bias_arguments_checked():
+    n, nb = 16, 2
+    inp = synth.shear_eb(n, seed=8)
+    bands = synth.log_bands(n, nb, C=2)
+    args = _dev(inp, inp.z, inp.P, bands)
+    kw = dict(n_sim=2, n_fd=1, precision="fp64", max_iter=5)
+    for bad in (dict(leak_split=2 * nb), dict(leak_split=-1), dict(leak_split=nb, fd_bands=[0, nb]),
+                dict(leak_split=1, trunc=(2, 0))):
+        with pytest.raises(wf.WfError, match="EINVAL"):
+            wf.bandpower_estimate(*args, 2 * nb, None, None, None, **kw, **bad)
+    one = synth.density_small(n, seed=2)
+    b1 = synth.log_bands(n, 3)
+    with pytest.raises(wf.WfError, match="EINVAL"):  # one channel: no E/B split
+        wf.bandpower_estimate(*_dev(one, one.z, one.P, b1), 3, None, None, None, leak_split=1, **kw)
+    with pytest.raises(ValueError, match="Fisher rows"):
+        z = torch.zeros((2, 2, n, n), dtype=torch.float64, device="cuda")
+        u = torch.zeros((2 * nb, 1, 2, n, n), dtype=torch.float64, device="cuda")
+        wf.bandpower_estimate(*args, 2 * nb, z, z, u, leak_split=nb, precision="fp64", max_iter=5)
