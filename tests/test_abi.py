@@ -48,9 +48,13 @@ def test_null_arguments_are_rejected_without_touching_the_device():
     assert L.wf_eval(None, None, None, None, None) == 1
 
 
-def test_wf_opts_layout_matches_the_header():
-    """Compile a tiny C program against include/wf.h and compare the field
-    offsets of wf_opts with the binding's."""
+@pytest.mark.parametrize("cname,pyname", [("wf_opts", "WfOpts"), ("wf_map", "WfMap"),
+                                           ("wf_solve_stats", "WfSolveStats"),
+                                           ("wf_bandpower_in", "WfBandpowerIn"),
+                                           ("wf_bandpower_out", "WfBandpowerOut")])
+def test_struct_layouts_match_the_header(cname, pyname):
+    """Compile a tiny C program against include/wf.h and compare the size and
+    field offsets of each struct the binding mirrors with the binding's."""
     import shutil
     import subprocess
     import tempfile
@@ -58,11 +62,12 @@ def test_wf_opts_layout_matches_the_header():
     if cc is None:
         pytest.skip("no C compiler")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    fields = [f[0] for f in wf.WfOpts._fields_]
+    cls = getattr(wf, pyname)
+    fields = [f[0] for f in cls._fields_]
     src = "#include <stdio.h>\n#include <stddef.h>\n#include \"wf.h\"\nint main(void){\n"
-    src += 'printf("%zu\\n", sizeof(wf_opts));\n'
+    src += f'printf("%zu\\n", sizeof({cname}));\n'
     for f in fields:
-        src += f'printf("%zu\\n", offsetof(wf_opts, {f}));\n'
+        src += f'printf("%zu\\n", offsetof({cname}, {f}));\n'
     src += "return 0;}\n"
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
@@ -70,8 +75,8 @@ def test_wf_opts_layout_matches_the_header():
         open(c, "w").write(src)
         subprocess.check_call([cc, "-I", os.path.join(root, "include"), "-I", "/usr/local/cuda/include", c, "-o", exe])
         out = [int(x) for x in subprocess.check_output([exe]).split()]
-    assert out[0] == ctypes.sizeof(wf.WfOpts)
-    assert out[1:] == [getattr(wf.WfOpts, f).offset for f in fields]
+    assert out[0] == ctypes.sizeof(cls)
+    assert out[1:] == [getattr(cls, f).offset for f in fields]
 
 
 def test_band_table_from_edges_matches_brute_force():
