@@ -79,3 +79,11 @@ def test_two_rank_reduction_equals_single_process():
     for rank in (0, 1):
         for k in ref:
             assert np.allclose(out[rank][k], ref[k], rtol=1e-12, atol=1e-14), (rank, k)
+
+
+@pytest.mark.parametrize("opt", [dict(fd_bands=[0, 2]), dict(leak_split=2)])
+def test_rank_estimate_rejects_forms_the_reduction_does_not_cover(opt):
+    """The reduction sums per-band Fisher maps of every band, so sampled
+    Fisher columns and the leakage-bias form are refused before any work."""
+    with pytest.raises(ValueError):
+        D.estimate_on_rank(None, None, None, None, None, 4, 2, 1, 2, 0, 0, **opt)
