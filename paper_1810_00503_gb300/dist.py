@@ -8,6 +8,9 @@ eq. blmv, fisher, eq:wfmv):
     F_ll'  = sum_j (E_l(d_l'j) - E_l(d_j)) / J_fd / Theta_fid,l'
     cov_E  = (sum_j E_j E_j^T - J b b^T) / (J - 1)
     Theta  = Theta_fid + F^-1 (E - b)
+With the leakage-bias form of App. C (leak_split = L: E bands 0..L-1 with
+per-band Fisher maps, one joint map of the B bands per Fisher simulation) the
+Fisher sums have L + 1 rows, and F keeps the EE block and the B diagonal only.
 No data path crosses GPUs; only these sums do.
 """
 from __future__ import annotations
@@ -33,27 +36,52 @@ def assignment(n_sim: int, n_fd: int, world: int, rank: int):
     return sims, (fd_lo, fd_hi)
 
 
-def local_sums(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int) -> np.ndarray:
+def fisher_rows(n_bands: int, leak_split: int = 0) -> int:
+    """Fisher-map rows of a rank's run: one per band, or the E bands plus the
+    joint B row of the leakage-bias form."""
+    return leak_split + 1 if leak_split > 0 else n_bands
+
+
+def local_sums(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int, leak_split: int = 0) -> np.ndarray:
     """Partial sums of one rank from its per-map band energies, rows ordered as
-    bandpower_estimate writes them: data, n_sim simulations, then n_bands x n_fd
-    Fisher maps (the j-th reusing simulation j).  Returns one FP64 vector:
-    [J, J_fd, sum E_j (nb), sum E_j E_j^T (nb^2), sum_j (E(d_l'j) - E(d_j)) (nb^2, [l][l'])]."""
+    bandpower_estimate writes them: data, n_sim simulations, then n_R x n_fd
+    Fisher maps (n_R = fisher_rows; the j-th reusing simulation j).  Returns one
+    FP64 vector: [J, J_fd, sum E_j (nb), sum E_j E_j^T (nb^2),
+    sum_j (E(d_kj) - E(d_j)) (n_R x nb, [k][l])]."""
     nb = n_bands
+    nR = fisher_rows(nb, leak_split)
     Es = E_maps[1:1 + n_sim]
-    Ef = E_maps[1 + n_sim:].reshape(nb, n_fd, nb)  # [l'][j][l]
-    diff = (Ef - Es[None, :n_fd, :]).sum(axis=1)      # [l'][l]
-    return np.concatenate([[float(n_sim), float(n_fd)], Es.sum(axis=0), (Es.T @ Es).ravel(), diff.T.ravel()])
+    Ef = E_maps[1 + n_sim:].reshape(nR, n_fd, nb)  # [k][j][l]
+    diff = (Ef - Es[None, :n_fd, :]).sum(axis=1)      # [k][l]
+    return np.concatenate([[float(n_sim), float(n_fd)], Es.sum(axis=0), (Es.T @ Es).ravel(), diff.ravel()])
 
 
-def combine(total: np.ndarray, E_data: np.ndarray, theta_fid: np.ndarray) -> dict:
-    """Band-power estimate from the all-reduced sums of `local_sums`."""
+def combine(total: np.ndarray, E_data: np.ndarray, theta_fid: np.ndarray, leak_split: int = 0,
+            trunc=(0, 0)) -> dict:
+    """Band-power estimate from the all-reduced sums of `local_sums`.  Fisher
+    terms as bandpower_estimate forms them: column l' from Fisher row l' (or,
+    with leak_split = L, the E columns from rows 0..L-1 restricted to the E
+    rows and each B band's diagonal from the joint row L); then trunc = (n, w)
+    zeroes F[l][l'] for l, l' < n with |l - l'| > w."""
     nb = theta_fid.size
+    L = int(leak_split)
     J, Jfd = total[0], total[1]
     S1 = total[2:2 + nb]
     S2 = total[2 + nb:2 + nb + nb * nb].reshape(nb, nb)
-    D = total[2 + nb + nb * nb:].reshape(nb, nb)
+    D = total[2 + nb + nb * nb:].reshape(fisher_rows(nb, L), nb)  # [k][l]
     b = S1 / J
-    F = D / Jfd / theta_fid[None, :]
+    if L > 0:
+        F = np.zeros((nb, nb))
+        F[:L, :L] = D[:L, :L].T / Jfd / theta_fid[None, :L]
+        for l in range(L, nb):
+            F[l, l] = D[L, l] / Jfd / theta_fid[l]
+    else:
+        F = D.T / Jfd / theta_fid[None, :]
+    n_t, w = int(trunc[0]), int(trunc[1])
+    for l in range(min(n_t, nb)):
+        for lp in range(min(n_t, nb)):
+            if abs(l - lp) > w:
+                F[l, lp] = 0.0
     covE = (S2 - J * np.outer(b, b)) / (J - 1)
     cov = np.linalg.inv(F)
     return dict(bias=b, fisher=F, cov=cov, cov_E=covE, theta_hat=theta_fid + cov @ (E_data - b),
@@ -61,18 +89,18 @@ def combine(total: np.ndarray, E_data: np.ndarray, theta_fid: np.ndarray) -> dic
 
 
 def reduce_bandpower(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int, theta_fid: np.ndarray,
-                     group=None) -> dict:
+                     group=None, leak_split: int = 0, trunc=(0, 0)) -> dict:
     """All-reduce the rank's partial sums (torch.distributed, any backend) and
     combine them.  E_maps: this rank's per-map energies; the data map's row 0
     is taken from rank 0."""
     import torch
     import torch.distributed as dist
-    part = torch.as_tensor(local_sums(E_maps, n_sim, n_bands, n_fd), dtype=torch.float64)
+    part = torch.as_tensor(local_sums(E_maps, n_sim, n_bands, n_fd, leak_split), dtype=torch.float64)
     e0 = torch.as_tensor(E_maps[0], dtype=torch.float64).clone()
     if dist.is_available() and dist.is_initialized():
         dist.all_reduce(part, group=group)
         dist.broadcast(e0, src=0, group=group)
-    return combine(part.numpy(), e0.numpy(), np.asarray(theta_fid, dtype=np.float64))
+    return combine(part.numpy(), e0.numpy(), np.asarray(theta_fid, dtype=np.float64), leak_split, trunc)
 
 
 def estimate_on_rank(d, mask, Ninv, P, band, n_bands, n_sim, n_fd, world, rank, seed, group=None, **opts):
@@ -85,10 +113,9 @@ def estimate_on_rank(d, mask, Ninv, P, band, n_bands, n_sim, n_fd, world, rank, 
     from . import wf
     if opts.get("fd_bands") is not None:
         raise ValueError("estimate_on_rank: every band needs Fisher maps (fd_bands is not supported)")
-    if opts.get("leak_split"):
-        raise ValueError("estimate_on_rank: the leakage-bias form (leak_split) is not supported")
     sims, (fd_lo, fd_hi) = assignment(n_sim, n_fd, world, rank)
     res, stats = wf.bandpower_estimate(d, mask, Ninv, P, band, n_bands, None, None, None, n_sim=len(sims),
                                        n_fd=fd_hi - fd_lo, sim_index=sims, seed=seed, **opts)
-    est = reduce_bandpower(res["E_maps"], len(sims), n_bands, fd_hi - fd_lo, res["theta_fid"], group)
+    est = reduce_bandpower(res["E_maps"], len(sims), n_bands, fd_hi - fd_lo, res["theta_fid"], group,
+                           opts.get("leak_split", 0), opts.get("trunc", (0, 0)))
     return est, stats

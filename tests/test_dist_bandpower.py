@@ -11,27 +11,38 @@ import torch.multiprocessing as mp
 from paper_1810_00503_gb300 import dist as D
 
 
-def _reference(E_all, n_sim, nb, n_fd, theta):
+def _reference(E_all, n_sim, nb, n_fd, theta, leak=0, trunc=(0, 0)):
+    nR = leak + 1 if leak else nb
     Es = E_all[1:1 + n_sim]
-    Ef = E_all[1 + n_sim:].reshape(nb, n_fd, nb)
+    Ef = E_all[1 + n_sim:].reshape(nR, n_fd, nb)
     b = Es.mean(axis=0)
     F = np.zeros((nb, nb))
-    for lp in range(nb):
-        F[:, lp] = (Ef[lp] - Es[:n_fd]).mean(axis=0) / theta[lp]
+    for k in range(nR):
+        resp = (Ef[k] - Es[:n_fd]).mean(axis=0)  # every band's response to Fisher row k
+        if not leak:
+            F[:, k] = resp / theta[k]
+        elif k < leak:                            # E column, E rows only
+            F[:leak, k] = resp[:leak] / theta[k]
+        else:                                     # joint B row: the B diagonal
+            F[leak:, leak:] = np.diag(resp[leak:] / theta[leak:])
+    for l in range(trunc[0]):
+        for lp in range(trunc[0]):
+            if abs(l - lp) > trunc[1]:
+                F[l, lp] = 0.0
     covE = np.cov(Es.T, ddof=1)
     return dict(bias=b, fisher=F, cov_E=covE, theta_hat=theta + np.linalg.solve(F, E_all[0] - b))
 
 
-def _worker(rank, world, port, n_sim, nb, n_fd, E_all, theta, out):
+def _worker(rank, world, port, n_sim, nb, n_fd, E_all, theta, out, leak=0, trunc=(0, 0)):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     sims, (fd_lo, fd_hi) = D.assignment(n_sim, n_fd, world, rank)
-    Ef = E_all[1 + n_sim:].reshape(nb, n_fd, nb)[:, fd_lo:fd_hi]
+    Ef = E_all[1 + n_sim:].reshape(D.fisher_rows(nb, leak), n_fd, nb)[:, fd_lo:fd_hi]
     Es_local = E_all[[1 + j for j in sims]]
     rows = np.concatenate([E_all[:1], Es_local, Ef.reshape(-1, nb)])
-    res = D.reduce_bandpower(rows, len(sims), nb, fd_hi - fd_lo, theta)
+    res = D.reduce_bandpower(rows, len(sims), nb, fd_hi - fd_lo, theta, leak_split=leak, trunc=trunc)
     out[rank] = {k: res[k] for k in ("bias", "fisher", "cov_E", "theta_hat")}
     dist.destroy_process_group()
 
@@ -62,28 +73,33 @@ def test_shard_covers_everything_once():
             assert idx == list(range(n))
 
 
-def test_two_rank_reduction_equals_single_process():
+@pytest.mark.parametrize("leak,trunc", [(0, (0, 0)), (2, (0, 0)), (0, (3, 1)), (3, (3, 0))])
+def test_two_rank_reduction_equals_single_process(leak, trunc):
+    """Plain, leakage-bias (E bands 0..leak-1, joint B row last) and truncated
+    forms: two gloo ranks give the single-process estimate."""
     rng = np.random.default_rng(3)
-    n_sim, nb, n_fd = 10, 4, 6
-    E_all = rng.uniform(0.5, 2.0, size=(1 + n_sim + nb * n_fd, nb))
+    n_sim, nb, n_fd = 10, 5, 6
+    nR = D.fisher_rows(nb, leak)
+    E_all = rng.uniform(0.5, 2.0, size=(1 + n_sim + nR * n_fd, nb))
     theta = rng.uniform(0.5, 1.5, size=nb)
-    ref = _reference(E_all, n_sim, nb, n_fd, theta)
-    single = D.combine(D.local_sums(E_all, n_sim, nb, n_fd), E_all[0], theta)
+    ref = _reference(E_all, n_sim, nb, n_fd, theta, leak, trunc)
+    if leak:
+        assert not ref["fisher"][:leak, leak:].any() and not ref["fisher"][leak:, :leak].any()
+    single = D.combine(D.local_sums(E_all, n_sim, nb, n_fd, leak), E_all[0], theta, leak, trunc)
     for k in ref:
         assert np.allclose(single[k], ref[k], rtol=1e-12)
     mgr = mp.Manager()
     out = mgr.dict()
     port = _free_port()
-    mp.start_processes(_worker, args=(2, port, n_sim, nb, n_fd, E_all, theta, out), nprocs=2,
+    mp.start_processes(_worker, args=(2, port, n_sim, nb, n_fd, E_all, theta, out, leak, trunc), nprocs=2,
                        start_method="spawn", join=True)
     for rank in (0, 1):
         for k in ref:
             assert np.allclose(out[rank][k], ref[k], rtol=1e-12, atol=1e-14), (rank, k)
 
 
-@pytest.mark.parametrize("opt", [dict(fd_bands=[0, 2]), dict(leak_split=2)])
-def test_rank_estimate_rejects_forms_the_reduction_does_not_cover(opt):
-    """The reduction sums per-band Fisher maps of every band, so sampled
-    Fisher columns and the leakage-bias form are refused before any work."""
+def test_rank_estimate_rejects_sampled_fisher_columns():
+    """The reduction needs the Fisher maps of every Fisher row, so sampled
+    Fisher columns are refused before any work."""
     with pytest.raises(ValueError):
-        D.estimate_on_rank(None, None, None, None, None, 4, 2, 1, 2, 0, 0, **opt)
+        D.estimate_on_rank(None, None, None, None, None, 4, 2, 1, 2, 0, 0, fd_bands=[0, 2])
