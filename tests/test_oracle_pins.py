@@ -431,3 +431,63 @@ def test_leakage_bias_blocks_under_a_mask():
     leak2 = O.bandpower_sims(d, mask, Ninv, P, bands, 2 * nb, z, nz, u2, leak_split=nb, **kw)
     assert np.array_equal(leak2["theta_hat"][:nb], leak["theta_hat"][:nb])
     assert not np.allclose(leak2["theta_hat"][nb:], leak["theta_hat"][nb:], rtol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Textbook L-BFGS pieces (Nocedal & Wright): two-loop recursion against the
+# dense inverse-Hessian update, and the strong-Wolfe conditions of the search
+# ---------------------------------------------------------------------------
+
+
+def test_two_loop_equals_dense_bfgs_inverse_update():
+    """-two_loop(g) = H g with H built densely by the BFGS inverse update
+    H <- V^T H V + rho s s^T, V = I - rho y s^T (N&W eq. 6.17), from
+    H0 = gamma I, gamma = s^T y / y^T y of the newest pair (N&W eq. 7.20);
+    and H satisfies the secant condition H y = s for the newest pair."""
+    rng = np.random.default_rng(12)
+    dim, m = 9, 4
+    A = rng.standard_normal((dim, dim))
+    Hs = A @ A.T + dim * np.eye(dim)            # SPD, so s^T y > 0
+    S = [rng.standard_normal(dim) for _ in range(m)]
+    Y = [Hs @ s for s in S]
+    g = rng.standard_normal(dim)
+    gamma = S[-1] @ Y[-1] / (Y[-1] @ Y[-1])
+    H = gamma * np.eye(dim)
+    for s, y in zip(S, Y):
+        rho = 1.0 / (y @ s)
+        V = np.eye(dim) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    p = O._two_loop(g, S, Y)
+    assert np.allclose(-p, H @ g, rtol=1e-12, atol=1e-12 * np.abs(H @ g).max())
+    assert np.allclose(H @ Y[-1], S[-1], rtol=1e-10)
+    assert np.allclose(O._two_loop(g, [], []), -g)    # no pairs: steepest descent
+
+
+@pytest.mark.parametrize("case", ["accept_unit", "expand", "zoom"])
+def test_line_search_returns_a_strong_wolfe_step(case):
+    """On phi(a) = f(x + a p) for a quadratic f, the returned step satisfies
+    f(a) <= f(0) + c1 a phi'(0) and |phi'(a)| <= c2 |phi'(0)| (N&W eq. 3.7);
+    a unit step that already does is returned unchanged (Alg. 3.5 tries 1 first)."""
+    c1, c2 = 1e-4, {"accept_unit": 0.9, "expand": 0.1, "zoom": 0.1}[case]
+    a_star = {"accept_unit": 1.2, "expand": 9.0, "zoom": 0.3}[case]  # minimiser along p
+    dim = 5
+    rng = np.random.default_rng(4)
+    Q = np.diag(rng.uniform(1.0, 3.0, dim))
+    x = rng.standard_normal(dim)
+    g0 = Q @ x
+    p = -g0 * (1.0 / a_star) * (g0 @ g0) / (g0 @ Q @ g0)  # exact minimiser at a = a_star
+
+    def fg(v):
+        return 0.5 * v @ Q @ v, Q @ v
+
+    f0 = fg(x)[0]
+    a, f, g = O._line_search(fg, x, f0, g0, p, c1, c2)
+    d0 = g0 @ p
+    fa, ga = fg(x + a * p)
+    assert fa <= f0 + c1 * a * d0 + 1e-14 * abs(f0)
+    assert abs(ga @ p) <= c2 * abs(d0) * (1 + 1e-12)
+    assert np.isclose(f, fa, rtol=1e-14)
+    if case == "accept_unit":
+        assert a == 1.0
+    else:
+        assert abs(a - a_star) <= 0.1 * a_star         # c2 = 0.1 pins the step near the minimiser
