@@ -65,3 +65,38 @@ def test_autograd_function_matches_finite_differences():
             fd = (fp - fm) / (2 * h)
             an = float((gs.real * dirs.real + gs.imag * dirs.imag).sum() + (gq * dq).sum())
             assert abs(fd - an) <= 1e-6 * abs(f.item()) / 1e3 + 1e-6 * abs(an), (k, fd, an)
+
+
+def test_autograd_eb_512_on_1000_random_directions():
+    """Joint E/B shear at 512^2: the adjoint stage behind the autograd Function
+    against central differences along 1000 random directions in (s, q), the s
+    part Hermitian-consistent (spectra of real fields).  chi^2 is quadratic in
+    s, so along s the differences are exact up to rounding; along q they carry
+    an O(h^2) term."""
+    from paper_1810_00503_gb300.autograd import chi2 as wf_chi2
+    n, nb = 512, 4
+    inp = synth.shear_eb(n, seed=21)
+    prob, _ = make_problem([inp], "fp64")
+    bands = synth.log_bands(n, nb, C=2)
+    band_t = to_dev(bands[..., : n // 2 + 1], torch.int16)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    s0 = torch.fft.rfft2(torch.randn(1, 2, n, n, generator=g, device="cuda", dtype=torch.float64), norm="ortho")
+    s = s0.clone().requires_grad_(True)
+    q = (0.5 + torch.rand(2 * nb, generator=g, device="cuda", dtype=torch.float64)).requires_grad_(True)
+    f = wf_chi2(s, q, prob, band_t).sum()
+    f.backward()
+    gs, gq = s.grad.clone(), q.grad.clone()
+    h, worst = 1e-4, 0.0
+    with torch.no_grad():
+        for k in range(1000):
+            dirs = torch.fft.rfft2(torch.randn(1, 2, n, n, generator=g, device="cuda", dtype=torch.float64),
+                                   norm="ortho")
+            dq = torch.randn(2 * nb, generator=g, device="cuda", dtype=torch.float64)
+            fp = wf_chi2(s0 + h * dirs, q + h * dq, prob, band_t).sum().item()
+            fm = wf_chi2(s0 - h * dirs, q - h * dq, prob, band_t).sum().item()
+            fd = (fp - fm) / (2 * h)
+            an = float((gs.real * dirs.real + gs.imag * dirs.imag).sum() + (gq * dq).sum())
+            err = abs(fd - an) / (1e-6 * abs(f.item()) / 1e3 + 1e-6 * abs(an))
+            worst = max(worst, err)
+    assert worst <= 1.0, worst
