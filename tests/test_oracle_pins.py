@@ -491,3 +491,49 @@ def test_line_search_returns_a_strong_wolfe_step(case):
         assert a == 1.0
     else:
         assert abs(a - a_star) <= 0.1 * a_star         # c2 = 0.1 pins the step near the minimiser
+
+
+@pytest.mark.parametrize("C", [1, 2])
+def test_envelope_identity_at_the_map(C):
+    """At the MAP the gradient vanishes, z = A^T W r, so the band derivative
+    d chi^2 / d log q_l = -r^T W A Pi_l z reduces to -z^T Pi_l z =
+    -2 Theta_fid,l E_l(z_MAP): the adjoint band derivative and the band energy
+    of eq. el agree at the solution, up to O(||g||), and not elsewhere."""
+    n, nb = 16, 3
+    inp = synth.density_small(n, seed=17) if C == 1 else synth.shear_eb(n, seed=17)
+    W = inp.mask[None] * inp.Ninv
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(n, nb, C=C)
+    nbt = nb * C
+    z, _ = O.map_solve(d, W, inp.P, m=10, gtol_rel=1e-13, max_iter=20000)
+    theta = O.theta_fid(inp.P, bands, nbt)
+    lhs = O.chi2_dlogq(z, d, W, inp.P, bands, nbt)
+    rhs = -2.0 * theta * O.band_E(z, bands, theta, nbt)
+    assert np.allclose(lhs, rhs, rtol=1e-8, atol=1e-10 * np.abs(rhs).max()), (lhs, rhs)
+    z2 = z + 0.1 * np.random.default_rng(1).standard_normal(z.shape)
+    assert not np.allclose(O.chi2_dlogq(z2, d, W, inp.P, bands, nbt),
+                           -2.0 * theta * O.band_E(z2, bands, theta, nbt), rtol=1e-3)
+
+
+def test_chi2_minimum_is_chi_square_distributed():
+    """For data drawn from the model, d = M (A z + n) with z ~ N(0, I) and
+    n ~ N(0, N), the observed pixels have covariance C = A_o A_o^T + N_o, so
+    chi^2_min = d_o^T C^-1 d_o is chi-square with N_obs degrees of freedom:
+    mean N_obs, variance 2 N_obs (checked within 4 and 5 standard errors).  A
+    white signal spectrum at the mean noise level gives signal and noise about
+    half of the degrees of freedom each, so a mis-scaled signal or noise term
+    moves the mean by many standard errors."""
+    n, K = 16, 300
+    inp = synth.density_small(n, seed=23, masked_frac=0.25)
+    obs = inp.mask == 1
+    P = np.full((1, n, n), float(np.mean(1.0 / inp.Ninv[0][obs])))
+    P[0, 0, 0] = 0.0
+    A = O.dense_operator(P)
+    nobs = int(obs.sum())
+    rng = np.random.default_rng(7)
+    sig = np.where(inp.Ninv > 0, 1.0 / np.sqrt(np.where(inp.Ninv > 0, inp.Ninv, 1.0)), 0.0)
+    vals = np.array([O.chi2_min_dense(O.synthesize_data(rng.standard_normal((1, n, n)),
+                                                        rng.standard_normal((1, n, n)) * sig, inp.mask, P),
+                                      inp.mask, inp.Ninv, P, A=A) for _ in range(K)])
+    assert abs(vals.mean() - nobs) <= 4.0 * np.sqrt(2.0 * nobs / K), (vals.mean(), nobs)
+    assert abs(vals.var(ddof=1) - 2.0 * nobs) <= 5.0 * np.sqrt(2.0 / K) * 2.0 * nobs, (vals.var(ddof=1), nobs)
