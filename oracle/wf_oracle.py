@@ -31,7 +31,8 @@ S/(S+N), Woodbury agreement of the two dense Wiener-filter forms, exact central
 differences of a quadratic, the lambda_min >= 1 certificate, analytic band
 terms without a mask, the Fisher identity Cov(E) = F, the two-loop recursion
 against the dense BFGS inverse update, strong-Wolfe steps, the envelope identity
-d chi^2 / d log q_l = -2 Theta_fid,l E_l at the MAP, chi^2_min ~ chi-square(N_obs), and the leakage-bias form
+d chi^2 / d log q_l = -2 Theta_fid,l E_l at the MAP, chi^2_min ~ chi-square(N_obs), the
+unbiasedness of Theta_hat (exact b and F) for a rescaled true spectrum, and the leakage-bias form
 of App. C against the full Fisher run where E and B do not mix.
 Parity unpinned: iteration counts and chi^2-versus-iteration curves, because the
 paper gives them only as figures.

@@ -537,3 +537,30 @@ def test_chi2_minimum_is_chi_square_distributed():
                                       inp.mask, inp.Ninv, P, A=A) for _ in range(K)])
     assert abs(vals.mean() - nobs) <= 4.0 * np.sqrt(2.0 * nobs / K), (vals.mean(), nobs)
     assert abs(vals.var(ddof=1) - 2.0 * nobs) <= 5.0 * np.sqrt(2.0 / K) * 2.0 * nobs, (vals.var(ddof=1), nobs)
+
+
+def test_estimator_is_unbiased_for_a_rescaled_true_spectrum():
+    """With the exact b and F, <E_l> over data drawn with any band powers is
+    b_l + sum_l' F_ll' (Theta_true,l' - Theta_fid,l'), because E is quadratic in
+    the data and C is linear in the band powers; so Theta_hat = Theta_fid +
+    F^-1 (E - b) (eq. eq:wfmv) averages to Theta_true.  Data drawn with each
+    band of the fiducial rescaled; mean of Theta_hat within 5 standard errors."""
+    n, nb, K = 8, 3, 4000
+    inp = synth.density_small(n, seed=29, masked_frac=0.25)
+    bands = synth.log_bands(n, nb)
+    q = np.array([1.6, 0.6, 1.3])
+    P_true = inp.P * np.where(bands >= 0, q[np.maximum(bands, 0)], 1.0)
+    b, F, theta = O.exact_band_terms(inp.mask, inp.Ninv, inp.P, bands, nb)
+    W = inp.mask[None] * inp.Ninv
+    A = O.dense_operator(inp.P)
+    sig = np.where(inp.Ninv > 0, 1.0 / np.sqrt(np.where(inp.Ninv > 0, inp.Ninv, 1.0)), 0.0)
+    rng = np.random.default_rng(31)
+    est = np.empty((K, nb))
+    for k in range(K):
+        d = O.synthesize_data(rng.standard_normal((1, n, n)), rng.standard_normal((1, n, n)) * sig, inp.mask,
+                              P_true)
+        z = O.dense_wf_whitened(d, W, inp.P, A=A)
+        est[k] = theta + np.linalg.solve(F, O.band_E(z, bands, theta, nb) - b)
+    se = est.std(axis=0, ddof=1) / np.sqrt(K)
+    assert np.all(np.abs(est.mean(axis=0) - theta * q) <= 5.0 * se), (est.mean(axis=0), theta * q, se)
+    assert np.any(np.abs(est.mean(axis=0) - theta) > 5.0 * se)     # distinguishable from the fiducial
