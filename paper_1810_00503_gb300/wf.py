@@ -136,6 +136,22 @@ def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
 
+def _need(t, name, shape=None, dtype=None):
+    """Check a tensor before its data pointer goes to the library, which reads
+    exactly the documented number of elements of the documented type from
+    device memory: a contiguous CUDA tensor of that shape and dtype."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, the call needs {tuple(shape)}")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, the call needs {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
 def _stream(stream) -> int:
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
@@ -258,11 +274,23 @@ def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, str
                     opts, fd_bands=None, trunc=(0, 0), out_on_device=False, leak_split=0):
     """ctypes arguments shared by bandpower_estimate and bandpower_iterate."""
     import torch
+    _need(Ninv, "Ninv")
+    if Ninv.dim() != 3 or Ninv.dtype not in (torch.float32, torch.float64):
+        raise ValueError("Ninv must be a float32 or float64 (C, n, n) tensor")
     C, n, _ = Ninv.shape
+    ddt = Ninv.dtype
+    wdt = torch.float64 if precision == "fp64" else torch.float32
+    _need(d, "d", (C, n, n), ddt)
+    _need(mask, "mask", (n, n), torch.uint8)
+    _need(P, "P", (C, n, n // 2 + 1), ddt)
+    _need(band, "band", (C, n, n // 2 + 1), torch.int16)
     m = WfMap(d=_ptr(d), mask=_ptr(mask), Ninv=_ptr(Ninv), P=_ptr(P))
     nb = int(n_bands)
     J = int(z.shape[0]) if z is not None else int(n_sim)
     F = int(u.shape[1]) if u is not None else int(n_fd)
+    for name, t in (("z", z), ("noise", noise)):  # all-or-none of the fields is the library's check
+        if t is not None:
+            _need(t, name, (J, C, n, n), wdt)
     idx = None
     if sim_index is not None:
         idx = np.ascontiguousarray(sim_index, dtype=np.int64)
@@ -273,6 +301,8 @@ def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, str
     nR = ((L if L > 0 else nb) if fdb is None else int(fdb.size)) + (1 if L > 0 else 0)  # Fisher rows of u
     if u is not None and int(u.shape[0]) != nR:
         raise ValueError(f"u has {int(u.shape[0])} Fisher rows, the call needs {nR}")
+    if u is not None:
+        _need(u, "u", (nR, F, C, n, n), wdt)
     bi = WfBandpowerIn(n_bands=nb, n_sim=J, n_fd=F, leak_split=L,
                        band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u),
                        sim_index=None if idx is None else idx.ctypes.data,
@@ -327,9 +357,9 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
     cross terms; u then has the E rows and one more, the B fields.
     Returns (dict of numpy arrays, or float64 CUDA tensors with out_on_device,
     per-map stats)."""
-    handle = handle or default_handle()
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
                         opts, fd_bands, trunc, out_on_device, leak_split)
+    handle = handle or default_handle()
     status = lib().bandpower_estimate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
                                       ctypes.byref(a["bi"]), ctypes.byref(a["o"]), ctypes.byref(a["bo"]), a["st"])
     if status not in (0, 5):
@@ -345,9 +375,9 @@ def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_
     estimate, per-map stats of the last run, Theta_hat of every estimate
     (n_iter, n_bands), final fiducial P as a CUDA tensor like P)."""
     import torch
-    handle = handle or default_handle()
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
                         opts, fd_bands, trunc, out_on_device, leak_split)
+    handle = handle or default_handle()
     hist = np.zeros((int(n_iter), a["nb"]))
     P_out = torch.empty_like(P)
     status = lib().bandpower_iterate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
@@ -371,12 +401,19 @@ class Problem:
 
     def __init__(self, d, mask, Ninv, P, precision="fp64", lbfgs_m=10, handle=None, stream=None):
         import torch
-        self.handle = handle or default_handle()
+        _need(Ninv, "Ninv")
+        if Ninv.dim() != 4:
+            raise ValueError("Ninv must have shape (B, C, n, n)")
         B, C, n, _ = Ninv.shape
         self.B, self.C, self.n = B, C, n
         dtype = Ninv.dtype
         if dtype not in (torch.float32, torch.float64):
             raise TypeError("inputs must be float32 or float64")
+        if d is not None:
+            _need(d, "d", (B, C, n, n), dtype)
+        _need(mask, "mask", (B, n, n) if mask.dim() == 3 else (n, n), torch.uint8)
+        _need(P, "P", (B, C, n, n // 2 + 1) if P.dim() == 4 else (C, n, n // 2 + 1), dtype)
+        self.handle = handle or default_handle()
         self.precision = WF_FP64 if precision == "fp64" else WF_MIXED
         self.wdtype = torch.float64 if self.precision == WF_FP64 else torch.float32
         masks = mask if mask.dim() == 3 else mask.unsqueeze(0).expand(B, n, n)
@@ -419,7 +456,8 @@ class Problem:
 
     def _spec(self, t):
         import torch
-        if t.dtype != self._cplx() or tuple(t.shape) != self.spec_shape() or not t.is_contiguous():
+        if (not t.is_cuda or t.dtype != self._cplx() or tuple(t.shape) != self.spec_shape()
+                or not t.is_contiguous()):
             raise ValueError(f"spectrum must be contiguous {self._cplx()} of shape {self.spec_shape()}")
         return t
 
@@ -481,15 +519,16 @@ class Problem:
     def simulate(self, z, noise, out=None, stream=None):
         import torch
         for t in (z, noise):
-            if t.dtype != self.wdtype or tuple(t.shape) != self.pix_shape():
-                raise ValueError("z and noise must be working-type pixel maps")
+            if (not t.is_cuda or t.dtype != self.wdtype or tuple(t.shape) != self.pix_shape()
+                    or not t.is_contiguous()):
+                raise ValueError("z and noise must be contiguous working-type CUDA pixel maps")
         out = torch.empty_like(z) if out is None else out
         _check(lib().wf_simulate_data(self._p, _ptr(z), _ptr(noise), _ptr(out), _stream(stream)))
         return out
 
     def set_data(self, d, stream=None):
-        if d.dtype != self.wdtype or tuple(d.shape) != self.pix_shape():
-            raise ValueError("d must be a working-type pixel map batch")
+        if not d.is_cuda or d.dtype != self.wdtype or tuple(d.shape) != self.pix_shape() or not d.is_contiguous():
+            raise ValueError("d must be a contiguous working-type CUDA pixel map batch")
         _check(lib().wf_problem_set_data(self._p, _ptr(d), _stream(stream)))
 
     def band_energy(self, s, band, theta, out=None, stream=None):

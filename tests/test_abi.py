@@ -97,3 +97,19 @@ def test_band_table_from_edges_matches_brute_force():
         assert np.array_equal(got, want)
     with pytest.raises(wf.WfError, match="EINVAL"):
         wf.band_table(16, [2.0, 1.0])
+
+
+def test_binding_refuses_host_tensors_before_any_call():
+    """The binding hands raw data pointers to the library, which reads them as
+    device memory: host tensors are refused before a handle or a call is made
+    (no GPU is needed to see it)."""
+    torch = pytest.importorskip("torch")
+    n, f64 = 16, torch.float64
+    d = torch.zeros(1, 1, n, n, dtype=f64)
+    mask = torch.ones(n, n, dtype=torch.uint8)
+    P = torch.ones(1, n, n // 2 + 1, dtype=f64)
+    with pytest.raises(TypeError, match="CUDA"):
+        wf.Problem(d, mask, d + 1.0, P)
+    band = torch.zeros(1, n, n // 2 + 1, dtype=torch.int16)
+    with pytest.raises(TypeError, match="CUDA"):
+        wf.bandpower_estimate(d[0], mask, d[0] + 1.0, P, band, 2, None, None, None, n_sim=2, n_fd=1)
