@@ -440,7 +440,8 @@ def run_bandpower(args, dev, n_sim=100, n_bands=20, n_fd=1):
     d = one.simulate(torch.randn(1, 1, n, n, generator=g, device=dev),
                      torch.randn(1, 1, n, n, generator=g, device=dev) * sig)[0]
     one.close()
-    bands = torch.as_tensor(synth.log_bands(n, n_bands)[..., : n // 2 + 1], dtype=torch.int16, device=dev)
+    bands = torch.as_tensor(np.ascontiguousarray(synth.log_bands(n, n_bands)[..., : n // 2 + 1]), dtype=torch.int16,
+                            device=dev)
     z = torch.randn(n_sim, 1, n, n, generator=g, device=dev)
     nz = torch.randn(n_sim, 1, n, n, generator=g, device=dev) * sig
     u = torch.randn(n_bands, n_fd, 1, n, n, generator=g, device=dev)
@@ -481,7 +482,8 @@ def run_eb_bandpower(args, dev, n=512, n_bands=8, n_sim=20, n_fd=2):
                      torch.randn(1, 2, n, n, generator=g, device=dev) * sig)[0]
     one.close()
     nbt = 2 * n_bands
-    bands = torch.as_tensor(synth.log_bands(n, n_bands, C=2)[..., : n // 2 + 1], dtype=torch.int16, device=dev)
+    bands = torch.as_tensor(np.ascontiguousarray(synth.log_bands(n, n_bands, C=2)[..., : n // 2 + 1]),
+                            dtype=torch.int16, device=dev)
     z = torch.randn(n_sim, 2, n, n, generator=g, device=dev)
     nz = torch.randn(n_sim, 2, n, n, generator=g, device=dev) * sig
     uE = torch.randn(n_bands, n_fd, 2, n, n, generator=g, device=dev)
