@@ -113,3 +113,67 @@ def test_binding_refuses_host_tensors_before_any_call():
     band = torch.zeros(1, n, n // 2 + 1, dtype=torch.int16)
     with pytest.raises(TypeError, match="CUDA"):
         wf.bandpower_estimate(d[0], mask, d[0] + 1.0, P, band, 2, None, None, None, n_sim=2, n_fd=1)
+
+
+def _stand_ins():
+    """A non-null handle and non-null pointers for argument checks that return
+    before the library reads the handle, reads a buffer or calls CUDA: the
+    host buffer behind them is never touched on these paths."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    return buf, ctypes.c_void_p(ctypes.addressof(buf)), ctypes.addressof(buf)
+
+
+def test_problem_create_refuses_bad_arguments_before_device_work():
+    L = ensure_lib()
+    buf, h, addr = _stand_ins()
+    maps = (wf.WfMap * 2)()
+    for m in maps:
+        m.d = m.mask = m.Ninv = m.P = addr
+    out = ctypes.c_void_p(1)
+    good = dict(count=1, n=16, C=1, dtype=wf.WF_F32, prec=wf.WF_MIXED, m=10)
+    for bad in (dict(count=0), dict(n=12), dict(n=4), dict(n=2048), dict(C=3), dict(C=0), dict(dtype=2),
+                dict(prec=2), dict(m=0), dict(m=33)):
+        a = {**good, **bad}
+        st = L.wf_problem_create(h, maps, a["count"], a["n"], a["C"], a["dtype"], a["prec"], a["m"], None,
+                                 ctypes.byref(out))
+        assert st == 1 and out.value is None, (bad, st)
+    maps[1].Ninv = None
+    assert L.wf_problem_create(h, maps, 2, 16, 1, wf.WF_F32, wf.WF_MIXED, 10, None, ctypes.byref(out)) == 1
+    assert b"map 1" in L.wf_last_error()
+
+
+def test_bandpower_refuses_bad_arguments_before_device_work():
+    """The band-power calls' argument rules, the leakage-bias ones included,
+    checked through the C ABI on the host."""
+    import numpy as np
+    L = ensure_lib()
+    buf, h, addr = _stand_ins()
+    data = wf.WfMap(d=addr, mask=addr, Ninv=addr, P=addr)
+    outs = {k: np.zeros(64 * 64 * 4) for k in ("theta_fid", "E", "bias", "fisher", "cov", "theta_hat", "cov_E")}
+    bo = wf.WfBandpowerOut(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for k, v in outs.items()})
+    o = wf.WfOpts()
+    L.wf_opts_default(ctypes.byref(o))
+    fdb = (ctypes.c_int * 2)(0, 2)
+
+    def estimate(C=2, **kw):
+        f = dict(n_bands=4, n_sim=2, n_fd=1, leak_split=0, band=addr, z=None, noise=None, u=None,
+                 sim_index=None, fd_bands=None, n_fd_bands=0, trunc_bands=0, trunc_width=0, out_on_device=0)
+        f.update(kw)
+        bi = wf.WfBandpowerIn(**f)
+        return L.bandpower_estimate(h, ctypes.byref(data), 16, C, wf.WF_F32, wf.WF_MIXED, ctypes.byref(bi),
+                                    ctypes.byref(o), ctypes.byref(bo), None)
+
+    for C, kw, msg in [(2, dict(n_bands=0), b"n_bands"), (2, dict(n_bands=65), b"n_bands"),
+                       (2, dict(n_sim=0), b"n_sim"), (2, dict(n_fd=3), b"n_fd"), (2, dict(band=None), b"band"),
+                       (2, dict(z=addr), b"random fields"), (2, dict(trunc_bands=5), b"trunc"),
+                       (2, dict(leak_split=4), b"leak_split"), (2, dict(leak_split=-1), b"leak_split"),
+                       (1, dict(leak_split=2), b"leak_split"), (2, dict(leak_split=1, trunc_bands=2), b"trunc_bands"),
+                       (2, dict(leak_split=2, fd_bands=ctypes.addressof(fdb), n_fd_bands=2), b"fd_bands"),
+                       (2, dict(out_on_device=2), b"out_on_device")]:
+        assert estimate(C, **kw) == 1, (C, kw)
+        assert msg in L.wf_last_error(), (kw, L.wf_last_error())
+    bi = wf.WfBandpowerIn(n_bands=4, n_sim=2, n_fd=1, band=addr)
+    for n_iter, qmin, qmax, msg in [(0, 0.1, 10.0, b"n_iter"), (2, 1.5, 10.0, b"q_min"), (2, 0.1, 0.5, b"q_min")]:
+        st = L.bandpower_iterate(h, ctypes.byref(data), 16, 1, wf.WF_F32, wf.WF_MIXED, ctypes.byref(bi),
+                                 ctypes.byref(o), n_iter, qmin, qmax, None, None, ctypes.byref(bo), None)
+        assert st == 1 and msg in L.wf_last_error(), (n_iter, qmin, qmax, L.wf_last_error())
