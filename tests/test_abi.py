@@ -177,3 +177,14 @@ def test_bandpower_refuses_bad_arguments_before_device_work():
         st = L.bandpower_iterate(h, ctypes.byref(data), 16, 1, wf.WF_F32, wf.WF_MIXED, ctypes.byref(bi),
                                  ctypes.byref(o), n_iter, qmin, qmax, None, None, ctypes.byref(bo), None)
         assert st == 1 and msg in L.wf_last_error(), (n_iter, qmin, qmax, L.wf_last_error())
+
+
+def test_normal_draw_refuses_bad_arguments_on_the_host():
+    L = ensure_lib()
+    buf, h, addr = _stand_ins()
+    assert L.wf_normal_draw(1, 0, 0, 10, wf.WF_F32, None, None) == 1
+    assert b"null output" in L.wf_last_error()
+    assert L.wf_normal_draw(1, 0, 0, 10, 7, addr, None) == 1
+    assert b"dtype" in L.wf_last_error()
+    assert L.wf_normal_draw(1, 0, 2 ** 64 - 5, 10, wf.WF_F32, addr, None) == 1
+    assert b"overflows" in L.wf_last_error()
