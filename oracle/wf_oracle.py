@@ -23,7 +23,9 @@ A = U^-1 R(k) diag(sqrt P_E, sqrt P_B) U with the per-mode Kaiser-Squires
 rotation R(k) = [[c, -s], [s, c]], c = (kx^2 - ky^2)/k^2, s = 2 kx ky / k^2.
 The paper's derivative operator equals this up to -k^2, absorbed into P.  The
 odd term s is set to 0 on the Nyquist row and column (where k and -k alias),
-the usual convention for odd spectral derivatives; R = I at k = 0.
+the usual convention for odd spectral derivatives; only an even side length
+has a Nyquist line; R = I at k = 0.  Grids may be rectangular (ny x nx) and of
+any side lengths; the GPU path takes square power-of-two maps.
 
 Pins (what fixes this file independently of itself) live in
 tests/test_oracle_pins.py: naive O(n^4) DFT, Parseval, unmasked closed form
@@ -33,7 +35,9 @@ terms without a mask, the Fisher identity Cov(E) = F, the two-loop recursion
 against the dense BFGS inverse update, strong-Wolfe steps, the envelope identity
 d chi^2 / d log q_l = -2 Theta_fid,l E_l at the MAP, chi^2_min ~ chi-square(N_obs), the
 unbiasedness of Theta_hat (exact b and F) for a rescaled true spectrum, and the leakage-bias form
-of App. C against the full Fisher run where E and B do not mix.
+of App. C against the full Fisher run where E and B do not mix; on rectangular and
+odd grids the DFT plane wave, the rotation's formula and k -> -k symmetry, the
+unmasked S/(S+N) MAP and exact central differences.
 Parity unpinned: iteration counts and chi^2-versus-iteration curves, because the
 paper gives them only as figures.
 """
@@ -47,16 +51,18 @@ import numpy as np
 
 
 def dft2_naive(x: np.ndarray) -> np.ndarray:
-    """Unitary 2-D DFT by the definition, O(n^4): X[ky,kx] = (1/n) sum
-    x[y,x] exp(-2 pi i (ky y + kx x)/n).  For pinning the FFT-based code."""
-    n = x.shape[-1]
+    """Unitary 2-D DFT by the definition, O(ny^2 nx^2): X[ky,kx] =
+    (ny nx)^-1/2 sum x[y,x] exp(-2 pi i (ky y / ny + kx x / nx)).  For pinning
+    the FFT-based code; any side lengths."""
+    ny, nx = x.shape[-2], x.shape[-1]
     out = np.zeros(x.shape, dtype=np.complex128)
-    idx = np.arange(n)
-    for ky in range(n):
-        ey = np.exp(-2j * np.pi * ky * idx / n)
-        for kx in range(n):
-            ex = np.exp(-2j * np.pi * kx * idx / n)
-            out[..., ky, kx] = np.einsum("...yx,y,x->...", x, ey, ex) / n
+    iy, ix = np.arange(ny), np.arange(nx)
+    norm = np.sqrt(float(ny * nx))
+    for ky in range(ny):
+        ey = np.exp(-2j * np.pi * ky * iy / ny)
+        for kx in range(nx):
+            ex = np.exp(-2j * np.pi * kx * ix / nx)
+            out[..., ky, kx] = np.einsum("...yx,y,x->...", x, ey, ex) / norm
     return out
 
 
@@ -68,32 +74,38 @@ def ifft2u(X):
     return np.fft.ifft2(X, norm="ortho")
 
 
-def signed_modes(n: int):
-    f = np.fft.fftfreq(n, d=1.0 / n)
-    my, mx = np.meshgrid(f, f, indexing="ij")
+def signed_modes(n: int, nx: int | None = None):
+    """Integer mode numbers (my, mx) of an n x nx grid (nx = n by default)."""
+    nx = n if nx is None else nx
+    fy = np.fft.fftfreq(n, d=1.0 / n)
+    fx = np.fft.fftfreq(nx, d=1.0 / nx)
+    my, mx = np.meshgrid(fy, fx, indexing="ij")
     return my, mx
 
 
-def ks_rotation(n: int):
-    """Per-mode Kaiser-Squires cosine and sine (App. C, E/B operator), full plane."""
-    my, mx = signed_modes(n)
+def ks_rotation(n: int, nx: int | None = None):
+    """Per-mode Kaiser-Squires cosine and sine (App. C, E/B operator), full
+    plane of an n x nx grid (nx = n by default).  The Nyquist line of an even
+    side, where k and -k alias, gets s = 0; an odd side has none."""
+    nx = n if nx is None else nx
+    my, mx = signed_modes(n, nx)
     k2 = mx * mx + my * my
-    c = np.ones((n, n))
-    s = np.zeros((n, n))
+    c = np.ones((n, nx))
+    s = np.zeros((n, nx))
     nz = k2 > 0
     c[nz] = (mx[nz] ** 2 - my[nz] ** 2) / k2[nz]
     s[nz] = 2.0 * mx[nz] * my[nz] / k2[nz]
-    nyq = (np.abs(mx) == n // 2) | (np.abs(my) == n // 2)
+    nyq = ((nx % 2 == 0) & (np.abs(mx) == nx // 2)) | ((n % 2 == 0) & (np.abs(my) == n // 2))
     s[nyq] = 0.0
     return c, s
 
 
 def apply_A(z: np.ndarray, P: np.ndarray) -> np.ndarray:
-    """Signal map s = A z for a whitened real field z (C, n, n); P (C, n, n)."""
-    C, n = z.shape[0], z.shape[-1]
+    """Signal map s = A z for a whitened real field z (C, ny, nx); P (C, ny, nx)."""
+    C = z.shape[0]
     Z = fft2u(z) * np.sqrt(P)
     if C == 2:
-        c, s = ks_rotation(n)
+        c, s = ks_rotation(z.shape[-2], z.shape[-1])
         Z = np.stack([c * Z[0] - s * Z[1], s * Z[0] + c * Z[1]])
     x = ifft2u(Z)
     return x.real
@@ -101,10 +113,10 @@ def apply_A(z: np.ndarray, P: np.ndarray) -> np.ndarray:
 
 def apply_At(x: np.ndarray, P: np.ndarray) -> np.ndarray:
     """Transpose of apply_A: A^T = U^-1 diag(sqrt P) R(k)^T U."""
-    C, n = x.shape[0], x.shape[-1]
+    C = x.shape[0]
     X = fft2u(x)
     if C == 2:
-        c, s = ks_rotation(n)
+        c, s = ks_rotation(x.shape[-2], x.shape[-1])
         X = np.stack([c * X[0] + s * X[1], -s * X[0] + c * X[1]])
     return ifft2u(X * np.sqrt(P)).real
 
@@ -159,14 +171,14 @@ def hess_vec(v, W, P) -> np.ndarray:
 
 
 def dense_operator(P: np.ndarray) -> np.ndarray:
-    """A as a dense (C n^2) x (C n^2) matrix, column j = A e_j."""
-    C, n = P.shape[0], P.shape[-1]
-    N = C * n * n
+    """A as a dense (C ny nx) x (C ny nx) matrix, column j = A e_j."""
+    C, ny, nx = P.shape
+    N = C * ny * nx
     A = np.empty((N, N))
     e = np.zeros(N)
     for j in range(N):
         e[j] = 1.0
-        A[:, j] = apply_A(e.reshape(C, n, n), P).ravel()
+        A[:, j] = apply_A(e.reshape(C, ny, nx), P).ravel()
         e[j] = 0.0
     return A
 
@@ -537,7 +549,6 @@ def exact_band_terms(mask, Ninv, P, bands, n_bands, A=None):
     eq:wf_exact_f, first equality; Sec. 2.1 Q_l = dC/dTheta_l):
     C = M A A^T M^T + N,  Q_l = M A Pi_l A^T M^T / Theta_fid,l,
     b_l = 1/2 tr(C^-1 Q_l),  F_ll' = 1/2 tr(C^-1 Q_l C^-1 Q_l')."""
-    C_, n = P.shape[0], P.shape[-1]
     A = dense_operator(P) if A is None else A
     obs = np.broadcast_to(mask[None] == 1, P.shape).ravel()
     Ao = A[obs]

@@ -564,3 +564,80 @@ def test_estimator_is_unbiased_for_a_rescaled_true_spectrum():
     se = est.std(axis=0, ddof=1) / np.sqrt(K)
     assert np.all(np.abs(est.mean(axis=0) - theta * q) <= 5.0 * se), (est.mean(axis=0), theta * q, se)
     assert np.any(np.abs(est.mean(axis=0) - theta) > 5.0 * se)     # distinguishable from the fiducial
+
+
+# ---------------------------------------------------------------------------
+# Rectangular and non-power-of-two grids (the oracle side of such maps)
+# ---------------------------------------------------------------------------
+
+RECT = [(4, 6), (5, 3), (6, 10), (7, 7), (9, 12)]
+
+
+@pytest.mark.parametrize("shape", RECT)
+def test_dft_rectangular_plane_wave_and_fft(shape):
+    """The naive DFT maps a plane wave exp(2 pi i (a y / ny + b x / nx)) to
+    sqrt(ny nx) at mode (a, b) and zero elsewhere; the FFT path agrees with it."""
+    ny, nx = shape
+    a, b = 1 % ny, (nx - 2) % nx
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    wave = np.exp(2j * np.pi * (a * y / ny + b * x / nx))[None]
+    X = O.dft2_naive(wave)
+    want = np.zeros((1, ny, nx), complex)
+    want[0, a, b] = np.sqrt(ny * nx)
+    assert np.allclose(X, want, atol=1e-12)
+    r = np.random.default_rng(sum(shape)).standard_normal((2, ny, nx))
+    assert np.allclose(O.fft2u(r), O.dft2_naive(r), atol=1e-12)
+
+
+@pytest.mark.parametrize("shape", RECT)
+def test_ks_rotation_rectangular_formula_and_symmetry(shape):
+    """Off the Nyquist lines c = (kx^2 - ky^2)/k^2 and s = 2 kx ky / k^2 (an odd
+    side has no Nyquist line), and both are even under k -> -k on the grid,
+    which is what keeps A z real (a Nyquist mode is its own negative, where s
+    is odd, hence s = 0 there)."""
+    ny, nx = shape
+    c, s = O.ks_rotation(ny, nx)
+    my, mx = O.signed_modes(ny, nx)
+    k2 = mx ** 2 + my ** 2
+    nyq = ((nx % 2 == 0) & (np.abs(mx) == nx / 2)) | ((ny % 2 == 0) & (np.abs(my) == ny / 2))
+    off = (k2 > 0) & ~nyq
+    assert np.allclose(c[off], (mx[off] ** 2 - my[off] ** 2) / k2[off], rtol=0, atol=1e-15)
+    assert np.allclose(s[off], 2 * mx[off] * my[off] / k2[off], rtol=0, atol=1e-15)
+    neg = (-np.arange(ny)) % ny, (-np.arange(nx)) % nx
+    assert np.array_equal(c, c[neg[0]][:, neg[1]]) and np.array_equal(s, s[neg[0]][:, neg[1]])
+    if ny % 2 and nx % 2:
+        assert np.allclose(c[k2 > 0] ** 2 + s[k2 > 0] ** 2, 1.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(6, 10), (5, 7), (9, 12)])
+def test_unmasked_rectangular_map_is_s_over_s_plus_n(shape):
+    """No mask, noise variance sigma^2 everywhere: the MAP is diagonal in
+    Fourier space, z_hat = sqrt(P) d_hat / (P + sigma^2) (S/(S+N) for the
+    signal), on rectangular and odd grids alike."""
+    ny, nx = shape
+    rng = np.random.default_rng(ny * nx)
+    my, mx = O.signed_modes(ny, nx)
+    P = (1.0 + np.hypot(my, mx))[None] ** -2.0 * 5.0
+    s2 = 0.3
+    mask = np.ones((ny, nx), np.uint8)
+    Ninv = np.full((1, ny, nx), 1.0 / s2)
+    d = O.synthesize_data(rng.standard_normal((1, ny, nx)), rng.standard_normal((1, ny, nx)) * np.sqrt(s2), mask, P)
+    z = O.dense_wf_whitened(d, mask[None] * Ninv, P)
+    want = O.ifft2u(np.sqrt(P) * O.fft2u(d) / (P + s2)).real
+    assert np.allclose(z, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("shape", [(6, 10), (5, 7)])
+def test_gradient_rectangular_eb_is_exact_central_difference(shape):
+    """chi^2 is quadratic, so central differences equal g^T v up to rounding,
+    here for the two-channel E/B operator on rectangular and odd grids."""
+    ny, nx = shape
+    rng = np.random.default_rng(3)
+    my, mx = O.signed_modes(ny, nx)
+    P = np.stack([(1.0 + np.hypot(my, mx)) ** -1.5, 0.1 * (1.0 + np.hypot(my, mx)) ** -1.5])
+    W = (rng.uniform(size=(ny, nx)) > 0.3)[None] * rng.uniform(0.5, 2.0, size=(2, ny, nx))
+    d = rng.standard_normal((2, ny, nx))
+    z, v = rng.standard_normal((2, ny, nx)), rng.standard_normal((2, ny, nx))
+    h = 1e-3
+    fd = (O.chi2(z + h * v, d, W, P) - O.chi2(z - h * v, d, W, P)) / (2 * h)
+    assert abs(fd - np.sum(O.grad(z, d, W, P) * v)) <= 1e-9 * abs(O.chi2(z, d, W, P))
