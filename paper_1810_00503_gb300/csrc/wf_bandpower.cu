@@ -229,6 +229,9 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (!h || !data || !in || !out) return wf_fail(WF_EINVAL, "bandpower_estimate: null argument");
   if (!data->d || !data->mask || !data->Ninv || !data->P)
     return wf_fail(WF_EINVAL, "bandpower_estimate: the data map needs d, mask, Ninv and P");
+  if (n < 8 || n > WF_NT || (n & (n - 1)) || (C != 1 && C != 2))
+    return wf_fail(WF_EINVAL, "bandpower_estimate: n = %d, C = %d (n a power of two in [8, %d], C 1 or 2)", n, C,
+                   WF_NT);
   const int nb = in->n_bands, J = in->n_sim, nfd = in->n_fd;
   if (nb < 1 || nb > 64) return wf_fail(WF_EINVAL, "bandpower_estimate: n_bands = %d outside [1, 64]", nb);
   if (J < 1) return wf_fail(WF_EINVAL, "bandpower_estimate: n_sim = %d (need >= 1)", J);
@@ -473,6 +476,9 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
     return wf_fail(WF_EINVAL, "bandpower_iterate: need 0 < q_min <= 1 <= q_max (got %g, %g)", q_min, q_max);
   if (in->n_fd < 1) return wf_fail(WF_EINVAL, "bandpower_iterate: needs n_fd >= 1 (the Fisher matrix)");
   if (!data->P || !in->band) return wf_fail(WF_EINVAL, "bandpower_iterate: null P or band table");
+  if (n < 8 || n > WF_NT || (n & (n - 1)) || (C != 1 && C != 2))
+    return wf_fail(WF_EINVAL, "bandpower_iterate: n = %d, C = %d (n a power of two in [8, %d], C 1 or 2)", n, C,
+                   WF_NT);
   if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "bandpower_iterate: bad dtype");
   wf_opts o;
   if (opts) o = *opts;

@@ -172,11 +172,20 @@ def test_bandpower_refuses_bad_arguments_before_device_work():
                        (2, dict(out_on_device=2), b"out_on_device")]:
         assert estimate(C, **kw) == 1, (C, kw)
         assert msg in L.wf_last_error(), (kw, L.wf_last_error())
+    sims = (ctypes.c_longlong * 2)(0, 1)
+    for n, C in ((0, 1), (12, 1), (2048, 1), (16, 0), (16, 3)):  # checked before any size arithmetic
+        bi = wf.WfBandpowerIn(n_bands=4, n_sim=2, n_fd=1, band=addr, sim_index=ctypes.addressof(sims))
+        st = L.bandpower_estimate(h, ctypes.byref(data), n, C, wf.WF_F32, wf.WF_MIXED, ctypes.byref(bi),
+                                  ctypes.byref(o), ctypes.byref(bo), None)
+        assert st == 1 and b"power of two" in L.wf_last_error(), (n, C, L.wf_last_error())
     bi = wf.WfBandpowerIn(n_bands=4, n_sim=2, n_fd=1, band=addr)
     for n_iter, qmin, qmax, msg in [(0, 0.1, 10.0, b"n_iter"), (2, 1.5, 10.0, b"q_min"), (2, 0.1, 0.5, b"q_min")]:
         st = L.bandpower_iterate(h, ctypes.byref(data), 16, 1, wf.WF_F32, wf.WF_MIXED, ctypes.byref(bi),
                                  ctypes.byref(o), n_iter, qmin, qmax, None, None, ctypes.byref(bo), None)
         assert st == 1 and msg in L.wf_last_error(), (n_iter, qmin, qmax, L.wf_last_error())
+    st = L.bandpower_iterate(h, ctypes.byref(data), 0, 1, wf.WF_F32, wf.WF_MIXED, ctypes.byref(bi),
+                             ctypes.byref(o), 2, 0.1, 10.0, None, None, ctypes.byref(bo), None)
+    assert st == 1 and b"power of two" in L.wf_last_error(), L.wf_last_error()
 
 
 def test_normal_draw_refuses_bad_arguments_on_the_host():
