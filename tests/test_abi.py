@@ -197,3 +197,19 @@ def test_normal_draw_refuses_bad_arguments_on_the_host():
     assert b"dtype" in L.wf_last_error()
     assert L.wf_normal_draw(1, 0, 2 ** 64 - 5, 10, wf.WF_F32, addr, None) == 1
     assert b"overflows" in L.wf_last_error()
+
+
+def test_eval_noalloc_refuses_bad_arguments_on_the_host():
+    L = ensure_lib()
+    buf, h, addr = _stand_ins()
+    chi2 = (ctypes.c_double * 4)()
+    other = ctypes.create_string_buffer(64)
+    g = ctypes.addressof(other)
+    ok = dict(s=addr, d=addr, w=addr, P=addr, n=16, C=1, count=1, prec=wf.WF_MIXED, grad=g)
+    for bad, msg in [(dict(s=None), b"null"), (dict(grad=addr), b"alias"), (dict(n=12), b"power of two"),
+                     (dict(n=2048), b"power of two"), (dict(C=3), b"C ="), (dict(count=0), b"count"),
+                     (dict(prec=5), b"precision")]:
+        a = {**ok, **bad}
+        st = L.wf_eval_noalloc(a["s"], a["d"], a["w"], a["P"], a["n"], a["C"], a["count"], a["prec"], chi2,
+                               a["grad"], None)
+        assert st == 1 and msg in L.wf_last_error(), (bad, L.wf_last_error())
