@@ -72,9 +72,9 @@ static int bp_fisher_rows(const wf_bandpower_in* in) {
 // EE terms).  leak > 0 (the leakage-bias form of App. C, B bands leak..nb-1):
 // fdk of every B band is the row of the joint B maps, a B band keeps only its
 // diagonal term, the E-B cross terms are zeroed, and the interpolation of an
-// E column stays inside the E block.  out = [theta | E | b | F | Finv | theta_hat | covE] (sizes nb,
-// nb, nb, nb^2, nb^2, nb, nb^2); flag[0] = 1 if F is singular.  One block,
-// nb <= 64.
+// E column stays inside the E block.  out = [theta | E | b | F | Finv |
+// theta_hat | covE] (sizes nb, nb, nb, nb^2, nb^2, nb, nb^2); flag[0] = 1 if F
+// is singular.  One block, nb <= 64.
 __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int J, int nfd, const int* fdk,
                            int trunc_n, int trunc_w, int leak, double* out, int* flag) {
   extern __shared__ double M[];  // [nb][2 nb] augmented matrix for Gauss-Jordan
