@@ -641,3 +641,28 @@ def test_gradient_rectangular_eb_is_exact_central_difference(shape):
     h = 1e-3
     fd = (O.chi2(z + h * v, d, W, P) - O.chi2(z - h * v, d, W, P)) / (2 * h)
     assert abs(fd - np.sum(O.grad(z, d, W, P) * v)) <= 1e-9 * abs(O.chi2(z, d, W, P))
+
+
+@pytest.mark.parametrize("shape", [(6, 10), (5, 7)])
+def test_exact_band_terms_rectangular_unmasked_closed_form(shape):
+    """The band terms on rectangular and odd grids: no mask and homogeneous
+    noise make C diagonal in Fourier space with P_m + sigma^2, so b_l and F_ll
+    take the per-mode closed forms and F is diagonal, as on square maps."""
+    ny, nx = shape
+    s2, nb = 0.4, 3
+    my, mx = O.signed_modes(ny, nx)
+    k = np.hypot(my, mx)
+    P = (2.0 * (1.0 + k) ** -1.7)[None]
+    edges = np.array([0.5, 1.6, 2.6, k.max() + 1.0])
+    bands = (np.searchsorted(edges, k, side="right") - 1)[None]
+    bands[(k < edges[0]) | (bands >= nb)] = -1
+    mask = np.ones((ny, nx), np.uint8)
+    Ninv = np.full((1, ny, nx), 1.0 / s2)
+    b, F, th = O.exact_band_terms(mask, Ninv, P, bands, nb)
+    for l in range(nb):
+        sel = bands == l
+        assert sel.any()
+        assert np.isclose(th[l], P[sel].mean(), rtol=1e-12)
+        assert np.isclose(b[l], 0.5 / th[l] * np.sum(P[sel] / (P[sel] + s2)), rtol=1e-11)
+        assert np.isclose(F[l, l], 0.5 / th[l] ** 2 * np.sum(P[sel] ** 2 / (P[sel] + s2) ** 2), rtol=1e-11)
+    assert np.abs(F - np.diag(np.diag(F))).max() <= 1e-12 * np.abs(F).max()
