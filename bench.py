@@ -276,9 +276,25 @@ def run_e2e(args, dev, host, iters):
         evals.append(sum(s["iters"] for s in res.stats))
     dt = min(times)
     ev = evals[times.index(dt)]
+    # the same job on a fresh handle: its first solve of the shape times the FFT-stage variants
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        h = wf.Handle()
+        prob = wf.Problem(h_d.to(dev, non_blocking=True), h_m.to(dev, non_blocking=True),
+                          h_N.to(dev, non_blocking=True), h_P.to(dev, non_blocking=True), precision="mixed",
+                          lbfgs_m=args.m, handle=h)
+        res = prob.solve(gtol_rel=0.0, max_iter=iters, check_every=iters, use_graphs=1)
+        h_s.copy_(res.s, non_blocking=True)
+    stream.synchronize()
+    cold = time.perf_counter() - t0
+    prob.close()
+    h.close()
     return {"value": ev / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / iters, "d2h_bytes_per_step": d2h / iters,
-            "iterations": iters, "evals": ev, "seconds": dt,
-            "note": "one wf_map_solve job from pinned host inputs incl. preparation; bytes per step = job bytes / iterations"}
+            "iterations": iters, "evals": ev, "seconds": dt, "seconds_fresh_handle": cold,
+            "note": "one wf_map_solve job from pinned host inputs incl. preparation, on a handle whose FFT-stage "
+                    "tuning for this shape is cached (a serving process keeps its handle); seconds_fresh_handle "
+                    "is the same job on a new handle, tuning included; bytes per step = job bytes / iterations"}
 
 
 def run_eval_pass(args, dev, prob, hbm, reps=20, B=None, n=None):
@@ -527,11 +543,14 @@ def iteration_flops(n, m):
     return 2 * fft + vals * (4 * (5 * m + 9) + 10)
 
 
-def run_fp64_reference(args, dev, gtol=1e-6, fp64_peak=None):
-    """The plain single-map FP64 GPU path on map 0 of the workload: iteration
-    throughput, and one solve to ||g|| / ||g0|| < gtol compared with the mixed
-    batched path's solution of the same map to the same tolerance."""
-    import numpy as np
+def run_fp64_reference(args, dev, cert_tol=1e-4, fp64_peak=None):
+    """Certified accuracy, mixed against the plain single-map FP64 GPU path, on
+    map 0 of the workload.  Both solve the same map (FP32-rounded inputs) with
+    wf_map_solve_refined to the error certificate |grad chi2| / 2 <= cert_tol |s|
+    (a bound on the relative L2 error of the MAP, since the whitened
+    half-Hessian has every eigenvalue >= 1): the mixed path with FP32 operator
+    passes and FP64 outer residuals, the FP64 path in FP64 throughout.  Also the
+    FP64 path's iteration throughput against the measured FP64 FMA peak."""
     import torch
     from paper_1810_00503_gb300 import synth, wf
     n = args.n
@@ -546,7 +565,10 @@ def run_fp64_reference(args, dev, gtol=1e-6, fp64_peak=None):
     nz = torch.randn(1, 1, n, n, generator=g, device=dev, dtype=torch.float64) * sig
     p64 = wf.Problem(torch.zeros_like(Ninv64)[None], mask, Ninv64[None], P64, precision="fp64", lbfgs_m=args.m)
     d64 = p64.simulate(z, nz)
-    p64.set_data(d64)
+    d32, N32, P32 = d64.float(), Ninv64.float()[None], P64.float()
+    p64.close()
+    p64 = wf.Problem(d32.double(), mask, N32.double(), P32.double(), precision="fp64", lbfgs_m=args.m)
+    p32 = wf.Problem(d32, mask, N32, P32, precision="mixed", lbfgs_m=args.m)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         p64.start(gtol_rel=0.0, max_iter=1 << 30, check_every=1)
@@ -559,18 +581,16 @@ def run_fp64_reference(args, dev, gtol=1e-6, fp64_peak=None):
         it_ms = e0.elapsed_time(e1) / args.steps
         p64.finish()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    r64 = p64.solve(gtol_rel=gtol, max_iter=50000, check_every=64)
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - t0
-    p32 = wf.Problem(d64.float(), mask, Ninv64.float()[None], P64.float(), precision="mixed", lbfgs_m=args.m)
-    t0 = time.perf_counter()
-    r32 = p32.solve(gtol_rel=gtol, max_iter=50000, check_every=64, refresh_every=200)
-    torch.cuda.synchronize()
-    t32 = time.perf_counter() - t0
-    a = r64.s[0].cpu().numpy()
-    b = r32.s[0].cpu().numpy().astype(np.complex128)
-    err = float(np.linalg.norm(a - b) / np.linalg.norm(a))
+    out = {}
+    opts = dict(cert_tol=cert_tol, max_rounds=8, gtol_rel=1e-5, max_iter=50000, check_every=64)
+    for name, p in (("mixed", p32), ("fp64", p64)):
+        p.solve_refined(**opts)  # first solve of the shape: the FFT-stage tuning
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r, c = p.solve_refined(**opts)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "certificate": float(c[0]), "iterations": r.stats[0]["iters"],
+                     "status": r.stats[0]["status"]}
     p64.close()
     p32.close()
     flops = iteration_flops(n, args.m)
@@ -578,13 +598,12 @@ def run_fp64_reference(args, dev, gtol=1e-6, fp64_peak=None):
     peak = fp64_peak or FP64_PEAK_TFLOPS
     src = ("measured on this GPU (wf_alu_peak, FP64 FMA chains)" if fp64_peak
            else "nominal GB300 FP64 rate (no measured FP64 peak)")
-    return {"fp64_single_map_evals_per_s": 1000.0 / it_ms, "fp64_single_map_ms_per_iteration": it_ms,
-            "fp64_single_map_solve_s": t64, "fp64_iterations": r64.stats[0]["iters"],
-            "mixed_single_map_solve_s": t32, "mixed_iterations": r32.stats[0]["iters"],
-            "gtol_rel": gtol, "mixed_vs_fp64_rel_l2": err,
+    return {"certified": {"tol": cert_tol, "mixed": out["mixed"], "fp64": out["fp64"],
+                          "mixed_speedup": out["fp64"]["seconds"] / out["mixed"]["seconds"],
+                          "how": "wf_map_solve_refined on map 0 of the workload, first round to |g|/|g0| < 1e-5"},
+            "fp64_single_map_evals_per_s": 1000.0 / it_ms, "fp64_single_map_ms_per_iteration": it_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "flops_per_iteration": flops, "peak_source": src},
-            "note": "map 0 of the workload; the batched mixed path's per-map cost is ms_per_step / maps"}
+                         "frac": achieved / peak, "flops_per_iteration": flops, "peak_source": src}}
 
 
 # ---------------------------------------------------------------------------
@@ -727,6 +746,10 @@ def main():
     if rank == 0:
         line["clocks"] = r["clocks"]
         line["eval_pass"] = run_eval_pass(args, dev, r["prob"], hbm)
+        ep = line["eval_pass"]
+        line["roofline"]["eval_pass"] = {"what": "wf_eval objective+gradient pass over the batch (3 FFT stages)",
+                                         "achieved": ep["achieved_GBps"], "frac": ep["frac"],
+                                         "ms": ep["ms_per_pass"], "algorithmic_bytes": ep["algorithmic_bytes_per_pass"]}
         r["prob"].close()
         if not args.no_extra:
             line["eval_shapes"] = run_eval_shapes(args, dev, hbm)
@@ -743,8 +766,6 @@ def main():
                 line["eb_bandpower"] = run_eb_bandpower(args, dev)
             except Exception as e:  # a side measurement: report it, keep the line
                 line["eb_bandpower"] = {"error": f"{type(e).__name__}: {e}"}
-        if not args.no_fp64:
-            line["fp64_reference"] = run_fp64_reference(args, dev, fp64_peak=alu.get("fp64_tflops"))
         if not args.no_e2e:
             line["e2e"] = run_e2e(args, dev, r["host"], iters=max(K, 10))
         if not args.no_cpu:
@@ -753,6 +774,8 @@ def main():
                                     "sample": f"textbook FP64 L-BFGS on one {args.n}^2 map of the batch, "
                                               f"{cnt} objective+gradient evaluations in {dt:.1f} s "
                                               f"(single-threaded numpy), of {cores_used()} host cores"}
+        if not args.no_fp64:  # last in the line: the certified mixed-against-FP64 comparison
+            line["fp64_reference"] = run_fp64_reference(args, dev, fp64_peak=alu.get("fp64_tflops"))
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

@@ -133,7 +133,11 @@ typedef struct {
   int iters;          /* L-BFGS iterations taken */
   int evals;          /* operator applications (Hessian-vector and gradient passes) */
   int status;         /* wf_status of this map */
-  int pad_;
+  int fft_variant;    /* FFT-stage variant the solve ran (wf_opts.fft_variant code).  Results
+                         are bitwise reproducible for a given variant (every sum runs in a
+                         fixed order); with autotune the variant comes from timing and may
+                         differ between runs, and variants round differently: pass this back
+                         as wf_opts.fft_variant to repeat a solve bit for bit. */
   double chi2;        /* final chi^2 (true value from the data at the returned state) */
   double gnorm_rel;   /* final |g| / |g0| (true gradient) */
 } wf_solve_stats;
@@ -230,6 +234,35 @@ wf_status wf_signal_map(wf_problem* p, const void* s, void* x, void* stream);
  * Synchronises the stream every opts->check_every iterations. */
 wf_status wf_map_solve(wf_problem* p, const wf_opts* opts, const void* s0, void* s_out,
                        void* x_out, wf_solve_stats* stats);
+
+/* MAP solve to a certified accuracy, with the state kept in FP64 (Sec. 2.2:
+ * the MAP minimises eq_chi).  Certificate: the whitened half-Hessian
+ * I + A^T W A has every eigenvalue >= 1, so |s - s_MAP| <= |grad chi2(s)| / 2
+ * for any state s; the call stops map b once |grad chi2(s_b)| / 2 <=
+ * cert_tol |s_b|, both evaluated in FP64, which bounds the relative L2 error
+ * of s_b by cert_tol (to first order in cert_tol).  Rounds of iterative
+ * refinement: the FP64 gradient g at the FP64 state; then the device L-BFGS
+ * in the problem's working precision minimises chi2(s + delta) over delta
+ * from delta = 0 (its gradient starting at g, Hessian-vector passes only),
+ * and s += delta in FP64.  The first round runs to opts->gtol_rel (relative
+ * to |g| at its start), later rounds only as far as the certificate needs.
+ * For a WF_MIXED problem every operator pass of the rounds runs in FP32 and
+ * only the outer evaluations run in FP64, on exact FP64 copies of the
+ * problem's working-precision d, W and sqrt(P) (allocated on the first call,
+ * about 3 C n^2 doubles per map plus the scratch).  A state kept in FP32 can
+ * fail the certificate on strongly curved modes even when it is accurate
+ * (its rounding alone, times curvatures up to ~1e6), hence the FP64 state.
+ * opts as for wf_map_solve; refresh_every is ignored (the outer evaluations
+ * are the refreshes) and opts->max_iter bounds each round.  max_rounds: 1..1000.
+ * s0: working type, spectrum layout, or NULL for 0.
+ * s_out: DEVICE complex double [count][C][n][n/2+1], written.
+ * cert: HOST double [count] or NULL: |grad chi2(s_b)| / (2 |s_b|) at s_out.
+ * stats: HOST [count] or NULL: iters and evals summed over the rounds (outer
+ * evaluations included), chi2 and |g| / |g0| from the FP64 evaluations,
+ * status WF_OK when certified, WF_ENOTCONVERGED when max_rounds ran out.
+ * Returns the worst per-map status; synchronises. */
+wf_status wf_map_solve_refined(wf_problem* p, const wf_opts* opts, double cert_tol, int max_rounds,
+                               const void* s0, void* s_out, double* cert, wf_solve_stats* stats);
 
 /* The same solve in three calls, for callers that drive the iterations
  * themselves (benchmarks, checkpoints, time-sliced serving):
@@ -429,7 +462,10 @@ wf_status wf_normal_draw(unsigned long long seed, unsigned int stream_id, unsign
  * from inputs the caller has already prepared, all DEVICE pointers of the
  * working type (double for WF_FP64, float for WF_MIXED):
  *   s    [count][C][n][n/2+1] complex   whitened state
- *   d    [count][C][n][n]               data (any value where w = 0)
+ *   d    [count][C][n][n]               data, finite everywhere (its value
+ *                                        where w = 0 does not matter, but a NaN
+ *                                        or Inf there still reaches chi2 and
+ *                                        grad through 0 * Inf; zero it)
  *   w    [count][C][n][n]               mask * Ninv, >= 0
  *   P    [C][n][n/2+1]                  signal power per mode, shared by the maps
  *   chi2 double [count], grad like s    outputs
@@ -438,9 +474,12 @@ wf_status wf_normal_draw(unsigned long long seed, unsigned int stream_id, unsign
  * (it needs about (C n^2 + C n (n/2+1)) working-type values per map plus
  * 264 KiB of twiddle tables) returns WF_EINVAL; FP32 fits up to three 1024^2
  * maps per call.
- * The first call on a device resolves the array's address and writes the
- * twiddle tables with blocking copies; make that first call before any stream
- * capture.  All calls share the one array and each call overwrites what it
+ * The first call on a device resolves the array's address, writes the
+ * twiddle tables and synchronises the legacy default stream until they have
+ * landed, so that the kernels of any caller stream (blocking or not) see them;
+ * make that first call before any stream capture.  The address and the tables
+ * are cached per device for the life of the process: cudaDeviceReset after the
+ * first call is not supported.  All calls share the one array and each call overwrites what it
  * uses before reading it, so nothing needs clearing between calls, but calls
  * that overlap on the GPU (different streams, or different host threads)
  * race on it: order them on one stream.  Inputs are not checked for

@@ -173,6 +173,10 @@ extern "C" wf_status wf_create(wf_handle** out, size_t workspace_limit) {
   if (s == WF_OK) e = cudaMemcpy(h->tw64, tw64, sizeof(double2) * WF_TWTAB_ALL, cudaMemcpyHostToDevice);
   if (s == WF_OK && e == cudaSuccess)
     e = cudaMemcpy(h->tw32, tw32, sizeof(float2) * WF_TWTAB_ALL, cudaMemcpyHostToDevice);
+  // A pageable host-to-device cudaMemcpy may return before the DMA into device
+  // memory ends; the handle's kernels may run on non-blocking streams that are
+  // not ordered after the legacy stream, so wait for the tables here.
+  if (s == WF_OK && e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
   free(tw64);
   free(tw32);
   if (s != WF_OK || e != cudaSuccess) {
@@ -202,7 +206,7 @@ extern "C" wf_status wf_workspace_used(const wf_handle* h, size_t* bytes) {
 
 static void free_problem(wf_problem* p) {
   if (!p) return;
-  void* ptrs[] = {p->d, p->w, p->sp, p->sp0, p->scratch, p->part, p->flags};
+  void* ptrs[] = {p->d, p->w, p->sp, p->sp0, p->scratch, p->part, p->flags, p->bpart};
   for (void* q : ptrs) wf_free(p->h, q);
   wf_solver_free(p);
   free(p);
@@ -392,11 +396,29 @@ extern "C" wf_status wf_simulate_data(wf_problem* p, const void* z, const void* 
   return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_simulate_data");
 }
 
+// Band-sum partials of nb bands for every map, kept by the problem and grown
+// on demand (the allocation orders itself after earlier work on the device).
+static wf_status band_partials(wf_problem* p, int nb) {
+  const size_t need = (size_t)p->count * wf_band_nblk(p->g) * nb;
+  if (p->bpart && p->bpart_n >= need) return WF_OK;
+  if (p->bpart) {
+    cudaDeviceSynchronize();  // a pending band sum may still read the old buffer
+    wf_free(p->h, p->bpart);
+    p->bpart = nullptr;
+    p->bpart_n = 0;
+  }
+  wf_status s = wf_alloc(p->h, (void**)&p->bpart, sizeof(double) * need, "band-sum partials");
+  if (s == WF_OK) p->bpart_n = need;
+  return s;
+}
+
 extern "C" wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
                                     const double* theta, int n_bands, double* E, void* stream) {
   if (!p || !s || !band || !theta || !E) return wf_fail(WF_EINVAL, "wf_band_energy: null argument");
   if (n_bands < 1 || n_bands > 4096) return wf_fail(WF_EINVAL, "wf_band_energy: n_bands = %d", n_bands);
-  cudaError_t e = WF_DISPATCH(p, wf_launch_band_energy)(p->g, p->count, s, band, theta, n_bands, E,
+  wf_status rs = band_partials(p, n_bands);
+  if (rs != WF_OK) return rs;
+  cudaError_t e = WF_DISPATCH(p, wf_launch_band_energy)(p->g, p->count, s, band, theta, n_bands, p->bpart, E,
                                                         (cudaStream_t)stream);
   return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_band_energy");
 }
@@ -423,8 +445,10 @@ extern "C" wf_status wf_eval_bands(wf_problem* p, const void* s, void* grad, dou
   if (!p || !s || !grad || !chi2 || !band || !dlogq) return wf_fail(WF_EINVAL, "wf_eval_bands: null argument");
   if (s == grad) return wf_fail(WF_EINVAL, "wf_eval_bands: s and grad must not alias");
   if (n_b < 1 || n_b > 1024) return wf_fail(WF_EINVAL, "wf_eval_bands: n_b = %d outside [1, 1024]", n_b);
+  wf_status rs = band_partials(p, n_b);
+  if (rs != WF_OK) return rs;
   WfBufs b = wf_bufs(p);
-  cudaError_t e = WF_DISPATCH(p, wf_launch_eval_bands)(p->g, b, s, grad, chi2, band, n_b, dlogq,
+  cudaError_t e = WF_DISPATCH(p, wf_launch_eval_bands)(p->g, b, s, grad, chi2, band, n_b, p->bpart, dlogq,
                                                        (cudaStream_t)stream);
   return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_eval_bands");
 }

@@ -31,6 +31,8 @@ struct wf_problem {
   void* scratch;         // [count][C][n][n/2] complex
   double* part;          // [count][WF_NSLOT][maxblk]
   int* flags;            // device status words
+  double* bpart;         // band-sum partials [count][blocks][bands] (grown on demand)
+  size_t bpart_n;        // doubles held by bpart
   WfSolver* solver;
 };
 

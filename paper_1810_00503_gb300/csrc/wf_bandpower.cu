@@ -18,24 +18,43 @@
 #include "wf_api_internal.h"
 
 // Theta_fid,l: full-plane mean of P over band l (half-plane multiplicity 1 on
-// the kx = 0 and kx = n/2 columns, 2 elsewhere).  One block.
+// the kx = 0 and kx = n/2 columns, 2 elsewhere).  One block; per-warp bins
+// ([warps][2 nb]: sums, then counts) summed in a fixed order, so the result is
+// the same on every run.
 template <typename S>
 __global__ void k_theta_fid(const S* P, const int16_t* band, int n, int C, int nb, double* theta) {
-  extern __shared__ double sh[];  // [2 nb]: sums, counts
-  for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) sh[i] = 0.0;
+  extern __shared__ double sh[];
+  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 2 * nb * nw; i += blockDim.x) sh[i] = 0.0;
   __syncthreads();
   const int h = n / 2;
   const size_t tot = (size_t)C * n * (h + 1);
-  for (size_t i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int l = band[i];
-    if (l < 0 || l >= nb) continue;
-    const int kx = (int)(i % (h + 1));
-    const double w = (kx == 0 || kx == h) ? 1.0 : 2.0;
-    atomicAdd(&sh[l], w * (double)P[i]);
-    atomicAdd(&sh[nb + l], w);
+  double* bins = sh + (size_t)w * 2 * nb;
+  for (size_t i0 = 0; i0 < tot; i0 += blockDim.x) {  // uniform trip count across the block
+    const size_t i = i0 + threadIdx.x;
+    int l = -1;
+    double wt = 0.0, pv = 0.0;
+    if (i < tot) {
+      l = band[i];
+      if (l >= nb) l = -1;
+      if (l >= 0) {
+        const int kx = (int)(i % (h + 1));
+        wt = (kx == 0 || kx == h) ? 1.0 : 2.0;
+        pv = wt * (double)P[i];
+      }
+    }
+    wf_warp_bin_add(bins, l, pv);
+    wf_warp_bin_add(bins + nb, l, wt);
   }
   __syncthreads();
-  for (int l = threadIdx.x; l < nb; l += blockDim.x) theta[l] = sh[nb + l] > 0.0 ? sh[l] / sh[nb + l] : 0.0;
+  for (int l = threadIdx.x; l < nb; l += blockDim.x) {
+    double sum = 0.0, cnt = 0.0;
+    for (int q = 0; q < nw; ++q) {
+      sum += sh[(size_t)q * 2 * nb + l];
+      cnt += sh[(size_t)q * 2 * nb + nb + l];
+    }
+    theta[l] = cnt > 0.0 ? sum / cnt : 0.0;
+  }
 }
 
 // P restricted to each band: out[l][i] = band[i] == l ? P[i] : 0; with lo > 0
@@ -296,9 +315,9 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   BP_OK(wf_alloc(h, (void**)&theta, sizeof(double) * nb, "theta_fid"));
   sc.add(theta);
   if (dtype == WF_F64)
-    k_theta_fid<double><<<1, 1024, 2 * nb * sizeof(double), st>>>((const double*)data->P, in->band, n, C, nb, theta);
+    k_theta_fid<double><<<1, 1024, 64 * nb * sizeof(double), st>>>((const double*)data->P, in->band, n, C, nb, theta);
   else
-    k_theta_fid<float><<<1, 1024, 2 * nb * sizeof(double), st>>>((const float*)data->P, in->band, n, C, nb, theta);
+    k_theta_fid<float><<<1, 1024, 64 * nb * sizeof(double), st>>>((const float*)data->P, in->band, n, C, nb, theta);
   BP_TRY(cudaGetLastError());
   void* Pl = nullptr;
   BP_OK(wf_alloc(h, &Pl, nsp * (nb + (L > 0)) * delt, "band-restricted power"));

@@ -131,6 +131,35 @@ __host__ __device__ inline int wf_plan_eff(int lgL, int plan) {
   return plan;
 }
 
+// Band sums that do not depend on scheduling.  Every lane of a warp offers
+// one (band l, value v) pair (l < 0: none); lanes with the same band are
+// summed in lane order and the lowest of them adds the sum to bins[l], a row
+// of per-warp bins that only this warp writes, so the result is the same on
+// every run.  All 32 lanes must call it.
+__device__ __forceinline__ void wf_warp_bin_add(double* bins, int l, double v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int l0 = __shfl_sync(full, l, 0);
+  if (__all_sync(full, l == l0)) {  // one band across the warp (the common case)
+    double t = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+    if (lane == 0 && l0 >= 0) bins[l0] += t;
+    return;
+  }
+  double t = 0.0;
+  bool lead = l >= 0;
+  for (int src = 0; src < 32; ++src) {
+    const int ls = __shfl_sync(full, l, src);
+    const double vs = __shfl_sync(full, v, src);
+    if (ls == l) {
+      t += vs;
+      if (src < lane) lead = false;
+    }
+  }
+  if (lead) bins[l] += t;
+}
+
 // Launch geometry of one (n, C) shape.
 // Kernel variants of the L-BFGS FFT stages, chosen per shape by the autotuner
 // (wf_solve.cu) or forced through wf_opts.fft_variant.
@@ -151,6 +180,12 @@ struct WfGeo {
 
 // Widest tiles and the default kernel variants.
 WfGeo wf_make_geo(int n, int C);
+// Blocks per map of the band reductions: about 4096 modes each, at most 64.
+inline int wf_band_nblk(const WfGeo& g) {
+  const long long nsp = (long long)g.C * g.n * (g.h + 1);
+  const long long k = (nsp + 4095) / 4096;
+  return (int)(k < 1 ? 1 : (k > 64 ? 64 : k));
+}
 // Tiles tc_div / rb_div times narrower (TC >= 2, RB >= 1), the same stride.
 WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_div, int rb_div, int col_plan = 0,
                      int row_plan = 0);
@@ -190,7 +225,7 @@ cudaError_t wf_launch_simulate(const WfGeo& g, const WfBufs& b, const void* z, c
                                void* dout, cudaStream_t st);
 template <typename T>
 cudaError_t wf_launch_band_energy(const WfGeo& g, int B, const void* s, const int16_t* band,
-                                  const double* theta, int n_bands, double* E, cudaStream_t st);
+                                  const double* theta, int n_bands, double* bpart, double* E, cudaStream_t st);
 // L-BFGS kernels.  Streaming-kernel modes: full iteration, materialise only, dots only.
 enum { WF_LB1_FULL = 0, WF_LB1_MATERIALIZE = 1, WF_LB1_DOTS = 2 };
 // The steps taken but not yet added to s are folded in one pass once this
@@ -223,7 +258,7 @@ template <typename T>
 cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st);
 template <typename T>
 cudaError_t wf_launch_eval_bands(const WfGeo& g, const WfBufs& b, const void* src, void* dst, double* chi2,
-                                 const int16_t* band, int n_b, double* dq, cudaStream_t st);
+                                 const int16_t* band, int n_b, double* bpart, double* dq, cudaStream_t st);
 template <typename T>
 cudaError_t wf_launch_band_scale(const WfGeo& g, const void* sp0, void* sp, int ntab, const int16_t* band,
                                  const double* q, int n_b, cudaStream_t st);

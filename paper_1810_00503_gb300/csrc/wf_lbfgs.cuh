@@ -434,12 +434,17 @@ k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, cons
     // A block-wide decision: every thread waits (bounded); if any gave up, the
     // tile never arrived and the block stops.  Its current and remaining maps
     // are marked WF_ETIMEOUT (none of them computes on missing data), and it
-    // returns after letting a copy it issued land (bounded again).
+    // returns after letting a copy it issued land.  That drain wait is bounded
+    // too, by at least the default limit (about 2 s), however short the
+    // caller's limit: a 2-D tile copy that was issued lands within
+    // microseconds, so a block leaves with a copy still writing into its
+    // shared memory only on a device that no longer makes progress at all.
     const bool late = !wf_mbar_wait(&full, parity, lb.spin_limit);
     if (__syncthreads_or(late)) {
       if (tid == 0) {
         for (int r = it; r < nitems; r = next_active(r + gridDim.x)) lb.st[r / g.ntile].status = WF_ETIMEOUT;
-        if (pending) wf_mbar_wait(&full, parity, lb.spin_limit);
+        if (pending)
+          wf_mbar_wait(&full, parity, lb.spin_limit > WF_WAIT_CYCLES_DEFAULT ? lb.spin_limit : WF_WAIT_CYCLES_DEFAULT);
       }
       return;
     }

@@ -28,7 +28,10 @@ static std::mutex g_noalloc_mu;
 static unsigned char* g_noalloc_ptr[WF_NOALLOC_MAXDEV];
 
 // Device address of the array on the current device; the first call on a
-// device resolves it and writes the twiddle tables (blocking copies).
+// device resolves it, writes the twiddle tables and waits until they have
+// landed.  The address and the tables are cached per device for the life of
+// the process, so a cudaDeviceReset after that first call is not supported
+// (the module's static array would come back zeroed, perhaps elsewhere).
 static wf_status noalloc_setup(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (g_noalloc_ptr[dev]) {
@@ -48,6 +51,11 @@ static wf_status noalloc_setup(int dev, unsigned char** out) {
   e = cudaMemcpy((unsigned char*)ptr + WF_NOALLOC_TW64, tw64, sizeof tw64, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy((unsigned char*)ptr + WF_NOALLOC_TW32, tw32, sizeof tw32, cudaMemcpyHostToDevice);
+  // A pageable host-to-device cudaMemcpy may return before its DMA into device
+  // memory has finished, and the kernels run on the caller's stream, which
+  // need not be ordered after the legacy default stream (a non-blocking or
+  // per-thread stream): wait for the copies before the tables are published.
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
   if (e != cudaSuccess) return wf_cuda_fail(e, "wf_eval_noalloc: writing the twiddle tables");
   g_noalloc_ptr[dev] = (unsigned char*)ptr;
   *out = g_noalloc_ptr[dev];

@@ -386,11 +386,10 @@ __device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* sc
 template <typename T, int C, int IN>
 __global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
 k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const void* scratch_,
-          void* dst_, double* part, const void* tw_, const int16_t* band, int n_b, double* dq) {
+          void* dst_, double* part, const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
-  double* bins = (double*)(buf + WF_TILE);  // [n_b] band sums of the optional epilogue
   const int b = blockIdx.y, n = g.n, h = g.h, lgn = g.lgn;
   const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
@@ -402,41 +401,12 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
   const V2<T>* src = (const V2<T>*)src_ + (size_t)b * sstride;
   V2<T>* dst = (V2<T>*)dst_ + (size_t)b * sstride;
-  // Optional band epilogue (standard-layout input only): D_l = -sum over the
-  // full-plane modes of band l of Re(conj(a) s), a = sqrt(P) R^T U W r, which is
-  // d chi^2 / d log q_l when band l's power is scaled by q_l.
-  const bool bands = (IN == WF_IN_STD) && band != nullptr;
-  if (bands) {
-    for (int i = threadIdx.x; i < n_b; i += blockDim.x) bins[i] = 0.0;
-    __syncthreads();
-    if (kx0 == 0) {  // packed column 0: unpack a, then kx = 0 and kx = n/2 modes
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int jm = (n - j) & (n - 1);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          V2<T> A0, Ah;
-          wf_unpack0<T>(buf[wf_sw<T>(j * CT + c * TC)], buf[wf_sw<T>(jm * CT + c * TC)], A0, Ah);
-          const V2<T>* row = src + ((size_t)c * n + j) * (h + 1);
-          const V2<T> S0 = row[0], Sh = row[h];
-          const int16_t* brow = band + ((size_t)c * n + j) * (h + 1);
-          const int l0 = brow[0], lh = brow[h];
-          if (l0 >= 0 && l0 < n_b) atomicAdd(&bins[l0], -(double)(A0.x * S0.x + A0.y * S0.y));
-          if (lh >= 0 && lh < n_b) atomicAdd(&bins[lh], -(double)(Ah.x * Sh.x + Ah.y * Sh.y));
-        }
-      }
-    }
-    __syncthreads();
-  }
   WfAcc<T> acc = 0, acc2 = 0;  // per-thread partials; FP64 from the block sum on
   for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
     const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
     const int kx = kx0 + t;
     const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n);
     const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
-    if (bands && kx > 0) {
-      const int l = band[((size_t)c * n + j) * (h + 1) + kx];
-      if (l >= 0 && l < n_b) atomicAdd(&bins[l], -2.0 * (double)(a.x * sv.x + a.y * sv.y));
-    }
     const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
     const T m2 = sv.x * sv.x + sv.y * sv.y;
     const T o2 = o.x * o.x + o.y * o.y;
@@ -469,11 +439,6 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_PRIOR) * g.maxblk + blockIdx.x] = tot;
   const double tot2 = wf_block_sum((double)acc2);
   if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_OUT2) * g.maxblk + blockIdx.x] = tot2;
-  if (bands) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_b; i += blockDim.x)
-      if (bins[i] != 0.0) atomicAdd(&dq[(size_t)b * n_b + i], bins[i]);
-  }
 }
 
 // Scale the sqrt(P)/n table by sqrt(q_l) on the modes of band l (others 1):
@@ -737,28 +702,65 @@ __global__ void k_unpack(WfGeo g, int B, const V2<T>* in, V2<T>* out) {
   }
 }
 
-// E[b][l] = 1/(2 theta_l) sum over full-plane modes of band l of |s|^2 (eq. el),
-// from a standard-layout spectrum: half-plane weight 1 on kx = 0, n/2, else 2.
-template <typename T>
+// Per-block band sums over the half-plane modes of standard-layout spectra,
+// with the full-plane multiplicity (1 on kx = 0 and n/2, else 2):
+//   MODE 0 (band energy, eq. el):      |s_k|^2
+//   MODE 1 (d chi2 / d log q, eq. pilin): -Re(conj(a_k) s_k), a = s - grad / 2
+//          (grad = 2 (s - a) from the objective + gradient pass)
+// Grid (nblk, B); block x of map b covers a fixed contiguous range of modes
+// and writes part[(b nblk + x) nb + l].  Per-warp bins in shared memory
+// ([warps][nb]), summed over the warps in a fixed order.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(WF_THREADS)
-k_band_energy(WfGeo g, const V2<T>* s, const int16_t* band, const double* theta, int n_bands,
-              double* E) {
-  extern __shared__ double s_bins[];
-  const int b = blockIdx.y, n = g.n, h = g.h;
-  const size_t nsp = (size_t)g.C * n * (h + 1);
-  for (int i = threadIdx.x; i < n_bands; i += blockDim.x) s_bins[i] = 0.0;
+k_band_reduce(WfGeo g, const V2<T>* s, const V2<T>* gr, const int16_t* band, int nb, double* part) {
+  extern __shared__ double s_bins[];  // [WF_THREADS / 32][nb]
+  const int b = blockIdx.y, h = g.h, nw = WF_THREADS / 32, w = threadIdx.x >> 5;
+  const size_t nsp = (size_t)g.C * g.n * (h + 1);
+  for (int i = threadIdx.x; i < nw * nb; i += blockDim.x) s_bins[i] = 0.0;
   __syncthreads();
+  const size_t per = (nsp + gridDim.x - 1) / gridDim.x;
+  const size_t lo = (size_t)blockIdx.x * per, hi = lo + per < nsp ? lo + per : nsp;
   const V2<T>* sb = s + (size_t)b * nsp;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsp; i += stride) {
-    const int l = band[i];
-    if (l < 0 || l >= n_bands) continue;
-    const int kx = (int)(i % (h + 1));
-    const V2<T> v = sb[i];
-    const double m2 = (double)v.x * v.x + (double)v.y * v.y;
-    atomicAdd(&s_bins[l], (kx == 0 || kx == h) ? m2 : 2.0 * m2);
+  const V2<T>* gb = MODE == 1 ? gr + (size_t)b * nsp : nullptr;
+  double* bins = s_bins + (size_t)w * nb;
+  for (size_t i0 = lo; i0 < hi; i0 += blockDim.x) {  // uniform trip count across the block
+    const size_t i = i0 + threadIdx.x;
+    int l = -1;
+    double v = 0.0;
+    if (i < hi) {
+      l = band[i];
+      if (l >= nb) l = -1;
+      if (l >= 0) {
+        const int kx = (int)(i % (h + 1));
+        const double mult = (kx == 0 || kx == h) ? 1.0 : 2.0;
+        const V2<T> x = sb[i];
+        if constexpr (MODE == 0) {
+          v = mult * ((double)x.x * x.x + (double)x.y * x.y);
+        } else {
+          const V2<T> gv = gb[i];
+          const T ax = x.x - (T)0.5 * gv.x, ay = x.y - (T)0.5 * gv.y;
+          v = -mult * (double)(ax * x.x + ay * x.y);
+        }
+      }
+    }
+    wf_warp_bin_add(bins, l, v);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n_bands; i += blockDim.x)
-    atomicAdd(&E[(size_t)b * n_bands + i], 0.5 * s_bins[i] / theta[i]);
+  for (int l = threadIdx.x; l < nb; l += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < nw; ++q) t += s_bins[(size_t)q * nb + l];
+    part[((size_t)b * gridDim.x + blockIdx.x) * nb + l] = t;
+  }
 }
+
+// out[b][l] = scale_l * sum over the nblk block partials of map b, in order:
+// scale 1/(2 theta_l) for the band energy (theta given), 1 otherwise.
+static __global__ void k_band_final(const double* part, int nblk, int nb, const double* theta, double* out) {
+  const int b = blockIdx.x;
+  for (int l = threadIdx.x; l < nb; l += blockDim.x) {
+    double t = 0.0;
+    for (int q = 0; q < nblk; ++q) t += part[((size_t)b * nblk + q) * nb + l];
+    out[(size_t)b * nb + l] = theta ? 0.5 * t / theta[l] : t;
+  }
+}
+

@@ -45,15 +45,33 @@ cudaError_t col_inv(const WfGeo& g, const WfBufs& b, const void* src, cudaStream
 }
 
 template <typename T, int C, int IN>
-cudaError_t col_fwd(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st,
-                    const int16_t* band = nullptr, int n_b = 0, double* dq = nullptr) {
+cudaError_t col_fwd(const WfGeo& g, const WfBufs& b, const void* src, void* dst, cudaStream_t st) {
   static int done = 0;
   auto k = k_col_fwd<T, C, IN>;
-  const size_t sm = band ? (WF_NT + (size_t)WF_TILE) * sizeof(V2<T>) + sizeof(double) * n_b : col_smem<T>(g);
+  const size_t sm = col_smem<T>(g);
   cudaError_t e = ensure_smem(k, sm, &done);
   if (e != cudaSuccess) return e;
   k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, dst,
-                                                b.part, b.tw, band, n_b, dq);
+                                                b.part, b.tw);
+  return cudaGetLastError();
+}
+
+// Deterministic band sums of standard-layout spectra (k_band_reduce, then
+// k_band_final); bpart holds B * wf_band_nblk(g) * nb doubles.
+template <typename T, int MODE>
+cudaError_t band_sums(const WfGeo& g, int B, const void* s, const void* grad, const int16_t* band, int nb,
+                      const double* theta, double* bpart, double* out, cudaStream_t st) {
+  const int nblk = wf_band_nblk(g);
+  const size_t sm = sizeof(double) * (WF_THREADS / 32) * (size_t)nb;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_band_reduce<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_band_reduce<T, MODE><<<dim3(nblk, B), WF_THREADS, sm, st>>>(g, (const V2<T>*)s, (const V2<T>*)grad, band, nb,
+                                                                bpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_band_final<<<B, 128, 0, st>>>(bpart, nblk, nb, theta, out);
   return cudaGetLastError();
 }
 
@@ -325,15 +343,9 @@ inline int grid1d(size_t total, int cap) {
   }
   template <typename T>
   cudaError_t wf_launch_band_energy(const WfGeo& g, int B, const void* s, const int16_t* band,
-                                       const double* theta, int n_bands, double* E,
+                                       const double* theta, int n_bands, double* bpart, double* E,
                                        cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(E, 0, sizeof(double) * (size_t)B * n_bands, st);
-    if (e != cudaSuccess) return e;
-    const size_t nsp = (size_t)g.C * g.n * (g.h + 1);
-    k_band_energy<T><<<dim3(wfimpl::grid1d(nsp, 256), B), WF_THREADS,
-                       sizeof(double) * (size_t)n_bands, st>>>(g, (const V2<T>*)s, band, theta,
-                                                               n_bands, E);
-    return cudaGetLastError();
+    return wfimpl::band_sums<T, 0>(g, B, s, nullptr, band, n_bands, theta, bpart, E, st);
   }
   template <typename T>
   cudaError_t wf_launch_pack(const WfGeo& g, int B, const void* in, void* out,
@@ -353,17 +365,9 @@ inline int grid1d(size_t total, int cap) {
 
 template <typename T>
 cudaError_t wf_launch_eval_bands(const WfGeo& g, const WfBufs& b, const void* src, void* dst, double* chi2,
-                                 const int16_t* band, int n_b, double* dq, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(dq, 0, sizeof(double) * (size_t)b.B * n_b, st);
-  if (e == cudaSuccess) e = wfimpl::col_inv_any<T>(g, b, WF_IN_STD, src, st);
-  if (e == cudaSuccess) e = wfimpl::row_any<T>(WF_ROW_DATA, g, b, nullptr, nullptr, st);
-  if (e == cudaSuccess)
-    e = g.C == 1 ? wfimpl::col_fwd<T, 1, WF_IN_STD>(g, b, src, dst, st, band, n_b, dq)
-                 : wfimpl::col_fwd<T, 2, WF_IN_STD>(g, b, src, dst, st, band, n_b, dq);
-  if (e == cudaSuccess && chi2) {
-    k_finalize_chi2<<<b.B, WF_THREADS, 0, st>>>(b.part, g.maxblk, g.ntile, g.nrb, chi2);
-    e = cudaGetLastError();
-  }
+                                 const int16_t* band, int n_b, double* bpart, double* dq, cudaStream_t st) {
+  cudaError_t e = wf_launch_eval<T>(g, b, WF_ROW_DATA, WF_IN_STD, src, dst, chi2, st);
+  if (e == cudaSuccess) e = wfimpl::band_sums<T, 1>(g, b.B, src, dst, band, n_b, nullptr, bpart, dq, st);
   return e;
 }
 template <typename T>
@@ -446,13 +450,14 @@ cudaError_t wf_launch_eval_pk(const WfGeo& g, const WfBufs& b, const void* src, 
   template cudaError_t wf_launch_simulate<T>(const WfGeo&, const WfBufs&, const void*,             \
                                              const void*, void*, cudaStream_t);                    \
   template cudaError_t wf_launch_band_energy<T>(const WfGeo&, int, const void*, const int16_t*,    \
-                                                const double*, int, double*, cudaStream_t);        \
+                                                const double*, int, double*, double*, cudaStream_t); \
   template cudaError_t wf_launch_pack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);     \
   template cudaError_t wf_launch_unpack<T>(const WfGeo&, int, const void*, void*, cudaStream_t);    \
   template cudaError_t wf_launch_eval_pk<T>(const WfGeo&, const WfBufs&, const void*, void*,       \
                                             cudaStream_t);                                         \
   template cudaError_t wf_launch_eval_bands<T>(const WfGeo&, const WfBufs&, const void*, void*,    \
-                                               double*, const int16_t*, int, double*, cudaStream_t);\
+                                               double*, const int16_t*, int, double*, double*,       \
+                                               cudaStream_t);                                        \
   template cudaError_t wf_launch_band_scale<T>(const WfGeo&, const void*, void*, int,               \
                                                const int16_t*, const double*, int, cudaStream_t);
 #define WF_INSTANTIATE_LBCOL(T)                                                                    \

@@ -59,7 +59,24 @@ struct WfSolver {
   int hist_cap;
   double* g_hist;      // ring the graph was captured with
   int g_hcap;
+  // FP64 state of the refined solve (wf_map_solve_refined), allocated on its
+  // first use: outer state and gradient (packed, FP64), and for a MIXED problem
+  // FP64 copies of d, W and sqrt(P)/n with the FP64 operator's scratch.
+  void* r_s64;
+  void* r_g64;
+  void* r_d64;
+  void* r_w64;
+  void* r_sp64;
+  void* r_scr64;
+  double* r_res;       // [B][WF_RES] per-map outer results (device)
+  double* r_res_host;  // pinned copy
 };
+
+// Per-map record of the refined solve: chi^2, |g|^2 and |s|^2 at the FP64
+// state, the certificate |g| / (2 |s|), inner iterations and evaluations so
+// far, the worst inner status, and |g|^2 at the first outer evaluation.
+enum { WF_RES_CHI2 = 0, WF_RES_GG, WF_RES_SS, WF_RES_CERT, WF_RES_ITERS, WF_RES_EVALS, WF_RES_STATUS, WF_RES_GG0,
+       WF_RES };
 
 enum { WF_PH_ITER = 0, WF_PH_REFRESH = 1 };
 
@@ -412,12 +429,89 @@ __global__ void k_lb_final(const WfLbMap* st, const double* part, int ntile, int
   out[b * 5 + 4] = M.gg0 > 0.0 ? sqrt(g2 / M.gg0) : 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// Kernels of the refined solve.  Spectra are handled as flat arrays of reals
+// (the packed complex layout interleaves re and im), `per` reals per map.
+// ---------------------------------------------------------------------------
+// Blocks of 256 threads for a grid-stride loop over `total` elements.
+static inline int wf_grid(size_t total) {
+  size_t b = (total + 255) / 256;
+  return (int)(b > 2048 ? 2048 : (b < 1 ? 1 : b));
+}
+
+template <typename S, typename D>
+__global__ void k_convert(const S* in, D* out, size_t total) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) out[i] = (D)in[i];
+}
+
+// s64 += delta (the correction of one round, in the working type).
+template <typename T>
+__global__ void k_refine_accum(const T* delta, double* s64, size_t total) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+    s64[i] += (double)delta[i];
+}
+
+// After an outer FP64 evaluation: chi^2, |g|^2, |s|^2 and the certificate
+// |g| / (2 |s|) of each map (the prior partial sums are |s|^2, the output
+// sums |g|^2, both with the half-plane weights).  One warp per map.
+__global__ void k_refine_round(const double* part, int ntile, int nrb, int maxblk, int B, int first,
+                               double* res) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const double* pb = part + (size_t)b * WF_NSLOT * maxblk;
+  const double prior = wf_warp_slot(pb, WF_SLOT_PRIOR, ntile, maxblk);
+  const double data = wf_warp_slot(pb, WF_SLOT_DATA, nrb, maxblk);
+  const double gg = wf_warp_slot(pb, WF_SLOT_OUT2, ntile, maxblk);
+  if ((threadIdx.x & 31) != 0) return;
+  double* r = res + (size_t)b * WF_RES;
+  r[WF_RES_CHI2] = prior + data;
+  r[WF_RES_GG] = gg;
+  r[WF_RES_SS] = prior;
+  r[WF_RES_CERT] = gg == 0.0 ? 0.0 : (prior > 0.0 ? 0.5 * sqrt(gg / prior) : INFINITY);
+  r[WF_RES_EVALS] += 1.0;
+  if (first) r[WF_RES_GG0] = gg;
+}
+
+// Start of an inner round: the correction problem's gradient at delta = 0 is
+// the FP64 gradient g64 (0 for the maps already certified, which then stop at
+// once), and its chi^2 is the outer one, seeded as the prior partial sum.
+template <typename T>
+__global__ void k_refine_seed(const double* g64, const double* res, double tol, size_t per, T* g, double* part,
+                              int ntile, int nrb, int maxblk) {
+  const int b = blockIdx.y;
+  const double* r = res + (size_t)b * WF_RES;
+  const bool done = !(r[WF_RES_CERT] > tol) || r[WF_RES_STATUS] != 0.0;  // certified, or stopped
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += stride)
+    g[(size_t)b * per + i] = done ? (T)0 : (T)g64[(size_t)b * per + i];
+  if (blockIdx.x == 0) {
+    double* pb = part + (size_t)b * WF_NSLOT * maxblk;
+    for (int i = threadIdx.x; i < ntile; i += blockDim.x) pb[(size_t)WF_SLOT_PRIOR * maxblk + i] = i == 0 ? r[WF_RES_CHI2] : 0.0;
+    for (int i = threadIdx.x; i < nrb; i += blockDim.x) pb[(size_t)WF_SLOT_DATA * maxblk + i] = 0.0;
+  }
+}
+
+// After an inner round: its iterations and evaluations, and a fatal status.
+__global__ void k_refine_tally(const WfLbMap* st, int B, double* res) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double* r = res + (size_t)b * WF_RES;
+  r[WF_RES_ITERS] += st[b].k;
+  r[WF_RES_EVALS] += st[b].evals;
+  const int s = st[b].status;
+  if (s == WF_ENONFINITE || s == WF_ETIMEOUT) r[WF_RES_STATUS] = s;
+}
+
 void wf_solver_free(wf_problem* p) {
   WfSolver* S = p->solver;
   if (!S) return;
   if (S->exec) cudaGraphExecDestroy(S->exec);
-  void* ptrs[] = {S->s, S->g, S->ring, S->st, S->nact, S->stats_dev, S->hist};
+  void* ptrs[] = {S->s, S->g, S->ring, S->st, S->nact, S->stats_dev, S->hist, S->r_s64, S->r_g64, S->r_d64,
+                  S->r_w64, S->r_sp64, S->r_scr64, S->r_res};
   for (void* q : ptrs) wf_free(p->h, q);
+  if (S->r_res_host) cudaFreeHost(S->r_res_host);
   if (S->nact_host) cudaFreeHost(S->nact_host);
   if (S->stats_host) cudaFreeHost(S->stats_host);
   if (S->stream) cudaStreamDestroy(S->stream);
@@ -664,9 +758,19 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   return WF_OK;
 }
 
-// Set up the state at s0 (or 0): true gradient, chi^2, first direction.
+// Start of an inner round of the refined solve: the correction starts at 0
+// with the FP64 gradient g64 of the outer state (see k_refine_seed).
+struct WfSeed {
+  const double* g64;
+  const double* res;
+  double tol;
+};
+
+// Set up the state at s0 (or 0): true gradient, chi^2, first direction.  With
+// a seed, the state is the correction delta = 0 of a refined solve's round and
+// its gradient and chi^2 come from the seed instead of an evaluation.
 template <typename T>
-static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
+static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0, const WfSeed* seed = nullptr) {
   const int m = o->lbfgs_m;
   wf_status rs = ensure_solver(p, m);
   if (rs != WF_OK) return rs;
@@ -709,14 +813,28 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0) {
   }
   WF_TRY(cudaEventRecord(S->ev_in, us));
   WF_TRY(cudaStreamWaitEvent(st, S->ev_in, 0));
-  if (s0) WF_TRY(wf_launch_pack<T>(p->g, p->count, s0, S->s, st));
+  if (s0 && !seed) WF_TRY(wf_launch_pack<T>(p->g, p->count, s0, S->s, st));
   else WF_TRY(cudaMemsetAsync(S->s, 0, (size_t)p->count * p->C * p->n * p->n * p->elt, st));
   WF_TRY(cudaMemsetAsync(S->st, 0, sizeof(WfLbMap) * p->count, st));
   rs = choose_variant<T>(p, S, st);  // before the first refresh: one variant for the whole solve
   if (rs != WF_OK) return rs;
   A.ntile = p->g.ntile;
   A.nrb = p->g.nrb;
-  WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
+  if (seed) {
+    const size_t per = (size_t)p->C * p->n * p->n;  // reals per packed map vector
+    k_refine_seed<T><<<dim3(wf_grid(per), p->count), 256, 0, st>>>(seed->g64, seed->res, seed->tol, per,
+                                                                     (T*)S->g, p->part, A.ntile, A.nrb, A.maxblk);
+    WF_TRY(cudaGetLastError());
+    WF_TRY(wf_launch_lb_comb<T>(p->g, b, lb, WF_LB1_DOTS, st));  // <g, g> (no stored pairs yet)
+    WF_TRY(cudaMemsetAsync(S->nact, 0, sizeof(int), st));
+    WfScalarArgs Ai = A;
+    Ai.phase = WF_PH_REFRESH;
+    Ai.init = 1;
+    k_lb_scalar<<<(p->count + WF_SW - 1) / WF_SW, 32 * WF_SW, 0, st>>>(lb.st, b.part, Ai, p->count, S->nact);
+    WF_TRY(cudaGetLastError());
+  } else {
+    WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
+  }
   const int chunk = o->check_every > 0 ? o->check_every : 16;
   if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
                          S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m && S->g_ls == A.ls &&
@@ -824,7 +942,7 @@ static wf_status finish_impl(wf_problem* p, void* s_out, void* x_out, wf_solve_s
       stats[i].iters = (int)r[0];
       stats[i].evals = (int)r[1];
       stats[i].status = status;
-      stats[i].pad_ = 0;
+      stats[i].fft_variant = variant_code(p->g);
       stats[i].chi2 = r[3];
       stats[i].gnorm_rel = r[4];
     }
@@ -837,9 +955,145 @@ static wf_status finish_impl(wf_problem* p, void* s_out, void* x_out, wf_solve_s
   return (wf_status)worst;
 }
 
-// Run n iterations with plain launches and CUDA events around each kernel on
-// the working stream; ms[0..3] = average duration of k_lb1, the row stage,
-// k_lb3 and the scalar step.
+// MAP solve with FP64 iterative refinement and an error certificate (Sec. 2.2
+// for the objective; the certificate follows from the whitened half-Hessian
+// I + A^T W A having every eigenvalue >= 1, so |s - s*| <= |grad chi2(s)| / 2).
+// Rounds: evaluate the true gradient g at the FP64 state s in FP64; stop the
+// maps with |g| <= 2 tol |s|; otherwise minimise the quadratic model of
+// chi^2(s + delta) from delta = 0 with the device L-BFGS in the problem's
+// working precision (its gradient starts at g; Hessian-vector passes only),
+// then s += delta in FP64.  The correction is small, so the working type's
+// rounding stays relative to it, not to s: the state converges to the FP64
+// answer although every operator pass of the inner solves runs in FP32.
+template <typename T>
+static wf_status refined_impl(wf_problem* p, const wf_opts* o, double tol, int max_rounds, const void* s0,
+                              void* s_out, double* cert, wf_solve_stats* stats) {
+  wf_status rs = ensure_solver(p, o->lbfgs_m);
+  if (rs != WF_OK) return rs;
+  WfSolver* S = p->solver;
+  const int B = p->count;
+  const size_t per = (size_t)p->C * p->n * p->n;  // reals per packed map vector, pixels per map
+  const size_t nsp = (size_t)p->C * p->n * (p->n / 2 + 1) * (p->sp_shared ? 1 : B);
+  const bool mixed = p->precision == WF_MIXED;
+  auto need = [&](void** q, size_t bytes, const char* what) {
+    if (rs == WF_OK && !*q) rs = wf_alloc(p->h, q, bytes, what);
+  };
+  need(&S->r_s64, sizeof(double) * per * B, "refined state");
+  need(&S->r_g64, sizeof(double) * per * B, "refined gradient");
+  need((void**)&S->r_res, sizeof(double) * WF_RES * B, "refined records");
+  if (mixed) {
+    need(&S->r_d64, sizeof(double) * per * B, "FP64 data maps");
+    need(&S->r_w64, sizeof(double) * per * B, "FP64 weights");
+    need(&S->r_sp64, sizeof(double) * nsp, "FP64 sqrt(P) tables");
+    need(&S->r_scr64, sizeof(double) * per * B, "FP64 scratch");
+  }
+  if (rs != WF_OK) return rs;
+  if (!S->r_res_host) {
+    cudaError_t e = cudaMallocHost((void**)&S->r_res_host, sizeof(double) * WF_RES * B);
+    if (e != cudaSuccess) { S->r_res_host = nullptr; return wf_cuda_fail(e, "wf_map_solve_refined: host records"); }
+  }
+  cudaStream_t us = (cudaStream_t)o->stream;
+  cudaStream_t st = wf_capturable(us) ? us : S->stream;
+  WF_TRY(cudaEventRecord(S->ev_in, us));
+  WF_TRY(cudaStreamWaitEvent(st, S->ev_in, 0));
+  // The FP64 operator of the outer evaluations: for a MIXED problem on exact
+  // FP64 copies of the working-precision inputs (the problem the inner solves
+  // see), always on the default tiles.
+  const WfGeo go = wf_make_geo(p->n, p->C);
+  WfBufs bo = wf_bufs(p);
+  if (mixed) {
+    k_convert<float, double><<<wf_grid(per * B), 256, 0, st>>>((const float*)p->d, (double*)S->r_d64, per * B);
+    k_convert<float, double><<<wf_grid(per * B), 256, 0, st>>>((const float*)p->w, (double*)S->r_w64, per * B);
+    k_convert<float, double><<<wf_grid(nsp), 256, 0, st>>>((const float*)p->sp, (double*)S->r_sp64, nsp);
+    WF_TRY(cudaGetLastError());
+    bo.d = S->r_d64;
+    bo.w = S->r_w64;
+    bo.sp = S->r_sp64;
+    bo.scratch = S->r_scr64;
+    bo.tw = p->h->tw64;
+  }
+  double* s64 = (double*)S->r_s64;
+  double* res = S->r_res;
+  if (s0) {
+    WF_TRY(wf_launch_pack<T>(p->g, B, s0, S->s, st));
+    k_convert<T, double><<<wf_grid(per * B), 256, 0, st>>>((const T*)S->s, s64, per * B);
+    WF_TRY(cudaGetLastError());
+  } else {
+    WF_TRY(cudaMemsetAsync(s64, 0, sizeof(double) * per * B, st));
+  }
+  WF_TRY(cudaMemsetAsync(res, 0, sizeof(double) * WF_RES * B, st));
+  double* rh = S->r_res_host;
+  for (int round = 0;; ++round) {
+    WF_TRY(wf_launch_eval_pk<double>(go, bo, s64, S->r_g64, st));
+    k_refine_round<<<B, 32, 0, st>>>(p->part, go.ntile, go.nrb, go.maxblk, B, round == 0, res);
+    WF_TRY(cudaGetLastError());
+    WF_TRY(cudaMemcpyAsync(rh, res, sizeof(double) * WF_RES * B, cudaMemcpyDeviceToHost, st));
+    WF_TRY(cudaStreamSynchronize(st));
+    int left = 0;
+    double ratio = 0.5;  // the largest reduction a round is asked for: at least 2x
+    for (int b = 0; b < B; ++b) {
+      const double* r = rh + (size_t)b * WF_RES;
+      if (r[WF_RES_STATUS] != 0.0 || !(r[WF_RES_CERT] > tol)) continue;
+      ++left;
+      if (r[WF_RES_SS] > 0.0 && r[WF_RES_GG] > 0.0) {
+        const double need_b = 0.5 * 2.0 * tol * sqrt(r[WF_RES_SS] / r[WF_RES_GG]);  // half the reduction needed
+        if (need_b < ratio) ratio = need_b;
+      }
+    }
+    if (left == 0 || round >= max_rounds) break;
+    // Inner round: the first from the caller's tolerance, later ones only as
+    // far as the least advanced map needs (with a factor 2 to spare).
+    wf_opts oi = *o;
+    oi.refresh_every = 0;  // the outer FP64 evaluations are this solve's refreshes
+    if (round > 0 && ratio > oi.gtol_rel) oi.gtol_rel = ratio;
+    const WfSeed sd{(const double*)S->r_g64, res, tol};
+    rs = start_impl<T>(p, &oi, nullptr, &sd);
+    if (rs != WF_OK) return rs;
+    const int chunk = oi.check_every > 0 ? oi.check_every : 16;
+    const long long max_chunks = (long long)oi.max_iter / chunk + 2;
+    for (long long c = 0; c < max_chunks; ++c) {
+      int nact = 0;
+      rs = step_impl<T>(p, chunk, &nact);
+      if (rs != WF_OK) return rs;
+      if (nact == 0) break;
+    }
+    const WfBufs bw = wf_bufs(p);
+    WF_TRY(wf_launch_lb_comb<T>(p->g, bw, lb_bufs<T>(S), WF_LB1_MATERIALIZE, st));  // delta into S->s
+    k_refine_tally<<<(B + 127) / 128, 128, 0, st>>>(S->st, B, res);
+    k_refine_accum<T><<<wf_grid(per * B), 256, 0, st>>>((const T*)S->s, s64, per * B);
+    WF_TRY(cudaGetLastError());
+    S->started = 0;
+  }
+  WF_TRY(wf_launch_unpack<double>(go, B, s64, s_out, st));
+  WF_TRY(cudaEventRecord(S->ev_out, st));
+  WF_TRY(cudaStreamWaitEvent(us, S->ev_out, 0));
+  WF_TRY(cudaStreamSynchronize(st));
+  int worst = WF_OK;
+  auto rank = [](int s) {
+    return s == WF_ETIMEOUT ? 4 : s == WF_ENONFINITE ? 3 : s == WF_ELINESEARCH ? 2 : s == WF_ENOTCONVERGED ? 1 : 0;
+  };
+  for (int b = 0; b < B; ++b) {
+    const double* r = rh + (size_t)b * WF_RES;
+    int status = (int)r[WF_RES_STATUS];
+    if (status == WF_OK && !(r[WF_RES_CERT] <= tol))
+      status = isfinite(r[WF_RES_CERT]) ? WF_ENOTCONVERGED : WF_ENONFINITE;
+    if (cert) cert[b] = r[WF_RES_CERT];
+    if (stats) {
+      stats[b].iters = (int)r[WF_RES_ITERS];
+      stats[b].evals = (int)r[WF_RES_EVALS];
+      stats[b].status = status;
+      stats[b].fft_variant = variant_code(p->g);
+      stats[b].chi2 = r[WF_RES_CHI2];
+      stats[b].gnorm_rel = r[WF_RES_GG0] > 0.0 ? sqrt(r[WF_RES_GG] / r[WF_RES_GG0]) : 0.0;
+    }
+    if (rank(status) > rank(worst)) worst = status;
+  }
+  if (worst != WF_OK)
+    wf_fail((wf_status)worst, worst == WF_ENOTCONVERGED ? "wf_map_solve_refined: certificate not reached"
+                                                        : "wf_map_solve_refined: a map stopped with an error");
+  return (wf_status)worst;
+}
+
 // Run n iterations with plain launches and CUDA events around each kernel on
 // the working stream; ms[0..5] = average duration of k_lb_comb, k_lb_colinv,
 // the row stage, k_lb_colfwd, k_lb_qdots and the scalar step.
@@ -957,6 +1211,23 @@ extern "C" wf_status wf_map_solve(wf_problem* p, const wf_opts* opts, const void
     if (nact == 0) break;
   }
   return wf_solver_finish(p, s_out, x_out, stats);
+}
+
+extern "C" wf_status wf_map_solve_refined(wf_problem* p, const wf_opts* opts, double cert_tol, int max_rounds,
+                                          const void* s0, void* s_out, double* cert, wf_solve_stats* stats) {
+  if (!p || !s_out) return wf_fail(WF_EINVAL, "wf_map_solve_refined: null problem or output");
+  if (!(cert_tol > 0.0) || !isfinite(cert_tol))
+    return wf_fail(WF_EINVAL, "wf_map_solve_refined: cert_tol must be finite and > 0");
+  if (max_rounds < 1 || max_rounds > 1000)
+    return wf_fail(WF_EINVAL, "wf_map_solve_refined: max_rounds = %d outside [1, 1000]", max_rounds);
+  wf_opts o;
+  if (opts) o = *opts;
+  else wf_opts_default(&o);
+  wf_status s = check_opts(p, &o);
+  if (s != WF_OK) return s;
+  if (o.inject_timeout_map > 0) return wf_fail(WF_EINVAL, "wf_map_solve_refined: no timeout injection");
+  return p->precision == WF_FP64 ? refined_impl<double>(p, &o, cert_tol, max_rounds, s0, s_out, cert, stats)
+                                 : refined_impl<float>(p, &o, cert_tol, max_rounds, s0, s_out, cert, stats);
 }
 
 // Several problems (typically one per map shape of a heterogeneous batch),

@@ -26,7 +26,8 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_solver_start", "wf_solver_step", "wf_solver_finish", "wf_solver_profile",
            "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
            "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table",
-           "bandpower_iterate", "wf_problem_variant", "wf_alu_peak", "wf_solver_history"]
+           "bandpower_iterate", "wf_problem_variant", "wf_alu_peak", "wf_solver_history",
+           "wf_map_solve_refined"]
 
 
 class WfMap(ctypes.Structure):
@@ -47,7 +48,7 @@ class WfOpts(ctypes.Structure):
 
 class WfSolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("evals", ctypes.c_int), ("status", ctypes.c_int),
-                ("pad_", ctypes.c_int), ("chi2", ctypes.c_double), ("gnorm_rel", ctypes.c_double)]
+                ("fft_variant", ctypes.c_int), ("chi2", ctypes.c_double), ("gnorm_rel", ctypes.c_double)]
 
 
 class WfBandpowerIn(ctypes.Structure):
@@ -102,6 +103,8 @@ def lib() -> ctypes.CDLL:
     L.wf_hess_vec.argtypes = [vp, vp, vp, vp]
     L.wf_signal_map.argtypes = [vp, vp, vp, vp]
     L.wf_map_solve.argtypes = [vp, ctypes.POINTER(WfOpts), vp, vp, vp, ctypes.POINTER(WfSolveStats)]
+    L.wf_map_solve_refined.argtypes = [vp, ctypes.POINTER(WfOpts), d, i, vp, vp, ctypes.POINTER(d),
+                                       ctypes.POINTER(WfSolveStats)]
     L.wf_simulate_data.argtypes = [vp, vp, vp, vp, vp]
     L.wf_band_energy.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.wf_solver_start.argtypes = [vp, ctypes.POINTER(WfOpts), vp]
@@ -205,17 +208,53 @@ class SolveResult:
     stats: list
 
 
+def _noalloc_check(s, d, w, P, chi2, grad, device):
+    """Argument rules of eval_noalloc, checked before any pointer reaches the
+    library: d (B, C, n, n) float32 or float64 sets the shape and the working
+    type; w like d; s and grad (B, C, n, n/2+1) of the matching complex type;
+    P (C, n, n/2+1) like d; chi2 float64 (B,); all contiguous and on `device`."""
+    import torch
+    if not isinstance(d, torch.Tensor) or d.dim() != 4 or d.dtype not in (torch.float32, torch.float64):
+        raise ValueError("d must be a float32 or float64 tensor of shape (B, C, n, n)")
+    B, C, n, n2 = d.shape
+    if n2 != n:
+        raise ValueError(f"d has shape {tuple(d.shape)}: maps must be n x n")
+    cdt = torch.complex128 if d.dtype == torch.float64 else torch.complex64
+    spec = (B, C, n, n // 2 + 1)
+    for t, name, shape, dtype in ((d, "d", (B, C, n, n), d.dtype), (w, "w", (B, C, n, n), d.dtype),
+                                  (s, "s", spec, cdt), (grad, "grad", spec, cdt),
+                                  (P, "P", (C, n, n // 2 + 1), d.dtype), (chi2, "chi2", (B,), torch.float64)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a tensor")
+        if t.device != device:
+            raise ValueError(f"{name} is on {t.device}, the call runs on {device}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, the call needs {tuple(shape)}")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} has dtype {t.dtype}, the call needs {dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    return B, C, n
+
+
 def eval_noalloc(s, d, w, P, chi2=None, grad=None, stream=None):
     """wf_eval_noalloc: objective + gradient without any device allocation in
     the library (scratch in a static device array).  s (B, C, n, n/2+1)
     complex, d and w (B, C, n, n), P (C, n, n/2+1), all CUDA tensors of the
-    working type; chi2 and grad are written (allocated here by torch if not
-    given, which is the caller's allocation, not the library's)."""
+    working type on the current device; chi2 and grad are written (allocated
+    here by torch if not given, which is the caller's allocation, not the
+    library's).  Every tensor is checked (device, shape, dtype, contiguity)
+    before the library is called."""
     import torch
-    B, C, n, _ = d.shape
-    precision = WF_FP64 if d.dtype == torch.float64 else WF_MIXED
+    if not isinstance(d, torch.Tensor) or not d.is_cuda:
+        raise TypeError("d must be a CUDA tensor")
+    dev = torch.device("cuda", torch.cuda.current_device())
     grad = torch.empty_like(s) if grad is None else grad
-    chi2 = torch.empty(B, dtype=torch.float64, device=d.device) if chi2 is None else chi2
+    chi2 = torch.empty(d.shape[0], dtype=torch.float64, device=d.device) if chi2 is None else chi2
+    B, C, n = _noalloc_check(s, d, w, P, chi2, grad, dev)
+    if s.data_ptr() == grad.data_ptr():
+        raise ValueError("s and grad must not alias")
+    precision = WF_FP64 if d.dtype == torch.float64 else WF_MIXED
     _check(lib().wf_eval_noalloc(_ptr(s), _ptr(d), _ptr(w), _ptr(P), n, C, B, precision, _ptr(chi2),
                                  _ptr(grad), _stream(stream)))
     return chi2, grad
@@ -583,7 +622,26 @@ class Problem:
     @staticmethod
     def _stats(st):
         return [dict(iters=e.iters, evals=e.evals, status=STATUS.get(e.status, e.status),
-                     chi2=e.chi2, gnorm_rel=e.gnorm_rel) for e in st]
+                     chi2=e.chi2, gnorm_rel=e.gnorm_rel, fft_variant=e.fft_variant) for e in st]
+
+    def solve_refined(self, cert_tol=1e-4, max_rounds=8, s0=None, stream=None, **opts):
+        """wf_map_solve_refined: MAP solve to the certificate |grad|/2 <= cert_tol |s|
+        with an FP64 state.  Returns (SolveResult with s complex128, certificates
+        as a numpy array)."""
+        import torch
+        o = self._opts(stream, opts)
+        if s0 is not None:
+            self._spec(s0)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        s = torch.empty(self.spec_shape(), dtype=torch.complex128, device=dev)
+        cert = np.zeros(self.B, dtype=np.float64)
+        st = (WfSolveStats * self.B)()
+        status = lib().wf_map_solve_refined(self._p, ctypes.byref(o), float(cert_tol), int(max_rounds), _ptr(s0),
+                                            _ptr(s), cert.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), st)
+        res = SolveResult(s=s, x=None, stats=self._stats(st))
+        if status not in (0, 5):
+            raise WfError(status, lib().wf_last_error().decode(), res)
+        return res, cert
 
     def solve(self, s0=None, x_out=False, stream=None, **opts):
         import torch

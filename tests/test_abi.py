@@ -213,3 +213,39 @@ def test_eval_noalloc_refuses_bad_arguments_on_the_host():
         st = L.wf_eval_noalloc(a["s"], a["d"], a["w"], a["P"], a["n"], a["C"], a["count"], a["prec"], chi2,
                                a["grad"], None)
         assert st == 1 and msg in L.wf_last_error(), (bad, L.wf_last_error())
+
+
+def test_eval_noalloc_binding_checks_every_tensor_before_the_library(monkeypatch):
+    """The binding hands seven raw pointers to wf_eval_noalloc; a tensor of the
+    wrong shape, dtype, layout or device would be read or written out of
+    bounds.  Each such mismatch raises before the library is reached (the
+    library loader is replaced by one that fails the test)."""
+    torch = pytest.importorskip("torch")
+
+    def no_lib():
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(wf, "lib", no_lib)
+    cpu = torch.device("cpu")
+    B, C, n = 2, 1, 16
+    f32, c64 = torch.float32, torch.complex64
+    good = dict(s=torch.zeros(B, C, n, n // 2 + 1, dtype=c64), d=torch.zeros(B, C, n, n, dtype=f32),
+                w=torch.zeros(B, C, n, n, dtype=f32), P=torch.zeros(C, n, n // 2 + 1, dtype=f32),
+                chi2=torch.zeros(B, dtype=torch.float64), grad=torch.zeros(B, C, n, n // 2 + 1, dtype=c64))
+    assert wf._noalloc_check(**good, device=cpu) == (B, C, n)
+    bad = [("s", torch.zeros(B, C, n, n // 2 + 1, dtype=torch.complex128), TypeError),
+           ("s", torch.zeros(B, C, n, n // 2, dtype=c64), ValueError),
+           ("grad", torch.zeros(B + 1, C, n, n // 2 + 1, dtype=c64), ValueError),
+           ("w", torch.zeros(B, C, n, n, dtype=torch.float64), TypeError),
+           ("w", torch.zeros(B, C, n, 2 * n, dtype=f32)[..., ::2], ValueError),
+           ("P", torch.zeros(2, n, n // 2 + 1, dtype=f32), ValueError),
+           ("P", torch.zeros(C, n, n // 2 + 1, dtype=torch.float64), TypeError),
+           ("chi2", torch.zeros(B, dtype=f32), TypeError),
+           ("chi2", torch.zeros(B + 1, dtype=torch.float64), ValueError),
+           ("d", torch.zeros(B, C, n, n // 2, dtype=f32), ValueError),
+           ("s", torch.zeros(B, C, n, n // 2 + 1, dtype=c64, device="meta"), ValueError)]
+    for name, t, exc in bad:
+        with pytest.raises(exc):
+            wf._noalloc_check(**{**good, name: t}, device=cpu)
+    with pytest.raises(TypeError, match="CUDA"):  # host tensors never reach the library
+        wf.eval_noalloc(good["s"], good["d"], good["w"], good["P"])
