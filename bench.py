@@ -53,6 +53,8 @@ def parse():
                     help="skip the single-map and 512^2 eval loops, the heterogeneous batch and the ALU peaks")
     ap.add_argument("--fft-variant", type=int, default=0,
                     help="force an FFT-stage variant (wf_opts.fft_variant code); 0 = autotune")
+    ap.add_argument("--eval-only", action="store_true",
+                    help="only the objective+gradient pass (wf_eval) over the batch, for kernel profiles")
     return ap.parse_args()
 
 
@@ -713,6 +715,13 @@ def main():
             build.build()
         if world > 1:
             torch.distributed.barrier()
+    if args.eval_only:
+        prob, _ = make_problem(args, rank, dev)
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        print(json.dumps({"eval_pass": run_eval_pass(args, dev, prob, hbm, reps=args.steps)}), flush=True)
+        prob.close()
+        return
     r = run_ours(args, rank, world, dev)
     B, K = args.batch, args.steps
     value = world * B * K / (r["ms"] / 1000.0)

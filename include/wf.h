@@ -279,6 +279,28 @@ wf_status wf_solver_start(wf_problem* p, const wf_opts* opts, const void* s0);
 wf_status wf_solver_step(wf_problem* p, int n_iter, int* n_active);
 wf_status wf_solver_finish(wf_problem* p, void* s_out, void* x_out, wf_solve_stats* stats);
 
+/* Checkpoint and resume of a started solve, for long solves (the paper's
+ * high-accuracy CMB solves run for thousands of iterations, App. B) and for
+ * time-sliced serving.  The checkpoint holds every map's L-BFGS state: the
+ * state s, the gradient, the m stored pairs, the FP64 scalars and Gram
+ * matrices, the iteration counters, the options and the FFT-stage variant.
+ *   wf_solver_state_size  bytes of the checkpoint of p's started solve;
+ *   wf_solver_export      writes it to dst (host or device memory that CUDA
+ *                         can address); synchronises the solver's stream;
+ *   wf_solver_import      restores it into p, which must have the same n, C,
+ *                         precision and map count (WF_EINVAL otherwise) and
+ *                         the same inputs (not checked: the state means
+ *                         nothing for other data), replacing any solve p had;
+ *                         then wf_solver_step and wf_solver_finish continue
+ *                         exactly where the exported solve stood, with the
+ *                         same iterates bit for bit.  stream: the stream the
+ *                         resumed solve runs on; the other options are the
+ *                         checkpoint's.  Synchronises stream.
+ * The convergence ring (opts.history) restarts empty on import. */
+wf_status wf_solver_state_size(const wf_problem* p, size_t* bytes);
+wf_status wf_solver_export(wf_problem* p, void* dst, size_t bytes);
+wf_status wf_solver_import(wf_problem* p, const void* src, size_t bytes, void* stream);
+
 /* Diagnostic: run n_iter more iterations of a started solve with plain
  * launches and CUDA events around each kernel on the working stream, and
  * store the average duration in milliseconds of the six kernels of an
@@ -423,6 +445,40 @@ typedef struct {
 wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
                              const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
                              wf_solve_stats* stats);
+
+/* Band powers spread over several GPUs (Sec. 2.5: the simulations are
+ * independent until the estimator averages them).  Each GPU runs
+ * bandpower_estimate on its own simulations (sim_index keeps their random
+ * fields independent of the split) and turns its per-map band energies
+ * (wf_bandpower_out.E_maps, HOST [1 + n_sim + n_rows n_fd][n_bands]: data,
+ * simulations, Fisher maps) into partial sums of
+ * bandpower_sums_len(n_bands, n_rows) doubles:
+ *   [J, J_fd, sum_j E_j (n_bands), sum_j E_j E_j^T (n_bands x n_bands),
+ *    sum_{j < J_fd} (E(Fisher map of row k, j) - E_j)  (n_rows x n_bands, [k][l])]
+ * n_rows: the Fisher rows of the call (the rows of wf_bandpower_in.u).
+ * Partial sums of different simulations add entry by entry (one all-reduce of
+ * a few KB).  Host only, no device work; bandpower_sums_len returns 0 for bad
+ * sizes. */
+size_t bandpower_sums_len(int n_bands, int n_rows);
+wf_status bandpower_sums(const double* E_maps, int n_bands, int n_sim, int n_fd, int n_rows, double* sums);
+
+/* The estimator from summed partial sums (eq. blmv, eq. fisher, eq:wfmv),
+ * the same code bandpower_estimate ends with:
+ *   b = sum E_j / J, cov_E = (sum E_j E_j^T - J b b^T) / (J - 1),
+ *   F[l][l'] = (sum of Fisher row k(l') differences)_l / J_fd / Theta_fid,l',
+ * the unsampled columns interpolated, the truncation and the leakage-bias
+ * form applied as wf_bandpower_in describes, cov = F^-1 (Gauss-Jordan in
+ * FP64), Theta_hat = Theta_fid + F^-1 (E - b).
+ * rules: the wf_bandpower_in of the contributing calls; n_bands, leak_split,
+ * fd_bands, n_fd_bands, trunc_bands, trunc_width and out_on_device are read,
+ * the rest ignored.  sums: HOST, the summed vector (its n_rows from rules);
+ * E_data, theta_fid: HOST [n_bands], the data map's band energies and the
+ * fiducial band powers (E_maps row 0 and theta_fid of any contributing call).
+ * out: as bandpower_estimate (E_maps not written); host arrays need no
+ * device.  J_fd = 0 leaves F, cov and theta_hat NaN.  WF_ENONFINITE if F is
+ * singular, WF_EINVAL for inconsistent counts in the sums. */
+wf_status bandpower_combine(const double* sums, const double* E_data, const double* theta_fid,
+                            const wf_bandpower_in* rules, wf_bandpower_out* out);
 
 /* Iterated fiducial (Sec. 2.3, after eq. pilin): n_iter band-power estimates
  * with the same random fields; between two, the fiducial P moves to the

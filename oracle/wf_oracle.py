@@ -136,12 +136,6 @@ def chi2(z, d, W, P) -> float:
     return float(np.sum(z * z) + np.sum(r * W * r))
 
 
-def chi2_parts(z, d, W, P):
-    """(prior z^T z, data (d - Az)^T W (d - Az))."""
-    r = d - apply_A(z, P)
-    return float(np.sum(z * z)), float(np.sum(r * W * r))
-
-
 def grad(z, d, W, P) -> np.ndarray:
     r = d - apply_A(z, P)
     return 2.0 * (z - apply_At(W * r, P))

@@ -13,6 +13,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
+#include <utility>
 #include <vector>
 
 #include "wf_api_internal.h"
@@ -79,62 +81,113 @@ static int bp_fisher_rows(const wf_bandpower_in* in) {
   return (in->fd_bands ? in->n_fd_bands : nE) + (in->leak_split > 0 ? 1 : 0);
 }
 
-// Estimator from the band energies of all solved maps.  Rows of Eall: 0 = data,
-// 1..J = noise-bias simulations, 1+J+k*nfd+j = Fisher map k (of band fdb[k]),
-// sim j.  fdk[l] = k for a band with Fisher maps, -1 for one without: its
-// column is interpolated from the sampled ones (Sec. 3.1: the Fisher matrix is
-// smooth and nearly translation invariant): between sampled s0 < l' < s1,
-// F[l'+o][l'] = (1-t) F[s0+o][s0] + t F[s1+o][s1], t = (l'-s0)/(s1-s0), a term
-// whose row leaves the matrix dropped and the other weighted alone; beyond the
-// first or last sampled column the nearest one is shifted.  Then the terms
-// |l - l'| > trunc_w with l, l' < trunc_n are zeroed (App. C: far off-diagonal
-// EE terms).  leak > 0 (the leakage-bias form of App. C, B bands leak..nb-1):
-// fdk of every B band is the row of the joint B maps, a B band keeps only its
-// diagonal term, the E-B cross terms are zeroed, and the interpolation of an
-// E column stays inside the E block.  out = [theta | E | b | F | Finv |
-// theta_hat | covE] (sizes nb, nb, nb, nb^2, nb^2, nb, nb^2); flag[0] = 1 if F
-// is singular.  One block, nb <= 64.
-__global__ void k_bp_final(const double* Eall, const double* theta, int nb, int J, int nfd, const int* fdk,
-                           int trunc_n, int trunc_w, int leak, double* out, int* flag) {
-  extern __shared__ double M[];  // [nb][2 nb] augmented matrix for Gauss-Jordan
-  __shared__ double piv_val;
-  __shared__ int piv_row;
+// Fisher-map bookkeeping shared by the estimator and the combination of
+// partial sums: fdb[k] is the band of Fisher row k (k < nbF), fdk[l] the row
+// band l's column comes from (-1: interpolated), with leak_split every B band
+// pointing at the last row, the joint B maps.  Checks fd_bands.
+static wf_status bp_rows(const wf_bandpower_in* in, const char* who, int* fdb, int* fdk, int* nbF_out) {
+  const int nb = in->n_bands, L = in->leak_split;
+  const int nE = L > 0 ? L : nb;
+  int nbF = 0;
+  for (int l = 0; l < nb; ++l) fdk[l] = -1;
+  if (in->fd_bands) {
+    if (in->n_fd_bands < 1 || in->n_fd_bands > nE) return wf_fail(WF_EINVAL, "%s: n_fd_bands = %d", who, in->n_fd_bands);
+    for (int k = 0; k < in->n_fd_bands; ++k) {
+      const int l = in->fd_bands[k];
+      if (l < 0 || l >= nE || (k > 0 && l <= fdb[k - 1]))
+        return wf_fail(WF_EINVAL, "%s: fd_bands must be ascending band ids in [0, %s)", who,
+                       L > 0 ? "leak_split" : "n_bands");
+      fdb[nbF] = l;
+      fdk[l] = nbF++;
+    }
+  } else {
+    for (int l = 0; l < nE; ++l) fdb[nbF] = l, fdk[l] = nbF++;
+  }
+  for (int l = nE; l < nb; ++l) fdk[l] = nbF;
+  *nbF_out = nbF;
+  return WF_OK;
+}
+
+// Partial sums of the estimator over a set of simulations, from the band
+// energies of its solved maps (rows: 0 = data, 1..J = noise-bias simulations,
+// 1+J+k*nfd+j = Fisher map of row k reusing simulation j):
+//   [J, J_fd, sum_j E_j (nb), sum_j E_j E_j^T (nb x nb),
+//    sum_{j < J_fd} (E(Fisher map k, j) - E_j) (nR x nb, [k][l])]
+// Sums over several GPUs' simulations add entry by entry.  Entry i, in a
+// fixed summation order (the device kernel and the host call share it).
+static __host__ __device__ inline size_t bp_sums_len(int nb, int nR) {
+  return 2 + (size_t)nb + (size_t)nb * nb + (size_t)nR * nb;
+}
+static __host__ __device__ double bp_sum_entry(const double* E, int nb, int J, int nfd, size_t i) {
+  if (i == 0) return (double)J;
+  if (i == 1) return (double)nfd;
+  i -= 2;
+  double s = 0.0;
+  if (i < (size_t)nb) {
+    for (int j = 0; j < J; ++j) s += E[(size_t)(1 + j) * nb + i];
+    return s;
+  }
+  i -= nb;
+  if (i < (size_t)nb * nb) {
+    const size_t l = i / nb, lp = i % nb;
+    for (int j = 0; j < J; ++j) s += E[(size_t)(1 + j) * nb + l] * E[(size_t)(1 + j) * nb + lp];
+    return s;
+  }
+  i -= (size_t)nb * nb;
+  const size_t k = i / nb, l = i % nb;
+  for (int j = 0; j < nfd; ++j) s += E[(size_t)(1 + J + k * nfd + j) * nb + l] - E[(size_t)(1 + j) * nb + l];
+  return s;
+}
+__global__ void k_bp_sums(const double* E, int nb, int J, int nfd, size_t len, double* sums) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+    sums[i] = bp_sum_entry(E, nb, J, nfd, i);
+}
+
+// The estimator from the partial sums (eq. blmv, eq. fisher, eq:wfmv), FP64 on
+// the host for any number of contributing GPUs:
+//   b = S1 / J;  cov_E = (S2 - J b b^T) / (J - 1);
+//   F[l][l'] = D[fdk[l']][l] / J_fd / Theta_fid,l' for a band with Fisher maps.
+// A column without them is interpolated from the sampled ones (Sec. 3.1: the
+// Fisher matrix is smooth and nearly translation invariant): between sampled
+// s0 < l' < s1, F[l'+o][l'] = (1-t) F[s0+o][s0] + t F[s1+o][s1],
+// t = (l'-s0)/(s1-s0), a term whose row leaves the matrix dropped and the other
+// weighted alone; beyond the first or last sampled column the nearest one is
+// shifted.  Then F[l][l'] = 0 for l, l' < trunc_n with |l - l'| > trunc_w
+// (App. C: far off-diagonal EE terms).  leak > 0 (the leakage-bias form of
+// App. C, B bands leak..nb-1): a B band keeps only its diagonal term, the E-B
+// cross terms are zero, and the interpolation of an E column stays inside the
+// E block.  F^-1 by Gauss-Jordan elimination with partial pivoting;
+// Theta_hat = Theta_fid + F^-1 (E - b).  out = [theta | E | b | F | Finv |
+// theta_hat | covE] (sizes nb, nb, nb, nb^2, nb^2, nb, nb^2).  J_fd = 0 leaves
+// F, F^-1 and Theta_hat NaN.  Returns true if F is singular.
+static bool bp_final(const double* sums, const double* E_data, const double* theta, int nb, const int* fdk,
+                     int trunc_n, int trunc_w, int leak, double* out) {
+  const double J = sums[0], Jfd = sums[1];
+  const double* S1 = sums + 2;
+  const double* S2 = S1 + nb;
+  const double* D = S2 + (size_t)nb * nb;
   double* o_theta = out;
   double* o_E = out + nb;
   double* o_b = out + 2 * nb;
   double* o_F = out + 3 * nb;
-  double* o_Fi = o_F + nb * nb;
-  double* o_th = o_Fi + nb * nb;
+  double* o_Fi = o_F + (size_t)nb * nb;
+  double* o_th = o_Fi + (size_t)nb * nb;
   double* o_cE = o_th + nb;
-  const int t = threadIdx.x;
-  for (int l = t; l < nb; l += blockDim.x) {
+  for (int l = 0; l < nb; ++l) {
     o_theta[l] = theta[l];
-    o_E[l] = Eall[l];
-    double s = 0.0;
-    for (int j = 0; j < J; ++j) s += Eall[(size_t)(1 + j) * nb + l];
-    o_b[l] = s / J;
+    o_E[l] = E_data[l];
+    o_b[l] = S1[l] / J;
   }
-  __syncthreads();
-  for (int idx = t; idx < nb * nb; idx += blockDim.x) {
-    const int l = idx / nb, lp = idx % nb, k = fdk[lp];
-    double s = 0.0;
-    for (int j = 0; j < nfd && k >= 0; ++j)
-      s += Eall[(size_t)(1 + J + k * nfd + j) * nb + l] - Eall[(size_t)(1 + j) * nb + l];
-    o_F[idx] = (nfd > 0 && k >= 0) ? s / nfd / theta[lp] : 0.0;
-    double c = 0.0;
-    for (int j = 0; j < J; ++j)
-      c += (Eall[(size_t)(1 + j) * nb + l] - o_b[l]) * (Eall[(size_t)(1 + j) * nb + lp] - o_b[lp]);
-    o_cE[idx] = J > 1 ? c / (J - 1) : NAN;
-  }
-  __syncthreads();
-  const int lim = leak > 0 ? leak : nb;  // bands an interpolated column draws on (its block)
-  for (int idx = t; idx < nb * nb; idx += blockDim.x) {  // columns without Fisher maps
-    const int l = idx / nb, lp = idx % nb;
-    if (fdk[lp] >= 0 || nfd == 0) continue;
-    if (l >= lim) {
-      o_F[idx] = 0.0;
-      continue;
+  for (int l = 0; l < nb; ++l)
+    for (int lp = 0; lp < nb; ++lp) {
+      const int k = fdk[lp];
+      o_F[l * nb + lp] = (Jfd > 0.0 && k >= 0) ? D[(size_t)k * nb + l] / Jfd / theta[lp] : 0.0;
+      o_cE[l * nb + lp] = J > 1.0 ? (S2[l * nb + lp] - J * o_b[l] * o_b[lp]) / (J - 1.0) : NAN;
     }
+  const int lim = leak > 0 ? leak : nb;  // bands an interpolated column draws on (its block)
+  std::vector<double> F0(o_F, o_F + (size_t)nb * nb);  // the sampled columns, read by the interpolation
+  for (int lp = 0; lp < nb && Jfd > 0.0; ++lp) {
+    if (fdk[lp] >= 0) continue;
     int s0 = -1, s1 = -1;
     for (int q = lp - 1; q >= 0 && s0 < 0; --q)
       if (fdk[q] >= 0) s0 = q;
@@ -149,69 +202,85 @@ __global__ void k_bp_final(const double* Eall, const double* theta, int nb, int 
     } else {
       w1 = 1.0;
     }
-    const int o = l - lp;
-    double acc = 0.0, ws = 0.0;
-    if (s0 >= 0 && w0 > 0.0 && s0 + o >= 0 && s0 + o < lim) {
-      acc += w0 * o_F[(s0 + o) * nb + s0];
-      ws += w0;
+    for (int l = 0; l < nb; ++l) {
+      if (l >= lim) {
+        o_F[l * nb + lp] = 0.0;
+        continue;
+      }
+      const int o = l - lp;
+      double acc = 0.0, ws = 0.0;
+      if (s0 >= 0 && w0 > 0.0 && s0 + o >= 0 && s0 + o < lim) {
+        acc += w0 * F0[(size_t)(s0 + o) * nb + s0];
+        ws += w0;
+      }
+      if (s1 >= 0 && w1 > 0.0 && s1 + o >= 0 && s1 + o < lim) {
+        acc += w1 * F0[(size_t)(s1 + o) * nb + s1];
+        ws += w1;
+      }
+      o_F[l * nb + lp] = ws > 0.0 ? acc / ws : 0.0;
     }
-    if (s1 >= 0 && w1 > 0.0 && s1 + o >= 0 && s1 + o < lim) {
-      acc += w1 * o_F[(s1 + o) * nb + s1];
-      ws += w1;
+  }
+  for (int l = 0; l < nb; ++l)
+    for (int lp = 0; lp < nb; ++lp) {
+      if (l < trunc_n && lp < trunc_n && abs(l - lp) > trunc_w) o_F[l * nb + lp] = 0.0;
+      if (leak > 0 && (l >= leak || lp >= leak) && l != lp) o_F[l * nb + lp] = 0.0;  // cross blocks, BB off-diagonal
     }
-    o_F[idx] = ws > 0.0 ? acc / ws : 0.0;
+  if (!(Jfd > 0.0)) {  // no Fisher maps: F, F^-1 and Theta_hat are undefined
+    for (size_t i = 0; i < (size_t)nb * nb; ++i) o_F[i] = o_Fi[i] = NAN;
+    for (int l = 0; l < nb; ++l) o_th[l] = NAN;
+    return false;
   }
-  __syncthreads();
-  for (int idx = t; idx < nb * nb; idx += blockDim.x) {
-    const int l = idx / nb, lp = idx % nb;
-    if (l < trunc_n && lp < trunc_n && abs(l - lp) > trunc_w) o_F[idx] = 0.0;
-    if (leak > 0 && (l >= leak || lp >= leak) && l != lp) o_F[idx] = 0.0;  // cross blocks, BB off-diagonal
-  }
-  __syncthreads();
   // Gauss-Jordan elimination with partial pivoting on [F | I]
   const int w2 = 2 * nb;
-  for (int idx = t; idx < nb * w2; idx += blockDim.x) {
-    const int r = idx / w2, c = idx % w2;
-    M[idx] = c < nb ? o_F[r * nb + c] : (c - nb == r ? 1.0 : 0.0);
-  }
-  __syncthreads();
+  std::vector<double> M((size_t)nb * w2);
+  for (int r = 0; r < nb; ++r)
+    for (int c = 0; c < w2; ++c) M[(size_t)r * w2 + c] = c < nb ? o_F[r * nb + c] : (c - nb == r ? 1.0 : 0.0);
+  bool singular = false;
   for (int col = 0; col < nb; ++col) {
-    if (t == 0) {
-      int best = col;
-      double bv = fabs(M[col * w2 + col]);
-      for (int r = col + 1; r < nb; ++r)
-        if (fabs(M[r * w2 + col]) > bv) { bv = fabs(M[r * w2 + col]); best = r; }
-      piv_row = best;
-      piv_val = M[best * w2 + col];
-      if (!(bv > 0.0) || !isfinite(bv)) flag[0] = 1;
+    int best = col;
+    double bv = fabs(M[(size_t)col * w2 + col]);
+    for (int r = col + 1; r < nb; ++r)
+      if (fabs(M[(size_t)r * w2 + col]) > bv) { bv = fabs(M[(size_t)r * w2 + col]); best = r; }
+    if (!(bv > 0.0) || !std::isfinite(bv)) singular = true;
+    if (best != col)
+      for (int c = 0; c < w2; ++c) std::swap(M[(size_t)col * w2 + c], M[(size_t)best * w2 + c]);
+    const double pv = M[(size_t)col * w2 + col];
+    for (int c = 0; c < w2; ++c) M[(size_t)col * w2 + c] /= pv;
+    for (int r = 0; r < nb; ++r) {
+      if (r == col) continue;
+      const double f = M[(size_t)r * w2 + col];
+      for (int c = 0; c < w2; ++c)
+        if (c != col) M[(size_t)r * w2 + c] -= f * M[(size_t)col * w2 + c];
+      M[(size_t)r * w2 + col] = 0.0;
     }
-    __syncthreads();
-    if (piv_row != col)
-      for (int c = t; c < w2; c += blockDim.x) {
-        const double a = M[col * w2 + c];
-        M[col * w2 + c] = M[piv_row * w2 + c];
-        M[piv_row * w2 + c] = a;
-      }
-    __syncthreads();
-    const double pv = piv_val;
-    for (int c = t; c < w2; c += blockDim.x) M[col * w2 + c] /= pv;
-    __syncthreads();
-    for (int idx = t; idx < nb * w2; idx += blockDim.x) {
-      const int r = idx / w2, c = idx % w2;
-      if (r != col && c != col) M[idx] -= M[r * w2 + col] * M[col * w2 + c];
-    }
-    __syncthreads();
-    for (int r = t; r < nb; r += blockDim.x)
-      if (r != col) M[r * w2 + col] = 0.0;
-    __syncthreads();
   }
-  for (int idx = t; idx < nb * nb; idx += blockDim.x) o_Fi[idx] = M[(idx / nb) * w2 + nb + idx % nb];
-  __syncthreads();
-  for (int l = t; l < nb; l += blockDim.x) {
+  for (int l = 0; l < nb; ++l)
+    for (int lp = 0; lp < nb; ++lp) o_Fi[l * nb + lp] = M[(size_t)l * w2 + nb + lp];
+  for (int l = 0; l < nb; ++l) {
     double s = 0.0;
     for (int k = 0; k < nb; ++k) s += o_Fi[l * nb + k] * (o_E[k] - o_b[k]);
     o_th[l] = o_theta[l] + s;
   }
+  return singular;
+}
+
+// Writes the estimator's host results (layout of bp_final) to the caller's
+// output arrays, host or device.
+static wf_status bp_write_out(const double* hout, int nb, int on_device, wf_bandpower_out* out, const char* who) {
+  const size_t nb2 = (size_t)nb * nb;
+  double* dst[7] = {out->theta_fid, out->E, out->bias, out->fisher, out->cov, out->theta_hat, out->cov_E};
+  const size_t off[7] = {0, (size_t)nb, 2 * (size_t)nb, 3 * (size_t)nb, 3 * nb + nb2, 3 * nb + 2 * nb2,
+                         4 * nb + 2 * nb2};
+  const size_t len[7] = {(size_t)nb, (size_t)nb, (size_t)nb, nb2, nb2, (size_t)nb, nb2};
+  for (int i = 0; i < 7; ++i) {
+    if (on_device) {
+      const cudaError_t e = cudaMemcpy(dst[i], hout + off[i], sizeof(double) * len[i], cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return wf_cuda_fail(e, who);
+    } else {
+      memcpy(dst[i], hout + off[i], sizeof(double) * len[i]);
+    }
+  }
+  return WF_OK;
 }
 
 namespace {
@@ -289,24 +358,8 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   const size_t delt = dtype == WF_F64 ? 8 : 4;
   const size_t welt = precision == WF_FP64 ? 8 : 4;
   const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
-  // bands given per-band Fisher maps (all, or all E bands, by default) and each
-  // band's Fisher-map row; with leak_split every B band points at the last row,
-  // the joint B maps
   int fdb[64], fdk[64], nbF = 0;
-  for (int l = 0; l < nb; ++l) fdk[l] = -1;
-  if (in->fd_bands) {
-    for (int k = 0; k < in->n_fd_bands; ++k) {
-      const int l = in->fd_bands[k];
-      if (l < 0 || l >= nE || (k > 0 && l <= fdb[k - 1]))
-        return wf_fail(WF_EINVAL, "bandpower_estimate: fd_bands must be ascending band ids in [0, %s)",
-                       L > 0 ? "leak_split" : "n_bands");
-      fdb[nbF] = l;
-      fdk[l] = nbF++;
-    }
-  } else {
-    for (int l = 0; l < nE; ++l) fdb[nbF] = l, fdk[l] = nbF++;
-  }
-  for (int l = nE; l < nb; ++l) fdk[l] = nbF;
+  BP_OK(bp_rows(in, "bandpower_estimate", fdb, fdk, &nbF));
   const int nR = bp_fisher_rows(in);  // nbF, plus the joint B row
   const int nF = nR * nfd, Btot = 1 + J + nF;
   Scope sc(h);
@@ -428,51 +481,74 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   BP_OK(wf_alloc(h, (void**)&Eall, sizeof(double) * Btot * nb, "band energies"));
   sc.add(Eall);
   BP_OK(wf_band_energy(ps, sall, in->band, theta, nb, Eall, st));
-  const size_t nout = 4 * (size_t)nb + 3 * (size_t)nb * nb;
-  double* dout = nullptr;
-  int* dflag = nullptr;
-  BP_OK(wf_alloc(h, (void**)&dout, sizeof(double) * nout, "estimator output"));
-  sc.add(dout);
-  BP_OK(wf_alloc(h, (void**)&dflag, sizeof(int), "flag"));
-  sc.add(dflag);
-  BP_TRY(cudaMemsetAsync(dflag, 0, sizeof(int), st));
-  int* dfdk = nullptr;
-  BP_OK(wf_alloc(h, (void**)&dfdk, sizeof(int) * 64, "Fisher rows"));
-  sc.add(dfdk);
-  BP_TRY(cudaMemcpyAsync(dfdk, fdk, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-  const size_t gj_smem = sizeof(double) * 2 * nb * nb;
-  BP_TRY(cudaFuncSetAttribute(k_bp_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 64 * 64 * 8)));
-  k_bp_final<<<1, 256, gj_smem, st>>>(Eall, theta, nb, J, nfd, dfdk, in->trunc_bands, in->trunc_width, L, dout,
-                                      dflag);
+  const size_t slen = bp_sums_len(nb, nR);
+  double* dsums = nullptr;
+  BP_OK(wf_alloc(h, (void**)&dsums, sizeof(double) * slen, "partial sums"));
+  sc.add(dsums);
+  k_bp_sums<<<(int)((slen + 127) / 128), 128, 0, st>>>(Eall, nb, J, nfd, slen, dsums);
   BP_TRY(cudaGetLastError());
-  double* hout = (double*)malloc(sizeof(double) * nout);
-  if (!hout) return wf_fail(WF_ENOMEM, "bandpower_estimate: host allocation");
-  int hflag = 0;
-  cudaError_t e = cudaMemcpyAsync(hout, dout, sizeof(double) * nout, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) { free(hout); return wf_cuda_fail(e, "bandpower_estimate: reading results"); }
-  const size_t nb2 = (size_t)nb * nb;
-  if (nfd == 0) {  // no Fisher maps on this call: F, F^-1 and Theta_hat are undefined
-    for (size_t i = 0; i < nb2; ++i) hout[3 * nb + i] = hout[3 * nb + nb2 + i] = NAN;
-    for (int l = 0; l < nb; ++l) hout[3 * nb + 2 * nb2 + l] = NAN;
-  }
-  // the outputs, host or device arrays
-  const cudaMemcpyKind kind = in->out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-  double* dst[7] = {out->theta_fid, out->E, out->bias, out->fisher, out->cov, out->theta_hat, out->cov_E};
-  const size_t off[7] = {0, (size_t)nb, 2 * (size_t)nb, 3 * (size_t)nb, 3 * nb + nb2, 3 * nb + 2 * nb2, 4 * nb + 2 * nb2};
-  const size_t len[7] = {(size_t)nb, (size_t)nb, (size_t)nb, nb2, nb2, (size_t)nb, nb2};
-  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaMemcpy(dst[i], hout + off[i], sizeof(double) * len[i], kind);
-  free(hout);
-  if (e != cudaSuccess) return wf_cuda_fail(e, "bandpower_estimate: writing results");
+  std::vector<double> hsums(slen), hhead(2 * (size_t)nb);  // sums; theta_fid and the data map's E
+  BP_TRY(cudaMemcpyAsync(hsums.data(), dsums, sizeof(double) * slen, cudaMemcpyDeviceToHost, st));
+  BP_TRY(cudaMemcpyAsync(hhead.data(), theta, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  BP_TRY(cudaMemcpyAsync(hhead.data() + nb, Eall, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  BP_TRY(cudaStreamSynchronize(st));
+  std::vector<double> hout(4 * (size_t)nb + 3 * (size_t)nb * nb);
+  const bool singular = bp_final(hsums.data(), hhead.data() + nb, hhead.data(), nb, fdk, in->trunc_bands,
+                                 in->trunc_width, L, hout.data());
+  BP_OK(bp_write_out(hout.data(), nb, in->out_on_device, out, "bandpower_estimate: writing results"));
   if (out->E_maps) {
-    e = cudaMemcpy(out->E_maps, Eall, sizeof(double) * (size_t)Btot * nb,
-                   in->out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaMemcpy(out->E_maps, Eall, sizeof(double) * (size_t)Btot * nb,
+                                     in->out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return wf_cuda_fail(e, "bandpower_estimate: reading E_maps");
   }
-  if (nfd == 0) return solve_status;
-  if (hflag) return wf_fail(WF_ENONFINITE, "bandpower_estimate: the Fisher matrix is singular");
+  if (nfd > 0 && singular) return wf_fail(WF_ENONFINITE, "bandpower_estimate: the Fisher matrix is singular");
   return solve_status;
+}
+
+extern "C" size_t bandpower_sums_len(int n_bands, int n_rows) {
+  if (n_bands < 1 || n_rows < 0) return 0;
+  return bp_sums_len(n_bands, n_rows);
+}
+
+extern "C" wf_status bandpower_sums(const double* E_maps, int n_bands, int n_sim, int n_fd, int n_rows,
+                                    double* sums) {
+  if (!E_maps || !sums) return wf_fail(WF_EINVAL, "bandpower_sums: null argument");
+  if (n_bands < 1 || n_bands > 64 || n_sim < 1 || n_fd < 0 || n_fd > n_sim || n_rows < 0 || (n_fd > 0 && n_rows < 1))
+    return wf_fail(WF_EINVAL, "bandpower_sums: n_bands = %d, n_sim = %d, n_fd = %d, n_rows = %d", n_bands, n_sim,
+                   n_fd, n_rows);
+  const size_t len = bp_sums_len(n_bands, n_rows);
+  for (size_t i = 0; i < len; ++i) sums[i] = bp_sum_entry(E_maps, n_bands, n_sim, n_fd, i);
+  return WF_OK;
+}
+
+extern "C" wf_status bandpower_combine(const double* sums, const double* E_data, const double* theta_fid,
+                                       const wf_bandpower_in* rules, wf_bandpower_out* out) {
+  if (!sums || !E_data || !theta_fid || !rules || !out) return wf_fail(WF_EINVAL, "bandpower_combine: null argument");
+  const int nb = rules->n_bands, L = rules->leak_split;
+  if (nb < 1 || nb > 64) return wf_fail(WF_EINVAL, "bandpower_combine: n_bands = %d outside [1, 64]", nb);
+  if (L < 0 || L >= nb) return wf_fail(WF_EINVAL, "bandpower_combine: leak_split = %d", L);
+  if (rules->trunc_bands < 0 || rules->trunc_bands > (L > 0 ? L : nb) || rules->trunc_width < 0)
+    return wf_fail(WF_EINVAL, "bandpower_combine: trunc_bands = %d, trunc_width = %d", rules->trunc_bands,
+                   rules->trunc_width);
+  if (rules->out_on_device != 0 && rules->out_on_device != 1)
+    return wf_fail(WF_EINVAL, "bandpower_combine: out_on_device = %d is not 0 or 1", rules->out_on_device);
+  if (!out->theta_fid || !out->E || !out->bias || !out->fisher || !out->cov || !out->theta_hat || !out->cov_E)
+    return wf_fail(WF_EINVAL, "bandpower_combine: null output array");
+  const double J = sums[0], Jfd = sums[1];
+  if (!(J >= 1.0) || !(Jfd >= 0.0) || Jfd > J || J != floor(J) || Jfd != floor(Jfd))
+    return wf_fail(WF_EINVAL, "bandpower_combine: the sums hold J = %g simulations, J_fd = %g Fisher ones", J, Jfd);
+  for (int l = 0; l < nb; ++l)
+    if (!(theta_fid[l] > 0.0)) return wf_fail(WF_EINVAL, "bandpower_combine: theta_fid[%d] = %g", l, theta_fid[l]);
+  int fdb[64], fdk[64], nbF = 0;
+  wf_status rs = bp_rows(rules, "bandpower_combine", fdb, fdk, &nbF);
+  if (rs != WF_OK) return rs;
+  std::vector<double> hout(4 * (size_t)nb + 3 * (size_t)nb * nb);
+  const bool singular = bp_final(sums, E_data, theta_fid, nb, fdk, rules->trunc_bands, rules->trunc_width, L,
+                                 hout.data());
+  rs = bp_write_out(hout.data(), nb, rules->out_on_device, out, "bandpower_combine: writing results");
+  if (rs != WF_OK) return rs;
+  if (Jfd > 0.0 && singular) return wf_fail(WF_ENONFINITE, "bandpower_combine: the Fisher matrix is singular");
+  return WF_OK;
 }
 
 // P <- P * q[l] on the modes of band l (others unchanged), in the input dtype.

@@ -51,6 +51,7 @@ struct WfSolver {
   double g_gtol2, g_dchi2, g_c1, g_c2;
   long long g_spin;
   int started;
+  int graph_pending;  // capture the iteration graph after the next plain iteration (a resumed solve)
   cudaStream_t work, g_stream;  // stream in use; stream the graph was captured on
   long long iters;     // iterations launched since the last start
   wf_opts o;
@@ -758,6 +759,92 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   return WF_OK;
 }
 
+// Scalar-step arguments and the convergence ring of a solve with options o.
+static wf_status setup_args(wf_problem* p, WfSolver* S, const wf_opts* o) {
+  const int m = o->lbfgs_m;
+  WfScalarArgs& A = S->A;
+  A.gtol2 = o->gtol_rel * o->gtol_rel;
+  A.dchi2 = o->dchi2_abs;
+  A.max_iter = o->max_iter;
+  A.m = m;
+  A.ls = o->line_search;
+  A.c1 = o->c1;
+  A.c2 = o->c2;
+  A.ntile = p->g.ntile;
+  A.nrb = p->g.nrb;
+  A.ncomb = p->g.ncomb;
+  A.maxblk = p->g.maxblk;
+  A.phase = WF_PH_ITER;
+  A.init = 0;
+  A.hcap = 0;
+  A.hist = nullptr;
+  if (o->history > 0) {  // the convergence ring, kept (and grown) across solves
+    if (S->hist_cap < o->history) {
+      wf_free(p->h, S->hist);
+      S->hist = nullptr;
+      S->hist_cap = 0;
+      const wf_status rs =
+          wf_alloc(p->h, (void**)&S->hist, sizeof(double) * 5 * (size_t)o->history * p->count, "history ring");
+      if (rs != WF_OK) return rs;
+      S->hist_cap = o->history;
+    }
+    A.hcap = o->history;
+    A.hist = S->hist;
+  }
+  return WF_OK;
+}
+
+// Capture `chunk` iterations in a CUDA graph on st (unless the graph in hand
+// was captured with the same settings).  Every kernel's attributes must have
+// been set outside capture: one plain iteration has run before.
+// Whether the graph in hand was captured with the solve's current settings.
+static bool graph_current(const wf_problem* p, const WfSolver* S, cudaStream_t st) {
+  const wf_opts* o = &S->o;
+  const WfScalarArgs& A = S->A;
+  const int chunk = o->check_every > 0 ? o->check_every : 16;
+  return S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter && S->g_gtol2 == A.gtol2 &&
+         S->g_dchi2 == A.dchi2 && S->g_m == o->lbfgs_m && S->g_ls == A.ls && S->g_c1 == A.c1 && S->g_c2 == A.c2 &&
+         S->g_inject == o->inject_timeout_map && S->g_spin == o->spin_limit && S->g_variant == variant_code(p->g) &&
+         S->g_hist == A.hist && S->g_hcap == A.hcap && S->g_stream == st;
+}
+
+template <typename T>
+static wf_status build_graph(wf_problem* p, WfSolver* S, cudaStream_t st) {
+  const wf_opts* o = &S->o;
+  const WfScalarArgs& A = S->A;
+  const WfBufs b = wf_bufs(p);
+  const WfLbBufs lb = lb_bufs<T>(S);
+  const int m = o->lbfgs_m;
+  const int chunk = o->check_every > 0 ? o->check_every : 16;
+  if (graph_current(p, S, st)) return WF_OK;
+  if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
+  cudaGraph_t graph;
+  WF_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  cudaError_t ce = cudaSuccess;
+  for (int i = 0; i < chunk && ce == cudaSuccess; ++i) ce = iteration<T>(p, b, lb, A, S, st);
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (ce != cudaSuccess) return wf_cuda_fail(ce, "wf_solver: graph capture");
+  if (ee != cudaSuccess) return wf_cuda_fail(ee, "wf_solver: end capture");
+  ce = cudaGraphInstantiate(&S->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) { S->exec = nullptr; return wf_cuda_fail(ce, "wf_solver: graph instantiate"); }
+  S->g_chunk = chunk;
+  S->g_maxit = o->max_iter;
+  S->g_gtol2 = A.gtol2;
+  S->g_dchi2 = A.dchi2;
+  S->g_m = m;
+  S->g_ls = A.ls;
+  S->g_c1 = A.c1;
+  S->g_c2 = A.c2;
+  S->g_inject = o->inject_timeout_map;
+  S->g_variant = variant_code(p->g);
+  S->g_spin = o->spin_limit;
+  S->g_hist = A.hist;
+  S->g_hcap = A.hcap;
+  S->g_stream = st;
+  return WF_OK;
+}
+
 // Start of an inner round of the refined solve: the correction starts at 0
 // with the FP64 gradient g64 of the outer state (see k_refine_seed).
 struct WfSeed {
@@ -783,34 +870,9 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0, con
   S->work = st;
   WfBufs b = wf_bufs(p);
   WfLbBufs lb = lb_bufs<T>(S);
+  rs = setup_args(p, S, o);
+  if (rs != WF_OK) return rs;
   WfScalarArgs& A = S->A;
-  A.gtol2 = o->gtol_rel * o->gtol_rel;
-  A.dchi2 = o->dchi2_abs;
-  A.max_iter = o->max_iter;
-  A.m = m;
-  A.ls = o->line_search;
-  A.c1 = o->c1;
-  A.c2 = o->c2;
-  A.ntile = p->g.ntile;
-  A.nrb = p->g.nrb;
-  A.ncomb = p->g.ncomb;
-  A.maxblk = p->g.maxblk;
-  A.phase = WF_PH_ITER;
-  A.init = 0;
-  A.hcap = 0;
-  A.hist = nullptr;
-  if (o->history > 0) {  // the convergence ring, kept (and grown) across solves
-    if (S->hist_cap < o->history) {
-      wf_free(p->h, S->hist);
-      S->hist = nullptr;
-      S->hist_cap = 0;
-      rs = wf_alloc(p->h, (void**)&S->hist, sizeof(double) * 5 * (size_t)o->history * p->count, "history ring");
-      if (rs != WF_OK) return rs;
-      S->hist_cap = o->history;
-    }
-    A.hcap = o->history;
-    A.hist = S->hist;
-  }
   WF_TRY(cudaEventRecord(S->ev_in, us));
   WF_TRY(cudaStreamWaitEvent(st, S->ev_in, 0));
   if (s0 && !seed) WF_TRY(wf_launch_pack<T>(p->g, p->count, s0, S->s, st));
@@ -835,42 +897,15 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0, con
   } else {
     WF_TRY(refresh<T>(p, b, lb, A, 1, S, st));
   }
-  const int chunk = o->check_every > 0 ? o->check_every : 16;
-  if (o->use_graphs && !(S->exec && S->g_chunk == chunk && S->g_maxit == o->max_iter &&
-                         S->g_gtol2 == A.gtol2 && S->g_dchi2 == A.dchi2 && S->g_m == m && S->g_ls == A.ls &&
-                         S->g_c1 == A.c1 && S->g_c2 == A.c2 && S->g_inject == o->inject_timeout_map &&
-                         S->g_spin == o->spin_limit && S->g_variant == variant_code(p->g) &&
-                         S->g_hist == A.hist && S->g_hcap == A.hcap)) {
-    if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
-    // Set every kernel's attributes outside capture: one iteration, then undo
-    // nothing (it is a genuine iteration of the solve).
+  if (o->use_graphs && !graph_current(p, S, st)) {
+    // Set every kernel's attributes outside capture: one iteration (a genuine
+    // iteration of the solve), then the graph.
     WF_TRY(iteration<T>(p, b, lb, A, S, st));
     S->iters += 1;
-    cudaGraph_t graph;
-    WF_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-    cudaError_t ce = cudaSuccess;
-    for (int i = 0; i < chunk && ce == cudaSuccess; ++i) ce = iteration<T>(p, b, lb, A, S, st);
-    cudaError_t ee = cudaStreamEndCapture(st, &graph);
-    if (ce != cudaSuccess) return wf_cuda_fail(ce, "wf_solver_start: capture");
-    if (ee != cudaSuccess) return wf_cuda_fail(ee, "wf_solver_start: end capture");
-    ce = cudaGraphInstantiate(&S->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) { S->exec = nullptr; return wf_cuda_fail(ce, "wf_solver_start: graph instantiate"); }
-    S->g_chunk = chunk;
-    S->g_maxit = o->max_iter;
-    S->g_gtol2 = A.gtol2;
-    S->g_dchi2 = A.dchi2;
-    S->g_m = m;
-    S->g_ls = A.ls;
-    S->g_c1 = A.c1;
-    S->g_c2 = A.c2;
-    S->g_inject = o->inject_timeout_map;
-    S->g_variant = variant_code(p->g);
-    S->g_spin = o->spin_limit;
-    S->g_hist = A.hist;
-    S->g_hcap = A.hcap;
-    S->g_stream = st;
+    rs = build_graph<T>(p, S, st);
+    if (rs != WF_OK) return rs;
   }
+  S->graph_pending = 0;
   S->started = 1;
   return WF_OK;
 }
@@ -894,7 +929,16 @@ static wf_status step_impl(wf_problem* p, int n_iter, int* n_active) {
       const int to_refresh = o->refresh_every - (int)(S->iters % o->refresh_every);
       if (to_refresh < left) left = to_refresh;
     }
-    if (o->use_graphs && S->exec && left >= chunk) {
+    if (o->use_graphs && S->graph_pending && left > chunk) {  // a resumed solve: one plain iteration, then capture
+      WF_TRY(iteration<T>(p, b, lb, S->A, S, st));
+      done += 1;
+      S->iters += 1;
+      const wf_status rs = build_graph<T>(p, S, st);
+      if (rs != WF_OK) return rs;
+      S->graph_pending = 0;
+      continue;
+    }
+    if (o->use_graphs && S->exec && !S->graph_pending && left >= chunk) {
       WF_TRY(cudaGraphLaunch(S->exec, st));
       done += chunk;
       S->iters += chunk;
@@ -1288,6 +1332,128 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
   }
   if (us) cudaStreamSynchronize(us);
   return worst;
+}
+
+// Checkpoint of a started solve: header, the per-map scalar state, then the
+// state s, the gradient g and the 2m stored vectors of the ring (packed, the
+// working type), each starting on a 256-byte boundary.
+struct WfStateHeader {
+  char magic[8];
+  int n, C, precision, count, lbfgs_m, variant;
+  long long iters;
+  size_t vbytes;  // bytes of one packed vector set (all maps)
+  wf_opts o;      // the solve's options (stream not kept)
+};
+static const char kWfStateMagic[8] = {'W', 'F', 'S', 'T', 'A', 'T', 'E', '1'};
+static size_t up256s(size_t x) { return (x + 255) & ~(size_t)255; }
+static size_t state_bytes(const wf_problem* p, int m, size_t* off_st, size_t* off_vec) {
+  const size_t vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;
+  *off_st = up256s(sizeof(WfStateHeader));
+  *off_vec = *off_st + up256s(sizeof(WfLbMap) * p->count);
+  return *off_vec + (2 + 2 * (size_t)m) * up256s(vbytes);
+}
+
+extern "C" wf_status wf_solver_state_size(const wf_problem* p, size_t* bytes) {
+  if (!p || !bytes) return wf_fail(WF_EINVAL, "wf_solver_state_size: null argument");
+  if (!p->solver || !p->solver->started) return wf_fail(WF_EINVAL, "wf_solver_state_size: no solve started");
+  size_t a, b;
+  *bytes = state_bytes(p, p->solver->o.lbfgs_m, &a, &b);
+  return WF_OK;
+}
+
+extern "C" wf_status wf_solver_export(wf_problem* p, void* dst, size_t bytes) {
+  if (!p || !dst) return wf_fail(WF_EINVAL, "wf_solver_export: null argument");
+  WfSolver* S = p->solver;
+  if (!S || !S->started) return wf_fail(WF_EINVAL, "wf_solver_export: no solve started");
+  const int m = S->o.lbfgs_m;
+  size_t off_st, off_vec;
+  const size_t need = state_bytes(p, m, &off_st, &off_vec);
+  if (bytes < need) return wf_fail(WF_EINVAL, "wf_solver_export: %zu bytes given, %zu needed", bytes, need);
+  WfStateHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kWfStateMagic, 8);
+  hd.n = p->n;
+  hd.C = p->C;
+  hd.precision = p->precision;
+  hd.count = p->count;
+  hd.lbfgs_m = m;
+  hd.variant = variant_code(p->g);
+  hd.iters = S->iters;
+  hd.vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;
+  hd.o = S->o;
+  hd.o.stream = nullptr;
+  cudaStream_t st = S->work;
+  char* out = (char*)dst;
+  WF_TRY(cudaStreamSynchronize(st));
+  WF_TRY(cudaMemcpy(out, &hd, sizeof hd, cudaMemcpyDefault));
+  WF_TRY(cudaMemcpy(out + off_st, S->st, sizeof(WfLbMap) * p->count, cudaMemcpyDefault));
+  const void* vecs[2] = {S->s, S->g};
+  const size_t vs = up256s(hd.vbytes);
+  for (int i = 0; i < 2; ++i) WF_TRY(cudaMemcpy(out + off_vec + i * vs, vecs[i], hd.vbytes, cudaMemcpyDefault));
+  for (int i = 0; i < 2 * m; ++i)
+    WF_TRY(cudaMemcpy(out + off_vec + (2 + (size_t)i) * vs, (const char*)S->ring + (size_t)i * hd.vbytes, hd.vbytes,
+                      cudaMemcpyDefault));
+  return WF_OK;
+}
+
+template <typename T>
+static wf_status import_impl(wf_problem* p, const WfStateHeader& hd, const char* in, void* stream) {
+  const int m = hd.lbfgs_m;
+  wf_status rs = ensure_solver(p, m);
+  if (rs != WF_OK) return rs;
+  WfSolver* S = p->solver;
+  S->o = hd.o;
+  S->o.stream = stream;
+  S->iters = hd.iters;
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStream_t st = wf_capturable(us) ? us : S->stream;
+  if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
+  S->work = st;
+  p->g = variant_geo(wf_make_geo(p->n, p->C), hd.variant);
+  rs = setup_args(p, S, &S->o);
+  if (rs != WF_OK) return rs;
+  size_t off_st, off_vec;
+  state_bytes(p, m, &off_st, &off_vec);
+  const size_t vs = up256s(hd.vbytes);
+  WF_TRY(cudaEventRecord(S->ev_in, us));
+  WF_TRY(cudaStreamWaitEvent(st, S->ev_in, 0));
+  WF_TRY(cudaMemcpyAsync(S->st, in + off_st, sizeof(WfLbMap) * p->count, cudaMemcpyDefault, st));
+  void* vecs[2] = {S->s, S->g};
+  for (int i = 0; i < 2; ++i) WF_TRY(cudaMemcpyAsync(vecs[i], in + off_vec + i * vs, hd.vbytes, cudaMemcpyDefault, st));
+  for (int i = 0; i < 2 * m; ++i)
+    WF_TRY(cudaMemcpyAsync((char*)S->ring + (size_t)i * hd.vbytes, in + off_vec + (2 + (size_t)i) * vs, hd.vbytes,
+                           cudaMemcpyDefault, st));
+  WF_TRY(cudaStreamSynchronize(st));  // the source may be pageable host memory the caller frees next
+  S->graph_pending = S->o.use_graphs ? 1 : 0;
+  S->started = 1;
+  return WF_OK;
+}
+
+extern "C" wf_status wf_solver_import(wf_problem* p, const void* src, size_t bytes, void* stream) {
+  if (!p || !src) return wf_fail(WF_EINVAL, "wf_solver_import: null argument");
+  if (bytes < sizeof(WfStateHeader)) return wf_fail(WF_EINVAL, "wf_solver_import: %zu bytes is no checkpoint", bytes);
+  WfStateHeader hd;
+  WF_TRY(cudaMemcpy(&hd, src, sizeof hd, cudaMemcpyDefault));
+  if (memcmp(hd.magic, kWfStateMagic, 8) != 0) return wf_fail(WF_EINVAL, "wf_solver_import: not a solver checkpoint");
+  if (hd.n != p->n || hd.C != p->C || hd.precision != p->precision || hd.count != p->count)
+    return wf_fail(WF_EINVAL,
+                   "wf_solver_import: checkpoint of n = %d, C = %d, precision %d, %d maps; problem has %d, %d, %d, %d",
+                   hd.n, hd.C, hd.precision, hd.count, p->n, p->C, p->precision, p->count);
+  if (!variant_valid(hd.variant) || hd.lbfgs_m < 1 || hd.lbfgs_m > WF_MAXM ||
+      hd.vbytes != (size_t)p->count * p->C * p->n * p->n * p->elt)
+    return wf_fail(WF_EINVAL, "wf_solver_import: corrupt checkpoint header");
+  size_t off_st, off_vec;
+  const size_t need = state_bytes(p, hd.lbfgs_m, &off_st, &off_vec);
+  if (bytes < need) return wf_fail(WF_EINVAL, "wf_solver_import: %zu bytes given, %zu needed", bytes, need);
+  wf_opts o = hd.o;
+  o.stream = stream;
+  o.fft_variant = 0;
+  o.inject_timeout_map = 0;
+  wf_status rs = check_opts(p, &o);
+  if (rs != WF_OK) return rs;
+  if (hd.o.inject_timeout_map != 0) return wf_fail(WF_EINVAL, "wf_solver_import: checkpoint of a diagnostic run");
+  return p->precision == WF_FP64 ? import_impl<double>(p, hd, (const char*)src, stream)
+                                 : import_impl<float>(p, hd, (const char*)src, stream);
 }
 
 extern "C" wf_status wf_problem_variant(const wf_problem* p, int* variant) {

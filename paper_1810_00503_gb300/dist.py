@@ -10,8 +10,12 @@ eq. blmv, fisher, eq:wfmv):
     Theta  = Theta_fid + F^-1 (E - b)
 With the leakage-bias form of App. C (leak_split = L: E bands 0..L-1 with
 per-band Fisher maps, one joint map of the B bands per Fisher simulation) the
-Fisher sums have L + 1 rows, and F keeps the EE block and the B diagonal only.
-No data path crosses GPUs; only these sums do.
+Fisher sums have L + 1 rows, and F keeps the EE block and the B diagonal only;
+with sampled Fisher columns (fd_bands) the sums have a row per sampled band and
+the other columns are interpolated.  The sums and the estimator are the
+library's (bandpower_sums, bandpower_combine); this module only splits the
+simulations, all-reduces and marshals.  No data path crosses GPUs; only these
+sums do.
 """
 from __future__ import annotations
 
@@ -36,71 +40,44 @@ def assignment(n_sim: int, n_fd: int, world: int, rank: int):
     return sims, (fd_lo, fd_hi)
 
 
-def fisher_rows(n_bands: int, leak_split: int = 0) -> int:
-    """Fisher-map rows of a rank's run: one per band, or the E bands plus the
-    joint B row of the leakage-bias form."""
-    return leak_split + 1 if leak_split > 0 else n_bands
+def fisher_rows(n_bands: int, leak_split: int = 0, fd_bands=None) -> int:
+    """Fisher-map rows of a rank's run: one per band with Fisher maps (every
+    band, the listed fd_bands, or the E bands), plus the joint B row of the
+    leakage-bias form."""
+    from . import wf
+    return wf.fisher_rows(n_bands, leak_split, fd_bands)
 
 
-def local_sums(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int, leak_split: int = 0) -> np.ndarray:
-    """Partial sums of one rank from its per-map band energies, rows ordered as
-    bandpower_estimate writes them: data, n_sim simulations, then n_R x n_fd
-    Fisher maps (n_R = fisher_rows; the j-th reusing simulation j).  Returns one
-    FP64 vector: [J, J_fd, sum E_j (nb), sum E_j E_j^T (nb^2),
-    sum_j (E(d_kj) - E(d_j)) (n_R x nb, [k][l])]."""
-    nb = n_bands
-    nR = fisher_rows(nb, leak_split)
-    Es = E_maps[1:1 + n_sim]
-    Ef = E_maps[1 + n_sim:].reshape(nR, n_fd, nb)  # [k][j][l]
-    diff = (Ef - Es[None, :n_fd, :]).sum(axis=1)      # [k][l]
-    return np.concatenate([[float(n_sim), float(n_fd)], Es.sum(axis=0), (Es.T @ Es).ravel(), diff.ravel()])
+def local_sums(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int, leak_split: int = 0,
+               fd_bands=None) -> np.ndarray:
+    """This rank's partial sums (the library's bandpower_sums) from its per-map
+    band energies, rows ordered as bandpower_estimate writes them: data, n_sim
+    simulations, then the Fisher maps."""
+    from . import wf
+    return wf.bandpower_sums(E_maps, n_sim, n_fd, fisher_rows(n_bands, leak_split, fd_bands))
 
 
 def combine(total: np.ndarray, E_data: np.ndarray, theta_fid: np.ndarray, leak_split: int = 0,
-            trunc=(0, 0)) -> dict:
-    """Band-power estimate from the all-reduced sums of `local_sums`.  Fisher
-    terms as bandpower_estimate forms them: column l' from Fisher row l' (or,
-    with leak_split = L, the E columns from rows 0..L-1 restricted to the E
-    rows and each B band's diagonal from the joint row L); then trunc = (n, w)
-    zeroes F[l][l'] for l, l' < n with |l - l'| > w."""
-    nb = theta_fid.size
-    L = int(leak_split)
-    J, Jfd = total[0], total[1]
-    S1 = total[2:2 + nb]
-    S2 = total[2 + nb:2 + nb + nb * nb].reshape(nb, nb)
-    D = total[2 + nb + nb * nb:].reshape(fisher_rows(nb, L), nb)  # [k][l]
-    b = S1 / J
-    if L > 0:
-        F = np.zeros((nb, nb))
-        F[:L, :L] = D[:L, :L].T / Jfd / theta_fid[None, :L]
-        for l in range(L, nb):
-            F[l, l] = D[L, l] / Jfd / theta_fid[l]
-    else:
-        F = D.T / Jfd / theta_fid[None, :]
-    n_t, w = int(trunc[0]), int(trunc[1])
-    for l in range(min(n_t, nb)):
-        for lp in range(min(n_t, nb)):
-            if abs(l - lp) > w:
-                F[l, lp] = 0.0
-    covE = (S2 - J * np.outer(b, b)) / (J - 1)
-    cov = np.linalg.inv(F)
-    return dict(bias=b, fisher=F, cov=cov, cov_E=covE, theta_hat=theta_fid + cov @ (E_data - b),
-                theta_fid=theta_fid, E=E_data)
+            trunc=(0, 0), fd_bands=None) -> dict:
+    """Band-power estimate from the all-reduced sums (the library's
+    bandpower_combine, the code bandpower_estimate ends with)."""
+    from . import wf
+    return wf.bandpower_combine(total, E_data, theta_fid, leak_split=leak_split, fd_bands=fd_bands, trunc=trunc)
 
 
 def reduce_bandpower(E_maps: np.ndarray, n_sim: int, n_bands: int, n_fd: int, theta_fid: np.ndarray,
-                     group=None, leak_split: int = 0, trunc=(0, 0)) -> dict:
+                     group=None, leak_split: int = 0, trunc=(0, 0), fd_bands=None) -> dict:
     """All-reduce the rank's partial sums (torch.distributed, any backend) and
     combine them.  E_maps: this rank's per-map energies; the data map's row 0
     is taken from rank 0."""
     import torch
     import torch.distributed as dist
-    part = torch.as_tensor(local_sums(E_maps, n_sim, n_bands, n_fd, leak_split), dtype=torch.float64)
+    part = torch.as_tensor(local_sums(E_maps, n_sim, n_bands, n_fd, leak_split, fd_bands), dtype=torch.float64)
     e0 = torch.as_tensor(E_maps[0], dtype=torch.float64).clone()
     if dist.is_available() and dist.is_initialized():
         dist.all_reduce(part, group=group)
         dist.broadcast(e0, src=0, group=group)
-    return combine(part.numpy(), e0.numpy(), np.asarray(theta_fid, dtype=np.float64), leak_split, trunc)
+    return combine(part.numpy(), e0.numpy(), np.asarray(theta_fid, dtype=np.float64), leak_split, trunc, fd_bands)
 
 
 def estimate_on_rank(d, mask, Ninv, P, band, n_bands, n_sim, n_fd, world, rank, seed, group=None, **opts):
@@ -111,11 +88,9 @@ def estimate_on_rank(d, mask, Ninv, P, band, n_bands, n_sim, n_fd, world, rank, 
     sums.  Returns (estimate, this rank's per-map stats); the estimate is the
     same on every rank and equals the single-process one."""
     from . import wf
-    if opts.get("fd_bands") is not None:
-        raise ValueError("estimate_on_rank: every band needs Fisher maps (fd_bands is not supported)")
     sims, (fd_lo, fd_hi) = assignment(n_sim, n_fd, world, rank)
     res, stats = wf.bandpower_estimate(d, mask, Ninv, P, band, n_bands, None, None, None, n_sim=len(sims),
                                        n_fd=fd_hi - fd_lo, sim_index=sims, seed=seed, **opts)
     est = reduce_bandpower(res["E_maps"], len(sims), n_bands, fd_hi - fd_lo, res["theta_fid"], group,
-                           opts.get("leak_split", 0), opts.get("trunc", (0, 0)))
+                           opts.get("leak_split", 0), opts.get("trunc", (0, 0)), opts.get("fd_bands"))
     return est, stats

@@ -27,7 +27,8 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_eval_noalloc", "bandpower_estimate", "wf_problem_set_band_scale", "wf_eval_bands",
            "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table",
            "bandpower_iterate", "wf_problem_variant", "wf_alu_peak", "wf_solver_history",
-           "wf_map_solve_refined"]
+           "wf_map_solve_refined", "bandpower_sums_len", "bandpower_sums", "bandpower_combine",
+           "wf_solver_state_size", "wf_solver_export", "wf_solver_import"]
 
 
 class WfMap(ctypes.Structure):
@@ -123,9 +124,17 @@ def lib() -> ctypes.CDLL:
     L.bandpower_iterate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
                                     ctypes.POINTER(WfOpts), i, d, d, vp, ctypes.POINTER(d),
                                     ctypes.POINTER(WfBandpowerOut), ctypes.POINTER(WfSolveStats)]
+    L.bandpower_sums.argtypes = [ctypes.POINTER(d), i, i, i, i, ctypes.POINTER(d)]
+    L.bandpower_combine.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
+                                    ctypes.POINTER(WfBandpowerIn), ctypes.POINTER(WfBandpowerOut)]
+    L.bandpower_sums_len.argtypes = [i, i]
+    L.wf_solver_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.wf_solver_export.argtypes = [vp, vp, ctypes.c_size_t]
+    L.wf_solver_import.argtypes = [vp, vp, ctypes.c_size_t, vp]
     for name in EXPORTS:
-        if name not in ("wf_last_error", "wf_opts_default"):
+        if name not in ("wf_last_error", "wf_opts_default", "bandpower_sums_len"):
             getattr(L, name).restype = ctypes.c_int
+    L.bandpower_sums_len.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -430,6 +439,58 @@ def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_
     return res, stats, hist, P_out
 
 
+def fisher_rows(n_bands, leak_split=0, fd_bands=None):
+    """Fisher-map rows of a band-power call (the rows of its u): the bands with
+    per-band Fisher maps, plus the joint B row of the leakage-bias form."""
+    L = int(leak_split)
+    per_band = len(fd_bands) if fd_bands is not None else (L if L > 0 else int(n_bands))
+    return per_band + (1 if L > 0 else 0)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def bandpower_sums(E_maps, n_sim, n_fd, n_rows):
+    """bandpower_sums: the partial-sum vector of one share of the simulations
+    from its per-map band energies (rows: data, n_sim simulations, n_rows x
+    n_fd Fisher maps).  Returns a float64 numpy vector; vectors of different
+    shares add entry by entry."""
+    E = np.ascontiguousarray(E_maps, dtype=np.float64)
+    if E.ndim != 2 or E.shape[0] != 1 + int(n_sim) + int(n_rows) * int(n_fd):
+        raise ValueError(f"E_maps has shape {E.shape}, expected (1 + n_sim + n_rows * n_fd, n_bands)")
+    L = lib()
+    out = np.zeros(L.bandpower_sums_len(E.shape[1], int(n_rows)))
+    _check(L.bandpower_sums(_dptr(E), E.shape[1], int(n_sim), int(n_fd), int(n_rows), _dptr(out)))
+    return out
+
+
+def bandpower_combine(sums, E_data, theta_fid, leak_split=0, fd_bands=None, trunc=(0, 0)):
+    """bandpower_combine: the band-power estimate from summed partial sums
+    (host arrays in, numpy arrays out), with the Fisher-row rules of the
+    contributing calls (leak_split, fd_bands, trunc)."""
+    th = np.ascontiguousarray(theta_fid, dtype=np.float64)
+    Ed = np.ascontiguousarray(E_data, dtype=np.float64)
+    S = np.ascontiguousarray(sums, dtype=np.float64)
+    nb = th.size
+    L = lib()
+    if Ed.shape != (nb,) or S.shape != (L.bandpower_sums_len(nb, fisher_rows(nb, leak_split, fd_bands)),):
+        raise ValueError("E_data needs n_bands entries and sums the length of the rules' partial sums")
+    fdb = None if fd_bands is None else np.ascontiguousarray(fd_bands, dtype=np.int32)
+    rules = WfBandpowerIn(n_bands=nb, leak_split=int(leak_split),
+                          fd_bands=None if fdb is None else fdb.ctypes.data,
+                          n_fd_bands=0 if fdb is None else int(fdb.size), trunc_bands=int(trunc[0]),
+                          trunc_width=int(trunc[1]), out_on_device=0)
+    sizes = (("theta_fid", nb), ("E", nb), ("bias", nb), ("fisher", nb * nb), ("cov", nb * nb),
+             ("theta_hat", nb), ("cov_E", nb * nb))
+    arrs = {k: np.zeros(sz) for k, sz in sizes}
+    bo = WfBandpowerOut(**{k: _dptr(v) for k, v in arrs.items()}, E_maps=None)
+    _check(L.bandpower_combine(_dptr(S), _dptr(Ed), _dptr(th), ctypes.byref(rules), ctypes.byref(bo)))
+    for k in ("fisher", "cov", "cov_E"):
+        arrs[k] = arrs[k].reshape(nb, nb)
+    return arrs
+
+
 class Problem:
     """A prepared batch of maps of one shape (wf_problem_create).
 
@@ -599,6 +660,27 @@ class Problem:
         na = ctypes.c_int(-1)
         _check(lib().wf_solver_step(self._p, int(n_iter), ctypes.byref(na) if sync else None))
         return na.value if sync else None
+
+    def export_state(self, out=None):
+        """wf_solver_state_size + wf_solver_export: the checkpoint of the started
+        solve as a uint8 tensor (a CUDA tensor by default; pass a pinned or
+        plain CPU uint8 tensor of at least that size to keep it on the host)."""
+        import torch
+        n = ctypes.c_size_t()
+        _check(lib().wf_solver_state_size(self._p, ctypes.byref(n)))
+        if out is None:
+            out = torch.empty(int(n.value), dtype=torch.uint8, device="cuda")
+        if out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < n.value:
+            raise ValueError(f"checkpoint buffer must be a contiguous uint8 tensor of >= {n.value} bytes")
+        _check(lib().wf_solver_export(self._p, _ptr(out), int(out.numel())))
+        return out
+
+    def import_state(self, buf, stream=None):
+        """wf_solver_import: resume the solve held in a checkpoint buffer."""
+        import torch
+        if not isinstance(buf, torch.Tensor) or buf.dtype != torch.uint8 or not buf.is_contiguous():
+            raise ValueError("checkpoint buffer must be a contiguous uint8 tensor")
+        _check(lib().wf_solver_import(self._p, _ptr(buf), int(buf.numel()), _stream(stream)))
 
     def profile(self, n_iter):
         """wf_solver_profile: average ms of the six kernels of one iteration."""
