@@ -53,6 +53,8 @@ def parse():
                     help="skip the single-map and 512^2 eval loops, the heterogeneous batch and the ALU peaks")
     ap.add_argument("--fft-variant", type=int, default=0,
                     help="force an FFT-stage variant (wf_opts.fft_variant code); 0 = autotune")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="working precision of the timed iteration (fp64: the plain FP64 path, for its counters)")
     ap.add_argument("--eval-only", action="store_true",
                     help="only the objective+gradient pass (wf_eval) over the batch, for kernel profiles")
     return ap.parse_args()
@@ -60,8 +62,9 @@ def parse():
 
 def config(args, world):
     return {"workload": f"cmb_{args.n}: {args.batch} maps of {args.n}x{args.n} (100 noise-bias + 20 Fisher "
-                        f"simulations), 20 log l-bands, mixed FP32/FP64",
-            "n": args.n, "maps_per_gpu": args.batch, "lbfgs_m": args.m, "precision": "mixed",
+                        f"simulations), 20 log l-bands, "
+                        f"{'FP64' if args.precision == 'fp64' else 'mixed FP32/FP64'}",
+            "n": args.n, "maps_per_gpu": args.batch, "lbfgs_m": args.m, "precision": args.precision,
             "step": "one L-BFGS iteration on every map (1 Hessian-vector evaluation each)",
             "l2_policy": "working set per step (~20 GB) far exceeds the 126 MB L2; no flush needed",
             "parallelism": f"independent batches per GPU x{world}"}
@@ -131,19 +134,21 @@ def make_problem(args, rank, dev):
     B = args.batch
     g = torch.Generator(device=dev)
     g.manual_seed(1000 + rank)
-    Ninv1 = torch.as_tensor(inp.Ninv, dtype=torch.float32, device=dev)
+    wdt = torch.float64 if getattr(args, "precision", "mixed") == "fp64" else torch.float32
+    Ninv1 = torch.as_tensor(inp.Ninv, dtype=wdt, device=dev)
     Ninv = Ninv1.unsqueeze(0).expand(B, -1, -1, -1).contiguous()
     mask = torch.as_tensor(inp.mask, dtype=torch.uint8, device=dev)
-    P = torch.as_tensor(inp.P_half, dtype=torch.float32, device=dev)
-    prob = wf.Problem(torch.zeros_like(Ninv), mask, Ninv, P, precision="mixed", lbfgs_m=args.m)
-    z = torch.randn(B, 1, args.n, args.n, generator=g, device=dev)
+    P = torch.as_tensor(inp.P_half, dtype=wdt, device=dev)
+    prob = wf.Problem(torch.zeros_like(Ninv), mask, Ninv, P, precision=getattr(args, "precision", "mixed"),
+                      lbfgs_m=args.m)
+    z = torch.randn(B, 1, args.n, args.n, generator=g, device=dev, dtype=wdt)
     sig = torch.where(Ninv > 0, torch.rsqrt(torch.clamp(Ninv, min=1e-30)), torch.zeros_like(Ninv))
-    noise = torch.randn(B, 1, args.n, args.n, generator=g, device=dev) * sig
+    noise = torch.randn(B, 1, args.n, args.n, generator=g, device=dev, dtype=wdt) * sig
     d = prob.simulate(z, noise)
     prob.set_data(d)
     torch.cuda.synchronize()
     host = dict(mask=inp.mask, Ninv=inp.Ninv.astype(np.float32), P=inp.P_half.astype(np.float32),
-                d=d.cpu().numpy())
+                d=d.float().cpu().numpy())
     return prob, host
 
 
@@ -345,16 +350,17 @@ def run_eval_shapes(args, dev, hbm):
     return out
 
 
-def run_hetero(args, dev, count=256, n_bands=10):
+def run_hetero(args, dev, count=256, n_bands=10, sizes=(64, 128, 256, 512, 1024)):
     """Heterogeneous batch: `count` independent maps of n in {64, 128, 256,
-    512} (uneven masks, noise levels and spectral slopes), one problem per
-    size solved together by wf_map_solve_many to ||g|| / ||g0|| < 1e-6 in
-    mixed precision; then d chi^2 / d log q for n_bands log-spaced bands at the
-    solutions through the adjoint stage (wf_eval_bands)."""
+    512, 1024} (uneven masks, noise levels and spectral slopes), one problem
+    per size, all solved as one batch by wf_map_solve_many (one CUDA graph per
+    round, a branch per size) to ||g|| / ||g0|| < 1e-6 in mixed precision;
+    then d chi^2 / d log q for n_bands log-spaced bands at the solutions
+    through the adjoint stage (wf_eval_bands)."""
     import numpy as np
     import torch
     from paper_1810_00503_gb300 import synth, wf
-    maps = synth.hetero_batch(count=count, seed=4)
+    maps = synth.hetero_batch(count=count, seed=4, sizes=sizes)
     groups = {}
     for mp in maps:
         groups.setdefault(mp.n, []).append(mp)
@@ -399,8 +405,8 @@ def run_hetero(args, dev, count=256, n_bands=10):
     return {"maps": count, "sizes": per, "seconds": dt, "map_solves_per_s": count / dt,
             "evals_per_s": evals / dt, "stop": "||g||/||g0|| < 1e-6", "statuses": statuses,
             "dchi2_dlogq": {"bands": n_bands, "ms_per_batch": dq_dt * 1e3, "maps_per_s": count / dq_dt},
-            "note": "one problem per size, all sizes solved together by wf_map_solve_many (one stream each); "
-                    "a 2-iteration solve first tunes each shape and captures its graphs"}
+            "note": "one problem per size, all sizes solved as one batch by wf_map_solve_many (each round one "
+                    "graph launch with a branch per size); a 2-iteration solve first tunes each shape"}
 
 
 def run_alu_peaks():
@@ -740,7 +746,7 @@ def main():
     achieved = ab[dom] * B / (kms[dom] / 1000.0) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": r["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic", "config": config(args, world),
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic", "config": config(args, world),
             "gpu_launches": 6 * K,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": measured_traffic(dom, B), "peak_source": peak_src,

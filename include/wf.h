@@ -322,14 +322,17 @@ wf_status wf_solver_profile(wf_problem* p, int n_iter, float* ms);
 wf_status wf_solver_history(const wf_problem* p, double* out, int* counts);
 
 /* MAP solves of several prepared problems at once, typically one per map
- * shape of a heterogeneous batch (Sec. 2.2).  Each problem runs on its own
- * internal stream, ordered after opts->stream, so the shapes' launches overlap
- * on the device; iterations advance round-robin, opts->check_every per
- * problem per round, until every map of every problem has stopped.
- * ps: HOST array of np problems; s_out: HOST array of np device outputs
- * (each [count][C][n][n/2+1] in its problem's working type); stats: HOST array
- * of np HOST arrays (each of its problem's count) or NULL.  Starts from 0.
- * Returns the worst status over all maps; synchronises. */
+ * shape of a heterogeneous batch (Sec. 2.2; the simulations of Sec. 2.5 need
+ * not share a size).  Every problem is started on its own internal stream,
+ * ordered after opts->stream; then opts->check_every iterations of every
+ * problem are captured in one CUDA graph with a parallel branch per problem,
+ * so that each round of the batch is one graph launch (plain launches when
+ * opts->use_graphs is 0) and one read of the active counts, until every map
+ * of every problem has stopped.  Refreshes (opts->refresh_every) run between
+ * rounds.  ps: HOST array of np distinct problems; s_out: HOST array of np
+ * device outputs (each [count][C][n][n/2+1] in its problem's working type);
+ * stats: HOST array of np HOST arrays (each of its problem's count) or NULL.
+ * Starts from 0.  Returns the worst status over all maps; synchronises. */
 wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_opts* opts, void* const* s_out,
                             wf_solve_stats* const* stats);
 

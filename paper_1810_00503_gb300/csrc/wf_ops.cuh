@@ -120,7 +120,12 @@ __device__ __forceinline__ V2<T> wf_pack0(V2<T> X0, V2<T> Xh) { return mk<T>(X0.
 // Apply the per-mode operator to a column tile held as [n][C*TC] in shared
 // memory (element (row j, channel c, column t) at j*C*TC + c*TC + t), tile
 // starting at packed column kx0.  The packed column 0 is unpacked in pairs.
-template <typename T, int C, bool ADJ>
+template <typename T, bool SWP>
+__device__ __forceinline__ int wf_swz(int x) {
+  if constexpr (SWP) return wf_swp<T>(x);
+  else return wf_sw<T>(x);
+}
+template <typename T, int C, bool ADJ, bool SWP = false>
 __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx0, const T* sp, T extra) {
   const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, pitch = h + 1;
   // U elements per trip, their sqrt(P) values loaded before any is used.  A
@@ -147,11 +152,11 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
       if (FULL || j < n) {
         V2<T> v[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = buf[wf_sw<T>(j * CT + c * TC + t)];
+        for (int c = 0; c < C; ++c) v[c] = buf[wf_swz<T, SWP>(j * CT + c * TC + t)];
         wf_mode_op_pre<T, C, ADJ>(v, j, kx, n, a0[u] * extra, C == 2 ? a1[u] * extra : (T)0);
         if (!keep) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) buf[wf_sw<T>(j * CT + c * TC + t)] = v[c];
+          for (int c = 0; c < C; ++c) buf[wf_swz<T, SWP>(j * CT + c * TC + t)] = v[c];
         }
       }
     }
@@ -166,7 +171,7 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
       V2<T> X0[C], Xh[C], X0m[C], Xhm[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const V2<T> Y = buf[wf_sw<T>(j * CT + c * TC)], Ym = buf[wf_sw<T>(jm * CT + c * TC)];
+        const V2<T> Y = buf[wf_swz<T, SWP>(j * CT + c * TC)], Ym = buf[wf_swz<T, SWP>(jm * CT + c * TC)];
         wf_unpack0<T>(Y, Ym, X0[c], Xh[c]);
         wf_unpack0<T>(Ym, Y, X0m[c], Xhm[c]);
       }
@@ -176,8 +181,8 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
       wf_mode_op<T, C, ADJ>(Xhm, jm, h, n, sp, extra);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        buf[wf_sw<T>(j * CT + c * TC)] = wf_pack0<T>(X0[c], Xh[c]);
-        buf[wf_sw<T>(jm * CT + c * TC)] = wf_pack0<T>(X0m[c], Xhm[c]);
+        buf[wf_swz<T, SWP>(j * CT + c * TC)] = wf_pack0<T>(X0[c], Xh[c]);
+        buf[wf_swz<T, SWP>(jm * CT + c * TC)] = wf_pack0<T>(X0m[c], Xhm[c]);
       }
     }
   }
@@ -378,6 +383,55 @@ __device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* sc
   __syncthreads();
 }
 
+// Epilogue of the forward column stage on a transformed, scaled tile `buf`
+// ([n][C TC], swizzled as the passes that produced it: SWP for the ping-pong
+// passes): out = 2 (src - a) for the tile's columns of src, dst (packed or
+// standard layout); the prior partial sum |src|^2 and |out|^2 with the
+// half-plane weights go to slot `slot_ix` of the map's partial sums part_b.
+template <typename T, int C, int IN, bool SWP>
+__device__ __forceinline__ void wf_col_fwd_out(const WfGeo& g, V2<T>* buf, const V2<T>* src, V2<T>* dst, int kx0,
+                                               double* part_b, int slot_ix) {
+  const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC;
+  WfAcc<T> acc = 0, acc2 = 0;  // per-thread partials; FP64 from the block sum on
+  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
+    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
+    const int kx = kx0 + t;
+    const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n);
+    const V2<T> a = buf[wf_swz<T, SWP>(j * CT + c * TC + t)];
+    const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
+    const T m2 = sv.x * sv.x + sv.y * sv.y;
+    const T o2 = o.x * o.x + o.y * o.y;
+    acc += (kx == 0) ? m2 : (T)2 * m2;
+    acc2 += (kx == 0) ? o2 : (T)2 * o2;
+    if constexpr (IN == WF_IN_PK) {
+      dst[((size_t)c * n + j) * h + kx] = o;
+    } else {
+      if (kx == 0) buf[wf_swz<T, SWP>(j * CT + c * TC + t)] = o;
+      else dst[((size_t)c * n + j) * (h + 1) + kx] = o;
+    }
+  }
+  if constexpr (IN == WF_IN_STD) {
+    if (kx0 == 0) {
+      __syncthreads();
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int jm = (n - j) & (n - 1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          V2<T> X0, Xh;
+          wf_unpack0<T>(buf[wf_swz<T, SWP>(j * CT + c * TC)], buf[wf_swz<T, SWP>(jm * CT + c * TC)], X0, Xh);
+          V2<T>* row = dst + ((size_t)c * n + j) * (h + 1);
+          row[0] = X0;
+          row[h] = Xh;
+        }
+      }
+    }
+  }
+  const double tot = wf_block_sum((double)acc);
+  if (threadIdx.x == 0) part_b[(size_t)WF_SLOT_PRIOR * g.maxblk + slot_ix] = tot;
+  const double tot2 = wf_block_sum((double)acc2);
+  if (threadIdx.x == 0) part_b[(size_t)WF_SLOT_OUT2 * g.maxblk + slot_ix] = tot2;
+}
+
 // ---------------------------------------------------------------------------
 // k_col_fwd: scratch tile -> forward FFT along y -> sqrt(P) R^T / n = a ->
 // out = 2 (src - a) (the gradient, or the Hessian-vector product when the row
@@ -399,46 +453,9 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   wf_col_scale<T, C, true>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
   __syncthreads();
   const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
-  const V2<T>* src = (const V2<T>*)src_ + (size_t)b * sstride;
-  V2<T>* dst = (V2<T>*)dst_ + (size_t)b * sstride;
-  WfAcc<T> acc = 0, acc2 = 0;  // per-thread partials; FP64 from the block sum on
-  for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
-    const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-    const int kx = kx0 + t;
-    const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n);
-    const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
-    const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
-    const T m2 = sv.x * sv.x + sv.y * sv.y;
-    const T o2 = o.x * o.x + o.y * o.y;
-    acc += (kx == 0) ? m2 : (T)2 * m2;
-    acc2 += (kx == 0) ? o2 : (T)2 * o2;
-    if constexpr (IN == WF_IN_PK) {
-      dst[((size_t)c * n + j) * h + kx] = o;
-    } else {
-      if (kx == 0) buf[wf_sw<T>(j * CT + c * TC + t)] = o;
-      else dst[((size_t)c * n + j) * (h + 1) + kx] = o;
-    }
-  }
-  if constexpr (IN == WF_IN_STD) {
-    if (kx0 == 0) {
-      __syncthreads();
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int jm = (n - j) & (n - 1);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          V2<T> X0, Xh;
-          wf_unpack0<T>(buf[wf_sw<T>(j * CT + c * TC)], buf[wf_sw<T>(jm * CT + c * TC)], X0, Xh);
-          V2<T>* row = dst + ((size_t)c * n + j) * (h + 1);
-          row[0] = X0;
-          row[h] = Xh;
-        }
-      }
-    }
-  }
-  const double tot = wf_block_sum((double)acc);
-  if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_PRIOR) * g.maxblk + blockIdx.x] = tot;
-  const double tot2 = wf_block_sum((double)acc2);
-  if (threadIdx.x == 0) part[((size_t)b * WF_NSLOT + WF_SLOT_OUT2) * g.maxblk + blockIdx.x] = tot2;
+  wf_col_fwd_out<T, C, IN, false>(g, buf, (const V2<T>*)src_ + (size_t)b * sstride,
+                                  (V2<T>*)dst_ + (size_t)b * sstride, kx0, part + (size_t)b * WF_NSLOT * g.maxblk,
+                                  blockIdx.x);
 }
 
 // Scale the sqrt(P)/n table by sqrt(q_l) on the modes of band l (others 1):

@@ -919,7 +919,9 @@ static wf_status step_impl(wf_problem* p, int n_iter, int* n_active) {
   cudaStream_t st = S->work;
   WfBufs b = wf_bufs(p);
   WfLbBufs lb = lb_bufs<T>(S);
-  const int chunk = S->g_chunk > 0 ? S->g_chunk : 16;
+  // iterations per graph launch: the graph's own count (a resumed solve
+  // captures its graph below, so this is read again after the capture)
+  int chunk = S->g_chunk > 0 ? S->g_chunk : (o->check_every > 0 ? o->check_every : 16);
   int done = 0;
   while (done < n_iter) {
     if (o->refresh_every > 0 && S->iters > 0 && S->iters % o->refresh_every == 0)
@@ -936,6 +938,7 @@ static wf_status step_impl(wf_problem* p, int n_iter, int* n_active) {
       const wf_status rs = build_graph<T>(p, S, st);
       if (rs != WF_OK) return rs;
       S->graph_pending = 0;
+      chunk = S->g_chunk;
       continue;
     }
     if (o->use_graphs && S->exec && !S->graph_pending && left >= chunk) {
@@ -1274,62 +1277,142 @@ extern "C" wf_status wf_map_solve_refined(wf_problem* p, const wf_opts* opts, do
                                  : refined_impl<float>(p, &o, cert_tol, max_rounds, s0, s_out, cert, stats);
 }
 
-// Several problems (typically one per map shape of a heterogeneous batch),
-// each solved on its own stream so that their launches overlap on the device;
-// iterations advance round-robin, check_every per problem per round.
+// Helpers of the batched multi-problem solve: one iteration or one refresh of
+// a started problem, in its working precision.
+template <typename T>
+static cudaError_t iteration_of(wf_problem* p, cudaStream_t st) {
+  WfSolver* S = p->solver;
+  return iteration<T>(p, wf_bufs(p), lb_bufs<T>(S), S->A, S, st);
+}
+static cudaError_t any_iteration(wf_problem* p, cudaStream_t st) {
+  return p->precision == WF_FP64 ? iteration_of<double>(p, st) : iteration_of<float>(p, st);
+}
+static cudaError_t any_refresh(wf_problem* p, cudaStream_t st) {
+  WfSolver* S = p->solver;
+  return p->precision == WF_FP64 ? refresh<double>(p, wf_bufs(p), lb_bufs<double>(S), S->A, 0, S, st)
+                                 : refresh<float>(p, wf_bufs(p), lb_bufs<float>(S), S->A, 0, S, st);
+}
+
+// Several problems (typically one per map shape of a heterogeneous batch)
+// solved as one batch: every problem is started on its own stream (tuning,
+// first gradient, one plain iteration), then check_every iterations of every
+// problem are captured in ONE CUDA graph, a parallel branch per problem, so
+// that each round is one graph launch for the whole batch; the maps of every
+// shape advance together and a problem whose maps have all stopped costs only
+// its kernels' early exits.  The host reads the active counts once per round.
 extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_opts* opts, void* const* s_out,
                                        wf_solve_stats* const* stats) {
   if (!ps || np < 1 || !s_out) return wf_fail(WF_EINVAL, "wf_map_solve_many: null or empty arguments");
   for (int i = 0; i < np; ++i)
     if (!ps[i] || !s_out[i]) return wf_fail(WF_EINVAL, "wf_map_solve_many: problem %d or its output is null", i);
+  for (int i = 0; i < np; ++i)
+    for (int k = 0; k < i; ++k)
+      if (ps[i] == ps[k]) return wf_fail(WF_EINVAL, "wf_map_solve_many: problem %d is listed twice", i);
   wf_opts o;
   if (opts) o = *opts;
   else wf_opts_default(&o);
-  cudaStream_t us = (cudaStream_t)o.stream;
-  cudaEvent_t ready;
-  cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-  if (e != cudaSuccess) return wf_cuda_fail(e, "wf_map_solve_many: event");
-  e = cudaEventRecord(ready, us);
-  wf_opts oi = o;
-  oi.stream = nullptr;  // every problem on its own internal stream
-  wf_status rs = WF_OK;
-  for (int i = 0; i < np && rs == WF_OK && e == cudaSuccess; ++i) {
-    rs = check_opts(ps[i], &oi);
-    if (rs != WF_OK) break;
-    rs = ensure_solver(ps[i], oi.lbfgs_m);
-    if (rs != WF_OK) break;
-    e = cudaStreamWaitEvent(ps[i]->solver->stream, ready, 0);
-    if (e == cudaSuccess)
-      rs = ps[i]->precision == WF_FP64 ? start_impl<double>(ps[i], &oi, nullptr) : start_impl<float>(ps[i], &oi, nullptr);
-  }
-  cudaEventDestroy(ready);
-  if (e != cudaSuccess) return wf_cuda_fail(e, "wf_map_solve_many: ordering");
-  if (rs != WF_OK) return rs;
   const int chunk = o.check_every > 0 ? o.check_every : 16;
-  int* live = (int*)calloc((size_t)np, sizeof(int));
-  if (!live) return wf_fail(WF_ENOMEM, "wf_map_solve_many: host allocation");
-  for (int i = 0; i < np; ++i) live[i] = 1;
+  cudaStream_t us = (cudaStream_t)o.stream;
+  std::vector<cudaEvent_t> ev((size_t)np + 1, nullptr);
+  cudaStream_t bs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (bs) cudaStreamDestroy(bs);
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[np], us);
+  if (e != cudaSuccess) { cleanup(); return wf_cuda_fail(e, "wf_map_solve_many: set-up"); }
+  wf_opts oi = o;
+  oi.stream = nullptr;  // every problem starts on its own internal stream
+  oi.use_graphs = 0;    // the batch graph replaces the per-problem ones
+  oi.inject_timeout_map = 0;
+  wf_status rs = WF_OK;
+  for (int i = 0; i < np && rs == WF_OK; ++i) {
+    rs = check_opts(ps[i], &oi);
+    if (rs == WF_OK) rs = ensure_solver(ps[i], oi.lbfgs_m);
+    if (rs != WF_OK) break;
+    e = cudaStreamWaitEvent(ps[i]->solver->stream, ev[np], 0);
+    if (e != cudaSuccess) { rs = wf_cuda_fail(e, "wf_map_solve_many: ordering"); break; }
+    rs = ps[i]->precision == WF_FP64 ? start_impl<double>(ps[i], &oi, nullptr) : start_impl<float>(ps[i], &oi, nullptr);
+  }
+  // one plain iteration of every problem (every kernel's attributes set outside
+  // capture), then the batch stream waits for all of them
+  for (int i = 0; i < np && rs == WF_OK; ++i) {
+    WfSolver* S = ps[i]->solver;
+    e = any_iteration(ps[i], S->work);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[i], S->work);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, ev[i], 0);
+    if (e != cudaSuccess) rs = wf_cuda_fail(e, "wf_map_solve_many: first iteration");
+    S->iters += 1;
+  }
+  if (rs == WF_OK && o.use_graphs) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[np], bs);
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {  // a branch per problem, forked from and joined to bs
+      cudaStream_t si = ps[i]->solver->work;
+      e = cudaStreamWaitEvent(si, ev[np], 0);
+      for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = any_iteration(ps[i], si);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[i], si);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, ev[i], 0);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(bs, &graph);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      exec = nullptr;
+      rs = wf_cuda_fail(e, "wf_map_solve_many: batch graph");
+    }
+  }
+  std::vector<int> live((size_t)np, 1);
+  std::vector<long long> last_refresh((size_t)np, 0);
   const long long max_rounds = (long long)o.max_iter / chunk + 2;
   for (long long r = 0; r < max_rounds && rs == WF_OK; ++r) {
-    int any = 0;
-    for (int i = 0; i < np && rs == WF_OK; ++i)
-      if (live[i]) rs = wf_solver_step(ps[i], chunk, nullptr);
-    for (int i = 0; i < np && rs == WF_OK; ++i)
-      if (live[i]) {
-        int na = 0;
-        rs = wf_solver_step(ps[i], 0, &na);
-        live[i] = na > 0;
-        any |= live[i];
+    for (int i = 0; i < np && rs == WF_OK; ++i) {  // refreshes that are due, on the batch stream
+      WfSolver* S = ps[i]->solver;
+      if (o.refresh_every > 0 && live[i] && S->iters / o.refresh_every > last_refresh[i]) {
+        last_refresh[i] = S->iters / o.refresh_every;
+        e = any_refresh(ps[i], bs);
+        if (e != cudaSuccess) rs = wf_cuda_fail(e, "wf_map_solve_many: refresh");
       }
+    }
+    if (rs != WF_OK) break;
+    if (exec) {
+      e = cudaGraphLaunch(exec, bs);
+    } else {
+      for (int i = 0; i < np && e == cudaSuccess; ++i)
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = any_iteration(ps[i], bs);
+    }
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+      ps[i]->solver->iters += chunk;
+      e = cudaMemcpyAsync(ps[i]->solver->nact_host, ps[i]->solver->nact, sizeof(int), cudaMemcpyDeviceToHost, bs);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
+    if (e != cudaSuccess) { rs = wf_cuda_fail(e, "wf_map_solve_many: iterations"); break; }
+    int any = 0;
+    for (int i = 0; i < np; ++i) {
+      live[i] = *ps[i]->solver->nact_host > 0;
+      any |= live[i];
+    }
     if (!any) break;
   }
-  free(live);
-  if (rs != WF_OK) return rs;
-  wf_status worst = WF_OK;
-  for (int i = 0; i < np; ++i) {
+  if (rs == WF_OK) {  // the problems' own streams continue after the batch stream
+    e = cudaEventRecord(ev[np], bs);
+    for (int i = 0; i < np && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ps[i]->solver->work, ev[np], 0);
+    if (e != cudaSuccess) rs = wf_cuda_fail(e, "wf_map_solve_many: ordering");
+  }
+  wf_status worst = rs;
+  for (int i = 0; i < np && rs == WF_OK; ++i) {
     const wf_status si = wf_solver_finish(ps[i], s_out[i], nullptr, stats ? stats[i] : nullptr);
     if (si != WF_OK && (worst == WF_OK || worst == WF_ENOTCONVERGED)) worst = si;
   }
+  cudaStreamSynchronize(bs);
+  cleanup();
   if (us) cudaStreamSynchronize(us);
   return worst;
 }
@@ -1382,17 +1465,22 @@ extern "C" wf_status wf_solver_export(wf_problem* p, void* dst, size_t bytes) {
   hd.vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;
   hd.o = S->o;
   hd.o.stream = nullptr;
+  // Every copy is ordered on the solver's stream and finished before the call
+  // returns: a device-to-device cudaMemcpy on the legacy stream would neither
+  // block the host nor order the solver's (non-blocking) stream, so the next
+  // step could overwrite the state while it is being copied.
   cudaStream_t st = S->work;
   char* out = (char*)dst;
-  WF_TRY(cudaStreamSynchronize(st));
-  WF_TRY(cudaMemcpy(out, &hd, sizeof hd, cudaMemcpyDefault));
-  WF_TRY(cudaMemcpy(out + off_st, S->st, sizeof(WfLbMap) * p->count, cudaMemcpyDefault));
+  WF_TRY(cudaMemcpyAsync(out, &hd, sizeof hd, cudaMemcpyDefault, st));
+  WF_TRY(cudaMemcpyAsync(out + off_st, S->st, sizeof(WfLbMap) * p->count, cudaMemcpyDefault, st));
   const void* vecs[2] = {S->s, S->g};
   const size_t vs = up256s(hd.vbytes);
-  for (int i = 0; i < 2; ++i) WF_TRY(cudaMemcpy(out + off_vec + i * vs, vecs[i], hd.vbytes, cudaMemcpyDefault));
+  for (int i = 0; i < 2; ++i)
+    WF_TRY(cudaMemcpyAsync(out + off_vec + i * vs, vecs[i], hd.vbytes, cudaMemcpyDefault, st));
   for (int i = 0; i < 2 * m; ++i)
-    WF_TRY(cudaMemcpy(out + off_vec + (2 + (size_t)i) * vs, (const char*)S->ring + (size_t)i * hd.vbytes, hd.vbytes,
-                      cudaMemcpyDefault));
+    WF_TRY(cudaMemcpyAsync(out + off_vec + (2 + (size_t)i) * vs, (const char*)S->ring + (size_t)i * hd.vbytes,
+                           hd.vbytes, cudaMemcpyDefault, st));
+  WF_TRY(cudaStreamSynchronize(st));
   return WF_OK;
 }
 

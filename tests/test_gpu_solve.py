@@ -218,3 +218,33 @@ def test_bad_line_search_options_rejected(bad):
     prob, host = make_problem([inp], "fp64")
     with pytest.raises(wf.WfError, match="EINVAL"):
         prob.solve(max_iter=3, **bad)
+
+
+def test_mixed_heterogeneous_batch_one_graph_each_size_certified():
+    """One map of each size 64^2 .. 1024^2 of the heterogeneous workload, in
+    mixed precision: the batch solve (one graph launch per round for all
+    sizes) stops every map with WF_OK, and a refined solve warm-started from
+    each batch solution is certified to 1e-4 by the oracle's gradient."""
+    from tests.test_gpu_certified import oracle_cert, p_eff
+    sizes = (64, 128, 256, 512, 1024)
+    maps = synth.hetero_batch(count=24, seed=4, sizes=sizes)
+    first = {}
+    for m in maps:
+        first.setdefault(m.n, m)
+    assert sorted(first) == list(sizes)
+    probs, hosts = [], []
+    for n in sizes:
+        pr, ho = make_problem([first[n]], "mixed")
+        probs.append(pr)
+        hosts.append(ho)
+    res = wf.solve_many(probs, gtol_rel=1e-6, max_iter=20000, check_every=16, refresh_every=200)
+    for r, n in zip(res, sizes):
+        assert [s["status"] for s in r.stats] == ["WF_OK"], (n, r.stats)
+    for p, r, ho, n in zip(probs, res, hosts, sizes):
+        ref, cert = p.solve_refined(s0=r.s, cert_tol=1e-4, gtol_rel=1e-5, max_iter=20000)
+        P = p_eff(ho["P"][0].astype(np.float32), n)
+        c = oracle_cert(ref.s[0].cpu().numpy(), ho["d"][0], ho["W"][0], P, n)
+        assert c <= 1e-4, (n, c, cert)
+        s_ref = ref.s[0].cpu().numpy()
+        assert rel(r.s[0].cpu().numpy().astype(np.complex128), s_ref) <= 1e-2, n
+        p.close()
