@@ -25,7 +25,8 @@ The paper's derivative operator equals this up to -k^2, absorbed into P.  The
 odd term s is set to 0 on the Nyquist row and column (where k and -k alias),
 the usual convention for odd spectral derivatives; only an even side length
 has a Nyquist line; R = I at k = 0.  Grids may be rectangular (ny x nx) and of
-any side lengths; the GPU path takes square power-of-two maps.
+any side lengths.  Pixels are square, so mode (my, mx) of an ny x nx grid has
+the wavevector (kx, ky) = 2 pi (mx / nx, my / ny) / pixel, the k of App. C.
 
 Pins (what fixes this file independently of itself) live in
 tests/test_oracle_pins.py: naive O(n^4) DFT, Parseval, unmasked closed form
@@ -36,8 +37,8 @@ against the dense BFGS inverse update, strong-Wolfe steps, the envelope identity
 d chi^2 / d log q_l = -2 Theta_fid,l E_l at the MAP, chi^2_min ~ chi-square(N_obs), the
 unbiasedness of Theta_hat (exact b and F) for a rescaled true spectrum, and the leakage-bias form
 of App. C against the full Fisher run where E and B do not mix; on rectangular and
-odd grids the DFT plane wave, the rotation's formula and k -> -k symmetry, the
-unmasked S/(S+N) MAP and exact central differences.
+odd grids the DFT plane wave, the rotation's shear of a plane-wave potential,
+its k -> -k symmetry, the unmasked S/(S+N) MAP and exact central differences.
 Parity unpinned: iteration counts and chi^2-versus-iteration curves, because the
 paper gives them only as figures.
 """
@@ -85,16 +86,19 @@ def signed_modes(n: int, nx: int | None = None):
 
 def ks_rotation(n: int, nx: int | None = None):
     """Per-mode Kaiser-Squires cosine and sine (App. C, E/B operator), full
-    plane of an n x nx grid (nx = n by default).  The Nyquist line of an even
+    plane of an n x nx grid (nx = n by default): c = (kx^2 - ky^2)/k^2,
+    s = 2 kx ky / k^2 at the mode's wavevector k ~ (mx / nx, my / n), here
+    scaled by n nx to the integers (mx n, my nx).  The Nyquist line of an even
     side, where k and -k alias, gets s = 0; an odd side has none."""
     nx = n if nx is None else nx
     my, mx = signed_modes(n, nx)
-    k2 = mx * mx + my * my
+    qx, qy = mx * n, my * nx
+    k2 = qx * qx + qy * qy
     c = np.ones((n, nx))
     s = np.zeros((n, nx))
     nz = k2 > 0
-    c[nz] = (mx[nz] ** 2 - my[nz] ** 2) / k2[nz]
-    s[nz] = 2.0 * mx[nz] * my[nz] / k2[nz]
+    c[nz] = (qx[nz] ** 2 - qy[nz] ** 2) / k2[nz]
+    s[nz] = 2.0 * qx[nz] * qy[nz] / k2[nz]
     nyq = ((nx % 2 == 0) & (np.abs(mx) == nx // 2)) | ((n % 2 == 0) & (np.abs(my) == n // 2))
     s[nyq] = 0.0
     return c, s

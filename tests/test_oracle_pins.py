@@ -589,24 +589,58 @@ def test_dft_rectangular_plane_wave_and_fft(shape):
     assert np.allclose(O.fft2u(r), O.dft2_naive(r), atol=1e-12)
 
 
+@pytest.mark.parametrize("shape", [(6, 10), (5, 7), (8, 16), (16, 8), (9, 12)])
+def test_ks_rotation_rectangular_shears_a_plane_wave_potential(shape):
+    """On a grid of square pixels, a lensing potential psi = cos(kx x + ky y)
+    with (kx, ky) = 2 pi (b / nx, a / ny) per pixel has convergence
+    kappa = (psi_xx + psi_yy) / 2 and shear gamma1 = (psi_xx - psi_yy) / 2,
+    gamma2 = psi_xy (App. C), all from the derivatives of the wave itself.  An
+    E field equal to kappa must come out of the operator as that shear; a B
+    field rotates the other way.  Pins the wavevector of a mode on a
+    rectangular grid, not only its mode numbers."""
+    ny, nx = shape
+    a, b = 1, 2  # off both Nyquist lines
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    kx, ky = 2 * np.pi * b / nx, 2 * np.pi * a / ny
+    psi = np.cos(kx * x + ky * y)
+    kappa = -0.5 * (kx * kx + ky * ky) * psi
+    g1, g2 = -0.5 * (kx * kx - ky * ky) * psi, -kx * ky * psi
+    zero = np.zeros_like(psi)
+    out = O.apply_A(np.stack([kappa, zero]), np.ones((2, ny, nx)))
+    assert np.allclose(out[0], g1, atol=1e-12) and np.allclose(out[1], g2, atol=1e-12)
+    outb = O.apply_A(np.stack([zero, kappa]), np.ones((2, ny, nx)))
+    assert np.allclose(outb[0], -g2, atol=1e-12) and np.allclose(outb[1], g1, atol=1e-12)
+
+
 @pytest.mark.parametrize("shape", RECT)
-def test_ks_rotation_rectangular_formula_and_symmetry(shape):
-    """Off the Nyquist lines c = (kx^2 - ky^2)/k^2 and s = 2 kx ky / k^2 (an odd
-    side has no Nyquist line), and both are even under k -> -k on the grid,
-    which is what keeps A z real (a Nyquist mode is its own negative, where s
-    is odd, hence s = 0 there)."""
+def test_ks_rotation_rectangular_symmetry_and_nyquist(shape):
+    """c and s are even under k -> -k on the grid, which is what keeps A z
+    real; s = 0 on a Nyquist line (a Nyquist mode is its own negative, where s
+    is odd), and an odd side has none, so there c^2 + s^2 = 1 everywhere but
+    k = 0."""
     ny, nx = shape
     c, s = O.ks_rotation(ny, nx)
     my, mx = O.signed_modes(ny, nx)
     k2 = mx ** 2 + my ** 2
     nyq = ((nx % 2 == 0) & (np.abs(mx) == nx / 2)) | ((ny % 2 == 0) & (np.abs(my) == ny / 2))
+    assert np.all(s[nyq] == 0)
     off = (k2 > 0) & ~nyq
-    assert np.allclose(c[off], (mx[off] ** 2 - my[off] ** 2) / k2[off], rtol=0, atol=1e-15)
-    assert np.allclose(s[off], 2 * mx[off] * my[off] / k2[off], rtol=0, atol=1e-15)
+    assert np.allclose(c[off] ** 2 + s[off] ** 2, 1.0, atol=1e-15)
     neg = (-np.arange(ny)) % ny, (-np.arange(nx)) % nx
     assert np.array_equal(c, c[neg[0]][:, neg[1]]) and np.array_equal(s, s[neg[0]][:, neg[1]])
-    if ny % 2 and nx % 2:
-        assert np.allclose(c[k2 > 0] ** 2 + s[k2 > 0] ** 2, 1.0, atol=1e-15)
+
+
+def test_ks_rotation_square_grid_is_the_mode_number_form():
+    """On a square grid the wavevector is proportional to the mode numbers, so
+    the rotation is c = (mx^2 - my^2)/m^2, s = 2 mx my / m^2 bit for bit."""
+    n = 16
+    c, s = O.ks_rotation(n)
+    my, mx = O.signed_modes(n)
+    k2 = mx ** 2 + my ** 2
+    nyq = (np.abs(mx) == n / 2) | (np.abs(my) == n / 2)
+    off = (k2 > 0) & ~nyq
+    assert np.array_equal(c[off], (mx[off] ** 2 - my[off] ** 2) / k2[off])
+    assert np.array_equal(s[off], 2 * mx[off] * my[off] / k2[off])
 
 
 @pytest.mark.parametrize("shape", [(6, 10), (5, 7), (9, 12)])
