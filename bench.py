@@ -315,7 +315,7 @@ def run_eval_pass(args, dev, prob, hbm, reps=20, B=None, n=None):
     n = args.n if n is None else n
     g = torch.Generator(device=dev)
     g.manual_seed(5)
-    s = torch.randn((B, 1, n, n // 2 + 1), generator=g, device=dev, dtype=torch.complex64)
+    s = torch.randn((B, 1, n, n // 2 + 1), generator=g, device=dev, dtype=prob._cplx())
     grad = torch.empty_like(s)
     chi2 = torch.empty(B, dtype=torch.float64, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -330,7 +330,8 @@ def run_eval_pass(args, dev, prob, hbm, reps=20, B=None, n=None):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     nh = n * (n // 2 + 1)
-    alg = B * (8 * nh + 4 * n * n + 4 * n * n + 8 * nh) + 4 * nh
+    e = 8 if prob._cplx() == torch.complex128 else 4  # bytes of the working type
+    alg = B * (2 * e * nh + e * n * n + e * n * n + 2 * e * nh) + e * nh
     achieved = alg / (ms / 1000.0) / 1e9
     return {"evals_per_s": B * 1000.0 / ms, "ms_per_pass": ms, "maps": B,
             "algorithmic_bytes_per_pass": alg, "achieved_GBps": achieved, "peak_GBps": hbm, "frac": achieved / hbm,
@@ -536,19 +537,25 @@ def run_eb_bandpower(args, dev, n=512, n_bands=8, n_sim=20, n_fd=2):
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64
 
 
+# FP64 FLOPs of one L-BFGS iteration counted by ncu on the FP64 path (DFMA as
+# two; profiles/fp64_iteration_cmb1024_counters.md), per (n, m).
+FP64_ITERATION_FLOPS_COUNTED = {(1024, 10): 158.3e6}
+
+
 def iteration_flops(n, m):
-    """FP64 arithmetic of one L-BFGS iteration on one n x n map (C = 1), counted
-    as 5 L log2 L per complex FFT of length L: two real 2-D transforms (n/2
-    column FFTs of length n and n row FFTs of length n/2 each); 5m + 9 complex
-    dot products or real-coefficient axpys per packed value, 4 flops each
-    (comb: 2m + 1 dots and 2m + 3 axpys; qdots: m - 1 dots; forward column
-    stage: 5 dots and q = 2 (p - a)); about 10 flops per value for the per-mode
-    and per-pixel steps."""
+    """FP64 arithmetic of one L-BFGS iteration on one n x n map (C = 1): the
+    ncu-counted figure where there is one, else a model (5 L log2 L per
+    complex FFT of length L: two real 2-D transforms; 5m + 9 complex dot
+    products or real-coefficient axpys per packed value, 4 flops each; about
+    10 flops per value for the per-mode and per-pixel steps), which
+    overcounts the radix-8/16 butterflies.  Returns (flops, source)."""
     import math
+    if (n, m) in FP64_ITERATION_FLOPS_COUNTED:
+        return FP64_ITERATION_FLOPS_COUNTED[(n, m)], "ncu FP64 instruction counters"
     h = n // 2
     fft = 5 * (h * n * math.log2(n) + n * h * math.log2(h))
     vals = n * h
-    return 2 * fft + vals * (4 * (5 * m + 9) + 10)
+    return 2 * fft + vals * (4 * (5 * m + 9) + 10), "model"
 
 
 def run_fp64_reference(args, dev, cert_tol=1e-4, fp64_peak=None):
@@ -601,7 +608,7 @@ def run_fp64_reference(args, dev, cert_tol=1e-4, fp64_peak=None):
                      "status": r.stats[0]["status"]}
     p64.close()
     p32.close()
-    flops = iteration_flops(n, args.m)
+    flops, flops_src = iteration_flops(n, args.m)
     achieved = flops / (it_ms / 1000.0) / 1e12
     peak = fp64_peak or FP64_PEAK_TFLOPS
     src = ("measured on this GPU (wf_alu_peak, FP64 FMA chains)" if fp64_peak
@@ -611,7 +618,8 @@ def run_fp64_reference(args, dev, cert_tol=1e-4, fp64_peak=None):
                           "how": "wf_map_solve_refined on map 0 of the workload, first round to |g|/|g0| < 1e-5"},
             "fp64_single_map_evals_per_s": 1000.0 / it_ms, "fp64_single_map_ms_per_iteration": it_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "flops_per_iteration": flops, "peak_source": src}}
+                         "frac": achieved / peak, "flops_per_iteration": flops, "flops_source": flops_src,
+                         "peak_source": src}}
 
 
 # ---------------------------------------------------------------------------

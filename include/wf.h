@@ -122,7 +122,9 @@ typedef struct {
                                ping-pong column and row passes (0: larger radices first,
                                1024 = 16 x 8 x 8; 1: ascending, 8 x 8 x 16; 2: radix 32 first
                                for lengths 512 and 1024, 32 x 32).  wf_problem_variant reports
-                               the one in use. */
+                               the one in use: a = 1 becomes 2 on maps whose column tile is
+                               wider than 128 values (few rows, many columns), which one TMA box
+                               cannot hold. */
   int history;              /* 0 (default): off.  k > 0: every map keeps a device ring of its
                                last k iterations' records (k, chi2, |g|/|g0|, step, evals), the
                                convergence trace the paper plots (Sec. 3, Fig. of chi2 against
@@ -183,6 +185,21 @@ void wf_opts_default(wf_opts* o);
 wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, int C,
                             int dtype, int precision, int lbfgs_m, void* stream,
                             wf_problem** out);
+
+/* The same for rectangular maps of ny rows by nx pixels, both powers of two
+ * in [8, 1024]; wf_problem_create(n) is wf_problem_create_rect(n, n).  Every
+ * [n][n] array of this header is then [ny][nx] (pixel maps, x = the last
+ * axis), every half-plane array [n][n/2+1] is [ny][nx/2+1], and the unitary
+ * DFT carries (ny nx)^-1/2.  Pixels are square: mode (my, mx) has the
+ * wavevector 2 pi (mx / nx, my / ny) / pixel, which is what the E/B rotation
+ * of App. C (C = 2) is evaluated on; P and the band tables are per mode and
+ * so take any convention the caller chooses.  Every call on the problem
+ * takes the rectangular shape (the solver, its checkpoints and
+ * wf_map_solve_many included); wf_eval_noalloc and bandpower_iterate take
+ * square maps only. */
+wf_status wf_problem_create_rect(wf_handle* h, const wf_map* maps, int count, int ny, int nx, int C,
+                                 int dtype, int precision, int lbfgs_m, void* stream,
+                                 wf_problem** out);
 wf_status wf_problem_destroy(wf_problem* p);
 
 /* Replace the data maps d of every map (device [count][C][n][n], working
@@ -448,6 +465,11 @@ typedef struct {
 wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
                              const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
                              wf_solve_stats* stats);
+/* The same on rectangular ny x nx maps (shapes as wf_problem_create_rect;
+ * npix = C ny nx in the draw rule above). */
+wf_status bandpower_estimate_rect(wf_handle* h, const wf_map* data, int ny, int nx, int C, int dtype,
+                                  int precision, const wf_bandpower_in* in, const wf_opts* opts,
+                                  wf_bandpower_out* out, wf_solve_stats* stats);
 
 /* Band powers spread over several GPUs (Sec. 2.5: the simulations are
  * independent until the estimator averages them).  Each GPU runs
@@ -545,6 +567,21 @@ wf_status wf_normal_draw(unsigned long long seed, unsigned int stream_id, unsign
  * non-finite values.  Stream ordered, no synchronisation after the first call. */
 wf_status wf_eval_noalloc(const void* s, const void* d, const void* w, const void* P, int n, int C,
                           int count, int precision, double* chi2, void* grad, void* stream);
+
+/* Bounds-checked build (no counterpart in the paper; the failure handling of
+ * the test plan).  A separate copy of this library compiled with
+ * -DWF_DEBUG_BOUNDS checks every shared-memory tile index of the FFT stages
+ * and their global spectrum, pixel and scratch accesses, and the vector
+ * accesses of the streaming L-BFGS kernels, against the buffers they address.
+ * A bad index is counted, the first one recorded, and the access redirected
+ * to element 0 of its buffer: nothing traps and no access leaves a buffer.
+ * wf_debug_bounds reads the count over the library's kernel translation units
+ * and, if first is not NULL (HOST long long [4]), the first violation: unit,
+ * source line, index, limit.  mode 0 reads, 1 reads and clears, 2 first runs a
+ * self-test kernel that checks one index five past the end of a tile (the
+ * count grows by one).  Synchronises the device.  In the normal build it sets
+ * *count = 0 and returns WF_EINVAL (not a bounds-checked build). */
+wf_status wf_debug_bounds(unsigned long long* count, long long* first, int mode);
 
 /* Measured fused multiply-add throughput of the current device, in flop/s
  * (2 per FMA), for dtype WF_F32 or WF_F64: every SM's resident blocks run

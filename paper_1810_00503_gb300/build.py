@@ -30,8 +30,8 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libwf.so")
 
 
-def _compile(src: str, extra: list[str]) -> tuple[str, str]:
-    obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, extra: list[str], obj_dir: str = OBJ) -> tuple[str, str]:
+    obj = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
     cmd = [_nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
@@ -102,27 +102,36 @@ def resource_report() -> str:
     return "\n".join(lines)
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
+DEBUG_OBJ = os.path.join(HERE, "_build_dbg")
+DEBUG_LIB = os.path.join(HERE, "libwf_dbg.so")
+
+
+def build(verbose: bool = False, extra: list[str] | None = None, debug_bounds: bool = False) -> str:
     """Compile every CUDA source and link libwf.so; returns the library path.
     verbose: pass -Xptxas -v and print its per-kernel resource report
-    (registers, spill bytes, shared memory) for every source to stderr."""
-    os.makedirs(OBJ, exist_ok=True)
+    (registers, spill bytes, shared memory) for every source to stderr.
+    debug_bounds: build the bounds-checked copy libwf_dbg.so instead
+    (-DWF_DEBUG_BOUNDS; load it with WF_LIB_PATH)."""
+    obj_dir, lib_path = (DEBUG_OBJ, DEBUG_LIB) if debug_bounds else (OBJ, LIB)
+    os.makedirs(obj_dir, exist_ok=True)
     extra = list(extra or [])
+    if debug_bounds:
+        extra += ["-DWF_DEBUG_BOUNDS"]
     if verbose:
         extra += ["-Xptxas", "-v"]
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        done = list(ex.map(lambda s: _compile(s, extra), SOURCES))
+        done = list(ex.map(lambda s: _compile(s, extra, obj_dir), SOURCES))
     objs = [o for o, _ in done]
     if verbose:
         for src, (_, log) in zip(SOURCES, done):
             sys.stderr.write(f"== {src}\n{log}")
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

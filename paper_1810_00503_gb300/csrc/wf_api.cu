@@ -49,6 +49,7 @@ extern "C" void wf_opts_default(wf_opts* o) {
 static void wf_geo_tiles(WfGeo& g, int tc_div, int rb_div) {
   int tc = WF_TILE / (g.C * g.n);
   if (tc > g.h) tc = g.h;
+  if (tc > WF_THREADS) tc = WF_THREADS;  // a thread keeps one column: the block spans a tile row
   tc /= tc_div;
   if (tc < 2) tc = g.h < 2 ? g.h : 2;
   g.TC = tc;
@@ -63,15 +64,29 @@ static void wf_geo_tiles(WfGeo& g, int tc_div, int rb_div) {
   g.rb_div = rb_div;
 }
 
-WfGeo wf_make_geo(int n, int C) {
+// A TMA box spans at most 256 elements per dimension: a column tile wider
+// than 128 complex values (a map of few rows and many columns) cannot be one
+// box row, so such shapes run the inverse column stage on ping-pong passes.
+static void wf_geo_fix_kind(WfGeo& g) {
+  if (g.colinv_kind == WF_COLINV_TMA_K && 2 * g.TC > 256) g.colinv_kind = WF_COLINV_PP_K;
+}
+
+WfGeo wf_make_geo(int ny, int nx, int C) {
   WfGeo g;
-  g.n = n;
-  g.h = n / 2;
+  g.n = ny;
+  g.nx = nx;
+  g.h = nx / 2;
   g.C = C;
   g.lgn = 0;
-  while ((1 << g.lgn) < n) ++g.lgn;
-  g.lgh = g.lgn - 1;
-  const long long vsz = (long long)C * n * (n / 2);
+  while ((1 << g.lgn) < ny) ++g.lgn;
+  g.lgnx = 0;
+  while ((1 << g.lgnx) < nx) ++g.lgnx;
+  g.lgh = g.lgnx - 1;
+  // mode (my, mx) has wavevector 2 pi (mx / nx, my / ny) / pixel: scaled by
+  // max(ny, nx) both components are integers
+  g.ksx = nx < ny ? ny / nx : 1;
+  g.ksy = ny < nx ? nx / ny : 1;
+  const long long vsz = (long long)C * ny * (nx / 2);
   g.ncomb = (int)((vsz + WF_COMB_CHUNK - 1) / WF_COMB_CHUNK);
   g.ncomb = (g.ncomb + WF_STREAM_GROUP - 1) / WF_STREAM_GROUP;
   wf_geo_tiles(g, WF_TUNE_MAXDIV, WF_TUNE_MAXDIV);  // the narrowest tiles set the stride
@@ -81,6 +96,7 @@ WfGeo wf_make_geo(int n, int C) {
   g.colinv_kind = WF_COLINV_TMA ? WF_COLINV_TMA_K : WF_COLINV_PP_K;
   g.row_kind = WF_ROW_PP_K;
   g.col_plan = g.row_plan = 0;
+  wf_geo_fix_kind(g);
   return g;
 }
 
@@ -92,6 +108,7 @@ WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_di
   g.row_kind = row_kind;
   g.col_plan = col_plan;
   g.row_plan = row_plan;
+  wf_geo_fix_kind(g);
   return g;
 }
 
@@ -247,15 +264,17 @@ void wf_free(wf_handle* h, void* ptr) {
   }
 }
 
-extern "C" wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, int C,
-                                       int dtype, int precision, int lbfgs_m, void* stream,
-                                       wf_problem** out) {
+extern "C" wf_status wf_problem_create_rect(wf_handle* h, const wf_map* maps, int count, int ny, int nx, int C,
+                                            int dtype, int precision, int lbfgs_m, void* stream,
+                                            wf_problem** out) {
   if (!out) return wf_fail(WF_EINVAL, "wf_problem_create: null output pointer");
   *out = nullptr;
   if (!h) return wf_fail(WF_EINVAL, "wf_problem_create: null handle");
   if (!maps || count < 1) return wf_fail(WF_EINVAL, "wf_problem_create: need count >= 1 maps");
-  if (n < 8 || n > WF_NT || (n & (n - 1)))
-    return wf_fail(WF_EINVAL, "wf_problem_create: n = %d is not a power of two in [8, %d]", n, WF_NT);
+  if (ny < 8 || ny > WF_NT || (ny & (ny - 1)))
+    return wf_fail(WF_EINVAL, "wf_problem_create: ny = %d is not a power of two in [8, %d]", ny, WF_NT);
+  if (nx < 8 || nx > WF_NT || (nx & (nx - 1)))
+    return wf_fail(WF_EINVAL, "wf_problem_create: nx = %d is not a power of two in [8, %d]", nx, WF_NT);
   if (C != 1 && C != 2) return wf_fail(WF_EINVAL, "wf_problem_create: C = %d (must be 1 or 2)", C);
   if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "wf_problem_create: bad dtype %d", dtype);
   if (precision != WF_FP64 && precision != WF_MIXED)
@@ -275,17 +294,18 @@ extern "C" wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int cou
   if (!p) return wf_fail(WF_ENOMEM, "wf_problem_create: host allocation failed");
   p->h = h;
   p->count = count;
-  p->n = n;
+  p->n = ny;
+  p->nx = nx;
   p->C = C;
   p->dtype = dtype;
   p->precision = precision;
   p->m = lbfgs_m;
-  p->g = wf_make_geo(n, C);
+  p->g = wf_make_geo(ny, nx, C);
   p->elt = precision == WF_FP64 ? sizeof(double) : sizeof(float);
   int shared = 1;
   for (int i = 1; i < count; ++i) shared &= maps[i].P == maps[0].P;
   p->sp_shared = shared;
-  const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
+  const size_t npix = (size_t)C * ny * nx, nsp = (size_t)C * ny * (nx / 2 + 1);
   p->sp_stride = shared ? 0 : (long long)nsp;
   wf_status s = WF_OK;
   if (s == WF_OK) s = wf_alloc(h, &p->d, npix * count * p->elt, "data maps");
@@ -331,6 +351,11 @@ extern "C" wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int cou
   }
   *out = p;
   return WF_OK;
+}
+
+extern "C" wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, int C, int dtype,
+                                       int precision, int lbfgs_m, void* stream, wf_problem** out) {
+  return wf_problem_create_rect(h, maps, count, n, n, C, dtype, precision, lbfgs_m, stream, out);
 }
 
 extern "C" wf_status wf_problem_destroy(wf_problem* p) {
@@ -427,7 +452,7 @@ extern "C" wf_status wf_problem_set_band_scale(wf_problem* p, const int16_t* ban
                                                void* stream) {
   if (!p || !band || !q) return wf_fail(WF_EINVAL, "wf_problem_set_band_scale: null argument");
   if (n_b < 1 || n_b > 1024) return wf_fail(WF_EINVAL, "wf_problem_set_band_scale: n_b = %d", n_b);
-  const size_t nsp = (size_t)p->C * p->n * (p->n / 2 + 1);
+  const size_t nsp = (size_t)p->C * p->n * (p->nx / 2 + 1);
   const int ntab = p->sp_shared ? 1 : p->count;
   cudaStream_t st = (cudaStream_t)stream;
   if (!p->sp0) {
@@ -479,4 +504,40 @@ extern "C" wf_status wf_band_table(int n, int C, const double* edges, int n_band
     }
   }
   return WF_OK;
+}
+
+cudaError_t wf_dbg_selftest();
+
+extern "C" wf_status wf_debug_bounds(unsigned long long* count, long long* first, int mode) {
+  if (!count) return wf_fail(WF_EINVAL, "wf_debug_bounds: null count");
+  *count = 0;
+  if (mode < 0 || mode > 2) return wf_fail(WF_EINVAL, "wf_debug_bounds: mode = %d (0 read, 1 read and clear, 2 self-test)", mode);
+#ifndef WF_DEBUG_BOUNDS
+  (void)first;
+  return wf_fail(WF_EINVAL, "wf_debug_bounds: this library was not built with bounds checks (WF_DEBUG_BOUNDS)");
+#else
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && mode == 2) e = wf_dbg_selftest();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return wf_cuda_fail(e, "wf_debug_bounds");
+  typedef cudaError_t (*Reader)(unsigned long long*, int);
+#define WF_DBG_ENTRY(name) wf_dbg_read_##name,
+  const Reader readers[] = {WF_DBG_TUS(WF_DBG_ENTRY)};
+#undef WF_DBG_ENTRY
+  bool have_first = false;
+  for (int u = 0; u < (int)(sizeof readers / sizeof readers[0]); ++u) {
+    unsigned long long rec[4];
+    e = readers[u](rec, mode == 1);
+    if (e != cudaSuccess) return wf_cuda_fail(e, "wf_debug_bounds: reading a record");
+    *count += rec[0];
+    if (rec[0] && !have_first && first) {
+      first[0] = u;
+      first[1] = (long long)rec[1];
+      first[2] = (long long)rec[2];
+      first[3] = (long long)rec[3];
+      have_first = true;
+    }
+  }
+  return WF_OK;
+#endif
 }

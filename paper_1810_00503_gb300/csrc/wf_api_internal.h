@@ -12,23 +12,23 @@ struct wf_handle {
   size_t used;   // device bytes held by this handle's allocations
   std::mutex mu;
   std::unordered_map<void*, size_t> live;  // allocation -> bytes
-  std::unordered_map<long long, int> tuned;  // (n, C, precision, maps) -> FFT-stage variant
+  std::unordered_map<long long, int> tuned;  // (ny, nx, C, precision, maps) -> FFT-stage variant
 };
 
 struct WfSolver;  // L-BFGS state, allocated on the first solve (wf_solve.cu)
 
 struct wf_problem {
   wf_handle* h;
-  int count, n, C, dtype, precision, m;
+  int count, n, nx, C, dtype, precision, m;  // n = ny rows of nx pixels
   WfGeo g;
   size_t elt;            // bytes of the working type
   int sp_shared;         // one sqrt(P) table serves every map
   long long sp_stride;   // elements between maps' sqrt(P) tables
-  void* d;               // [count][C][n][n] working type
-  void* w;               // [count][C][n][n] mask * Ninv
-  void* sp;              // [1 or count][C][n][n/2+1] sqrt(P)/n (band-scaled if set)
+  void* d;               // [count][C][ny][nx] working type
+  void* w;               // [count][C][ny][nx] mask * Ninv
+  void* sp;              // [1 or count][C][ny][nx/2+1] sqrt(P/(ny nx)) (band-scaled if set)
   void* sp0;             // unscaled copy, kept once a band scale has been set
-  void* scratch;         // [count][C][n][n/2] complex
+  void* scratch;         // [count][C][ny][nx/2] complex
   double* part;          // [count][WF_NSLOT][maxblk]
   int* flags;            // device status words
   double* bpart;         // band-sum partials [count][blocks][bands] (grown on demand)

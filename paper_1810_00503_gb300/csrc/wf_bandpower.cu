@@ -20,17 +20,17 @@
 #include "wf_api_internal.h"
 
 // Theta_fid,l: full-plane mean of P over band l (half-plane multiplicity 1 on
-// the kx = 0 and kx = n/2 columns, 2 elsewhere).  One block; per-warp bins
+// the kx = 0 and kx = nx/2 columns, 2 elsewhere; P is [C][ny][nx/2+1]).  One block; per-warp bins
 // ([warps][2 nb]: sums, then counts) summed in a fixed order, so the result is
 // the same on every run.
 template <typename S>
-__global__ void k_theta_fid(const S* P, const int16_t* band, int n, int C, int nb, double* theta) {
+__global__ void k_theta_fid(const S* P, const int16_t* band, int ny, int nx, int C, int nb, double* theta) {
   extern __shared__ double sh[];
   const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < 2 * nb * nw; i += blockDim.x) sh[i] = 0.0;
   __syncthreads();
-  const int h = n / 2;
-  const size_t tot = (size_t)C * n * (h + 1);
+  const int h = nx / 2;
+  const size_t tot = (size_t)C * ny * (h + 1);
   double* bins = sh + (size_t)w * 2 * nb;
   for (size_t i0 = 0; i0 < tot; i0 += blockDim.x) {  // uniform trip count across the block
     const size_t i = i0 + threadIdx.x;
@@ -311,14 +311,15 @@ struct Scope {  // frees what the estimator allocates, on every return path
     if (s_ != WF_OK) return s_;            \
   } while (0)
 
-extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
-                                        const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
-                                        wf_solve_stats* stats) {
+extern "C" wf_status bandpower_estimate_rect(wf_handle* h, const wf_map* data, int ny, int nx, int C, int dtype,
+                                             int precision, const wf_bandpower_in* in, const wf_opts* opts,
+                                             wf_bandpower_out* out, wf_solve_stats* stats) {
   if (!h || !data || !in || !out) return wf_fail(WF_EINVAL, "bandpower_estimate: null argument");
   if (!data->d || !data->mask || !data->Ninv || !data->P)
     return wf_fail(WF_EINVAL, "bandpower_estimate: the data map needs d, mask, Ninv and P");
-  if (n < 8 || n > WF_NT || (n & (n - 1)) || (C != 1 && C != 2))
-    return wf_fail(WF_EINVAL, "bandpower_estimate: n = %d, C = %d (n a power of two in [8, %d], C 1 or 2)", n, C,
+  if (ny < 8 || ny > WF_NT || (ny & (ny - 1)) || nx < 8 || nx > WF_NT || (nx & (nx - 1)) || (C != 1 && C != 2))
+    return wf_fail(WF_EINVAL,
+                   "bandpower_estimate: %d x %d maps, C = %d (each side a power of two in [8, %d], C 1 or 2)", ny, nx, C,
                    WF_NT);
   const int nb = in->n_bands, J = in->n_sim, nfd = in->n_fd;
   if (nb < 1 || nb > 64) return wf_fail(WF_EINVAL, "bandpower_estimate: n_bands = %d outside [1, 64]", nb);
@@ -341,7 +342,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   if (in->fd_bands && (in->n_fd_bands < 1 || in->n_fd_bands > nE))
     return wf_fail(WF_EINVAL, "bandpower_estimate: n_fd_bands = %d", in->n_fd_bands);
   if (in->sim_index) {
-    const unsigned long long lim = (1ull << 62) / ((unsigned long long)C * n * n * (nb + 1));
+    const unsigned long long lim = (1ull << 62) / ((unsigned long long)C * ny * nx * (nb + 1));
     for (int j = 0; j < J; ++j)
       if (in->sim_index[j] < 0 || (unsigned long long)in->sim_index[j] >= lim)
         return wf_fail(WF_EINVAL, "bandpower_estimate: sim_index[%d] = %lld out of range", j, in->sim_index[j]);
@@ -357,7 +358,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   cudaStream_t st = (cudaStream_t)o.stream;
   const size_t delt = dtype == WF_F64 ? 8 : 4;
   const size_t welt = precision == WF_FP64 ? 8 : 4;
-  const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (n / 2 + 1);
+  const size_t npix = (size_t)C * ny * nx, nsp = (size_t)C * ny * (nx / 2 + 1);
   int fdb[64], fdk[64], nbF = 0;
   BP_OK(bp_rows(in, "bandpower_estimate", fdb, fdk, &nbF));
   const int nR = bp_fisher_rows(in);  // nbF, plus the joint B row
@@ -368,9 +369,9 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   BP_OK(wf_alloc(h, (void**)&theta, sizeof(double) * nb, "theta_fid"));
   sc.add(theta);
   if (dtype == WF_F64)
-    k_theta_fid<double><<<1, 1024, 64 * nb * sizeof(double), st>>>((const double*)data->P, in->band, n, C, nb, theta);
+    k_theta_fid<double><<<1, 1024, 64 * nb * sizeof(double), st>>>((const double*)data->P, in->band, ny, nx, C, nb, theta);
   else
-    k_theta_fid<float><<<1, 1024, 64 * nb * sizeof(double), st>>>((const float*)data->P, in->band, n, C, nb, theta);
+    k_theta_fid<float><<<1, 1024, 64 * nb * sizeof(double), st>>>((const float*)data->P, in->band, ny, nx, C, nb, theta);
   BP_TRY(cudaGetLastError());
   void* Pl = nullptr;
   BP_OK(wf_alloc(h, &Pl, nsp * (nb + (L > 0)) * delt, "band-restricted power"));
@@ -392,7 +393,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
     maps[i].P = data->P;
   }
   wf_problem* psim = nullptr;
-  wf_status rs = wf_problem_create(h, maps, J, n, C, dtype, precision, 1, (void*)st, &psim);
+  wf_status rs = wf_problem_create_rect(h, maps, J, ny, nx, C, dtype, precision, 1, (void*)st, &psim);
   if (rs != WF_OK) { free(maps); return rs; }
   sc.addp(psim);
   const void* zin = in->z;
@@ -436,7 +437,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   void* dfd = nullptr;
   if (nF > 0) {
     wf_problem* pfd = nullptr;
-    rs = wf_problem_create(h, maps, nF, n, C, dtype, precision, 1, (void*)st, &pfd);
+    rs = wf_problem_create_rect(h, maps, nF, ny, nx, C, dtype, precision, 1, (void*)st, &pfd);
     if (rs != WF_OK) { free(maps); return rs; }
     sc.addp(pfd);
     void* nfd_in = nullptr;
@@ -459,7 +460,7 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   for (int i = 0; i < Btot; ++i) maps[i].P = data->P;
   maps[0].d = data->d;
   wf_problem* ps = nullptr;
-  rs = wf_problem_create(h, maps, Btot, n, C, dtype, precision, o.lbfgs_m, (void*)st, &ps);
+  rs = wf_problem_create_rect(h, maps, Btot, ny, nx, C, dtype, precision, o.lbfgs_m, (void*)st, &ps);
   free(maps);
   if (rs != WF_OK) return rs;
   sc.addp(ps);
@@ -503,6 +504,12 @@ extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n,
   }
   if (nfd > 0 && singular) return wf_fail(WF_ENONFINITE, "bandpower_estimate: the Fisher matrix is singular");
   return solve_status;
+}
+
+extern "C" wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
+                                        const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
+                                        wf_solve_stats* stats) {
+  return bandpower_estimate_rect(h, data, n, n, C, dtype, precision, in, opts, out, stats);
 }
 
 extern "C" size_t bandpower_sums_len(int n_bands, int n_rows) {
@@ -643,3 +650,5 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
   if (worst != WF_OK) wf_fail(worst, "bandpower_iterate: a solve hit its iteration limit");
   return worst;
 }
+
+WF_DBG_READER(bandpower)

@@ -138,6 +138,7 @@ __device__ __forceinline__ void dft_reg(V2<T>* v) {
 // passes, whose lanes walk the rows of one column of a column tile.
 template <typename T>
 __device__ __forceinline__ int wf_sw(int x) {
+  x = (int)WF_CHK(x, WF_TILE);
   if constexpr (sizeof(T) == 4) return x ^ (((x >> 4) ^ (x >> 8)) & 15);
   else return x ^ (((x >> 3) ^ (x >> 6)) & 7);
 }
@@ -147,6 +148,7 @@ __device__ __forceinline__ int wf_sw(int x) {
 // every pass of the plans used; 16-byte values keep two.
 template <typename T>
 __device__ __forceinline__ int wf_swp(int x) {
+  x = (int)WF_CHK(x, WF_TILE);
   if constexpr (sizeof(T) == 4) return x ^ ((x >> 4) & 15);
   else return x ^ (((x >> 3) ^ (x >> 6)) & 7);
 }

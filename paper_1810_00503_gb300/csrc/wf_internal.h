@@ -6,6 +6,55 @@
 
 #include "../../include/wf.h"
 
+// Bounds-checked debug build (compiled with -DWF_DEBUG_BOUNDS into a separate
+// library): WF_CHK(i, lim) checks an index against the size of the buffer it
+// addresses; a bad one is counted in this translation unit's record (the
+// first kept: source line, index, limit) and replaced by 0, an element that
+// exists, so that no access leaves its buffer and nothing traps.  Every
+// shared-memory tile index passes through the swizzles, which check it;
+// global accesses of the FFT stages and the streaming kernels check theirs at
+// the call.  In the normal build WF_CHK(i, lim) is i.
+#ifdef WF_DEBUG_BOUNDS
+static __device__ unsigned long long wf_dbg_rec[4];  // count, line, index, limit
+__device__ __noinline__ inline long long wf_dbg_bad(long long i, long long lim, int line) {
+  if (atomicAdd(&wf_dbg_rec[0], 1ull) == 0ull) {
+    wf_dbg_rec[1] = (unsigned long long)line;
+    wf_dbg_rec[2] = (unsigned long long)i;
+    wf_dbg_rec[3] = (unsigned long long)lim;
+  }
+  return 0;
+}
+__device__ __forceinline__ long long wf_chk(long long i, long long lim, int line) {
+  return (i >= 0 && i < lim) ? i : wf_dbg_bad(i, lim, line);
+}
+#define WF_CHK(i, lim) wf_chk((long long)(i), (long long)(lim), __LINE__)
+// the same for an index that is used only when `cond` holds
+#define WF_CHK_IF(cond, i, lim) ((cond) ? WF_CHK(i, lim) : (long long)(i))
+// Host reader of this translation unit's record (out: count, line, index,
+// limit; reset clears it), one per kernel translation unit.
+#define WF_DBG_READER(name)                                                              \
+  cudaError_t wf_dbg_read_##name(unsigned long long* out, int reset) {                   \
+    cudaError_t e = cudaMemcpyFromSymbol(out, wf_dbg_rec, sizeof(unsigned long long) * 4); \
+    if (e == cudaSuccess && reset) {                                                     \
+      const unsigned long long z[4] = {0, 0, 0, 0};                                      \
+      e = cudaMemcpyToSymbol(wf_dbg_rec, z, sizeof z);                                   \
+    }                                                                                    \
+    return e;                                                                            \
+  }
+#else
+#define WF_CHK(i, lim) (i)
+#define WF_CHK_IF(cond, i, lim) (i)
+#define WF_DBG_READER(name)                                                    \
+  cudaError_t wf_dbg_read_##name(unsigned long long* out, int reset) {         \
+    (void)reset;                                                               \
+    out[0] = out[1] = out[2] = out[3] = 0;                                     \
+    return cudaSuccess;                                                        \
+  }
+#endif
+#define WF_DBG_TUS(X) X(ops_f32) X(ops_f64) X(lbcol_f32) X(lbcol_f64) X(lbrow_f32) X(lbrow_f64) X(solve) X(noalloc) X(bandpower)
+#define WF_DBG_DECL(name) cudaError_t wf_dbg_read_##name(unsigned long long* out, int reset);
+WF_DBG_TUS(WF_DBG_DECL)
+
 #define WF_NT 1024          // largest transform length and twiddle-table size
 #define WF_LOG2_NT 10
 // Twiddle buffer: [0, WF_NT) roots of unity exp(-2 pi i k / WF_NT); then for
@@ -160,7 +209,10 @@ __device__ __forceinline__ void wf_warp_bin_add(double* bins, int l, double v) {
   if (lead) bins[l] += t;
 }
 
-// Launch geometry of one (n, C) shape.
+// Launch geometry of one (ny, nx, C) shape: C channels of ny rows by nx
+// pixels, both powers of two.  The column stages run length-ny transforms over
+// the packed half plane of ny rows by h = nx/2 columns; the row stages run the
+// length-nx real transforms.
 // Kernel variants of the L-BFGS FFT stages, chosen per shape by the autotuner
 // (wf_solve.cu) or forced through wf_opts.fft_variant.
 enum { WF_COLINV_TMA_K = 1, WF_COLINV_PP_K = 2, WF_COLINV_INPLACE_K = 3 };
@@ -168,7 +220,9 @@ enum { WF_ROW_PP_K = 1, WF_ROW_INPLACE_K = 2 };
 #define WF_TUNE_MAXDIV 4  // tiles may be 1, 2 or 4 times narrower than the widest
 
 struct WfGeo {
-  int n, h, lgn, lgh, C;
+  int n, h, lgn, lgh, C;  // n = ny rows (column-transform length), h = nx / 2
+  int nx, lgnx;           // pixels per row
+  int ksx, ksy;           // wavevector of mode (my, mx) along (ksx mx, ksy my): square pixels
   int TC, ntile;   // packed columns per column tile, tiles per map
   int RB, nrb;     // rows per row block (over the C*n rows), row blocks per map
   int ncomb;       // partial sums per map and slot of the streaming L-BFGS kernels
@@ -179,7 +233,8 @@ struct WfGeo {
 };
 
 // Widest tiles and the default kernel variants.
-WfGeo wf_make_geo(int n, int C);
+WfGeo wf_make_geo(int ny, int nx, int C);
+inline WfGeo wf_make_geo(int n, int C) { return wf_make_geo(n, n, C); }
 // Blocks per map of the band reductions: about 4096 modes each, at most 64.
 inline int wf_band_nblk(const WfGeo& g) {
   const long long nsp = (long long)g.C * g.n * (g.h + 1);
@@ -192,11 +247,11 @@ WfGeo wf_geo_variant(const WfGeo& base, int colinv_kind, int row_kind, int tc_di
 
 // Device pointers of one problem, in the working type T (float or double).
 struct WfBufs {
-  const void* d;      // [B][C][n][n]
-  const void* w;      // [B][C][n][n]   mask * Ninv
-  const void* sp;     // [B or 1][C][n][h+1]   sqrt(P) / n
+  const void* d;      // [B][C][ny][nx]
+  const void* w;      // [B][C][ny][nx]   mask * Ninv
+  const void* sp;     // [B or 1][C][ny][h+1]   sqrt(P / (ny nx))
   long long sp_stride;  // elements between maps' sqrt(P) tables (0 if shared)
-  void* scratch;      // [B][C][n][h] complex: between the column and row stages
+  void* scratch;      // [B][C][ny][h] complex: between the column and row stages
   double* part;       // [B][WF_NSLOT][maxblk]
   const void* tw;     // twiddle table, WF_NT complex of type T
   int B;
@@ -236,9 +291,9 @@ __host__ __device__ inline int wf_sfold(int m) { return m > 1 ? m - 1 : 1; }
 #define WF_WAIT_CYCLES_DEFAULT 4000000000ll
 struct WfLbBufs {
   WfLbMap* st;      // [B]
-  void* s;          // packed state [B][C][n][h]
+  void* s;          // packed state [B][C][ny][h]
   void* g;          // packed gradient
-  void* ring;       // [2m][B][C][n][h]: P slots then Q slots
+  void* ring;       // [2m][B][C][ny][h]: P slots then Q slots
   int m;
   int inject_map;   // map whose tile copies are never issued (-1: none), see wf_opts
   long long spin_limit;  // bound of device waits, SM cycles

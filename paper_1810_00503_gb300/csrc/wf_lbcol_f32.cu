@@ -2,3 +2,5 @@
 #include "wf_ops_impl.cuh"
 
 WF_INSTANTIATE_LBCOL(float)
+
+WF_DBG_READER(lbcol_f32)

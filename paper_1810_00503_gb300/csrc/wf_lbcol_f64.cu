@@ -2,3 +2,5 @@
 #include "wf_ops_impl.cuh"
 
 WF_INSTANTIATE_LBCOL(double)
+
+WF_DBG_READER(lbcol_f64)

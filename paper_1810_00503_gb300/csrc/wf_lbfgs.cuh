@@ -185,7 +185,7 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
     for (int i = 0; i < NV; ++i) {
       const int c = (tid + i * WF_COMB_THREADS) * VW;
       ok[i] = c < clen;
-      u[i] = c / VW;
+      u[i] = (int)(WF_CHK_IF(ok[i], c0 + c, vsz) - c0) / VW;  // the map vector's element c0 + c
       col0[i] = ((c0 + c) % h) == 0;
     }
     auto wdot = [&](VT a, VT c, int i) -> float {
@@ -312,7 +312,7 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
     for (int i = 0; i < NV; ++i) {
       const int c = (tid + i * WF_COMB_THREADS) * VW;
       ok[i] = c < clen;
-      u[i] = c / VW;
+      u[i] = (int)(WF_CHK_IF(ok[i], c0 + c, vsz) - c0) / VW;  // the map vector's element c0 + c
       col0[i] = ((c0 + c) % h) == 0;
     }
     auto wdot = [&](VT a, VT c, int i) -> float {
@@ -380,8 +380,8 @@ k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const vo
 // FFT passes of one tile, the copy engine brings in the next tile, whose first
 // pass then reads shared memory (the per-mode operator R sqrt(P)/n applied on
 // the way in, as in wf_col_inv_pp).  tm: 2-D view of the whole history ring,
-// rows of n/2 packed values; the map's direction P[next] is rows
-// ((next B + b) C n + r).
+// rows of h = nx/2 packed values; the map's direction P[next] is rows
+// ((next B + b) C ny + r).
 template <typename T>
 __host__ __device__ constexpr size_t wf_colinv_tma_smem() {
   return (3 * (size_t)WF_TILE + WF_NT) * sizeof(V2<T>) + 128;  // + room to align the TMA tile to 128 B
@@ -451,10 +451,12 @@ k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, cons
     parity ^= 1u;
     auto ld0 = [&](int t, int row) -> V2<T> {
       const int c = t >> lgTC, col = t & (TC - 1);
-      auto lds = [&](int cc, int rr) { return Ct[(size_t)(cc * n + rr) * TC + col]; };
-      return wf_mode_packed<T, C, false>(lds, row, c, kx0 + col, n, sp);
+      auto lds = [&](int cc, int rr) { return Ct[WF_CHK((size_t)(cc * n + rr) * TC + col, WF_TILE)]; };
+      return wf_mode_packed<T, C, false>(lds, row, c, kx0 + col, g, sp);
     };
-    auto stl = [&](int t, int row, V2<T> v) { scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))] = v; };
+    auto stl = [&](int t, int row, V2<T> v) {
+      scr[WF_CHK(((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1)), vsz)] = v;
+    };
     const int itn = next_active(it + gridDim.x);
     auto after1 = [&]() {  // every thread is done with Ct: bring in the next tile
       if (tid == 0) pending = itn < nitems ? issue(itn) : false;
@@ -502,8 +504,8 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
     for (int ii = 0; ii < EB; ++ii) {
       const int r = r0 + ii * rstep;
       if (r < rows) {
-        pl[ii] = Pb[r * h];
-        gl[ii] = gb[r * h];
+        pl[ii] = Pb[WF_CHK((size_t)r * h + kx, vsz) - kx];
+        gl[ii] = gb[WF_CHK((size_t)r * h + kx, vsz) - kx];
       }
     }
 #pragma unroll
@@ -514,7 +516,7 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
         const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
         const V2<T> p = pl[ii], gg = gl[ii];
         const V2<T> q = mk<T>((T)2 * (p.x - a.x), (T)2 * (p.y - a.y));
-        Qb[r * h] = q;
+        Qb[WF_CHK((size_t)r * h + kx, vsz) - kx] = q;
         qq += wk * (A)(q.x * q.x + q.y * q.y);
         pq += wk * (A)(p.x * q.x + p.y * q.y);
         pp += wk * (A)(p.x * p.x + p.y * p.y);

@@ -2,3 +2,5 @@
 #include "wf_ops_impl.cuh"
 
 WF_INSTANTIATE_LBROW(float)
+
+WF_DBG_READER(lbrow_f32)

@@ -129,3 +129,5 @@ extern "C" wf_status wf_eval_noalloc(const void* s, const void* d, const void* w
   return precision == WF_FP64 ? noalloc_impl<double>(base, s, d, w, P, n, C, count, chi2, grad, st)
                               : noalloc_impl<float>(base, s, d, w, P, n, C, count, chi2, grad, st);
 }
+
+WF_DBG_READER(noalloc)

@@ -1,6 +1,7 @@
 // Operator kernels of the Wiener-filter objective (Sec. 2.2, eq_chi / eq_cost).
 //
-// One objective+gradient pass over a batch of n x n maps is three kernels:
+// One objective+gradient pass over a batch of ny x nx maps (n = ny rows of
+// nx pixels, h = nx/2 packed columns) is three kernels:
 //   k_col_inv  column stage of the inverse transform: load a tile of packed
 //              spectrum columns, multiply by R(k) sqrt(P)/n (step A1), inverse
 //              FFT along y (first half of A2), store the tile to scratch;
@@ -9,11 +10,12 @@
 //              along x (first half of A4), store back to scratch;
 //   k_col_fwd  forward FFT along y (rest of A4), sqrt(P) R(k)^T / n (adjoint,
 //              A5), g = 2 (s - .), prior term sum |s|^2, store g.
-// Spectra are held in a packed half-plane layout [n][n/2] in which column 0
-// carries the two self-conjugate columns kx = 0 and kx = n/2 as X0 + i Xh;
+// Spectra are held in a packed half-plane layout [ny][nx/2] in which column 0
+// carries the two self-conjugate columns kx = 0 and kx = nx/2 as X0 + i Xh;
 // the column FFT of that packed column is then an ordinary complex FFT whose
 // real and imaginary parts are the two real row-DC / row-Nyquist signals.
-// Only per-mode operations unpack it, pairing ky with n - ky.
+// Only per-mode operations unpack it, pairing ky with ny - ky.  The scale
+// written sqrt(P)/n below is sqrt(P / (ny nx)), the unitary normalisation.
 #pragma once
 #include "wf_fft.cuh"
 #include "wf_internal.h"
@@ -58,33 +60,36 @@ __device__ __forceinline__ void wf_stage_tw(V2<T>* s_tw, const V2<T>* g_tw, int 
 }
 
 // Kaiser-Squires cosine / sine of half-plane mode (row j, column kx), kx in
-// [0, n/2]: c = (kx^2 - ky^2)/k^2, s = 2 kx ky / k^2 with ky the signed row
-// frequency (row n/2 taken as -n/2); s = 0 on the Nyquist row and column, and
-// R = identity at k = 0 (App. C operator divided by -k^2).
+// [0, nx/2]: c = (qx^2 - qy^2)/q^2, s = 2 qx qy / q^2 for the wavevector
+// q = (ksx kx, ksy my) of the mode, my the signed row frequency (row ny/2
+// taken as -ny/2; on square maps q is the pair of mode numbers); s = 0 on the
+// Nyquist row and column, and R = identity at k = 0 (App. C operator divided
+// by -k^2).
 template <typename T>
-__device__ __forceinline__ void wf_ks(int kx, int j, int n, T& c, T& s) {
-  const int h = n >> 1;
-  const int ky = j < h ? j : j - n;
-  const int k2 = kx * kx + ky * ky;
+__device__ __forceinline__ void wf_ks(int kx, int j, const WfGeo& g, T& c, T& s) {
+  const int hy = g.n >> 1;
+  const int ky = j < hy ? j : j - g.n;
+  const int qx = kx * g.ksx, qy = ky * g.ksy;
+  const int k2 = qx * qx + qy * qy;
   if (k2 == 0) { c = (T)1; s = (T)0; return; }
   const T inv = (T)1 / (T)k2;
-  c = (T)(kx * kx - ky * ky) * inv;
-  s = (kx == h || ky == -h) ? (T)0 : (T)(2 * kx * ky) * inv;
+  c = (T)(qx * qx - qy * qy) * inv;
+  s = (kx == g.h || ky == -hy) ? (T)0 : (T)(2 * qx * qy) * inv;
 }
 
 // Per-mode operator on the C channel values of one mode.
 //   forward (ADJ = false): v <- R(k) diag(sp) v * extra        (step A1)
 //   adjoint (ADJ = true):  v <- diag(sp) R(k)^T v * extra      (step A5)
 // wf_mode_op_pre takes a0, a1 = the two channels' sqrt(P)/n times extra (a1
-// unused for C = 1); wf_mode_op reads them from sp, this map's [C][n][n/2+1]
+// unused for C = 1); wf_mode_op reads them from sp, this map's [C][ny][nx/2+1]
 // table of sqrt(P)/n.
 template <typename T, int C, bool ADJ>
-__device__ __forceinline__ void wf_mode_op_pre(V2<T>* v, int j, int kx, int n, T a0, T a1) {
+__device__ __forceinline__ void wf_mode_op_pre(V2<T>* v, int j, int kx, const WfGeo& g, T a0, T a1) {
   if constexpr (C == 1) {
     v[0] = cscale<T>(v[0], a0);
   } else {
     T c, s;
-    wf_ks<T>(kx, j, n, c, s);
+    wf_ks<T>(kx, j, g, c, s);
     if constexpr (!ADJ) {
       const V2<T> e = cscale<T>(v[0], a0), b = cscale<T>(v[1], a1);
       v[0] = mk<T>(c * e.x - s * b.x, c * e.y - s * b.y);
@@ -98,15 +103,15 @@ __device__ __forceinline__ void wf_mode_op_pre(V2<T>* v, int j, int kx, int n, T
 }
 
 template <typename T, int C, bool ADJ>
-__device__ __forceinline__ void wf_mode_op(V2<T>* v, int j, int kx, int n, const T* sp, T extra) {
-  const int pitch = (n >> 1) + 1;
+__device__ __forceinline__ void wf_mode_op(V2<T>* v, int j, int kx, const WfGeo& g, const T* sp, T extra) {
+  const int pitch = g.h + 1;
   const T a0 = sp[j * pitch + kx] * extra;
-  const T a1 = C == 2 ? sp[(size_t)n * pitch + j * pitch + kx] * extra : (T)0;
-  wf_mode_op_pre<T, C, ADJ>(v, j, kx, n, a0, a1);
+  const T a1 = C == 2 ? sp[(size_t)g.n * pitch + j * pitch + kx] * extra : (T)0;
+  wf_mode_op_pre<T, C, ADJ>(v, j, kx, g, a0, a1);
 }
 
-// Unpack the packed column value pair (Y[j], Y[n-j]) into the kx = 0 and
-// kx = n/2 values at row j: X0 = (Y + conj Ym)/2, Xh = -i (Y - conj Ym)/2.
+// Unpack the packed column value pair (Y[j], Y[ny-j]) into the kx = 0 and
+// kx = nx/2 values at row j: X0 = (Y + conj Ym)/2, Xh = -i (Y - conj Ym)/2.
 template <typename T>
 __device__ __forceinline__ void wf_unpack0(V2<T> Y, V2<T> Ym, V2<T>& X0, V2<T>& Xh) {
   X0 = mk<T>((T)0.5 * (Y.x + Ym.x), (T)0.5 * (Y.y - Ym.y));
@@ -117,7 +122,7 @@ __device__ __forceinline__ void wf_unpack0(V2<T> Y, V2<T> Ym, V2<T>& X0, V2<T>& 
 template <typename T>
 __device__ __forceinline__ V2<T> wf_pack0(V2<T> X0, V2<T> Xh) { return mk<T>(X0.x - Xh.y, X0.y + Xh.x); }
 
-// Apply the per-mode operator to a column tile held as [n][C*TC] in shared
+// Apply the per-mode operator to a column tile held as [ny][C*TC] in shared
 // memory (element (row j, channel c, column t) at j*C*TC + c*TC + t), tile
 // starting at packed column kx0.  The packed column 0 is unpacked in pairs.
 template <typename T, bool SWP>
@@ -126,8 +131,8 @@ __device__ __forceinline__ int wf_swz(int x) {
   else return wf_sw<T>(x);
 }
 template <typename T, int C, bool ADJ, bool SWP = false>
-__device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx0, const T* sp, T extra) {
-  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, pitch = h + 1;
+__device__ __forceinline__ void wf_col_scale(V2<T>* buf, const WfGeo& g, int lgTC, int kx0, const T* sp, T extra) {
+  const int n = g.n, TC = 1 << lgTC, CT = C * TC, h = g.h, pitch = h + 1;
   // U elements per trip, their sqrt(P) values loaded before any is used.  A
   // thread's column t is fixed (blockDim is a multiple of TC); the packed
   // column kx = 0 is not written here (its threads' stores are predicated
@@ -153,7 +158,7 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
         V2<T> v[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) v[c] = buf[wf_swz<T, SWP>(j * CT + c * TC + t)];
-        wf_mode_op_pre<T, C, ADJ>(v, j, kx, n, a0[u] * extra, C == 2 ? a1[u] * extra : (T)0);
+        wf_mode_op_pre<T, C, ADJ>(v, j, kx, g, a0[u] * extra, C == 2 ? a1[u] * extra : (T)0);
         if (!keep) {
 #pragma unroll
           for (int c = 0; c < C; ++c) buf[wf_swz<T, SWP>(j * CT + c * TC + t)] = v[c];
@@ -166,7 +171,7 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
   for (int i = 0; i < full_trips; ++i, j0 += U * jstep) trip(j0, std::true_type());
   if (j0 < n) trip(j0, std::false_type());
   if (kx0 == 0) {
-    for (int j = threadIdx.x; j <= h; j += blockDim.x) {
+    for (int j = threadIdx.x; j <= (n >> 1); j += blockDim.x) {
       const int jm = (n - j) & (n - 1);
       V2<T> X0[C], Xh[C], X0m[C], Xhm[C];
 #pragma unroll
@@ -175,10 +180,10 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
         wf_unpack0<T>(Y, Ym, X0[c], Xh[c]);
         wf_unpack0<T>(Ym, Y, X0m[c], Xhm[c]);
       }
-      wf_mode_op<T, C, ADJ>(X0, j, 0, n, sp, extra);
-      wf_mode_op<T, C, ADJ>(Xh, j, h, n, sp, extra);
-      wf_mode_op<T, C, ADJ>(X0m, jm, 0, n, sp, extra);
-      wf_mode_op<T, C, ADJ>(Xhm, jm, h, n, sp, extra);
+      wf_mode_op<T, C, ADJ>(X0, j, 0, g, sp, extra);
+      wf_mode_op<T, C, ADJ>(Xh, j, h, g, sp, extra);
+      wf_mode_op<T, C, ADJ>(X0m, jm, 0, g, sp, extra);
+      wf_mode_op<T, C, ADJ>(Xhm, jm, h, g, sp, extra);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         buf[wf_swz<T, SWP>(j * CT + c * TC)] = wf_pack0<T>(X0[c], Xh[c]);
@@ -191,14 +196,13 @@ __device__ __forceinline__ void wf_col_scale(V2<T>* buf, int n, int lgTC, int kx
 // Load a column tile of a spectrum given either packed ([C][n][h]) or in the
 // standard rfft2 layout ([C][n][h+1]); the tile is stored packed.
 template <typename T, int C, int IN>
-__device__ __forceinline__ V2<T> wf_load_spec(const V2<T>* src, int c, int j, int kx, int n) {
-  const int h = n >> 1;
+__device__ __forceinline__ V2<T> wf_load_spec(const V2<T>* src, int c, int j, int kx, int n, int h) {
   if constexpr (IN == WF_IN_PK) {
-    return src[((size_t)c * n + j) * h + kx];
+    return src[WF_CHK(((size_t)c * n + j) * h + kx, (size_t)C * n * h)];
   } else {
-    const V2<T>* row = src + ((size_t)c * n + j) * (h + 1);
+    const V2<T>* row = src + WF_CHK(((size_t)c * n + j) * (h + 1), (size_t)C * n * (h + 1) - h);
     if (kx == 0) return wf_pack0<T>(row[0], row[h]);
-    return row[kx];
+    return row[WF_CHK(kx, h + 1)];
   }
 }
 
@@ -206,8 +210,8 @@ __device__ __forceinline__ V2<T> wf_load_spec(const V2<T>* src, int c, int j, in
 // single complex values.  Tile element (row j, channel c, column t) lives at
 // buf[j*C*TC + c*TC + t]; in the packed vector at ((c*n + j)*h + kx0 + t).
 template <typename T, int C, int IN>
-__device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n, int lgTC, int kx0) {
-  const int TC = 1 << lgTC, CT = C * TC, lgn = __ffs(n) - 1, tot = C * n * TC, h = n >> 1;
+__device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n, int h, int lgTC, int kx0) {
+  const int TC = 1 << lgTC, CT = C * TC, lgn = __ffs(n) - 1, tot = C * n * TC;
   if constexpr (IN == WF_IN_PK && sizeof(T) == 4) {
     if (TC >= 2) {
       // a thread's column pair t is fixed (blockDim is a multiple of TC / 2);
@@ -220,7 +224,7 @@ __device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n
 #pragma unroll
       for (int i = 0; i < WF_EMAX / 2; ++i) {
         const int r = r0 + i * rstep;
-        if (r < rows) v[i] = *(const float4*)(sb + r * h);
+        if (r < rows) v[i] = *(const float4*)(sb + WF_CHK((size_t)r * h + kx0 + t, (size_t)rows * h - 1) - kx0 - t);
       }
 #pragma unroll
       for (int i = 0; i < WF_EMAX / 2; ++i) {
@@ -240,7 +244,7 @@ __device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n
     const int e = threadIdx.x + i * WF_THREADS;
     if (e < tot) {
       const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
-      v[i] = wf_load_spec<T, C, IN>(src, c, j, kx0 + t, n);
+      v[i] = wf_load_spec<T, C, IN>(src, c, j, kx0 + t, n, h);
     }
   }
 #pragma unroll
@@ -254,8 +258,8 @@ __device__ __forceinline__ void wf_tile_load(V2<T>* buf, const V2<T>* src, int n
 }
 
 template <typename T, int C>
-__device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, int n, int lgTC, int kx0) {
-  const int TC = 1 << lgTC, CT = C * TC, h = n >> 1, lgn = __ffs(n) - 1, tot = C * n * TC;
+__device__ __forceinline__ void wf_tile_store_pk(V2<T>* dst, const V2<T>* buf, int n, int h, int lgTC, int kx0) {
+  const int TC = 1 << lgTC, CT = C * TC, lgn = __ffs(n) - 1, tot = C * n * TC;
   if constexpr (sizeof(T) == 4) {
     if (TC >= 2) {
       // as in wf_tile_load: fixed column pair t, rows r0 + i rstep
@@ -352,12 +356,12 @@ __device__ __forceinline__ void wf_col_inv_body(const WfGeo& g, const V2<T>* src
   V2<T>* buf = s_tw + WF_NT;
   const int n = g.n, lgTC = __ffs(g.TC) - 1, kx0 = blockIdx.x * g.TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, g.lgn);
-  wf_tile_load<T, C, IN>(buf, src, n, lgTC, kx0);
+  wf_tile_load<T, C, IN>(buf, src, n, g.h, lgTC, kx0);
   __syncthreads();
-  wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp, (T)1);
+  wf_col_scale<T, C, false>(buf, g, lgTC, kx0, sp, (T)1);
   __syncthreads();
   fft_smem<T, +1, WF_EMAX>(buf, g.lgn, C * g.TC, 1, C * g.TC, s_tw);
-  wf_tile_store_pk<T, C>(scr, buf, n, lgTC, kx0);
+  wf_tile_store_pk<T, C>(scr, buf, n, g.h, lgTC, kx0);
 }
 
 template <typename T, int C, int IN>
@@ -376,10 +380,10 @@ __device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* sc
                                                  V2<T>* s_tw, const void* tw_) {
   const int n = g.n, lgTC = __ffs(g.TC) - 1, CT = C * g.TC, kx0 = blockIdx.x * g.TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, g.lgn);
-  wf_tile_load<T, C, WF_IN_PK>(buf, scr, n, lgTC, kx0);
+  wf_tile_load<T, C, WF_IN_PK>(buf, scr, n, g.h, lgTC, kx0);
   __syncthreads();
   fft_smem<T, -1, WF_EMAX>(buf, g.lgn, CT, 1, CT, s_tw);
-  wf_col_scale<T, C, true>(buf, n, lgTC, kx0, sp, (T)1);
+  wf_col_scale<T, C, true>(buf, g, lgTC, kx0, sp, (T)1);
   __syncthreads();
 }
 
@@ -396,7 +400,7 @@ __device__ __forceinline__ void wf_col_fwd_out(const WfGeo& g, V2<T>* buf, const
   for (int e = threadIdx.x; e < C * n * TC; e += blockDim.x) {
     const int t = e & (TC - 1), r = e >> lgTC, j = r & (n - 1), c = r >> lgn;
     const int kx = kx0 + t;
-    const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n);
+    const V2<T> sv = wf_load_spec<T, C, IN>(src, c, j, kx, n, h);
     const V2<T> a = buf[wf_swz<T, SWP>(j * CT + c * TC + t)];
     const V2<T> o = mk<T>((T)2 * (sv.x - a.x), (T)2 * (sv.y - a.y));
     const T m2 = sv.x * sv.x + sv.y * sv.y;
@@ -404,10 +408,10 @@ __device__ __forceinline__ void wf_col_fwd_out(const WfGeo& g, V2<T>* buf, const
     acc += (kx == 0) ? m2 : (T)2 * m2;
     acc2 += (kx == 0) ? o2 : (T)2 * o2;
     if constexpr (IN == WF_IN_PK) {
-      dst[((size_t)c * n + j) * h + kx] = o;
+      dst[WF_CHK(((size_t)c * n + j) * h + kx, (size_t)C * n * h)] = o;
     } else {
       if (kx == 0) buf[wf_swz<T, SWP>(j * CT + c * TC + t)] = o;
-      else dst[((size_t)c * n + j) * (h + 1) + kx] = o;
+      else dst[WF_CHK(((size_t)c * n + j) * (h + 1) + kx, (size_t)C * n * (h + 1))] = o;
     }
   }
   if constexpr (IN == WF_IN_STD) {
@@ -419,7 +423,7 @@ __device__ __forceinline__ void wf_col_fwd_out(const WfGeo& g, V2<T>* buf, const
         for (int c = 0; c < C; ++c) {
           V2<T> X0, Xh;
           wf_unpack0<T>(buf[wf_swz<T, SWP>(j * CT + c * TC)], buf[wf_swz<T, SWP>(jm * CT + c * TC)], X0, Xh);
-          V2<T>* row = dst + ((size_t)c * n + j) * (h + 1);
+          V2<T>* row = dst + WF_CHK(((size_t)c * n + j) * (h + 1), (size_t)C * n * (h + 1) - h);
           row[0] = X0;
           row[h] = Xh;
         }
@@ -447,10 +451,10 @@ k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const vo
   const int b = blockIdx.y, n = g.n, h = g.h, lgn = g.lgn;
   const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
-  wf_tile_load<T, C, WF_IN_PK>(buf, (const V2<T>*)scratch_ + (size_t)b * C * n * h, n, lgTC, kx0);
+  wf_tile_load<T, C, WF_IN_PK>(buf, (const V2<T>*)scratch_ + (size_t)b * C * n * h, n, h, lgTC, kx0);
   __syncthreads();
   fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
-  wf_col_scale<T, C, true>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
+  wf_col_scale<T, C, true>(buf, g, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1);
   __syncthreads();
   const size_t sstride = (size_t)C * n * (IN == WF_IN_PK ? h : h + 1);
   wf_col_fwd_out<T, C, IN, false>(g, buf, (const V2<T>*)src_ + (size_t)b * sstride,
@@ -474,7 +478,7 @@ __global__ void k_band_scale(const T* sp0, T* sp, size_t nsp, int ntab, const in
 
 // ---------------------------------------------------------------------------
 // k_col_sim: scratch tile holding the row r2c of a white field z -> forward
-// FFT along y -> scale by 1/n (unitary U z) -> R sqrt(P)/n -> inverse FFT
+// FFT along y -> scale by 1/sqrt(ny nx) (unitary U z) -> R sqrt(P)/n -> inverse FFT
 // along y -> scratch.  Used to synthesise A z for simulations.
 // ---------------------------------------------------------------------------
 template <typename T, int C>
@@ -487,17 +491,18 @@ k_col_sim(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void
   const int TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC, kx0 = blockIdx.x * TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, lgn);
   V2<T>* sc = (V2<T>*)scratch_ + (size_t)b * C * n * h;
-  wf_tile_load<T, C, WF_IN_PK>(buf, sc, n, lgTC, kx0);
+  wf_tile_load<T, C, WF_IN_PK>(buf, sc, n, h, lgTC, kx0);
   __syncthreads();
   fft_smem<T, -1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
-  wf_col_scale<T, C, false>(buf, n, lgTC, kx0, sp_ + (size_t)b * sp_stride, (T)1 / (T)n);
+  const T unit = (T)(1.0 / sqrt((double)n * (double)g.nx));
+  wf_col_scale<T, C, false>(buf, g, lgTC, kx0, sp_ + (size_t)b * sp_stride, unit);
   __syncthreads();
   fft_smem<T, +1, WF_EMAX>(buf, lgn, CT, 1, CT, s_tw);
-  wf_tile_store_pk<T, C>(sc, buf, n, lgTC, kx0);
+  wf_tile_store_pk<T, C>(sc, buf, n, h, lgTC, kx0);
 }
 
 // ---------------------------------------------------------------------------
-// k_row: row stage over RB of the C*n rows of each map.
+// k_row: row stage over RB of the C*ny rows of each map (rows of nx pixels).
 //   MODE DATA / NODATA: c2r, r = d - x (or -x), wr = w r, data partial sum
 //     r.wr, r2c of wr, store packed rows back to scratch.
 //   MODE SIGNAL: c2r, write x to out (pixel layout).
@@ -509,27 +514,27 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
                                            const void* aux_, void* out_, double* part, const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   V2<T>* s_tw = (V2<T>*)wf_smem;   // roots of unity (real-FFT pre/post twiddles)
-  V2<T>* s_pt = s_tw + WF_NT;       // pass table of length n/2
+  V2<T>* s_pt = s_tw + WF_NT;       // pass table of length nx/2
   V2<T>* buf = s_pt + WF_NT;
-  const int b = blockIdx.y, n = g.n, h = g.h, lgh = g.lgh, RB = g.RB;
+  const int b = blockIdx.y, n = g.n, nx = g.nx, h = g.h, lgh = g.lgh, RB = g.RB;
   const int row0 = blockIdx.x * RB;
-  const size_t npix = (size_t)g.C * n * n;
+  const size_t npix = (size_t)g.C * n * nx;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_);
   wf_stage_tw<T>(s_pt, (const V2<T>*)tw_, lgh);
   V2<T>* sc = (V2<T>*)scratch_ + (size_t)b * g.C * n * h + (size_t)row0 * h;
   const int tot = RB * h;
-  const int lgNTn = WF_LOG2_NT - g.lgn;  // table stride of the n-th roots
+  const int lgNTn = WF_LOG2_NT - g.lgnx;  // table stride of the nx-th roots
   double acc = 0.0;
 
   if constexpr (MODE == WF_ROW_RFFT) {
-    const V2<T>* z = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * n);
+    const V2<T>* z = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * nx);
     wf_g2s<T>(buf, z, tot);
     __syncthreads();
   } else {
     wf_g2s<T>(buf, sc, tot);
     __syncthreads();
     // c2r pre-processing: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]),
-    // w = exp(+2 pi i / n), X[0], X[h] the real parts packed in Y[0].
+    // w = exp(+2 pi i / nx), X[0], X[h] the real parts packed in Y[0].
     for (int e = threadIdx.x; e < RB * (h / 2 + 1); e += blockDim.x) {
       const int t = e / (h / 2 + 1), k = e - t * (h / 2 + 1);
       const int r0 = t * h;
@@ -549,15 +554,15 @@ __device__ __forceinline__ void k_row_body(WfGeo g, void* scratch_, const void* 
     __syncthreads();
     fft_smem<T, +1, WF_EMAX>(buf, lgh, RB, h, 1, s_pt);
     // pixel stage: buf[t][m] holds pixels (2m, 2m+1) of row row0 + t
-    const V2<T>* dv = (const V2<T>*)((const T*)d_ + (size_t)b * npix + (size_t)row0 * n);
-    const V2<T>* wv = (const V2<T>*)((const T*)w_ + (size_t)b * npix + (size_t)row0 * n);
+    const V2<T>* dv = (const V2<T>*)((const T*)d_ + (size_t)b * npix + (size_t)row0 * nx);
+    const V2<T>* wv = (const V2<T>*)((const T*)w_ + (size_t)b * npix + (size_t)row0 * nx);
     if constexpr (MODE == WF_ROW_SIGNAL) {
-      V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * n);
+      V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * nx);
       wf_s2g<T>(ov, buf, tot);
       return;
     } else if constexpr (MODE == WF_ROW_SIM) {
-      V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * n);
-      const V2<T>* nz = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * n);
+      V2<T>* ov = (V2<T>*)((T*)out_ + (size_t)b * npix + (size_t)row0 * nx);
+      const V2<T>* nz = (const V2<T>*)((const T*)aux_ + (size_t)b * npix + (size_t)row0 * nx);
       for (int e = threadIdx.x; e < tot; e += blockDim.x) {
         const V2<T> x = buf[wf_sw<T>(e)], w = wv[e], q = nz[e];
         ov[e] = mk<T>(w.x > (T)0 ? x.x + q.x : (T)0, w.y > (T)0 ? x.y + q.y : (T)0);
@@ -640,7 +645,7 @@ k_finalize_chi2(const double* part, int maxblk, int nprior, int ndata, double* c
 }
 
 // ---------------------------------------------------------------------------
-// Input preparation: working-type copies of d, W = mask * Ninv, sqrt(P)/n,
+// Input preparation: working-type copies of d, W = mask * Ninv, sqrt(P/(ny nx)),
 // with checks recorded in flags[0] as a wf_status bit set (1 << status).
 // ---------------------------------------------------------------------------
 struct WfMapPtrs { const void* d; const unsigned char* mask; const void* Ninv; const void* P; };
@@ -652,11 +657,11 @@ template <typename T>
 __global__ void k_prep(WfGeo g, const WfMapPtrs* maps, int in_f64, T* d, T* w, T* sp, int sp_shared,
                        int* flags) {
   const int b = blockIdx.y, n = g.n, C = g.C;
-  const size_t npix = (size_t)C * n * n, nsp = (size_t)C * n * (g.h + 1);
+  const size_t npix = (size_t)C * n * g.nx, nsp = (size_t)C * n * (g.h + 1);
   const WfMapPtrs m = maps[b];
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride) {
-    const size_t pix = i % ((size_t)n * n);
+    const size_t pix = i % ((size_t)n * g.nx);
     const double ni = in_f64 ? wf_rd<double>(m.Ninv, i) : wf_rd<float>(m.Ninv, i);
     const double dv = m.d ? (in_f64 ? wf_rd<double>(m.d, i) : wf_rd<float>(m.d, i)) : 0.0;
     const bool obs = m.mask[pix] != 0;
@@ -672,7 +677,8 @@ __global__ void k_prep(WfGeo g, const WfMapPtrs* maps, int in_f64, T* d, T* w, T
     const double pv = in_f64 ? wf_rd<double>(m.P, i) : wf_rd<float>(m.P, i);
     if (!isfinite(pv)) atomicOr(flags, 1 << WF_ENONFINITE);
     else if (pv < 0.0) atomicOr(flags, 1 << WF_EINVAL);
-    const double s = (isfinite(pv) && pv > 0.0) ? sqrt(pv) / (double)n : 0.0;
+    const double s = !(isfinite(pv) && pv > 0.0) ? 0.0
+                     : (g.nx == n ? sqrt(pv) / (double)n : sqrt(pv / ((double)n * (double)g.nx)));
     sp[(size_t)b * nsp + i] = (T)s;
   }
 }
@@ -683,7 +689,7 @@ __global__ void k_set_data(size_t total, const T* src, T* d) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) d[i] = src[i];
 }
 
-// Standard [C][n][h+1] <-> packed [C][n][h] spectra.
+// Standard [C][ny][h+1] <-> packed [C][ny][h] spectra.
 template <typename T>
 __global__ void k_pack(WfGeo g, int B, const V2<T>* in, V2<T>* out) {
   const int n = g.n, h = g.h;
@@ -720,7 +726,7 @@ __global__ void k_unpack(WfGeo g, int B, const V2<T>* in, V2<T>* out) {
 }
 
 // Per-block band sums over the half-plane modes of standard-layout spectra,
-// with the full-plane multiplicity (1 on kx = 0 and n/2, else 2):
+// with the full-plane multiplicity (1 on kx = 0 and nx/2, else 2):
 //   MODE 0 (band energy, eq. el):      |s_k|^2
 //   MODE 1 (d chi2 / d log q, eq. pilin): -Re(conj(a_k) s_k), a = s - grad / 2
 //          (grad = 2 (s - a) from the objective + gradient pass)

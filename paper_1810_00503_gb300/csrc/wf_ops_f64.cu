@@ -2,3 +2,5 @@
 #include "wf_ops_impl.cuh"
 
 WF_INSTANTIATE_OPS(double)
+
+WF_DBG_READER(ops_f64)

@@ -5,12 +5,20 @@
 
 namespace wfimpl {
 
+// Shared memory of the in-place stages: the pass tables and the tile (a full
+// WF_TILE in the bounds-checked build, where tile indices are checked against
+// WF_TILE).
+#ifdef WF_DEBUG_BOUNDS
+template <typename T> inline size_t col_smem(const WfGeo&) { return (WF_NT + (size_t)WF_TILE) * sizeof(V2<T>); }
+template <typename T> inline size_t row_smem(const WfGeo&) { return (2 * WF_NT + (size_t)WF_TILE) * sizeof(V2<T>); }
+#else
 template <typename T> inline size_t col_smem(const WfGeo& g) {
   return (WF_NT + (size_t)g.C * g.TC * g.n) * sizeof(V2<T>);
 }
 template <typename T> inline size_t row_smem(const WfGeo& g) {
   return (2 * WF_NT + (size_t)g.RB * g.h) * sizeof(V2<T>);
 }
+#endif
 
 // Raise the dynamic shared-memory limit of a kernel once per device.
 template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes, int* done_mask) {
@@ -220,23 +228,6 @@ inline cudaError_t persistent_grid(K k, size_t smem, int* occ, int* nsm, int* gr
   return cudaSuccess;
 }
 
-// 2-D tensor map of [rows][2 h] values of type T (packed spectra), boxes of
-// 2 TC values by min(C n, 256) rows.
-template <typename T>
-inline cudaError_t spectra_map(const WfGeo& g, void* base, long long rows, CUtensorMap* tm) {
-  WfEncodeTiled enc = wf_encode_fn();
-  if (!enc) return cudaErrorNotSupported;
-  const int crow = g.C * g.n;
-  const cuuint64_t dims[2] = {(cuuint64_t)2 * g.h, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)2 * g.h * sizeof(T)};
-  const cuuint32_t box[2] = {(cuuint32_t)(2 * g.TC), (cuuint32_t)(crow < 256 ? crow : 256)};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(tm, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
-                         base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 template <typename T, int C, int KIND, int PLAN>
 cudaError_t lb_colinv_tile(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
   static int done = 0;
@@ -295,7 +286,7 @@ inline int grid1d(size_t total, int cap) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(dm, hm, sizeof(WfMapPtrs) * (size_t)B,
                                               cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-      const size_t npix = (size_t)g.C * g.n * g.n;
+      const size_t npix = (size_t)g.C * g.n * g.nx;
       k_prep<T><<<dim3(wfimpl::grid1d(npix, 1024), B), 256, 0, st>>>(g, dm, in_f64, (T*)d, (T*)w,
                                                                      (T*)sp, sp_shared, flags);
       e = cudaGetLastError();
@@ -308,7 +299,7 @@ inline int grid1d(size_t total, int cap) {
   template <typename T>
   cudaError_t wf_launch_set_data(const WfGeo& g, const void* src, int B, void* d,
                                     cudaStream_t st) {
-    const size_t total = (size_t)B * g.C * g.n * g.n;
+    const size_t total = (size_t)B * g.C * g.n * g.nx;
     k_set_data<T><<<wfimpl::grid1d(total, 4096), 256, 0, st>>>(total, (const T*)src, (T*)d);
     return cudaGetLastError();
   }

@@ -530,7 +530,7 @@ static wf_status ensure_solver(wf_problem* p, int m) {
   p->solver = S;
   S->m = m;
   S->B = p->count;
-  const size_t vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;  // packed complex = n^2 reals
+  const size_t vbytes = (size_t)p->count * p->C * p->n * p->nx * p->elt;  // packed complex = ny nx reals
   wf_status s = wf_alloc(p->h, &S->s, vbytes, "L-BFGS state");
   if (s == WF_OK) s = wf_alloc(p->h, &S->g, vbytes, "L-BFGS gradient");
   if (s == WF_OK) s = wf_alloc(p->h, &S->ring, vbytes * 2 * m, "L-BFGS history");
@@ -648,12 +648,12 @@ __global__ void k_tune_state(WfLbMap* st, int B, int m) {
 // fastest.  Column choices (inverse column stage variant, radix plan and
 // column tile width) are timed with the forward column stage, then the row
 // choices (row stage variant, radix plan and row block height) with those
-// fixed.  Results are cached in the handle per (n, C, precision, history
-// length, maps).
+// fixed.  Results are cached in the handle per (ny, nx, C, precision,
+// history length, maps).
 template <typename T>
 static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   const wf_opts* o = &S->o;
-  const WfGeo base = wf_make_geo(p->n, p->C);
+  const WfGeo base = wf_make_geo(p->n, p->nx, p->C);
   if (o->fft_variant) {
     p->g = variant_geo(base, o->fft_variant);
     return WF_OK;
@@ -663,7 +663,8 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
     return WF_OK;
   }
   const int m = S->o.lbfgs_m;
-  const long long key = ((((long long)p->n * 4 + p->C) * 2 + p->precision) * 64 + m) * 1000000LL + p->count;
+  const long long key =
+      (((((long long)p->n * 2048 + p->nx) * 4 + p->C) * 2 + p->precision) * 64 + m) * 1000000LL + p->count;
   {
     std::lock_guard<std::mutex> lock(p->h->mu);
     auto it = p->h->tuned.find(key);
@@ -682,7 +683,7 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
     p->g = base;  // no room to time the candidates: the defaults, not cached
     return WF_OK;
   }
-  cudaError_t ce = cudaMemcpyAsync(S->ring, S->s, (size_t)p->count * p->C * p->n * p->n * p->elt,
+  cudaError_t ce = cudaMemcpyAsync(S->ring, S->s, (size_t)p->count * p->C * p->n * p->nx * p->elt,
                                    cudaMemcpyDeviceToDevice, st);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(tst, 0, sizeof(WfLbMap) * p->count, st);
   if (ce == cudaSuccess) {
@@ -876,14 +877,14 @@ static wf_status start_impl(wf_problem* p, const wf_opts* o, const void* s0, con
   WF_TRY(cudaEventRecord(S->ev_in, us));
   WF_TRY(cudaStreamWaitEvent(st, S->ev_in, 0));
   if (s0 && !seed) WF_TRY(wf_launch_pack<T>(p->g, p->count, s0, S->s, st));
-  else WF_TRY(cudaMemsetAsync(S->s, 0, (size_t)p->count * p->C * p->n * p->n * p->elt, st));
+  else WF_TRY(cudaMemsetAsync(S->s, 0, (size_t)p->count * p->C * p->n * p->nx * p->elt, st));
   WF_TRY(cudaMemsetAsync(S->st, 0, sizeof(WfLbMap) * p->count, st));
   rs = choose_variant<T>(p, S, st);  // before the first refresh: one variant for the whole solve
   if (rs != WF_OK) return rs;
   A.ntile = p->g.ntile;
   A.nrb = p->g.nrb;
   if (seed) {
-    const size_t per = (size_t)p->C * p->n * p->n;  // reals per packed map vector
+    const size_t per = (size_t)p->C * p->n * p->nx;  // reals per packed map vector
     k_refine_seed<T><<<dim3(wf_grid(per), p->count), 256, 0, st>>>(seed->g64, seed->res, seed->tol, per,
                                                                      (T*)S->g, p->part, A.ntile, A.nrb, A.maxblk);
     WF_TRY(cudaGetLastError());
@@ -1019,8 +1020,8 @@ static wf_status refined_impl(wf_problem* p, const wf_opts* o, double tol, int m
   if (rs != WF_OK) return rs;
   WfSolver* S = p->solver;
   const int B = p->count;
-  const size_t per = (size_t)p->C * p->n * p->n;  // reals per packed map vector, pixels per map
-  const size_t nsp = (size_t)p->C * p->n * (p->n / 2 + 1) * (p->sp_shared ? 1 : B);
+  const size_t per = (size_t)p->C * p->n * p->nx;  // reals per packed map vector, pixels per map
+  const size_t nsp = (size_t)p->C * p->n * (p->nx / 2 + 1) * (p->sp_shared ? 1 : B);
   const bool mixed = p->precision == WF_MIXED;
   auto need = [&](void** q, size_t bytes, const char* what) {
     if (rs == WF_OK && !*q) rs = wf_alloc(p->h, q, bytes, what);
@@ -1046,7 +1047,7 @@ static wf_status refined_impl(wf_problem* p, const wf_opts* o, double tol, int m
   // The FP64 operator of the outer evaluations: for a MIXED problem on exact
   // FP64 copies of the working-precision inputs (the problem the inner solves
   // see), always on the default tiles.
-  const WfGeo go = wf_make_geo(p->n, p->C);
+  const WfGeo go = wf_make_geo(p->n, p->nx, p->C);
   WfBufs bo = wf_bufs(p);
   if (mixed) {
     k_convert<float, double><<<wf_grid(per * B), 256, 0, st>>>((const float*)p->d, (double*)S->r_d64, per * B);
@@ -1202,6 +1203,9 @@ static wf_status check_opts(const wf_problem* p, const wf_opts* o) {
                    o->fft_variant);
   if (o->inject_timeout_map < 0 || o->inject_timeout_map > p->count)
     return wf_fail(WF_EINVAL, "inject_timeout_map = %d outside [0, %d]", o->inject_timeout_map, p->count);
+  if (o->inject_timeout_map > 0 && wf_make_geo(p->n, p->nx, p->C).colinv_kind != WF_COLINV_TMA_K)
+    return wf_fail(WF_EINVAL, "inject_timeout_map: %d x %d maps have no TMA-fed inverse column stage", p->n,
+                   p->nx);
   if (o->line_search != WF_LS_EXACT && o->line_search != WF_LS_WOLFE)
     return wf_fail(WF_EINVAL, "line_search = %d is not WF_LS_EXACT or WF_LS_WOLFE", o->line_search);
   if (o->line_search == WF_LS_WOLFE && !(0.0 < o->c1 && o->c1 < o->c2 && o->c2 < 1.0))
@@ -1422,15 +1426,15 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
 // working type), each starting on a 256-byte boundary.
 struct WfStateHeader {
   char magic[8];
-  int n, C, precision, count, lbfgs_m, variant;
+  int n, nx, C, precision, count, lbfgs_m, variant;
   long long iters;
   size_t vbytes;  // bytes of one packed vector set (all maps)
   wf_opts o;      // the solve's options (stream not kept)
 };
-static const char kWfStateMagic[8] = {'W', 'F', 'S', 'T', 'A', 'T', 'E', '1'};
+static const char kWfStateMagic[8] = {'W', 'F', 'S', 'T', 'A', 'T', 'E', '2'};
 static size_t up256s(size_t x) { return (x + 255) & ~(size_t)255; }
 static size_t state_bytes(const wf_problem* p, int m, size_t* off_st, size_t* off_vec) {
-  const size_t vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;
+  const size_t vbytes = (size_t)p->count * p->C * p->n * p->nx * p->elt;
   *off_st = up256s(sizeof(WfStateHeader));
   *off_vec = *off_st + up256s(sizeof(WfLbMap) * p->count);
   return *off_vec + (2 + 2 * (size_t)m) * up256s(vbytes);
@@ -1456,13 +1460,14 @@ extern "C" wf_status wf_solver_export(wf_problem* p, void* dst, size_t bytes) {
   memset(&hd, 0, sizeof hd);
   memcpy(hd.magic, kWfStateMagic, 8);
   hd.n = p->n;
+  hd.nx = p->nx;
   hd.C = p->C;
   hd.precision = p->precision;
   hd.count = p->count;
   hd.lbfgs_m = m;
   hd.variant = variant_code(p->g);
   hd.iters = S->iters;
-  hd.vbytes = (size_t)p->count * p->C * p->n * p->n * p->elt;
+  hd.vbytes = (size_t)p->count * p->C * p->n * p->nx * p->elt;
   hd.o = S->o;
   hd.o.stream = nullptr;
   // Every copy is ordered on the solver's stream and finished before the call
@@ -1497,7 +1502,7 @@ static wf_status import_impl(wf_problem* p, const WfStateHeader& hd, const char*
   cudaStream_t st = wf_capturable(us) ? us : S->stream;
   if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
   S->work = st;
-  p->g = variant_geo(wf_make_geo(p->n, p->C), hd.variant);
+  p->g = variant_geo(wf_make_geo(p->n, p->nx, p->C), hd.variant);
   rs = setup_args(p, S, &S->o);
   if (rs != WF_OK) return rs;
   size_t off_st, off_vec;
@@ -1523,12 +1528,13 @@ extern "C" wf_status wf_solver_import(wf_problem* p, const void* src, size_t byt
   WfStateHeader hd;
   WF_TRY(cudaMemcpy(&hd, src, sizeof hd, cudaMemcpyDefault));
   if (memcmp(hd.magic, kWfStateMagic, 8) != 0) return wf_fail(WF_EINVAL, "wf_solver_import: not a solver checkpoint");
-  if (hd.n != p->n || hd.C != p->C || hd.precision != p->precision || hd.count != p->count)
+  if (hd.n != p->n || hd.nx != p->nx || hd.C != p->C || hd.precision != p->precision || hd.count != p->count)
     return wf_fail(WF_EINVAL,
-                   "wf_solver_import: checkpoint of n = %d, C = %d, precision %d, %d maps; problem has %d, %d, %d, %d",
-                   hd.n, hd.C, hd.precision, hd.count, p->n, p->C, p->precision, p->count);
+                   "wf_solver_import: checkpoint of %d x %d maps, C = %d, precision %d, %d maps; problem has %d x %d, "
+                   "%d, %d, %d",
+                   hd.n, hd.nx, hd.C, hd.precision, hd.count, p->n, p->nx, p->C, p->precision, p->count);
   if (!variant_valid(hd.variant) || hd.lbfgs_m < 1 || hd.lbfgs_m > WF_MAXM ||
-      hd.vbytes != (size_t)p->count * p->C * p->n * p->n * p->elt)
+      hd.vbytes != (size_t)p->count * p->C * p->n * p->nx * p->elt)
     return wf_fail(WF_EINVAL, "wf_solver_import: corrupt checkpoint header");
   size_t off_st, off_vec;
   const size_t need = state_bytes(p, hd.lbfgs_m, &off_st, &off_vec);
@@ -1575,3 +1581,15 @@ extern "C" wf_status wf_solver_history(const wf_problem* p, double* out, int* co
   }
   return WF_OK;
 }
+
+// Self-test of the bounds checks: one index five past the end of a tile.
+__global__ void k_dbg_selftest(int* sink) {
+  const long long i = WF_CHK((long long)WF_TILE + 5, WF_TILE);
+  if (sink) *sink = (int)i;
+}
+cudaError_t wf_dbg_selftest() {
+  k_dbg_selftest<<<1, 1>>>(nullptr);
+  return cudaGetLastError();
+}
+
+WF_DBG_READER(solve)

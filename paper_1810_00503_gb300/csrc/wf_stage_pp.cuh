@@ -16,23 +16,23 @@ __host__ __device__ constexpr size_t wf_pp_smem() {
 // Packed value of column tile element (row j, channel c, column kx) after the
 // per-mode operator (R(k) sqrt(P)/n, or its adjoint), read through `ld(cc, row)`
 // (channel cc's packed value at row `row` of this column).  Column 0 is
-// unpacked with row n - j, the operator applied at kx = 0 and kx = n/2, and
+// unpacked with row ny - j, the operator applied at kx = 0 and kx = nx/2, and
 // packed again.
 template <typename T, int C, bool ADJ, class LD>
-__device__ __forceinline__ V2<T> wf_mode_packed(LD& ld, int j, int c, int kx, int n, const T* sp) {
+__device__ __forceinline__ V2<T> wf_mode_packed(LD& ld, int j, int c, int kx, const WfGeo& g, const T* sp) {
   V2<T> v[C];
   if (kx != 0) {
 #pragma unroll
     for (int cc = 0; cc < C; ++cc) v[cc] = ld(cc, j);
-    wf_mode_op<T, C, ADJ>(v, j, kx, n, sp, (T)1);
+    wf_mode_op<T, C, ADJ>(v, j, kx, g, sp, (T)1);
     return v[c];
   }
-  const int jm = (n - j) & (n - 1);
+  const int jm = (g.n - j) & (g.n - 1);
   V2<T> X0[C], Xh[C];
 #pragma unroll
   for (int cc = 0; cc < C; ++cc) wf_unpack0<T>(ld(cc, j), ld(cc, jm), X0[cc], Xh[cc]);
-  wf_mode_op<T, C, ADJ>(X0, j, 0, n, sp, (T)1);
-  wf_mode_op<T, C, ADJ>(Xh, j, n >> 1, n, sp, (T)1);
+  wf_mode_op<T, C, ADJ>(X0, j, 0, g, sp, (T)1);
+  wf_mode_op<T, C, ADJ>(Xh, j, g.h, g, sp, (T)1);
   return wf_pack0<T>(X0[c], Xh[c]);
 }
 
@@ -51,27 +51,27 @@ __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, 
   auto ld0 = [&](int t, int row) -> V2<T> {
     const int c = t >> lgTC, kx = kx0 + (t & (TC - 1));
     if constexpr (IN == WF_IN_STD) {
-      if (kx == 0) {  // kx = 0 and kx = n/2 stored separately
+      if (kx == 0) {  // kx = 0 and kx = nx/2 stored separately
         V2<T> X0[C], Xh[C];
 #pragma unroll
         for (int cc = 0; cc < C; ++cc) {
-          const V2<T>* r = src + ((size_t)cc * n + row) * (h + 1);
+          const V2<T>* r = src + WF_CHK(((size_t)cc * n + row) * (h + 1), (size_t)C * n * (h + 1) - h);
           X0[cc] = r[0];
           Xh[cc] = r[h];
         }
-        wf_mode_op<T, C, false>(X0, row, 0, n, sp, (T)1);
-        wf_mode_op<T, C, false>(Xh, row, h, n, sp, (T)1);
+        wf_mode_op<T, C, false>(X0, row, 0, g, sp, (T)1);
+        wf_mode_op<T, C, false>(Xh, row, h, g, sp, (T)1);
         return wf_pack0<T>(X0[c], Xh[c]);
       }
-      auto ldg = [&](int cc, int rr) { return src[((size_t)cc * n + rr) * (h + 1) + kx]; };
-      return wf_mode_packed<T, C, false>(ldg, row, c, kx, n, sp);
+      auto ldg = [&](int cc, int rr) { return src[WF_CHK(((size_t)cc * n + rr) * (h + 1) + kx, (size_t)C * n * (h + 1))]; };
+      return wf_mode_packed<T, C, false>(ldg, row, c, kx, g, sp);
     } else {
-      auto ldg = [&](int cc, int rr) { return src[((size_t)cc * n + rr) * h + kx]; };
-      return wf_mode_packed<T, C, false>(ldg, row, c, kx, n, sp);
+      auto ldg = [&](int cc, int rr) { return src[WF_CHK(((size_t)cc * n + rr) * h + kx, (size_t)C * n * h)]; };
+      return wf_mode_packed<T, C, false>(ldg, row, c, kx, g, sp);
     }
   };
   auto stl = [&](int t, int row, V2<T> v) {
-    scr[((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1))] = v;
+    scr[WF_CHK(((size_t)(t >> lgTC) * n + row) * h + kx0 + (t & (TC - 1)), (size_t)C * n * h)] = v;
   };
   wf_pp_fft<T, +1, true, PLAN>(lgn, lgCT, 1, C * TC, A, Bf, s_tw, ld0, stl);
 }
@@ -82,24 +82,24 @@ __device__ __forceinline__ void wf_col_inv_pp(const WfGeo& g, const V2<T>* src, 
 // the same row and is applied as the first pass loads; the r2c post-step runs
 // from the last pass's shared output.  src: the RB rows of packed spectra (h
 // values each, global or shared memory); sc: where the result rows go
-// (global); d, w: the pixel rows (RB n values from the block's first row);
-// roots: exp(-2 pi i k / n) for k < n/2, in shared memory.  Returns this
+// (global); d, w: the pixel rows (RB nx values from the block's first row);
+// roots: exp(-2 pi i k / nx) for k < nx/2, in shared memory.  Returns this
 // thread's part of sum r.wr.  after1 runs once the first pass has finished
 // reading src.
 template <typename T, int MODE, int PLAN, class H = WfNoHook>
 __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* src, V2<T>* sc, const T* d,
                                                    const T* w, const V2<T>* roots, const V2<T>* s_pt, V2<T>* A,
                                                    V2<T>* Bf, H after1 = H()) {
-  const int n = g.n, h = g.h, lgh = g.lgh, RB = g.RB, lgRB = __ffs(RB) - 1;
+  const int h = g.h, lgh = g.lgh, RB = g.RB, lgRB = __ffs(RB) - 1;
   const V2<T>* dv = (const V2<T>*)d;
   const V2<T>* wv = (const V2<T>*)w;
-  // c2r pre-step: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]), w = exp(+2 pi i / n);
+  // c2r pre-step: Z[k] = (X[k] + conj X[h-k]) + i w^k (X[k] - conj X[h-k]), w = exp(+2 pi i / nx);
   // Z[0] from the packed X[0] + i X[h].
   auto ld0 = [&](int t, int k) -> V2<T> {
-    const V2<T>* row = src + (size_t)t * h;
-    const V2<T> Xk = row[k];
+    const V2<T>* row = src + WF_CHK((size_t)t * h, (size_t)RB * h);
+    const V2<T> Xk = row[WF_CHK(k, h)];
     if (k == 0) return mk<T>(Xk.x + Xk.y, Xk.x - Xk.y);
-    const V2<T> Xm = row[h - k];
+    const V2<T> Xm = row[WF_CHK(h - k, h)];
     const V2<T> w1 = twid<T, +1>(roots, k);
     const V2<T> s1 = mk<T>(Xk.x + Xm.x, Xk.y - Xm.y), d1 = mk<T>(Xk.x - Xm.x, Xk.y + Xm.y);
     return cadd<T>(s1, mul_i<T>(cmul<T>(w1, d1)));
@@ -108,7 +108,7 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
   V2<T>* O = wf_pp_out<T>(lgh, PLAN, A, Bf);
   WfAcc<T> acc = 0;
   auto stpix = [&](int t, int m, V2<T> x) {
-    const size_t e = (size_t)t * n / 2 + m;
+    const size_t e = WF_CHK((size_t)t * h + m, (size_t)RB * h);
     const V2<T> wl = wv[e];
     V2<T> r;
     if constexpr (MODE == WF_ROW_DATA) {
@@ -144,7 +144,7 @@ __device__ __forceinline__ WfAcc<T> wf_row_pp_core(const WfGeo& g, const V2<T>* 
       const V2<T> i1 = mul_i<T>(cmul<T>(w1, d1));
       X = mk<T>((T)0.5 * (s1.x - i1.x), (T)0.5 * (s1.y - i1.y));
     }
-    sc[e] = X;
+    sc[WF_CHK(e, RB * h)] = X;
   }
   return acc;
 }
@@ -156,19 +156,19 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
   V2<T>* s_pt = (V2<T>*)wf_smem;
   V2<T>* A = s_pt + WF_NT;
   V2<T>* Bf = A + WF_TILE;
-  const int b = blockIdx.y, n = g.n, h = g.h;
+  const int b = blockIdx.y, n = g.n, nx = g.nx, h = g.h;
   const int row0 = blockIdx.x * g.RB;
-  const size_t npix = (size_t)g.C * n * n;
+  const size_t npix = (size_t)g.C * n * nx;
   {  // the pixel rows are read by the last pass: start them towards L2
-    const size_t off = (size_t)b * npix + (size_t)row0 * n;
-    wf_prefetch_rows(w + off, 1, 0, g.RB * n * (int)sizeof(T));
-    if (MODE == WF_ROW_DATA) wf_prefetch_rows(d + off, 1, 0, g.RB * n * (int)sizeof(T));
+    const size_t off = (size_t)b * npix + (size_t)row0 * nx;
+    wf_prefetch_rows(w + off, 1, 0, g.RB * nx * (int)sizeof(T));
+    if (MODE == WF_ROW_DATA) wf_prefetch_rows(d + off, 1, 0, g.RB * nx * (int)sizeof(T));
   }
   {  // the length-h pass table (under WF_NT / 2 entries for h <= 512), then the
-     // n-th roots the real-FFT pre- and post-steps use
+     // nx-th roots the real-FFT pre- and post-steps use
     const V2<T>* gt = (const V2<T>*)tw_;
     const V2<T>* src = gt + (size_t)WF_TWTAB * PLAN + (size_t)WF_NT * g.lgh;
-    const int lgNTn = WF_LOG2_NT - g.lgn;
+    const int lgNTn = WF_LOG2_NT - g.lgnx;
     for (int i = threadIdx.x; i < WF_NT / 2; i += blockDim.x) {
       s_pt[i] = src[i];
       if (i < h) s_pt[WF_NT / 2 + i] = gt[i << lgNTn];
@@ -176,7 +176,7 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
   }
   __syncthreads();
   V2<T>* sc = scratch + (size_t)b * g.C * n * h + (size_t)row0 * h;
-  const size_t poff = (size_t)b * npix + (size_t)row0 * n;
+  const size_t poff = (size_t)b * npix + (size_t)row0 * nx;
   const WfAcc<T> acc = wf_row_pp_core<T, MODE, PLAN>(g, sc, sc, MODE == WF_ROW_DATA ? d + poff : nullptr, w + poff,
                                                      s_pt + WF_NT / 2, s_pt, A, Bf);
   const double s = wf_block_sum((double)acc);

@@ -9,12 +9,14 @@ mistake here changes the test data, never the expected answer.
 
 Conventions
 -----------
-* Maps are n x n periodic pixels; C channels (1 = density/CMB, 2 = E/B shear).
+* Maps are n x n periodic pixels (ny x nx where a generator takes nx: square
+  pixels, so mode (my, mx) has wavevector 2 pi (mx / nx, my / ny) per pixel);
+  C channels (1 = density/CMB, 2 = E/B shear).
 * Fourier index m = (my, mx) in signed form, my, mx in [-n/2, n/2).
 * P[c, my, mx] is the variance of the unitary DFT coefficient of channel c at
   mode m (full plane).  For a continuous spectrum P(k) on an L-sided box this
   is P(k) n^2 / L^2 with k in units of the fundamental 2 pi / L; P at m = 0 is 0.
-* ``P_half`` is the real-FFT half plane P[..., : n // 2 + 1].
+* ``P_half`` is the real-FFT half plane P[..., : nx // 2 + 1].
 * mask is uint8, 1 = observed; Ninv = 1 / noise variance on observed pixels,
   0 on masked ones.
 """
@@ -39,7 +41,7 @@ class MapInputs:
 
     @property
     def P_half(self) -> np.ndarray:
-        return np.ascontiguousarray(self.P[..., : self.n // 2 + 1])
+        return np.ascontiguousarray(self.P[..., : self.P.shape[-1] // 2 + 1])
 
 
 def signed_freqs(n: int):
@@ -48,57 +50,69 @@ def signed_freqs(n: int):
     return np.meshgrid(f, f, indexing="ij")
 
 
-def mode_modulus(n: int) -> np.ndarray:
-    my, mx = signed_freqs(n)
-    return np.sqrt(my.astype(np.float64) ** 2 + mx.astype(np.float64) ** 2)
+def mode_modulus(n: int, nx: int | None = None) -> np.ndarray:
+    """|k| per mode in units of the fundamental of the longer side (square
+    pixels): sqrt((mx N / nx)^2 + (my N / n)^2), N = max(n, nx); for a square
+    map the modulus of the mode numbers."""
+    if nx is None or nx == n:
+        my, mx = signed_freqs(n)
+        return np.sqrt(my.astype(np.float64) ** 2 + mx.astype(np.float64) ** 2)
+    N = max(n, nx)
+    fy = np.fft.fftfreq(n, d=1.0 / n) * (N / n)
+    fx = np.fft.fftfreq(nx, d=1.0 / nx) * (N / nx)
+    my, mx = np.meshgrid(fy, fx, indexing="ij")
+    return np.sqrt(my ** 2 + mx ** 2)
 
 
-def _disk_mask(n: int, rng, count: int, radius: float) -> np.ndarray:
+def _disk_mask(n: int, rng, count: int, radius: float, nx: int | None = None) -> np.ndarray:
     """Boolean map of `count` periodic disks of the given radius (True = hole)."""
-    holes = np.zeros((n, n), dtype=bool)
+    nx = n if nx is None else nx
+    holes = np.zeros((n, nx), dtype=bool)
     cy = rng.integers(0, n, size=count)
-    cx = rng.integers(0, n, size=count)
+    cx = rng.integers(0, nx, size=count)
     r = int(np.ceil(radius))
     off = np.arange(-r, r + 1)
     oy, ox = np.meshgrid(off, off, indexing="ij")
     inside = (oy * oy + ox * ox) <= radius * radius
     oy, ox = oy[inside], ox[inside]
     for y0, x0 in zip(cy, cx):
-        holes[(y0 + oy) % n, (x0 + ox) % n] = True
+        holes[(y0 + oy) % n, (x0 + ox) % nx] = True
     return holes
 
 
 def _normalise_to_snr1(P: np.ndarray, noise_var_obs_mean: float) -> np.ndarray:
     """Scale P so the mean pixel signal variance, sum_m P_m / n^2, equals the
     mean observed noise variance (signal-to-noise 1 per pixel on average)."""
-    n = P.shape[-1]
-    pix_var = P.reshape(P.shape[0], -1).sum(axis=1).mean() / (n * n)
+    npix = P.shape[-2] * P.shape[-1]
+    pix_var = P.reshape(P.shape[0], -1).sum(axis=1).mean() / npix
     return P * (noise_var_obs_mean / pix_var)
 
 
 def _finish(n, C, mask_bool_obs, var, P, rng, meta) -> MapInputs:
     """Common tail: white field, noise, Ninv with zeros on masked pixels."""
     mask = mask_bool_obs.astype(np.uint8)
-    var = np.broadcast_to(var, (C, n, n)).astype(np.float64)
+    shape = (C,) + mask.shape
+    var = np.broadcast_to(var, shape).astype(np.float64)
     Ninv = np.where(mask[None] == 1, 1.0 / var, 0.0)
-    z = rng.standard_normal((C, n, n))
-    noise = rng.standard_normal((C, n, n)) * np.sqrt(var)
+    z = rng.standard_normal(shape)
+    noise = rng.standard_normal(shape) * np.sqrt(var)
     return MapInputs(n=n, C=C, mask=mask, Ninv=np.ascontiguousarray(Ninv),
                      P=np.ascontiguousarray(P), z=z, noise=noise, meta=meta)
 
 
 def density_small(n: int = 32, seed: int = 0, masked_frac: float = 0.2,
-                  sigma2: float = 0.1) -> MapInputs:
+                  sigma2: float = 0.1, nx: int | None = None) -> MapInputs:
     """Plain FP64 density case: P(k) = k^-2 (A = 1, box L = 1), Bernoulli mask
     with ``masked_frac`` of pixels removed, per-pixel noise variance
-    sigma2 * U[0.5, 1.5]."""
+    sigma2 * U[0.5, 1.5].  nx: a rectangular n x nx map."""
     rng = np.random.default_rng(seed)
-    k = mode_modulus(n)
-    P = np.zeros((1, n, n))
+    nx = n if nx is None else nx
+    k = mode_modulus(n, nx)
+    P = np.zeros((1, n, nx))
     nz = k > 0
-    P[0][nz] = k[nz] ** -2.0 * n * n
-    observed = rng.random((n, n)) >= masked_frac
-    var = sigma2 * rng.uniform(0.5, 1.5, size=(n, n))
+    P[0][nz] = k[nz] ** -2.0 * n * nx
+    observed = rng.random((n, nx)) >= masked_frac
+    var = sigma2 * rng.uniform(0.5, 1.5, size=(n, nx))
     return _finish(n, 1, observed, var, P, rng,
                    dict(kind="density", spectrum="k^-2", masked_frac=masked_frac))
 
@@ -126,28 +140,32 @@ def density_projected(n: int = 256, seed: int = 1) -> MapInputs:
                    dict(kind="density", spectrum="k^-1.5 exp(-(2k/kNyq)^2)"))
 
 
-def shear_eb(n: int = 512, seed: int = 2, b_frac: float = 0.01) -> MapInputs:
+def shear_eb(n: int = 512, seed: int = 2, b_frac: float = 0.01, nx: int | None = None) -> MapInputs:
     """Joint E/B shear: P_E ~ k^-1.2, P_B = b_frac P_E; shape noise
     0.09 / n_gal per component with n_gal ~ Poisson(10); mask = Gaussian-smoothed
-    white noise (sigma 8 px) above its 70th percentile (30% masked)."""
+    white noise (sigma 8 px) above its 70th percentile (30% masked).  nx: a
+    rectangular n x nx patch (k in units of the longer side's fundamental)."""
     rng = np.random.default_rng(seed)
-    k = mode_modulus(n)
-    PE = np.zeros((n, n))
+    nx = n if nx is None else nx
+    k = mode_modulus(n, nx)
+    PE = np.zeros((n, nx))
     nz = k > 0
     PE[nz] = k[nz] ** -1.2
     P = np.stack([PE, b_frac * PE])
     # Smoothing is done in Fourier space with a Gaussian kernel (numpy FFT).
-    white = rng.standard_normal((n, n))
-    my, mx = signed_freqs(n)
-    kern = np.exp(-0.5 * (2 * np.pi * 8.0 / n) ** 2 * (my ** 2 + mx ** 2))
+    white = rng.standard_normal((n, nx))
+    N = max(n, nx)
+    my, mx = np.meshgrid(np.fft.fftfreq(n, d=1.0 / n) * (N / n), np.fft.fftfreq(nx, d=1.0 / nx) * (N / nx),
+                         indexing="ij")
+    kern = np.exp(-0.5 * (2 * np.pi * 8.0 / N) ** 2 * (my ** 2 + mx ** 2))
     smooth = np.fft.ifft2(np.fft.fft2(white) * kern).real
     thr = np.quantile(smooth, 0.70)
-    ngal = rng.poisson(10.0, size=(n, n))
+    ngal = rng.poisson(10.0, size=(n, nx))
     observed = (smooth <= thr) & (ngal > 0)
     var = np.where(ngal > 0, 0.09 / np.maximum(ngal, 1), 1.0)
     P = _normalise_to_snr1(P, float(var[observed].mean()))
     return _finish(n, 2, observed, var, P, rng,
-                   dict(kind="shear_eb", spectrum="k^-1.2", b_frac=b_frac))
+                   dict(kind="shear_eb", spectrum="k^-1.2", b_frac=b_frac, nx=nx))
 
 
 def cmb_cl(ell: np.ndarray) -> np.ndarray:
@@ -189,13 +207,14 @@ def cmb_patch(n: int = 1024, seed: int = 3, pix_arcmin: float = 2.0,
 
 
 def log_bands(n: int, n_bands: int, kmin: float = 1.0, kmax: float | None = None,
-              C: int = 1) -> np.ndarray:
+              C: int = 1, nx: int | None = None) -> np.ndarray:
     """Band id per full-plane mode: log-spaced shells in |m| between kmin and
     kmax (default the Nyquist n/2); -1 for modes outside every band (m = 0 and
     corners beyond kmax).  Shape (C, n, n), int16; channel c uses ids offset by
-    c * n_bands."""
-    kmax = n / 2 if kmax is None else kmax
-    k = mode_modulus(n)
+    c * n_bands.  nx: an n x nx map, |k| as mode_modulus(n, nx) and kmax
+    defaulting to max(n, nx)/2."""
+    kmax = max(n, n if nx is None else nx) / 2 if kmax is None else kmax
+    k = mode_modulus(n, nx)
     edges = np.geomspace(kmin, kmax, n_bands + 1)
     edges[-1] = kmax * (1 + 1e-12)
     ids = np.searchsorted(edges, k, side="right") - 1
@@ -231,9 +250,9 @@ def hetero_batch(count: int = 256, seed: int = 4,
     return out
 
 
-def random_state(n: int, C: int, seed: int) -> np.ndarray:
-    """A random real pixel field (C, n, n) used as an evaluation point."""
-    return np.random.default_rng(seed).standard_normal((C, n, n))
+def random_state(n: int, C: int, seed: int, nx: int | None = None) -> np.ndarray:
+    """A random real pixel field (C, n, n), or (C, n, nx), used as an evaluation point."""
+    return np.random.default_rng(seed).standard_normal((C, n, n if nx is None else nx))
 
 
 def white_noise_batch(count: int, C: int, n: int, seed: int) -> np.ndarray:

@@ -11,7 +11,8 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libwf.so")
+# WF_LIB_PATH selects another build of the library, e.g. the bounds-checked one.
+LIB_PATH = os.environ.get("WF_LIB_PATH") or os.path.join(HERE, "libwf.so")
 
 WF_FP64, WF_MIXED = 0, 1
 WF_F32, WF_F64 = 0, 1
@@ -28,7 +29,8 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "wf_map_solve_many", "wf_normal_draw", "wf_workspace_used", "wf_band_table",
            "bandpower_iterate", "wf_problem_variant", "wf_alu_peak", "wf_solver_history",
            "wf_map_solve_refined", "bandpower_sums_len", "bandpower_sums", "bandpower_combine",
-           "wf_solver_state_size", "wf_solver_export", "wf_solver_import"]
+           "wf_solver_state_size", "wf_solver_export", "wf_solver_import", "wf_debug_bounds",
+           "wf_problem_create_rect", "bandpower_estimate_rect"]
 
 
 class WfMap(ctypes.Structure):
@@ -98,6 +100,7 @@ def lib() -> ctypes.CDLL:
     L.wf_opts_default.argtypes = [ctypes.POINTER(WfOpts)]
     L.wf_opts_default.restype = None
     L.wf_problem_create.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, i, i, vp, ctypes.POINTER(vp)]
+    L.wf_problem_create_rect.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, i, i, i, vp, ctypes.POINTER(vp)]
     L.wf_problem_destroy.argtypes = [vp]
     L.wf_problem_set_data.argtypes = [vp, vp, vp]
     L.wf_eval.argtypes = [vp, vp, vp, vp, vp]
@@ -120,6 +123,9 @@ def lib() -> ctypes.CDLL:
     L.bandpower_estimate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
                                      ctypes.POINTER(WfOpts), ctypes.POINTER(WfBandpowerOut),
                                      ctypes.POINTER(WfSolveStats)]
+    L.bandpower_estimate_rect.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, i, ctypes.POINTER(WfBandpowerIn),
+                                          ctypes.POINTER(WfOpts), ctypes.POINTER(WfBandpowerOut),
+                                          ctypes.POINTER(WfSolveStats)]
     L.wf_normal_draw.argtypes = [ctypes.c_ulonglong, ctypes.c_uint, ctypes.c_ulonglong, ctypes.c_size_t, i, vp, vp]
     L.bandpower_iterate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
                                     ctypes.POINTER(WfOpts), i, d, d, vp, ctypes.POINTER(d),
@@ -128,6 +134,7 @@ def lib() -> ctypes.CDLL:
     L.bandpower_combine.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                     ctypes.POINTER(WfBandpowerIn), ctypes.POINTER(WfBandpowerOut)]
     L.bandpower_sums_len.argtypes = [i, i]
+    L.wf_debug_bounds.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_longlong), i]
     L.wf_solver_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.wf_solver_export.argtypes = [vp, vp, ctypes.c_size_t]
     L.wf_solver_import.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -269,6 +276,15 @@ def eval_noalloc(s, d, w, P, chi2=None, grad=None, stream=None):
     return chi2, grad
 
 
+def debug_bounds(mode=0):
+    """wf_debug_bounds (bounds-checked build only): (violations, first) with
+    first = (unit, source line, index, limit) of the first one or None."""
+    cnt = ctypes.c_ulonglong()
+    first = (ctypes.c_longlong * 4)(-1, -1, -1, -1)
+    _check(lib().wf_debug_bounds(ctypes.byref(cnt), first, int(mode)))
+    return int(cnt.value), (tuple(first) if cnt.value else None)
+
+
 def solve_many(problems, stream=None, **opts):
     """wf_map_solve_many: solve several problems (one per map shape) at once.
     Returns one SolveResult per problem."""
@@ -324,21 +340,21 @@ def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, str
     import torch
     _need(Ninv, "Ninv")
     if Ninv.dim() != 3 or Ninv.dtype not in (torch.float32, torch.float64):
-        raise ValueError("Ninv must be a float32 or float64 (C, n, n) tensor")
-    C, n, _ = Ninv.shape
+        raise ValueError("Ninv must be a float32 or float64 (C, ny, nx) tensor")
+    C, n, nx = Ninv.shape
     ddt = Ninv.dtype
     wdt = torch.float64 if precision == "fp64" else torch.float32
-    _need(d, "d", (C, n, n), ddt)
-    _need(mask, "mask", (n, n), torch.uint8)
-    _need(P, "P", (C, n, n // 2 + 1), ddt)
-    _need(band, "band", (C, n, n // 2 + 1), torch.int16)
+    _need(d, "d", (C, n, nx), ddt)
+    _need(mask, "mask", (n, nx), torch.uint8)
+    _need(P, "P", (C, n, nx // 2 + 1), ddt)
+    _need(band, "band", (C, n, nx // 2 + 1), torch.int16)
     m = WfMap(d=_ptr(d), mask=_ptr(mask), Ninv=_ptr(Ninv), P=_ptr(P))
     nb = int(n_bands)
     J = int(z.shape[0]) if z is not None else int(n_sim)
     F = int(u.shape[1]) if u is not None else int(n_fd)
     for name, t in (("z", z), ("noise", noise)):  # all-or-none of the fields is the library's check
         if t is not None:
-            _need(t, name, (J, C, n, n), wdt)
+            _need(t, name, (J, C, n, nx), wdt)
     idx = None
     if sim_index is not None:
         idx = np.ascontiguousarray(sim_index, dtype=np.int64)
@@ -350,7 +366,7 @@ def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, str
     if u is not None and int(u.shape[0]) != nR:
         raise ValueError(f"u has {int(u.shape[0])} Fisher rows, the call needs {nR}")
     if u is not None:
-        _need(u, "u", (nR, F, C, n, n), wdt)
+        _need(u, "u", (nR, F, C, n, nx), wdt)
     bi = WfBandpowerIn(n_bands=nb, n_sim=J, n_fd=F, leak_split=L,
                        band=_ptr(band), z=_ptr(z), noise=_ptr(noise), u=_ptr(u),
                        sim_index=None if idx is None else idx.ctypes.data,
@@ -374,7 +390,7 @@ def _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, str
     st = (WfSolveStats * nmaps)()
     prec = WF_FP64 if precision == "fp64" else WF_MIXED
     dt = WF_F64 if Ninv.dtype == torch.float64 else WF_F32
-    return dict(m=m, bi=bi, bo=bo, o=o, st=st, arrs=arrs, n=n, C=C, nb=nb, nmaps=nmaps, prec=prec, dt=dt,
+    return dict(m=m, bi=bi, bo=bo, o=o, st=st, arrs=arrs, n=n, nx=nx, C=C, nb=nb, nmaps=nmaps, prec=prec, dt=dt,
                 keep=(idx, fdb))
 
 
@@ -390,9 +406,9 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
                        handle=None, stream=None, n_sim=None, n_fd=None, sim_index=None, fd_bands=None,
                        trunc=(0, 0), out_on_device=False, leak_split=0, **opts):
     """bandpower_estimate: band powers, noise bias, Fisher matrix and covariance
-    of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, n, n) and P
-    (C, n, n/2+1) CUDA tensors of one float dtype; mask (n, n) uint8; band
-    (C, n, n/2+1) int16; z, noise (n_sim, C, n, n), u (n_bands, n_fd, C, n, n)
+    of one data map from simulations (Sec. 2.4-2.5).  d, Ninv (C, ny, nx) and P
+    (C, ny, nx/2+1) CUDA tensors of one float dtype; mask (ny, nx) uint8; band
+    (C, ny, nx/2+1) int16; z, noise (n_sim, C, ny, nx), u (n_bands, n_fd, C, ny, nx)
     in the working type, or all three None with n_sim and n_fd given (the
     library then draws them from opts `seed`; sim_index gives the global index
     of each simulation, so that the draws do not depend on how simulations are
@@ -408,8 +424,9 @@ def bandpower_estimate(d, mask, Ninv, P, band, n_bands, z, noise, u, precision="
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
                         opts, fd_bands, trunc, out_on_device, leak_split)
     handle = handle or default_handle()
-    status = lib().bandpower_estimate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
-                                      ctypes.byref(a["bi"]), ctypes.byref(a["o"]), ctypes.byref(a["bo"]), a["st"])
+    status = lib().bandpower_estimate_rect(handle.ptr, ctypes.byref(a["m"]), a["n"], a["nx"], a["C"], a["dt"],
+                                           a["prec"], ctypes.byref(a["bi"]), ctypes.byref(a["o"]),
+                                           ctypes.byref(a["bo"]), a["st"])
     if status not in (0, 5):
         _check(status)
     return _bandpower_result(a)
@@ -425,6 +442,8 @@ def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_
     import torch
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
                         opts, fd_bands, trunc, out_on_device, leak_split)
+    if a["nx"] != a["n"]:
+        raise ValueError("bandpower_iterate takes square maps (bandpower_estimate takes rectangular ones)")
     handle = handle or default_handle()
     hist = np.zeros((int(n_iter), a["nb"]))
     P_out = torch.empty_like(P)
@@ -492,10 +511,10 @@ def bandpower_combine(sums, E_data, theta_fid, leak_split=0, fd_bands=None, trun
 
 
 class Problem:
-    """A prepared batch of maps of one shape (wf_problem_create).
+    """A prepared batch of maps of one shape (wf_problem_create_rect).
 
-    d, Ninv: (B, C, n, n) CUDA tensors; mask: (B, n, n) or (n, n) uint8;
-    P: (B, C, n, n/2+1) or (C, n, n/2+1).  Floating inputs must share one dtype
+    d, Ninv: (B, C, ny, nx) CUDA tensors (square or not, sides powers of two);
+    mask: (B, ny, nx) or (ny, nx) uint8; P: (B, C, ny, nx/2+1) or (C, ny, nx/2+1).  Floating inputs must share one dtype
     (float32 or float64).  precision: "fp64" or "mixed".  State arrays (s, grad,
     z, noise, outputs) use the working type: float64 for fp64, float32 for mixed."""
 
@@ -503,20 +522,20 @@ class Problem:
         import torch
         _need(Ninv, "Ninv")
         if Ninv.dim() != 4:
-            raise ValueError("Ninv must have shape (B, C, n, n)")
-        B, C, n, _ = Ninv.shape
-        self.B, self.C, self.n = B, C, n
+            raise ValueError("Ninv must have shape (B, C, ny, nx)")
+        B, C, n, nx = Ninv.shape
+        self.B, self.C, self.n, self.nx = B, C, n, nx
         dtype = Ninv.dtype
         if dtype not in (torch.float32, torch.float64):
             raise TypeError("inputs must be float32 or float64")
         if d is not None:
-            _need(d, "d", (B, C, n, n), dtype)
-        _need(mask, "mask", (B, n, n) if mask.dim() == 3 else (n, n), torch.uint8)
-        _need(P, "P", (B, C, n, n // 2 + 1) if P.dim() == 4 else (C, n, n // 2 + 1), dtype)
+            _need(d, "d", (B, C, n, nx), dtype)
+        _need(mask, "mask", (B, n, nx) if mask.dim() == 3 else (n, nx), torch.uint8)
+        _need(P, "P", (B, C, n, nx // 2 + 1) if P.dim() == 4 else (C, n, nx // 2 + 1), dtype)
         self.handle = handle or default_handle()
         self.precision = WF_FP64 if precision == "fp64" else WF_MIXED
         self.wdtype = torch.float64 if self.precision == WF_FP64 else torch.float32
-        masks = mask if mask.dim() == 3 else mask.unsqueeze(0).expand(B, n, n)
+        masks = mask if mask.dim() == 3 else mask.unsqueeze(0).expand(B, n, nx)
         Ps = P if P.dim() == 4 else P.unsqueeze(0).expand(B, *P.shape)
         self._keep = (d, masks, Ninv, Ps)
         arr = (WfMap * B)()
@@ -526,9 +545,9 @@ class Problem:
             arr[b].Ninv = _ptr(Ninv[b])
             arr[b].P = _ptr(Ps[b])
         out = ctypes.c_void_p()
-        _check(lib().wf_problem_create(self.handle.ptr, arr, B, n, C,
-                                       WF_F64 if dtype == torch.float64 else WF_F32,
-                                       self.precision, lbfgs_m, _stream(stream), ctypes.byref(out)))
+        _check(lib().wf_problem_create_rect(self.handle.ptr, arr, B, n, nx, C,
+                                            WF_F64 if dtype == torch.float64 else WF_F32,
+                                            self.precision, lbfgs_m, _stream(stream), ctypes.byref(out)))
         self._p = out
         self._keep = None
 
@@ -545,10 +564,10 @@ class Problem:
 
     # shapes -----------------------------------------------------------------
     def spec_shape(self):
-        return (self.B, self.C, self.n, self.n // 2 + 1)
+        return (self.B, self.C, self.n, self.nx // 2 + 1)
 
     def pix_shape(self):
-        return (self.B, self.C, self.n, self.n)
+        return (self.B, self.C, self.n, self.nx)
 
     def _cplx(self):
         import torch
@@ -587,7 +606,7 @@ class Problem:
         return chi2, grad
 
     def set_band_scale(self, band, q, stream=None):
-        """wf_problem_set_band_scale: P <- q[band] P (band int16 (C, n, n/2+1),
+        """wf_problem_set_band_scale: P <- q[band] P (band int16 (C, ny, nx/2+1),
         q float64 (n_b,) CUDA tensors)."""
         _check(lib().wf_problem_set_band_scale(self._p, _ptr(band), _ptr(q), int(q.numel()), _stream(stream)))
 

@@ -19,8 +19,8 @@ def rfft_u(x):
     return np.fft.rfft2(x, norm="ortho")
 
 
-def irfft_u(S, n):
-    return np.fft.irfft2(S, s=(n, n), norm="ortho")
+def irfft_u(S, n, nx=None):
+    return np.fft.irfft2(S, s=(n, n if nx is None else nx), norm="ortho")
 
 
 def rel(a, b):
@@ -47,14 +47,14 @@ def make_problem(inputs, precision="fp64", d_list=None, lbfgs_m=10, shared_P=Tru
         Nr = inp.Ninv.astype(npdt).astype(np.float64)
         d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P) if d_list is None else d_list[i]
         ds.append(d.astype(npdt).astype(np.float64)); Ns.append(Nr); Ps.append(Pr); Ms.append(inp.mask)
-    n = inputs[0].n
+    h1 = inputs[0].P.shape[-1] // 2 + 1  # half-plane columns
     d_t = to_dev(np.stack(ds), fdt)
     N_t = to_dev(np.stack(Ns), fdt)
     M_t = to_dev(np.stack(Ms), torch.uint8)
     if shared_P:
-        P_t = to_dev(Ps[0][..., : n // 2 + 1], fdt)
+        P_t = to_dev(Ps[0][..., :h1], fdt)
     else:
-        P_t = to_dev(np.stack(Ps)[..., : n // 2 + 1], fdt)
+        P_t = to_dev(np.stack(Ps)[..., :h1], fdt)
     prob = wf.Problem(d_t, M_t, N_t, P_t, precision=precision, lbfgs_m=lbfgs_m)
     host = dict(d=ds, Ninv=Ns, P=Ps, mask=Ms, W=[m[None] * N for m, N in zip(Ms, Ns)])
     return prob, host

@@ -137,8 +137,14 @@ def test_problem_create_refuses_bad_arguments_before_device_work():
         st = L.wf_problem_create(h, maps, a["count"], a["n"], a["C"], a["dtype"], a["prec"], a["m"], None,
                                  ctypes.byref(out))
         assert st == 1 and out.value is None, (bad, st)
+    for ny, nx in ((16, 12), (12, 16), (4, 16), (16, 4), (16, 2048), (2048, 16), (0, 16)):
+        st = L.wf_problem_create_rect(h, maps, 1, ny, nx, 1, wf.WF_F32, wf.WF_MIXED, 10, None, ctypes.byref(out))
+        assert st == 1 and out.value is None and b"power of two" in L.wf_last_error(), (ny, nx)
     maps[1].Ninv = None
     assert L.wf_problem_create(h, maps, 2, 16, 1, wf.WF_F32, wf.WF_MIXED, 10, None, ctypes.byref(out)) == 1
+    assert b"map 1" in L.wf_last_error()
+    assert L.wf_problem_create_rect(h, maps, 2, 16, 64, 1, wf.WF_F32, wf.WF_MIXED, 10, None,
+                                    ctypes.byref(out)) == 1
     assert b"map 1" in L.wf_last_error()
 
 
