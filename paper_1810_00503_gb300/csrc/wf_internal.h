@@ -127,6 +127,15 @@ __host__ __device__ inline int wf_plan_bits(int lgL, int plan, int p) {
 #define WF_MINB32 3
 #endif
 #define WF_MINB(T) (sizeof(T) == 4 ? WF_MINB32 : 1)
+// The same for the objective pass's forward column stage (k_col_fwd): its tile
+// and tables take 40 KB of shared memory, so four blocks fit, and at 64
+// registers it does not spill (1.67 against 1.73 ms for the 120 x 1024^2 pass;
+// five blocks, 48 registers: 1.76 ms).  The iteration's forward stage
+// (k_lb_colfwd) spills at 64 and keeps WF_MINB (0.68 against 0.77 ms).
+#ifndef WF_MINB_COLFWD32
+#define WF_MINB_COLFWD32 4
+#endif
+#define WF_MINB_COLFWD(T) (sizeof(T) == 4 ? WF_MINB_COLFWD32 : 1)
 
 // Partial-sum slots per map (one FP64 value per block and slot).
 #define WF_MAXM 32

@@ -32,15 +32,55 @@ template <typename K> inline cudaError_t ensure_smem(K kernel, size_t bytes, int
   return e;
 }
 
+// Resident blocks of a persistent kernel: SMs x blocks per SM (cached per device).
+template <typename K>
+inline cudaError_t persistent_grid(K k, size_t smem, int* occ, int* nsm, int* grid) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int di = dev & 31;
+  if (!occ[di]) {
+    int o = 0, ns = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, WF_THREADS, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    occ[di] = o > 0 ? o : 1;
+    nsm[di] = ns;
+  }
+  *grid = occ[di] * nsm[di];
+  return cudaSuccess;
+}
+
+// Grid of a persistent launch over nitems work items: the resident blocks, at
+// most nitems (the items loop inside the kernel, so any grid is correct).
+template <typename K>
+inline cudaError_t items_grid(K k, size_t smem, int nitems, int* occ, int* nsm, int* grid) {
+  cudaError_t e = persistent_grid(k, smem, occ, nsm, grid);
+  if (e == cudaSuccess && *grid > nitems) *grid = nitems;
+  return e;
+}
+
 template <typename T, int C, int IN, int PLAN>
 cudaError_t col_inv_r(const WfGeo& g, const WfBufs& b, const void* src, cudaStream_t st) {
   static int done = 0;
-  auto k = WF_FFT_PP ? k_col_inv_pp<T, C, IN, PLAN> : k_col_inv<T, C, IN>;
-  const size_t sm = WF_FFT_PP ? wf_pp_smem<T>() : col_smem<T>(g);
-  cudaError_t e = ensure_smem(k, sm, &done);
-  if (e != cudaSuccess) return e;
-  k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, b.tw);
-  return cudaGetLastError();
+  if constexpr (WF_FFT_PP) {
+    static int occ[32] = {0}, nsm[32] = {0};
+    auto k = k_col_inv_pp_pers<T, C, IN, PLAN>;
+    const size_t sm = wf_pp_smem<T>();
+    cudaError_t e = ensure_smem(k, sm, &done);
+    int grid = 0;
+    if (e == cudaSuccess) e = items_grid(k, sm, g.ntile * b.B, occ, nsm, &grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, b.B);
+    return cudaGetLastError();
+  } else {
+    auto k = k_col_inv<T, C, IN>;
+    const size_t sm = col_smem<T>(g);
+    cudaError_t e = ensure_smem(k, sm, &done);
+    if (e != cudaSuccess) return e;
+    k<<<dim3(g.ntile, b.B), WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, b.tw);
+    return cudaGetLastError();
+  }
 }
 
 template <typename T, int C, int IN>
@@ -209,24 +249,6 @@ cudaError_t lb_colinv_tma(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, c
   return cudaGetLastError();
 }
 
-// Resident blocks of a persistent kernel: SMs x blocks per SM (cached per device).
-template <typename K>
-inline cudaError_t persistent_grid(K k, size_t smem, int* occ, int* nsm, int* grid) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const int di = dev & 31;
-  if (!occ[di]) {
-    int o = 0, ns = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, WF_THREADS, smem);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    occ[di] = o > 0 ? o : 1;
-    nsm[di] = ns;
-  }
-  *grid = occ[di] * nsm[di];
-  return cudaSuccess;
-}
 
 template <typename T, int C, int KIND, int PLAN>
 cudaError_t lb_colinv_tile(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, cudaStream_t st) {
