@@ -354,8 +354,9 @@ def run_eval_shapes(args, dev, hbm):
 def run_hetero(args, dev, count=256, n_bands=10, sizes=(64, 128, 256, 512, 1024)):
     """Heterogeneous batch: `count` independent maps of n in {64, 128, 256,
     512, 1024} (uneven masks, noise levels and spectral slopes), one problem
-    per size, all solved as one batch by wf_map_solve_many (one CUDA graph per
-    round, a branch per size) to ||g|| / ||g0|| < 1e-6 in mixed precision;
+    per size, all solved as one batch by wf_map_solve_many (each iteration one
+    set of seven launches shared by every size, one CUDA graph per round) to
+    ||g|| / ||g0|| < 1e-6 in mixed precision;
     then d chi^2 / d log q for n_bands log-spaced bands at the solutions
     through the adjoint stage (wf_eval_bands)."""
     import numpy as np
@@ -378,7 +379,7 @@ def run_hetero(args, dev, count=256, n_bands=10, sizes=(64, 128, 256, 512, 1024)
         probs.append(prob)
         sizes.append((n, B))
     torch.cuda.synchronize()
-    wf.solve_many(probs, gtol_rel=1e-6, max_iter=2)  # tunes each shape, builds the graphs
+    wf.solve_many(probs, gtol_rel=1e-6, max_iter=2)  # the solvers' buffers and the kernels' attributes
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = wf.solve_many(probs, gtol_rel=1e-6, max_iter=20000, check_every=32, refresh_every=200)
@@ -406,8 +407,9 @@ def run_hetero(args, dev, count=256, n_bands=10, sizes=(64, 128, 256, 512, 1024)
     return {"maps": count, "sizes": per, "seconds": dt, "map_solves_per_s": count / dt,
             "evals_per_s": evals / dt, "stop": "||g||/||g0|| < 1e-6", "statuses": statuses,
             "dchi2_dlogq": {"bands": n_bands, "ms_per_batch": dq_dt * 1e3, "maps_per_s": count / dq_dt},
-            "note": "one problem per size, all sizes solved as one batch by wf_map_solve_many (each round one "
-                    "graph launch with a branch per size); a 2-iteration solve first tunes each shape"}
+            "note": "one problem per size, all sizes solved as one batch by wf_map_solve_many: each iteration "
+                    "is seven launches shared by the five sizes (every map on FFT-stage variant 2111), each "
+                    "round of 32 iterations one graph launch; a 2-iteration solve first sets up the solvers"}
 
 
 def run_alu_peaks():

@@ -341,12 +341,19 @@ wf_status wf_solver_history(const wf_problem* p, double* out, int* counts);
 /* MAP solves of several prepared problems at once, typically one per map
  * shape of a heterogeneous batch (Sec. 2.2; the simulations of Sec. 2.5 need
  * not share a size).  Every problem is started on its own internal stream,
- * ordered after opts->stream; then opts->check_every iterations of every
- * problem are captured in one CUDA graph with a parallel branch per problem,
- * so that each round of the batch is one graph launch (plain launches when
- * opts->use_graphs is 0) and one read of the active counts, until every map
- * of every problem has stopped.  Refreshes (opts->refresh_every) run between
- * rounds.  ps: HOST array of np distinct problems; s_out: HOST array of np
+ * ordered after opts->stream (first gradient).  When 2 to 8 problems share
+ * the precision and C and opts->fft_variant is 0, each L-BFGS iteration of
+ * the whole batch is one set of seven shared launches: every launch covers
+ * the blocks of every problem's own grid, each block running the
+ * single-problem kernel at its place in its problem's grid, on the FFT-stage
+ * variant 2111 for every problem (ping-pong column and row stages, widest
+ * tiles, plan 0; no tuning), so each map ends exactly where its problem
+ * solved alone with that variant ends.  Otherwise every problem is tuned and
+ * runs its own kernels, a parallel branch per problem.  opts->check_every
+ * iterations are captured in one CUDA graph, so that each round of the batch
+ * is one graph launch (plain launches when opts->use_graphs is 0) and one
+ * read of the active counts, until every map of every problem has stopped.
+ * Refreshes (opts->refresh_every) run between rounds, per problem.  ps: HOST array of np distinct problems; s_out: HOST array of np
  * device outputs (each [count][C][n][n/2+1] in its problem's working type);
  * stats: HOST array of np HOST arrays (each of its problem's count) or NULL.
  * Starts from 0.  Returns the worst status over all maps; synchronises. */

@@ -51,7 +51,7 @@ __device__ __forceinline__ long long wf_chk(long long i, long long lim, int line
     return cudaSuccess;                                                        \
   }
 #endif
-#define WF_DBG_TUS(X) X(ops_f32) X(ops_f64) X(lbcol_f32) X(lbcol_f64) X(lbrow_f32) X(lbrow_f64) X(solve) X(noalloc) X(bandpower)
+#define WF_DBG_TUS(X) X(ops_f32) X(ops_f64) X(lbcol_f32) X(lbcol_f64) X(lbrow_f32) X(lbrow_f64) X(solve) X(noalloc) X(bandpower) X(multi)
 #define WF_DBG_DECL(name) cudaError_t wf_dbg_read_##name(unsigned long long* out, int reset);
 WF_DBG_TUS(WF_DBG_DECL)
 
@@ -307,6 +307,34 @@ struct WfLbBufs {
   int inject_map;   // map whose tile copies are never issued (-1: none), see wf_opts
   long long spin_limit;  // bound of device waits, SM cycles
 };
+// Launches shared by several problems (wf_map_solve_many: one problem per map
+// shape of a heterogeneous batch).  Every problem keeps its own geometry,
+// buffers and L-BFGS state; a shared launch covers the blocks of every
+// problem's own grid, problem q's at blocks start[q] .. start[q+1] - 1, and
+// each block runs the single-problem kernel body at its coordinates in its
+// problem's grid, so that every map computes what it computes alone with the
+// same FFT-stage variant.  The problems share the working type and C.
+#define WF_MULTI_MAX 8
+struct WfMultiArgs {
+  int np;
+  WfGeo g[WF_MULTI_MAX];
+  WfBufs b[WF_MULTI_MAX];
+  WfLbBufs lb[WF_MULTI_MAX];
+};
+// FFT-stage variant the shared launches run (ping-pong inverse column and row
+// stages, widest tiles, radix plan 0).
+#define WF_MULTI_VARIANT 2111
+template <typename T>
+cudaError_t wf_launch_multi_comb(const WfMultiArgs& a, int mode, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_multi_colinv(const WfMultiArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_multi_row(const WfMultiArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_multi_colfwd(const WfMultiArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t wf_launch_multi_qdots(const WfMultiArgs& a, cudaStream_t st);
+
 template <typename T>
 cudaError_t wf_launch_lb_comb(const WfGeo& g, const WfBufs& b, const WfLbBufs& lb, int mode, cudaStream_t st);
 template <typename T>

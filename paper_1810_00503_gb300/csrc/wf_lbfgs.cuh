@@ -22,6 +22,15 @@
 #include "wf_tma.cuh"
 
 
+// Coordinates of a block in its problem's own launch grid: tile or chunk
+// group x of map y, in a grid of nx by ny (the map count).  A single-problem
+// launch takes them from blockIdx / gridDim; a launch shared by several
+// problems (wf_multi.cuh) from its table of problems.
+struct WfBlk {
+  int x, y, nx, ny;
+};
+__device__ __forceinline__ WfBlk wf_blk() { return WfBlk{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y}; }
+
 // Stage per-warp partial dot products: red[slot * NW + warp] (NW = warps of the block).
 __device__ __forceinline__ void wf_warp_stash(double v, double* red, int slot, int nw) {
 #pragma unroll
@@ -29,13 +38,13 @@ __device__ __forceinline__ void wf_warp_stash(double v, double* red, int slot, i
   if ((threadIdx.x & 31) == 0) red[slot * nw + (threadIdx.x >> 5)] = v;
 }
 
-// Sum the staged warp partials of slots [0, nslot) into part_b[ids[i] * maxblk + blockIdx.x].
+// Sum the staged warp partials of slots [0, nslot) into part_b[ids[i] * maxblk + bx].
 __device__ __forceinline__ void wf_flush_slots(const double* red, int nslot, int nw, const int* ids,
-                                               double* part_b, int maxblk) {
+                                               double* part_b, int maxblk, int bx) {
   for (int i = threadIdx.x; i < nslot; i += blockDim.x) {
     double acc = 0.0;
     for (int w = 0; w < nw; ++w) acc += red[i * nw + w];
-    part_b[(size_t)ids[i] * maxblk + blockIdx.x] = acc;
+    part_b[(size_t)ids[i] * maxblk + bx] = acc;
   }
 }
 
@@ -102,14 +111,14 @@ __device__ __forceinline__ double wf_vdotd(typename WfVec<T>::type a, typename W
 // Block sums of per-thread partial dot products pdot[slot][thread], one warp
 // per slot, accumulated in FP64 in a fixed order.
 __device__ __forceinline__ void wf_reduce_pdots(const float* pdot, int nslot, const int* ids, double* part_b,
-                                                int maxblk) {
+                                                int maxblk, int bx) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int k = wid; k < nslot; k += nw) {
     double v = 0.0;
     for (int i = lane; i < (int)blockDim.x; i += 32) v += (double)pdot[k * blockDim.x + i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) part_b[(size_t)ids[k] * maxblk + blockIdx.x] = v;
+    if (lane == 0) part_b[(size_t)ids[k] * maxblk + bx] = v;
   }
 }
 
@@ -133,14 +142,14 @@ constexpr size_t wf_comb_smem(int m) {
 #define WF_COMB_MINB 4
 #endif
 template <typename T>
-__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? WF_COMB_MINB : 2)
-k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
+__device__ __forceinline__ void wf_lb_comb(const WfGeo& g, const WfLbBufs& lb, double* part, int mode,
+                                           const WfBlk kb) {
   typedef typename WfVec<T>::type VT;
   constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW;
   extern __shared__ __align__(16) unsigned char wf_smem[];
   float* pdot = (float*)wf_smem;  // [2m + 1][threads], this thread's column only until the final sums
   __shared__ int ids[2 * WF_MAXM + 1];
-  const int b = blockIdx.y, tid = threadIdx.x;
+  const int b = kb.y, tid = threadIdx.x;
   const WfLbMap* M = lb.st + b;
   const int active = M->active;
   const double pa = M->pend_alpha;
@@ -155,7 +164,7 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
                     : (mode == WF_LB1_MATERIALIZE || unfolded >= wf_sfold(m)) ? unfolded : 0;  // into s now
   const bool full = (mode == WF_LB1_FULL);
   const size_t vsz = (size_t)g.C * g.n * g.h;  // complex values per map vector
-  const int h = g.h, B = gridDim.y;
+  const int h = g.h, B = kb.ny;
   const V2<T>* ring = (const V2<T>*)lb.ring;
   const int head = M->head;
   const int np = (mode == WF_LB1_MATERIALIZE) ? 0 : M->npairs;  // pairs of the direction and dots
@@ -174,7 +183,7 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   }
   const T dg = (T)M->dg;
   for (int cg = 0; cg < WF_STREAM_GROUP; ++cg) {
-    const size_t c0 = ((size_t)blockIdx.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
+    const size_t c0 = ((size_t)kb.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
     if (c0 >= vsz) break;
     const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
     VT* sv = (VT*)((V2<T>*)lb.s + (size_t)b * vsz + c0);
@@ -267,7 +276,12 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
   }
   if (mode == WF_LB1_MATERIALIZE) return;
   __syncthreads();
-  wf_reduce_pdots(pdot, nslot, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_reduce_pdots(pdot, nslot, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk, kb.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? WF_COMB_MINB : 2)
+k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
+  wf_lb_comb<T>(g, lb, part, mode, wf_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -275,18 +289,17 @@ k_lb_comb(WfGeo g, WfLbBufs lb, double* part, int mode) {
 // stored vectors per trip, over the same chunk groups as k_lb_comb.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? 4 : 2)
-k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
+__device__ __forceinline__ void wf_lb_qdots(const WfGeo& g, const WfLbBufs& lb, double* part, const WfBlk kb) {
   typedef typename WfVec<T>::type VT;
   constexpr int VW = WfVec<T>::VW, NV = WF_COMB_EPT / VW;
   extern __shared__ __align__(16) unsigned char wf_smem[];
   float* pdot = (float*)wf_smem;
   __shared__ int ids[WF_MAXM];
-  const int b = blockIdx.y, tid = threadIdx.x;
+  const int b = kb.y, tid = threadIdx.x;
   const WfLbMap* M = lb.st + b;
   if (!M->active) return;
   const size_t vsz = (size_t)g.C * g.n * g.h;
-  const int h = g.h, B = gridDim.y, m = lb.m;
+  const int h = g.h, B = kb.ny, m = lb.m;
   const V2<T>* ring = (const V2<T>*)lb.ring;
   const int nx = M->next, np = M->npairs, head = M->head;
   __shared__ const VT* qv[WF_MAXM];  // the stored Q other than q, newest first
@@ -303,7 +316,7 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
   for (int v = 0; v < nvec; ++v) pdot[v * WF_COMB_THREADS + tid] = 0.f;
   __syncthreads();
   for (int cg = 0; cg < WF_STREAM_GROUP; ++cg) {
-    const size_t c0 = ((size_t)blockIdx.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
+    const size_t c0 = ((size_t)kb.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
     if (c0 >= vsz) break;
     const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
     int u[NV];
@@ -351,7 +364,12 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
     }
   }
   __syncthreads();
-  wf_reduce_pdots(pdot, nvec, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_reduce_pdots(pdot, nvec, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk, kb.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(WF_COMB_THREADS, sizeof(T) == 4 ? 4 : 2)
+k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
+  wf_lb_qdots<T>(g, lb, part, wf_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -360,17 +378,24 @@ k_lb_qdots(WfGeo g, WfLbBufs lb, double* part) {
 // One block per column tile; KIND WF_COLINV_PP_K (ping-pong passes) or
 // WF_COLINV_INPLACE_K (in-place passes).
 template <typename T, int C, int KIND, int PLAN>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB_PLAN(T, PLAN))
-k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb) {
-  const int b = blockIdx.y;
+__device__ __forceinline__ void wf_lb_colinv(const WfGeo& g, const T* sp_, long long sp_stride, void* scratch_,
+                                             const void* tw_, const WfLbBufs& lb, const WfBlk kb) {
+  const int b = kb.y;
   const WfLbMap* M = lb.st + b;
   if (!M->active) return;
   const size_t vsz = (size_t)C * g.n * g.h;
-  const V2<T>* p = (const V2<T>*)lb.ring + ((size_t)M->next * gridDim.y + b) * vsz;
+  const V2<T>* p = (const V2<T>*)lb.ring + ((size_t)M->next * kb.ny + b) * vsz;
   if constexpr (KIND == WF_COLINV_PP_K)
-    wf_col_inv_pp<T, C, WF_IN_PK, PLAN>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
+    wf_col_inv_pp<T, C, WF_IN_PK, PLAN>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_,
+                                        kb.x * g.TC);
   else
-    wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_);
+    wf_col_inv_body<T, C, WF_IN_PK>(g, p, sp_ + (size_t)b * sp_stride, (V2<T>*)scratch_ + (size_t)b * vsz, tw_,
+                                    kb.x * g.TC);
+}
+template <typename T, int C, int KIND, int PLAN>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_PLAN(T, PLAN))
+k_lb_colinv(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, const void* tw_, WfLbBufs lb) {
+  wf_lb_colinv<T, C, KIND, PLAN>(g, sp_, sp_stride, scratch_, tw_, lb, wf_blk());
 }
 
 // Persistent inverse column stage with the next tile prefetched by TMA.
@@ -467,26 +492,25 @@ k_lb_colinv_tma(WfGeo g, const T* sp_, long long sp_stride, void* scratch_, cons
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
-k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, const void* tw_, WfLbBufs lb,
-            double* part) {
+__device__ __forceinline__ void wf_lb_colfwd(const WfGeo& g, const T* sp_, long long sp_stride, const void* scratch_,
+                                             const void* tw_, const WfLbBufs& lb, double* part, const WfBlk kb) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
-  const int b = blockIdx.y;
+  const int b = kb.y;
   const WfLbMap* M = lb.st + b;
   if (!M->active) return;
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
   const int n = g.n, h = g.h, lgn = g.lgn, TC = g.TC, lgTC = __ffs(TC) - 1, CT = C * TC;
-  const int kx0 = blockIdx.x * TC, tot = C * n * TC;
+  const int kx0 = kb.x * TC, tot = C * n * TC;
   const size_t vsz = (size_t)C * n * h;
-  const int B = gridDim.y, m = lb.m, nx = M->next;
+  const int B = kb.ny, m = lb.m, nx = M->next;
   const V2<T>* Pn = (const V2<T>*)lb.ring + ((size_t)nx * B + b) * vsz;
   V2<T>* Qn = (V2<T>*)lb.ring + ((size_t)(m + nx) * B + b) * vsz;
   const V2<T>* gv = (const V2<T>*)lb.g + (size_t)b * vsz;
   typedef WfAcc<T> A;
   A qq = 0, pq = 0, pp = 0, gq = 0, gp = 0;
   wf_col_fwd_front<T, C>(g, (const V2<T>*)scratch_ + (size_t)b * vsz, sp_ + (size_t)b * sp_stride, buf, s_tw,
-                         tw_);
+                         tw_, kx0);
   constexpr int EB = WF_EMAX;
   // element ii of this thread: packed row r = r0 + ii * rstep (rows c n + j of
   // the C channels), column kx0 + t, fixed for the thread (blockDim is a
@@ -536,7 +560,13 @@ k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, co
     ids[0] = WF_SLOT_QQ; ids[1] = WF_SLOT_PQ; ids[2] = WF_SLOT_PP; ids[3] = WF_SLOT_GQN; ids[4] = WF_SLOT_GPN;
   }
   __syncthreads();
-  wf_flush_slots(red, 5, WF_THREADS / 32, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk);
+  wf_flush_slots(red, 5, WF_THREADS / 32, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk, kb.x);
+}
+template <typename T, int C>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, const void* tw_, WfLbBufs lb,
+            double* part) {
+  wf_lb_colfwd<T, C>(g, sp_, sp_stride, scratch_, tw_, lb, part, wf_blk());
 }
 
 // Row stage of the Hessian-vector product for the maps still iterating.

@@ -352,11 +352,12 @@ __device__ __forceinline__ void wf_s2g(V2<T>* dst, const V2<T>* src, int tot) {
 // ---------------------------------------------------------------------------
 template <typename T, int C, int IN>
 __device__ __forceinline__ void wf_col_inv_body(const WfGeo& g, const V2<T>* src, const T* sp, V2<T>* scr,
-                                                const void* tw_) {
+                                                const void* tw_, int kx0 = -1) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
   V2<T>* s_tw = (V2<T>*)wf_smem;
   V2<T>* buf = s_tw + WF_NT;
-  const int n = g.n, lgTC = __ffs(g.TC) - 1, kx0 = blockIdx.x * g.TC;
+  const int n = g.n, lgTC = __ffs(g.TC) - 1;
+  if (kx0 < 0) kx0 = blockIdx.x * g.TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, g.lgn);
   wf_tile_load<T, C, IN>(buf, src, n, g.h, lgTC, kx0);
   __syncthreads();
@@ -376,11 +377,12 @@ k_col_inv(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* sc
 }
 
 // Forward column stage shared by the gradient and Hessian-vector epilogues:
-// scratch tile -> forward FFT along y -> sqrt(P) R^T / n, left in buf.
+// scratch tile at packed column kx0 -> forward FFT along y -> sqrt(P) R^T / n,
+// left in buf.
 template <typename T, int C>
 __device__ __forceinline__ void wf_col_fwd_front(const WfGeo& g, const V2<T>* scr, const T* sp, V2<T>* buf,
-                                                 V2<T>* s_tw, const void* tw_) {
-  const int n = g.n, lgTC = __ffs(g.TC) - 1, CT = C * g.TC, kx0 = blockIdx.x * g.TC;
+                                                 V2<T>* s_tw, const void* tw_, int kx0) {
+  const int n = g.n, lgTC = __ffs(g.TC) - 1, CT = C * g.TC;
   wf_stage_tw<T>(s_tw, (const V2<T>*)tw_, g.lgn);
   wf_tile_load<T, C, WF_IN_PK>(buf, scr, n, g.h, lgTC, kx0);
   __syncthreads();

@@ -215,14 +215,12 @@ __device__ double wf_wolfe_step(double d0, double c, double c1, double c2) {
 // One warp per map.  ITER: exact or Wolfe step along p, chi^2 and Gram-matrix
 // update of the new pair, convergence test, two-loop for the next direction.
 // REFRESH: true chi^2 and gradient dots after a full evaluation.
-__global__ void __launch_bounds__(32 * WF_SW)
-k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
+__device__ __forceinline__ void wf_lb_scalar(WfLbMap* st, const double* part, const WfScalarArgs& A, int b,
+                                             int* nact) {
   __shared__ double red[WF_SCAL_SLOTS][33];
   __shared__ double S[WF_SCAL_SLOTS];
   __shared__ int slots[WF_SCAL_SLOTS], cnt[WF_SCAL_SLOTS];
   const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x;
-  if (b >= B) return;
   WfLbMap& M = st[b];
   const double* pb = part + (size_t)b * WF_NSLOT * A.maxblk;
   const int m = A.m;
@@ -409,6 +407,32 @@ k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
     wf_two_loop(M, m, lane);
     if (lane == 0) atomicAdd(nact, 1);
   }
+}
+
+__global__ void __launch_bounds__(32 * WF_SW)
+k_lb_scalar(WfLbMap* st, const double* part, WfScalarArgs A, int B, int* nact) {
+  if ((int)blockIdx.x < B) wf_lb_scalar(st, part, A, blockIdx.x, nact);
+}
+
+// The scalar step of several problems in one launch (wf_map_solve_many): one
+// block (warp) per map of every problem, problem q's maps at blocks
+// start[q] .. start[q+1] - 1; and the zeroing of their active counters.
+struct WfMultiScalar {
+  int np;
+  int start[WF_MULTI_MAX + 1];
+  WfLbMap* st[WF_MULTI_MAX];
+  const double* part[WF_MULTI_MAX];
+  int* nact[WF_MULTI_MAX];
+  WfScalarArgs A[WF_MULTI_MAX];
+};
+__global__ void __launch_bounds__(32 * WF_SW) k_multi_scalar(const __grid_constant__ WfMultiScalar ms) {
+  const int bid = blockIdx.x;
+  int q = 0;
+  while (q + 1 < ms.np && bid >= ms.start[q + 1]) ++q;
+  wf_lb_scalar(ms.st[q], ms.part[q], ms.A[q], bid - ms.start[q], ms.nact[q]);
+}
+__global__ void k_multi_zero(const __grid_constant__ WfMultiScalar ms) {
+  if ((int)threadIdx.x < ms.np) *ms.nact[threadIdx.x] = 0;
 }
 
 // Final statistics from the closing true evaluation: [k, evals, status, chi2, gnorm_rel].
@@ -1297,13 +1321,39 @@ static cudaError_t any_refresh(wf_problem* p, cudaStream_t st) {
                                  : refresh<float>(p, wf_bufs(p), lb_bufs<float>(S), S->A, 0, S, st);
 }
 
+// One L-BFGS iteration of several problems in shared launches (see
+// WfMultiArgs): the five kernels of iteration() plus the active counters'
+// reset and the scalar step, seven launches whatever the number of problems.
+static_assert(WF_SW == 1, "the shared scalar launch takes one block per map");
+template <typename T>
+static cudaError_t multi_iteration(const WfMultiArgs& a, const WfMultiScalar& ms, cudaStream_t st) {
+  cudaError_t e = wf_launch_multi_comb<T>(a, WF_LB1_FULL, st);
+  if (e == cudaSuccess) e = wf_launch_multi_colinv<T>(a, st);
+  if (e == cudaSuccess) e = wf_launch_multi_row<T>(a, st);
+  if (e == cudaSuccess) e = wf_launch_multi_colfwd<T>(a, st);
+  if (e == cudaSuccess) e = wf_launch_multi_qdots<T>(a, st);
+  if (e == cudaSuccess) {
+    k_multi_zero<<<1, 32, 0, st>>>(ms);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_multi_scalar<<<ms.start[ms.np], 32 * WF_SW, 0, st>>>(ms);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 // Several problems (typically one per map shape of a heterogeneous batch)
-// solved as one batch: every problem is started on its own stream (tuning,
-// first gradient, one plain iteration), then check_every iterations of every
-// problem are captured in ONE CUDA graph, a parallel branch per problem, so
-// that each round is one graph launch for the whole batch; the maps of every
-// shape advance together and a problem whose maps have all stopped costs only
-// its kernels' early exits.  The host reads the active counts once per round.
+// solved as one batch.  Every problem is started on its own stream (first
+// gradient).  When the problems share the working type and C (and no FFT-stage
+// variant is forced), each iteration of the whole batch is seven shared
+// launches (multi_iteration), every problem on the default ping-pong variant
+// WF_MULTI_VARIANT (no tuning); otherwise each problem is tuned and runs its
+// own kernels, as a parallel branch per problem.  check_every iterations are
+// captured in one CUDA graph, so that each round is one graph launch for the
+// whole batch; the maps of every shape advance together and a problem whose
+// maps have all stopped costs only its blocks' early exits.  The host reads
+// the active counts once per round.
 extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_opts* opts, void* const* s_out,
                                        wf_solve_stats* const* stats) {
   if (!ps || np < 1 || !s_out) return wf_fail(WF_EINVAL, "wf_map_solve_many: null or empty arguments");
@@ -1334,6 +1384,14 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
   oi.stream = nullptr;  // every problem starts on its own internal stream
   oi.use_graphs = 0;    // the batch graph replaces the per-problem ones
   oi.inject_timeout_map = 0;
+  bool shared = np >= 2 && np <= WF_MULTI_MAX && o.fft_variant == 0;
+  for (int i = 1; i < np && shared; ++i) shared = ps[i]->precision == ps[0]->precision && ps[i]->C == ps[0]->C;
+  if (shared) oi.fft_variant = WF_MULTI_VARIANT;
+  const bool f64 = ps[0]->precision == WF_FP64;
+  WfMultiArgs ma;
+  WfMultiScalar ms;
+  memset(&ma, 0, sizeof ma);
+  memset(&ms, 0, sizeof ms);
   wf_status rs = WF_OK;
   for (int i = 0; i < np && rs == WF_OK; ++i) {
     rs = check_opts(ps[i], &oi);
@@ -1343,26 +1401,52 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
     if (e != cudaSuccess) { rs = wf_cuda_fail(e, "wf_map_solve_many: ordering"); break; }
     rs = ps[i]->precision == WF_FP64 ? start_impl<double>(ps[i], &oi, nullptr) : start_impl<float>(ps[i], &oi, nullptr);
   }
+  if (shared && rs == WF_OK) {
+    ma.np = ms.np = np;
+    ms.start[0] = 0;
+    for (int i = 0; i < np; ++i) {
+      WfSolver* S = ps[i]->solver;
+      ma.g[i] = ps[i]->g;
+      ma.b[i] = wf_bufs(ps[i]);
+      ma.lb[i] = lb_bufs<float>(S);
+      ms.st[i] = S->st;
+      ms.part[i] = ps[i]->part;
+      ms.nact[i] = S->nact;
+      ms.A[i] = S->A;
+      ms.start[i + 1] = ms.start[i] + ps[i]->count;
+    }
+  }
+  auto batch_iteration = [&](cudaStream_t s) -> cudaError_t {
+    return f64 ? multi_iteration<double>(ma, ms, s) : multi_iteration<float>(ma, ms, s);
+  };
   // one plain iteration of every problem (every kernel's attributes set outside
   // capture), then the batch stream waits for all of them
   for (int i = 0; i < np && rs == WF_OK; ++i) {
     WfSolver* S = ps[i]->solver;
-    e = any_iteration(ps[i], S->work);
+    e = shared ? cudaSuccess : any_iteration(ps[i], S->work);
     if (e == cudaSuccess) e = cudaEventRecord(ev[i], S->work);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, ev[i], 0);
     if (e != cudaSuccess) rs = wf_cuda_fail(e, "wf_map_solve_many: first iteration");
     S->iters += 1;
   }
+  if (shared && rs == WF_OK) {
+    e = batch_iteration(bs);
+    if (e != cudaSuccess) rs = wf_cuda_fail(e, "wf_map_solve_many: first iteration");
+  }
   if (rs == WF_OK && o.use_graphs) {
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[np], bs);
-    for (int i = 0; i < np && e == cudaSuccess; ++i) {  // a branch per problem, forked from and joined to bs
-      cudaStream_t si = ps[i]->solver->work;
-      e = cudaStreamWaitEvent(si, ev[np], 0);
-      for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = any_iteration(ps[i], si);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[i], si);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, ev[i], 0);
+    if (shared) {
+      for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = batch_iteration(bs);
+    } else {
+      if (e == cudaSuccess) e = cudaEventRecord(ev[np], bs);
+      for (int i = 0; i < np && e == cudaSuccess; ++i) {  // a branch per problem, forked from and joined to bs
+        cudaStream_t si = ps[i]->solver->work;
+        e = cudaStreamWaitEvent(si, ev[np], 0);
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = any_iteration(ps[i], si);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[i], si);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, ev[i], 0);
+      }
     }
     const cudaError_t ee = cudaStreamEndCapture(bs, &graph);
     if (e == cudaSuccess) e = ee;
@@ -1388,6 +1472,8 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
     if (rs != WF_OK) break;
     if (exec) {
       e = cudaGraphLaunch(exec, bs);
+    } else if (shared) {
+      for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = batch_iteration(bs);
     } else {
       for (int i = 0; i < np && e == cudaSuccess; ++i)
         for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = any_iteration(ps[i], bs);

@@ -194,15 +194,19 @@ __device__ __forceinline__ void wf_row_pp_prefetch_pix(const WfGeo& g, const T* 
   if (MODE == WF_ROW_DATA) wf_prefetch_rows(d + off, 1, 0, g.RB * g.nx * (int)sizeof(T));
 }
 
-// One block per row block (blockIdx.x) of map blockIdx.y.
+// Row block rb of map b, one block (by default blockIdx.x of map blockIdx.y).
 template <typename T, int MODE, int PLAN>
 __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const T* d, const T* w, double* part,
-                                          const void* tw_) {
+                                          const void* tw_, int b = -1, int rb = -1) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
-  wf_row_pp_prefetch_pix<T, MODE>(g, d, w, blockIdx.y, blockIdx.x);
+  if (b < 0) {
+    b = blockIdx.y;
+    rb = blockIdx.x;
+  }
+  wf_row_pp_prefetch_pix<T, MODE>(g, d, w, b, rb);
   wf_row_pp_tables<T, PLAN>(g, (V2<T>*)wf_smem, tw_);
   __syncthreads();
-  wf_row_pp_item<T, MODE, PLAN>(g, scratch, d, w, part, blockIdx.y, blockIdx.x);
+  wf_row_pp_item<T, MODE, PLAN>(g, scratch, d, w, part, b, rb);
 }
 
 // Kernels of the objective + gradient pass on the ping-pong stages.

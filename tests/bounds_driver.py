@@ -69,6 +69,20 @@ def main():
                 prob.step(5)
                 prob.finish()
                 prob.close()
+    # heterogeneous batches in shared launches (square and rectangular shapes)
+    for C in (1, 2):
+        for prec in ("fp64", "mixed"):
+            made = []
+            for i, (n, nx) in enumerate([(8, 8), (16, 64), (64, 16), (32, 32)]):
+                inp = synth.density_small(n, seed=i, nx=nx) if C == 1 else synth.shear_eb(n, seed=i, nx=nx)
+                made.append(make_problem([inp, inp], prec)[0])
+            try:
+                wf.solve_many(made, gtol_rel=0.0, max_iter=12, check_every=4, refresh_every=5)
+            except wf.WfError as e:
+                out.setdefault("solve_errors", []).append(["many", C, prec, str(e)[:80]])
+            runs += 1
+            for p in made:
+                p.close()
     torch.cuda.synchronize()
     count, first = wf.debug_bounds(mode=0)
     out.update(violations=count, first=first, solves=runs, worst_grad_rel=worst)
