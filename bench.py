@@ -180,7 +180,7 @@ def kernel_source_hash():
     import hashlib
     import re
     src = open(os.path.join(ROOT, "paper_1810_00503_gb300/csrc/wf_lbfgs.cuh")).read()
-    a = src.index("k_lb_comb(WfGeo g")
+    a = src.index("wf_lb_comb(const WfGeo& g")
     b = src.index("// ----", a)
     consts = open(os.path.join(ROOT, "paper_1810_00503_gb300/csrc/wf_internal.h")).read()
     keep = "\n".join(re.findall(r"#define WF_(?:COMB_\w+|STREAM_GROUP|MAXM)\b.*", consts))

@@ -144,7 +144,10 @@ typedef struct {
   double gnorm_rel;   /* final |g| / |g0| (true gradient) */
 } wf_solve_stats;
 
-/* Library handle: owns the twiddle tables for the current device and charges
+/* Library plumbing (the calls up to wf_opts_default have no counterpart in
+ * the paper; they manage devices, memory and errors for the calls that do).
+ *
+ * Library handle: owns the twiddle tables for the current device and charges
  * every device allocation of its problems, solvers and band-power runs to one
  * workspace.  workspace_limit: most device bytes the handle may hold at once
  * (0 = no limit); an allocation beyond it fails with WF_ENOMEM and the call
@@ -155,17 +158,20 @@ wf_status wf_create(wf_handle** out, size_t workspace_limit);
 wf_status wf_destroy(wf_handle* h);
 
 /* FFT-stage variant the problem's last solver start chose (wf_opts.fft_variant
- * encoding); before any start, the defaults. */
+ * encoding); before any start, the defaults.  Plumbing: how the transforms of
+ * Sec. 2.2's objective are executed, not what they compute. */
 wf_status wf_problem_variant(const wf_problem* p, int* variant);
 
-/* Device bytes the handle holds now (twiddle tables, problems, solver state). */
+/* Device bytes the handle holds now (twiddle tables, problems, solver state).
+ * Plumbing. */
 wf_status wf_workspace_used(const wf_handle* h, size_t* bytes);
 
 /* Message for the last failing call on this thread ("" if none).  The pointer
- * stays valid until the next call from the same thread. */
+ * stays valid until the next call from the same thread.  Plumbing. */
 const char* wf_last_error(void);
 
-/* Fill *o with the defaults listed in wf_opts. */
+/* Fill *o with the defaults listed in wf_opts (the solver settings of
+ * Sec. 2.2 and Sec. 3 the paper leaves open, as listed there). */
 void wf_opts_default(wf_opts* o);
 
 /* Prepare a batch of `count` maps of one shape (n, C) for repeated use:
@@ -200,10 +206,12 @@ wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, 
 wf_status wf_problem_create_rect(wf_handle* h, const wf_map* maps, int count, int ny, int nx, int C,
                                  int dtype, int precision, int lbfgs_m, void* stream,
                                  wf_problem** out);
+/* Free a problem and its solver state (synchronises the device).  Plumbing. */
 wf_status wf_problem_destroy(wf_problem* p);
 
 /* Replace the data maps d of every map (device [count][C][n][n], working
- * type); masked pixels are ignored.  Stream ordered, no synchronisation. */
+ * type; the d of Sec. 2.1's data model); masked pixels are ignored.  Stream
+ * ordered, no synchronisation. */
 wf_status wf_problem_set_data(wf_problem* p, const void* d, void* stream);
 
 /* One objective + gradient pass per map (Sec. 2.2, eq_chi and eq_cost):
@@ -224,8 +232,9 @@ wf_status wf_eval(wf_problem* p, const void* s, void* grad, double* chi2, void* 
 wf_status wf_problem_set_band_scale(wf_problem* p, const int16_t* band, const double* q, int n_b,
                                     void* stream);
 
-/* wf_eval plus the derivative of chi^2 with respect to the band amplitudes,
- * computed in the adjoint stage: dlogq[b][l] = d chi2_b / d log q_l
+/* wf_eval plus the derivative of chi^2 with respect to the band amplitudes
+ * q_l of Sec. 2.3 (eq. pilin), computed in the adjoint stage (Sec. 2.2,
+ * eq_cost): dlogq[b][l] = d chi2_b / d log q_l
  *   = -sum over the full-plane modes k of band l of Re(conj(a_k) s_k),
  * a = sqrt(P) R^T U W (d - x) at the current scale (divide by q_l for
  * d chi2 / d q_l).  band: device int16 [C][n][n/2+1]; dlogq: device double
@@ -238,7 +247,8 @@ wf_status wf_eval_bands(wf_problem* p, const void* s, void* grad, double* chi2, 
 wf_status wf_hess_vec(wf_problem* p, const void* v, void* hv, void* stream);
 
 /* Signal map x = A s_w for a whitened state (the Wiener-filtered map when s is
- * the MAP): s [count][C][n][n/2+1], x [count][C][n][n].  Stream ordered. */
+ * the MAP, Sec. 2.2: the field s of eq_chi in pixel space; App. C for E/B):
+ * s [count][C][n][n/2+1], x [count][C][n][n].  Stream ordered. */
 wf_status wf_signal_map(wf_problem* p, const void* s, void* x, void* stream);
 
 /* MAP solve of every map by L-BFGS with an exact line search (Sec. 2.2; the
@@ -318,7 +328,8 @@ wf_status wf_solver_state_size(const wf_problem* p, size_t* bytes);
 wf_status wf_solver_export(wf_problem* p, void* dst, size_t bytes);
 wf_status wf_solver_import(wf_problem* p, const void* src, size_t bytes, void* stream);
 
-/* Diagnostic: run n_iter more iterations of a started solve with plain
+/* Measurement hook, no counterpart in the paper (Sec. 2.2's iteration, timed
+ * kernel by kernel).  Runs n_iter more iterations of a started solve with plain
  * launches and CUDA events around each kernel on the working stream, and
  * store the average duration in milliseconds of the six kernels of an
  * iteration in ms (HOST float[6]): direction / state update / dot products,
@@ -472,8 +483,8 @@ typedef struct {
 wf_status bandpower_estimate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
                              const wf_bandpower_in* in, const wf_opts* opts, wf_bandpower_out* out,
                              wf_solve_stats* stats);
-/* The same on rectangular ny x nx maps (shapes as wf_problem_create_rect;
- * npix = C ny nx in the draw rule above). */
+/* The same on rectangular ny x nx maps (Sec. 2.4-2.5 as above; shapes as
+ * wf_problem_create_rect; npix = C ny nx in the draw rule above). */
 wf_status bandpower_estimate_rect(wf_handle* h, const wf_map* data, int ny, int nx, int C, int dtype,
                                   int precision, const wf_bandpower_in* in, const wf_opts* opts,
                                   wf_bandpower_out* out, wf_solve_stats* stats);
