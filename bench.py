@@ -379,7 +379,7 @@ def run_hetero(args, dev, count=256, n_bands=10, sizes=(64, 128, 256, 512, 1024)
         probs.append(prob)
         sizes.append((n, B))
     torch.cuda.synchronize()
-    wf.solve_many(probs, gtol_rel=1e-6, max_iter=2)  # the solvers' buffers and the kernels' attributes
+    wf.solve_many(probs, gtol_rel=1e-6, max_iter=2)  # tunes each size's tiles, sets up the solvers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = wf.solve_many(probs, gtol_rel=1e-6, max_iter=20000, check_every=32, refresh_every=200)
@@ -408,8 +408,8 @@ def run_hetero(args, dev, count=256, n_bands=10, sizes=(64, 128, 256, 512, 1024)
             "evals_per_s": evals / dt, "stop": "||g||/||g0|| < 1e-6", "statuses": statuses,
             "dchi2_dlogq": {"bands": n_bands, "ms_per_batch": dq_dt * 1e3, "maps_per_s": count / dq_dt},
             "note": "one problem per size, all sizes solved as one batch by wf_map_solve_many: each iteration "
-                    "is seven launches shared by the five sizes (every map on FFT-stage variant 2111), each "
-                    "round of 32 iterations one graph launch; a 2-iteration solve first sets up the solvers"}
+                    "is seven launches shared by the five sizes (ping-pong stages, tile widths tuned per size), each "
+                    "round of 32 iterations one graph launch; a 2-iteration solve first tunes and sets up the solvers"}
 
 
 def run_alu_peaks():

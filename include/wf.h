@@ -356,10 +356,11 @@ wf_status wf_solver_history(const wf_problem* p, double* out, int* counts);
  * the precision and C and opts->fft_variant is 0, each L-BFGS iteration of
  * the whole batch is one set of seven shared launches: every launch covers
  * the blocks of every problem's own grid, each block running the
- * single-problem kernel at its place in its problem's grid, on the FFT-stage
- * variant 2111 for every problem (ping-pong column and row stages, widest
- * tiles, plan 0; no tuning), so each map ends exactly where its problem
- * solved alone with that variant ends.  Otherwise every problem is tuned and
+ * single-problem kernel at its place in its problem's grid, every problem on
+ * the ping-pong column and row stages with radix plan 0 and its own tile
+ * widths (tuned per shape when opts->autotune, else the widest: variant
+ * 2111), so each map ends exactly where its problem solved alone with the
+ * variant its stats report ends.  Otherwise every problem is tuned and
  * runs its own kernels, a parallel branch per problem.  opts->check_every
  * iterations are captured in one CUDA graph, so that each round of the batch
  * is one graph launch (plain launches when opts->use_graphs is 0) and one

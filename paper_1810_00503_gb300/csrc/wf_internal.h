@@ -322,7 +322,8 @@ struct WfMultiArgs {
   WfLbBufs lb[WF_MULTI_MAX];
 };
 // FFT-stage variant the shared launches run (ping-pong inverse column and row
-// stages, widest tiles, radix plan 0).
+// stages, radix plan 0; the widest tiles here, the tile widths tuned per
+// problem when the solve autotunes).
 #define WF_MULTI_VARIANT 2111
 template <typename T>
 cudaError_t wf_launch_multi_comb(const WfMultiArgs& a, int mode, cudaStream_t st);

@@ -36,6 +36,8 @@ static inline bool wf_capturable(cudaStream_t s) {
 struct WfSolver {
   int m;
   int B;
+  int shared_tune;    // the next start tunes only what the shared launches can run
+
   void* s;
   void* g;
   void* ring;
@@ -673,11 +675,16 @@ __global__ void k_tune_state(WfLbMap* st, int B, int m) {
 // column tile width) are timed with the forward column stage, then the row
 // choices (row stage variant, radix plan and row block height) with those
 // fixed.  Results are cached in the handle per (ny, nx, C, precision,
-// history length, maps).
+// history length, maps).  For a problem of a batch in shared launches
+// (S->shared_tune) only the stage kinds and radix plan of those launches are
+// candidates (WF_MULTI_VARIANT), so only the tile widths are tuned; that
+// choice is cached apart.
 template <typename T>
 static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   const wf_opts* o = &S->o;
-  const WfGeo base = wf_make_geo(p->n, p->nx, p->C);
+  const bool shared = S->shared_tune != 0;
+  const WfGeo base = shared ? variant_geo(wf_make_geo(p->n, p->nx, p->C), WF_MULTI_VARIANT)
+                            : wf_make_geo(p->n, p->nx, p->C);
   if (o->fft_variant) {
     p->g = variant_geo(base, o->fft_variant);
     return WF_OK;
@@ -688,7 +695,8 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   }
   const int m = S->o.lbfgs_m;
   const long long key =
-      (((((long long)p->n * 2048 + p->nx) * 4 + p->C) * 2 + p->precision) * 64 + m) * 1000000LL + p->count;
+      ((((((long long)p->n * 2048 + p->nx) * 4 + p->C) * 2 + p->precision) * 64 + m) * 1000000LL + p->count) * 2 +
+      (shared ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(p->h->mu);
     auto it = p->h->tuned.find(key);
@@ -746,6 +754,7 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   for (int ck = WF_COLINV_TMA_K; ck <= WF_COLINV_INPLACE_K; ++ck)
     for (int cp = 0; cp < (ck == WF_COLINV_INPLACE_K ? 1 : WF_NPLAN); ++cp) {
       if (!plan_new(p->g.lgn, cp)) continue;
+      if (shared && (ck != base.colinv_kind || cp != base.col_plan)) continue;
       int last_tc = -1;
       for (int di : divs) {
         const WfGeo g = wf_geo_variant(base, ck, base.row_kind, di, 1, cp, 0);
@@ -764,6 +773,7 @@ static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   for (int rk = WF_ROW_PP_K; rk <= WF_ROW_INPLACE_K; ++rk)
     for (int rp = 0; rp < (rk == WF_ROW_INPLACE_K ? 1 : WF_NPLAN); ++rp) {
       if (!plan_new(p->g.lgh, rp)) continue;
+      if (shared && (rk != base.row_kind || rp != base.row_plan)) continue;
       int last_rb = -1;
       for (int di : divs) {
         const WfGeo g = wf_geo_variant(base, best.colinv_kind, rk, best.tc_div, di, best.col_plan, rp);
@@ -1347,9 +1357,9 @@ static cudaError_t multi_iteration(const WfMultiArgs& a, const WfMultiScalar& ms
 // solved as one batch.  Every problem is started on its own stream (first
 // gradient).  When the problems share the working type and C (and no FFT-stage
 // variant is forced), each iteration of the whole batch is seven shared
-// launches (multi_iteration), every problem on the default ping-pong variant
-// WF_MULTI_VARIANT (no tuning); otherwise each problem is tuned and runs its
-// own kernels, as a parallel branch per problem.  check_every iterations are
+// launches (multi_iteration), every problem on the ping-pong stages of
+// WF_MULTI_VARIANT with its own tuned tile widths; otherwise each problem is
+// tuned freely and runs its own kernels, as a parallel branch per problem.  check_every iterations are
 // captured in one CUDA graph, so that each round is one graph launch for the
 // whole batch; the maps of every shape advance together and a problem whose
 // maps have all stopped costs only its blocks' early exits.  The host reads
@@ -1386,7 +1396,6 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
   oi.inject_timeout_map = 0;
   bool shared = np >= 2 && np <= WF_MULTI_MAX && o.fft_variant == 0;
   for (int i = 1; i < np && shared; ++i) shared = ps[i]->precision == ps[0]->precision && ps[i]->C == ps[0]->C;
-  if (shared) oi.fft_variant = WF_MULTI_VARIANT;
   const bool f64 = ps[0]->precision == WF_FP64;
   WfMultiArgs ma;
   WfMultiScalar ms;
@@ -1399,7 +1408,9 @@ extern "C" wf_status wf_map_solve_many(wf_problem* const* ps, int np, const wf_o
     if (rs != WF_OK) break;
     e = cudaStreamWaitEvent(ps[i]->solver->stream, ev[np], 0);
     if (e != cudaSuccess) { rs = wf_cuda_fail(e, "wf_map_solve_many: ordering"); break; }
+    ps[i]->solver->shared_tune = shared ? 1 : 0;
     rs = ps[i]->precision == WF_FP64 ? start_impl<double>(ps[i], &oi, nullptr) : start_impl<float>(ps[i], &oi, nullptr);
+    ps[i]->solver->shared_tune = 0;
   }
   if (shared && rs == WF_OK) {
     ma.np = ms.np = np;
