@@ -27,7 +27,9 @@
  *   P            [C][n][n/2+1] real: variance of each unitary Fourier mode of
  *                the signal, >= 0; the kx = 0 and kx = n/2 columns must be
  *                symmetric under ky -> n - ky.
- * n is a power of two in [8, 1024]; C is 1 or 2.
+ * n is a power of two in [8, 1024]; C is 1 or 2.  The _rect calls take ny x nx
+ * maps instead (each side a power of two in [8, 1024]): read [n][n] as
+ * [ny][nx] and [n][n/2+1] as [ny][nx/2+1].
  *
  * Pointers.  Every array pointer is a DEVICE pointer owned by the caller,
  * unless stated otherwise; the library never frees a caller pointer nor keeps
@@ -201,8 +203,7 @@ wf_status wf_problem_create(wf_handle* h, const wf_map* maps, int count, int n, 
  * of App. C (C = 2) is evaluated on; P and the band tables are per mode and
  * so take any convention the caller chooses.  Every call on the problem
  * takes the rectangular shape (the solver, its checkpoints and
- * wf_map_solve_many included); wf_eval_noalloc and bandpower_iterate take
- * square maps only. */
+ * wf_map_solve_many included); wf_eval_noalloc takes square maps only. */
 wf_status wf_problem_create_rect(wf_handle* h, const wf_map* maps, int count, int ny, int nx, int C,
                                  int dtype, int precision, int lbfgs_m, void* stream,
                                  wf_problem** out);
@@ -398,6 +399,12 @@ wf_status wf_band_energy(wf_problem* p, const void* s, const int16_t* band,
  * [C][n][n/2+1], the same table for every channel.  Host only (no device
  * work); WF_EINVAL for bad sizes or edges that do not increase. */
 wf_status wf_band_table(int n, int C, const double* edges, int n_bands, double kscale, int16_t* out);
+/* The same for an ny x nx map of square pixels: mode (row j, column kx) has
+ * |k| = kscale * sqrt((kx N / nx)^2 + (ky N / ny)^2), N = max(ny, nx) (units
+ * of the fundamental of the longer side), so kscale = 2 pi / L for a longer
+ * side L; out: HOST [C][ny][nx/2+1].  Both sides even, at least 2. */
+wf_status wf_band_table_rect(int ny, int nx, int C, const double* edges, int n_bands, double kscale,
+                             int16_t* out);
 
 /* Inputs of the band-power estimator.  Pointers are DEVICE pointers except
  * sim_index.  The random fields z, noise and u are either all supplied by the
@@ -539,6 +546,12 @@ wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, int C, int 
                             const wf_bandpower_in* in, const wf_opts* opts, int n_iter, double q_min,
                             double q_max, void* P_out, double* theta_hat_hist, wf_bandpower_out* out,
                             wf_solve_stats* stats);
+/* The same on rectangular ny x nx maps (Sec. 2.3 and 2.5 as above; shapes as
+ * wf_problem_create_rect). */
+wf_status bandpower_iterate_rect(wf_handle* h, const wf_map* data, int ny, int nx, int C, int dtype, int precision,
+                                 const wf_bandpower_in* in, const wf_opts* opts, int n_iter, double q_min,
+                                 double q_max, void* P_out, double* theta_hat_hist, wf_bandpower_out* out,
+                                 wf_solve_stats* stats);
 
 /* Standard normal deviates on the device: out[k] = deviate offset + k of
  * (seed, stream_id), k < count, in dtype WF_F32 or WF_F64 (computed in FP64).

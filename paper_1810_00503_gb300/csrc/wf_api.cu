@@ -478,18 +478,22 @@ extern "C" wf_status wf_eval_bands(wf_problem* p, const void* s, void* grad, dou
   return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_eval_bands");
 }
 
-extern "C" wf_status wf_band_table(int n, int C, const double* edges, int n_bands, double kscale, int16_t* out) {
+extern "C" wf_status wf_band_table_rect(int ny, int nx, int C, const double* edges, int n_bands, double kscale,
+                                        int16_t* out) {
   if (!edges || !out) return wf_fail(WF_EINVAL, "wf_band_table: null argument");
-  if (n < 2 || (n & 1) || (C != 1 && C != 2)) return wf_fail(WF_EINVAL, "wf_band_table: n = %d, C = %d", n, C);
+  if (ny < 2 || (ny & 1) || nx < 2 || (nx & 1) || (C != 1 && C != 2))
+    return wf_fail(WF_EINVAL, "wf_band_table: %d x %d, C = %d", ny, nx, C);
   if (n_bands < 1 || n_bands > 32767) return wf_fail(WF_EINVAL, "wf_band_table: n_bands = %d", n_bands);
   if (!(kscale > 0.0)) return wf_fail(WF_EINVAL, "wf_band_table: kscale must be > 0");
   for (int l = 0; l < n_bands; ++l)
     if (!(edges[l] < edges[l + 1])) return wf_fail(WF_EINVAL, "wf_band_table: edges must increase");
-  const int h = n / 2;
-  for (int j = 0; j < n; ++j) {
-    const int ky = j < h ? j : j - n;
+  const int h = nx / 2, N = ny > nx ? ny : nx;
+  const double fx = (double)(N / nx), fy = (double)(N / ny);  // exact for power-of-two sides; 1 when square
+  for (int j = 0; j < ny; ++j) {
+    const int ky = j < ny / 2 ? j : j - ny;
     for (int kx = 0; kx <= h; ++kx) {
-      const double k = kscale * sqrt((double)kx * kx + (double)ky * ky);
+      const double qx = fx * kx, qy = fy * ky;
+      const double k = kscale * sqrt(qx * qx + qy * qy);
       int band = -1;
       if (k >= edges[0] && k < edges[n_bands]) {
         int lo = 0, hi = n_bands;  // edges[lo] <= k < edges[hi]
@@ -500,10 +504,14 @@ extern "C" wf_status wf_band_table(int n, int C, const double* edges, int n_band
         }
         band = lo;
       }
-      for (int c = 0; c < C; ++c) out[((size_t)c * n + j) * (h + 1) + kx] = (int16_t)band;
+      for (int c = 0; c < C; ++c) out[((size_t)c * ny + j) * (h + 1) + kx] = (int16_t)band;
     }
   }
   return WF_OK;
+}
+
+extern "C" wf_status wf_band_table(int n, int C, const double* edges, int n_bands, double kscale, int16_t* out) {
+  return wf_band_table_rect(n, n, C, edges, n_bands, kscale, out);
 }
 
 cudaError_t wf_dbg_selftest();

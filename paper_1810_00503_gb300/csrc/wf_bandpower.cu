@@ -568,19 +568,20 @@ __global__ void k_scale_bands(S* P, const int16_t* band, size_t tot, const doubl
   }
 }
 
-extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
-                                       const wf_bandpower_in* in, const wf_opts* opts, int n_iter, double q_min,
-                                       double q_max, void* P_out, double* theta_hat_hist, wf_bandpower_out* out,
-                                       wf_solve_stats* stats) {
+extern "C" wf_status bandpower_iterate_rect(wf_handle* h, const wf_map* data, int ny, int nx, int C, int dtype,
+                                            int precision, const wf_bandpower_in* in, const wf_opts* opts,
+                                            int n_iter, double q_min, double q_max, void* P_out,
+                                            double* theta_hat_hist, wf_bandpower_out* out, wf_solve_stats* stats) {
   if (!h || !data || !in || !out) return wf_fail(WF_EINVAL, "bandpower_iterate: null argument");
   if (n_iter < 1 || n_iter > 100) return wf_fail(WF_EINVAL, "bandpower_iterate: n_iter = %d outside [1, 100]", n_iter);
   if (!(q_min > 0.0 && q_min <= 1.0 && q_max >= 1.0 && isfinite(q_max)))
     return wf_fail(WF_EINVAL, "bandpower_iterate: need 0 < q_min <= 1 <= q_max (got %g, %g)", q_min, q_max);
   if (in->n_fd < 1) return wf_fail(WF_EINVAL, "bandpower_iterate: needs n_fd >= 1 (the Fisher matrix)");
   if (!data->P || !in->band) return wf_fail(WF_EINVAL, "bandpower_iterate: null P or band table");
-  if (n < 8 || n > WF_NT || (n & (n - 1)) || (C != 1 && C != 2))
-    return wf_fail(WF_EINVAL, "bandpower_iterate: n = %d, C = %d (n a power of two in [8, %d], C 1 or 2)", n, C,
-                   WF_NT);
+  if (ny < 8 || ny > WF_NT || (ny & (ny - 1)) || nx < 8 || nx > WF_NT || (nx & (nx - 1)) || (C != 1 && C != 2))
+    return wf_fail(WF_EINVAL,
+                   "bandpower_iterate: %d x %d maps, C = %d (each side a power of two in [8, %d], C 1 or 2)", ny,
+                   nx, C, WF_NT);
   if (dtype != WF_F32 && dtype != WF_F64) return wf_fail(WF_EINVAL, "bandpower_iterate: bad dtype");
   wf_opts o;
   if (opts) o = *opts;
@@ -588,7 +589,7 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
   cudaStream_t st = (cudaStream_t)o.stream;
   const int nb = in->n_bands;
   const size_t delt = dtype == WF_F64 ? 8 : 4;
-  const size_t nsp = (size_t)C * n * (n / 2 + 1);
+  const size_t nsp = (size_t)C * ny * (nx / 2 + 1);
   Scope sc(h);
   void* Pc = nullptr;
   double* qd = nullptr;
@@ -623,7 +624,7 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
   }
   wf_bandpower_out* ob = dev ? &hs : out;
   for (int it = 0; it < n_iter; ++it) {
-    const wf_status rs = bandpower_estimate(h, &m, n, C, dtype, precision, &inh, &o, ob, stats);
+    const wf_status rs = bandpower_estimate_rect(h, &m, ny, nx, C, dtype, precision, &inh, &o, ob, stats);
     if (rs != WF_OK && rs != WF_ENOTCONVERGED) return rs;
     if (rs != WF_OK) worst = rs;
     if (theta_hat_hist) memcpy(theta_hat_hist + (size_t)it * nb, ob->theta_hat, sizeof(double) * nb);
@@ -649,6 +650,14 @@ extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, 
   }
   if (worst != WF_OK) wf_fail(worst, "bandpower_iterate: a solve hit its iteration limit");
   return worst;
+}
+
+extern "C" wf_status bandpower_iterate(wf_handle* h, const wf_map* data, int n, int C, int dtype, int precision,
+                                       const wf_bandpower_in* in, const wf_opts* opts, int n_iter, double q_min,
+                                       double q_max, void* P_out, double* theta_hat_hist, wf_bandpower_out* out,
+                                       wf_solve_stats* stats) {
+  return bandpower_iterate_rect(h, data, n, n, C, dtype, precision, in, opts, n_iter, q_min, q_max, P_out,
+                                theta_hat_hist, out, stats);
 }
 
 WF_DBG_READER(bandpower)

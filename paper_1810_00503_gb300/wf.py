@@ -30,7 +30,7 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "bandpower_iterate", "wf_problem_variant", "wf_alu_peak", "wf_solver_history",
            "wf_map_solve_refined", "bandpower_sums_len", "bandpower_sums", "bandpower_combine",
            "wf_solver_state_size", "wf_solver_export", "wf_solver_import", "wf_debug_bounds",
-           "wf_problem_create_rect", "bandpower_estimate_rect"]
+           "wf_problem_create_rect", "bandpower_estimate_rect", "bandpower_iterate_rect", "wf_band_table_rect"]
 
 
 class WfMap(ctypes.Structure):
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
     L.wf_alu_peak.argtypes = [i, ctypes.POINTER(d)]
     L.wf_solver_history.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(i)]
     L.wf_band_table.argtypes = [i, i, ctypes.POINTER(d), i, d, vp]
+    L.wf_band_table_rect.argtypes = [i, i, i, ctypes.POINTER(d), i, d, vp]
     L.wf_destroy.argtypes = [vp]
     L.wf_opts_default.argtypes = [ctypes.POINTER(WfOpts)]
     L.wf_opts_default.restype = None
@@ -130,6 +131,9 @@ def lib() -> ctypes.CDLL:
     L.bandpower_iterate.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, ctypes.POINTER(WfBandpowerIn),
                                     ctypes.POINTER(WfOpts), i, d, d, vp, ctypes.POINTER(d),
                                     ctypes.POINTER(WfBandpowerOut), ctypes.POINTER(WfSolveStats)]
+    L.bandpower_iterate_rect.argtypes = [vp, ctypes.POINTER(WfMap), i, i, i, i, i, ctypes.POINTER(WfBandpowerIn),
+                                         ctypes.POINTER(WfOpts), i, d, d, vp, ctypes.POINTER(d),
+                                         ctypes.POINTER(WfBandpowerOut), ctypes.POINTER(WfSolveStats)]
     L.bandpower_sums.argtypes = [ctypes.POINTER(d), i, i, i, i, ctypes.POINTER(d)]
     L.bandpower_combine.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d),
                                     ctypes.POINTER(WfBandpowerIn), ctypes.POINTER(WfBandpowerOut)]
@@ -314,12 +318,14 @@ def alu_peak(dtype="f32"):
     return v.value
 
 
-def band_table(n, edges, C=1, kscale=1.0):
-    """wf_band_table: int16 numpy array (C, n, n/2+1) of band ids from |k| edges."""
+def band_table(n, edges, C=1, kscale=1.0, nx=None):
+    """wf_band_table (wf_band_table_rect with nx): int16 numpy array
+    (C, n, nx/2+1) of band ids from |k| edges (nx = n by default)."""
     e = np.ascontiguousarray(edges, dtype=np.float64)
-    out = np.empty((C, n, n // 2 + 1), dtype=np.int16)
-    _check(lib().wf_band_table(int(n), int(C), e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(e) - 1,
-                               float(kscale), out.ctypes.data))
+    nx = n if nx is None else nx
+    out = np.empty((C, n, nx // 2 + 1), dtype=np.int16)
+    _check(lib().wf_band_table_rect(int(n), int(nx), int(C), e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    len(e) - 1, float(kscale), out.ctypes.data))
     return out
 
 
@@ -442,16 +448,14 @@ def bandpower_iterate(d, mask, Ninv, P, band, n_bands, z, noise, u, n_iter=2, q_
     import torch
     a = _bandpower_args(d, mask, Ninv, P, band, n_bands, z, noise, u, precision, stream, n_sim, n_fd, sim_index,
                         opts, fd_bands, trunc, out_on_device, leak_split)
-    if a["nx"] != a["n"]:
-        raise ValueError("bandpower_iterate takes square maps (bandpower_estimate takes rectangular ones)")
     handle = handle or default_handle()
     hist = np.zeros((int(n_iter), a["nb"]))
     P_out = torch.empty_like(P)
-    status = lib().bandpower_iterate(handle.ptr, ctypes.byref(a["m"]), a["n"], a["C"], a["dt"], a["prec"],
-                                     ctypes.byref(a["bi"]), ctypes.byref(a["o"]), int(n_iter), float(q_min),
-                                     float(q_max), _ptr(P_out),
-                                     hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(a["bo"]),
-                                     a["st"])
+    status = lib().bandpower_iterate_rect(handle.ptr, ctypes.byref(a["m"]), a["n"], a["nx"], a["C"], a["dt"],
+                                          a["prec"], ctypes.byref(a["bi"]), ctypes.byref(a["o"]), int(n_iter),
+                                          float(q_min), float(q_max), _ptr(P_out),
+                                          hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          ctypes.byref(a["bo"]), a["st"])
     if status not in (0, 5):
         _check(status)
     res, stats = _bandpower_result(a)

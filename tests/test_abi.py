@@ -99,6 +99,29 @@ def test_band_table_from_edges_matches_brute_force():
         wf.band_table(16, [2.0, 1.0])
 
 
+def test_rect_band_table_uses_the_physical_wavevector():
+    """wf_band_table_rect against a loop over modes with the wavevector of a
+    mode of an ny x nx map of square pixels, N (mx / nx, my / ny) in units of
+    the longer side's fundamental, N = max(ny, nx)."""
+    ensure_lib()
+    import numpy as np
+    edges = np.array([1.1, 2.55, 4.05, 7.3, 11.2, 20.1])
+    for ny, nx, C, kscale in ((16, 64, 2, 1.0), (32, 8, 1, 0.5), (8, 8, 1, 1.0)):
+        got = wf.band_table(ny, edges, C=C, kscale=kscale, nx=nx)
+        N = max(ny, nx)
+        want = np.full((C, ny, nx // 2 + 1), -1, dtype=np.int16)
+        for j in range(ny):
+            my = j if j < ny // 2 else j - ny
+            for kx in range(nx // 2 + 1):
+                k = kscale * N * np.hypot(kx / nx, my / ny)
+                for lb in range(len(edges) - 1):
+                    if edges[lb] <= k < edges[lb + 1]:
+                        want[:, j, kx] = lb
+        assert np.array_equal(got, want), (ny, nx)
+    with pytest.raises(wf.WfError, match="EINVAL"):
+        wf.band_table(16, [1.0, 2.0], nx=7)
+
+
 def test_binding_refuses_host_tensors_before_any_call():
     """The binding hands raw data pointers to the library, which reads them as
     device memory: host tensors are refused before a handle or a call is made

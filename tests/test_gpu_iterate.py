@@ -238,3 +238,32 @@ def test_leakage_bias_arguments_checked():
         z = torch.zeros((2, 2, n, n), dtype=torch.float64, device="cuda")
         u = torch.zeros((2 * nb, 1, 2, n, n), dtype=torch.float64, device="cuda")
         wf.bandpower_estimate(*args, 2 * nb, z, z, u, leak_split=nb, precision="fp64", max_iter=5)
+
+
+def test_iterate_on_a_rectangular_map_matches_oracle_iteration():
+    """bandpower_iterate_rect on a 16 x 32 map: every estimate's Theta_hat and
+    the final fiducial as the oracle's iteration on the same grid."""
+    ny, nx, nb, J, nfd, n_iter = 16, 32, 3, 6, 3, 2
+    inp = synth.density_small(ny, seed=14, masked_frac=0.2, nx=nx)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, inp.P)
+    bands = synth.log_bands(ny, nb, nx=nx)
+    P0 = inp.P.copy()
+    for lb, f in enumerate((0.3, 1.0, 2.5)):
+        P0[bands == lb] *= f
+    rng = np.random.default_rng(6)
+    sig = np.where(inp.Ninv > 0, 1.0 / np.sqrt(np.where(inp.Ninv > 0, inp.Ninv, 1.0)), 0.0)
+    z = rng.standard_normal((J, 1, ny, nx))
+    nz = rng.standard_normal((J, 1, ny, nx)) * sig
+    u = rng.standard_normal((nb, nfd, 1, ny, nx))
+    dt, h1 = torch.float64, nx // 2 + 1
+    res, stats, hist, Pf = wf.bandpower_iterate(
+        to_dev(d, dt), to_dev(inp.mask, torch.uint8), to_dev(inp.Ninv, dt), to_dev(P0[..., :h1], dt),
+        to_dev(bands[..., :h1], torch.int16), nb, to_dev(z, dt), to_dev(nz, dt), to_dev(u, dt), n_iter=n_iter,
+        q_min=0.05, q_max=20.0, precision="fp64", gtol_rel=1e-12, max_iter=20000)
+    ref, Pref = O.bandpower_iterate(d, inp.mask, inp.Ninv, P0, bands, nb, z, nz, u, n_iter, q_min=0.05, q_max=20.0,
+                                    gtol_rel=1e-12, max_iter=20000)
+    for it in range(n_iter):
+        th = ref[it]["theta_hat"]
+        assert np.abs(hist[it] - th).max() <= 1e-7 * np.abs(th).max(), (it, hist[it], th)
+    assert np.abs(Pf.cpu().numpy() - Pref[..., :h1]).max() <= 1e-7 * np.abs(Pref).max()
+    assert all(s["status"] == "WF_OK" for s in stats)
