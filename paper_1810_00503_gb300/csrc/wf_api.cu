@@ -71,7 +71,7 @@ static void wf_geo_fix_kind(WfGeo& g) {
   if (g.colinv_kind == WF_COLINV_TMA_K && 2 * g.TC > 256) g.colinv_kind = WF_COLINV_PP_K;
 }
 
-WfGeo wf_make_geo(int ny, int nx, int C) {
+WfGeo wf_make_geo(int ny, int nx, int C, int B) {
   WfGeo g;
   g.n = ny;
   g.nx = nx;
@@ -87,8 +87,11 @@ WfGeo wf_make_geo(int ny, int nx, int C) {
   g.ksx = nx < ny ? ny / nx : 1;
   g.ksy = ny < nx ? nx / ny : 1;
   const long long vsz = (long long)C * ny * (nx / 2);
-  g.ncomb = (int)((vsz + WF_COMB_CHUNK - 1) / WF_COMB_CHUNK);
-  g.ncomb = (g.ncomb + WF_STREAM_GROUP - 1) / WF_STREAM_GROUP;
+  const int nchunk = (int)((vsz + WF_COMB_CHUNK - 1) / WF_COMB_CHUNK);
+  g.sgroup = WF_STREAM_GROUP;
+  if (B > 0)
+    while (g.sgroup > 1 && (long long)B * ((nchunk + g.sgroup - 1) / g.sgroup) < WF_STREAM_MIN_BLOCKS) g.sgroup /= 2;
+  g.ncomb = (nchunk + g.sgroup - 1) / g.sgroup;
   wf_geo_tiles(g, WF_TUNE_MAXDIV, WF_TUNE_MAXDIV);  // the narrowest tiles set the stride
   g.maxblk = g.ntile > g.nrb ? g.ntile : g.nrb;
   if (g.ncomb > g.maxblk) g.maxblk = g.ncomb;
@@ -300,7 +303,7 @@ extern "C" wf_status wf_problem_create_rect(wf_handle* h, const wf_map* maps, in
   p->dtype = dtype;
   p->precision = precision;
   p->m = lbfgs_m;
-  p->g = wf_make_geo(ny, nx, C);
+  p->g = wf_make_geo(ny, nx, C, count);
   p->elt = precision == WF_FP64 ? sizeof(double) : sizeof(float);
   int shared = 1;
   for (int i = 1; i < count; ++i) shared &= maps[i].P == maps[0].P;

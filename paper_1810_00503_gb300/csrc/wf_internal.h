@@ -101,10 +101,14 @@ __host__ __device__ inline int wf_plan_bits(int lgL, int plan, int p) {
 #define WF_COMB_THREADS 256
 #define WF_COMB_EPT 4
 #define WF_COMB_CHUNK (WF_COMB_THREADS * WF_COMB_EPT)
-// Chunks a streaming block walks in turn; one partial-sum entry per group.
+// Chunks a streaming block walks in turn (at most; one partial-sum entry per
+// group), and the fewest blocks a streaming launch should have: a small batch
+// takes fewer chunks per block, down to one, so that its launch still fills
+// the GPU (WfGeo.sgroup).
 #ifndef WF_STREAM_GROUP
 #define WF_STREAM_GROUP 8
 #endif
+#define WF_STREAM_MIN_BLOCKS 2048
 // FFT stages of the L-BFGS iteration on ping-pong passes with direct global
 // input/output (1) or on in-place shared-memory passes (0).
 #ifndef WF_FFT_PP
@@ -235,6 +239,7 @@ struct WfGeo {
   int TC, ntile;   // packed columns per column tile, tiles per map
   int RB, nrb;     // rows per row block (over the C*n rows), row blocks per map
   int ncomb;       // partial sums per map and slot of the streaming L-BFGS kernels
+  int sgroup;      // chunks a streaming block walks (WF_STREAM_GROUP, fewer for small batches)
   int maxblk;      // stride of the partial-sum slots: covers every tile choice
   int colinv_kind, row_kind;  // WF_COLINV_*_K, WF_ROW_*_K
   int tc_div, rb_div;         // TC and RB are the widest tile divided by these (1, 2, 4)
@@ -242,7 +247,8 @@ struct WfGeo {
 };
 
 // Widest tiles and the default kernel variants.
-WfGeo wf_make_geo(int ny, int nx, int C);
+// B: maps per launch, which sets the streaming kernels' chunk groups (0: many).
+WfGeo wf_make_geo(int ny, int nx, int C, int B = 0);
 inline WfGeo wf_make_geo(int n, int C) { return wf_make_geo(n, n, C); }
 // Blocks per map of the band reductions: about 4096 modes each, at most 64.
 inline int wf_band_nblk(const WfGeo& g) {

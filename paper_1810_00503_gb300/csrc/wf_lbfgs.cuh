@@ -130,7 +130,7 @@ constexpr size_t wf_comb_smem(int m) {
 }
 
 // ---------------------------------------------------------------------------
-// k_lb_comb: grid (ncomb, B).  A block walks WF_STREAM_GROUP consecutive
+// k_lb_comb: grid (ncomb, B).  A block walks g.sgroup consecutive
 // chunks of WF_COMB_CHUNK complex values of the map's packed vectors (fewer for
 // small maps), summing its partial dot products once at the end.  Each thread owns
 // WF_COMB_EPT complex values of the chunk; the stored vectors are read with
@@ -182,8 +182,8 @@ __device__ __forceinline__ void wf_lb_comb(const WfGeo& g, const WfLbBufs& lb, d
     }
   }
   const T dg = (T)M->dg;
-  for (int cg = 0; cg < WF_STREAM_GROUP; ++cg) {
-    const size_t c0 = ((size_t)kb.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
+  for (int cg = 0; cg < g.sgroup; ++cg) {
+    const size_t c0 = ((size_t)kb.x * g.sgroup + cg) * WF_COMB_CHUNK;
     if (c0 >= vsz) break;
     const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
     VT* sv = (VT*)((V2<T>*)lb.s + (size_t)b * vsz + c0);
@@ -315,8 +315,8 @@ __device__ __forceinline__ void wf_lb_qdots(const WfGeo& g, const WfLbBufs& lb, 
   }
   for (int v = 0; v < nvec; ++v) pdot[v * WF_COMB_THREADS + tid] = 0.f;
   __syncthreads();
-  for (int cg = 0; cg < WF_STREAM_GROUP; ++cg) {
-    const size_t c0 = ((size_t)kb.x * WF_STREAM_GROUP + cg) * WF_COMB_CHUNK;
+  for (int cg = 0; cg < g.sgroup; ++cg) {
+    const size_t c0 = ((size_t)kb.x * g.sgroup + cg) * WF_COMB_CHUNK;
     if (c0 >= vsz) break;
     const int clen = (int)((vsz - c0) < (size_t)WF_COMB_CHUNK ? (vsz - c0) : (size_t)WF_COMB_CHUNK);
     int u[NV];

@@ -683,8 +683,8 @@ template <typename T>
 static wf_status choose_variant(wf_problem* p, WfSolver* S, cudaStream_t st) {
   const wf_opts* o = &S->o;
   const bool shared = S->shared_tune != 0;
-  const WfGeo base = shared ? variant_geo(wf_make_geo(p->n, p->nx, p->C), WF_MULTI_VARIANT)
-                            : wf_make_geo(p->n, p->nx, p->C);
+  const WfGeo base = shared ? variant_geo(wf_make_geo(p->n, p->nx, p->C, p->count), WF_MULTI_VARIANT)
+                            : wf_make_geo(p->n, p->nx, p->C, p->count);
   if (o->fft_variant) {
     p->g = variant_geo(base, o->fft_variant);
     return WF_OK;
@@ -1081,7 +1081,7 @@ static wf_status refined_impl(wf_problem* p, const wf_opts* o, double tol, int m
   // The FP64 operator of the outer evaluations: for a MIXED problem on exact
   // FP64 copies of the working-precision inputs (the problem the inner solves
   // see), always on the default tiles.
-  const WfGeo go = wf_make_geo(p->n, p->nx, p->C);
+  const WfGeo go = wf_make_geo(p->n, p->nx, p->C, p->count);
   WfBufs bo = wf_bufs(p);
   if (mixed) {
     k_convert<float, double><<<wf_grid(per * B), 256, 0, st>>>((const float*)p->d, (double*)S->r_d64, per * B);
@@ -1599,7 +1599,7 @@ static wf_status import_impl(wf_problem* p, const WfStateHeader& hd, const char*
   cudaStream_t st = wf_capturable(us) ? us : S->stream;
   if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
   S->work = st;
-  p->g = variant_geo(wf_make_geo(p->n, p->nx, p->C), hd.variant);
+  p->g = variant_geo(wf_make_geo(p->n, p->nx, p->C, p->count), hd.variant);
   rs = setup_args(p, S, &S->o);
   if (rs != WF_OK) return rs;
   size_t off_st, off_vec;
