@@ -134,12 +134,23 @@ __host__ __device__ inline int wf_plan_bits(int lgL, int plan, int p) {
 // The same for the objective pass's forward column stage (k_col_fwd): its tile
 // and tables take 40 KB of shared memory, so four blocks fit, and at 64
 // registers it does not spill (1.67 against 1.73 ms for the 120 x 1024^2 pass;
-// five blocks, 48 registers: 1.76 ms).  The iteration's forward stage
-// (k_lb_colfwd) spills at 64 and keeps WF_MINB (0.68 against 0.77 ms).
+// five blocks, 48 registers: 1.76 ms).  The iteration's forward stage has its
+// own setting below.
 #ifndef WF_MINB_COLFWD32
 #define WF_MINB_COLFWD32 4
 #endif
 #define WF_MINB_COLFWD(T) (sizeof(T) == 4 ? WF_MINB_COLFWD32 : 1)
+// The iteration's forward column stage (k_lb_colfwd): blocks per SM, and the
+// groups its epilogue takes its rows of p and g in.  Four groups fit 64
+// registers without spills at four blocks per SM: 0.668 against 0.683 ms (one
+// group, 80 registers, three blocks) on 120 x 1024^2.
+#ifndef WF_MINB_LBCOLFWD32
+#define WF_MINB_LBCOLFWD32 4
+#endif
+#define WF_MINB_LBCOLFWD(T) (sizeof(T) == 4 ? WF_MINB_LBCOLFWD32 : 1)
+#ifndef WF_LBCF_SPLIT
+#define WF_LBCF_SPLIT 4
+#endif
 
 // Partial-sum slots per map (one FP64 value per block and slot).
 #define WF_MAXM 32

@@ -522,19 +522,24 @@ __device__ __forceinline__ void wf_lb_colfwd(const WfGeo& g, const T* sp_, long 
   const V2<T>* gb = gv + kx;
   V2<T>* Qb = Qn + kx;
   const int rows = C * n;
-  {
-    V2<T> pl[EB], gl[EB];
+  // the thread's EB rows in WF_LBCF_SPLIT groups: the loads of a group are
+  // issued together, and fewer values are live at once the more groups
+  constexpr int EG = EB / WF_LBCF_SPLIT;
 #pragma unroll
-    for (int ii = 0; ii < EB; ++ii) {
-      const int r = r0 + ii * rstep;
+  for (int g0 = 0; g0 < EB; g0 += EG) {
+    V2<T> pl[EG], gl[EG];
+#pragma unroll
+    for (int i = 0; i < EG; ++i) {
+      const int r = r0 + (g0 + i) * rstep;
       if (r < rows) {
-        pl[ii] = Pb[WF_CHK((size_t)r * h + kx, vsz) - kx];
-        gl[ii] = gb[WF_CHK((size_t)r * h + kx, vsz) - kx];
+        pl[i] = Pb[WF_CHK((size_t)r * h + kx, vsz) - kx];
+        gl[i] = gb[WF_CHK((size_t)r * h + kx, vsz) - kx];
       }
     }
 #pragma unroll
-    for (int ii = 0; ii < EB; ++ii) {
-      const int r = r0 + ii * rstep;
+    for (int i = 0; i < EG; ++i) {
+      const int ii = i;
+      const int r = r0 + (g0 + i) * rstep;
       if (r < rows) {
         const int j = r & (n - 1), c = r >> lgn;
         const V2<T> a = buf[wf_sw<T>(j * CT + c * TC + t)];
@@ -563,7 +568,7 @@ __device__ __forceinline__ void wf_lb_colfwd(const WfGeo& g, const T* sp_, long 
   wf_flush_slots(red, 5, WF_THREADS / 32, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk, kb.x);
 }
 template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_LBCOLFWD(T))
 k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, const void* tw_, WfLbBufs lb,
             double* part) {
   wf_lb_colfwd<T, C>(g, sp_, sp_stride, scratch_, tw_, lb, part, wf_blk());
