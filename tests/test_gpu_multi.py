@@ -82,3 +82,24 @@ def test_mixed_types_fall_back_to_a_branch_per_problem():
         assert all(s["status"] == "WF_OK" for s in r.stats), r.stats
     p1.close()
     p2.close()
+
+
+def test_more_problems_than_shared_slots_and_mixed_channels_fall_back():
+    """Nine problems (one more than a shared launch holds), and a pair with
+    different channel counts, run a branch per problem: every map still
+    solves, each problem on its own tuned variant."""
+    shapes = [(16, 16, 1)] * 9
+    made = _problems(shapes, 1, "fp64", seed=60)
+    res = wf.solve_many([p for p, _ in made], gtol_rel=1e-10, max_iter=20000)
+    for (p, host), r in zip(made, res):
+        assert all(s["status"] == "WF_OK" for s in r.stats), r.stats
+        zs = O.dense_wf_whitened(host["d"][0], host["W"][0], host["P"][0])
+        assert rel(r.s[0].cpu().numpy(), rfft_u(zs)) <= 1e-8
+        p.close()
+    (p1, _), = _problems([(32, 32, 1)], 1, "mixed", seed=70)
+    (p2, _), = _problems([(32, 64, 1)], 2, "mixed", seed=71)
+    res = wf.solve_many([p1, p2], gtol_rel=1e-6, max_iter=20000)
+    for r in res:
+        assert all(s["status"] == "WF_OK" for s in r.stats), r.stats
+    p1.close()
+    p2.close()

@@ -260,3 +260,29 @@ def test_rect_shapes_refused():
             wf.Problem(N * 0, torch.ones((ny, nx), dtype=torch.uint8, device="cuda"), N,
                        torch.ones((1, ny, nx // 2 + 1), dtype=dt, device="cuda"))
     del inp
+
+
+def test_bandpower_rect_mixed_matches_oracle_to_1e3():
+    """Mixed precision (FP32 fields, FP64 sums) on a 64 x 128 map with the
+    stated band-power tolerance of 1e-3."""
+    ny, nx, nb, J, nfd, seed = 64, 128, 4, 8, 3, 17
+    inp = synth.density_small(ny, seed=seed, masked_frac=0.25, nx=nx)
+    P = inp.P.astype(np.float32).astype(np.float64)
+    Ninv = inp.Ninv.astype(np.float32).astype(np.float64)
+    d = O.synthesize_data(inp.z, inp.noise, inp.mask, P).astype(np.float32).astype(np.float64)
+    bands = synth.log_bands(ny, nb, nx=nx)
+    rng = np.random.default_rng(seed + 100)
+    sig = np.where(Ninv > 0, 1.0 / np.sqrt(np.where(Ninv > 0, Ninv, 1.0)), 0.0)
+    z = rng.standard_normal((J, 1, ny, nx)).astype(np.float32).astype(np.float64)
+    nz = (rng.standard_normal((J, 1, ny, nx)) * sig).astype(np.float32).astype(np.float64)
+    u = rng.standard_normal((nb, nfd, 1, ny, nx)).astype(np.float32).astype(np.float64)
+    dt, h1 = torch.float32, nx // 2 + 1
+    res, stats = wf.bandpower_estimate(
+        to_dev(d, dt), to_dev(inp.mask, torch.uint8), to_dev(Ninv, dt), to_dev(P[..., :h1], dt),
+        to_dev(bands[..., :h1], torch.int16), nb, to_dev(z, dt), to_dev(nz, dt), to_dev(u, dt),
+        precision="mixed", gtol_rel=1e-7, max_iter=20000, refresh_every=50)
+    ref = O.bandpower_sims(d, inp.mask, Ninv, P, bands, nb, z, nz, u, gtol_rel=1e-12, max_iter=20000)
+    for k in ("E", "b", "F", "theta_hat"):
+        kk = {"b": "bias", "F": "fisher"}.get(k, k)
+        a, b = np.asarray(res[kk]), np.asarray(ref[k])
+        assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max(), (k, a, b)
