@@ -134,20 +134,22 @@ __host__ __device__ inline int wf_plan_bits(int lgL, int plan, int p) {
 // The same for the objective pass's forward column stage (k_col_fwd): its tile
 // and tables take 40 KB of shared memory, so four blocks fit, and at 64
 // registers it does not spill (1.67 against 1.73 ms for the 120 x 1024^2 pass;
-// five blocks, 48 registers: 1.76 ms).  The iteration's forward stage has its
-// own setting below.
+// five blocks, 48 registers: 1.76 ms).  Two channels keep three blocks (at 64
+// registers they spill).  The iteration's forward stage has its own setting
+// below.
 #ifndef WF_MINB_COLFWD32
 #define WF_MINB_COLFWD32 4
 #endif
-#define WF_MINB_COLFWD(T) (sizeof(T) == 4 ? WF_MINB_COLFWD32 : 1)
+#define WF_MINB_COLFWD(T, C) (sizeof(T) == 4 ? ((C) == 1 ? WF_MINB_COLFWD32 : WF_MINB32) : 1)
 // The iteration's forward column stage (k_lb_colfwd): blocks per SM, and the
 // groups its epilogue takes its rows of p and g in.  Four groups fit 64
 // registers without spills at four blocks per SM: 0.668 against 0.683 ms (one
-// group, 80 registers, three blocks) on 120 x 1024^2.
+// group, 80 registers, three blocks) on 120 x 1024^2.  Two channels (E/B) keep
+// three blocks, where 64 registers would spill.
 #ifndef WF_MINB_LBCOLFWD32
 #define WF_MINB_LBCOLFWD32 4
 #endif
-#define WF_MINB_LBCOLFWD(T) (sizeof(T) == 4 ? WF_MINB_LBCOLFWD32 : 1)
+#define WF_MINB_LBCOLFWD(T, C) (sizeof(T) == 4 ? ((C) == 1 ? WF_MINB_LBCOLFWD32 : WF_MINB32) : 1)
 #ifndef WF_LBCF_SPLIT
 #define WF_LBCF_SPLIT 4
 #endif

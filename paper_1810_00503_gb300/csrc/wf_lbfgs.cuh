@@ -568,7 +568,7 @@ __device__ __forceinline__ void wf_lb_colfwd(const WfGeo& g, const T* sp_, long 
   wf_flush_slots(red, 5, WF_THREADS / 32, ids, part + (size_t)b * WF_NSLOT * g.maxblk, g.maxblk, kb.x);
 }
 template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB_LBCOLFWD(T))
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_LBCOLFWD(T, C))
 k_lb_colfwd(WfGeo g, const T* sp_, long long sp_stride, const void* scratch_, const void* tw_, WfLbBufs lb,
             double* part) {
   wf_lb_colfwd<T, C>(g, sp_, sp_stride, scratch_, tw_, lb, part, wf_blk());

@@ -74,7 +74,7 @@ k_multi_row(const __grid_constant__ WfMultiGrid r, const __grid_constant__ WfMul
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB(T))
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_LBCOLFWD(T, C))
 k_multi_colfwd(const __grid_constant__ WfMultiGrid r, const __grid_constant__ WfMultiArgs a) {
   WfBlk kb;
   const int q = wf_multi_block(r, kb);

@@ -450,7 +450,7 @@ __device__ __forceinline__ void wf_col_fwd_out(const WfGeo& g, V2<T>* buf, const
 // neighbouring columns of the same rows, which a static round-robin loses.)
 // ---------------------------------------------------------------------------
 template <typename T, int C, int IN>
-__global__ void __launch_bounds__(WF_THREADS, WF_MINB_COLFWD(T))
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_COLFWD(T, C))
 k_col_fwd(WfGeo g, const void* src_, const T* sp_, long long sp_stride, const void* scratch_,
           void* dst_, double* part, const void* tw_) {
   extern __shared__ __align__(16) unsigned char wf_smem[];
