@@ -491,7 +491,7 @@ extern "C" wf_status wf_band_table_rect(int ny, int nx, int C, const double* edg
   for (int l = 0; l < n_bands; ++l)
     if (!(edges[l] < edges[l + 1])) return wf_fail(WF_EINVAL, "wf_band_table: edges must increase");
   const int h = nx / 2, N = ny > nx ? ny : nx;
-  const double fx = (double)(N / nx), fy = (double)(N / ny);  // exact for power-of-two sides; 1 when square
+  const double fx = (double)N / nx, fy = (double)N / ny;  // 1 when square
   for (int j = 0; j < ny; ++j) {
     const int ky = j < ny / 2 ? j : j - ny;
     for (int kx = 0; kx <= h; ++kx) {

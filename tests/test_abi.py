@@ -106,7 +106,7 @@ def test_rect_band_table_uses_the_physical_wavevector():
     ensure_lib()
     import numpy as np
     edges = np.array([1.1, 2.55, 4.05, 7.3, 11.2, 20.1])
-    for ny, nx, C, kscale in ((16, 64, 2, 1.0), (32, 8, 1, 0.5), (8, 8, 1, 1.0)):
+    for ny, nx, C, kscale in ((16, 64, 2, 1.0), (32, 8, 1, 0.5), (8, 8, 1, 1.0), (6, 10, 1, 1.0), (12, 8, 2, 0.7)):
         got = wf.band_table(ny, edges, C=C, kscale=kscale, nx=nx)
         N = max(ny, nx)
         want = np.full((C, ny, nx // 2 + 1), -1, dtype=np.int16)
