@@ -123,6 +123,12 @@ __host__ __device__ inline int wf_plan_bits(int lgL, int plan, int p) {
 #define WF_COLINV_TMA 1
 #endif
 
+// Items ahead whose rows the objective pass's persistent inverse column stage
+// asks L2 for (one: 1.70 ms per 120 x 1024^2 pass; two: 1.75; three: 1.77).
+#ifndef WF_COLINV_AHEAD
+#define WF_COLINV_AHEAD 1
+#endif
+
 // Resident blocks per SM requested from the compiler for the FFT-stage kernels.
 // FP32: three blocks of 256 threads (85 registers a thread; the radix-16 passes
 // spill a few hundred bytes to L1-resident local memory, and the extra resident

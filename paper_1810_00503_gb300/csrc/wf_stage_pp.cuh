@@ -226,14 +226,18 @@ k_col_inv_pp_pers(WfGeo g, const void* src_, const T* sp_, long long sp_stride, 
   const size_t sstride = (size_t)C * n * pitch;
   const int nitems = B * g.ntile;
   wf_stage_tw<T>((V2<T>*)wf_smem, (const V2<T>*)tw_, g.lgn, PLAN);
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int b = it / g.ntile, kx0 = (it - b * g.ntile) * g.TC;
-    const int nt = it + gridDim.x;
+  auto prefetch = [&](int nt) {
     if (nt < nitems) {
       const int nb = nt / g.ntile, nk = (nt - nb * g.ntile) * g.TC;
       wf_prefetch_rows((const V2<T>*)src_ + (size_t)nb * sstride + nk, C * n, (size_t)pitch * sizeof(V2<T>),
                        g.TC * (int)sizeof(V2<T>));
     }
+  };
+  // the tiles WF_COLINV_AHEAD items ahead are asked for (all of them at the start)
+  for (int a = 1; a < WF_COLINV_AHEAD; ++a) prefetch(blockIdx.x + a * gridDim.x);
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int b = it / g.ntile, kx0 = (it - b * g.ntile) * g.TC;
+    prefetch(it + WF_COLINV_AHEAD * gridDim.x);
     wf_col_inv_pp<T, C, IN, PLAN>(g, (const V2<T>*)src_ + (size_t)b * sstride, sp_ + (size_t)b * sp_stride,
                                   (V2<T>*)scratch_ + (size_t)b * C * n * h, tw_, kx0, false);
     __syncthreads();  // the next item's first pass rewrites the tiles this one's last pass read
