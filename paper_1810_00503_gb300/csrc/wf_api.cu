@@ -378,6 +378,7 @@ WfBufs wf_bufs(const wf_problem* p) {
   b.scratch = p->scratch;
   b.part = p->part;
   b.tw = p->precision == WF_FP64 ? p->h->tw64 : p->h->tw32;
+  b.ticket = p->flags + 2;  // flags[0] holds the input checks
   b.B = p->count;
   return b;
 }

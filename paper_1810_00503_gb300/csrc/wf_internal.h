@@ -123,6 +123,15 @@ __host__ __device__ inline int wf_plan_bits(int lgL, int plan, int p) {
 #define WF_COLINV_TMA 1
 #endif
 
+// Work queue for the objective pass's inverse column stage: the resident
+// blocks take (map, tile) items from an atomic counter, in order, each claiming
+// its next item before it transforms the current one and asking L2 for that
+// item's rows (1.63 ms per 120 x 1024^2 pass against 1.69 with the items taken
+// round-robin).
+#ifndef WF_COLINV_QUEUE
+#define WF_COLINV_QUEUE 1
+#endif
+
 // Items ahead whose rows the objective pass's persistent inverse column stage
 // asks L2 for (one: 1.70 ms per 120 x 1024^2 pass; two: 1.75; three: 1.77).
 #ifndef WF_COLINV_AHEAD
@@ -288,6 +297,8 @@ struct WfBufs {
   void* scratch;      // [B][C][ny][h] complex: between the column and row stages
   double* part;       // [B][WF_NSLOT][maxblk]
   const void* tw;     // twiddle table, WF_NT complex of type T
+  int* ticket;        // device counter of the objective pass's inverse column stage
+                      // work queue (nullptr: that stage runs its round-robin form)
   int B;
 };
 

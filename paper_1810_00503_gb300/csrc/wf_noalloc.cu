@@ -103,6 +103,7 @@ static wf_status noalloc_impl(unsigned char* base, const void* s, const void* d,
   b.scratch = base + off_scr;
   b.part = (double*)(base + off_part);
   b.tw = base + (sizeof(T) == 8 ? WF_NOALLOC_TW64 : WF_NOALLOC_TW32);
+  b.ticket = nullptr;
   b.B = count;
   e = wf_launch_eval<T>(g, b, WF_ROW_DATA, WF_IN_STD, s, grad, chi2, st);
   return e == cudaSuccess ? WF_OK : wf_cuda_fail(e, "wf_eval_noalloc");

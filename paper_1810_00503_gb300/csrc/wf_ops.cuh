@@ -444,10 +444,10 @@ __device__ __forceinline__ void wf_col_fwd_out(const WfGeo& g, V2<T>* buf, const
 // k_col_fwd: scratch tile -> forward FFT along y -> sqrt(P) R^T / n = a ->
 // out = 2 (src - a) (the gradient, or the Hessian-vector product when the row
 // stage ran without data); prior partial sum |src|^2 with half-plane weights.
-// One block per column tile.  (A persistent form, items taken in turn with the
-// next tile's rows prefetched, measured 1.01 ms against 0.69 ms on 120 x
-// 1024^2: the hardware's in-order block dispatch keeps the tiles in flight on
-// neighbouring columns of the same rows, which a static round-robin loses.)
+// One block per column tile.  (Persistent forms, the next tile's rows
+// prefetched, measured slower on 120 x 1024^2: items taken round-robin 1.01 ms
+// against 0.69 ms; items taken in order from an atomic counter, 2.00 ms for
+// the whole objective pass against 1.69 ms.)
 // ---------------------------------------------------------------------------
 template <typename T, int C, int IN>
 __global__ void __launch_bounds__(WF_THREADS, WF_MINB_COLFWD(T, C))

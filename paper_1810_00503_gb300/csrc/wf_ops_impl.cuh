@@ -63,6 +63,20 @@ inline cudaError_t items_grid(K k, size_t smem, int nitems, int* occ, int* nsm, 
 template <typename T, int C, int IN, int PLAN>
 cudaError_t col_inv_r(const WfGeo& g, const WfBufs& b, const void* src, cudaStream_t st) {
   static int done = 0;
+  if constexpr (WF_FFT_PP && WF_COLINV_QUEUE) {
+    if (b.ticket) {
+      static int occq[32] = {0}, nsmq[32] = {0}, doneq = 0;
+      auto k = k_col_inv_pp_q<T, C, IN, PLAN>;
+      const size_t sm = wf_pp_smem<T>();
+      cudaError_t e = ensure_smem(k, sm, &doneq);
+      int grid = 0;
+      if (e == cudaSuccess) e = items_grid(k, sm, g.ntile * b.B, occq, nsmq, &grid);
+      if (e == cudaSuccess) e = cudaMemsetAsync(b.ticket, 0, sizeof(int), st);
+      if (e != cudaSuccess) return e;
+      k<<<grid, WF_THREADS, sm, st>>>(g, src, (const T*)b.sp, b.sp_stride, b.scratch, b.tw, b.B, b.ticket);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (WF_FFT_PP) {
     static int occ[32] = {0}, nsm[32] = {0};
     auto k = k_col_inv_pp_pers<T, C, IN, PLAN>;

@@ -214,7 +214,8 @@ __device__ __forceinline__ void wf_row_pp(const WfGeo& g, V2<T>* scratch, const 
 // the (map, column tile) items in turn, and while a block transforms one tile
 // it asks L2 for the rows of the tile it takes next, so that the first pass of
 // that tile, which reads global memory directly, finds them there (0.51 ms
-// against 0.59 ms one block per tile on 120 x 1024^2).  The row stage runs one
+// against 0.59 ms one block per tile on 120 x 1024^2).  The objective pass
+// runs its work-queue form below when the problem has a counter for it.  The row stage runs one
 // block per row block (as k_row): its persistent form measured 0.59 against
 // 0.55 ms.
 template <typename T, int C, int IN, int PLAN>
@@ -241,6 +242,41 @@ k_col_inv_pp_pers(WfGeo g, const void* src_, const T* sp_, long long sp_stride, 
     wf_col_inv_pp<T, C, IN, PLAN>(g, (const V2<T>*)src_ + (size_t)b * sstride, sp_ + (size_t)b * sp_stride,
                                   (V2<T>*)scratch_ + (size_t)b * C * n * h, tw_, kx0, false);
     __syncthreads();  // the next item's first pass rewrites the tiles this one's last pass read
+  }
+}
+
+// The same stage on a work queue: items from the counter *ticket (zero at
+// launch), so the items in flight follow one another as under the hardware's
+// in-order block dispatch; a block claims its next item before transforming
+// the current one and asks L2 for that item's rows.
+template <typename T, int C, int IN, int PLAN>
+__global__ void __launch_bounds__(WF_THREADS, WF_MINB_PLAN(T, PLAN))
+k_col_inv_pp_q(WfGeo g, const void* src_, const T* sp_, long long sp_stride, void* scratch_, const void* tw_,
+               int B, int* ticket) {
+  extern __shared__ __align__(16) unsigned char wf_smem[];
+  __shared__ int s_item[2];
+  const int n = g.n, h = g.h, pitch = IN == WF_IN_PK ? h : h + 1;
+  const size_t sstride = (size_t)C * n * pitch;
+  const int nitems = B * g.ntile;
+  wf_stage_tw<T>((V2<T>*)wf_smem, (const V2<T>*)tw_, g.lgn, PLAN);
+  if (threadIdx.x == 0) s_item[0] = atomicAdd(ticket, 1);
+  __syncthreads();
+  int it = s_item[0], cur = 0;
+  while (it < nitems) {
+    if (threadIdx.x == 0) s_item[cur ^ 1] = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int nt = s_item[cur ^ 1];
+    if (nt < nitems) {
+      const int nb = nt / g.ntile, nk = (nt - nb * g.ntile) * g.TC;
+      wf_prefetch_rows((const V2<T>*)src_ + (size_t)nb * sstride + nk, C * n, (size_t)pitch * sizeof(V2<T>),
+                       g.TC * (int)sizeof(V2<T>));
+    }
+    const int b = it / g.ntile, kx0 = (it - b * g.ntile) * g.TC;
+    wf_col_inv_pp<T, C, IN, PLAN>(g, (const V2<T>*)src_ + (size_t)b * sstride, sp_ + (size_t)b * sp_stride,
+                                  (V2<T>*)scratch_ + (size_t)b * C * n * h, tw_, kx0, false);
+    __syncthreads();  // the next item's first pass rewrites the tiles this one's last pass read
+    it = nt;
+    cur ^= 1;
   }
 }
 
