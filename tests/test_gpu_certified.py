@@ -1,5 +1,5 @@
 """Certified accuracy of the MAP at the benchmarked configurations, with the
-oracle's gradient as the judge.
+oracle's FP64 gradient deciding the error bound.
 
 Certificate (Sec. 2.2 in whitened variables): the half-Hessian I + A^T W A of
 chi^2 has every eigenvalue >= 1, so for any state s the exact MAP s* satisfies
