@@ -600,6 +600,40 @@ wf_status wf_normal_draw(unsigned long long seed, unsigned int stream_id, unsign
 wf_status wf_eval_noalloc(const void* s, const void* d, const void* w, const void* P, int n, int C,
                           int count, int precision, double* chi2, void* grad, void* stream);
 
+/* Objective and gradient (Sec. 2.2, eq_chi and eq_cost; E/B rotation of
+ * App. C) on maps whose sides are not powers of two: ny rows by nx pixels,
+ * each side in [2, 1024] with no prime factor above 7 (e.g. 360, 640, 768,
+ * 1000), any parity.  The same chi2 and gradient as wf_eval, with the unitary
+ * DFT carrying (ny nx)^-1/2, the rotation at the wavevector (mx / nx, my / ny)
+ * of square pixels and its sine 0 on the Nyquist line of an even side, and
+ * the prior |s|^2 summed over the half plane with weight 1 on column 0 (and
+ * on column nx/2 when nx is even), 2 elsewhere.  With d = NULL the data term
+ * takes d = 0 and grad is the Hessian-vector product 2 (I + A^T W A) s
+ * (eq_curv), chi2 then s^T s + x^T W x.
+ * Stateless: no problem object, no solver (wf_problem_create_rect stays for
+ * powers of two, where the fused kernels, the solver and the band powers
+ * run).  DEVICE pointers, working type (double for WF_FP64, float for
+ * WF_MIXED; complex = two of them):
+ *   s     [count][C][ny][nx/2+1] complex   half-plane spectrum of real fields
+ *                                           (the kx = 0 and Nyquist columns
+ *                                           Hermitian, as rfft2 gives them)
+ *   d     [count][C][ny][nx] or NULL        data, finite everywhere
+ *   mask  uint8 [count][ny][nx]             1 = observed
+ *   Ninv  [count][C][ny][nx]                inverse noise variance, >= 0
+ *   P     [C][ny][nx/2+1]                   signal power per mode, >= 0, shared
+ *   grad  like s, chi2 double [count]       outputs
+ * Values are not checked.  Allocates its scratch (C ny (nx/2+1) complex per
+ * map plus partial sums) from the handle, synchronises the stream and frees
+ * it before returning.  Kernels: Stockham transforms with radix 4, 2, 3, 5 and
+ * 7 passes in shared memory, one kernel per stage (inverse column, row,
+ * forward column), partial sums added in a fixed order.
+ * Errors: WF_EINVAL (null pointer, s == grad, count < 1, C not 1 or 2, a side
+ * outside [2, 1024] or with a prime factor above 7, unknown precision),
+ * WF_ENOMEM, WF_ECUDA. */
+wf_status wf_eval_any(wf_handle* h, int count, int C, int ny, int nx, int precision, const void* d,
+                      const uint8_t* mask, const void* Ninv, const void* P, const void* s, void* grad,
+                      double* chi2, void* stream);
+
 /* Bounds-checked build (no counterpart in the paper; the failure handling of
  * the test plan).  A separate copy of this library compiled with
  * -DWF_DEBUG_BOUNDS checks every shared-memory tile index of the FFT stages

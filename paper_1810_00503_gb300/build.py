@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwf.so")
 SOURCES = ["wf_api.cu", "wf_solve.cu", "wf_ops_f32.cu", "wf_ops_f64.cu", "wf_lbcol_f32.cu", "wf_lbcol_f64.cu",
            "wf_lbrow_f32.cu", "wf_lbrow_f64.cu", "wf_noalloc.cu", "wf_bandpower.cu", "wf_rng.cu", "wf_peak.cu",
-           "wf_multi.cu"]
+           "wf_multi.cu", "wf_any.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

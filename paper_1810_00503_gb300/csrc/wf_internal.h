@@ -51,7 +51,7 @@ __device__ __forceinline__ long long wf_chk(long long i, long long lim, int line
     return cudaSuccess;                                                        \
   }
 #endif
-#define WF_DBG_TUS(X) X(ops_f32) X(ops_f64) X(lbcol_f32) X(lbcol_f64) X(lbrow_f32) X(lbrow_f64) X(solve) X(noalloc) X(bandpower) X(multi)
+#define WF_DBG_TUS(X) X(ops_f32) X(ops_f64) X(lbcol_f32) X(lbcol_f64) X(lbrow_f32) X(lbrow_f64) X(solve) X(noalloc) X(bandpower) X(multi) X(any)
 #define WF_DBG_DECL(name) cudaError_t wf_dbg_read_##name(unsigned long long* out, int reset);
 WF_DBG_TUS(WF_DBG_DECL)
 

@@ -30,7 +30,8 @@ EXPORTS = ["wf_create", "wf_destroy", "wf_last_error", "wf_opts_default", "wf_pr
            "bandpower_iterate", "wf_problem_variant", "wf_alu_peak", "wf_solver_history",
            "wf_map_solve_refined", "bandpower_sums_len", "bandpower_sums", "bandpower_combine",
            "wf_solver_state_size", "wf_solver_export", "wf_solver_import", "wf_debug_bounds",
-           "wf_problem_create_rect", "bandpower_estimate_rect", "bandpower_iterate_rect", "wf_band_table_rect"]
+           "wf_problem_create_rect", "bandpower_estimate_rect", "bandpower_iterate_rect", "wf_band_table_rect",
+           "wf_eval_any"]
 
 
 class WfMap(ctypes.Structure):
@@ -117,6 +118,7 @@ def lib() -> ctypes.CDLL:
     L.wf_solver_finish.argtypes = [vp, vp, vp, ctypes.POINTER(WfSolveStats)]
     L.wf_solver_profile.argtypes = [vp, i, ctypes.POINTER(ctypes.c_float)]
     L.wf_eval_noalloc.argtypes = [vp, vp, vp, vp, i, i, i, i, vp, vp, vp]
+    L.wf_eval_any.argtypes = [vp, i, i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp]
     L.wf_problem_set_band_scale.argtypes = [vp, vp, vp, i, vp]
     L.wf_eval_bands.argtypes = [vp, vp, vp, vp, vp, i, vp, vp]
     L.wf_map_solve_many.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(WfOpts), ctypes.POINTER(vp),
@@ -277,6 +279,60 @@ def eval_noalloc(s, d, w, P, chi2=None, grad=None, stream=None):
     precision = WF_FP64 if d.dtype == torch.float64 else WF_MIXED
     _check(lib().wf_eval_noalloc(_ptr(s), _ptr(d), _ptr(w), _ptr(P), n, C, B, precision, _ptr(chi2),
                                  _ptr(grad), _stream(stream)))
+    return chi2, grad
+
+
+def _any_check(s, mask, Ninv, P, d, chi2, grad, device):
+    """Argument rules of eval_any, checked before any pointer reaches the
+    library: Ninv (B, C, ny, nx) float32 or float64 sets the shape and the
+    working type; d like Ninv or None; mask uint8 (B, ny, nx); s and grad
+    (B, C, ny, nx/2+1) of the matching complex type; P (C, ny, nx/2+1) like
+    Ninv; chi2 float64 (B,); all contiguous and on `device`."""
+    import torch
+    if not isinstance(Ninv, torch.Tensor) or Ninv.dim() != 4 or Ninv.dtype not in (torch.float32, torch.float64):
+        raise ValueError("Ninv must be a float32 or float64 tensor of shape (B, C, ny, nx)")
+    B, C, ny, nx = Ninv.shape
+    cdt = torch.complex128 if Ninv.dtype == torch.float64 else torch.complex64
+    spec = (B, C, ny, nx // 2 + 1)
+    checks = [(Ninv, "Ninv", (B, C, ny, nx), Ninv.dtype), (mask, "mask", (B, ny, nx), torch.uint8),
+              (s, "s", spec, cdt), (grad, "grad", spec, cdt), (P, "P", (C, ny, nx // 2 + 1), Ninv.dtype),
+              (chi2, "chi2", (B,), torch.float64)]
+    if d is not None:
+        checks.append((d, "d", (B, C, ny, nx), Ninv.dtype))
+    for t, name, shape, dtype in checks:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a tensor")
+        if t.device != device:
+            raise ValueError(f"{name} is on {t.device}, the call runs on {device}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, the call needs {tuple(shape)}")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} has dtype {t.dtype}, the call needs {dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    return B, C, ny, nx
+
+
+def eval_any(s, mask, Ninv, P, d=None, handle=None, chi2=None, grad=None, stream=None):
+    """wf_eval_any: objective and gradient on ny x nx maps whose sides have no
+    prime factor above 7 (d None: the Hessian-vector product in grad).
+    s (B, C, ny, nx/2+1) complex, mask uint8 (B, ny, nx), Ninv and d
+    (B, C, ny, nx), P (C, ny, nx/2+1), all CUDA tensors of the working type
+    (float64: FP64, float32: mixed) on the current device.  Every tensor is
+    checked before the library is called.  Returns (chi2, grad)."""
+    import torch
+    if not isinstance(Ninv, torch.Tensor) or not Ninv.is_cuda:
+        raise TypeError("Ninv must be a CUDA tensor")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    grad = torch.empty_like(s) if grad is None else grad
+    chi2 = torch.empty(Ninv.shape[0], dtype=torch.float64, device=Ninv.device) if chi2 is None else chi2
+    B, C, ny, nx = _any_check(s, mask, Ninv, P, d, chi2, grad, dev)
+    if s.data_ptr() == grad.data_ptr():
+        raise ValueError("s and grad must not alias")
+    h = handle if handle is not None else default_handle()
+    precision = WF_FP64 if Ninv.dtype == torch.float64 else WF_MIXED
+    _check(lib().wf_eval_any(h.ptr, B, C, ny, nx, precision, _ptr(d), _ptr(mask), _ptr(Ninv), _ptr(P), _ptr(s),
+                             _ptr(grad), _ptr(chi2), _stream(stream)))
     return chi2, grad
 
 

@@ -3,8 +3,9 @@ in a child process with WF_LIB_PATH pointing at the bounds-checked library):
 tiny square maps of every size and rectangular ones of both aspects up to the
 extreme strips (8 x 1024, 1024 x 8), every channel count and precision,
 through every entry point that launches the FFT stages, and short solves
-under a covering set of FFT-stage variants; prints one JSON line with the
-violation count."""
+under a covering set of FFT-stage variants; the mixed-radix objective on
+sides that are not powers of two; prints one JSON line with the violation
+count."""
 import json
 import os
 import sys
@@ -83,6 +84,21 @@ def main():
             runs += 1
             for p in made:
                 p.close()
+    # the mixed-radix objective on sides that are not powers of two (odd and
+    # even sides, every radix, strips, the 1024 limit)
+    from tests.helpers import any_inputs
+    for ny, nx in [(2, 2), (3, 5), (7, 12), (30, 42), (96, 60), (343, 20), (1024, 6), (6, 1000)]:
+        for C in (1, 2):
+            for prec in ("fp64", "mixed"):
+                I = any_inputs(ny, nx, C, 2, seed=ny + nx)
+                wdt = torch.float64 if prec == "fp64" else torch.float32
+                cdt = torch.complex128 if prec == "fp64" else torch.complex64
+                s = to_dev(np.stack([rfft_u(f) for f in I["f"]]), cdt)
+                args = (to_dev(np.stack(I["mask"]), torch.uint8), to_dev(np.stack(I["Ninv"]), wdt),
+                        to_dev(np.ascontiguousarray(I["P"][..., : nx // 2 + 1]), wdt))
+                wf.eval_any(s, *args, d=to_dev(np.stack(I["d"]), wdt))
+                wf.eval_any(s, *args)
+                runs += 1
     torch.cuda.synchronize()
     count, first = wf.debug_bounds(mode=0)
     out.update(violations=count, first=first, solves=runs, worst_grad_rel=worst)

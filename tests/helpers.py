@@ -58,3 +58,29 @@ def make_problem(inputs, precision="fp64", d_list=None, lbfgs_m=10, shared_P=Tru
     prob = wf.Problem(d_t, M_t, N_t, P_t, precision=precision, lbfgs_m=lbfgs_m)
     host = dict(d=ds, Ninv=Ns, P=Ps, mask=Ms, W=[m[None] * N for m, N in zip(Ms, Ns)])
     return prob, host
+
+
+def any_inputs(ny, nx, C, B, seed):
+    """Seeded inputs on an ny x nx grid of any side lengths: real white fields
+    z, masks (about 30% masked), inverse noise variances in [0.5, 1.5), a
+    red power spectrum P ~ (|k| + 0.05)^-2 over the full plane (0 at k = 0;
+    the second channel at 0.3 of the first), data d = M (A z + n) from the
+    oracle, and the half-plane states s of independent white fields."""
+    from oracle import wf_oracle as O
+    rng = np.random.default_rng(seed)
+    my, mx = O.signed_modes(ny, nx)
+    k = np.sqrt((mx / nx) ** 2 + (my / ny) ** 2)
+    P1 = np.where(k > 0, 1.0 / (k + 0.05) ** 2, 0.0) / (ny * nx) ** 0.5
+    P = np.stack([P1, 0.3 * P1][:C])
+    out = dict(P=P, z=[], d=[], mask=[], Ninv=[], f=[])
+    for _ in range(B):
+        z = rng.standard_normal((C, ny, nx))
+        mask = (rng.random((ny, nx)) > 0.3).astype(np.uint8)
+        Ninv = rng.random((C, ny, nx)) + 0.5
+        noise = rng.standard_normal((C, ny, nx)) / np.sqrt(Ninv)
+        out["z"].append(z)
+        out["mask"].append(mask)
+        out["Ninv"].append(Ninv)
+        out["d"].append(O.synthesize_data(z, noise, mask, P))
+        out["f"].append(rng.standard_normal((C, ny, nx)))
+    return out

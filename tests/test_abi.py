@@ -278,3 +278,59 @@ def test_eval_noalloc_binding_checks_every_tensor_before_the_library(monkeypatch
             wf._noalloc_check(**{**good, name: t}, device=cpu)
     with pytest.raises(TypeError, match="CUDA"):  # host tensors never reach the library
         wf.eval_noalloc(good["s"], good["d"], good["w"], good["P"])
+
+
+def test_eval_any_refuses_bad_arguments_on_the_host():
+    """wf_eval_any checks its sizes, pointers and precision before it reads the
+    handle, allocates or calls CUDA (stand-in pointers are never touched)."""
+    L = ensure_lib()
+    buf, h, addr = _stand_ins()
+    other = ctypes.create_string_buffer(64)
+    g = ctypes.addressof(other)
+    ok = dict(h=h, B=1, C=1, ny=12, nx=20, prec=wf.WF_MIXED, d=addr, mask=addr, Ninv=addr, P=addr, s=addr, grad=g,
+              chi2=addr)
+    for bad, msg in [(dict(h=None), b"null"), (dict(mask=None), b"null"), (dict(chi2=None), b"null"),
+                     (dict(grad=addr), b"alias"), (dict(B=0), b"count"), (dict(C=3), b"C ="),
+                     (dict(prec=7), b"precision"), (dict(ny=11), b"prime factor"), (dict(nx=26), b"prime factor"),
+                     (dict(ny=1), b"prime factor"), (dict(nx=1050), b"prime factor"),
+                     (dict(ny=2048), b"prime factor")]:
+        a = {**ok, **bad}
+        st = L.wf_eval_any(a["h"], a["B"], a["C"], a["ny"], a["nx"], a["prec"], a["d"], a["mask"], a["Ninv"], a["P"],
+                           a["s"], a["grad"], a["chi2"], None)
+        assert st == 1 and msg in L.wf_last_error(), (bad, L.wf_last_error())
+
+
+def test_eval_any_binding_checks_every_tensor_before_the_library(monkeypatch):
+    """The binding hands eight raw pointers to wf_eval_any; each mismatch of
+    shape, dtype, layout or device raises before the library is reached."""
+    torch = pytest.importorskip("torch")
+
+    def no_lib():
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(wf, "lib", no_lib)
+    cpu = torch.device("cpu")
+    B, C, ny, nx = 2, 2, 12, 30
+    h1 = nx // 2 + 1
+    f32, c64 = torch.float32, torch.complex64
+    good = dict(s=torch.zeros(B, C, ny, h1, dtype=c64), mask=torch.zeros(B, ny, nx, dtype=torch.uint8),
+                Ninv=torch.zeros(B, C, ny, nx, dtype=f32), P=torch.zeros(C, ny, h1, dtype=f32),
+                d=torch.zeros(B, C, ny, nx, dtype=f32), chi2=torch.zeros(B, dtype=torch.float64),
+                grad=torch.zeros(B, C, ny, h1, dtype=c64))
+    assert wf._any_check(**good, device=cpu) == (B, C, ny, nx)
+    assert wf._any_check(**{**good, "d": None}, device=cpu) == (B, C, ny, nx)
+    bad = [("s", torch.zeros(B, C, ny, h1, dtype=torch.complex128), TypeError),
+           ("s", torch.zeros(B, C, ny, h1 - 1, dtype=c64), ValueError),
+           ("grad", torch.zeros(B + 1, C, ny, h1, dtype=c64), ValueError),
+           ("mask", torch.zeros(B, ny, nx, dtype=torch.bool), TypeError),
+           ("mask", torch.zeros(B, C, ny, nx, dtype=torch.uint8), ValueError),
+           ("d", torch.zeros(B, C, ny, nx, dtype=torch.float64), TypeError),
+           ("d", torch.zeros(B, C, ny, 2 * nx, dtype=f32)[..., ::2], ValueError),
+           ("P", torch.zeros(1, ny, h1, dtype=f32), ValueError),
+           ("chi2", torch.zeros(B, dtype=f32), TypeError),
+           ("s", torch.zeros(B, C, ny, h1, dtype=c64, device="meta"), ValueError)]
+    for name, t, exc in bad:
+        with pytest.raises(exc):
+            wf._any_check(**{**good, name: t}, device=cpu)
+    with pytest.raises(TypeError):
+        wf.eval_any(good["s"], good["mask"], good["Ninv"], good["P"])  # host tensors: refused before any call
