@@ -360,6 +360,44 @@ def run_eval_shapes(args, dev, hbm):
     return out
 
 
+def run_eval_any(dev, hbm, B=64, ny=768, nx=768, reps=10):
+    """wf_eval_any (the mixed-radix path for sides that are not powers of two)
+    on B maps of ny x nx in mixed precision, device-timed per call on its
+    stream; each call includes its scratch allocation, free and stream
+    synchronisation.  Algorithmic bytes: read s, d, the mask (1 byte a pixel)
+    and Ninv, write the gradient, and P once (shared by the maps)."""
+    import torch
+    from paper_1810_00503_gb300 import wf
+    g = torch.Generator(device=dev)
+    g.manual_seed(6)
+    h1 = nx // 2 + 1
+    s = torch.randn((B, 1, ny, h1), generator=g, device=dev, dtype=torch.complex64)
+    d = torch.randn((B, 1, ny, nx), generator=g, device=dev)
+    mask = (torch.rand((B, ny, nx), generator=g, device=dev) > 0.2).to(torch.uint8)
+    Ninv = torch.rand((B, 1, ny, nx), generator=g, device=dev) + 0.5
+    P = torch.rand((1, ny, h1), generator=g, device=dev)
+    grad = torch.empty_like(s)
+    chi2 = torch.empty(B, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            wf.eval_any(s, mask, Ninv, P, d=d, chi2=chi2, grad=grad, stream=stream)
+        e0.record(stream)
+        for _ in range(reps):
+            wf.eval_any(s, mask, Ninv, P, d=d, chi2=chi2, grad=grad, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    e, N, nh = 4, ny * nx, ny * h1
+    alg = B * (2 * e * nh + e * N + N + e * N + 2 * e * nh) + e * nh
+    achieved = alg / (ms / 1000.0) / 1e9
+    return {"evals_per_s": B * 1000.0 / ms, "ms_per_call": ms, "maps": B, "shape": [ny, nx],
+            "algorithmic_bytes_per_call": alg, "achieved_GBps": achieved, "frac": achieved / hbm,
+            "note": "wf_eval_any, mixed precision, radix 4 x 4 x 4 x 4 x 3 transforms; per call including its "
+                    "scratch allocation, free and synchronisation"}
+
+
 def run_hetero(args, dev, count=256, n_bands=10, sizes=(64, 128, 256, 512, 1024)):
     """Heterogeneous batch: `count` independent maps of n in {64, 128, 256,
     512, 1024} (uneven masks, noise levels and spectral slopes), one problem
@@ -788,6 +826,7 @@ def main():
         r["prob"].close()
         if not args.no_extra:
             line["eval_shapes"] = run_eval_shapes(args, dev, hbm)
+            line["eval_shapes"]["any_64x768"] = run_eval_any(dev, hbm)
         if not args.no_solves:
             line["map_solves"] = run_map_solves(args, dev)
         if not args.no_extra:
